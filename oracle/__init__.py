@@ -1,0 +1,167 @@
+"""FP64 CPU oracle for the dark-siren hierarchical log-likelihood (test infrastructure).
+
+This package is the independent reference that the CUDA library is checked against.
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the library never does.  The arithmetic lives in
+``gwc_oracle.cpp`` (plain C++17, FP64, libm, OpenMP over events); this module only
+compiles it with g++ and marshals numpy arrays through ctypes.
+
+Every function is pinned by the tests in ``tests/test_oracle_*.py`` (closed forms,
+unit normalisations, invariants, finite differences and a brute-force mpmath
+restatement); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+NP = 13
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gwc_oracle.cpp")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liborc.so`` (g++, -O2, no fast-math)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wno-unused-function", _SRC, "-o", _LIB + ".tmp"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class Inputs(ctypes.Structure):
+    _fields_ = [
+        ("n_events", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("offsets", ctypes.c_void_p),
+        ("m1", ctypes.c_void_p), ("m2", ctypes.c_void_p), ("dl", ctypes.c_void_p),
+        ("lnpe", ctypes.c_void_p), ("pix", ctypes.c_void_p),
+        ("n_pix", ctypes.c_int32), ("n_z", ctypes.c_int32), ("z_max", ctypes.c_double),
+        ("los", ctypes.c_void_p),
+        ("n_inj", ctypes.c_int64), ("n_draw", ctypes.c_double),
+        ("im1", ctypes.c_void_p), ("im2", ctypes.c_void_p), ("idl", ctypes.c_void_p),
+        ("ilnpd", ctypes.c_void_p),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            d, i32, i64, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+            L = _lib
+            L.orc_loglik.restype = ctypes.c_int
+            L.orc_loglik.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, d, d, i32,
+                                     vp, vp, vp, vp, vp, vp, vp]
+            for name, args in [("orc_E", [d, d]), ("orc_I", [d, d]), ("orc_D", [d, d]),
+                               ("orc_Dprime", [d, d]), ("orc_z_of_x", [d, d, d]),
+                               ("orc_S", [d, d, d]), ("orc_ln_p_m1", [d, vp]),
+                               ("orc_ln_p_m2", [d, d, vp]), ("orc_C", [d, vp]),
+                               ("orc_ln_Zm1", [vp]), ("orc_ln_psi", [d, vp]),
+                               ("orc_ln_Nz", [vp, vp, i32, d]), ("orc_rule_poly", [i32, i32])]:
+                fn = getattr(L, name)
+                fn.restype = d
+                fn.argtypes = args
+            L.orc_los_cell_f32.restype = i32
+            L.orc_los_cell_f32.argtypes = [ctypes.c_float, i32, d]
+            L.orc_ln_w_row.restype = ctypes.c_int
+            L.orc_ln_w_row.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, d, vp, vp]
+        return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _lam(lam):
+    a = np.ascontiguousarray(lam, dtype=np.float64)
+    assert a.shape[-1] == NP
+    return a
+
+
+def E(z, om): return lib().orc_E(z, om)
+def I(z, om): return lib().orc_I(z, om)
+def D(z, om): return lib().orc_D(z, om)
+def Dprime(z, om): return lib().orc_Dprime(z, om)
+def z_of_x(x, om, zmax=10.0): return lib().orc_z_of_x(x, om, zmax)
+def S(m, mmin, dm): return lib().orc_S(m, mmin, dm)
+def ln_p_m1(m1, lam): a = _lam(lam); return lib().orc_ln_p_m1(m1, _ptr(a))
+def ln_p_m2(m2, m1, lam): a = _lam(lam); return lib().orc_ln_p_m2(m2, m1, _ptr(a))
+def C(m1, lam): a = _lam(lam); return lib().orc_C(m1, _ptr(a))
+def ln_Zm1(lam): a = _lam(lam); return lib().orc_ln_Zm1(_ptr(a))
+def ln_psi(z, lam): a = _lam(lam); return lib().orc_ln_psi(z, _ptr(a))
+def rule_poly(k, which): return lib().orc_rule_poly(k, which)
+
+
+def ln_Nz(lam, pbar, zmax):
+    a = _lam(lam)
+    p = np.ascontiguousarray(pbar, dtype=np.float64)
+    return lib().orc_ln_Nz(_ptr(a), _ptr(p), len(p), zmax)
+
+
+def los_cell_f32(z, nz, zmax):
+    return lib().orc_los_cell_f32(ctypes.c_float(float(np.float32(z))), nz, zmax)
+
+
+def ln_w_row(lam, m1, m2, dl, lnpi, row, zmax, grad=False):
+    """Per-sample ln w against one LOS row (which also defines N_z); -inf where w = 0."""
+    a = _lam(lam)
+    f32 = lambda x: np.ascontiguousarray(x, dtype=np.float32)
+    m1, m2, dl, lnpi, row = f32(m1), f32(m2), f32(dl), f32(lnpi), f32(row)
+    n = len(m1)
+    out = np.empty(n, np.float64)
+    g = np.empty((n, NP), np.float64) if grad else None
+    rc = lib().orc_ln_w_row(_ptr(a), n, _ptr(m1), _ptr(m2), _ptr(dl), _ptr(lnpi), _ptr(row),
+                            len(row), zmax, _ptr(out), _ptr(g))
+    if rc != 0:
+        raise ValueError("Lambda outside its domain")
+    return (out, g) if grad else out
+
+
+def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads=0):
+    """Evaluate the whole likelihood for a Lambda batch ``lam`` [K, 13].
+
+    ``cat`` is a dict of numpy arrays with the keys produced by
+    ``paper_2605_23538_gb300.synth`` (offsets, m1, m2, dl, lnpe, pix, los, z_max,
+    inj_m1, inj_m2, inj_dl, inj_lnpd, n_draw).  Returns a dict of outputs.
+    """
+    lam = np.atleast_2d(_lam(lam))
+    K = lam.shape[0]
+    keep = {}
+
+    def arr(key, dt):
+        a = np.ascontiguousarray(cat[key], dtype=dt)
+        keep[key] = a
+        return _ptr(a)
+
+    los = np.ascontiguousarray(cat["los"], dtype=np.float32)
+    keep["los"] = los
+    n_ev = len(cat["offsets"]) - 1
+    inp = Inputs(n_events=n_ev, pad0=0, offsets=arr("offsets", np.int64),
+                 m1=arr("m1", np.float32), m2=arr("m2", np.float32), dl=arr("dl", np.float32),
+                 lnpe=arr("lnpe", np.float32), pix=arr("pix", np.int32),
+                 n_pix=los.shape[0], n_z=los.shape[1], z_max=float(cat["z_max"]),
+                 los=_ptr(los), n_inj=len(cat["inj_m1"]), n_draw=float(cat["n_draw"]),
+                 im1=arr("inj_m1", np.float32), im2=arr("inj_m2", np.float32),
+                 idl=arr("inj_dl", np.float32), ilnpd=arr("inj_lnpd", np.float32))
+    out = dict(lnL_event=np.empty((K, n_ev)), neff_event=np.empty((K, n_ev)),
+               ln_xi=np.empty(K), neff_sel=np.empty(K), lnL_total=np.empty(K),
+               flags=np.empty(K, np.int32), grad_total=np.zeros((K, NP)) if grad else None)
+    rc = lib().orc_loglik(ctypes.byref(inp), K, _ptr(lam), int(bool(grad)), neff_min_event,
+                          neff_min_sel, n_threads, _ptr(out["lnL_event"]), _ptr(out["neff_event"]),
+                          _ptr(out["ln_xi"]), _ptr(out["neff_sel"]), _ptr(out["lnL_total"]),
+                          _ptr(out["flags"]), _ptr(out["grad_total"]))
+    if rc != 0:
+        raise ValueError("oracle rejected the inputs")
+    if not grad:
+        del out["grad_total"]
+    return out

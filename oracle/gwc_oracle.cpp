@@ -1,0 +1,754 @@
+// gwc_oracle.cpp -- FP64 CPU oracle for the dark-siren hierarchical log-likelihood.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, independent restatement of
+// the method against which the CUDA library is checked.  Only the test suite, the
+// smoke check and the CPU-baseline leg of the benchmark load it.  The library never
+// calls it, and the two share no code, header, table or constant generator.
+//
+// What it computes, and the passage each step follows (Papadopoulos et al.,
+// "Scalable Dark Siren Cosmology with gwcosmo"):
+//   * Eq. 1: luminosity distance d_L(z) = (1+z) * int_0^z c dz'/H(z'),
+//     H(z) = H0 sqrt(Om (1+z)^3 + OL), read as flat LCDM (OL = 1 - Om, no radiation).
+//   * Eqs. 2-4: hierarchical likelihood; the selection function alpha(Lambda)
+//     (called xi here) enters as xi^-Ndet; a scale-free rate prior removes p(Ndet|Lambda).
+//   * Eq. hier_pixels (Sec. 2.1): each posterior sample carries its sky pixel; the
+//     pixel's line-of-sight (LOS) redshift prior multiplies the population model;
+//     detection does not depend on sky position, so the selection term uses the
+//     pixel-averaged LOS prior.
+//   * Eqs. 5-6: per-sample weights w = p_pop(z, theta'|Lambda) / pi_PE.  The Gaussian
+//     kernel of Eq. 5 is taken in its zero-width limit, so each event term is the
+//     Monte-Carlo mean of w over the event's samples.
+//   * Eq. 7: effective sample size (sum w)^2 / sum w^2, applied per event.
+// The mass model (power law + Gaussian peak, low-mass smoothing) and the
+// Madau-Dickinson rate are named but not written out in the paper; the standard
+// population-literature definitions are used (see the functions below).
+//
+// Numerics are deliberately direct: every integral is an adaptive Gauss-Kronrod
+// quadrature of its own definition, z(d_L) is a safeguarded Newton root of
+// D(z) = x, and sums over samples are explicit logsumexp's in FP64.  Gradients are
+// exact forward-mode derivatives of the same code (13-component dual numbers), with
+// the root's derivative taken by one Newton step from the converged root (implicit
+// function theorem).
+//
+// Parity status: every function here is pinned by tests of closed forms, invariants,
+// unit normalisations and brute force (tests/test_oracle_*.py); none is "unpinned".
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr int NP = 13;                       // hyperparameters per Lambda point
+constexpr double C_KMS = 299792.458;         // speed of light [km/s]
+constexpr double NEG_INF = -std::numeric_limits<double>::infinity();
+constexpr double LN_SQRT_2PI = 0.91893853320467274178032973640562;
+
+// Lambda layout: [H0, Om, alpha, beta, m_min, m_max, delta_m, mu_g, sigma_g,
+//                 lambda_peak, gamma, kappa, z_p]
+enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
+
+// ---------------------------------------------------------------- dual numbers
+struct Dual {
+  double v;
+  double d[NP];
+  Dual() : v(0.0) { for (int i = 0; i < NP; ++i) d[i] = 0.0; }
+  Dual(double c) : v(c) { for (int i = 0; i < NP; ++i) d[i] = 0.0; }  // NOLINT: implicit on purpose
+};
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v + b.v;
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v - b.v;
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a) {
+  Dual r; r.v = -a.v;
+  for (int i = 0; i < NP; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v * b.v;
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v / b.v;
+  for (int i = 0; i < NP; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+  return r;
+}
+inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+inline Dual operator+(double a, const Dual& b) { Dual r = b; r.v += a; return r; }
+inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
+inline Dual operator-(double a, const Dual& b) { Dual r = -b; r.v += a; return r; }
+inline Dual operator*(const Dual& a, double b) {
+  Dual r; r.v = a.v * b;
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+inline Dual operator*(double a, const Dual& b) { return b * a; }
+inline Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
+inline Dual operator/(double a, const Dual& b) { return Dual(a) / b; }
+
+// f(a) with f(a.v) = fv and f'(a.v) = dfv
+inline Dual chain(const Dual& a, double fv, double dfv) {
+  Dual r; r.v = fv;
+  for (int i = 0; i < NP; ++i) r.d[i] = dfv * a.d[i];
+  return r;
+}
+
+inline double fexp(double x) { return std::exp(x); }
+inline double flog(double x) { return std::log(x); }
+inline double flog1p(double x) { return std::log1p(x); }
+inline double fsqrt(double x) { return std::sqrt(x); }
+inline double ferf(double x) { return std::erf(x); }
+inline Dual fexp(const Dual& a) { const double e = std::exp(a.v); return chain(a, e, e); }
+inline Dual flog(const Dual& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
+inline Dual flog1p(const Dual& a) { return chain(a, std::log1p(a.v), 1.0 / (1.0 + a.v)); }
+inline Dual fsqrt(const Dual& a) { const double s = std::sqrt(a.v); return chain(a, s, 0.5 / s); }
+inline Dual ferf(const Dual& a) {
+  return chain(a, std::erf(a.v), 1.12837916709551257389615890312154 * std::exp(-a.v * a.v));
+}
+// ln(1 + e^a), stable for either sign of a
+template <class T> T softplus(const T& a) {
+  if (val(a) > 0.0) return a + flog1p(fexp(-a));
+  return flog1p(fexp(a));
+}
+
+// component access used by the quadrature's convergence test
+inline int ncomp(double) { return 1; }
+inline int ncomp(const Dual&) { return NP + 1; }
+inline double comp(double x, int) { return x; }
+inline double comp(const Dual& x, int i) { return i == 0 ? x.v : x.d[i - 1]; }
+inline double cabs_comp(double x, int) { return std::fabs(x); }
+inline double cabs_comp(const Dual& x, int i) { return std::fabs(comp(x, i)); }
+
+// ------------------------------------------------------ adaptive Gauss-Kronrod
+// Kronrod's 15-point extension of the 7-point Gauss-Legendre rule on [-1, 1]
+// (abscissae in decreasing order; the Gauss nodes are the odd-indexed ones and 0).
+const double XGK[8] = {
+    0.991455371120812639206854697526329, 0.949107912342758524526189684047851,
+    0.864864423359769072789712788640926, 0.741531185599394439863864773280788,
+    0.586087235467691130294144845693013, 0.405845151377397166906606412076961,
+    0.207784955007898467600689403773245, 0.000000000000000000000000000000000};
+const double WGK[8] = {
+    0.022935322010529224963732008058970, 0.063092092629978553290700663189204,
+    0.104790010322250183839876322541518, 0.140653259715525918745189590510238,
+    0.169004726639267902826583426598550, 0.190350578064785409913256402421014,
+    0.204432940075298892414161999234649, 0.209482141084727828012999174891714};
+const double WG[4] = {
+    0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
+    0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
+
+constexpr int NC_MAX = NP + 1;
+
+template <class T, class F>
+void gk15(const F& f, const T& a, const T& b, T& K, T& G, double* kabs) {
+  const T c = (a + b) * 0.5;
+  const T h = (b - a) * 0.5;
+  const T fc = f(c);
+  K = fc * WGK[7];
+  G = fc * WG[3];
+  const int nc = ncomp(K);
+  for (int i = 0; i < nc; ++i) kabs[i] = WGK[7] * cabs_comp(fc, i);
+  for (int j = 0; j < 7; ++j) {
+    const T dx = h * XGK[j];
+    const T f1 = f(c - dx);
+    const T f2 = f(c + dx);
+    K = K + (f1 + f2) * WGK[j];
+    if (j % 2 == 1) G = G + (f1 + f2) * WG[j / 2];
+    for (int i = 0; i < nc; ++i) kabs[i] += WGK[j] * (cabs_comp(f1, i) + cabs_comp(f2, i));
+  }
+  K = K * h;
+  G = G * h;
+  const double hv = std::fabs(val(h));
+  for (int i = 0; i < nc; ++i) kabs[i] *= hv;
+}
+
+template <class T, class F>
+T adapt_rec(const F& f, const T& a, const T& b, double rtol, const double* atol_density, int depth) {
+  T K, G;
+  double kabs[NC_MAX];
+  gk15(f, a, b, K, G, kabs);
+  const double w = std::fabs(val(b) - val(a));
+  bool ok = true;
+  for (int i = 0; i < ncomp(K) && ok; ++i) {
+    const double err = std::fabs(comp(K, i) - comp(G, i));
+    ok = err <= rtol * std::fabs(comp(K, i)) + atol_density[i] * w;
+  }
+  if (ok || depth >= 40) return K;
+  const T m = (a + b) * 0.5;
+  return adapt_rec(f, a, m, rtol, atol_density, depth + 1) +
+         adapt_rec(f, m, b, rtol, atol_density, depth + 1);
+}
+
+// int_a^b f, to relative tolerance rtol of the integral of |f| (per component).
+template <class T, class F>
+T integrate(const F& f, const T& a, const T& b, double rtol) {
+  if (!(val(b) > val(a))) return (b - a) * f(a);  // zero-width: keeps the Leibniz term
+  T K, G;
+  double kabs[NC_MAX], atol_density[NC_MAX];
+  gk15(f, a, b, K, G, kabs);
+  const double w = val(b) - val(a);
+  for (int i = 0; i < ncomp(K); ++i) atol_density[i] = 1e-3 * rtol * kabs[i] / w;
+  return adapt_rec(f, a, b, rtol, atol_density, 0);
+}
+
+// ------------------------------------------------------------------ cosmology
+// E(z) = H(z)/H0 for flat LCDM (Eq. 1 with OL = 1 - Om)
+template <class T> T E_of(const T& z, const T& om) {
+  const T u = 1.0 + z;
+  return fsqrt(om * u * u * u + (1.0 - om));
+}
+// I(z) = int_0^z dz'/E(z'); D(z) = (1+z) I(z) = d_L H0 / c
+template <class T> T I_of(const T& z, const T& om) {
+  auto f = [&om](const T& zp) { return 1.0 / E_of(zp, om); };
+  return integrate(f, T(0.0), z, 1e-14);
+}
+template <class T> T D_of(const T& z, const T& om) { return (1.0 + z) * I_of(z, om); }
+template <class T> T Dprime_of(const T& z, const T& om) {
+  return I_of(z, om) + (1.0 + z) / E_of(z, om);
+}
+
+// root of D(z) = x on [0, zmax] by Newton's method kept inside a bisection bracket.
+// For 0 <= Om <= 1 and z >= 0, E >= 1, so D(z) <= z (1+z): the Om = 0 inverse is a
+// lower bound and a safe start.
+double z_root(double x, double om, double zmax) {
+  double lo = 0.0, hi = zmax;
+  double z = 0.5 * (std::sqrt(1.0 + 4.0 * x) - 1.0);
+  z = std::min(std::max(z, lo), hi);
+  for (int it = 0; it < 200; ++it) {
+    const double I = I_of(z, om);
+    const double F = (1.0 + z) * I - x;
+    if (F > 0.0) hi = z; else lo = z;
+    const double Dp = I + (1.0 + z) / E_of(z, om);
+    double zn = z - F / Dp;
+    if (!(zn >= lo && zn <= hi)) zn = 0.5 * (lo + hi);
+    const bool done = std::fabs(zn - z) <= 1e-15 * (1.0 + z);
+    z = zn;
+    if (done) break;
+  }
+  return z;
+}
+
+// z(x; Om) with derivatives: one Newton step from the converged root z0.
+template <class T> T z_of_x(const T& x, const T& om, double z0) {
+  const T z(z0);
+  const T I = I_of(z, om);
+  const T u = 1.0 + z;
+  const T F = u * I - x;
+  const T Dp = I + u / E_of(z, om);
+  return z - F / Dp;
+}
+
+// ----------------------------------------------------------------- population
+template <class T> struct Pop {
+  T H0, om, alpha, beta, mmin, mmax, dm, mu, sig, lam, gam, kap, zp;
+  T lnZP;    // ln int_{mmin}^{mmax} m^-alpha dm
+  T lnZG;    // ln of the Gaussian's mass inside [mmin, mmax]
+  T lnZm1;   // ln int p_unnormalised(m1) dm1
+  T lnNz;    // ln of the redshift-prior normalisation over the pixel-averaged LOS prior
+  double xmax;  // D(z_max; Om)
+};
+
+// ln S(m): low-mass smoothing.  S = 0 below m_min, 1 above m_min + dm, and
+// 1/(1 + exp(dm/m' + dm/(m' - dm))) with m' = m - m_min in between (S = 0 at m' = 0).
+// Returns false where S = 0.
+template <class T> bool ln_S(const T& m, const T& mmin, const T& dm, T& out) {
+  if (val(m) < val(mmin)) return false;
+  if (val(m) >= val(mmin) + val(dm)) { out = T(0.0); return true; }
+  const T mp = m - mmin;
+  if (!(val(mp) > 0.0)) return false;
+  const T f = dm / mp + dm / (mp - dm);
+  out = -softplus(f);
+  return true;
+}
+
+// unnormalised primary-mass density: (1-lam) m^-alpha/Z_P + lam N(m; mu, sig)/Z_G
+template <class T> T m1_mixture(const T& m, const Pop<T>& P) {
+  const T pl = fexp(-P.alpha * flog(m) - P.lnZP);
+  const T zg = (m - P.mu) / P.sig;
+  const T ga = fexp(-0.5 * zg * zg - flog(P.sig) - LN_SQRT_2PI - P.lnZG);
+  return (1.0 - P.lam) * pl + P.lam * ga;
+}
+
+template <class T> T m1_unnormalised(const T& m, const Pop<T>& P) {
+  T ls;
+  if (!ln_S(m, P.mmin, P.dm, ls)) return T(0.0) * m;
+  return m1_mixture(m, P) * fexp(ls);
+}
+
+// C(m1) = int_{mmin}^{m1} m^beta S(m) dm, the normaliser of p(m2 | m1)
+template <class T> T C_of(const T& m1, const Pop<T>& P) {
+  auto fw = [&P](const T& m) {
+    T ls;
+    if (!ln_S(m, P.mmin, P.dm, ls)) return T(0.0) * m;
+    return fexp(P.beta * flog(m) + ls);
+  };
+  auto fa = [&P](const T& m) { return fexp(P.beta * flog(m)); };
+  const T mw = P.mmin + P.dm;
+  if (val(m1) <= val(mw)) return integrate(fw, P.mmin, m1, 1e-13);
+  return integrate(fw, P.mmin, mw, 1e-13) + integrate(fa, mw, m1, 1e-13);
+}
+
+template <class T> bool ln_p_m1(const T& m1, const Pop<T>& P, T& out) {
+  if (val(m1) > val(P.mmax)) return false;
+  T ls;
+  if (!ln_S(m1, P.mmin, P.dm, ls)) return false;
+  const T mix = m1_mixture(m1, P);
+  if (!(val(mix) > 0.0)) return false;
+  out = flog(mix) + ls - P.lnZm1;
+  return true;
+}
+
+template <class T> bool ln_p_m2(const T& m2, const T& m1, const Pop<T>& P, T& out) {
+  if (val(m2) > val(m1)) return false;
+  T ls;
+  if (!ln_S(m2, P.mmin, P.dm, ls)) return false;
+  const T C = C_of(m1, P);
+  if (!(val(C) > 0.0)) return false;
+  out = P.beta * flog(m2) + ls - flog(C);
+  return true;
+}
+
+// Madau-Dickinson shape, psi(0) = 1:
+//   psi(z) = [1 + (1+zp)^-(g+k)] (1+z)^g / [1 + ((1+z)/(1+zp))^(g+k)]
+template <class T> T ln_psi(const T& z, const Pop<T>& P) {
+  const T gk = P.gam + P.kap;
+  const T lu = flog(1.0 + z);
+  const T lp = flog(1.0 + P.zp);
+  return softplus(-gk * lp) + P.gam * lu - softplus(gk * (lu - lp));
+}
+
+// N_z = trapezoid over the LOS grid of pbar(z_j) psi(z_j) / (1 + z_j)
+template <class T> T Nz_of(const std::vector<double>& pbar, double zmax, const Pop<T>& P) {
+  const int nz = (int)pbar.size();
+  const double dz = zmax / (double)(nz - 1);
+  T acc(0.0);
+  for (int j = 0; j < nz; ++j) {
+    const double zj = (double)j * dz;
+    const double cj = (j == 0 || j == nz - 1) ? 0.5 : 1.0;
+    acc = acc + (cj * pbar[j] * dz) * fexp(ln_psi(T(zj), P)) / (1.0 + zj);
+  }
+  return acc;
+}
+
+template <class T> void set_norms(Pop<T>& P, const std::vector<double>& pbar, double zmax) {
+  auto fpl = [&P](const T& m) { return fexp(-P.alpha * flog(m)); };
+  P.lnZP = flog(integrate(fpl, P.mmin, P.mmax, 1e-14));
+  const double r2 = 0.70710678118654752440084436210485;
+  P.lnZG = flog(0.5 * (ferf((P.mmax - P.mu) / P.sig * r2) - ferf((P.mmin - P.mu) / P.sig * r2)));
+  // Z_m1 over [mmin, mmin+dm] and [mmin+dm, mmax]; the upper piece is split around the
+  // peak (fixed split points do not change the integral, only help the adaptivity)
+  auto fm = [&P](const T& m) { return m1_unnormalised(m, P); };
+  const T mw = P.mmin + P.dm;
+  T Z = integrate(fm, P.mmin, mw, 1e-14);
+  std::vector<double> cuts;
+  for (double k : {-5.0, 0.0, 5.0}) {
+    const double c = val(P.mu) + k * val(P.sig);
+    if (c > val(mw) && c < val(P.mmax)) cuts.push_back(c);
+  }
+  T lo = mw;
+  for (double c : cuts) { Z = Z + integrate(fm, lo, T(c), 1e-14); lo = T(c); }
+  Z = Z + integrate(fm, lo, P.mmax, 1e-14);
+  P.lnZm1 = flog(Z);
+  P.lnNz = flog(Nz_of(pbar, zmax, P));
+  P.xmax = D_of(zmax, val(P.om));
+}
+
+bool lambda_in_domain(const double* L) {
+  for (int i = 0; i < NP; ++i) if (!std::isfinite(L[i])) return false;
+  return L[P_H0] > 0.0 && L[P_OM] >= 0.0 && L[P_OM] <= 1.0 && L[P_MMIN] > 0.0 &&
+         L[P_MMAX] > L[P_MMIN] && L[P_DM] >= 0.0 && L[P_MMIN] + L[P_DM] < L[P_MMAX] &&
+         L[P_SIG] > 0.0 && L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0 && L[P_ZP] > -1.0;
+}
+
+template <class T> Pop<T> make_pop(const double* L, const std::vector<double>& pbar, double zmax);
+
+template <> Pop<double> make_pop<double>(const double* L, const std::vector<double>& pbar, double zmax) {
+  Pop<double> P;
+  P.H0 = L[0]; P.om = L[1]; P.alpha = L[2]; P.beta = L[3]; P.mmin = L[4]; P.mmax = L[5];
+  P.dm = L[6]; P.mu = L[7]; P.sig = L[8]; P.lam = L[9]; P.gam = L[10]; P.kap = L[11]; P.zp = L[12];
+  set_norms(P, pbar, zmax);
+  return P;
+}
+
+template <> Pop<Dual> make_pop<Dual>(const double* L, const std::vector<double>& pbar, double zmax) {
+  Dual v[NP];
+  for (int i = 0; i < NP; ++i) { v[i] = Dual(L[i]); v[i].d[i] = 1.0; }
+  Pop<Dual> P;
+  P.H0 = v[0]; P.om = v[1]; P.alpha = v[2]; P.beta = v[3]; P.mmin = v[4]; P.mmax = v[5];
+  P.dm = v[6]; P.mu = v[7]; P.sig = v[8]; P.lam = v[9]; P.gam = v[10]; P.kap = v[11]; P.zp = v[12];
+  set_norms(P, pbar, zmax);
+  return P;
+}
+
+// ---------------------------------------------------------------------- LOS
+// linear interpolation of a row tabulated at z_j = j * zmax / (nz - 1); zero outside
+// [0, zmax].  The cell index is the exact floor of z (nz - 1) / zmax.
+template <class T> bool los_interp(const double* row, int nz, double zmax, const T& z, T& p) {
+  const double zv = val(z);
+  if (zv < 0.0 || zv > zmax) return false;
+  const double s = (double)(nz - 1) / zmax;
+  int j = (int)std::floor(zv * s);
+  if (j > nz - 2) j = nz - 2;
+  if (j < 0) j = 0;
+  const T t = z * s - (double)j;
+  p = row[j] + t * (row[j + 1] - row[j]);
+  return val(p) > 0.0;
+}
+
+// ----------------------------------------------------------------- one sample
+// ln w for one detector-frame sample (m1d, m2d, dL) with PE prior ln pi:
+//   ln w = ln p_LOS(z) + ln psi(z) - ln(1+z) - ln N_z            (redshift prior, Eq. hier_pixels)
+//        + ln p(m1s) + ln p(m2s | m1s)                           (source-frame masses)
+//        - 2 ln(1+z) - ln(d d_L/dz)                              (Jacobian to detector frame)
+//        - ln pi_PE                                              (Eq. 6)
+// with z solving D(z) = d_L H0 / c and m_s = m_d / (1+z).  Returns false where w = 0.
+template <class T>
+bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, double m2d,
+          double dl, double lnpi, T& out) {
+  if (!(dl > 0.0)) return false;
+  const T x = dl * P.H0 / C_KMS;
+  if (val(x) > P.xmax) return false;
+  const double z0 = z_root(val(x), val(P.om), zmax);
+  const T z = z_of_x(x, P.om, z0);
+  T plos;
+  if (!los_interp(row, nz, zmax, z, plos)) return false;
+  const T u = 1.0 + z;
+  const T m1s = m1d / u;
+  const T m2s = m2d / u;
+  T lp1, lp2;
+  if (!ln_p_m1(m1s, P, lp1)) return false;
+  if (!ln_p_m2(m2s, m1s, P, lp2)) return false;
+  const T ddl_dz = (C_KMS / P.H0) * Dprime_of(z, P.om);
+  const T lu = flog(u);
+  out = flog(plos) + ln_psi(z, P) - lu - P.lnNz + lp1 + lp2 - 2.0 * lu - flog(ddl_dz) - lnpi;
+  return true;
+}
+
+// ------------------------------------------------------------ sums of weights
+// (max, sum e^(l - max), sum e^(2(l - max)), sum e^(l - max) dl/dLambda) over a set
+template <class T> struct Sums {
+  double m = NEG_INF, s1 = 0.0, s2 = 0.0;
+  double g[NP] = {0};
+  long n_pos = 0;
+};
+
+inline void grad_parts(const double&, double*, double) {}
+inline void grad_parts(const Dual& l, double* g, double t) { for (int i = 0; i < NP; ++i) g[i] += t * l.d[i]; }
+
+template <class T> Sums<T> sums_of(const std::vector<T>& ls) {
+  Sums<T> S;
+  for (const T& l : ls) S.m = std::max(S.m, val(l));
+  for (const T& l : ls) {
+    const double t = std::exp(val(l) - S.m);
+    S.s1 += t;
+    S.s2 += t * t;
+    grad_parts(l, S.g, t);
+    ++S.n_pos;
+  }
+  return S;
+}
+
+template <class T> Sums<T> merge(const std::vector<Sums<T>>& parts) {
+  Sums<T> S;
+  for (const auto& p : parts) S.m = std::max(S.m, p.m);
+  if (S.m == NEG_INF) return S;
+  for (const auto& p : parts) {
+    if (p.n_pos == 0) continue;
+    const double r = std::exp(p.m - S.m);
+    S.s1 += p.s1 * r;
+    S.s2 += p.s2 * r * r;
+    for (int i = 0; i < NP; ++i) S.g[i] += p.g[i] * r;
+    S.n_pos += p.n_pos;
+  }
+  return S;
+}
+
+struct Inputs {
+  int32_t n_events;
+  int32_t pad0;
+  const int64_t* offsets;
+  const float* m1;
+  const float* m2;
+  const float* dl;
+  const float* lnpe;
+  const int32_t* pix;
+  int32_t n_pix;
+  int32_t n_z;
+  double z_max;
+  const float* los;
+  int64_t n_inj;
+  double n_draw;
+  const float* im1;
+  const float* im2;
+  const float* idl;
+  const float* ilnpd;
+};
+
+std::vector<double> pixel_mean(const Inputs& in) {
+  std::vector<double> pbar((size_t)in.n_z, 0.0);
+  for (int p = 0; p < in.n_pix; ++p)
+    for (int j = 0; j < in.n_z; ++j) pbar[(size_t)j] += (double)in.los[(size_t)p * in.n_z + j];
+  for (double& v : pbar) v /= (double)in.n_pix;
+  return pbar;
+}
+
+bool inputs_valid(const Inputs& in) {
+  if (in.n_events < 0 || in.n_pix < 1 || in.n_z < 2 || !(in.z_max > 0.0)) return false;
+  if (in.n_inj < 1 || !(in.n_draw >= (double)in.n_inj)) return false;
+  if (in.offsets[0] != 0) return false;
+  for (int e = 0; e < in.n_events; ++e)
+    if (in.offsets[e + 1] <= in.offsets[e]) return false;
+  const int64_t ns = in.offsets[in.n_events];
+  for (int64_t k = 0; k < ns; ++k)
+    if (in.pix[k] < 0 || in.pix[k] >= in.n_pix) return false;
+  return true;
+}
+
+template <class T>
+void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double* L,
+                 double neff_min_event, double neff_min_sel, double* lnL_event, double* neff_event,
+                 double* ln_xi, double* neff_sel, double* lnL_total, int32_t* flag, double* grad) {
+  const int ne = in.n_events;
+  const double zmax = in.z_max;
+  const int nz = in.n_z;
+  *flag = 0;
+  if (grad) for (int i = 0; i < NP; ++i) grad[i] = 0.0;
+  if (!lambda_in_domain(L)) {
+    *flag = 1;
+    for (int e = 0; e < ne; ++e) { lnL_event[e] = NEG_INF; neff_event[e] = 0.0; }
+    *ln_xi = NEG_INF; *neff_sel = 0.0; *lnL_total = NEG_INF;
+    return;
+  }
+  const Pop<T> P = make_pop<T>(L, pbar, zmax);
+
+  // ---- numerator: one event at a time
+  std::vector<double> ev_grad((size_t)ne * NP, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < ne; ++e) {
+    std::vector<T> ls;
+    std::vector<double> row((size_t)nz);
+    int cur_pix = -1;
+    for (int64_t k = in.offsets[e]; k < in.offsets[e + 1]; ++k) {
+      if (in.pix[k] != cur_pix) {
+        cur_pix = in.pix[k];
+        for (int j = 0; j < nz; ++j) row[(size_t)j] = (double)in.los[(size_t)cur_pix * nz + j];
+      }
+      T l;
+      if (ln_w(P, row.data(), nz, zmax, in.m1[k], in.m2[k], in.dl[k], in.lnpe[k], l)) ls.push_back(l);
+    }
+    const Sums<T> S = sums_of(ls);
+    const double n_i = (double)(in.offsets[e + 1] - in.offsets[e]);
+    if (S.n_pos == 0) {
+      lnL_event[e] = NEG_INF;
+      neff_event[e] = 0.0;
+    } else {
+      lnL_event[e] = S.m + std::log(S.s1) - std::log(n_i);
+      neff_event[e] = S.s1 * S.s1 / S.s2;
+      for (int i = 0; i < NP; ++i) ev_grad[(size_t)e * NP + i] = S.g[i] / S.s1;
+    }
+  }
+
+  // ---- selection: injections against the pixel-averaged LOS prior, in fixed chunks
+  const int64_t chunk = 65536;
+  const int64_t nchunk = (in.n_inj + chunk - 1) / chunk;
+  std::vector<Sums<T>> parts((size_t)nchunk);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < nchunk; ++c) {
+    std::vector<T> ls;
+    const int64_t a = c * chunk, b = std::min(in.n_inj, a + chunk);
+    for (int64_t k = a; k < b; ++k) {
+      T l;
+      if (ln_w(P, pbar.data(), nz, zmax, in.im1[k], in.im2[k], in.idl[k], in.ilnpd[k], l)) ls.push_back(l);
+    }
+    parts[(size_t)c] = sums_of(ls);
+  }
+  const Sums<T> Ssel = merge(parts);
+  double sel_grad[NP] = {0};
+  if (Ssel.n_pos == 0) {
+    *ln_xi = NEG_INF;
+    *neff_sel = 0.0;
+  } else {
+    *ln_xi = Ssel.m + std::log(Ssel.s1) - std::log(in.n_draw);
+    *neff_sel = Ssel.s1 * Ssel.s1 / Ssel.s2;
+    for (int i = 0; i < NP; ++i) sel_grad[i] = Ssel.g[i] / Ssel.s1;
+  }
+
+  // ---- total = sum_i ln L_i - N_det ln xi (Neumaier-compensated sum in event order)
+  bool neff_fail = false;
+  double sum = 0.0, comp_ = 0.0;
+  for (int e = 0; e < ne; ++e) {
+    if (!(neff_event[e] >= neff_min_event)) neff_fail = true;
+    const double v = lnL_event[e];
+    const double t = sum + v;
+    if (std::fabs(sum) >= std::fabs(v)) comp_ += (sum - t) + v; else comp_ += (v - t) + sum;
+    sum = t;
+  }
+  // flags: bit 1 some event below the N_eff threshold, bit 2 selection below its
+  // threshold (only when one is set), bit 3 every injection weight is zero.  Any
+  // flag makes the total -inf.
+  if (neff_fail) *flag |= 2;
+  if (neff_min_sel > 0.0 && !(*neff_sel >= neff_min_sel)) *flag |= 4;
+  if (Ssel.n_pos == 0) *flag |= 8;
+  if (*flag) {
+    *lnL_total = NEG_INF;
+    return;
+  }
+  *lnL_total = (sum + comp_) - (double)ne * (*ln_xi);
+  if (grad) {
+    for (int i = 0; i < NP; ++i) {
+      double g = 0.0;
+      for (int e = 0; e < ne; ++e) g += ev_grad[(size_t)e * NP + i];
+      grad[i] = g - (double)ne * sel_grad[i];
+    }
+  }
+}
+
+std::vector<double> row_to_double(const float* row, int nz) {
+  std::vector<double> r((size_t)nz);
+  for (int j = 0; j < nz; ++j) r[(size_t)j] = (double)row[j];
+  return r;
+}
+
+}  // namespace
+
+// ============================================================== C entry points
+extern "C" {
+
+// Full likelihood for K Lambda points.  Arrays are host memory; outputs are
+// lnL_event[K][n_events], neff_event[K][n_events], ln_xi[K], neff_sel[K],
+// lnL_total[K], flags[K] and, if grad_total != NULL, grad_total[K][13]
+// (want_grad != 0 selects the dual-number pass).  Returns 0, or -1 on invalid inputs.
+int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad,
+               double neff_min_event, double neff_min_sel, int32_t n_threads, double* lnL_event,
+               double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
+               int32_t* flags, double* grad_total) {
+  if (!in || K < 0 || !inputs_valid(*in)) return -1;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+  const std::vector<double> pbar = pixel_mean(*in);
+  const int ne = in->n_events;
+  for (int k = 0; k < K; ++k) {
+    double* g = (want_grad && grad_total) ? grad_total + (size_t)k * NP : nullptr;
+    if (want_grad)
+      eval_lambda<Dual>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
+                        lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
+                        neff_sel + k, lnL_total + k, flags + k, g);
+    else
+      eval_lambda<double>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
+                          lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
+                          neff_sel + k, lnL_total + k, flags + k, nullptr);
+  }
+  return 0;
+}
+
+int orc_num_params(void) { return NP; }
+
+// --- pieces, exposed for the pin tests ---------------------------------------
+double orc_E(double z, double om) { return E_of(z, om); }
+double orc_I(double z, double om) { return I_of(z, om); }
+double orc_D(double z, double om) { return D_of(z, om); }
+double orc_Dprime(double z, double om) { return Dprime_of(z, om); }
+double orc_z_of_x(double x, double om, double zmax) { return z_of_x(x, om, z_root(x, om, zmax)); }
+
+double orc_S(double m, double mmin, double dm) {
+  double ls;
+  return ln_S(m, mmin, dm, ls) ? std::exp(ls) : 0.0;
+}
+
+static Pop<double> pop_from(const double* L) {
+  std::vector<double> pbar(2, 1.0);  // N_z is not needed by the mass and rate pieces
+  return make_pop<double>(L, pbar, 1.0);
+}
+
+double orc_ln_p_m1(double m1, const double* L) {
+  const Pop<double> P = pop_from(L);
+  double o;
+  return ln_p_m1(m1, P, o) ? o : NEG_INF;
+}
+double orc_ln_p_m2(double m2, double m1, const double* L) {
+  const Pop<double> P = pop_from(L);
+  double o;
+  return ln_p_m2(m2, m1, P, o) ? o : NEG_INF;
+}
+double orc_C(double m1, const double* L) { return C_of(m1, pop_from(L)); }
+double orc_ln_Zm1(const double* L) { return pop_from(L).lnZm1; }
+double orc_ln_psi(double z, const double* L) { return ln_psi(z, pop_from(L)); }
+
+double orc_ln_Nz(const double* L, const double* pbar, int32_t nz, double zmax) {
+  std::vector<double> pb(pbar, pbar + nz);
+  return flog(Nz_of(pb, zmax, pop_from(L)));
+}
+
+// The LOS cell index as the CUDA library defines it on single-precision z:
+// s = (float)((nz - 1) / zmax) (rounded once from double), t = z * s rounded to
+// single precision, j = floor(t) clamped to [0, nz - 2].
+int32_t orc_los_cell_f32(float z, int32_t nz, double zmax) {
+  const float s = (float)((double)(nz - 1) / zmax);
+  const volatile float t = z * s;
+  int j = (int)std::floor((double)t);
+  if (j < 0) j = 0;
+  if (j > nz - 2) j = nz - 2;
+  return j;
+}
+
+// ln w for n samples against one LOS row that also defines N_z (as the pixel
+// average does for injections).  out_grad[n][13] is filled when non-NULL.
+// Samples with w = 0 get -inf (and a zero gradient).
+int orc_ln_w_row(const double* L, int64_t n, const float* m1, const float* m2, const float* dl,
+                 const float* lnpi, const float* row_f32, int32_t nz, double zmax, double* out,
+                 double* out_grad) {
+  if (!lambda_in_domain(L)) return -1;
+  const std::vector<double> row = row_to_double(row_f32, nz);
+  if (!out_grad) {
+    const Pop<double> P = make_pop<double>(L, row, zmax);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+      double l;
+      out[k] = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l) ? l : NEG_INF;
+    }
+    return 0;
+  }
+  const Pop<Dual> P = make_pop<Dual>(L, row, zmax);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < n; ++k) {
+    Dual l;
+    if (ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l)) {
+      out[k] = l.v;
+      for (int i = 0; i < NP; ++i) out_grad[(size_t)k * NP + i] = l.d[i];
+    } else {
+      out[k] = NEG_INF;
+      for (int i = 0; i < NP; ++i) out_grad[(size_t)k * NP + i] = 0.0;
+    }
+  }
+  return 0;
+}
+
+// single application of the 15-point Kronrod (which = 0) or 7-point Gauss
+// (which = 1) rule to x^k on [-1, 1]; used to pin the quadrature constants.
+double orc_rule_poly(int32_t k, int32_t which) {
+  auto f = [k](const double& x) { return std::pow(x, (double)k); };
+  double K, G, kabs[NC_MAX];
+  gk15(f, -1.0, 1.0, K, G, kabs);
+  return which == 0 ? K : G;
+}
+
+}  // extern "C"
