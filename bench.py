@@ -1,0 +1,360 @@
+"""Benchmark: posterior-sample x Lambda log-likelihood + gradient evaluations per second.
+
+Workload (O5-like, the paper's Sec. 3.1 scale): 2000 events with log-uniform 1k-16k
+posterior samples each (~1.08e7 samples), nside-64 HEALPix LOS priors (49,152 pixels)
+on a 2,048-point redshift grid, 1e7 detected injections, and a batch of K = 256
+Lambda points per call.  One step = one gwc_loglik_grad call on the whole batch:
+prologue, fused sample x Lambda value+gradient kernel, merge.  Inputs are synthetic
+(seeded) and resident in HBM before timing; their ~0.8 GB exceeds the 129 MB L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead,
+on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "posterior-sample×Λ log-lik+grad evals/s at O5 scale vs plain GPU path"
+WORKLOAD = "c3"
+K_LAMBDA = 256
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# Algorithmic work per (sample, Lambda) evaluation of the fused value+gradient kernel,
+# counted from its formula (one transcendental = one special-function-unit op):
+#   value: ln(1+z), 1/(1+z), e^-|a-b| (mass mixture), e^-|r| (rate), 1/sqrt(E^2),
+#          ln(product), the product's reciprocal, (1+beta)-power above the smoothing
+#          window, the logsumexp exponential                                  -> 9 SFU
+#   gradient adds 1/(1+e^-|a-b|), 1/(1+e^-|r|), 1/D', 1/C                      -> 4 SFU
+# and about 190 FP32 operations in all (value ~75: Hermite position, LOS lerp, masses,
+# mixture, rate, Jacobian, online logsumexp; gradient ~115: the z-chain and 13
+# derivative terms with their accumulation).
+SFU_PER_EVAL = 13
+FP32_PER_EVAL = 190
+SMS, FP32_LANES, SFU_LANES, SM_MAX_GHZ = 152, 128, 16, 2.07
+
+
+def alu_roofline(evals, seconds):
+    """Binding ALU unit for evals evaluations in `seconds` (peaks at the maximum SM clock)."""
+    sfu_peak = SMS * SFU_LANES * SM_MAX_GHZ * 1e9          # SFU ops/s
+    fp32_peak = SMS * FP32_LANES * SM_MAX_GHZ * 1e9        # FP32 instructions/s
+    t_sfu = evals * SFU_PER_EVAL / sfu_peak
+    t_fp32 = evals * FP32_PER_EVAL / fp32_peak
+    if t_fp32 >= t_sfu:
+        ach = evals * FP32_PER_EVAL / seconds / 1e12
+        return dict(bound="alu", unit="Tinst/s (FP32 pipe)", achieved=ach, peak=fp32_peak / 1e12,
+                    frac=ach / (fp32_peak / 1e12), peak_source="152 SMs x 128 FP32 lanes x 2.07 GHz")
+    ach = evals * SFU_PER_EVAL / seconds / 1e12
+    return dict(bound="alu", unit="Top/s (SFU)", achieved=ach, peak=sfu_peak / 1e12,
+                frac=ach / (sfu_peak / 1e12), peak_source="152 SMs x 16 SFU lanes x 2.07 GHz")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(cat, lam, max_seconds=20.0):
+    """The FP64 oracle (value + gradient) on a bounded sample of the workload."""
+    import oracle
+    from paper_2605_23538_gb300 import synth
+    cores = os.cpu_count() or 1
+    # grow the sample until one timed pass takes a few seconds, then scale it
+    n_ev, n_inj = 4, 20_000
+    while True:
+        sub = synth.subset_events(cat, range(n_ev))
+        for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
+            sub[k] = cat[k][:n_inj]
+        evals = int(sub["offsets"][-1]) + n_inj
+        t0 = time.perf_counter()
+        oracle.loglik(sub, lam[:1], grad=True, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * max_seconds or n_ev >= 64:
+            break
+        grow = max(2.0, min(8.0, 0.3 * max_seconds / max(dt, 1e-3)))
+        n_ev = min(64, int(n_ev * grow))
+        n_inj = int(n_inj * grow)
+    return dict(value=evals / dt, unit="evals/s", cores=cores, kind="oracle",
+                sample=f"1 Lambda x ({int(sub['offsets'][-1])} samples of the first {n_ev} events "
+                       f"+ the first {n_inj} injections), FP64 value+gradient, {dt:.1f} s")
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, one bounded sample per step."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2605_23538_gb300 import synth
+    oracle.build()
+    cat = synth.catalogue(WORKLOAD)
+    lam = synth.lambda_batch(K_LAMBDA)
+    cores = os.cpu_count() or 1
+    n_ev, n_inj = 6, 40_000
+    sub = synth.subset_events(cat, range(n_ev))
+    for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
+        sub[k] = cat[k][:n_inj]
+    evals = int(sub["offsets"][-1]) + n_inj
+    for w in range(args.warmup):
+        oracle.loglik(sub, lam[w % K_LAMBDA:w % K_LAMBDA + 1], grad=True, n_threads=cores)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        k = (args.warmup + s) % K_LAMBDA
+        oracle.loglik(sub, lam[k:k + 1], grad=True, n_threads=cores)
+    dt = time.perf_counter() - t0
+    value = evals * args.steps / dt
+    sample = (f"per step 1 Lambda x ({int(sub['offsets'][-1])} samples of the first {n_ev} events "
+              f"+ the first {n_inj} injections)")
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "c3: 2000 events x log-uniform 1k-16k samples, nside-64 x 2048 LOS, "
+                                   "1e7 injections, K=256", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gwc", choices=["gwc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-k", type=int, default=32, help="Lambda points timed on the plain path")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import paper_2605_23538_gb300 as g
+    from paper_2605_23538_gb300 import build, synth
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    cat = synth.catalogue(WORKLOAD)
+    log(f"[rank {rank}] catalogue {time.perf_counter() - t0:.1f} s: {len(cat['m1'])} samples, "
+        f"{len(cat['inj_m1'])} injections, LOS {cat['los'].shape}")
+    n_s, n_i = len(cat["m1"]), len(cat["inj_m1"])
+    ctx = g.Context(cat, max_K=K_LAMBDA)
+    info = ctx.info()
+    # each rank evaluates its own Lambda batch over the full catalogue (weak scaling)
+    lam_np = synth.lambda_batch(K_LAMBDA, purpose=4 + 100 * rank)
+    lam = torch.tensor(lam_np, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = g._outputs(K_LAMBDA, ctx.n_events, lam.device, True)
+
+    def step():
+        g.loglik_grad(ctx._ctx, lam, ctx.n_events, stream, out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    stage_ms, n_calls = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ms_total = float(ms.item())
+    evals_step = (n_s + n_i) * K_LAMBDA
+    value = evals_step * args.steps * world / (ms_total / 1e3)
+    flags = out["flags"].cpu().numpy()
+    fused_ms = stage_ms[1] / max(n_calls, 1)
+    roof = alu_roofline(evals_step, fused_ms / 1e3)
+    roof["traffic"] = None
+
+    # value-only throughput (same batch)
+    outv = g._outputs(K_LAMBDA, ctx.n_events, lam.device, False)
+    for _ in range(2):
+        g.loglik(ctx._ctx, lam, ctx.n_events, stream, outv)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.loglik(ctx._ctx, lam, ctx.n_events, stream, outv)
+    ev1.record(stream)
+    barrier()
+    value_only = evals_step * args.steps / (ev0.elapsed_time(ev1) / 1e3)
+
+    # the plain single-Lambda FP32 path, value+gradient, on the first plain_k points
+    kp = max(1, min(args.plain_k, K_LAMBDA))
+    lam_p = lam[:kp].contiguous()
+    outp = g._outputs(kp, ctx.n_events, lam.device, True)
+    g.loglik_plain(ctx._ctx, lam_p, ctx.n_events, True, stream, outp)
+    barrier()
+    ev0.record(stream)
+    psteps = 2
+    for _ in range(psteps):
+        g.loglik_plain(ctx._ctx, lam_p, ctx.n_events, True, stream, outp)
+    ev1.record(stream)
+    barrier()
+    plain = (n_s + n_i) * kp * psteps / (ev0.elapsed_time(ev1) / 1e3)
+
+    # end to end through the host-memory entry point (Lambda in, totals and gradient out)
+    for _ in range(2):
+        ctx.loglik_grad_host(lam_np)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.loglik_grad_host(lam_np)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": evals_step * args.steps / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": K_LAMBDA * 13 * 8,
+           "d2h_bytes_per_step": K_LAMBDA * 8 + K_LAMBDA * 4 + K_LAMBDA * 13 * 8}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        base = cpu_baseline(cat, lam_np)
+
+    if rank == 0:
+        peaks, src = load_peaks()
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "c3: 2000 events x log-uniform 1k-16k samples (O5-like), "
+                                   "nside-64 (49152 px) x 2048-z LOS, 1e7 detected injections",
+                       "K": K_LAMBDA, "n_samples": n_s, "n_injections": n_i,
+                       "evals_per_step": evals_step, "parallelism": f"lambda-batch x{world}",
+                       "l2": "inputs larger than L2 (resident catalogue %.2f GB), no flush"
+                             % (info["device_bytes"] / 1e9),
+                       "chunk": info["chunk"], "n_items": info["n_items"]},
+            "roofline": roof,
+            "stage_ms_per_step": {"prologue": stage_ms[0] / max(n_calls, 1), "fused": fused_ms,
+                                  "merge": stage_ms[2] / max(n_calls, 1)},
+            "value_only": {"value": value_only, "unit": "evals/s"},
+            "plain_gpu": {"value": plain, "unit": "evals/s", "K": kp,
+                          "speedup": value / world / plain},
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "flags_nonzero": int(np.count_nonzero(flags)),
+            "peaks": {"source": src, "hbm_gbs": peaks.get("hbm_gbs")},
+        }
+        if clocks is not None:
+            line["clocks"] = clocks
+        if base is not None:
+            line["cpu_baseline"] = base
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * gwc.h -- C ABI of the GB300 dark-siren hierarchical likelihood library (libgwc.so).
+ *
+ * The library evaluates, for a batch of K hyperparameter points Lambda, the
+ * hierarchical log-likelihood of a gravitational-wave event catalogue with a galaxy
+ * catalogue prior (Papadopoulos et al., "Scalable Dark Siren Cosmology with gwcosmo"):
+ *
+ *   ln L(Lambda) = sum_i ln L_i(Lambda) - N_det ln xi(Lambda)            (Eqs. 2-4)
+ *   ln L_i       = ln( (1/N_i) sum_k w_ik )                              (Eqs. 5-6, kernel width -> 0)
+ *   w_ik         = p_LOS(z_ik | pixel_ik) psi(z)/(1+z) / N_z
+ *                  * p(m1_s) p(m2_s | m1_s) / [(1+z)^2 d d_L/dz] / pi_PE  (Eq. hier_pixels, Eq. 6)
+ *   ln xi        = ln( (1/N_draw) sum_m w~_m )   with the pixel-averaged LOS prior and
+ *                  the injections' draw density in place of pi_PE       (Eq. 4, Eq. hier_pixels)
+ *   N_eff,i      = (sum_k w_ik)^2 / sum_k w_ik^2                          (Eq. 7, applied per event)
+ *
+ * z solves d_L = (c/H0)(1+z) int_0^z dz'/E(z'), E = sqrt(Om (1+z)^3 + 1 - Om) (Eq. 1, flat).
+ * The mass model is a power law plus a Gaussian peak with a low-mass smoothing window,
+ * and psi is the Madau-Dickinson rate shape with psi(0) = 1.
+ *
+ * Lambda layout (13 doubles, in this order):
+ *   [H0 (km/s/Mpc), Om, alpha, beta, m_min, m_max, delta_m, mu_g, sigma_g, lambda_peak,
+ *    gamma, kappa, z_p]
+ * Domain: H0 > 0, 0 <= Om <= 1, m_min > 0, m_max > m_min, delta_m >= 0,
+ * m_min + delta_m < m_max, sigma_g > 0, 0 <= lambda_peak <= 1, z_p > -1, all finite.
+ * A point outside the domain is not an error: its flags bit 0 is set and its
+ * log-likelihood outputs are -inf.
+ *
+ * Memory: gwc_create copies every host input into device memory owned by the context;
+ * the caller may free its inputs on return.  The per-call Lambda and output buffers are
+ * caller-owned device memory, read and written asynchronously on the given stream
+ * (a cudaStream_t passed as void*, NULL for the legacy default stream).  A context
+ * serves one stream at a time.  The per-call path allocates nothing, synchronises
+ * nothing and touches no host memory, except gwc_loglik_grad_host, which stages
+ * through the context's pinned buffers and synchronises its stream.
+ *
+ * Errors: every entry point returns a gwc_status; no exception crosses the ABI.
+ * gwc_last_error returns the message of the last failure (per context, or
+ * thread-local when the context is NULL).
+ */
+#ifndef GWC_H
+#define GWC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWC_NUM_PARAMS 13
+
+typedef enum {
+  GWC_OK = 0,
+  GWC_E_INVALID = -1,     /* malformed inputs, sizes or options */
+  GWC_E_CUDA = -2,        /* a CUDA call failed; gwc_last_error has its message */
+  GWC_E_NOMEM = -3,       /* a device or pinned allocation failed (nothing leaked) */
+  GWC_E_TIMEOUT = -4,     /* reserved: the kernels contain no waits */
+  GWC_E_UNSUPPORTED = -5  /* no usable CUDA device, or an option this build lacks */
+} gwc_status;
+
+/* flags[k] bits */
+#define GWC_FLAG_DOMAIN 1       /* Lambda outside its domain */
+#define GWC_FLAG_NEFF_EVENT 2   /* some event has N_eff below options.neff_min_event */
+#define GWC_FLAG_NEFF_SEL 4     /* N_eff,sel below options.neff_min_sel (when > 0) */
+#define GWC_FLAG_XI_ZERO 8      /* every injection weight is zero */
+/* any flag makes lnL_total -inf and grad_total zero */
+
+#define GWC_LOS_F32 0
+#define GWC_LOS_BF16 1
+
+typedef struct gwc_ctx gwc_ctx;
+
+/* Posterior samples, CSR by event (host memory, structure of arrays).
+ * offsets[n_events + 1]: offsets[0] = 0, strictly increasing (every event has at least
+ * one sample); sample k of event i is k in [offsets[i], offsets[i+1]).  Detector-frame
+ * masses m1_det >= m2_det are expected (pairs with m2_det > m1_det get zero weight),
+ * dl_mpc is the luminosity distance in Mpc (d_L <= 0 gets zero weight), ln_pe_prior the
+ * natural log of the parameter-estimation prior density in (m1_det, m2_det, d_L), and
+ * pix the sample's sky pixel, 0 <= pix < n_pix.  All values finite. */
+typedef struct {
+  int32_t n_events;
+  const int64_t* offsets;
+  const float* m1_det;
+  const float* m2_det;
+  const float* dl_mpc;
+  const float* ln_pe_prior;
+  const int32_t* pix;
+} gwc_events;
+
+/* Line-of-sight redshift priors: row-major [n_pix][n_z] (host memory), row j tabulated at
+ * z_j = j z_max / (n_z - 1) and linearly interpolated in between (zero outside
+ * [0, z_max]).  dtype GWC_LOS_F32 (float) or GWC_LOS_BF16 (uint16 bfloat16 bits).
+ * n_pix >= 1, n_z >= 2, z_max > 0; values finite and >= 0. */
+typedef struct {
+  int32_t n_pix;
+  int32_t n_z;
+  double z_max;
+  int32_t dtype;
+  const void* p_z;
+} gwc_los;
+
+/* Detected injections (host memory): n_found >= 1 rows, drawn from a known density
+ * whose natural log in (m1_det, m2_det, d_L) is ln_p_draw; n_draw >= n_found is the
+ * number of draws made. */
+typedef struct {
+  int64_t n_found;
+  double n_draw;
+  const float* m1_det;
+  const float* m2_det;
+  const float* dl_mpc;
+  const float* ln_p_draw;
+} gwc_injections;
+
+typedef struct {
+  double neff_min_event; /* per-event N_eff threshold (default 2) */
+  double neff_min_sel;   /* selection N_eff threshold; 0 = report only (default) */
+  int32_t accum;         /* 0: plain FP32 per-lane sums; 1: compensated (Kahan) sums */
+  int32_t los_dtype;     /* device storage of the LOS table: GWC_LOS_F32 or GWC_LOS_BF16 */
+  int32_t n_x_table;     /* nodes of the per-Lambda z(d_L) inversion table, a multiple of 4
+                            in [16, 4096] (default 512) */
+  int32_t max_K;         /* largest Lambda batch a call may pass (default 256) */
+  int32_t chunk;         /* samples per work item, 64..4096 (default 1024) */
+  int32_t lambda_tile;   /* Lambda points per CTA when K >= 8 (default 8; 0 = choose) */
+} gwc_options;
+
+/* Fill *o with the defaults listed above. */
+void gwc_default_options(gwc_options* o);
+
+/* Validate the inputs, copy them to the current CUDA device and build the context.
+ * opts may be NULL (defaults).  On success *out owns all device memory. */
+gwc_status gwc_create(const gwc_events* events, const gwc_los* los,
+                      const gwc_injections* inj, const gwc_options* opts, gwc_ctx** out);
+
+/* Log-likelihood for K Lambda points (1 <= K <= max_K).  Device pointers:
+ *   d_lambda[K][13] (in), d_lnL_event[K][n_events], d_neff_event[K][n_events],
+ *   d_ln_xi[K], d_neff_sel[K], d_lnL_total[K], d_flags[K] (out).
+ * d_lnL_event and d_neff_event may be NULL when n_events == 0. */
+gwc_status gwc_loglik(gwc_ctx* ctx, int32_t K, const double* d_lambda, double* d_lnL_event,
+                      double* d_neff_event, double* d_ln_xi, double* d_neff_sel,
+                      double* d_lnL_total, int32_t* d_flags, void* stream);
+
+/* As gwc_loglik, plus d_grad_total[K][13] = d lnL_total / d Lambda (zero where a flag
+ * is set).  Each sample's derivative is recomputed in the same pass as its weight. */
+gwc_status gwc_loglik_grad(gwc_ctx* ctx, int32_t K, const double* d_lambda, double* d_lnL_event,
+                           double* d_neff_event, double* d_ln_xi, double* d_neff_sel,
+                           double* d_lnL_total, int32_t* d_flags, double* d_grad_total,
+                           void* stream);
+
+/* The plain single-Lambda path, kept as the speed-up baseline: the same per-sample
+ * arithmetic, one Lambda per launch sequence, every sample re-read from memory for each
+ * Lambda, per-sample weights (and, for the gradient, per-sample weighted derivatives)
+ * written to device memory and reduced in separate passes.  Same outputs as
+ * gwc_loglik_grad (d_grad_total may be NULL for the value only). */
+gwc_status gwc_loglik_plain(gwc_ctx* ctx, int32_t K, const double* d_lambda,
+                            double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
+                            double* d_neff_sel, double* d_lnL_total, int32_t* d_flags,
+                            double* d_grad_total, void* stream);
+
+/* Host-memory convenience form of gwc_loglik_grad: h_lambda[K][13] in; h_lnL_total[K],
+ * h_flags[K] and h_grad_total[K][13] out (h_grad_total may be NULL for the value only).
+ * Copies through the context's pinned staging buffers and synchronises the stream. */
+gwc_status gwc_loglik_grad_host(gwc_ctx* ctx, int32_t K, const double* h_lambda,
+                                double* h_lnL_total, int32_t* h_flags, double* h_grad_total,
+                                void* stream);
+
+/* Release every resource of the context (NULL is a no-op). */
+void gwc_destroy(gwc_ctx* ctx);
+
+/* Message of the last failure on ctx, or of the calling thread when ctx is NULL. */
+const char* gwc_last_error(const gwc_ctx* ctx);
+
+/* Sizes of a context (for callers and tests). */
+typedef struct {
+  int32_t n_events;
+  int64_t n_samples;
+  int64_t n_injections;
+  int32_t n_pix;
+  int32_t n_z;
+  int32_t n_items;       /* work items (sample chunks) the kernels iterate over */
+  int32_t chunk;
+  int32_t n_x_table;
+  int32_t max_K;
+  int64_t device_bytes;  /* device memory held by the context */
+} gwc_info;
+
+gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
+
+/* Per-kernel timing.  While enabled, every call records CUDA events on its stream around
+ * its three stages (the prologue kernel, the sample kernel or the plain path's sample
+ * passes, and the merge kernel).  gwc_profile_read waits for the recorded events,
+ * returns ms[0..2] = summed stage times in milliseconds and *n_calls = calls recorded
+ * since the last read, then resets the sums.  Enabling creates the events (no per-call
+ * allocation); disabling destroys them.  Not for use inside stream capture. */
+gwc_status gwc_profile_enable(gwc_ctx* ctx, int32_t enable);
+gwc_status gwc_profile_read(gwc_ctx* ctx, double* ms, int64_t* n_calls);
+
+/* The library's LOS grid cell index, for tests of bit-exact indexing: for each z (device
+ * array of n floats) d_cell receives floor(z * ((n_z - 1) / z_max)) evaluated in double
+ * precision and clamped to [0, n_z - 2] (the index the linear interpolation uses, with
+ * the -1 marker for z < 0 or z > z_max).  The fused kernels reach the same cells through
+ * their split-precision position tables. */
+gwc_status gwc_los_cell_index(const float* d_z, int64_t n, int32_t n_z, double z_max,
+                              int32_t* d_cell, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWC_H */

@@ -61,7 +61,7 @@ def lib():
             L = _lib
             L.orc_loglik.restype = ctypes.c_int
             L.orc_loglik.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, d, d, i32,
-                                     vp, vp, vp, vp, vp, vp, vp]
+                                     vp, vp, vp, vp, vp, vp, vp, vp]
             for name, args in [("orc_E", [d, d]), ("orc_I", [d, d]), ("orc_D", [d, d]),
                                ("orc_Dprime", [d, d]), ("orc_z_of_x", [d, d, d]),
                                ("orc_S", [d, d, d]), ("orc_ln_p_m1", [d, vp]),
@@ -71,8 +71,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.restype = d
                 fn.argtypes = args
-            L.orc_los_cell_f32.restype = i32
-            L.orc_los_cell_f32.argtypes = [ctypes.c_float, i32, d]
+            L.orc_los_cell.restype = i32
+            L.orc_los_cell.argtypes = [ctypes.c_float, i32, d]
             L.orc_ln_w_row.restype = ctypes.c_int
             L.orc_ln_w_row.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, d, vp, vp]
         return _lib
@@ -108,8 +108,9 @@ def ln_Nz(lam, pbar, zmax):
     return lib().orc_ln_Nz(_ptr(a), _ptr(p), len(p), zmax)
 
 
-def los_cell_f32(z, nz, zmax):
-    return lib().orc_los_cell_f32(ctypes.c_float(float(np.float32(z))), nz, zmax)
+def los_cell(z, nz, zmax):
+    """LOS grid cell of the float32 value z (-1 outside [0, zmax])."""
+    return lib().orc_los_cell(ctypes.c_float(float(np.float32(z))), nz, zmax)
 
 
 def ln_w_row(lam, m1, m2, dl, lnpi, row, zmax, grad=False):
@@ -155,13 +156,14 @@ def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads
                  idl=arr("inj_dl", np.float32), ilnpd=arr("inj_lnpd", np.float32))
     out = dict(lnL_event=np.empty((K, n_ev)), neff_event=np.empty((K, n_ev)),
                ln_xi=np.empty(K), neff_sel=np.empty(K), lnL_total=np.empty(K),
-               flags=np.empty(K, np.int32), grad_total=np.zeros((K, NP)) if grad else None)
+               flags=np.empty(K, np.int32), grad_total=np.zeros((K, NP)) if grad else None,
+               grad_scale=np.zeros((K, NP)) if grad else None)
     rc = lib().orc_loglik(ctypes.byref(inp), K, _ptr(lam), int(bool(grad)), neff_min_event,
                           neff_min_sel, n_threads, _ptr(out["lnL_event"]), _ptr(out["neff_event"]),
                           _ptr(out["ln_xi"]), _ptr(out["neff_sel"]), _ptr(out["lnL_total"]),
-                          _ptr(out["flags"]), _ptr(out["grad_total"]))
+                          _ptr(out["flags"]), _ptr(out["grad_total"]), _ptr(out["grad_scale"]))
     if rc != 0:
         raise ValueError("oracle rejected the inputs")
     if not grad:
-        del out["grad_total"]
+        del out["grad_total"], out["grad_scale"]
     return out

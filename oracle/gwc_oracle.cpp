@@ -444,12 +444,18 @@ bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, d
 // (max, sum e^(l - max), sum e^(2(l - max)), sum e^(l - max) dl/dLambda) over a set
 template <class T> struct Sums {
   double m = NEG_INF, s1 = 0.0, s2 = 0.0;
-  double g[NP] = {0};
+  double g[NP] = {0};      // sum e^(l - m) dl/dLambda
+  double gabs[NP] = {0};   // sum e^(l - m) |dl/dLambda| (a magnitude scale for tests)
   long n_pos = 0;
 };
 
-inline void grad_parts(const double&, double*, double) {}
-inline void grad_parts(const Dual& l, double* g, double t) { for (int i = 0; i < NP; ++i) g[i] += t * l.d[i]; }
+inline void grad_parts(const double&, double*, double*, double) {}
+inline void grad_parts(const Dual& l, double* g, double* gabs, double t) {
+  for (int i = 0; i < NP; ++i) {
+    g[i] += t * l.d[i];
+    gabs[i] += t * std::fabs(l.d[i]);
+  }
+}
 
 template <class T> Sums<T> sums_of(const std::vector<T>& ls) {
   Sums<T> S;
@@ -458,7 +464,7 @@ template <class T> Sums<T> sums_of(const std::vector<T>& ls) {
     const double t = std::exp(val(l) - S.m);
     S.s1 += t;
     S.s2 += t * t;
-    grad_parts(l, S.g, t);
+    grad_parts(l, S.g, S.gabs, t);
     ++S.n_pos;
   }
   return S;
@@ -473,7 +479,10 @@ template <class T> Sums<T> merge(const std::vector<Sums<T>>& parts) {
     const double r = std::exp(p.m - S.m);
     S.s1 += p.s1 * r;
     S.s2 += p.s2 * r * r;
-    for (int i = 0; i < NP; ++i) S.g[i] += p.g[i] * r;
+    for (int i = 0; i < NP; ++i) {
+      S.g[i] += p.g[i] * r;
+      S.gabs[i] += p.gabs[i] * r;
+    }
     S.n_pos += p.n_pos;
   }
   return S;
@@ -523,12 +532,14 @@ bool inputs_valid(const Inputs& in) {
 template <class T>
 void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double* L,
                  double neff_min_event, double neff_min_sel, double* lnL_event, double* neff_event,
-                 double* ln_xi, double* neff_sel, double* lnL_total, int32_t* flag, double* grad) {
+                 double* ln_xi, double* neff_sel, double* lnL_total, int32_t* flag, double* grad,
+                 double* gscale) {
   const int ne = in.n_events;
   const double zmax = in.z_max;
   const int nz = in.n_z;
   *flag = 0;
   if (grad) for (int i = 0; i < NP; ++i) grad[i] = 0.0;
+  if (gscale) for (int i = 0; i < NP; ++i) gscale[i] = 0.0;
   if (!lambda_in_domain(L)) {
     *flag = 1;
     for (int e = 0; e < ne; ++e) { lnL_event[e] = NEG_INF; neff_event[e] = 0.0; }
@@ -538,7 +549,7 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
   const Pop<T> P = make_pop<T>(L, pbar, zmax);
 
   // ---- numerator: one event at a time
-  std::vector<double> ev_grad((size_t)ne * NP, 0.0);
+  std::vector<double> ev_grad((size_t)ne * NP, 0.0), ev_gabs((size_t)ne * NP, 0.0);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int e = 0; e < ne; ++e) {
     std::vector<T> ls;
@@ -560,7 +571,10 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
     } else {
       lnL_event[e] = S.m + std::log(S.s1) - std::log(n_i);
       neff_event[e] = S.s1 * S.s1 / S.s2;
-      for (int i = 0; i < NP; ++i) ev_grad[(size_t)e * NP + i] = S.g[i] / S.s1;
+      for (int i = 0; i < NP; ++i) {
+        ev_grad[(size_t)e * NP + i] = S.g[i] / S.s1;
+        ev_gabs[(size_t)e * NP + i] = S.gabs[i] / S.s1;
+      }
     }
   }
 
@@ -579,21 +593,25 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
     parts[(size_t)c] = sums_of(ls);
   }
   const Sums<T> Ssel = merge(parts);
-  double sel_grad[NP] = {0};
+  double sel_grad[NP] = {0}, sel_gabs[NP] = {0};
   if (Ssel.n_pos == 0) {
     *ln_xi = NEG_INF;
     *neff_sel = 0.0;
   } else {
     *ln_xi = Ssel.m + std::log(Ssel.s1) - std::log(in.n_draw);
     *neff_sel = Ssel.s1 * Ssel.s1 / Ssel.s2;
-    for (int i = 0; i < NP; ++i) sel_grad[i] = Ssel.g[i] / Ssel.s1;
+    for (int i = 0; i < NP; ++i) {
+      sel_grad[i] = Ssel.g[i] / Ssel.s1;
+      sel_gabs[i] = Ssel.gabs[i] / Ssel.s1;
+    }
   }
 
   // ---- total = sum_i ln L_i - N_det ln xi (Neumaier-compensated sum in event order)
-  bool neff_fail = false;
+  bool neff_fail = false, dead = false;
   double sum = 0.0, comp_ = 0.0;
   for (int e = 0; e < ne; ++e) {
     if (!(neff_event[e] >= neff_min_event)) neff_fail = true;
+    if (lnL_event[e] == NEG_INF) { dead = true; continue; }   // the product of Eq. 3 vanishes
     const double v = lnL_event[e];
     const double t = sum + v;
     if (std::fabs(sum) >= std::fabs(v)) comp_ += (sum - t) + v; else comp_ += (v - t) + sum;
@@ -605,7 +623,7 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
   if (neff_fail) *flag |= 2;
   if (neff_min_sel > 0.0 && !(*neff_sel >= neff_min_sel)) *flag |= 4;
   if (Ssel.n_pos == 0) *flag |= 8;
-  if (*flag) {
+  if (*flag || dead) {
     *lnL_total = NEG_INF;
     return;
   }
@@ -615,6 +633,13 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
       double g = 0.0;
       for (int e = 0; e < ne; ++e) g += ev_grad[(size_t)e * NP + i];
       grad[i] = g - (double)ne * sel_grad[i];
+    }
+  }
+  if (gscale) {
+    for (int i = 0; i < NP; ++i) {
+      double a = 0.0;
+      for (int e = 0; e < ne; ++e) a += ev_gabs[(size_t)e * NP + i];
+      gscale[i] = a + (double)ne * sel_gabs[i];
     }
   }
 }
@@ -633,11 +658,13 @@ extern "C" {
 // Full likelihood for K Lambda points.  Arrays are host memory; outputs are
 // lnL_event[K][n_events], neff_event[K][n_events], ln_xi[K], neff_sel[K],
 // lnL_total[K], flags[K] and, if grad_total != NULL, grad_total[K][13]
-// (want_grad != 0 selects the dual-number pass).  Returns 0, or -1 on invalid inputs.
+// (want_grad != 0 selects the dual-number pass).  grad_scale[K][13] (may be NULL)
+// receives sum_i sum_k p_ik |d ln w_ik| + N_det sum_m q_m |d ln w_m|, the size of the
+// terms whose difference is the gradient.  Returns 0, or -1 on invalid inputs.
 int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad,
                double neff_min_event, double neff_min_sel, int32_t n_threads, double* lnL_event,
                double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
-               int32_t* flags, double* grad_total) {
+               int32_t* flags, double* grad_total, double* grad_scale) {
   if (!in || K < 0 || !inputs_valid(*in)) return -1;
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -648,14 +675,15 @@ int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad
   const int ne = in->n_events;
   for (int k = 0; k < K; ++k) {
     double* g = (want_grad && grad_total) ? grad_total + (size_t)k * NP : nullptr;
+    double* gs = (want_grad && grad_scale) ? grad_scale + (size_t)k * NP : nullptr;
     if (want_grad)
       eval_lambda<Dual>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
                         lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
-                        neff_sel + k, lnL_total + k, flags + k, g);
+                        neff_sel + k, lnL_total + k, flags + k, g, gs);
     else
       eval_lambda<double>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
                           lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
-                          neff_sel + k, lnL_total + k, flags + k, nullptr);
+                          neff_sel + k, lnL_total + k, flags + k, nullptr, nullptr);
   }
   return 0;
 }
@@ -698,15 +726,16 @@ double orc_ln_Nz(const double* L, const double* pbar, int32_t nz, double zmax) {
   return flog(Nz_of(pb, zmax, pop_from(L)));
 }
 
-// The LOS cell index as the CUDA library defines it on single-precision z:
-// s = (float)((nz - 1) / zmax) (rounded once from double), t = z * s rounded to
-// single precision, j = floor(t) clamped to [0, nz - 2].
-int32_t orc_los_cell_f32(float z, int32_t nz, double zmax) {
-  const float s = (float)((double)(nz - 1) / zmax);
-  const volatile float t = z * s;
-  int j = (int)std::floor((double)t);
-  if (j < 0) j = 0;
+// The LOS grid cell of z, as used by los_interp above and as the CUDA library documents
+// it: floor(z * ((nz - 1) / zmax)) in double precision, clamped to [0, nz - 2]; -1 for
+// z outside [0, zmax].
+int32_t orc_los_cell(float zf, int32_t nz, double zmax) {
+  const double z = (double)zf;
+  if (z < 0.0 || z > zmax) return -1;
+  const double s = (double)(nz - 1) / zmax;
+  int j = (int)std::floor(z * s);
   if (j > nz - 2) j = nz - 2;
+  if (j < 0) j = 0;
   return j;
 }
 

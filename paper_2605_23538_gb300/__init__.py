@@ -1,0 +1,345 @@
+"""Python binding of libgwc.so, the GB300 dark-siren hierarchical likelihood.
+
+Argument marshalling only: every step of the likelihood runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams; there is no CPU fallback, and
+every entry point raises if the compiled library is missing or a call fails.
+
+Names mirror the C ABI in include/gwc.h:
+    create / destroy / loglik / loglik_grad / loglik_plain / loglik_grad_host /
+    get_info / last_error / los_cell_index / default_options
+The ``Context`` class wraps a gwc_ctx, and ``GwcLogLik`` is the autograd.Function
+whose backward applies the gradient computed in the same pass as the value.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+NUM_PARAMS = 13
+FLAG_DOMAIN, FLAG_NEFF_EVENT, FLAG_NEFF_SEL, FLAG_XI_ZERO = 1, 2, 4, 8
+LOS_F32, LOS_BF16 = 0, 1
+STATUS = {0: "GWC_OK", -1: "GWC_E_INVALID", -2: "GWC_E_CUDA", -3: "GWC_E_NOMEM",
+          -4: "GWC_E_TIMEOUT", -5: "GWC_E_UNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgwc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class GwcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Events(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_int32), ("offsets", ctypes.c_void_p),
+                ("m1_det", ctypes.c_void_p), ("m2_det", ctypes.c_void_p),
+                ("dl_mpc", ctypes.c_void_p), ("ln_pe_prior", ctypes.c_void_p),
+                ("pix", ctypes.c_void_p)]
+
+
+class Los(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int32), ("n_z", ctypes.c_int32), ("z_max", ctypes.c_double),
+                ("dtype", ctypes.c_int32), ("p_z", ctypes.c_void_p)]
+
+
+class Injections(ctypes.Structure):
+    _fields_ = [("n_found", ctypes.c_int64), ("n_draw", ctypes.c_double),
+                ("m1_det", ctypes.c_void_p), ("m2_det", ctypes.c_void_p),
+                ("dl_mpc", ctypes.c_void_p), ("ln_p_draw", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("neff_min_event", ctypes.c_double), ("neff_min_sel", ctypes.c_double),
+                ("accum", ctypes.c_int32), ("los_dtype", ctypes.c_int32),
+                ("n_x_table", ctypes.c_int32), ("max_K", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_int32), ("n_samples", ctypes.c_int64),
+                ("n_injections", ctypes.c_int64), ("n_pix", ctypes.c_int32),
+                ("n_z", ctypes.c_int32), ("n_items", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("n_x_table", ctypes.c_int32), ("max_K", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
+           "gwc_loglik_plain", "gwc_loglik_grad_host", "gwc_destroy", "gwc_last_error",
+           "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read")
+
+
+def lib():
+    """Load libgwc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2605_23538_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.gwc_default_options.restype = None
+        L.gwc_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.gwc_create.restype = ctypes.c_int
+        L.gwc_create.argtypes = [ctypes.POINTER(Events), ctypes.POINTER(Los),
+                                 ctypes.POINTER(Injections), ctypes.POINTER(Options),
+                                 ctypes.POINTER(vp)]
+        L.gwc_loglik.restype = ctypes.c_int
+        L.gwc_loglik.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gwc_loglik_grad.restype = ctypes.c_int
+        L.gwc_loglik_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gwc_loglik_plain.restype = ctypes.c_int
+        L.gwc_loglik_plain.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gwc_loglik_grad_host.restype = ctypes.c_int
+        L.gwc_loglik_grad_host.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.gwc_destroy.restype = None
+        L.gwc_destroy.argtypes = [vp]
+        L.gwc_last_error.restype = ctypes.c_char_p
+        L.gwc_last_error.argtypes = [vp]
+        L.gwc_get_info.restype = ctypes.c_int
+        L.gwc_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.gwc_profile_enable.restype = ctypes.c_int
+        L.gwc_profile_enable.argtypes = [vp, i32]
+        L.gwc_profile_read.restype = ctypes.c_int
+        L.gwc_profile_read.argtypes = [vp, vp, vp]
+        L.gwc_los_cell_index.restype = ctypes.c_int
+        L.gwc_los_cell_index.argtypes = [vp, i64, i32, d, vp, vp]
+        _lib = L
+        return L
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().gwc_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def last_error(ctx=None) -> str:
+    msg = lib().gwc_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        raise GwcError(status, last_error(ctx))
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def create(cat: dict, options: Options | None = None, los_dtype_in: int = LOS_F32):
+    """gwc_create from a catalogue dict of numpy arrays (see synth.catalogue)."""
+    keep = {}
+
+    def arr(key, dt):
+        a = np.ascontiguousarray(cat[key], dtype=dt)
+        keep[key] = a
+        return _np_ptr(a)
+
+    los = np.ascontiguousarray(cat["los"], dtype=np.uint16 if los_dtype_in == LOS_BF16 else np.float32)
+    keep["los"] = los
+    n_ev = len(cat["offsets"]) - 1
+    ev = Events(n_events=n_ev, offsets=arr("offsets", np.int64), m1_det=arr("m1", np.float32),
+                m2_det=arr("m2", np.float32), dl_mpc=arr("dl", np.float32),
+                ln_pe_prior=arr("lnpe", np.float32), pix=arr("pix", np.int32))
+    lo = Los(n_pix=los.shape[0], n_z=los.shape[1], z_max=float(cat["z_max"]), dtype=los_dtype_in,
+             p_z=_np_ptr(los))
+    inj = Injections(n_found=len(cat["inj_m1"]), n_draw=float(cat["n_draw"]),
+                     m1_det=arr("inj_m1", np.float32), m2_det=arr("inj_m2", np.float32),
+                     dl_mpc=arr("inj_dl", np.float32), ln_p_draw=arr("inj_lnpd", np.float32))
+    out = ctypes.c_void_p()
+    opt = options if options is not None else default_options()
+    st = lib().gwc_create(ctypes.byref(ev), ctypes.byref(lo), ctypes.byref(inj), ctypes.byref(opt),
+                          ctypes.byref(out))
+    _check(st)
+    return out
+
+
+def destroy(ctx):
+    lib().gwc_destroy(ctx)
+
+
+def get_info(ctx) -> dict:
+    info = Info()
+    _check(lib().gwc_get_info(ctx, ctypes.byref(info)), ctx)
+    return {f: getattr(info, f) for f, _ in Info._fields_}
+
+
+def _outputs(K, n_ev, device, grad):
+    import torch
+    f64 = dict(dtype=torch.float64, device=device)
+    out = dict(lnL_event=torch.empty((K, n_ev), **f64), neff_event=torch.empty((K, n_ev), **f64),
+               ln_xi=torch.empty(K, **f64), neff_sel=torch.empty(K, **f64),
+               lnL_total=torch.empty(K, **f64),
+               flags=torch.empty(K, dtype=torch.int32, device=device))
+    if grad:
+        out["grad_total"] = torch.empty((K, NUM_PARAMS), **f64)
+    return out
+
+
+def _call(fn, ctx, lam, n_events, grad, stream, out, plain=False):
+    import torch
+    if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
+        raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
+    lam = lam.contiguous()
+    K = lam.shape[0]
+    if out is None:
+        out = _outputs(K, n_events, lam.device, grad)
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    args = [ctx, K, p(lam), p(out["lnL_event"]), p(out["neff_event"]), p(out["ln_xi"]),
+            p(out["neff_sel"]), p(out["lnL_total"]), p(out["flags"])]
+    if grad or plain:
+        args.append(p(out.get("grad_total")))
+    args.append(_stream_ptr(stream))
+    _check(fn(*args), ctx)
+    return out
+
+
+def loglik(ctx, lam, n_events, stream=None, out=None):
+    """gwc_loglik: lam is a CUDA float64 tensor [K, 13]; returns a dict of tensors."""
+    return _call(lib().gwc_loglik, ctx, lam, n_events, False, stream, out)
+
+
+def loglik_grad(ctx, lam, n_events, stream=None, out=None):
+    """gwc_loglik_grad: as loglik, plus grad_total [K, 13]."""
+    return _call(lib().gwc_loglik_grad, ctx, lam, n_events, True, stream, out)
+
+
+def loglik_plain(ctx, lam, n_events, grad=True, stream=None, out=None):
+    """gwc_loglik_plain: the single-Lambda baseline path (same outputs)."""
+    if out is None:
+        import torch
+        out = _outputs(lam.shape[0], n_events, lam.device, grad)
+        if not grad:
+            out["grad_total"] = None
+    return _call(lib().gwc_loglik_plain, ctx, lam, n_events, False, stream, out, plain=True)
+
+
+def loglik_grad_host(ctx, lam: np.ndarray, grad=True, stream=None):
+    """gwc_loglik_grad_host: host Lambda in, host total / flags / gradient out."""
+    lam = np.ascontiguousarray(np.atleast_2d(lam), dtype=np.float64)
+    K = lam.shape[0]
+    tot = np.empty(K, np.float64)
+    flags = np.empty(K, np.int32)
+    g = np.empty((K, NUM_PARAMS), np.float64) if grad else None
+    st = lib().gwc_loglik_grad_host(ctx, K, _np_ptr(lam), _np_ptr(tot), _np_ptr(flags),
+                                    _np_ptr(g) if grad else None, _stream_ptr(stream))
+    _check(st, ctx)
+    return (tot, flags, g) if grad else (tot, flags)
+
+
+def profile_enable(ctx, enable=True):
+    """gwc_profile_enable: record per-stage CUDA events in every call."""
+    _check(lib().gwc_profile_enable(ctx, int(bool(enable))), ctx)
+
+
+def profile_read(ctx):
+    """gwc_profile_read: (ms[prologue, samples, merge], n_calls) since the last read."""
+    ms = np.zeros(3, np.float64)
+    n = np.zeros(1, np.int64)
+    _check(lib().gwc_profile_read(ctx, _np_ptr(ms), _np_ptr(n)), ctx)
+    return ms, int(n[0])
+
+
+def los_cell_index(z, n_z, z_max, stream=None):
+    """gwc_los_cell_index on a CUDA float32 tensor; returns int32 cells (-1 outside)."""
+    import torch
+    z = z.contiguous()
+    cell = torch.empty(z.shape, dtype=torch.int32, device=z.device)
+    st = lib().gwc_los_cell_index(ctypes.c_void_p(z.data_ptr()), z.numel(), n_z, z_max,
+                                  ctypes.c_void_p(cell.data_ptr()), _stream_ptr(stream))
+    _check(st)
+    return cell
+
+
+class Context:
+    """A gwc_ctx: the catalogue resident on the device, evaluated at Lambda batches."""
+
+    def __init__(self, cat: dict, options: Options | None = None, **opt_kw):
+        if options is None:
+            options = default_options(**opt_kw)
+        self.options = options
+        self.n_events = len(cat["offsets"]) - 1
+        self._ctx = create(cat, options)
+
+    def loglik(self, lam, stream=None):
+        return loglik(self._ctx, lam, self.n_events, stream)
+
+    def loglik_grad(self, lam, stream=None):
+        return loglik_grad(self._ctx, lam, self.n_events, stream)
+
+    def loglik_plain(self, lam, grad=True, stream=None):
+        return loglik_plain(self._ctx, lam, self.n_events, grad, stream)
+
+    def loglik_grad_host(self, lam, grad=True, stream=None):
+        return loglik_grad_host(self._ctx, lam, grad, stream)
+
+    def info(self):
+        return get_info(self._ctx)
+
+    def profile_enable(self, enable=True):
+        profile_enable(self._ctx, enable)
+
+    def profile_read(self):
+        return profile_read(self._ctx)
+
+    def close(self):
+        if self._ctx is not None:
+            destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _autograd_function():
+    import torch
+
+    class GwcLogLik(torch.autograd.Function):
+        """Total log-likelihood [K] of a Lambda batch; backward uses the fused gradient."""
+
+        @staticmethod
+        def forward(ctx, lam, context):
+            out = context.loglik_grad(lam.detach())
+            ctx.save_for_backward(out["grad_total"])
+            return out["lnL_total"]
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out[:, None] * g, None
+
+    return GwcLogLik
+
+
+def __getattr__(name):
+    if name == "GwcLogLik":
+        fn = _autograd_function()
+        globals()["GwcLogLik"] = fn
+        return fn
+    raise AttributeError(name)

@@ -1,0 +1,878 @@
+// gwc_kernels.cu -- CUDA kernels of the dark-siren likelihood (sm_103a).
+//
+//   k_prologue   one CTA per Lambda, FP64: domain check, the d_L(z) inversion table
+//                (Eq. 1), mass-model normalisations and smoothing-window tables, the
+//                redshift-prior normalisation, and the constants each sample needs.
+//   k_fused      the hot loop: a CTA stages a chunk of samples (or injections) in
+//                shared memory once and its warps sweep them for a tile of Lambda
+//                points, each warp accumulating the per-(chunk, Lambda) logsumexp
+//                partial (max, sum w, sum w^2 and, with the gradient, 13 weighted
+//                derivatives) of Eqs. 5-7 online in registers.
+//   k_plain_*    the single-Lambda baseline: per-sample weights written to memory and
+//                reduced in separate passes.
+//   k_merge      one CTA per Lambda, FP64: merges the partials of each event in a fixed
+//                order into ln L_i and N_eff,i, the injection partials into ln xi, and
+//                forms the total of Eq. 3 and its gradient.  Deterministic.
+#include "gwc_internal.cuh"
+#include "gwc_kernels.h"
+
+#include <cfloat>
+
+namespace gwc {
+
+__constant__ double c_glx[NGL];   // Gauss-Legendre nodes on [-1, 1]
+__constant__ double c_glw[NGL];   // and weights
+
+cudaError_t set_gauss_legendre(const double* x, const double* w) {
+  cudaError_t e = cudaMemcpyToSymbol(c_glx, x, sizeof(double) * NGL);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_glw, w, sizeof(double) * NGL);
+}
+
+// ------------------------------------------------------------------ FP64 helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sums of V values (fixed order); every thread gets the totals
+template <int V>
+__device__ void block_sum(double (&v)[V], double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < V; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+    for (int i = 0; i < V; ++i) red[i * 32 + w] = v[i];
+  __syncthreads();
+  if (threadIdx.x < V) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += red[threadIdx.x * 32 + k];
+    red[threadIdx.x * 32] = s;
+  }
+  __syncthreads();
+  for (int i = 0; i < V; ++i) v[i] = red[i * 32];
+  __syncthreads();
+}
+
+// inclusive scan of V values over the block (fixed order)
+template <int V>
+__device__ void block_scan(double (&v)[V], double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, v[i], o);
+      if (lane >= o) v[i] += y;
+    }
+  }
+  if (lane == 31)
+    for (int i = 0; i < V; ++i) red[i * 32 + w] = v[i];
+  __syncthreads();
+  for (int i = 0; i < V; ++i) {
+    double off = 0.0;
+    for (int k = 0; k < w; ++k) off += red[i * 32 + k];
+    v[i] += off;
+  }
+  __syncthreads();
+  (void)nw;
+}
+
+__device__ __forceinline__ double softplus_d(double a) {
+  return a > 0.0 ? a + log1p(exp(-a)) : log1p(exp(a));
+}
+__device__ __forceinline__ double sigmoid_d(double a) {
+  return a >= 0.0 ? 1.0 / (1.0 + exp(-a)) : exp(a) / (1.0 + exp(a));
+}
+
+// S(m), 1 - S(m) and dS/d(delta_m) inside the smoothing window (0 < mp < dm)
+__device__ __forceinline__ void smooth_d(double mp, double dm, double& S, double& oneS, double& dSddm) {
+  const double f = dm / mp + dm / (mp - dm);
+  if (f > 0.0) {
+    const double e = exp(-f);
+    S = e / (1.0 + e);
+    oneS = 1.0 / (1.0 + e);
+  } else {
+    const double e = exp(f);
+    S = 1.0 / (1.0 + e);
+    oneS = e / (1.0 + e);
+  }
+  const double dfddm = 1.0 / mp + mp / ((mp - dm) * (mp - dm));
+  dSddm = -S * oneS * dfddm;
+}
+
+__device__ bool lambda_ok(const double* L) {
+  for (int i = 0; i < NP; ++i)
+    if (!isfinite(L[i])) return false;
+  return L[P_H0] > 0.0 && L[P_OM] >= 0.0 && L[P_OM] <= 1.0 && L[P_MMIN] > 0.0 &&
+         L[P_MMAX] > L[P_MMIN] && L[P_DM] >= 0.0 && L[P_MMIN] + L[P_DM] < L[P_MMAX] &&
+         L[P_SIG] > 0.0 && L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0 && L[P_ZP] > -1.0;
+}
+
+// ---------------------------------------------------------------------- prologue
+constexpr int PRO_THREADS = 256;
+constexpr int ZPANELS = 256;   // panels of the z quadrature (one per thread)
+
+__global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
+  extern __shared__ double sdyn[];               // 2 * nx doubles: P_n, D_n
+  __shared__ double sI[ZPANELS + 1], sJ[ZPANELS + 1], sD[ZPANELS + 1];
+  __shared__ double red[32 * 16];
+  __shared__ double sc[32];                      // scalar broadcast
+
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const double* L = A.lam + (size_t)k * NP;
+  LamF* lf = A.lf + k;
+  LamD* ld = A.ld + k;
+  float* tb = A.tables + (size_t)k * A.tstride;
+  const int nx = A.nx, nz = A.nz;
+  const double zmax = A.zmax;
+
+  if (!lambda_ok(L)) {
+    if (tid == 0) {
+      LamF f;
+      memset(&f, 0, sizeof(f));
+      f.xmax = -1.f;
+      *lf = f;
+      ld->c = 0.0;
+      for (int i = 0; i < NP; ++i) ld->dc[i] = 0.0;
+      ld->flag = 1;
+    }
+    return;
+  }
+  const double H0 = L[P_H0], om = L[P_OM], alpha = L[P_ALPHA], beta = L[P_BETA];
+  const double mmin = L[P_MMIN], mmax = L[P_MMAX], dm = L[P_DM], mu = L[P_MU], sig = L[P_SIG];
+  const double lam = L[P_LAM], gam = L[P_GAM], kap = L[P_KAP], zp = L[P_ZP];
+
+  // ---- (1) I(z) and J(z) = dI/dOm on panel edges of [0, zmax]
+  const double hz = zmax / ZPANELS;
+  {
+    double v[2] = {0.0, 0.0};
+    const double za = tid * hz;
+    for (int q = 0; q < NGL; ++q) {
+      const double zq = za + 0.5 * hz * (1.0 + c_glx[q]);
+      const double u = 1.0 + zq, u3 = u * u * u;
+      const double E2 = om * (u3 - 1.0) + 1.0, E = sqrt(E2);
+      v[0] += c_glw[q] / E;
+      v[1] += c_glw[q] * (-0.5 * (u3 - 1.0) / (E2 * E));
+    }
+    v[0] *= 0.5 * hz;
+    v[1] *= 0.5 * hz;
+    block_scan<2>(v, red);
+    sI[tid + 1] = v[0];
+    sJ[tid + 1] = v[1];
+    if (tid == 0) { sI[0] = 0.0; sJ[0] = 0.0; }
+    __syncthreads();
+    for (int p = tid; p <= ZPANELS; p += PRO_THREADS) sD[p] = (1.0 + p * hz) * sI[p];
+    __syncthreads();
+  }
+  const double xmax = sD[ZPANELS];
+  const double dx = xmax / (nx - 1);
+  const double pscale = (double)(nz - 1) / zmax;   // LOS grid units per unit z
+
+  // ---- (2) inversion table on the uniform x grid
+  float2* jt = reinterpret_cast<float2*>(tb + 5 * nx);
+  for (int n = tid; n < nx; n += PRO_THREADS) {
+    const double xn = (n == nx - 1) ? xmax : n * dx;
+    double z = 0.0, Dp = 1.0, Jz = 0.0, jd = 0.0;
+    if (n > 0) {
+      int lo = 0, hi = ZPANELS - 1;   // largest p with sD[p] <= xn
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sD[mid] <= xn) lo = mid; else hi = mid - 1;
+      }
+      const int p = lo;
+      const double z0 = p * hz;
+      z = z0 + hz * (xn - sD[p]) / (sD[p + 1] - sD[p]);
+      double Iz = 0.0, E = 1.0;
+      for (int it = 0; it < 5; ++it) {
+        // I(z) = I(z0) + int_{z0}^{z} dz'/E by the Gauss-Legendre rule
+        const double h = z - z0;
+        double acc = 0.0;
+        for (int q = 0; q < NGL; ++q) {
+          const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
+          const double u = 1.0 + zq;
+          acc += c_glw[q] / sqrt(om * (u * u * u - 1.0) + 1.0);
+        }
+        Iz = sI[p] + 0.5 * h * acc;
+        const double u = 1.0 + z;
+        E = sqrt(om * (u * u * u - 1.0) + 1.0);
+        Dp = Iz + u / E;
+        if (it == 4) break;
+        z -= (u * Iz - xn) / Dp;
+        z = fmin(fmax(z, z0), z0 + hz);
+      }
+      const double h = z - z0;
+      double accj = 0.0;
+      for (int q = 0; q < NGL; ++q) {
+        const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
+        const double u = 1.0 + zq, u3 = u * u * u, E2 = om * (u3 - 1.0) + 1.0;
+        accj += c_glw[q] * (-0.5 * (u3 - 1.0) / (E2 * sqrt(E2)));
+      }
+      Jz = sJ[p] + 0.5 * h * accj;
+      const double u = 1.0 + z, u3 = u * u * u, E2 = om * (u3 - 1.0) + 1.0;
+      jd = -0.5 * (u3 - 1.0) / (E2 * sqrt(E2));
+    }
+    sdyn[2 * n] = z * pscale;                // P_n
+    sdyn[2 * n + 1] = pscale / Dp * dx;      // dP/dx * dx
+    if (A.want_grad) jt[n] = make_float2((float)Jz, (float)(jd / Dp * dx));
+  }
+  __syncthreads();
+  float4* pos = reinterpret_cast<float4*>(tb);
+  float* pc3 = tb + 4 * nx;
+  for (int n = tid; n < nx; n += PRO_THREADS) {
+    const double P0 = sdyn[2 * n], D0 = sdyn[2 * n + 1];
+    double c2 = 0.0, c3 = 0.0;
+    if (n < nx - 1) {
+      const double P1 = sdyn[2 * n + 2], D1 = sdyn[2 * n + 3];
+      c2 = 3.0 * (P1 - P0) - 2.0 * D0 - D1;
+      c3 = 2.0 * (P0 - P1) + D0 + D1;
+    }
+    const float hi = (float)P0;
+    pos[n] = make_float4(hi, (float)(P0 - (double)hi), (float)D0, (float)c2);
+    pc3[n] = (float)c3;
+  }
+
+  // ---- (3) mass-model normalisations (thread 0), broadcast through shared memory
+  if (tid == 0) {
+    // Z_P = int_{mmin}^{mmax} m^-alpha dm = e^{t a} (b - a) phi1(t (b - a)), t = 1 - alpha
+    const double t = 1.0 - alpha, a = log(mmin), b = log(mmax), Lr = b - a, y = t * Lr;
+    const double phi1 = fabs(y) < 1e-5 ? 1.0 + y * (0.5 + y / 6.0) : expm1(y) / y;
+    const double gy = fabs(y) < 1e-5 ? 0.5 + y / 12.0 : 1.0 / (-expm1(-y)) - 1.0 / y;
+    const double lnZP = t * a + log(Lr) + log(phi1);
+    sc[0] = lnZP;
+    sc[1] = -(a + Lr * gy);                          // d ln Z_P / d alpha
+    sc[2] = -exp(-alpha * a - lnZP);                 // d ln Z_P / d m_min
+    sc[3] = exp(-alpha * b - lnZP);                  // d ln Z_P / d m_max
+    // Z_G = Phi(B) - Phi(A)
+    const double A_ = (mmin - mu) / sig, B_ = (mmax - mu) / sig, r2 = 0.70710678118654752440;
+    double ZG;
+    if (A_ > 0.0) ZG = 0.5 * (erfc(A_ * r2) - erfc(B_ * r2));
+    else if (B_ < 0.0) ZG = 0.5 * (erfc(-B_ * r2) - erfc(-A_ * r2));
+    else ZG = 1.0 - 0.5 * (erfc(B_ * r2) + erfc(-A_ * r2));
+    const double phA = 0.39894228040143267794 * exp(-0.5 * A_ * A_);
+    const double phB = 0.39894228040143267794 * exp(-0.5 * B_ * B_);
+    sc[4] = log(ZG);
+    sc[5] = (phA - phB) / (sig * ZG);                // d ln Z_G / d mu
+    sc[6] = (A_ * phA - B_ * phB) / (sig * ZG);      // d ln Z_G / d sigma
+    sc[7] = -phA / (sig * ZG);                       // d ln Z_G / d m_min
+    sc[8] = phB / (sig * ZG);                        // d ln Z_G / d m_max
+  }
+  __syncthreads();
+  const double lnZP = sc[0], dZPa = sc[1], dZPmin = sc[2], dZPmax = sc[3];
+  const double lnZG = sc[4], dZGmu = sc[5], dZGsig = sc[6], dZGmin = sc[7], dZGmax = sc[8];
+  const double lnsig2pi = log(sig) + 0.91893853320467274178;
+
+  // ---- (4) smoothing window [mmin, mmin + dm]: W = int h (1 - S), its derivatives,
+  //          and the cumulative C-family integrals at the table nodes
+  const double hw = dm / NW_WIN;
+  double cum[4] = {0.0, 0.0, 0.0, 0.0};   // C, C_beta, J, K over this thread's panel
+  double wv[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (tid < NW_WIN && dm > 0.0) {
+    const double ma = mmin + tid * hw;
+    for (int q = 0; q < NGL; ++q) {
+      const double m = ma + 0.5 * hw * (1.0 + c_glx[q]);
+      const double mp = m - mmin, lm = log(m);
+      double S, oneS, dSddm;
+      smooth_d(mp, dm, S, oneS, dSddm);
+      const double mb = exp(beta * lm);
+      const double w = c_glw[q] * 0.5 * hw;
+      cum[0] += w * mb * S;
+      cum[1] += w * mb * lm * S;
+      cum[2] += w * mb / m * S;
+      cum[3] += w * mb * dSddm;
+      const double P = exp(-alpha * lm - lnZP);
+      const double zg = (m - mu) / sig;
+      const double G = exp(-0.5 * zg * zg - lnsig2pi - lnZG);
+      const double h = (1.0 - lam) * P + lam * G;
+      wv[0] += w * h * oneS;
+      wv[1] += w * (1.0 - lam) * P * (-lm - dZPa) * oneS;
+      wv[2] += w * (G - P) * oneS;
+      wv[3] += w * lam * G * (zg / sig - dZGmu) * oneS;
+      wv[4] += w * lam * G * ((zg * zg - 1.0) / sig - dZGsig) * oneS;
+      wv[5] += w * P * oneS;
+      wv[6] += w * G * oneS;
+      wv[7] += w * ((1.0 - lam) * P * (-alpha / m - dZPmin) + lam * G * (-zg / sig - dZGmin)) * oneS;
+      wv[8] += w * (-h * dSddm);
+    }
+  }
+  block_sum<9>(wv, red);
+  block_scan<4>(cum, red);   // inclusive: cum at node tid + 1
+  const double W = wv[0];
+  const double Zm1 = 1.0 - W;
+  // d ln Z_m1 / d theta = -dW/d theta / Z_m1
+  const double dWa = wv[1], dWl = wv[2], dWmu = wv[3], dWsig = wv[4];
+  const double dWmax = -(1.0 - lam) * dZPmax * wv[5] - lam * dZGmax * wv[6];
+  const double dWmin = wv[7], dWdm = wv[8];
+
+  // window tables: ratios R = I(m) / (m^beta S(m)) at nodes m_k = mmin + k hw
+  float2* win = reinterpret_cast<float2*>(tb + 7 * nx);
+  __shared__ double scum[4][NW_WIN + 1];
+  if (tid < NW_WIN)
+    for (int i = 0; i < 4; ++i) scum[i][tid + 1] = cum[i];
+  if (tid == 0)
+    for (int i = 0; i < 4; ++i) scum[i][0] = 0.0;
+  __syncthreads();
+  if (tid <= NW_WIN) {
+    float2 r[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                   make_float2(0.f, 0.f)};
+    if (tid > 0 && dm > 0.0) {
+      const double m = mmin + tid * hw, mp = m - mmin, lm = log(m);
+      double S = 1.0, oneS = 0.0, dSddm = 0.0, dlnS = 0.0, dSS = 0.0;
+      if (tid < NW_WIN) {
+        smooth_d(mp, dm, S, oneS, dSddm);
+        dlnS = oneS * dm * (1.0 / (mp * mp) + 1.0 / ((mp - dm) * (mp - dm)));
+        dSS = -oneS * (1.0 / mp + mp / ((mp - dm) * (mp - dm)));   // (dS/d delta_m) / S
+      }
+      const double g = exp(beta * lm) * S;
+      const double gl = beta / m + dlnS;     // g'/g
+      const double Rc = scum[0][tid] / g, Rb = scum[1][tid] / g;
+      const double Rj = scum[2][tid] / g, Rk = scum[3][tid] / g;
+      r[0] = make_float2((float)Rc, (float)((1.0 - Rc * gl) * hw));
+      r[1] = make_float2((float)Rb, (float)((lm - Rb * gl) * hw));
+      r[2] = make_float2((float)Rj, (float)((1.0 / m - Rj * gl) * hw));
+      r[3] = make_float2((float)Rk, (float)((dSS - Rk * gl) * hw));
+    }
+    for (int i = 0; i < 4; ++i) win[i * (NW_WIN + 1) + tid] = r[i];
+  }
+
+  // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
+  //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
+  const double gpk = gam + kap, lp = log1p(zp);
+  {
+    const double dzg = zmax / (nz - 1);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < nz; j += PRO_THREADS) {
+      const double zj = j * dzg, l = log1p(zj);
+      const double r = gpk * (l - lp);
+      const double term = ((j == 0 || j == nz - 1) ? 0.5 : 1.0) * dzg * A.pbar64[j] *
+                          exp(gam * l - softplus_d(r) - l);
+      const double s = sigmoid_d(r);
+      v[0] += term;
+      v[1] += term * (l - s * (l - lp));
+      v[2] += term * (-s * (l - lp));
+      v[3] += term * (s * gpk / (1.0 + zp));
+    }
+    block_sum<4>(v, red);
+    if (tid == 0) {
+      sc[16] = v[0];
+      sc[17] = v[1] / v[0];
+      sc[18] = v[2] / v[0];
+      sc[19] = v[3] / v[0];
+    }
+  }
+  __syncthreads();
+
+  // ---- (6) constants
+  if (tid == 0) {
+    const double Nz = sc[16];
+    const double Cw = dm > 0.0 ? scum[0][NW_WIN] : 0.0;
+    const double Cwb = dm > 0.0 ? scum[1][NW_WIN] : 0.0;
+    const double Jw = dm > 0.0 ? scum[2][NW_WIN] : 0.0;
+    const double Kw = dm > 0.0 ? scum[3][NW_WIN] : 0.0;
+    const double mw = mmin + dm, eps = 1.0 + beta;
+    LamF f;
+    f.H0c = (float)(H0 / C_KMS);
+    f.xmax = (float)xmax;
+    f.inv_dx = (float)(1.0 / dx);
+    f.live = 1.f;
+    f.om = (float)om;
+    f.zstep = (float)(zmax / (nz - 1));
+    f.inv_zstep = (float)pscale;
+    f.lp = (float)lp;
+    f.alpha = (float)alpha;
+    f.beta = (float)beta;
+    f.mmin = (float)mmin;
+    f.mmax = (float)mmax;
+    f.dm = (float)dm;
+    f.mw = (float)mw;
+    f.mu = (float)mu;
+    f.inv_sig = (float)(1.0 / sig);
+    f.la = lam < 1.0 ? (float)(log1p(-lam) - lnZP) : -INFINITY;
+    f.lb = lam > 0.0 ? (float)(log(lam) - lnsig2pi - lnZG) : -INFINITY;
+    f.Cw = (float)Cw;
+    f.mw1b = (float)exp(eps * log(mw));
+    f.eps_b = (float)eps;
+    f.inv_eps_b = fabs(eps) > 1e-30 ? (float)(1.0 / eps) : 0.f;
+    f.lmw = (float)log(mw);
+    f.gam = (float)gam;
+    f.gpk = (float)gpk;
+    f.inv_wh = dm > 0.0 ? (float)(NW_WIN / dm) : 0.f;
+    f.invH0 = (float)(1.0 / H0);
+    f.inv1zp = (float)(1.0 / (1.0 + zp));
+    f.dZPa = (float)dZPa;
+    f.dZPmin = (float)dZPmin;
+    f.dZPmax = (float)dZPmax;
+    f.dZGmu = (float)dZGmu;
+    f.dZGsig = (float)dZGsig;
+    f.dZGmin = (float)dZGmin;
+    f.dZGmax = (float)dZGmax;
+    f.Cwb = (float)Cwb;
+    f.Jw = (float)Jw;
+    f.Kw = (float)Kw;
+    f.la0 = (float)(-lnZP);
+    f.lb0 = (float)(-lnsig2pi - lnZG);
+    f.lam = (float)lam;
+    f.inv_lam = lam > 0.0 ? (float)(1.0 / lam) : 0.f;
+    f.inv_1ml = lam < 1.0 ? (float)(1.0 / (1.0 - lam)) : 0.f;
+    f.pad = 0.f;
+    *lf = f;
+    // c = -ln N'_z - ln Z_m1 + ln(H0 / c)
+    ld->c = -log(Nz) - log(Zm1) + log(H0 / C_KMS);
+    double dc[NP];
+    for (int i = 0; i < NP; ++i) dc[i] = 0.0;
+    const double iZ = 1.0 / Zm1;   // -d ln Z_m1 = dW / Z_m1
+    dc[P_H0] = 1.0 / H0;
+    dc[P_ALPHA] = dWa * iZ;
+    dc[P_MMIN] = dWmin * iZ;
+    dc[P_MMAX] = dWmax * iZ;
+    dc[P_DM] = dWdm * iZ;
+    dc[P_MU] = dWmu * iZ;
+    dc[P_SIG] = dWsig * iZ;
+    dc[P_LAM] = dWl * iZ;
+    dc[P_GAM] = -sc[17];
+    dc[P_KAP] = -sc[18];
+    dc[P_ZP] = -sc[19];
+    for (int i = 0; i < NP; ++i) ld->dc[i] = dc[i];
+    ld->flag = 0;
+  }
+}
+
+// ---------------------------------------------------------------- fused kernel
+template <bool GRAD, bool KAHAN, typename RowT>
+__global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
+  extern __shared__ __align__(16) float sm[];
+  const int CH = A.chunk;
+  float* s_m1 = sm;
+  float* s_m2 = s_m1 + CH;
+  float* s_dl = s_m2 + CH;
+  float* s_lpe = s_dl + CH;
+  float* s_lm1 = s_lpe + CH;
+  float* s_lm2 = s_lm1 + CH;
+  int* s_pix = reinterpret_cast<int*>(s_lm2 + CH);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int unit = blockIdx.x;
+  const int ipos = unit / A.n_slabs, slab = unit - ipos * A.n_slabs;
+  const int item = A.sched[ipos];
+  const Item it = A.items[item];
+  const bool inj = it.kind == 1;
+
+  const float4* src = inj ? A.inj : A.smp;
+  for (int i = tid; i < it.count; i += THREADS) {
+    const float4 v = __ldg(src + it.begin + i);
+    s_m1[i] = v.x;
+    s_m2[i] = v.y;
+    s_dl[i] = v.z;
+    s_lpe[i] = v.w;
+    s_lm1[i] = logf(v.x);
+    s_lm2[i] = logf(v.y);
+    s_pix[i] = inj ? 0 : __ldg(A.pix + it.begin + i);
+  }
+  __syncthreads();
+
+  const int k0 = slab * A.slab;
+  const int nk = min(A.slab, A.K - k0);
+  const int ntask = nk * A.P;
+  const int nx = A.nx, nz = A.nz;
+  for (int task = warp; task < ntask; task += WARPS) {
+    const int k = k0 + task / A.P, part = task - (task / A.P) * A.P;
+    const LamF L = A.lf[k];
+    Acc<GRAD, KAHAN> acc;
+    if (L.live != 0.f) {
+      const float* tb = A.tables + (size_t)k * A.tstride;
+      const float4* pos = reinterpret_cast<const float4*>(tb);
+      const float* pc3 = tb + 4 * nx;
+      const float2* jt = reinterpret_cast<const float2*>(tb + 5 * nx);
+      const float2* wt = reinterpret_cast<const float2*>(tb + 7 * nx);
+      const int a = (int)((long long)it.count * part / A.P);
+      const int b = (int)((long long)it.count * (part + 1) / A.P);
+      for (int i = a + lane; i < b; i += 32) {
+        SampleIn s;
+        s.m1 = s_m1[i]; s.m2 = s_m2[i]; s.dl = s_dl[i]; s.lpe = s_lpe[i];
+        s.lm1 = s_lm1[i]; s.lm2 = s_lm2[i];
+        float lw, g[GRAD ? NP : 1];
+        bool ok;
+        if (inj)
+          ok = sample_lnw<GRAD>(L, s, A.pbar32, nz, pos, pc3, nx, jt, wt, lw, g);
+        else
+          ok = sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
+                                nz, pos, pc3, nx, jt, wt, lw, g);
+        if (ok) acc.add(lw, g);
+      }
+      if (KAHAN) { acc.s1 -= acc.c1; acc.s2 -= acc.c2; }
+    }
+    // butterfly reduction across the warp (every lane ends with the same sums)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float om_ = __shfl_xor_sync(0xffffffffu, acc.m, o);
+      const float o1 = __shfl_xor_sync(0xffffffffu, acc.s1, o);
+      const float o2 = __shfl_xor_sync(0xffffffffu, acc.s2, o);
+      float og[GRAD ? NP : 1];
+      if (GRAD) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) og[i] = __shfl_xor_sync(0xffffffffu, acc.g[i], o);
+      }
+      acc.merge(om_, o1, o2, og);
+    }
+    float* out = A.partials + (((size_t)k * A.n_items + item) * A.P + part) * PSTRIDE;
+    if (lane == 0) {
+      out[0] = acc.m;
+      out[1] = acc.s1;
+      out[2] = acc.s2;
+    }
+    if (GRAD && lane < NP) {
+      float gv = 0.f;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) gv = (lane == i) ? acc.g[i] : gv;
+      out[3 + lane] = gv;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ plain path
+// pass 1 (value) and pass 3 (gradient): one thread per sample, one Lambda, tables and
+// samples straight from global memory.  Pass 1 writes ln w; pass 3 writes
+// e^(ln w - m_item) d ln w / d Lambda for the item's max m from pass 2.
+template <bool GRAD, typename RowT>
+__global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n_total) return;
+  const LamF L = A.lf[A.k];
+  const bool inj = i >= A.n_samples;
+  float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
+  SampleIn s;
+  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.lpe = v.w;
+  s.lm1 = logf(v.x); s.lm2 = logf(v.y);
+  const float* tb = A.tables + (size_t)A.k * A.tstride;
+  const int nx = A.nx;
+  float lw = -INFINITY, g[GRAD ? NP : 1];
+  bool ok = false;
+  if (L.live != 0.f) {
+    if (inj)
+      ok = sample_lnw<GRAD>(L, s, A.pbar32, A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
+                            reinterpret_cast<const float2*>(tb + 5 * nx),
+                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g);
+    else
+      ok = sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
+                            A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
+                            reinterpret_cast<const float2*>(tb + 5 * nx),
+                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g);
+  }
+  if (!GRAD) {
+    A.lw[i] = ok ? lw : -INFINITY;
+  } else {
+    const float m = A.partials[((size_t)A.k * A.n_items + A.sample_item[i]) * PSTRIDE];
+    const float t = ok ? expf(lw - m) : 0.f;
+    for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * g[q] : 0.f;
+  }
+}
+
+// pass 2 / pass 4: one CTA per item reduces its range of the per-sample arrays
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
+  __shared__ float red[3][8];
+  __shared__ float redg[NP][8];
+  const int item = blockIdx.x;
+  const Item it = A.items[item];
+  const long long base = it.kind == 1 ? A.n_samples + it.begin : it.begin;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float* out = A.partials + ((size_t)A.k * A.n_items + item) * PSTRIDE;
+  if (!GRAD) {
+    float m = -INFINITY;
+    for (int i = tid; i < it.count; i += 256) m = fmaxf(m, A.lw[base + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[0][w] = m;
+    __syncthreads();
+    m = red[0][0];
+    for (int q = 1; q < 8; ++q) m = fmaxf(m, red[0][q]);
+    float s1 = 0.f, s2 = 0.f;
+    if (m > -INFINITY)
+      for (int i = tid; i < it.count; i += 256) {
+        const float t = expf(A.lw[base + i] - m);
+        s1 += t;
+        s2 += t * t;
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    __syncthreads();
+    if (lane == 0) { red[1][w] = s1; red[2][w] = s2; }
+    __syncthreads();
+    if (tid == 0) {
+      float a = 0.f, b = 0.f;
+      for (int q = 0; q < 8; ++q) { a += red[1][q]; b += red[2][q]; }
+      out[0] = m;
+      out[1] = a;
+      out[2] = b;
+    }
+  } else {
+    float gs[NP];
+    for (int q = 0; q < NP; ++q) gs[q] = 0.f;
+    for (int i = tid; i < it.count; i += 256)
+      for (int q = 0; q < NP; ++q) gs[q] += A.tg[(size_t)q * A.n_total + base + i];
+    for (int q = 0; q < NP; ++q) {
+      for (int o = 16; o > 0; o >>= 1) gs[q] += __shfl_xor_sync(0xffffffffu, gs[q], o);
+      if (lane == 0) redg[q][w] = gs[q];
+    }
+    __syncthreads();
+    if (tid < NP) {
+      float a = 0.f;
+      for (int q = 0; q < 8; ++q) a += redg[tid][q];
+      out[3 + tid] = a;
+    }
+  }
+}
+
+// -------------------------------------------------------------------- merge
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
+  __shared__ double rs[8][2 + NP];
+  __shared__ double rsel[8][3 + NP];
+  __shared__ int rfail[8];
+  const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const LamD D = A.ld[k];
+  const int ne = A.n_events;
+  if (D.flag & 1) {
+    for (int e = tid; e < ne; e += 256) {
+      A.lnL_event[(size_t)k * ne + e] = -INFINITY;
+      A.neff_event[(size_t)k * ne + e] = 0.0;
+    }
+    if (tid == 0) {
+      A.ln_xi[k] = -INFINITY;
+      A.neff_sel[k] = 0.0;
+      A.lnL_total[k] = -INFINITY;
+      A.flags[k] = 1;
+      if (GRAD)
+        for (int i = 0; i < NP; ++i) A.grad_total[(size_t)k * NP + i] = 0.0;
+    }
+    return;
+  }
+  const int P = A.P;
+  const float* pk = A.partials + (size_t)k * A.n_items * P * PSTRIDE;
+
+  // ---- events: thread-strided, each event merged in item order
+  double sumL = 0.0, cmp = 0.0, sg[NP];
+  for (int i = 0; i < NP; ++i) sg[i] = 0.0;
+  int fail = 0;   // bit 0: an event below the N_eff threshold; bit 1: an event with no weight
+  for (int e = tid; e < ne; e += 256) {
+    const int s0 = A.ev_item0[e] * P, s1 = A.ev_item0[e + 1] * P;
+    double M = -INFINITY;
+    for (int s = s0; s < s1; ++s) M = fmax(M, (double)pk[(size_t)s * PSTRIDE]);
+    double S1 = 0.0, S2 = 0.0, G[GRAD ? NP : 1];
+    if (GRAD)
+      for (int i = 0; i < NP; ++i) G[i] = 0.0;
+    if (M > -INFINITY) {
+      for (int s = s0; s < s1; ++s) {
+        const float* p = pk + (size_t)s * PSTRIDE;
+        if (!(p[0] > -INFINITY)) continue;
+        const double r = exp((double)p[0] - M);
+        S1 += (double)p[1] * r;
+        S2 += (double)p[2] * r * r;
+        if (GRAD)
+          for (int i = 0; i < NP; ++i) G[i] += (double)p[3 + i] * r;
+      }
+    }
+    double lnL = -INFINITY, neff = 0.0;
+    if (S1 > 0.0) {
+      lnL = M + log(S1) - log(A.ev_n[e]) + D.c;
+      neff = S1 * S1 / S2;
+      if (GRAD)
+        for (int i = 0; i < NP; ++i) sg[i] += G[i] / S1 + D.dc[i];
+    }
+    A.lnL_event[(size_t)k * ne + e] = lnL;
+    A.neff_event[(size_t)k * ne + e] = neff;
+    if (!(neff >= A.neff_min_event)) fail |= 1;
+    if (!(S1 > 0.0)) {
+      fail |= 2;   // a zero-weight event makes the product of Eq. 3 vanish
+      continue;
+    }
+    // Neumaier-compensated sum in this thread's event order
+    const double t = sumL + lnL;
+    if (fabs(sumL) >= fabs(lnL)) cmp += (sumL - t) + lnL; else cmp += (lnL - t) + sumL;
+    sumL = t;
+  }
+
+  // ---- injections: online merge of the injection partials
+  double sM = -INFINITY, sS1 = 0.0, sS2 = 0.0, sG[GRAD ? NP : 1];
+  if (GRAD)
+    for (int i = 0; i < NP; ++i) sG[i] = 0.0;
+  for (int s = A.inj_item0 * P + tid; s < A.n_items * P; s += 256) {
+    const float* p = pk + (size_t)s * PSTRIDE;
+    const double m = p[0];
+    if (!(m > -INFINITY)) continue;
+    if (m > sM) {
+      const double r = exp(sM - m);
+      sS1 *= r;
+      sS2 *= r * r;
+      if (GRAD)
+        for (int i = 0; i < NP; ++i) sG[i] *= r;
+      sM = m;
+    }
+    const double r = exp(m - sM);
+    sS1 += (double)p[1] * r;
+    sS2 += (double)p[2] * r * r;
+    if (GRAD)
+      for (int i = 0; i < NP; ++i) sG[i] += (double)p[3 + i] * r;
+  }
+
+  // ---- fixed-order reductions: butterfly within warps, then warps in order
+  sumL += cmp;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sumL += __shfl_xor_sync(0xffffffffu, sumL, o);
+    fail |= __shfl_xor_sync(0xffffffffu, fail, o);
+    if (GRAD)
+      for (int i = 0; i < NP; ++i) sg[i] += __shfl_xor_sync(0xffffffffu, sg[i], o);
+    const double oM = __shfl_xor_sync(0xffffffffu, sM, o);
+    const double o1 = __shfl_xor_sync(0xffffffffu, sS1, o);
+    const double o2 = __shfl_xor_sync(0xffffffffu, sS2, o);
+    double oG[GRAD ? NP : 1];
+    if (GRAD)
+      for (int i = 0; i < NP; ++i) oG[i] = __shfl_xor_sync(0xffffffffu, sG[i], o);
+    const double M = fmax(sM, oM);
+    if (M > -INFINITY) {
+      const double ra = exp(sM - M), rb = exp(oM - M);
+      sS1 = sS1 * ra + o1 * rb;
+      sS2 = sS2 * ra * ra + o2 * rb * rb;
+      if (GRAD)
+        for (int i = 0; i < NP; ++i) sG[i] = sG[i] * ra + oG[i] * rb;
+      sM = M;
+    }
+  }
+  if (lane == 0) {
+    rs[w][0] = sumL;
+    if (GRAD)
+      for (int i = 0; i < NP; ++i) rs[w][2 + i] = sg[i];
+    rfail[w] = fail;
+    rsel[w][0] = sM;
+    rsel[w][1] = sS1;
+    rsel[w][2] = sS2;
+    if (GRAD)
+      for (int i = 0; i < NP; ++i) rsel[w][3 + i] = sG[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0, gt[NP], M = -INFINITY, S1 = 0.0, S2 = 0.0, G[NP];
+    int fl = 0;
+    for (int i = 0; i < NP; ++i) { gt[i] = 0.0; G[i] = 0.0; }
+    for (int q = 0; q < 8; ++q) {
+      tot += rs[q][0];
+      fl |= rfail[q];
+      if (GRAD)
+        for (int i = 0; i < NP; ++i) gt[i] += rs[q][2 + i];
+      M = fmax(M, rsel[q][0]);
+    }
+    if (M > -INFINITY)
+      for (int q = 0; q < 8; ++q) {
+        if (!(rsel[q][0] > -INFINITY)) continue;
+        const double r = exp(rsel[q][0] - M);
+        S1 += rsel[q][1] * r;
+        S2 += rsel[q][2] * r * r;
+        if (GRAD)
+          for (int i = 0; i < NP; ++i) G[i] += rsel[q][3 + i] * r;
+      }
+    int flag = (fl & 1) ? 2 : 0;
+    const bool dead = (fl & 2) != 0;
+    double lnxi = -INFINITY, neffs = 0.0;
+    if (S1 > 0.0) {
+      lnxi = M + log(S1) - log(A.n_draw) + D.c;
+      neffs = S1 * S1 / S2;
+    } else {
+      flag |= 8;
+    }
+    if (A.neff_min_sel > 0.0 && !(neffs >= A.neff_min_sel)) flag |= 4;
+    A.ln_xi[k] = lnxi;
+    A.neff_sel[k] = neffs;
+    A.flags[k] = flag;
+    A.lnL_total[k] = (flag || dead) ? -INFINITY : tot - (double)ne * lnxi;
+    if (GRAD)
+      for (int i = 0; i < NP; ++i)
+        A.grad_total[(size_t)k * NP + i] =
+            (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + D.dc[i]);
+  }
+}
+
+// ------------------------------------------------------------ cell index (tests)
+__global__ void k_los_cell(const float* z, long long n, int nz, double zmax, int* cell) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double zv = (double)z[i];
+  int j = -1;
+  if (zv >= 0.0 && zv <= zmax) {
+    const double s = (double)(nz - 1) / zmax;
+    j = (int)floor(zv * s);
+    j = min(max(j, 0), nz - 2);
+  }
+  cell[i] = j;
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 2 * (size_t)a.nx;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_prologue<<<K, PRO_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool G, bool KH, typename RT>
+static cudaError_t launch_fused_t(const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_fused<G, KH, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fused_smem_max());
+  if (e != cudaSuccess) return e;
+  k_fused<G, KH, RT><<<grid, THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+size_t fused_smem_bytes(int chunk) { return (size_t)chunk * 7 * sizeof(float); }
+size_t fused_smem_max() { return fused_smem_bytes(4096); }
+
+cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s) {
+  const size_t smem = fused_smem_bytes(a.chunk);
+  if (grad) {
+    if (kahan) return bf16 ? launch_fused_t<true, true, __nv_bfloat16>(a, grid, smem, s)
+                           : launch_fused_t<true, true, float>(a, grid, smem, s);
+    return bf16 ? launch_fused_t<true, false, __nv_bfloat16>(a, grid, smem, s)
+                : launch_fused_t<true, false, float>(a, grid, smem, s);
+  }
+  if (kahan) return bf16 ? launch_fused_t<false, true, __nv_bfloat16>(a, grid, smem, s)
+                         : launch_fused_t<false, true, float>(a, grid, smem, s);
+  return bf16 ? launch_fused_t<false, false, __nv_bfloat16>(a, grid, smem, s)
+              : launch_fused_t<false, false, float>(a, grid, smem, s);
+}
+
+cudaError_t launch_plain_sample(const PlainArgs& a, bool grad, bool bf16, cudaStream_t s) {
+  const int grid = (int)((a.n_total + 255) / 256);
+  if (grad) {
+    if (bf16) k_plain_sample<true, __nv_bfloat16><<<grid, 256, 0, s>>>(a);
+    else k_plain_sample<true, float><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (bf16) k_plain_sample<false, __nv_bfloat16><<<grid, 256, 0, s>>>(a);
+    else k_plain_sample<false, float><<<grid, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_reduce(const PlainArgs& a, bool grad, cudaStream_t s) {
+  if (grad) k_plain_reduce<true><<<a.n_items, 256, 0, s>>>(a);
+  else k_plain_reduce<false><<<a.n_items, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const MergeArgs& a, int K, bool grad, cudaStream_t s) {
+  if (grad) k_merge<true><<<K, 256, 0, s>>>(a);
+  else k_merge<false><<<K, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_los_cell(const float* z, long long n, int nz, double zmax, int* cell, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_los_cell<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(z, n, nz, zmax, cell);
+  return cudaGetLastError();
+}
+
+}  // namespace gwc

@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every function
+declared in include/gwc.h, the binding's struct layouts match the header, and calls
+made without a device fail with a status instead of crashing."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2605_23538_gb300 import build
+    build.build()
+    import paper_2605_23538_gb300 as g
+    g.lib()
+    return g
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gwc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gwc_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_function(g):
+    declared = header_functions()
+    assert len(declared) >= 10
+    import ctypes
+    lib = ctypes.CDLL(g.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(g.EXPORTS) == declared
+
+
+def test_struct_sizes_match_header(g):
+    import ctypes
+    # sizes from the header's field lists (x86-64 / aarch64 LP64 ABI)
+    assert ctypes.sizeof(g.Events) == 56
+    assert ctypes.sizeof(g.Los) == 32
+    assert ctypes.sizeof(g.Injections) == 48
+    assert ctypes.sizeof(g.Options) == 40
+    assert ctypes.sizeof(g.Info) == 56
+
+
+def test_defaults(g):
+    o = g.default_options()
+    assert (o.neff_min_event, o.neff_min_sel, o.accum, o.los_dtype) == (2.0, 0.0, 0, 0)
+    assert (o.n_x_table, o.max_K, o.chunk, o.lambda_tile) == (512, 256, 1024, 0)
+
+
+def test_invalid_inputs_rejected_before_any_device_work(g, synth):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the host-side path on a machine without a GPU")
+    w = synth.scaled("t", 3, ("fixed", 50), 2, 16, 100, "draws")
+    cat = synth.catalogue(w)
+    bad = dict(cat)
+    bad["pix"] = cat["pix"].copy()
+    bad["pix"][0] = 10_000
+    with pytest.raises(g.GwcError) as e:
+        g.create(bad)
+    assert e.value.status == -1 and "pixel" in str(e.value)
+    bad = dict(cat)
+    bad["offsets"] = cat["offsets"].copy()
+    bad["offsets"][1] = 0
+    with pytest.raises(g.GwcError) as e:
+        g.create(bad)
+    assert e.value.status == -1
+    bad = dict(cat)
+    bad["dl"] = cat["dl"].copy()
+    bad["dl"][3] = np.nan
+    with pytest.raises(g.GwcError) as e:
+        g.create(bad)
+    assert e.value.status == -1
+    with pytest.raises(g.GwcError) as e:
+        g.create(cat, g.default_options(chunk=8))
+    assert e.value.status == -1
+    # valid inputs reach the device query, which fails without a GPU
+    with pytest.raises(g.GwcError) as e:
+        g.create(cat)
+    assert e.value.status == -5
+
+
+def test_null_context_calls_fail_cleanly(g):
+    import ctypes
+    lib = g.lib()
+    assert lib.gwc_loglik(None, 1, None, None, None, None, None, None, None, None) == -1
+    assert "context" in g.last_error()
+    lib.gwc_destroy(None)
+    info = g.Info()
+    assert lib.gwc_get_info(None, ctypes.byref(info)) == -1

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA library against the FP64 oracle, through the C ABI.
+
+Tolerances (from the target accuracy of the method's FP32 path):
+  * per-event ln L_i: |d| <= 1e-5 absolute; total ln L: |d| <= 1e-3 absolute;
+  * ln xi: |d| <= 1e-5 absolute (it is multiplied by N_det in the total);
+  * N_eff (event and selection): relative 1e-4;
+  * gradient: |d g| <= 1e-4 * max(|g|, 1e-2 * scale), where scale is the size of the
+    per-sample derivatives whose weighted difference the gradient is (returned by the
+    oracle): near the likelihood peak the total gradient is a small difference of large
+    terms that no FP32 evaluation resolves to 1e-4 of itself;
+  * flags and the finite/-inf pattern: exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL_EVENT, TOL_TOTAL, TOL_XI, TOL_NEFF, TOL_GRAD = 1e-5, 1e-3, 1e-5, 1e-4, 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def g(torch):
+    from paper_2605_23538_gb300 import build
+    build.build()
+    import paper_2605_23538_gb300 as g
+    return g
+
+
+def dev(torch, a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def compare(got, ref, grad=False, label=""):
+    ge = got["lnL_event"].cpu().numpy()
+    re_ = ref["lnL_event"]
+    assert np.array_equal(np.isfinite(ge), np.isfinite(re_)), f"{label}: finite pattern"
+    fin = np.isfinite(re_)
+    d_ev = np.max(np.abs(ge[fin] - re_[fin]), initial=0.0)
+    assert d_ev <= TOL_EVENT, f"{label}: per-event |d| = {d_ev}"
+    np.testing.assert_array_equal(got["flags"].cpu().numpy(), ref["flags"], err_msg=label)
+    gx = got["ln_xi"].cpu().numpy()
+    fx = np.isfinite(ref["ln_xi"])
+    assert np.array_equal(np.isfinite(gx), fx)
+    d_xi = np.max(np.abs(gx[fx] - ref["ln_xi"][fx]), initial=0.0)
+    assert d_xi <= TOL_XI, f"{label}: ln xi |d| = {d_xi}"
+    gt = got["lnL_total"].cpu().numpy()
+    ft = np.isfinite(ref["lnL_total"])
+    assert np.array_equal(np.isfinite(gt), ft)
+    d_tot = np.max(np.abs(gt[ft] - ref["lnL_total"][ft]), initial=0.0)
+    assert d_tot <= TOL_TOTAL, f"{label}: total |d| = {d_tot}"
+    ne = got["neff_event"].cpu().numpy()
+    ok = ref["neff_event"] > 0
+    np.testing.assert_allclose(ne[ok], ref["neff_event"][ok], rtol=TOL_NEFF)
+    np.testing.assert_allclose(got["neff_sel"].cpu().numpy(), ref["neff_sel"], rtol=TOL_NEFF)
+    out = dict(d_event=d_ev, d_xi=d_xi, d_total=d_tot)
+    if grad:
+        gg = got["grad_total"].cpu().numpy()
+        gr, sc = ref["grad_total"], ref["grad_scale"]
+        rel = np.abs(gg - gr) / np.maximum(np.abs(gr), 1e-2 * sc + 1e-300)
+        rel[~ft] = 0.0
+        assert np.all(rel <= TOL_GRAD), f"{label}: grad rel err {rel.max()} at {np.unravel_index(rel.argmax(), rel.shape)}"
+        out["grad_rel"] = float(rel.max())
+    print(label, out)
+    return out
+
+
+@pytest.fixture(scope="module")
+def cat_c1(synth):
+    return synth.catalogue("c1")
+
+
+@pytest.fixture(scope="module")
+def lam_c1(synth):
+    return np.vstack([synth.FIDUCIAL, synth.lambda_batch(7, purpose=11)])
+
+
+def test_c1_value_and_gradient(torch, g, orc, cat_c1, lam_c1):
+    ref = orc.loglik(cat_c1, lam_c1, grad=True)
+    with g.Context(cat_c1, max_K=8) as ctx:
+        got = ctx.loglik_grad(dev(torch, lam_c1))
+        torch.cuda.synchronize()
+        compare(got, ref, grad=True, label="c1 grad")
+        val = ctx.loglik(dev(torch, lam_c1))
+        compare(val, ref, label="c1 value")
+        # the value and value+gradient passes agree to the last bit on the value
+        assert torch.equal(val["lnL_total"], got["lnL_total"]) or \
+            np.allclose(val["lnL_total"].cpu().numpy(), got["lnL_total"].cpu().numpy(), atol=1e-9)
+
+
+def test_c1_each_lambda_alone(torch, g, orc, cat_c1, lam_c1):
+    # K = 1 uses the sample-split geometry (8 warps on one Lambda)
+    ref = orc.loglik(cat_c1, lam_c1[:3], grad=True)
+    with g.Context(cat_c1, max_K=8) as ctx:
+        for k in range(3):
+            got = ctx.loglik_grad(dev(torch, lam_c1[k:k + 1]))
+            r = {key: v[k:k + 1] for key, v in ref.items()}
+            compare(got, r, grad=True, label=f"c1 K=1 #{k}")
+
+
+@pytest.fixture(scope="module")
+def cat_ragged(synth):
+    # several chunks per event and ragged tails: 24 events of 300..5000 samples
+    w = synth.scaled("ragged", 24, ("uniform", 300, 5000), 8, 512, 30_000, "found")
+    return synth.catalogue(w)
+
+
+def test_batch_of_64_ragged(torch, g, orc, synth, cat_ragged):
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(63, purpose=12)])
+    ref = orc.loglik(cat_ragged, lam)
+    with g.Context(cat_ragged, max_K=64, chunk=1024) as ctx:
+        got = ctx.loglik(dev(torch, lam))
+        compare(got, ref, label="ragged K=64")
+
+
+def test_batch_gradient_ragged(torch, g, orc, synth, cat_ragged):
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(9, purpose=13)])
+    ref = orc.loglik(cat_ragged, lam, grad=True)
+    with g.Context(cat_ragged, max_K=16, chunk=512, lambda_tile=8) as ctx:
+        got = ctx.loglik_grad(dev(torch, lam))
+        compare(got, ref, grad=True, label="ragged grad K=10")
+
+
+@pytest.mark.parametrize("chunk,tile", [(64, 1), (256, 3), (4096, 40)])
+def test_tiling_does_not_change_results(torch, g, synth, cat_ragged, chunk, tile):
+    lam = dev(torch, np.vstack([synth.FIDUCIAL, synth.lambda_batch(11, purpose=14)]))
+    with g.Context(cat_ragged, max_K=16) as a, g.Context(cat_ragged, max_K=16, chunk=chunk,
+                                                         lambda_tile=tile) as b:
+        ra, rb = a.loglik_grad(lam), b.loglik_grad(lam)
+        ea, eb = ra["lnL_event"].cpu().numpy(), rb["lnL_event"].cpu().numpy()
+        fin = np.isfinite(ea)
+        assert np.array_equal(fin, np.isfinite(eb))
+        assert np.max(np.abs(ea[fin] - eb[fin])) < 2e-6
+        assert np.allclose(ra["grad_total"].cpu().numpy(), rb["grad_total"].cpu().numpy(), rtol=1e-4, atol=1e-3)
+
+
+def test_deterministic(torch, g, synth, cat_ragged):
+    lam = dev(torch, synth.lambda_batch(16, purpose=15))
+    with g.Context(cat_ragged, max_K=16) as ctx:
+        a = ctx.loglik_grad(lam)
+        b = ctx.loglik_grad(lam)
+        for k in a:
+            assert torch.equal(a[k], b[k]) or torch.equal(torch.nan_to_num(a[k]), torch.nan_to_num(b[k])), k
+
+
+def test_plain_path_matches(torch, g, orc, synth, cat_c1, lam_c1):
+    ref = orc.loglik(cat_c1, lam_c1[:4], grad=True)
+    with g.Context(cat_c1, max_K=8) as ctx:
+        got = ctx.loglik_plain(dev(torch, lam_c1[:4]), grad=True)
+        compare(got, ref, grad=True, label="plain")
+        val = ctx.loglik_plain(dev(torch, lam_c1[:4]), grad=False)
+        compare(val, ref, label="plain value")
+
+
+def test_host_entry_point(torch, g, synth, cat_c1, lam_c1):
+    with g.Context(cat_c1, max_K=8) as ctx:
+        d = ctx.loglik_grad(dev(torch, lam_c1))
+        tot, flags, grad = ctx.loglik_grad_host(lam_c1)
+        np.testing.assert_array_equal(tot, d["lnL_total"].cpu().numpy())
+        np.testing.assert_array_equal(flags, d["flags"].cpu().numpy())
+        np.testing.assert_array_equal(grad, d["grad_total"].cpu().numpy())
+
+
+def test_autograd_function(torch, g, cat_c1, lam_c1):
+    with g.Context(cat_c1, max_K=8) as ctx:
+        lam = dev(torch, lam_c1[:3]).requires_grad_(True)
+        tot = g.GwcLogLik.apply(lam, ctx)
+        w = torch.tensor([0.5, -1.0, 2.0], dtype=torch.float64, device="cuda")
+        (tot * w).sum().backward()
+        ref = ctx.loglik_grad(lam.detach())["grad_total"] * w[:, None]
+        assert torch.allclose(lam.grad, ref)
+
+
+def test_los_cell_index_bit_exact(torch, g, orc):
+    rng = np.random.default_rng(3)
+    for nz, zmax in ((512, 2.0), (2048, 2.0), (1000, 1.7), (2, 0.3)):
+        z = rng.uniform(-0.1, zmax * 1.05, 4000).astype(np.float32)
+        # values on and next to every 37th grid node, in float32
+        nodes = (np.arange(0, nz, 37) * (zmax / (nz - 1))).astype(np.float32)
+        z = np.concatenate([z, nodes, np.nextafter(nodes, np.float32(-1)), np.nextafter(nodes, np.float32(9)),
+                            np.float32([0.0, zmax, -0.0])])
+        got = g.los_cell_index(torch.tensor(z, device="cuda"), nz, zmax).cpu().numpy()
+        ref = np.array([orc.los_cell(v, nz, zmax) for v in z], dtype=np.int32)
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_pixel_ids_used_verbatim(torch, g, orc, synth, cat_c1):
+    # shifting every sample to another block of pixels changes results exactly as the
+    # oracle says (a pixel mix-up would not)
+    cat = dict(cat_c1)
+    cat["pix"] = ((cat_c1["pix"].astype(np.int64) + 101) % cat_c1["los"].shape[0]).astype(np.int32)
+    lam = np.vstack([synth.FIDUCIAL])
+    ref = orc.loglik(cat, lam, neff_min_event=0.0)
+    with g.Context(cat, max_K=1, neff_min_event=0.0) as ctx:
+        compare(ctx.loglik(dev(torch, lam)), ref, label="shifted pixels")
+
+
+def test_edge_lambdas(torch, g, orc, synth, cat_c1):
+    base = synth.FIDUCIAL
+    pts = []
+    for idx, v in ((9, 0.0), (9, 1.0), (6, 0.0), (2, 1.0), (3, -1.0), (3, -1.0005), (1, 0.0), (1, 1.0)):
+        p = base.copy()
+        p[idx] = v
+        pts.append(p)
+    bad = base.copy()
+    bad[5] = 4.0          # m_max < m_min: outside the domain
+    pts.append(bad)
+    nan = base.copy()
+    nan[0] = np.nan
+    pts.append(nan)
+    lam = np.vstack(pts)
+    ref = orc.loglik(cat_c1, lam, grad=True, neff_min_event=0.0)
+    with g.Context(cat_c1, max_K=16, neff_min_event=0.0) as ctx:
+        got = ctx.loglik_grad(dev(torch, lam))
+        compare(got, ref, grad=True, label="edges")
+        fl = got["flags"].cpu().numpy()
+        assert fl[-1] == 1 and fl[-2] == 1
+        assert got["lnL_total"][-1].item() == -math.inf
+
+
+def test_event_beyond_the_grid_and_thresholds(torch, g, orc, synth, cat_c1):
+    cat = dict(cat_c1)
+    cat["dl"] = cat_c1["dl"].copy()
+    cat["dl"][: cat_c1["offsets"][1]] = np.float32(1e6)   # event 0 entirely beyond z_max
+    lam = np.vstack([synth.FIDUCIAL])
+    for nmin, smin in ((2.0, 0.0), (0.0, 0.0), (0.0, 1e12)):
+        ref = orc.loglik(cat, lam, neff_min_event=nmin, neff_min_sel=smin)
+        with g.Context(cat, max_K=1, neff_min_event=nmin, neff_min_sel=smin) as ctx:
+            got = ctx.loglik(dev(torch, lam))
+            compare(got, ref, label=f"thresholds {nmin} {smin}")
+            assert got["lnL_total"][0].item() == -math.inf
+
+
+def test_single_event_single_sample_and_tiny_inputs(torch, g, orc, synth):
+    from conftest import tiny_catalogue
+    cat = tiny_catalogue([[0.5, 0.5]], [[(45.0, 30.0, 2500.0, 15.7, 0)]],
+                         [(50.0, 40.0, 3000.0, -18.0)], n_draw=3.0)
+    lam = np.vstack([synth.FIDUCIAL])
+    ref = orc.loglik(cat, lam, neff_min_event=0.0)
+    with g.Context(cat, max_K=1, neff_min_event=0.0) as ctx:
+        compare(ctx.loglik(dev(torch, lam)), ref, label="tiny")
+
+
+def test_no_events(torch, g, synth, cat_c1):
+    cat = synth.subset_events(cat_c1, [])
+    with g.Context(cat, max_K=2) as ctx:
+        out = ctx.loglik(dev(torch, np.vstack([synth.FIDUCIAL] * 2)))
+        assert out["lnL_total"].cpu().numpy().tolist() == [0.0, 0.0]
+
+
+def test_compensated_and_bf16_variants(torch, g, orc, synth, cat_c1, lam_c1):
+    ref = orc.loglik(cat_c1, lam_c1)
+    with g.Context(cat_c1, max_K=8, accum=1) as ctx:
+        compare(ctx.loglik(dev(torch, lam_c1)), ref, label="compensated")
+    with g.Context(cat_c1, max_K=8, los_dtype=1) as ctx:
+        got = ctx.loglik(dev(torch, lam_c1))
+        d = np.nanmax(np.abs(got["lnL_event"].cpu().numpy() - ref["lnL_event"]))
+        assert d < 1e-2   # bfloat16 rows carry 8 significand bits: an error study, not parity
+        print("bf16 LOS: max per-event |d| =", d)
+
+
+def test_invalid_calls(torch, g, synth, cat_c1):
+    with g.Context(cat_c1, max_K=2) as ctx:
+        with pytest.raises(g.GwcError):
+            ctx.loglik(dev(torch, np.vstack([synth.FIDUCIAL] * 3)))   # K > max_K
+        with pytest.raises(TypeError):
+            ctx.loglik(torch.zeros((1, 13), dtype=torch.float32, device="cuda"))
