@@ -34,6 +34,7 @@
 // unit normalisations and brute force (tests/test_oracle_*.py); none is "unpinned".
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -178,8 +179,14 @@ void gk15(const F& f, const T& a, const T& b, T& K, T& G, double* kabs) {
   for (int i = 0; i < nc; ++i) kabs[i] *= hv;
 }
 
+// Convergence of one component: |K - G| within the relative tolerance, within its share
+// of the absolute tolerance, or at the noise level of the local integral of |f| below
+// which splitting cannot improve the estimate (50 ulp for values; 1e-13 for derivative
+// components, whose integrands carry chain-rule rounding).  Every call also has a
+// budget of splits, so the recursion always ends.
 template <class T, class F>
-T adapt_rec(const F& f, const T& a, const T& b, double rtol, const double* atol_density, int depth) {
+T adapt_rec(const F& f, const T& a, const T& b, double rtol, const double* atol_density, int depth,
+            int& budget) {
   T K, G;
   double kabs[NC_MAX];
   gk15(f, a, b, K, G, kabs);
@@ -187,12 +194,15 @@ T adapt_rec(const F& f, const T& a, const T& b, double rtol, const double* atol_
   bool ok = true;
   for (int i = 0; i < ncomp(K) && ok; ++i) {
     const double err = std::fabs(comp(K, i) - comp(G, i));
-    ok = err <= rtol * std::fabs(comp(K, i)) + atol_density[i] * w;
+    const double floor_ = (i == 0 ? 50.0 * DBL_EPSILON : 1e-13) * kabs[i];
+    const double rt = i == 0 ? rtol : std::max(rtol, 1e-11);
+    ok = err <= rt * std::fabs(comp(K, i)) + atol_density[i] * w + floor_;
   }
-  if (ok || depth >= 40) return K;
+  if (ok || depth >= 30 || budget <= 0) return K;
+  --budget;
   const T m = (a + b) * 0.5;
-  return adapt_rec(f, a, m, rtol, atol_density, depth + 1) +
-         adapt_rec(f, m, b, rtol, atol_density, depth + 1);
+  return adapt_rec(f, a, m, rtol, atol_density, depth + 1, budget) +
+         adapt_rec(f, m, b, rtol, atol_density, depth + 1, budget);
 }
 
 // int_a^b f, to relative tolerance rtol of the integral of |f| (per component).
@@ -203,15 +213,17 @@ T integrate(const F& f, const T& a, const T& b, double rtol) {
   double kabs[NC_MAX], atol_density[NC_MAX];
   gk15(f, a, b, K, G, kabs);
   const double w = val(b) - val(a);
-  for (int i = 0; i < ncomp(K); ++i) atol_density[i] = 1e-3 * rtol * kabs[i] / w;
-  return adapt_rec(f, a, b, rtol, atol_density, 0);
+  for (int i = 0; i < ncomp(K); ++i) atol_density[i] = 1e-2 * rtol * kabs[i] / w;
+  int budget = 20000;
+  return adapt_rec(f, a, b, rtol, atol_density, 0, budget);
 }
 
 // ------------------------------------------------------------------ cosmology
-// E(z) = H(z)/H0 for flat LCDM (Eq. 1 with OL = 1 - Om)
+// E(z) = H(z)/H0 for flat LCDM (Eq. 1 with OL = 1 - Om), written as
+// E^2 = 1 + Om ((1+z)^3 - 1) = 1 + Om z (3 + 3z + z^2), which avoids the cancellation
+// in (1+z)^3 - 1 at small z (it matters for d/dOm)
 template <class T> T E_of(const T& z, const T& om) {
-  const T u = 1.0 + z;
-  return fsqrt(om * u * u * u + (1.0 - om));
+  return fsqrt(1.0 + om * (z * (3.0 + z * (3.0 + z))));
 }
 // I(z) = int_0^z dz'/E(z'); D(z) = (1+z) I(z) = d_L H0 / c
 template <class T> T I_of(const T& z, const T& om) {

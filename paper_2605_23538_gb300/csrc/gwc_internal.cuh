@@ -189,8 +189,8 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float er = expf(-fabsf(r));
 
   // d d_L / dz = (c/H0) D'(z), D' = I(z) + u/E with I(z) = x/u on the root
-  const float u3 = u * u * u;
-  const float E2 = fmaf(L.om, u3 - 1.f, 1.f);
+  const float u3m1 = z * fmaf(z, z + 3.f, 3.f);   // (1+z)^3 - 1 without cancellation
+  const float E2 = fmaf(L.om, u3m1, 1.f);
   const float rE = rsqrtf(E2);
   const float Dp = fmaf(x, ru, u * rE);
 
@@ -251,14 +251,14 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     Gz += fmaf(pa, L.alpha, pb * zz * m1s * L.inv_sig) * ru;
     Gz -= m2s * dS2_dm * ru;
     Gz += Gc * ru;
-    const float D2 = 2.f * rE - 1.5f * L.om * u3 * rE3;
+    const float D2 = 2.f * rE - 1.5f * L.om * (u3m1 + 1.f) * rE3;
     Gz -= D2 * invDp;
 
     // z depends on H0 and Om through x and the inverted distance relation
     const float J = hermite_val(__ldg(jtab + n), __ldg(jtab + n + 1), t);
     g[P_H0] = Gz * x * L.invH0 * invDp;
     const float dz_dom = -u * J * invDp;
-    const float dDp_dom = J - 0.5f * u * (u3 - 1.f) * rE3;
+    const float dDp_dom = J - 0.5f * u * u3m1 * rE3;
     g[P_OM] = fmaf(Gz, dz_dom, -dDp_dom * invDp);
     g[P_ALPHA] = pa * (-lm1s - L.dZPa);
     g[P_BETA] = lm2s - dlnC_db;

@@ -151,10 +151,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const double za = tid * hz;
     for (int q = 0; q < NGL; ++q) {
       const double zq = za + 0.5 * hz * (1.0 + c_glx[q]);
-      const double u = 1.0 + zq, u3 = u * u * u;
-      const double E2 = om * (u3 - 1.0) + 1.0, E = sqrt(E2);
+      const double u3m1 = zq * (3.0 + zq * (3.0 + zq));   // (1+z)^3 - 1
+      const double E2 = om * u3m1 + 1.0, E = sqrt(E2);
       v[0] += c_glw[q] / E;
-      v[1] += c_glw[q] * (-0.5 * (u3 - 1.0) / (E2 * E));
+      v[1] += c_glw[q] * (-0.5 * u3m1 / (E2 * E));
     }
     v[0] *= 0.5 * hz;
     v[1] *= 0.5 * hz;
@@ -191,12 +191,11 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
         double acc = 0.0;
         for (int q = 0; q < NGL; ++q) {
           const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
-          const double u = 1.0 + zq;
-          acc += c_glw[q] / sqrt(om * (u * u * u - 1.0) + 1.0);
+          acc += c_glw[q] / sqrt(om * (zq * (3.0 + zq * (3.0 + zq))) + 1.0);
         }
         Iz = sI[p] + 0.5 * h * acc;
         const double u = 1.0 + z;
-        E = sqrt(om * (u * u * u - 1.0) + 1.0);
+        E = sqrt(om * (z * (3.0 + z * (3.0 + z))) + 1.0);
         Dp = Iz + u / E;
         if (it == 4) break;
         z -= (u * Iz - xn) / Dp;
@@ -206,12 +205,12 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       double accj = 0.0;
       for (int q = 0; q < NGL; ++q) {
         const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
-        const double u = 1.0 + zq, u3 = u * u * u, E2 = om * (u3 - 1.0) + 1.0;
-        accj += c_glw[q] * (-0.5 * (u3 - 1.0) / (E2 * sqrt(E2)));
+        const double u3m1 = zq * (3.0 + zq * (3.0 + zq)), E2 = om * u3m1 + 1.0;
+        accj += c_glw[q] * (-0.5 * u3m1 / (E2 * sqrt(E2)));
       }
       Jz = sJ[p] + 0.5 * h * accj;
-      const double u = 1.0 + z, u3 = u * u * u, E2 = om * (u3 - 1.0) + 1.0;
-      jd = -0.5 * (u3 - 1.0) / (E2 * sqrt(E2));
+      const double u3m1 = z * (3.0 + z * (3.0 + z)), E2 = om * u3m1 + 1.0;
+      jd = -0.5 * u3m1 / (E2 * sqrt(E2));
     }
     sdyn[2 * n] = z * pscale;                // P_n
     sdyn[2 * n + 1] = pscale / Dp * dx;      // dP/dx * dx
