@@ -185,6 +185,16 @@ typedef struct {
 
 gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
 
+/* Per-sample terms for one Lambda point (diagnostics and element-wise tests).  For every
+ * event sample, in the context's order (events in input order; within an event, samples
+ * stably sorted by pixel id), followed by every injection in input order:
+ *   d_lnw[n_samples + n_found]          ln w minus the per-Lambda constant c (-inf where w = 0)
+ *   d_dlnw[13][n_samples + n_found]     (optional, may be NULL) d(ln w - c)/d Lambda
+ *   d_c[14]                             c and dc/d Lambda, so ln w = d_lnw + c
+ * d_lambda points to 13 doubles on the device.  Uses the context's per-call scratch. */
+gwc_status gwc_sample_terms(gwc_ctx* ctx, const double* d_lambda, float* d_lnw, float* d_dlnw,
+                            double* d_c, void* stream);
+
 /* Per-kernel timing.  While enabled, every call records CUDA events on its stream around
  * its three stages (the prologue kernel, the sample kernel or the plain path's sample
  * passes, and the merge kernel).  gwc_profile_read waits for the recorded events,

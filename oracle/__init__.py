@@ -61,7 +61,7 @@ def lib():
             L = _lib
             L.orc_loglik.restype = ctypes.c_int
             L.orc_loglik.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, d, d, i32,
-                                     vp, vp, vp, vp, vp, vp, vp, vp]
+                                     vp, vp, vp, vp, vp, vp, vp, vp, vp]
             for name, args in [("orc_E", [d, d]), ("orc_I", [d, d]), ("orc_D", [d, d]),
                                ("orc_Dprime", [d, d]), ("orc_z_of_x", [d, d, d]),
                                ("orc_S", [d, d, d]), ("orc_ln_p_m1", [d, vp]),
@@ -73,6 +73,8 @@ def lib():
                 fn.argtypes = args
             L.orc_los_cell.restype = i32
             L.orc_los_cell.argtypes = [ctypes.c_float, i32, d]
+            L.orc_ln_w_samples.restype = ctypes.c_int
+            L.orc_ln_w_samples.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp]
             L.orc_ln_w_row.restype = ctypes.c_int
             L.orc_ln_w_row.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, d, vp, vp]
         return _lib
@@ -128,6 +130,29 @@ def ln_w_row(lam, m1, m2, dl, lnpi, row, zmax, grad=False):
     return (out, g) if grad else out
 
 
+def ln_w_samples(lam, cat, which="events", idx=None, grad=False):
+    """Per-sample ln w exactly as the likelihood uses it: event samples against their
+    pixel's LOS row, injections against the pixel mean, N_z from the pixel mean."""
+    a = _lam(lam)
+    f32 = lambda x: np.ascontiguousarray(x, dtype=np.float32)
+    keys = ("m1", "m2", "dl", "lnpe") if which == "events" else ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd")
+    sel = slice(None) if idx is None else idx
+    m1, m2, dl, lp = (f32(cat[k][sel]) for k in keys)
+    pix = np.ascontiguousarray(cat["pix"][sel], dtype=np.int32) if which == "events" else None
+    los = f32(cat["los"])
+    n = len(m1)
+    out = np.empty(n, np.float64)
+    g = np.empty((n, NP), np.float64) if grad else None
+    kink = np.empty((n, NP), np.float64) if grad else None
+    rc = lib().orc_ln_w_samples(_ptr(a), n, _ptr(m1), _ptr(m2), _ptr(dl), _ptr(lp),
+                                _ptr(pix) if pix is not None else None, _ptr(los), los.shape[0],
+                                los.shape[1], float(cat["z_max"]), _ptr(out), _ptr(g),
+                                _ptr(kink) if grad else None)
+    if rc != 0:
+        raise ValueError("Lambda outside its domain")
+    return (out, g, kink) if grad else out
+
+
 def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads=0):
     """Evaluate the whole likelihood for a Lambda batch ``lam`` [K, 13].
 
@@ -157,13 +182,15 @@ def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads
     out = dict(lnL_event=np.empty((K, n_ev)), neff_event=np.empty((K, n_ev)),
                ln_xi=np.empty(K), neff_sel=np.empty(K), lnL_total=np.empty(K),
                flags=np.empty(K, np.int32), grad_total=np.zeros((K, NP)) if grad else None,
-               grad_scale=np.zeros((K, NP)) if grad else None)
+               grad_scale=np.zeros((K, NP)) if grad else None,
+               grad_kink=np.zeros((K, NP)) if grad else None)
     rc = lib().orc_loglik(ctypes.byref(inp), K, _ptr(lam), int(bool(grad)), neff_min_event,
                           neff_min_sel, n_threads, _ptr(out["lnL_event"]), _ptr(out["neff_event"]),
                           _ptr(out["ln_xi"]), _ptr(out["neff_sel"]), _ptr(out["lnL_total"]),
-                          _ptr(out["flags"]), _ptr(out["grad_total"]), _ptr(out["grad_scale"]))
+                          _ptr(out["flags"]), _ptr(out["grad_total"]), _ptr(out["grad_scale"]),
+                          _ptr(out["grad_kink"]))
     if rc != 0:
         raise ValueError("oracle rejected the inputs")
     if not grad:
-        del out["grad_total"], out["grad_scale"]
+        del out["grad_total"], out["grad_scale"], out["grad_kink"]
     return out

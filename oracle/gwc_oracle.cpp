@@ -423,6 +423,18 @@ template <class T> bool los_interp(const double* row, int nz, double zmax, const
   return val(p) > 0.0;
 }
 
+// Size of the jump of d ln p_LOS / dz at a grid node within `kappa` cells of z (0 if
+// none): the LOS prior is piecewise linear, so at a node the derivative has two valid
+// one-sided values.  Tests use it to accept either side (see grad_kink below).
+double los_kink(const double* row, int nz, double zmax, double zv, double p, double kappa) {
+  const double s = (double)(nz - 1) / zmax;
+  const double pos = zv * s;
+  const int k = (int)std::floor(pos + 0.5);
+  if (std::fabs(pos - k) > kappa || k <= 0 || k >= nz - 1 || !(p > 0.0)) return 0.0;
+  const double left = row[k] - row[k - 1], right = row[k + 1] - row[k];
+  return std::fabs(right - left) * s / p;
+}
+
 // ----------------------------------------------------------------- one sample
 // ln w for one detector-frame sample (m1d, m2d, dL) with PE prior ln pi:
 //   ln w = ln p_LOS(z) + ln psi(z) - ln(1+z) - ln N_z            (redshift prior, Eq. hier_pixels)
@@ -430,9 +442,14 @@ template <class T> bool los_interp(const double* row, int nz, double zmax, const
 //        - 2 ln(1+z) - ln(d d_L/dz)                              (Jacobian to detector frame)
 //        - ln pi_PE                                              (Eq. 6)
 // with z solving D(z) = d_L H0 / c and m_s = m_d / (1+z).  Returns false where w = 0.
+inline void kink_parts(const double&, double, double*) {}
+inline void kink_parts(const Dual& z, double jump, double* kink) {
+  for (int i = 0; i < NP; ++i) kink[i] = jump * std::fabs(z.d[i]);
+}
+
 template <class T>
 bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, double m2d,
-          double dl, double lnpi, T& out) {
+          double dl, double lnpi, T& out, double* kink = nullptr) {
   if (!(dl > 0.0)) return false;
   const T x = dl * P.H0 / C_KMS;
   if (val(x) > P.xmax) return false;
@@ -449,6 +466,7 @@ bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, d
   const T ddl_dz = (C_KMS / P.H0) * Dprime_of(z, P.om);
   const T lu = flog(u);
   out = flog(plos) + ln_psi(z, P) - lu - P.lnNz + lp1 + lp2 - 2.0 * lu - flog(ddl_dz) - lnpi;
+  if (kink) kink_parts(z, los_kink(row, nz, zmax, val(z), val(plos), 2e-5), kink);
   return true;
 }
 
@@ -458,6 +476,7 @@ template <class T> struct Sums {
   double m = NEG_INF, s1 = 0.0, s2 = 0.0;
   double g[NP] = {0};      // sum e^(l - m) dl/dLambda
   double gabs[NP] = {0};   // sum e^(l - m) |dl/dLambda| (a magnitude scale for tests)
+  double gkink[NP] = {0};  // sum e^(l - m) (one-sided derivative ambiguity at LOS nodes)
   long n_pos = 0;
 };
 
@@ -469,14 +488,17 @@ inline void grad_parts(const Dual& l, double* g, double* gabs, double t) {
   }
 }
 
-template <class T> Sums<T> sums_of(const std::vector<T>& ls) {
+template <class T> Sums<T> sums_of(const std::vector<T>& ls, const std::vector<double>& kinks) {
   Sums<T> S;
   for (const T& l : ls) S.m = std::max(S.m, val(l));
-  for (const T& l : ls) {
+  for (size_t q = 0; q < ls.size(); ++q) {
+    const T& l = ls[q];
     const double t = std::exp(val(l) - S.m);
     S.s1 += t;
     S.s2 += t * t;
     grad_parts(l, S.g, S.gabs, t);
+    if (!kinks.empty())
+      for (int i = 0; i < NP; ++i) S.gkink[i] += t * kinks[q * NP + i];
     ++S.n_pos;
   }
   return S;
@@ -494,6 +516,7 @@ template <class T> Sums<T> merge(const std::vector<Sums<T>>& parts) {
     for (int i = 0; i < NP; ++i) {
       S.g[i] += p.g[i] * r;
       S.gabs[i] += p.gabs[i] * r;
+      S.gkink[i] += p.gkink[i] * r;
     }
     S.n_pos += p.n_pos;
   }
@@ -545,13 +568,14 @@ template <class T>
 void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double* L,
                  double neff_min_event, double neff_min_sel, double* lnL_event, double* neff_event,
                  double* ln_xi, double* neff_sel, double* lnL_total, int32_t* flag, double* grad,
-                 double* gscale) {
+                 double* gscale, double* gkink) {
   const int ne = in.n_events;
   const double zmax = in.z_max;
   const int nz = in.n_z;
   *flag = 0;
   if (grad) for (int i = 0; i < NP; ++i) grad[i] = 0.0;
   if (gscale) for (int i = 0; i < NP; ++i) gscale[i] = 0.0;
+  if (gkink) for (int i = 0; i < NP; ++i) gkink[i] = 0.0;
   if (!lambda_in_domain(L)) {
     *flag = 1;
     for (int e = 0; e < ne; ++e) { lnL_event[e] = NEG_INF; neff_event[e] = 0.0; }
@@ -561,21 +585,29 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
   const Pop<T> P = make_pop<T>(L, pbar, zmax);
 
   // ---- numerator: one event at a time
-  std::vector<double> ev_grad((size_t)ne * NP, 0.0), ev_gabs((size_t)ne * NP, 0.0);
+  std::vector<double> ev_grad((size_t)ne * NP, 0.0), ev_gabs((size_t)ne * NP, 0.0),
+      ev_gkink((size_t)ne * NP, 0.0);
+  const bool want_kink = gkink != nullptr;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int e = 0; e < ne; ++e) {
     std::vector<T> ls;
+    std::vector<double> kinks;
     std::vector<double> row((size_t)nz);
     int cur_pix = -1;
+    double kk[NP];
     for (int64_t k = in.offsets[e]; k < in.offsets[e + 1]; ++k) {
       if (in.pix[k] != cur_pix) {
         cur_pix = in.pix[k];
         for (int j = 0; j < nz; ++j) row[(size_t)j] = (double)in.los[(size_t)cur_pix * nz + j];
       }
       T l;
-      if (ln_w(P, row.data(), nz, zmax, in.m1[k], in.m2[k], in.dl[k], in.lnpe[k], l)) ls.push_back(l);
+      if (ln_w(P, row.data(), nz, zmax, in.m1[k], in.m2[k], in.dl[k], in.lnpe[k], l,
+               want_kink ? kk : nullptr)) {
+        ls.push_back(l);
+        if (want_kink) kinks.insert(kinks.end(), kk, kk + NP);
+      }
     }
-    const Sums<T> S = sums_of(ls);
+    const Sums<T> S = sums_of(ls, kinks);
     const double n_i = (double)(in.offsets[e + 1] - in.offsets[e]);
     if (S.n_pos == 0) {
       lnL_event[e] = NEG_INF;
@@ -586,6 +618,7 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
       for (int i = 0; i < NP; ++i) {
         ev_grad[(size_t)e * NP + i] = S.g[i] / S.s1;
         ev_gabs[(size_t)e * NP + i] = S.gabs[i] / S.s1;
+        ev_gkink[(size_t)e * NP + i] = S.gkink[i] / S.s1;
       }
     }
   }
@@ -597,15 +630,21 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t c = 0; c < nchunk; ++c) {
     std::vector<T> ls;
+    std::vector<double> kinks;
+    double kk[NP];
     const int64_t a = c * chunk, b = std::min(in.n_inj, a + chunk);
     for (int64_t k = a; k < b; ++k) {
       T l;
-      if (ln_w(P, pbar.data(), nz, zmax, in.im1[k], in.im2[k], in.idl[k], in.ilnpd[k], l)) ls.push_back(l);
+      if (ln_w(P, pbar.data(), nz, zmax, in.im1[k], in.im2[k], in.idl[k], in.ilnpd[k], l,
+               want_kink ? kk : nullptr)) {
+        ls.push_back(l);
+        if (want_kink) kinks.insert(kinks.end(), kk, kk + NP);
+      }
     }
-    parts[(size_t)c] = sums_of(ls);
+    parts[(size_t)c] = sums_of(ls, kinks);
   }
   const Sums<T> Ssel = merge(parts);
-  double sel_grad[NP] = {0}, sel_gabs[NP] = {0};
+  double sel_grad[NP] = {0}, sel_gabs[NP] = {0}, sel_gkink[NP] = {0};
   if (Ssel.n_pos == 0) {
     *ln_xi = NEG_INF;
     *neff_sel = 0.0;
@@ -615,6 +654,7 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
     for (int i = 0; i < NP; ++i) {
       sel_grad[i] = Ssel.g[i] / Ssel.s1;
       sel_gabs[i] = Ssel.gabs[i] / Ssel.s1;
+      sel_gkink[i] = Ssel.gkink[i] / Ssel.s1;
     }
   }
 
@@ -654,6 +694,13 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
       gscale[i] = a + (double)ne * sel_gabs[i];
     }
   }
+  if (gkink) {
+    for (int i = 0; i < NP; ++i) {
+      double a = 0.0;
+      for (int e = 0; e < ne; ++e) a += ev_gkink[(size_t)e * NP + i];
+      gkink[i] = a + (double)ne * sel_gkink[i];
+    }
+  }
 }
 
 std::vector<double> row_to_double(const float* row, int nz) {
@@ -672,11 +719,14 @@ extern "C" {
 // lnL_total[K], flags[K] and, if grad_total != NULL, grad_total[K][13]
 // (want_grad != 0 selects the dual-number pass).  grad_scale[K][13] (may be NULL)
 // receives sum_i sum_k p_ik |d ln w_ik| + N_det sum_m q_m |d ln w_m|, the size of the
-// terms whose difference is the gradient.  Returns 0, or -1 on invalid inputs.
+// terms whose difference is the gradient.  grad_kink[K][13] (may be NULL) receives the
+// same weighted sum of the one-sided-derivative ambiguity of samples lying within 2e-5
+// LOS cells of a grid node (where either one-sided derivative is correct).  Returns 0,
+// or -1 on invalid inputs.
 int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad,
                double neff_min_event, double neff_min_sel, int32_t n_threads, double* lnL_event,
                double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
-               int32_t* flags, double* grad_total, double* grad_scale) {
+               int32_t* flags, double* grad_total, double* grad_scale, double* grad_kink) {
   if (!in || K < 0 || !inputs_valid(*in)) return -1;
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -688,14 +738,15 @@ int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad
   for (int k = 0; k < K; ++k) {
     double* g = (want_grad && grad_total) ? grad_total + (size_t)k * NP : nullptr;
     double* gs = (want_grad && grad_scale) ? grad_scale + (size_t)k * NP : nullptr;
+    double* gk = (want_grad && grad_kink) ? grad_kink + (size_t)k * NP : nullptr;
     if (want_grad)
       eval_lambda<Dual>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
                         lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
-                        neff_sel + k, lnL_total + k, flags + k, g, gs);
+                        neff_sel + k, lnL_total + k, flags + k, g, gs, gk);
     else
       eval_lambda<double>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
                           lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
-                          neff_sel + k, lnL_total + k, flags + k, nullptr, nullptr);
+                          neff_sel + k, lnL_total + k, flags + k, nullptr, nullptr, nullptr);
   }
   return 0;
 }
@@ -778,6 +829,50 @@ int orc_ln_w_row(const double* L, int64_t n, const float* m1, const float* m2, c
     } else {
       out[k] = NEG_INF;
       for (int i = 0; i < NP; ++i) out_grad[(size_t)k * NP + i] = 0.0;
+    }
+  }
+  return 0;
+}
+
+// ln w of n samples as the likelihood uses them: event samples (pix != NULL) against their
+// pixel's LOS row, injections (pix == NULL) against the pixel mean; N_z from the pixel
+// mean in both cases.  -inf where w = 0; out_grad[n][13] when non-NULL, and out_kink[n][13]
+// (with out_grad) the one-sided-derivative ambiguity of samples near a LOS grid node.
+int orc_ln_w_samples(const double* L, int64_t n, const float* m1, const float* m2, const float* dl,
+                     const float* lnpi, const int32_t* pix, const float* los, int32_t n_pix,
+                     int32_t nz, double zmax, double* out, double* out_grad, double* out_kink) {
+  if (!lambda_in_domain(L)) return -1;
+  std::vector<double> pbar((size_t)nz, 0.0);
+  for (int p = 0; p < n_pix; ++p)
+    for (int j = 0; j < nz; ++j) pbar[(size_t)j] += (double)los[(size_t)p * nz + j];
+  for (double& v : pbar) v /= (double)n_pix;
+  auto row_of = [&](int64_t k, std::vector<double>& row) {
+    if (!pix) { row = pbar; return; }
+    for (int j = 0; j < nz; ++j) row[(size_t)j] = (double)los[(size_t)pix[k] * nz + j];
+  };
+  if (!out_grad) {
+    const Pop<double> P = make_pop<double>(L, pbar, zmax);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+      std::vector<double> row((size_t)nz);
+      row_of(k, row);
+      double l;
+      out[k] = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l) ? l : NEG_INF;
+    }
+    return 0;
+  }
+  const Pop<Dual> P = make_pop<Dual>(L, pbar, zmax);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < n; ++k) {
+    std::vector<double> row((size_t)nz);
+    row_of(k, row);
+    Dual l;
+    double kk[NP] = {0};
+    const bool ok = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l, kk);
+    out[k] = ok ? l.v : NEG_INF;
+    for (int i = 0; i < NP; ++i) {
+      out_grad[(size_t)k * NP + i] = ok ? l.d[i] : 0.0;
+      if (out_kink) out_kink[(size_t)k * NP + i] = ok ? kk[i] : 0.0;
     }
   }
   return 0;

@@ -71,7 +71,8 @@ class Info(ctypes.Structure):
 
 EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_loglik_plain", "gwc_loglik_grad_host", "gwc_destroy", "gwc_last_error",
-           "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read")
+           "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read",
+           "gwc_sample_terms")
 
 
 def lib():
@@ -105,6 +106,8 @@ def lib():
         L.gwc_last_error.argtypes = [vp]
         L.gwc_get_info.restype = ctypes.c_int
         L.gwc_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.gwc_sample_terms.restype = ctypes.c_int
+        L.gwc_sample_terms.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gwc_profile_enable.restype = ctypes.c_int
         L.gwc_profile_enable.argtypes = [vp, i32]
         L.gwc_profile_read.restype = ctypes.c_int
@@ -244,6 +247,29 @@ def loglik_grad_host(ctx, lam: np.ndarray, grad=True, stream=None):
     return (tot, flags, g) if grad else (tot, flags)
 
 
+def sample_terms(ctx, lam, n_total, grad=True, stream=None):
+    """gwc_sample_terms for one Lambda (CUDA float64 tensor [13]): (ln w - c, d, c[14])."""
+    import torch
+    lam = lam.contiguous()
+    lnw = torch.empty(n_total, dtype=torch.float32, device=lam.device)
+    d = torch.empty((13, n_total), dtype=torch.float32, device=lam.device) if grad else None
+    c = torch.empty(14, dtype=torch.float64, device=lam.device)
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(lib().gwc_sample_terms(ctx, p(lam), p(lnw), p(d), p(c), _stream_ptr(stream)), ctx)
+    return lnw, d, c
+
+
+def sample_order(cat):
+    """Input index of each sample in the library's order (stable sort by pixel per event)."""
+    off = np.asarray(cat["offsets"], dtype=np.int64)
+    pix = np.asarray(cat["pix"])
+    out = []
+    for e in range(len(off) - 1):
+        idx = np.arange(off[e], off[e + 1])
+        out.append(idx[np.argsort(pix[idx], kind="stable")])
+    return np.concatenate(out) if out else np.zeros(0, np.int64)
+
+
 def profile_enable(ctx, enable=True):
     """gwc_profile_enable: record per-stage CUDA events in every call."""
     _check(lib().gwc_profile_enable(ctx, int(bool(enable))), ctx)
@@ -292,6 +318,10 @@ class Context:
 
     def info(self):
         return get_info(self._ctx)
+
+    def sample_terms(self, lam, grad=True, stream=None):
+        info = get_info(self._ctx)
+        return sample_terms(self._ctx, lam, info["n_samples"] + info["n_injections"], grad, stream)
 
     def profile_enable(self, enable=True):
         profile_enable(self._ctx, enable)

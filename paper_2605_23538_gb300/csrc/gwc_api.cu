@@ -702,6 +702,35 @@ gwc_status gwc_get_info(const gwc_ctx* c, gwc_info* out) {
   return GWC_OK;
 }
 
+gwc_status gwc_sample_terms(gwc_ctx* c, const double* d_lambda, float* d_lnw, float* d_dlnw,
+                            double* d_c, void* stream) {
+  if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
+  if (!d_lambda || !d_lnw || !d_c) return fail(c, GWC_E_INVALID, "NULL pointer");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gwc_status st = run_prologue(c, 1, d_lambda, true, s);
+  if (st != GWC_OK) return st;
+  TermsArgs ta;
+  ta.smp = c->smp;
+  ta.pix = c->pix;
+  ta.inj = c->inj;
+  ta.los = c->los;
+  ta.pbar32 = c->pbar32;
+  ta.nz = c->n_z;
+  ta.nx = c->opt.n_x_table;
+  ta.n_samples = c->n_samples;
+  ta.n_total = c->n_samples + c->n_inj;
+  ta.lf = c->lf;
+  ta.ld = c->ld;
+  ta.tables = c->tables;
+  ta.lnw = d_lnw;
+  ta.dlnw = d_dlnw;
+  ta.c = d_c;
+  cudaError_t e = launch_sample_terms(ta, c->bf16, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sample-terms launch");
+  return GWC_OK;
+}
+
 gwc_status gwc_profile_enable(gwc_ctx* c, int32_t enable) {
   if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");

@@ -6,8 +6,13 @@
 //     relation on a uniform x = d_L H0 / c grid, as cubic Hermite segments stored in a
 //     split (hi + lo) form so the cell index and the in-cell fraction keep ~1e-7 of a cell;
 //   * J(x) = d I / d Om at z(x) (gradient only), I(z) = int_0^z dz'/E;
-//   * four smoothing-window tables of ratios R = (integral) / (m^beta S(m)) over
-//     m in [m_min, m_min + delta_m] (the value path uses the first).
+//   * four smoothing-window tables over m in [m_min, m_min + delta_m] (the value path
+//     uses the first).  With m' = m - m_min, g = m^beta S(m) and R_X = X(m) / g for the
+//     integrals C = int m^beta S, C_beta = int m^beta ln m S, J = int m^(beta-1) S and
+//     K = int m^beta dS/d delta_m from m_min, the tables hold the smooth, positive-definite
+//     ratios Q_C = R_C delta_m / m'^2 (-> 1 at m_min), Q_beta = R_beta / R_C (-> ln m_min),
+//     Q_J = R_J / R_C (-> 1/m_min) and Q_K = R_K delta_m / m' (-> -1), which a cubic Hermite
+//     interpolates to FP32 precision right down to m_min.
 #pragma once
 
 #include <cstdint>
@@ -26,9 +31,11 @@ constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the pr
 
 enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
 
-// FP32 constants of one Lambda point for the sample kernels (44 floats = 11 float4).
+// FP32 constants of one Lambda point for the sample kernels (48 floats = 12 float4).
 struct __align__(16) LamF {
   float H0c, xmax, inv_dx, live;       // x = dL * H0/c; table spacing; 0 = skip this Lambda
+  float H0c_lo, inv_dx_lo, inv_dm, lam_edge;   // low parts of H0/c and (nx-1)/xmax; 1/delta_m;
+                                               // 1 when lambda_peak is 0 or 1 (see Acc)
   float om, zstep, inv_zstep, lp;      // Om; z_max/(n_z-1); its inverse; ln(1+z_p)
   float alpha, beta, mmin, mmax;
   float dm, mw, mu, inv_sig;           // mw = m_min + delta_m
@@ -41,7 +48,7 @@ struct __align__(16) LamF {
   float Jw, Kw, la0, lb0;              // int m^(beta-1) S; int m^beta dS/d delta_m; la, lb without ln(1-lam), ln lam
   float lam, inv_lam, inv_1ml, pad;    // lambda_peak, 1/lambda, 1/(1-lambda)
 };
-static_assert(sizeof(LamF) == 44 * 4, "LamF layout");
+static_assert(sizeof(LamF) == 48 * 4, "LamF layout");
 
 // FP64 constants of one Lambda point for the merge: ln w = (per-sample term) + c.
 struct LamD {
@@ -56,8 +63,8 @@ struct LamD {
 //                      segment n: P = P_n + t (D + t (c2 + t c3)), t in [0, 1)
 //   [4 NX, 5 NX)       float c3[NX]
 //   [5 NX, 7 NX)       float2 jtab[NX] {J, dJ/dx * dx} (Hermite)
-//   [7 NX, 7 NX + 8 (NW_WIN + 1))  float2 win[4][NW_WIN + 1] {R, dR/dm * h}: R_C, R_beta,
-//                      R_J, R_K (Hermite in m over [m_min, m_min + delta_m])
+//   [7 NX, 7 NX + 8 (NW_WIN + 1))  float2 win[4][NW_WIN + 1] {Q, dQ/dm * h}: Q_C, Q_beta,
+//                      Q_J, Q_K (Hermite in m over [m_min, m_min + delta_m])
 __host__ __device__ inline int table_floats(int nx) { return 7 * nx + 8 * (NW_WIN + 1); }
 
 struct Item {          // one work item: a contiguous run of samples of one event, or of injections
@@ -105,6 +112,11 @@ __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int
 // ln w (without the per-Lambda constant c) and, for GRAD, d ln w / d Lambda.
 // row: the sample's LOS row (or the pixel-averaged row for injections).
 // pos/pc3/jtab/win: this Lambda's tables (global memory, read through L1).
+// When L.lam_edge is set (lambda_peak = 0 or 1) the lambda derivative
+// e^(ln G - mix) - e^(ln P - mix) can exceed the float range for samples far from one
+// mixture component, although its product with the sample's weight does not; g[P_LAM]
+// then holds ln P - mix and lam_lb holds ln G - mix, and the accumulator forms the
+// weighted difference in the exponent (lam_edge_term).
 // Returns false where w = 0.
 template <bool GRAD, typename RowT>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
@@ -112,15 +124,20 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const float4* __restrict__ pos,
                                            const float* __restrict__ pc3, int nx,
                                            const float2* __restrict__ jtab,
-                                           const float2* __restrict__ win, float& lw, float* g) {
+                                           const float2* __restrict__ win, float& lw, float* g,
+                                           float& lam_lb) {
+  // x = d_L H0 / c and the table coordinate x / dx carried with their rounding errors
+  // (exact products by FMA), so the LOS-grid position keeps ~1e-7 of a cell
   const float x = s.dl * L.H0c;
   if (!(x > 0.f) || x > L.xmax) return false;
   if (s.m2 > s.m1) return false;
+  const float x_lo = fmaf(s.dl, L.H0c, -x) + s.dl * L.H0c_lo;
+  const float sx = x * L.inv_dx;
+  const float sx_lo = fmaf(x, L.inv_dx, -sx) + fmaf(x, L.inv_dx_lo, x_lo * L.inv_dx);
 
   // --- d_L -> z: position on the LOS grid from the Hermite table (split precision)
-  const float sx = x * L.inv_dx;
   const int n = min((int)sx, nx - 2);
-  const float t = sx - (float)n;
+  const float t = (sx - (float)n) + sx_lo;
   const float4 nd = __ldg(pos + n);
   const float frac = nd.y + t * (nd.z + t * (nd.w + t * __ldg(pc3 + n)));
   int j = (int)floorf(nd.x + frac);
@@ -164,15 +181,19 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   float2 wa = make_float2(0.f, 0.f), wb = wa;
   float wt = 0.f;
   int wk = 0;
+  float mp1 = 0.f, Qc = 0.f;
   if (win1) {
-    // in the window C(m1) = m1^beta S(m1) R_C(m1); S(m1) cancels against p(m1)
-    const float ws = (m1s - L.mmin) * L.inv_wh;
+    // in the window C(m1) = m1^beta S(m1) R_C(m1) with R_C = Q_C m'^2 / delta_m;
+    // S(m1) cancels against p(m1)
+    mp1 = m1s - L.mmin;
+    const float ws = mp1 * L.inv_wh;
     wk = min((int)ws, NW_WIN - 1);
     wt = ws - (float)wk;
     wa = __ldg(win + wk);
     wb = __ldg(win + wk + 1);
-    Cx = fmaxf(hermite_val(wa, wb, wt), 1e-37f);
-    Cprod = 1.f;   // R_C can be tiny near m_min: keep its log separate
+    Qc = hermite_val(wa, wb, wt);
+    Cx = Qc * (mp1 * mp1) * L.inv_dm;   // R_C >= ~1e-14 (m' >= one float ulp of m_min)
+    Cprod = 1.f;                         // R_C can be small near m_min: keep its log separate
     lmass = L.beta * (lm2s - lm1s) - logf(Cx);
   } else {
     // above it C(m1) = C(mw) + mw^(1+beta) (exp((1+beta)(ln m1 - ln mw)) - 1) / (1+beta)
@@ -225,15 +246,15 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
       const float i1 = __frcp_rn(mp1), i2 = __frcp_rn(mp1 - L.dm);
       dS1_dmin = -sf1 * L.dm * (i1 * i1 + i2 * i2);
       dS1_ddm = -sf1 * (i1 + mp1 * i2 * i2);
-      const float iR = __frcp_rn(Cx);
-      const float Rb = hermite_val(__ldg(win + (NW_WIN + 1) + wk), __ldg(win + (NW_WIN + 1) + wk + 1), wt);
-      const float Rj = hermite_val(__ldg(win + 2 * (NW_WIN + 1) + wk), __ldg(win + 2 * (NW_WIN + 1) + wk + 1), wt);
-      const float Rk = hermite_val(__ldg(win + 3 * (NW_WIN + 1) + wk), __ldg(win + 3 * (NW_WIN + 1) + wk + 1), wt);
-      dlnC_db = Rb * iR;
-      dlnC_dmin = fmaf(L.beta, Rj, -1.f) * iR;
-      dlnC_ddm = Rk * iR;
-      // -ln R_C(m1s) through m1s = m1/u:  + m1s R_C'/R_C / u
-      Gc = m1s * hermite_dt(wa, wb, wt) * L.inv_wh * iR;
+      const float Qb = hermite_val(__ldg(win + (NW_WIN + 1) + wk), __ldg(win + (NW_WIN + 1) + wk + 1), wt);
+      const float Qj = hermite_val(__ldg(win + 2 * (NW_WIN + 1) + wk), __ldg(win + 2 * (NW_WIN + 1) + wk + 1), wt);
+      const float Qk = hermite_val(__ldg(win + 3 * (NW_WIN + 1) + wk), __ldg(win + 3 * (NW_WIN + 1) + wk + 1), wt);
+      const float iQ = __frcp_rn(Qc), im = __frcp_rn(mp1);
+      dlnC_db = Qb;                                     // R_beta / R_C
+      dlnC_dmin = fmaf(L.beta, Qj, -__frcp_rn(Cx));     // (-1 + beta R_J) / R_C
+      dlnC_ddm = Qk * iQ * im;                          // R_K / R_C
+      // -ln R_C(m1s) through m1s = m1/u:  m1s (Q_C'/Q_C + 2/m') / u
+      Gc = m1s * fmaf(hermite_dt(wa, wb, wt) * L.inv_wh, iQ, 2.f * im);
     } else {
       const float iC = __frcp_rn(Cx);
       A = L.mw1b * (Q * L.eps_b + 1.f);   // m1s^(1+beta)
@@ -267,11 +288,12 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     g[P_DM] = dS1_ddm + dS2_ddm - dlnC_ddm;
     g[P_MU] = pb * (zz * L.inv_sig - L.dZGmu);
     g[P_SIG] = pb * (fmaf(zz, zz, -1.f) * L.inv_sig - L.dZGsig);
-    if (L.lam > 0.f && L.lam < 1.f) {
+    if (L.lam_edge == 0.f) {
       g[P_LAM] = pb * L.inv_lam - pa * L.inv_1ml;
     } else {
       const float mix = mx + log1pf(eab);
-      g[P_LAM] = expf(fmaf(-0.5f * zz, zz, L.lb0) - mix) - expf(L.la0 - L.alpha * lm1s - mix);
+      g[P_LAM] = L.la0 - L.alpha * lm1s - mix;         // ln P - mix
+      lam_lb = fmaf(-0.5f * zz, zz, L.lb0) - mix;      // ln G - mix
     }
     const float dl = lu - L.lp;
     g[P_GAM] = lu - sr * dl;
@@ -279,6 +301,11 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     g[P_ZP] = sr * L.gpk * L.inv1zp;
   }
   return true;
+}
+
+// e^d (e^lb - e^la) without forming either exponential on its own
+__device__ __forceinline__ float lam_edge_term(float d, float la, float lb) {
+  return expf(d + lb) - expf(d + la);
 }
 
 // Online (max, sum e^(l-max), sum e^(2(l-max)), sum e^(l-max) dl) accumulator.
@@ -290,7 +317,8 @@ struct Acc {
 #pragma unroll
     for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] = 0.f;
   }
-  __device__ __forceinline__ void add(float lw, const float* dg) {
+  __device__ __forceinline__ void add(float lw, const float* dg, bool lam_edge = false,
+                                      float lam_lb = 0.f) {
     if (lw > m) {
       const float sc = expf(m - lw);   // 0 on the first sample
       s1 = fmaf(s1, sc, 1.f);
@@ -298,8 +326,9 @@ struct Acc {
       c1 *= sc;
       c2 *= sc * sc;
       if (GRAD) {
+        const float dl = lam_edge ? lam_edge_term(0.f, dg[P_LAM], lam_lb) : dg[P_LAM];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) g[i] = fmaf(g[i], sc, dg[i]);
+        for (int i = 0; i < NP; ++i) g[i] = fmaf(g[i], sc, i == P_LAM ? dl : dg[i]);
       }
       m = lw;
     } else {
@@ -316,8 +345,9 @@ struct Acc {
         s2 = fmaf(tt, tt, s2);
       }
       if (GRAD) {
+        const float cl = lam_edge ? lam_edge_term(lw - m, dg[P_LAM], lam_lb) : tt * dg[P_LAM];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) g[i] = fmaf(tt, dg[i], g[i]);
+        for (int i = 0; i < NP; ++i) g[i] = i == P_LAM ? g[i] + cl : fmaf(tt, dg[i], g[i]);
       }
     }
   }

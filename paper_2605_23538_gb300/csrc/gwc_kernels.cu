@@ -16,6 +16,7 @@
 #include "gwc_internal.cuh"
 #include "gwc_kernels.h"
 
+#include <algorithm>
 #include <cfloat>
 
 namespace gwc {
@@ -304,36 +305,48 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double dWmax = -(1.0 - lam) * dZPmax * wv[5] - lam * dZGmax * wv[6];
   const double dWmin = wv[7], dWdm = wv[8];
 
-  // window tables: ratios R = I(m) / (m^beta S(m)) at nodes m_k = mmin + k hw
+  // window tables at nodes m_k = mmin + k hw: with R_X = X / (m^beta S(m)),
+  //   Q_C = R_C dm / m'^2, Q_beta = R_beta / R_C, Q_J = R_J / R_C, Q_K = R_K dm / m'
+  // and their m-derivatives (times hw).  Node 0 takes the m' -> 0 limits (1, ln mmin,
+  // 1/mmin, -1) with secant slopes: weights there carry S(m1) < e^-127.
   float2* win = reinterpret_cast<float2*>(tb + 7 * nx);
   __shared__ double scum[4][NW_WIN + 1];
+  __shared__ double sq[4][NW_WIN + 1];
   if (tid < NW_WIN)
     for (int i = 0; i < 4; ++i) scum[i][tid + 1] = cum[i];
   if (tid == 0)
     for (int i = 0; i < 4; ++i) scum[i][0] = 0.0;
   __syncthreads();
-  if (tid <= NW_WIN) {
-    float2 r[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                   make_float2(0.f, 0.f)};
-    if (tid > 0 && dm > 0.0) {
-      const double m = mmin + tid * hw, mp = m - mmin, lm = log(m);
-      double S = 1.0, oneS = 0.0, dSddm = 0.0, dlnS = 0.0, dSS = 0.0;
-      if (tid < NW_WIN) {
-        smooth_d(mp, dm, S, oneS, dSddm);
-        dlnS = oneS * dm * (1.0 / (mp * mp) + 1.0 / ((mp - dm) * (mp - dm)));
-        dSS = -oneS * (1.0 / mp + mp / ((mp - dm) * (mp - dm)));   // (dS/d delta_m) / S
-      }
-      const double g = exp(beta * lm) * S;
-      const double gl = beta / m + dlnS;     // g'/g
-      const double Rc = scum[0][tid] / g, Rb = scum[1][tid] / g;
-      const double Rj = scum[2][tid] / g, Rk = scum[3][tid] / g;
-      r[0] = make_float2((float)Rc, (float)((1.0 - Rc * gl) * hw));
-      r[1] = make_float2((float)Rb, (float)((lm - Rb * gl) * hw));
-      r[2] = make_float2((float)Rj, (float)((1.0 / m - Rj * gl) * hw));
-      r[3] = make_float2((float)Rk, (float)((dSS - Rk * gl) * hw));
+  double qv[4] = {1.0, log(mmin), 1.0 / mmin, -1.0}, qd[4] = {0.0, 0.0, 0.0, 0.0};
+  if (tid <= NW_WIN && tid > 0 && dm > 0.0) {
+    const double mp = tid * hw, m = mmin + mp, lm = log(m);
+    double S = 1.0, oneS = 0.0, dSddm = 0.0, dlnS = 0.0, dSS = 0.0;
+    if (tid < NW_WIN) {
+      smooth_d(mp, dm, S, oneS, dSddm);
+      dlnS = oneS * dm * (1.0 / (mp * mp) + 1.0 / ((mp - dm) * (mp - dm)));
+      dSS = -oneS * (1.0 / mp + mp / ((mp - dm) * (mp - dm)));   // (dS/d delta_m) / S
     }
-    for (int i = 0; i < 4; ++i) win[i * (NW_WIN + 1) + tid] = r[i];
+    const double gg = exp(beta * lm) * S;
+    const double gl = beta / m + dlnS;     // g'/g
+    const double Rc = scum[0][tid] / gg, Rb = scum[1][tid] / gg;
+    const double Rj = scum[2][tid] / gg, Rk = scum[3][tid] / gg;
+    const double dRc = 1.0 - Rc * gl, dRb = lm - Rb * gl, dRj = 1.0 / m - Rj * gl, dRk = dSS - Rk * gl;
+    qv[0] = Rc * dm / (mp * mp);
+    qv[1] = Rb / Rc;
+    qv[2] = Rj / Rc;
+    qv[3] = Rk * dm / mp;
+    qd[0] = dm * (dRc / (mp * mp) - 2.0 * Rc / (mp * mp * mp));
+    qd[1] = (dRb - qv[1] * dRc) / Rc;
+    qd[2] = (dRj - qv[2] * dRc) / Rc;
+    qd[3] = dm * (dRk / mp - Rk / (mp * mp));
   }
+  if (tid <= NW_WIN)
+    for (int i = 0; i < 4; ++i) sq[i][tid] = qv[i];
+  __syncthreads();
+  if (tid == 0 && dm > 0.0)
+    for (int i = 0; i < 4; ++i) qd[i] = (sq[i][1] - sq[i][0]) / hw;
+  if (tid <= NW_WIN)
+    for (int i = 0; i < 4; ++i) win[i * (NW_WIN + 1) + tid] = make_float2((float)qv[i], (float)(qd[i] * hw));
 
   // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
   //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
@@ -375,6 +388,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.xmax = (float)xmax;
     f.inv_dx = (float)(1.0 / dx);
     f.live = 1.f;
+    f.H0c_lo = (float)(H0 / C_KMS - (double)f.H0c);
+    f.inv_dx_lo = (float)(1.0 / dx - (double)f.inv_dx);
+    f.inv_dm = dm > 0.0 ? (float)(1.0 / dm) : 0.f;
+    f.lam_edge = (lam > 0.0 && lam < 1.0) ? 0.f : 1.f;
     f.om = (float)om;
     f.zstep = (float)(zmax / (nz - 1));
     f.inv_zstep = (float)pscale;
@@ -477,6 +494,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
   for (int task = warp; task < ntask; task += WARPS) {
     const int k = k0 + task / A.P, part = task - (task / A.P) * A.P;
     const LamF L = A.lf[k];
+    const bool lam_edge = L.lam_edge != 0.f;
     Acc<GRAD, KAHAN> acc;
     if (L.live != 0.f) {
       const float* tb = A.tables + (size_t)k * A.tstride;
@@ -490,14 +508,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
         SampleIn s;
         s.m1 = s_m1[i]; s.m2 = s_m2[i]; s.dl = s_dl[i]; s.lpe = s_lpe[i];
         s.lm1 = s_lm1[i]; s.lm2 = s_lm2[i];
-        float lw, g[GRAD ? NP : 1];
+        float lw, g[GRAD ? NP : 1], lb = 0.f;
         bool ok;
         if (inj)
-          ok = sample_lnw<GRAD>(L, s, A.pbar32, nz, pos, pc3, nx, jt, wt, lw, g);
+          ok = sample_lnw<GRAD>(L, s, A.pbar32, nz, pos, pc3, nx, jt, wt, lw, g, lb);
         else
           ok = sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
-                                nz, pos, pc3, nx, jt, wt, lw, g);
-        if (ok) acc.add(lw, g);
+                                nz, pos, pc3, nx, jt, wt, lw, g, lb);
+        if (ok) acc.add(lw, g, GRAD && lam_edge, lb);
       }
       if (KAHAN) { acc.s1 -= acc.c1; acc.s2 -= acc.c2; }
     }
@@ -545,18 +563,18 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
   s.lm1 = logf(v.x); s.lm2 = logf(v.y);
   const float* tb = A.tables + (size_t)A.k * A.tstride;
   const int nx = A.nx;
-  float lw = -INFINITY, g[GRAD ? NP : 1];
+  float lw = -INFINITY, g[GRAD ? NP : 1], lb = 0.f;
   bool ok = false;
   if (L.live != 0.f) {
     if (inj)
       ok = sample_lnw<GRAD>(L, s, A.pbar32, A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
                             reinterpret_cast<const float2*>(tb + 5 * nx),
-                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g);
+                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
     else
       ok = sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
                             A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
                             reinterpret_cast<const float2*>(tb + 5 * nx),
-                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g);
+                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
   }
   if (!GRAD) {
     A.lw[i] = ok ? lw : -INFINITY;
@@ -564,6 +582,8 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
     const float m = A.partials[((size_t)A.k * A.n_items + A.sample_item[i]) * PSTRIDE];
     const float t = ok ? expf(lw - m) : 0.f;
     for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * g[q] : 0.f;
+    if (ok && L.lam_edge != 0.f)
+      A.tg[(size_t)P_LAM * A.n_total + i] = lam_edge_term(lw - m, g[P_LAM], lb);
   }
 }
 
@@ -791,6 +811,49 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
         A.grad_total[(size_t)k * NP + i] =
             (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + D.dc[i]);
   }
+}
+
+// --------------------------------------------------------- per-sample terms (tests)
+template <typename RowT>
+__global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    A.c[0] = A.ld->c;
+    for (int q = 0; q < NP; ++q) A.c[1 + q] = A.ld->dc[q];
+  }
+  if (i >= A.n_total) return;
+  const LamF L = A.lf[0];
+  const bool inj = i >= A.n_samples;
+  const float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
+  SampleIn s;
+  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.lpe = v.w;
+  s.lm1 = logf(v.x); s.lm2 = logf(v.y);
+  const float* tb = A.tables;
+  const int nx = A.nx;
+  float lw = -INFINITY, g[NP], lb = 0.f;
+  bool ok = false;
+  if (L.live != 0.f) {
+    if (inj)
+      ok = sample_lnw<true>(L, s, A.pbar32, A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
+                            reinterpret_cast<const float2*>(tb + 5 * nx),
+                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
+    else
+      ok = sample_lnw<true>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
+                            A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
+                            reinterpret_cast<const float2*>(tb + 5 * nx),
+                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
+    if (ok && L.lam_edge != 0.f) g[P_LAM] = lam_edge_term(0.f, g[P_LAM], lb);   // may overflow
+  }
+  A.lnw[i] = ok ? lw : -INFINITY;
+  if (A.dlnw)
+    for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? g[q] : 0.f;
+}
+
+cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s) {
+  const int grid = (int)std::max(1LL, (a.n_total + 255) / 256);
+  if (bf16) k_sample_terms<__nv_bfloat16><<<grid, 256, 0, s>>>(a);
+  else k_sample_terms<float><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ cell index (tests)

@@ -95,6 +95,24 @@ cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, i
 cudaError_t launch_plain_sample(const PlainArgs& a, bool grad, bool bf16, cudaStream_t s);
 cudaError_t launch_plain_reduce(const PlainArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_merge(const MergeArgs& a, int K, bool grad, cudaStream_t s);
+struct TermsArgs {
+  const float4* smp;
+  const int32_t* pix;
+  const float4* inj;
+  const void* los;
+  const float* pbar32;
+  int nz;
+  int nx;
+  long long n_samples;
+  long long n_total;
+  const LamF* lf;
+  const LamD* ld;
+  const float* tables;
+  float* lnw;       // [n_total]
+  float* dlnw;      // [13][n_total] or nullptr
+  double* c;        // [14]
+};
+cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s);
 cudaError_t launch_los_cell(const float* z, long long n, int nz, double zmax, int* cell, cudaStream_t s);
 
 }  // namespace gwc
