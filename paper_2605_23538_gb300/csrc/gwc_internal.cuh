@@ -152,7 +152,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   // --- LOS prior of the sample's pixel, linear in z
   const float p0 = ld_row(row, j), p1 = ld_row(row, j + 1);
   const float dp = p1 - p0;
-  const float plos = fmaf(tl, dp, p0);
+  const float plos = fmaf(tl, p1, (1.f - tl) * p0);   // convex form: no cancellation in tails
   if (!(plos > 0.f)) return false;
 
   // --- source-frame masses
