@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 METRIC = "posterior-sample×Λ log-lik+grad evals/s at O5 scale vs plain GPU path"
 WORKLOAD = "c3"
 K_LAMBDA = 256
+WORKLOAD_NAMES = {
+    "c2": "c2: 150 events x U{2000..8000} samples, nside-32 (12288 px) x 2048-z LOS, 1e6 injections",
+    "c3": "c3: 2000 events x log-uniform 1k-16k samples (O5-like), nside-64 (49152 px) x 2048-z LOS, "
+          "1e7 detected injections",
+    "c5": "c5: 10000 events x 4096 samples, nside-64 x 2048-z LOS, 5e7 injections",
+}
 
 
 def log(*a):
@@ -208,6 +214,11 @@ def main():
     ap.add_argument("--impl", default="gwc", choices=["gwc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-k", type=int, default=32, help="Lambda points timed on the plain path")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["c2", "c3", "c5"],
+                    help="catalogue size (c3 = the O5-scale headline; c2 for small profiling cases)")
+    ap.add_argument("--K", type=int, default=K_LAMBDA, help="Lambda points per call")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the value+gradient step (no value-only, plain or e2e legs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -233,17 +244,18 @@ def main():
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    cat = synth.catalogue(WORKLOAD)
+    K = args.K
+    cat = synth.catalogue(args.workload)
     log(f"[rank {rank}] catalogue {time.perf_counter() - t0:.1f} s: {len(cat['m1'])} samples, "
         f"{len(cat['inj_m1'])} injections, LOS {cat['los'].shape}")
     n_s, n_i = len(cat["m1"]), len(cat["inj_m1"])
-    ctx = g.Context(cat, max_K=K_LAMBDA)
+    ctx = g.Context(cat, max_K=K)
     info = ctx.info()
     # each rank evaluates its own Lambda batch over the full catalogue (weak scaling)
-    lam_np = synth.lambda_batch(K_LAMBDA, purpose=4 + 100 * rank)
+    lam_np = synth.lambda_batch(K, purpose=4 + 100 * rank)
     lam = torch.tensor(lam_np, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    out = g._outputs(K_LAMBDA, ctx.n_events, lam.device, True)
+    out = g._outputs(K, ctx.n_events, lam.device, True)
 
     def step():
         g.loglik_grad(ctx._ctx, lam, ctx.n_events, stream, out)
@@ -270,53 +282,55 @@ def main():
     if dist is not None:
         dist.all_reduce(ms, op=dist.ReduceOp.MAX)
     ms_total = float(ms.item())
-    evals_step = (n_s + n_i) * K_LAMBDA
+    evals_step = (n_s + n_i) * K
     value = evals_step * args.steps * world / (ms_total / 1e3)
     flags = out["flags"].cpu().numpy()
     fused_ms = stage_ms[1] / max(n_calls, 1)
     roof = alu_roofline(evals_step, fused_ms / 1e3)
     roof["traffic"] = None
 
-    # value-only throughput (same batch)
-    outv = g._outputs(K_LAMBDA, ctx.n_events, lam.device, False)
-    for _ in range(2):
-        g.loglik(ctx._ctx, lam, ctx.n_events, stream, outv)
-    barrier()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        g.loglik(ctx._ctx, lam, ctx.n_events, stream, outv)
-    ev1.record(stream)
-    barrier()
-    value_only = evals_step * args.steps / (ev0.elapsed_time(ev1) / 1e3)
+    value_only = plain = e2e = None
+    if not args.no_extras:
+        # value-only throughput (same batch)
+        outv = g._outputs(K, ctx.n_events, lam.device, False)
+        for _ in range(2):
+            g.loglik(ctx._ctx, lam, ctx.n_events, stream, outv)
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g.loglik(ctx._ctx, lam, ctx.n_events, stream, outv)
+        ev1.record(stream)
+        barrier()
+        value_only = evals_step * args.steps / (ev0.elapsed_time(ev1) / 1e3)
 
-    # the plain single-Lambda FP32 path, value+gradient, on the first plain_k points
-    kp = max(1, min(args.plain_k, K_LAMBDA))
-    lam_p = lam[:kp].contiguous()
-    outp = g._outputs(kp, ctx.n_events, lam.device, True)
-    g.loglik_plain(ctx._ctx, lam_p, ctx.n_events, True, stream, outp)
-    barrier()
-    ev0.record(stream)
-    psteps = 2
-    for _ in range(psteps):
+        # the plain single-Lambda FP32 path, value+gradient, on the first plain_k points
+        kp = max(1, min(args.plain_k, K))
+        lam_p = lam[:kp].contiguous()
+        outp = g._outputs(kp, ctx.n_events, lam.device, True)
         g.loglik_plain(ctx._ctx, lam_p, ctx.n_events, True, stream, outp)
-    ev1.record(stream)
-    barrier()
-    plain = (n_s + n_i) * kp * psteps / (ev0.elapsed_time(ev1) / 1e3)
+        barrier()
+        ev0.record(stream)
+        psteps = 2
+        for _ in range(psteps):
+            g.loglik_plain(ctx._ctx, lam_p, ctx.n_events, True, stream, outp)
+        ev1.record(stream)
+        barrier()
+        plain = (n_s + n_i) * kp * psteps / (ev0.elapsed_time(ev1) / 1e3)
 
-    # end to end through the host-memory entry point (Lambda in, totals and gradient out)
-    for _ in range(2):
-        ctx.loglik_grad_host(lam_np)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.loglik_grad_host(lam_np)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": evals_step * args.steps / e2e_s, "unit": "evals/s",
-           "h2d_bytes_per_step": K_LAMBDA * 13 * 8,
-           "d2h_bytes_per_step": K_LAMBDA * 8 + K_LAMBDA * 4 + K_LAMBDA * 13 * 8}
+        # end to end through the host-memory entry point (Lambda in, totals and gradient out)
+        for _ in range(2):
+            ctx.loglik_grad_host(lam_np)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.loglik_grad_host(lam_np)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": evals_step * args.steps / e2e_s, "unit": "evals/s",
+               "h2d_bytes_per_step": K * 13 * 8,
+               "d2h_bytes_per_step": K * 8 + K * 4 + K * 13 * 8}
 
     base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
         import oracle
         oracle.build()
         base = cpu_baseline(cat, lam_np)
@@ -328,9 +342,8 @@ def main():
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "c3: 2000 events x log-uniform 1k-16k samples (O5-like), "
-                                   "nside-64 (49152 px) x 2048-z LOS, 1e7 detected injections",
-                       "K": K_LAMBDA, "n_samples": n_s, "n_injections": n_i,
+            "config": {"workload": WORKLOAD_NAMES[args.workload],
+                       "K": K, "n_samples": n_s, "n_injections": n_i,
                        "evals_per_step": evals_step, "parallelism": f"lambda-batch x{world}",
                        "l2": "inputs larger than L2 (resident catalogue %.2f GB), no flush"
                              % (info["device_bytes"] / 1e9),
@@ -338,14 +351,15 @@ def main():
             "roofline": roof,
             "stage_ms_per_step": {"prologue": stage_ms[0] / max(n_calls, 1), "fused": fused_ms,
                                   "merge": stage_ms[2] / max(n_calls, 1)},
-            "value_only": {"value": value_only, "unit": "evals/s"},
-            "plain_gpu": {"value": plain, "unit": "evals/s", "K": kp,
-                          "speedup": value / world / plain},
-            "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "flags_nonzero": int(np.count_nonzero(flags)),
             "peaks": {"source": src, "hbm_gbs": peaks.get("hbm_gbs")},
         }
+        if value_only is not None:
+            line["value_only"] = {"value": value_only, "unit": "evals/s"}
+            line["plain_gpu"] = {"value": plain, "unit": "evals/s", "K": kp,
+                                 "speedup": value / world / plain}
+            line["e2e"] = e2e
         if clocks is not None:
             line["clocks"] = clocks
         if base is not None:
