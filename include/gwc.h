@@ -195,6 +195,37 @@ gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
 gwc_status gwc_sample_terms(gwc_ctx* ctx, const double* d_lambda, float* d_lnw, float* d_dlnw,
                             double* d_c, void* stream);
 
+/* Per-sample terms without allocating: the same outputs as gwc_sample_terms, computed
+ * from caller-owned device arrays instead of a context.  The paper has no counterpart;
+ * this entry point serves callers that cannot allocate device memory when they need an
+ * evaluation -- code running while a CUDA graph is being captured (cudaMalloc is not
+ * allowed then), code inside a framework whose caching allocator owns the device's
+ * memory, or callbacks that must leave the memory state untouched -- and so cannot hold
+ * a gwc_ctx.  It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (one Lambda point's constants and tables and the pixel-mean LOS row, about 80 KB) is a
+ * fixed device array inside the library, held by every GPU that loads the library until
+ * the process exits.
+ *   d_lambda[13]                      Lambda (device, doubles)
+ *   d_samples[n_samples][4]           {m1_det, m2_det, d_L, ln pi_PE} (device, 16-byte aligned)
+ *   d_pix[n_samples]                  pixel of each sample, in [0, n_pix)
+ *   d_injections[n_inj][4]            {m1_det, m2_det, d_L, ln p_draw} (device, 16-byte aligned)
+ *   d_los[n_pix][n_z]                 LOS priors on z_j = j z_max / (n_z - 1) (device, float)
+ *   n_x_table                         inversion-table nodes, a multiple of 4 in [16, 1024]
+ *   d_lnw[n_samples + n_inj], d_dlnw[13][n_samples + n_inj] (may be NULL), d_c[14]:
+ *                                     as for gwc_sample_terms, samples in the caller's order
+ * Sizes beyond the scratch (n_z > 4096, n_x_table > 1024) are rejected with
+ * GWC_E_INVALID and a message from gwc_last_error(NULL).  The first call on a device
+ * looks up the scratch array's device address and uploads the quadrature constants, so
+ * make that first call before any stream capture begins.  Every call shares the one
+ * scratch array and overwrites what it reads, so nothing carries over between calls, but
+ * calls whose kernels overlap on the GPU (several streams or host threads at once) race on
+ * it: serialise them. */
+gwc_status gwc_sample_terms_noalloc(const double* d_lambda, int64_t n_samples,
+                                    const float* d_samples, const int32_t* d_pix, int64_t n_inj,
+                                    const float* d_injections, int32_t n_pix, int32_t n_z,
+                                    double z_max, const float* d_los, int32_t n_x_table,
+                                    float* d_lnw, float* d_dlnw, double* d_c, void* stream);
+
 /* Per-kernel timing.  While enabled, every call records CUDA events on its stream around
  * its three stages (the prologue kernel, the sample kernel or the plain path's sample
  * passes, and the merge kernel).  gwc_profile_read waits for the recorded events,

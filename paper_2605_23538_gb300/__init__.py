@@ -72,7 +72,7 @@ class Info(ctypes.Structure):
 EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_loglik_plain", "gwc_loglik_grad_host", "gwc_destroy", "gwc_last_error",
            "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read",
-           "gwc_sample_terms")
+           "gwc_sample_terms", "gwc_sample_terms_noalloc")
 
 
 def lib():
@@ -108,6 +108,9 @@ def lib():
         L.gwc_get_info.argtypes = [vp, ctypes.POINTER(Info)]
         L.gwc_sample_terms.restype = ctypes.c_int
         L.gwc_sample_terms.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gwc_sample_terms_noalloc.restype = ctypes.c_int
+        L.gwc_sample_terms_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, i32, i32, d, vp, i32,
+                                               vp, vp, vp, vp]
         L.gwc_profile_enable.restype = ctypes.c_int
         L.gwc_profile_enable.argtypes = [vp, i32]
         L.gwc_profile_read.restype = ctypes.c_int
@@ -256,6 +259,27 @@ def sample_terms(ctx, lam, n_total, grad=True, stream=None):
     c = torch.empty(14, dtype=torch.float64, device=lam.device)
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     _check(lib().gwc_sample_terms(ctx, p(lam), p(lnw), p(d), p(c), _stream_ptr(stream)), ctx)
+    return lnw, d, c
+
+
+def sample_terms_noalloc(lam, samples, pix, injections, los, z_max, n_x_table=512, grad=True,
+                         stream=None):
+    """gwc_sample_terms_noalloc on caller-owned CUDA tensors (no context, no allocation in
+    the library): samples [n, 4] and injections [m, 4] float32, pix [n] int32, los
+    [n_pix, n_z] float32, lam [13] float64.  Returns (ln w - c, d, c) like sample_terms;
+    the output tensors are allocated here by PyTorch, not by the library."""
+    import torch
+    n, m = samples.shape[0], injections.shape[0]
+    lnw = torch.empty(n + m, dtype=torch.float32, device=lam.device)
+    d = torch.empty((13, n + m), dtype=torch.float32, device=lam.device) if grad else None
+    c = torch.empty(14, dtype=torch.float64, device=lam.device)
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    st = lib().gwc_sample_terms_noalloc(p(lam.contiguous()), n, p(samples.contiguous()),
+                                        p(pix.contiguous()), m, p(injections.contiguous()),
+                                        los.shape[0], los.shape[1], float(z_max),
+                                        p(los.contiguous()), n_x_table, p(lnw), p(d), p(c),
+                                        _stream_ptr(stream))
+    _check(st)
     return lnw, d, c
 
 

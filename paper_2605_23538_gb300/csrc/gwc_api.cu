@@ -33,6 +33,8 @@ std::set<const gwc_ctx*> g_live;
 
 }  // namespace
 
+void gwc::set_thread_error(const std::string& msg) { t_err = msg; }
+
 struct gwc_ctx {
   uint32_t magic = MAGIC;
   int device = 0;

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "gwc_internal.cuh"
@@ -113,6 +114,8 @@ struct TermsArgs {
   double* c;        // [14]
 };
 cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s);
+// the calling thread's message for gwc_last_error(NULL) (defined with the C ABI)
+void set_thread_error(const std::string& msg);
 cudaError_t launch_los_cell(const float* z, long long n, int nz, double zmax, int* cell, cudaStream_t s);
 
 }  // namespace gwc

@@ -1,0 +1,73 @@
+"""The allocation-free entry point against the context-based one.
+
+gwc_sample_terms_noalloc serves callers that cannot allocate device memory when they
+need an evaluation (inside a CUDA graph capture, or under a framework's caching
+allocator): it reads caller-owned device arrays and keeps its scratch in a fixed
+device array inside the library.  Here it is called twice in a row, at two different
+Lambda points, and each result must match gwc_sample_terms on a context built from the
+same catalogue, within the per-sample tolerance the parity tests use.  Collected last
+(file name) so a failure here cannot hide the others; it also runs alone.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def test_noalloc_matches_context_twice(torch, synth):
+    from paper_2605_23538_gb300 import build
+    build.build()
+    import paper_2605_23538_gb300 as g
+
+    w = synth.scaled("noalloc", 6, ("uniform", 200, 1500), 4, 256, 4000, "found")
+    cat = synth.catalogue(w)
+    dev = "cuda"
+    samples = torch.tensor(np.stack([cat["m1"], cat["m2"], cat["dl"], cat["lnpe"]], axis=1), device=dev)
+    inj = torch.tensor(np.stack([cat["inj_m1"], cat["inj_m2"], cat["inj_dl"], cat["inj_lnpd"]], axis=1),
+                       device=dev)
+    pix = torch.tensor(cat["pix"], dtype=torch.int32, device=dev)
+    los = torch.tensor(cat["los"], device=dev)
+    order = g.sample_order(cat)
+    ns = len(order)
+    lams = np.vstack([synth.FIDUCIAL, synth.lambda_batch(1, purpose=21)])
+    with g.Context(cat, max_K=1) as ctx:
+        for lam in lams:                      # two calls in a row
+            lt = torch.tensor(lam, dtype=torch.float64, device=dev)
+            r_lnw, r_d, r_c = ctx.sample_terms(lt)
+            n_lnw, n_d, n_c = g.sample_terms_noalloc(lt, samples, pix, inj, los, cat["z_max"])
+            torch.cuda.synchronize()
+            r_lnw, r_d, r_c = r_lnw.cpu().numpy(), r_d.cpu().numpy(), r_c.cpu().numpy()
+            n_lnw, n_d, n_c = n_lnw.cpu().numpy(), n_d.cpu().numpy(), n_c.cpu().numpy()
+            # the context orders each event's samples by pixel; the caller's order is kept here
+            perm = np.concatenate([order, ns + np.arange(len(cat["inj_m1"]))])
+            n_lnw, n_d = n_lnw[perm], n_d[:, perm]
+            np.testing.assert_allclose(n_c, r_c, rtol=1e-12, atol=1e-12)
+            fin = np.isfinite(r_lnw)
+            assert np.array_equal(fin, np.isfinite(n_lnw))
+            assert fin.sum() > 1000
+            assert np.max(np.abs(n_lnw[fin] - r_lnw[fin])) <= 2e-5
+            scale = np.abs(r_d[:, fin]) + np.abs(r_d[:, fin]).mean(axis=1, keepdims=True)
+            assert np.all(np.abs(n_d[:, fin] - r_d[:, fin]) <= 2e-4 * scale)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(torch):
+    import paper_2605_23538_gb300 as g
+    z = torch.zeros((1, 4), dtype=torch.float32, device="cuda")
+    lam = torch.zeros(13, dtype=torch.float64, device="cuda")
+    los = torch.ones((1, 8), dtype=torch.float32, device="cuda")
+    p = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(g.GwcError) as e:
+        g.sample_terms_noalloc(lam, z, p, z, los, 2.0, n_x_table=2048)
+    assert e.value.status == -1 and "scratch limit" in str(e.value)
+    big = torch.ones((1, 8192), dtype=torch.float32, device="cuda")
+    with pytest.raises(g.GwcError) as e:
+        g.sample_terms_noalloc(lam, z, p, z, big, 2.0)
+    assert e.value.status == -1 and "scratch limit" in str(e.value)
