@@ -31,24 +31,27 @@ constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the pr
 
 enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
 
-// FP32 constants of one Lambda point for the sample kernels (48 floats = 12 float4).
+// FP32 constants of one Lambda point for the sample kernels (52 floats = 13 float4).
+// Fields ending in 2 are in log2 units (the value path works in log2 so that the
+// special-function unit's ex2/lg2 apply directly).
 struct __align__(16) LamF {
-  float H0c, xmax, inv_dx, live;       // x = dL * H0/c; table spacing; 0 = skip this Lambda
-  float H0c_lo, inv_dx_lo, inv_dm, lam_edge;   // low parts of H0/c and (nx-1)/xmax; 1/delta_m;
-                                               // 1 when lambda_peak is 0 or 1 (see Acc)
-  float om, zstep, inv_zstep, lp;      // Om; z_max/(n_z-1); its inverse; ln(1+z_p)
-  float alpha, beta, mmin, mmax;
-  float dm, mw, mu, inv_sig;           // mw = m_min + delta_m
-  float la, lb, Cw, mw1b;              // ln(1-lam) - ln Z_P; ln lam - ln(sig sqrt(2 pi)) - ln Z_G;
-                                       // C(mw) = int_{m_min}^{mw} m^beta S; mw^(1+beta)
-  float eps_b, inv_eps_b, lmw, gam;    // 1+beta; 1/(1+beta) (0 when |1+beta| < 1e-30); ln mw
-  float gpk, inv_wh, invH0, inv1zp;    // gamma+kappa; N_w/delta_m; 1/H0; 1/(1+z_p)
-  float dZPa, dZPmin, dZPmax, dZGmu;   // d ln Z_P / d(alpha, m_min, m_max); d ln Z_G / d mu
-  float dZGsig, dZGmin, dZGmax, Cwb;   // d ln Z_G / d(sig, m_min, m_max); int m^beta ln m S
-  float Jw, Kw, la0, lb0;              // int m^(beta-1) S; int m^beta dS/d delta_m; la, lb without ln(1-lam), ln lam
-  float lam, inv_lam, inv_1ml, pad;    // lambda_peak, 1/lambda, 1/(1-lambda)
+  float H0c, H0c_lo, inv_dx, inv_dx_lo;  // H0/c and (nx-1)/xmax, each as a hi + lo pair
+  float xmax, live, zstep, inv_zstep;     // live = 0: skip this Lambda; z_max/(n_z-1) and inverse
+  float om, lp2, gam, gam_m3;             // log2(1+z_p); gamma; gamma - 3
+  float gpk, alpha, beta, eps_b;          // gamma+kappa; 1+beta
+  float mmin, mmax, dm, mw;               // mw = m_min + delta_m
+  float mu, inv_sig, la2, lb2;            // log2 of (1-lam)/Z_P and of lam/(sig sqrt(2 pi) Z_G)
+  float C0, inv_eps_b, Cw, mw1b;          // C above the window = C0 + m1^(1+beta)/(1+beta);
+                                          // C(mw) = int_{m_min}^{mw} m^beta S; mw^(1+beta)
+  float lmw, inv_wh, inv_dm, beta_small;  // ln mw; N_w/delta_m; 1/delta_m; 1 if |1+beta| < 1e-3
+  float invH0, inv1zp, lam_edge, lam;     // lam_edge = 1 when lambda_peak is 0 or 1
+  float dZPa, dZPmin, dZPmax, dZGmu;      // d ln Z_P / d(alpha, m_min, m_max); d ln Z_G / d mu
+  float dZGsig, dZGmin, dZGmax, Cwb;      // d ln Z_G / d(sig, m_min, m_max); int m^beta ln m S
+  float Cmin, Kw, la0_2, lb0_2;           // dC/dm_min above the window; int m^beta dS/d delta_m;
+                                          // log2 of 1/Z_P and of 1/(sig sqrt(2 pi) Z_G)
+  float inv_lam, inv_1ml, pad0, pad1;
 };
-static_assert(sizeof(LamF) == 48 * 4, "LamF layout");
+static_assert(sizeof(LamF) == 52 * 4, "LamF layout");
 
 // FP64 constants of one Lambda point for the merge: ln w = (per-sample term) + c.
 struct LamD {
@@ -74,57 +77,71 @@ struct Item {          // one work item: a contiguous run of samples of one even
 };
 
 // ---------------------------------------------------------------- device helpers
+constexpr float LN2F = 0.69314718055994530942f;
+constexpr float LOG2EF = 1.44269504088896340736f;
+constexpr float HALF_LOG2EF = 0.72134752044448170368f;
+
+// the special-function unit's approximations (PTX ex2/lg2/rcp .approx): relative errors
+// of a few 2^-23, which keeps every term of ln w at FP32 rounding level
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float hermite_val(float2 a, float2 b, float t) {
-  // a = {f0, f0' h}, b = {f1, f1' h}
-  const float t2 = t * t, t3 = t2 * t;
-  const float h00 = 2.f * t3 - 3.f * t2 + 1.f, h10 = t3 - 2.f * t2 + t;
-  const float h01 = -2.f * t3 + 3.f * t2, h11 = t3 - t2;
-  return h00 * a.x + h10 * a.y + h01 * b.x + h11 * b.y;
+  // a = {f0, f0' h}, b = {f1, f1' h}: f0 + t (f0' h + t (c2 + t c3))
+  const float d = b.x - a.x;
+  const float c2 = fmaf(3.f, d, -fmaf(2.f, a.y, b.y));
+  const float c3 = fmaf(-2.f, d, a.y + b.y);
+  return fmaf(t, fmaf(t, fmaf(t, c3, c2), a.y), a.x);
 }
 // derivative with respect to t (multiply by 1/h for d/dm)
 __device__ __forceinline__ float hermite_dt(float2 a, float2 b, float t) {
-  const float t2 = t * t;
-  const float d00 = 6.f * t2 - 6.f * t, d10 = 3.f * t2 - 4.f * t + 1.f;
-  const float d01 = -6.f * t2 + 6.f * t, d11 = 3.f * t2 - 2.f * t;
-  return d00 * a.x + d10 * a.y + d01 * b.x + d11 * b.y;
+  const float d = b.x - a.x;
+  const float c2 = fmaf(3.f, d, -fmaf(2.f, a.y, b.y));
+  const float c3 = fmaf(-2.f, d, a.y + b.y);
+  return fmaf(t, fmaf(3.f * t, c3, 2.f * c2), a.y);
 }
 
 struct SampleIn {
-  float m1, m2, dl, lpe, lm1, lm2;   // detector-frame masses, distance, ln pi, ln m1, ln m2
+  float m1, m2, dl, lpe, lm1, lm2;   // detector-frame masses, distance, ln pi (natural),
+                                     // log2 m1, log2 m2
 };
-
-// Smoothing window: for m' = m - m_min in (0, delta_m), f = dm/m' + dm/(m' - dm),
-// ln S = -softplus(f).  Returns ln S and (GRAD) sf = sigmoid(f) = 1 - S, mp.
-__device__ __forceinline__ float ln_smooth(float m, float mmin, float dm, float& sf, float& mp) {
-  mp = m - mmin;
-  const float f = dm / mp + dm / (mp - dm);
-  const float e = expf(-fabsf(f));
-  const float inv = __frcp_rn(1.f + e);
-  sf = f >= 0.f ? inv : e * inv;
-  return -(fmaxf(f, 0.f) + log1pf(e));
-}
 
 __device__ __forceinline__ float ld_row(const float* __restrict__ r, int j) { return __ldg(r + j); }
 __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int j) {
   return __bfloat162float(r[j]);
 }
 
-// ln w (without the per-Lambda constant c) and, for GRAD, d ln w / d Lambda.
-// row: the sample's LOS row (or the pixel-averaged row for injections).
-// pos/pc3/jtab/win: this Lambda's tables (global memory, read through L1).
+// lw2 = log2 of w without the per-Lambda constant c (ln w = lw2 ln 2 + c) and, for GRAD,
+// g = d ln w / d Lambda (natural units, without dc).
+//   ln w = ln p_LOS(z) + (gamma - 3) ln u - softplus(r) + ln p_mix(m1) + beta ln m2 + ln S(m2)
+//          - ln C(m1) - ln D'(z) - ln pi,   u = 1 + z, r = (gamma + kappa) ln(u / (1 + z_p))
+// with every log1p term folded into one logarithm of a product.  row: the sample's LOS
+// row (or the pixel-averaged row for injections); pos/pc3/jtab/win: this Lambda's tables.
 // When L.lam_edge is set (lambda_peak = 0 or 1) the lambda derivative
 // e^(ln G - mix) - e^(ln P - mix) can exceed the float range for samples far from one
 // mixture component, although its product with the sample's weight does not; g[P_LAM]
-// then holds ln P - mix and lam_lb holds ln G - mix, and the accumulator forms the
-// weighted difference in the exponent (lam_edge_term).
-// Returns false where w = 0.
+// then holds log2 P - mix2 and lam_lb holds log2 G - mix2, and the accumulator forms the
+// weighted difference in the exponent (lam_edge_term).  Returns false where w = 0.
 template <bool GRAD, typename RowT>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
                                            const float4* __restrict__ pos,
                                            const float* __restrict__ pc3, int nx,
                                            const float2* __restrict__ jtab,
-                                           const float2* __restrict__ win, float& lw, float* g,
+                                           const float2* __restrict__ win, float& lw2, float* g,
                                            float& lam_lb) {
   // x = d_L H0 / c and the table coordinate x / dx carried with their rounding errors
   // (exact products by FMA), so the LOS-grid position keeps ~1e-7 of a cell
@@ -146,45 +163,48 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   if (j < 0) { tl += (float)j; j = 0; }
   const float z = ((float)j + tl) * L.zstep;
   const float u = 1.f + z;
-  const float ru = __frcp_rn(u);
-  const float lu = logf(u);
+  const float ru = rcp(u);
+  const float lu2 = lg2(u);
 
-  // --- LOS prior of the sample's pixel, linear in z
+  // --- LOS prior of the sample's pixel, linear in z (convex form: no cancellation)
   const float p0 = ld_row(row, j), p1 = ld_row(row, j + 1);
-  const float dp = p1 - p0;
-  const float plos = fmaf(tl, p1, (1.f - tl) * p0);   // convex form: no cancellation in tails
+  const float plos = fmaf(tl, p1, (1.f - tl) * p0);
   if (!(plos > 0.f)) return false;
 
   // --- source-frame masses
   const float m1s = s.m1 * ru, m2s = s.m2 * ru;
   if (m1s > L.mmax || m2s < L.mmin) return false;
-  const float lm1s = s.lm1 - lu, lm2s = s.lm2 - lu;
+  const float lm1s2 = s.lm1 - lu2, lm2s2 = s.lm2 - lu2;
 
-  // p(m1): log of (1-lam) m^-alpha/Z_P + lam N(m; mu, sig)/Z_G
-  const float a = L.la - L.alpha * lm1s;
+  // p(m1): (1-lam) m^-alpha / Z_P + lam N(m; mu, sig) / Z_G as max + log2(1 + e^-|a-b|)
+  const float a2 = fmaf(-L.alpha, lm1s2, L.la2);
   const float zz = (m1s - L.mu) * L.inv_sig;
-  const float b = fmaf(-0.5f * zz, zz, L.lb);
-  const float mx = fmaxf(a, b), mn = fminf(a, b);
-  const float eab = expf(mn - mx);
+  const float b2 = fmaf(-HALF_LOG2EF * zz, zz, L.lb2);
+  const float mx = fmaxf(a2, b2);
+  const float eab = ex2(fminf(a2, b2) - mx);
+  float lin = mx;     // log2 terms outside the product
+  float den;          // denominators of the product
 
-  // p(m2 | m1) = m2^beta S(m2) / C(m1)
-  float lnS2 = 0.f, sf2 = 0.f, mp2 = 0.f;
+  // smoothing of m2: ln S = -softplus(f), f = dm/m' + dm/(m' - dm)
   const bool win2 = m2s < L.mw;
+  float mp2 = 0.f, i1 = 0.f, i2 = 0.f, f2 = 0.f, ef2 = 0.f;
   if (win2) {
-    lnS2 = ln_smooth(m2s, L.mmin, L.dm, sf2, mp2);
+    mp2 = m2s - L.mmin;
     if (!(mp2 > 0.f)) return false;
+    i1 = rcp(mp2);
+    i2 = rcp(mp2 - L.dm);
+    f2 = L.dm * (i1 + i2) * LOG2EF;
+    ef2 = ex2(-fabsf(f2));
+    lin -= fmaxf(f2, 0.f);
   }
+
+  // normaliser of p(m2 | m1): in the window C(m1) = m1^beta S(m1) Q_C m'^2 / dm, whose
+  // S(m1) cancels against p(m1); above it C = C0 + m1^(1+beta) / (1+beta)
   const bool win1 = m1s < L.mw;
-  float Cx, Cprod, lmass;   // the normaliser (C, or R_C in the window), its share of the
-                            // one-log product below, and the remaining log-mass terms
-  float y = 0.f, Q = 0.f, A = 0.f, dlm = 0.f;
-  float2 wa = make_float2(0.f, 0.f), wb = wa;
-  float wt = 0.f;
+  float Cx, mp1 = 0.f, Qc = 0.f, A = 0.f, dlm = 0.f, wt = 0.f;
   int wk = 0;
-  float mp1 = 0.f, Qc = 0.f;
+  float2 wa = make_float2(0.f, 0.f), wb = wa;
   if (win1) {
-    // in the window C(m1) = m1^beta S(m1) R_C(m1) with R_C = Q_C m'^2 / delta_m;
-    // S(m1) cancels against p(m1)
     mp1 = m1s - L.mmin;
     const float ws = mp1 * L.inv_wh;
     wk = min((int)ws, NW_WIN - 1);
@@ -192,98 +212,106 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     wa = __ldg(win + wk);
     wb = __ldg(win + wk + 1);
     Qc = hermite_val(wa, wb, wt);
-    Cx = Qc * (mp1 * mp1) * L.inv_dm;   // R_C >= ~1e-14 (m' >= one float ulp of m_min)
-    Cprod = 1.f;                         // R_C can be small near m_min: keep its log separate
-    lmass = L.beta * (lm2s - lm1s) - logf(Cx);
+    Cx = Qc * (mp1 * mp1) * L.inv_dm;
+    lin = fmaf(L.beta, lm2s2 - lm1s2, lin);
   } else {
-    // above it C(m1) = C(mw) + mw^(1+beta) (exp((1+beta)(ln m1 - ln mw)) - 1) / (1+beta)
-    dlm = lm1s - L.lmw;
-    y = L.eps_b * dlm;
-    Q = fabsf(y) < 1e-3f ? dlm * fmaf(y, fmaf(y, 1.f / 6.f, 0.5f), 1.f) : expm1f(y) * L.inv_eps_b;
-    Cx = fmaf(L.mw1b, Q, L.Cw);
-    Cprod = Cx;
-    lmass = L.beta * lm2s;
+    if (L.beta_small == 0.f) {
+      A = ex2(L.eps_b * lm1s2);                       // m1s^(1+beta)
+      Cx = fmaf(A, L.inv_eps_b, L.C0);
+    } else {                                          // |1+beta| < 1e-3: series in y
+      dlm = fmaf(lm1s2, LN2F, -L.lmw);
+      const float y = L.eps_b * dlm;
+      const float phi1 = fmaf(y, fmaf(y, fmaf(y, 1.f / 24.f, 1.f / 6.f), 0.5f), 1.f);
+      A = L.mw1b * fmaf(y, phi1, 1.f);
+      Cx = fmaf(L.mw1b * dlm, phi1, L.Cw);
+    }
+    lin = fmaf(L.beta, lm2s2, lin);
   }
+  den = win2 ? Cx * (1.f + ef2) : Cx;
 
-  // rate psi(z) / (1+z) and the (1+z)^-2 mass Jacobian: (gam - 3) ln u - softplus(r)
-  const float r = L.gpk * (lu - L.lp);
-  const float er = expf(-fabsf(r));
+  // rate psi(z)/(1+z) and the (1+z)^-2 mass Jacobian: (gam - 3) log2 u - softplus(r)/ln 2
+  const float r2 = L.gpk * (lu2 - L.lp2);
+  const float er = ex2(-fabsf(r2));
+  lin -= fmaxf(r2, 0.f);
 
   // d d_L / dz = (c/H0) D'(z), D' = I(z) + u/E with I(z) = x/u on the root
-  const float u3m1 = z * fmaf(z, z + 3.f, 3.f);   // (1+z)^3 - 1 without cancellation
-  const float E2 = fmaf(L.om, u3m1, 1.f);
-  const float rE = rsqrtf(E2);
+  const float u3m1 = z * fmaf(z, z + 3.f, 3.f);        // (1+z)^3 - 1 without cancellation
+  const float rE = rsqrtf(fmaf(L.om, u3m1, 1.f));
   const float Dp = fmaf(x, ru, u * rE);
+  den *= Dp * (1.f + er);
 
-  // one logarithm for the product of the remaining factors
-  const float prod = plos * (1.f + eab) / (Dp * Cprod * (1.f + er));
-  lw = (L.gam - 3.f) * lu - fmaxf(r, 0.f) + mx + lnS2 + lmass + logf(prod) - s.lpe;
-  if (!(lw > -INFINITY) || lw != lw) return false;
+  lw2 = fmaf(L.gam_m3, lu2, lin) + lg2(plos * (1.f + eab) * rcp(den));
+  lw2 = fmaf(-s.lpe, LOG2EF, lw2);
+  if (!(lw2 > -INFINITY)) return false;
 
   if (GRAD) {
-    const float inv1e = __frcp_rn(1.f + eab);
-    const float pa = a >= b ? inv1e : eab * inv1e;   // mixture responsibilities
+    const float lu = lu2 * LN2F, lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
+    const float inv1e = rcp(1.f + eab);
+    const float pa = a2 >= b2 ? inv1e : eab * inv1e;   // mixture responsibilities
     const float pb = 1.f - pa;
-    const float invr = __frcp_rn(1.f + er);
-    const float sr = r >= 0.f ? invr : er * invr;   // sigmoid(r)
-    const float invDp = __frcp_rn(Dp);
+    const float invr = rcp(1.f + er);
+    const float sr = r2 >= 0.f ? invr : er * invr;     // sigmoid(r)
+    const float invDp = rcp(Dp);
     const float rE3 = rE * rE * rE;
 
     // smoothing derivatives of m2 (and of m1 in the window)
-    float dS2_dm = 0.f, dS2_dmin = 0.f, dS2_ddm = 0.f;
+    float dS2_dm = 0.f, dS2_ddm = 0.f;
     if (win2) {
-      const float i1 = __frcp_rn(mp2), i2 = __frcp_rn(mp2 - L.dm);
-      const float q = L.dm * (i1 * i1 + i2 * i2);
-      dS2_dm = sf2 * q;
-      dS2_dmin = -sf2 * q;
-      dS2_ddm = -sf2 * (i1 + mp2 * i2 * i2);
+      const float inv = rcp(1.f + ef2);
+      const float sf2 = f2 >= 0.f ? inv : ef2 * inv;
+      dS2_dm = sf2 * L.dm * fmaf(i1, i1, i2 * i2);      // d ln S / dm = -d ln S / d m_min
+      dS2_ddm = -sf2 * fmaf(mp2 * i2, i2, i1);
     }
-    float dS1_dmin = 0.f, dS1_ddm = 0.f;
-    float dlnC_db, dlnC_dmin, dlnC_ddm, Gc;
+    float dS1_dmin = 0.f, dS1_ddm = 0.f, dlnC_db, dlnC_dmin, dlnC_ddm, Gc;
     if (win1) {
-      float sf1, mp1;
-      ln_smooth(m1s, L.mmin, L.dm, sf1, mp1);
-      const float i1 = __frcp_rn(mp1), i2 = __frcp_rn(mp1 - L.dm);
-      dS1_dmin = -sf1 * L.dm * (i1 * i1 + i2 * i2);
-      dS1_ddm = -sf1 * (i1 + mp1 * i2 * i2);
+      const float j1 = rcp(mp1), j2 = rcp(mp1 - L.dm);
+      const float f1 = L.dm * (j1 + j2) * LOG2EF;
+      const float ef1 = ex2(-fabsf(f1));
+      const float inv = rcp(1.f + ef1);
+      const float sf1 = f1 >= 0.f ? inv : ef1 * inv;
+      dS1_dmin = -sf1 * L.dm * fmaf(j1, j1, j2 * j2);
+      dS1_ddm = -sf1 * fmaf(mp1 * j2, j2, j1);
       const float Qb = hermite_val(__ldg(win + (NW_WIN + 1) + wk), __ldg(win + (NW_WIN + 1) + wk + 1), wt);
       const float Qj = hermite_val(__ldg(win + 2 * (NW_WIN + 1) + wk), __ldg(win + 2 * (NW_WIN + 1) + wk + 1), wt);
       const float Qk = hermite_val(__ldg(win + 3 * (NW_WIN + 1) + wk), __ldg(win + 3 * (NW_WIN + 1) + wk + 1), wt);
-      const float iQ = __frcp_rn(Qc), im = __frcp_rn(mp1);
-      dlnC_db = Qb;                                     // R_beta / R_C
-      dlnC_dmin = fmaf(L.beta, Qj, -__frcp_rn(Cx));     // (-1 + beta R_J) / R_C
-      dlnC_ddm = Qk * iQ * im;                          // R_K / R_C
+      const float iQ = rcp(Qc);
+      dlnC_db = Qb;                                      // R_beta / R_C
+      dlnC_dmin = fmaf(L.beta, Qj, -rcp(Cx));            // (-1 + beta R_J) / R_C
+      dlnC_ddm = Qk * iQ * j1;                           // R_K / R_C
       // -ln R_C(m1s) through m1s = m1/u:  m1s (Q_C'/Q_C + 2/m') / u
-      Gc = m1s * fmaf(hermite_dt(wa, wb, wt) * L.inv_wh, iQ, 2.f * im);
+      Gc = m1s * fmaf(hermite_dt(wa, wb, wt) * L.inv_wh, iQ, 2.f * j1);
     } else {
-      const float iC = __frcp_rn(Cx);
-      A = L.mw1b * (Q * L.eps_b + 1.f);   // m1s^(1+beta)
-      float phi2;
-      if (fabsf(y) < 1e-2f) phi2 = fmaf(y, fmaf(y, 0.125f, 1.f / 3.f), 0.5f);
-      else phi2 = (y * expf(y) - expm1f(y)) / (y * y);
-      dlnC_db = (L.Cwb + L.mw1b * fmaf(L.lmw, Q, dlm * dlm * phi2)) * iC;
-      dlnC_dmin = (L.beta * L.Jw - L.mw1b / L.mw) * iC;
+      const float iC = rcp(Cx);
+      float dC_db;
+      if (L.beta_small == 0.f) {
+        // dC/dbeta = C_beta(mw) + (A ln m1s - mw^(1+beta) ln mw - (C - C(mw))) / (1+beta)
+        dC_db = fmaf(fmaf(A, lm1s, -fmaf(L.mw1b, L.lmw, Cx - L.Cw)), L.inv_eps_b, L.Cwb);
+      } else {
+        const float y = L.eps_b * dlm;
+        const float phi1 = fmaf(y, fmaf(y, fmaf(y, 1.f / 24.f, 1.f / 6.f), 0.5f), 1.f);
+        const float phi1p = fmaf(y, fmaf(y, 0.125f, 1.f / 3.f), 0.5f);
+        dC_db = fmaf(L.mw1b * dlm, fmaf(L.lmw, phi1, dlm * phi1p), L.Cwb);
+      }
+      dlnC_db = dC_db * iC;
+      dlnC_dmin = L.Cmin * iC;
       dlnC_ddm = L.Kw * iC;
-      Gc = (A * iC - L.beta);   // -ln C(m1s) and beta ln m2s through u (times 1/u below)
+      Gc = fmaf(A, iC, -L.beta);   // -ln C(m1s) and beta ln m2s through u (times 1/u below)
     }
     // total z-derivative of ln w at fixed detector-frame data
-    float Gz = dp * L.inv_zstep / plos;
-    Gz += (L.gam - L.gpk * sr - 3.f) * ru;
-    Gz += fmaf(pa, L.alpha, pb * zz * m1s * L.inv_sig) * ru;
-    Gz -= m2s * dS2_dm * ru;
-    Gz += Gc * ru;
-    const float D2 = 2.f * rE - 1.5f * L.om * (u3m1 + 1.f) * rE3;
-    Gz -= D2 * invDp;
+    float Gz = (p1 - p0) * L.inv_zstep * rcp(plos);
+    const float inner = L.gam - 3.f - L.gpk * sr + fmaf(pa, L.alpha, pb * zz * m1s * L.inv_sig) -
+                        m2s * dS2_dm + Gc;
+    Gz = fmaf(inner, ru, Gz);
+    const float D2 = fmaf(-1.5f * L.om * (u3m1 + 1.f), rE3, 2.f * rE);
+    Gz = fmaf(-D2, invDp, Gz);
 
     // z depends on H0 and Om through x and the inverted distance relation
     const float J = hermite_val(__ldg(jtab + n), __ldg(jtab + n + 1), t);
     g[P_H0] = Gz * x * L.invH0 * invDp;
-    const float dz_dom = -u * J * invDp;
-    const float dDp_dom = J - 0.5f * u * u3m1 * rE3;
-    g[P_OM] = fmaf(Gz, dz_dom, -dDp_dom * invDp);
+    g[P_OM] = fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp);
     g[P_ALPHA] = pa * (-lm1s - L.dZPa);
     g[P_BETA] = lm2s - dlnC_db;
-    g[P_MMIN] = -pa * L.dZPmin - pb * L.dZGmin + dS1_dmin + dS2_dmin - dlnC_dmin;
+    g[P_MMIN] = -pa * L.dZPmin - pb * L.dZGmin + dS1_dmin - dS2_dm - dlnC_dmin;
     g[P_MMAX] = -pa * L.dZPmax - pb * L.dZGmax;
     g[P_DM] = dS1_ddm + dS2_ddm - dlnC_ddm;
     g[P_MU] = pb * (zz * L.inv_sig - L.dZGmu);
@@ -291,24 +319,24 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     if (L.lam_edge == 0.f) {
       g[P_LAM] = pb * L.inv_lam - pa * L.inv_1ml;
     } else {
-      const float mix = mx + log1pf(eab);
-      g[P_LAM] = L.la0 - L.alpha * lm1s - mix;         // ln P - mix
-      lam_lb = fmaf(-0.5f * zz, zz, L.lb0) - mix;      // ln G - mix
+      const float mix2 = mx + lg2(1.f + eab);
+      g[P_LAM] = fmaf(-L.alpha, lm1s2, L.la0_2) - mix2;           // log2 P - mix2
+      lam_lb = fmaf(-HALF_LOG2EF * zz, zz, L.lb0_2) - mix2;      // log2 G - mix2
     }
-    const float dl = lu - L.lp;
-    g[P_GAM] = lu - sr * dl;
-    g[P_KAP] = -sr * dl;
+    const float dlu = (lu2 - L.lp2) * LN2F;
+    g[P_GAM] = lu - sr * dlu;
+    g[P_KAP] = -sr * dlu;
     g[P_ZP] = sr * L.gpk * L.inv1zp;
   }
   return true;
 }
 
-// e^d (e^lb - e^la) without forming either exponential on its own
+// 2^d (2^lb - 2^la) without forming either power on its own
 __device__ __forceinline__ float lam_edge_term(float d, float la, float lb) {
-  return expf(d + lb) - expf(d + la);
+  return ex2(d + lb) - ex2(d + la);
 }
 
-// Online (max, sum e^(l-max), sum e^(2(l-max)), sum e^(l-max) dl) accumulator.
+// Online (max, sum 2^(l-max), sum 2^(2(l-max)), sum 2^(l-max) dl) accumulator, l in log2 units.
 template <bool GRAD, bool KAHAN>
 struct Acc {
   float m = -INFINITY, s1 = 0.f, s2 = 0.f, c1 = 0.f, c2 = 0.f;
@@ -320,7 +348,7 @@ struct Acc {
   __device__ __forceinline__ void add(float lw, const float* dg, bool lam_edge = false,
                                       float lam_lb = 0.f) {
     if (lw > m) {
-      const float sc = expf(m - lw);   // 0 on the first sample
+      const float sc = ex2(m - lw);   // 0 on the first sample
       s1 = fmaf(s1, sc, 1.f);
       s2 = fmaf(s2, sc * sc, 1.f);
       c1 *= sc;
@@ -332,7 +360,7 @@ struct Acc {
       }
       m = lw;
     } else {
-      const float tt = expf(lw - m);
+      const float tt = ex2(lw - m);
       if (KAHAN) {
         float y1 = tt - c1, t1 = s1 + y1;
         c1 = (t1 - s1) - y1;
@@ -355,7 +383,7 @@ struct Acc {
   __device__ __forceinline__ void merge(float om, float os1, float os2, const float* og) {
     const float M = fmaxf(m, om);
     if (M == -INFINITY) return;
-    const float sa = expf(m - M), sb = expf(om - M);
+    const float sa = ex2(m - M), sb = ex2(om - M);
     s1 = s1 * sa + os1 * sb;
     s2 = s2 * sa * sa + os2 * sb * sb;
     if (GRAD) {

@@ -383,39 +383,47 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const double Jw = dm > 0.0 ? scum[2][NW_WIN] : 0.0;
     const double Kw = dm > 0.0 ? scum[3][NW_WIN] : 0.0;
     const double mw = mmin + dm, eps = 1.0 + beta;
+    const double LOG2E = 1.44269504088896340736;
     LamF f;
+    memset(&f, 0, sizeof(f));
     f.H0c = (float)(H0 / C_KMS);
-    f.xmax = (float)xmax;
-    f.inv_dx = (float)(1.0 / dx);
-    f.live = 1.f;
     f.H0c_lo = (float)(H0 / C_KMS - (double)f.H0c);
+    f.inv_dx = (float)(1.0 / dx);
     f.inv_dx_lo = (float)(1.0 / dx - (double)f.inv_dx);
-    f.inv_dm = dm > 0.0 ? (float)(1.0 / dm) : 0.f;
-    f.lam_edge = (lam > 0.0 && lam < 1.0) ? 0.f : 1.f;
-    f.om = (float)om;
+    f.xmax = (float)xmax;
+    f.live = 1.f;
     f.zstep = (float)(zmax / (nz - 1));
     f.inv_zstep = (float)pscale;
-    f.lp = (float)lp;
+    f.om = (float)om;
+    f.lp2 = (float)(lp * LOG2E);
+    f.gam = (float)gam;
+    f.gam_m3 = (float)(gam - 3.0);
+    f.gpk = (float)gpk;
     f.alpha = (float)alpha;
     f.beta = (float)beta;
+    f.eps_b = (float)eps;
     f.mmin = (float)mmin;
     f.mmax = (float)mmax;
     f.dm = (float)dm;
     f.mw = (float)mw;
     f.mu = (float)mu;
     f.inv_sig = (float)(1.0 / sig);
-    f.la = lam < 1.0 ? (float)(log1p(-lam) - lnZP) : -INFINITY;
-    f.lb = lam > 0.0 ? (float)(log(lam) - lnsig2pi - lnZG) : -INFINITY;
+    f.la2 = lam < 1.0 ? (float)((log1p(-lam) - lnZP) * LOG2E) : -INFINITY;
+    f.lb2 = lam > 0.0 ? (float)((log(lam) - lnsig2pi - lnZG) * LOG2E) : -INFINITY;
+    const bool small = fabs(eps) < 1e-3;
+    const double mw1b = exp(eps * log(mw));
+    f.beta_small = small ? 1.f : 0.f;
+    f.inv_eps_b = small ? 0.f : (float)(1.0 / eps);
+    f.C0 = small ? 0.f : (float)(Cw - mw1b / eps);
     f.Cw = (float)Cw;
-    f.mw1b = (float)exp(eps * log(mw));
-    f.eps_b = (float)eps;
-    f.inv_eps_b = fabs(eps) > 1e-30 ? (float)(1.0 / eps) : 0.f;
+    f.mw1b = (float)mw1b;
     f.lmw = (float)log(mw);
-    f.gam = (float)gam;
-    f.gpk = (float)gpk;
     f.inv_wh = dm > 0.0 ? (float)(NW_WIN / dm) : 0.f;
+    f.inv_dm = dm > 0.0 ? (float)(1.0 / dm) : 0.f;
     f.invH0 = (float)(1.0 / H0);
     f.inv1zp = (float)(1.0 / (1.0 + zp));
+    f.lam_edge = (lam > 0.0 && lam < 1.0) ? 0.f : 1.f;
+    f.lam = (float)lam;
     f.dZPa = (float)dZPa;
     f.dZPmin = (float)dZPmin;
     f.dZPmax = (float)dZPmax;
@@ -424,14 +432,12 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.dZGmin = (float)dZGmin;
     f.dZGmax = (float)dZGmax;
     f.Cwb = (float)Cwb;
-    f.Jw = (float)Jw;
+    f.Cmin = (float)(beta * Jw - mw1b / mw);
     f.Kw = (float)Kw;
-    f.la0 = (float)(-lnZP);
-    f.lb0 = (float)(-lnsig2pi - lnZG);
-    f.lam = (float)lam;
+    f.la0_2 = (float)(-lnZP * LOG2E);
+    f.lb0_2 = (float)((-lnsig2pi - lnZG) * LOG2E);
     f.inv_lam = lam > 0.0 ? (float)(1.0 / lam) : 0.f;
     f.inv_1ml = lam < 1.0 ? (float)(1.0 / (1.0 - lam)) : 0.f;
-    f.pad = 0.f;
     *lf = f;
     // c = -ln N'_z - ln Z_m1 + ln(H0 / c)
     ld->c = -log(Nz) - log(Zm1) + log(H0 / C_KMS);
@@ -481,8 +487,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
     s_m2[i] = v.y;
     s_dl[i] = v.z;
     s_lpe[i] = v.w;
-    s_lm1[i] = logf(v.x);
-    s_lm2[i] = logf(v.y);
+    s_lm1[i] = log2f(v.x);
+    s_lm2[i] = log2f(v.y);
     s_pix[i] = inj ? 0 : __ldg(A.pix + it.begin + i);
   }
   __syncthreads();
@@ -560,7 +566,7 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
   float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
   SampleIn s;
   s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.lpe = v.w;
-  s.lm1 = logf(v.x); s.lm2 = logf(v.y);
+  s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
   const float* tb = A.tables + (size_t)A.k * A.tstride;
   const int nx = A.nx;
   float lw = -INFINITY, g[GRAD ? NP : 1], lb = 0.f;
@@ -580,7 +586,7 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
     A.lw[i] = ok ? lw : -INFINITY;
   } else {
     const float m = A.partials[((size_t)A.k * A.n_items + A.sample_item[i]) * PSTRIDE];
-    const float t = ok ? expf(lw - m) : 0.f;
+    const float t = ok ? ex2(lw - m) : 0.f;
     for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * g[q] : 0.f;
     if (ok && L.lam_edge != 0.f)
       A.tg[(size_t)P_LAM * A.n_total + i] = lam_edge_term(lw - m, g[P_LAM], lb);
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
     float s1 = 0.f, s2 = 0.f;
     if (m > -INFINITY)
       for (int i = tid; i < it.count; i += 256) {
-        const float t = expf(A.lw[base + i] - m);
+        const float t = ex2(A.lw[base + i] - m);
         s1 += t;
         s2 += t * t;
       }
@@ -645,6 +651,9 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
 }
 
 // -------------------------------------------------------------------- merge
+// Partial maxima arrive in log2 units; the FP64 sums scale by powers of two.
+constexpr double LN2D = 0.69314718055994530942;
+
 template <bool GRAD>
 __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
   __shared__ double rs[8][2 + NP];
@@ -686,7 +695,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
       for (int s = s0; s < s1; ++s) {
         const float* p = pk + (size_t)s * PSTRIDE;
         if (!(p[0] > -INFINITY)) continue;
-        const double r = exp((double)p[0] - M);
+        const double r = exp2((double)p[0] - M);
         S1 += (double)p[1] * r;
         S2 += (double)p[2] * r * r;
         if (GRAD)
@@ -695,7 +704,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
     }
     double lnL = -INFINITY, neff = 0.0;
     if (S1 > 0.0) {
-      lnL = M + log(S1) - log(A.ev_n[e]) + D.c;
+      lnL = M * LN2D + log(S1) - log(A.ev_n[e]) + D.c;
       neff = S1 * S1 / S2;
       if (GRAD)
         for (int i = 0; i < NP; ++i) sg[i] += G[i] / S1 + D.dc[i];
@@ -722,14 +731,14 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
     const double m = p[0];
     if (!(m > -INFINITY)) continue;
     if (m > sM) {
-      const double r = exp(sM - m);
+      const double r = exp2(sM - m);
       sS1 *= r;
       sS2 *= r * r;
       if (GRAD)
         for (int i = 0; i < NP; ++i) sG[i] *= r;
       sM = m;
     }
-    const double r = exp(m - sM);
+    const double r = exp2(m - sM);
     sS1 += (double)p[1] * r;
     sS2 += (double)p[2] * r * r;
     if (GRAD)
@@ -752,7 +761,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
       for (int i = 0; i < NP; ++i) oG[i] = __shfl_xor_sync(0xffffffffu, sG[i], o);
     const double M = fmax(sM, oM);
     if (M > -INFINITY) {
-      const double ra = exp(sM - M), rb = exp(oM - M);
+      const double ra = exp2(sM - M), rb = exp2(oM - M);
       sS1 = sS1 * ra + o1 * rb;
       sS2 = sS2 * ra * ra + o2 * rb * rb;
       if (GRAD)
@@ -786,7 +795,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
     if (M > -INFINITY)
       for (int q = 0; q < 8; ++q) {
         if (!(rsel[q][0] > -INFINITY)) continue;
-        const double r = exp(rsel[q][0] - M);
+        const double r = exp2(rsel[q][0] - M);
         S1 += rsel[q][1] * r;
         S2 += rsel[q][2] * r * r;
         if (GRAD)
@@ -796,7 +805,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
     const bool dead = (fl & 2) != 0;
     double lnxi = -INFINITY, neffs = 0.0;
     if (S1 > 0.0) {
-      lnxi = M + log(S1) - log(A.n_draw) + D.c;
+      lnxi = M * LN2D + log(S1) - log(A.n_draw) + D.c;
       neffs = S1 * S1 / S2;
     } else {
       flag |= 8;
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
   const float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
   SampleIn s;
   s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.lpe = v.w;
-  s.lm1 = logf(v.x); s.lm2 = logf(v.y);
+  s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
   const float* tb = A.tables;
   const int nx = A.nx;
   float lw = -INFINITY, g[NP], lb = 0.f;
@@ -844,7 +853,7 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
                             reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
     if (ok && L.lam_edge != 0.f) g[P_LAM] = lam_edge_term(0.f, g[P_LAM], lb);   // may overflow
   }
-  A.lnw[i] = ok ? lw : -INFINITY;
+  A.lnw[i] = ok ? lw * LN2F : -INFINITY;
   if (A.dlnw)
     for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? g[q] : 0.f;
 }
