@@ -119,8 +119,9 @@ typedef struct {
   int32_t n_x_table;     /* nodes of the per-Lambda z(d_L) inversion table, a multiple of 4
                             in [16, 4096] (default 512) */
   int32_t max_K;         /* largest Lambda batch a call may pass (default 256) */
-  int32_t chunk;         /* samples per work item, 64..4096 (default 1024) */
-  int32_t lambda_tile;   /* Lambda points per CTA when K >= 8 (default 8; 0 = choose) */
+  int32_t chunk;         /* samples per work item, 64..4096 (default 2048) */
+  int32_t lambda_tile;   /* Lambda points per CTA tile, 0..64 (0 = default 64) */
+  int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 2) */
 } gwc_options;
 
 /* Fill *o with the defaults listed above. */
@@ -187,7 +188,9 @@ gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
 
 /* Per-sample terms for one Lambda point (diagnostics and element-wise tests).  For every
  * event sample, in the context's order (events in input order; within an event, samples
- * stably sorted by pixel id), followed by every injection in input order:
+ * stably sorted by pixel id, then by dl_mpc), followed by every injection in the
+ * context's order (stably sorted by dl_mpc, then each consecutive block of 256 stably
+ * sorted by m1_det):
  *   d_lnw[n_samples + n_found]          ln w minus the per-Lambda constant c (-inf where w = 0)
  *   d_dlnw[13][n_samples + n_found]     (optional, may be NULL) d(ln w - c)/d Lambda
  *   d_c[14]                             c and dc/d Lambda, so ln w = d_lnw + c

@@ -58,7 +58,8 @@ class Options(ctypes.Structure):
     _fields_ = [("neff_min_event", ctypes.c_double), ("neff_min_sel", ctypes.c_double),
                 ("accum", ctypes.c_int32), ("los_dtype", ctypes.c_int32),
                 ("n_x_table", ctypes.c_int32), ("max_K", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32),
+                ("lambda_group", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -284,14 +285,29 @@ def sample_terms_noalloc(lam, samples, pix, injections, los, z_max, n_x_table=51
 
 
 def sample_order(cat):
-    """Input index of each sample in the library's order (stable sort by pixel per event)."""
+    """Input index of each sample in the library's order (per event, stable sort by
+    pixel id, then by d_L)."""
     off = np.asarray(cat["offsets"], dtype=np.int64)
     pix = np.asarray(cat["pix"])
+    dl = np.asarray(cat["dl"], dtype=np.float32)
     out = []
     for e in range(len(off) - 1):
         idx = np.arange(off[e], off[e + 1])
-        out.append(idx[np.argsort(pix[idx], kind="stable")])
+        out.append(idx[np.lexsort((dl[idx], pix[idx]))])
     return np.concatenate(out) if out else np.zeros(0, np.int64)
+
+
+INJ_BLOCK = 256
+
+
+def injection_order(cat):
+    """Input index of each injection in the library's order (stable sort by d_L, then
+    each consecutive block of INJ_BLOCK stably sorted by detector-frame m1)."""
+    order = np.argsort(np.asarray(cat["inj_dl"], dtype=np.float32), kind="stable")
+    m1 = np.asarray(cat["inj_m1"], dtype=np.float32)[order]
+    for a in range(0, len(order), INJ_BLOCK):
+        order[a:a + INJ_BLOCK] = order[a:a + INJ_BLOCK][np.argsort(m1[a:a + INJ_BLOCK], kind="stable")]
+    return order
 
 
 def profile_enable(ctx, enable=True):

@@ -27,6 +27,7 @@ using namespace gwc;
 namespace {
 
 constexpr uint32_t MAGIC = 0x67776331u;   // "gwc1"
+constexpr size_t INJ_BLOCK = 256;          // injections sorted by m1_det within blocks of this size
 thread_local std::string t_err;
 std::mutex g_mu;
 std::set<const gwc_ctx*> g_live;
@@ -209,15 +210,9 @@ void split_items(int64_t begin, int64_t count, int chunk, int32_t kind, std::vec
 }
 
 // launch geometry of the fused kernel for a batch of K points
-void fused_geometry(const gwc_ctx* c, int K, int& slab, int& P, int& n_slabs) {
-  if (K >= WARPS) {
-    slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : 32;
-    slab = std::max(1, std::min(slab, K));
-    P = 1;
-  } else {
-    slab = K;
-    P = WARPS / K;
-  }
+void fused_geometry(const gwc_ctx* c, int K, int& slab, int& n_slabs) {
+  slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : 64;
+  slab = std::max(1, std::min(std::min(slab, K), MAX_SLAB));
   n_slabs = (K + slab - 1) / slab;
 }
 
@@ -287,8 +282,8 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   gwc_status st = run_prologue(c, K, d_lambda, grad, s);
   if (st != GWC_OK) return st;
   if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
-  int slab, P, n_slabs;
-  fused_geometry(c, K, slab, P, n_slabs);
+  int slab, n_slabs;
+  fused_geometry(c, K, slab, n_slabs);
   FusedArgs fa;
   fa.smp = c->smp;
   fa.pix = c->pix;
@@ -302,7 +297,7 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   fa.n_items = c->n_items;
   fa.n_slabs = n_slabs;
   fa.slab = slab;
-  fa.P = P;
+  fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : 2;
   fa.K = K;
   fa.chunk = c->opt.chunk;
   fa.lf = c->lf;
@@ -314,7 +309,7 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   cudaError_t e = launch_fused(fa, grad, c->opt.accum == 1, c->bf16, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "sample kernel launch");
   if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
-  st = run_merge(c, K, P, grad, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, flags,
+  st = run_merge(c, K, 1, grad, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, flags,
                  grad_total, s);
   if (st != GWC_OK) return st;
   if ((e = prof_mark(c, 3, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
@@ -333,8 +328,9 @@ void gwc_default_options(gwc_options* o) {
   o->los_dtype = GWC_LOS_F32;
   o->n_x_table = 512;
   o->max_K = 256;
-  o->chunk = 1024;
+  o->chunk = 2048;
   o->lambda_tile = 0;
+  o->lambda_group = 0;
 }
 
 gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_injections* inj,
@@ -351,7 +347,11 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   if (o.chunk < 64 || o.chunk > 4096) return fail(nullptr, GWC_E_INVALID, "chunk must be in [64, 4096]");
   if (o.accum != 0 && o.accum != 1) return fail(nullptr, GWC_E_INVALID, "accum must be 0 or 1");
   if (o.los_dtype != GWC_LOS_F32 && o.los_dtype != GWC_LOS_BF16) return fail(nullptr, GWC_E_INVALID, "bad los_dtype");
-  if (o.lambda_tile < 0) return fail(nullptr, GWC_E_INVALID, "lambda_tile must be >= 0");
+  if (o.lambda_group != 0 && o.lambda_group != 1 && o.lambda_group != 2 && o.lambda_group != 4 &&
+      o.lambda_group != 8)
+    return fail(nullptr, GWC_E_INVALID, "lambda_group must be 0 (default), 1, 2, 4 or 8");
+  if (o.lambda_tile < 0 || o.lambda_tile > MAX_SLAB)
+    return fail(nullptr, GWC_E_INVALID, "lambda_tile must be in [0, " + std::to_string(MAX_SLAB) + "]");
   if (!(o.neff_min_event >= 0.0) || !(o.neff_min_sel >= 0.0)) return fail(nullptr, GWC_E_INVALID, "N_eff thresholds must be >= 0");
 
   // ---- validate the events
@@ -424,7 +424,12 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
       const int64_t a = ev->offsets[e], b = ev->offsets[e + 1];
       idx.resize((size_t)(b - a));
       for (int64_t k = a; k < b; ++k) idx[(size_t)(k - a)] = k;
-      std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return ev->pix[x] < ev->pix[y]; });
+      // by pixel (few LOS rows per chunk), then by d_L: a warp's 32 lanes then read
+      // neighbouring nodes of the inversion table and neighbouring cells of the LOS row
+      std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
+        return ev->pix[x] < ev->pix[y] || (ev->pix[x] == ev->pix[y] && ev->dl_mpc[x] < ev->dl_mpc[y]);
+      });
+
       for (int64_t q = 0; q < b - a; ++q) {
         const int64_t k = idx[(size_t)q];
         h_smp[(size_t)(a + q)] = make_float4(ev->m1_det[k], ev->m2_det[k], ev->dl_mpc[k], ev->ln_pe_prior[k]);
@@ -432,9 +437,24 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
       }
     }
   }
+  // injections by d_L, for the same reason (their sum does not depend on the order), then
+  // each block of INJ_BLOCK by m1_det: a block spans so little d_L that z is almost the
+  // same for all of it, so the injections above m_max (1 + z) -- often 40% of a broad
+  // injection set -- gather into whole warps that leave the loop early
   std::vector<float4> h_inj((size_t)ni);
-  for (int64_t k = 0; k < ni; ++k)
-    h_inj[(size_t)k] = make_float4(inj->m1_det[k], inj->m2_det[k], inj->dl_mpc[k], inj->ln_p_draw[k]);
+  {
+    std::vector<int64_t> idx((size_t)ni);
+    for (int64_t k = 0; k < ni; ++k) idx[(size_t)k] = k;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int64_t x, int64_t y) { return inj->dl_mpc[x] < inj->dl_mpc[y]; });
+    for (size_t q0 = 0; q0 < idx.size(); q0 += INJ_BLOCK)
+      std::stable_sort(idx.begin() + q0, idx.begin() + std::min(idx.size(), q0 + INJ_BLOCK),
+                       [&](int64_t x, int64_t y) { return inj->m1_det[x] < inj->m1_det[y]; });
+    for (int64_t q = 0; q < ni; ++q) {
+      const int64_t k = idx[(size_t)q];
+      h_inj[(size_t)q] = make_float4(inj->m1_det[k], inj->m2_det[k], inj->dl_mpc[k], inj->ln_p_draw[k]);
+    }
+  }
   std::vector<Item> items;
   std::vector<int32_t> ev_item0((size_t)ne + 1);
   std::vector<double> ev_n((size_t)std::max(ne, 1));
@@ -469,7 +489,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   }
 
   // ---- device memory
-  const int kcap = std::max(o.max_K, WARPS);
+  const int kcap = o.max_K;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   chk(dalloc(c, &c->smp, (size_t)ns));

@@ -26,7 +26,7 @@ constexpr double C_KMS = 299792.458;
 constexpr int WARPS = 8;             // warps per CTA of the sample kernels
 constexpr int THREADS = WARPS * 32;
 constexpr int NW_WIN = 128;          // panels of the smoothing-window tables
-constexpr int PSTRIDE = 16;          // floats per partial sum: m, s1, s2, g[13]
+constexpr int PSTRIDE = 18;          // floats per partial sum: m, s1, s2, g[13], mO, sO
 constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the prologue
 
 enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
@@ -54,21 +54,22 @@ struct __align__(16) LamF {
 static_assert(sizeof(LamF) == 52 * 4, "LamF layout");
 
 // FP64 constants of one Lambda point for the merge: ln w = (per-sample term) + c.
+// lam_sigma = +1 at lambda_peak = 1, -1 at lambda_peak = 0, else 0 (see Acc).
 struct LamD {
   double c;
   double dc[NP];
   int32_t flag;
-  int32_t pad;
+  int32_t lam_sigma;
 };
 
 // Per-Lambda table block (floats):
 //   [0, 4 NX)          float4 pos[NX]  {hi, lo, D, c2}: P(x_n) = hi + lo; cubic in t on
 //                      segment n: P = P_n + t (D + t (c2 + t c3)), t in [0, 1)
-//   [4 NX, 5 NX)       float c3[NX]
-//   [5 NX, 7 NX)       float2 jtab[NX] {J, dJ/dx * dx} (Hermite)
-//   [7 NX, 7 NX + 8 (NW_WIN + 1))  float2 win[4][NW_WIN + 1] {Q, dQ/dm * h}: Q_C, Q_beta,
-//                      Q_J, Q_K (Hermite in m over [m_min, m_min + delta_m])
-__host__ __device__ inline int table_floats(int nx) { return 7 * nx + 8 * (NW_WIN + 1); }
+//   [4 NX, 8 NX)       float4 aux[NX]  {c3, J, dJ/dx * dx, 0} (J Hermite in x)
+//   [8 NX, 8 NX + 4 (NW_WIN + 1))   float4 wval[NW_WIN + 1] {Q_C, Q_beta, Q_J, Q_K}
+//   [.., + 4 (NW_WIN + 1))           float4 wslp[NW_WIN + 1] the same times dQ/dm * h
+//                      (Hermite in m over [m_min, m_min + delta_m])
+__host__ __device__ constexpr int table_floats(int nx) { return 8 * nx + 8 * (NW_WIN + 1); }
 
 struct Item {          // one work item: a contiguous run of samples of one event, or of injections
   int64_t begin;
@@ -114,6 +115,21 @@ __device__ __forceinline__ float hermite_dt(float2 a, float2 b, float t) {
   return fmaf(t, fmaf(3.f * t, c3, 2.f * c2), a.y);
 }
 
+// cubic Hermite basis at t: f = h00 f0 + h10 f0'h + h01 f1 + h11 f1'h
+struct HermiteBasis {
+  float h00, h10, h01, h11;
+  __device__ __forceinline__ explicit HermiteBasis(float t) {
+    const float t2 = t * t, tm = t - 1.f;
+    h01 = t2 * fmaf(-2.f, t, 3.f);
+    h00 = 1.f - h01;
+    h10 = t * tm * tm;
+    h11 = t2 * tm;
+  }
+  __device__ __forceinline__ float operator()(float f0, float d0, float f1, float d1) const {
+    return fmaf(h00, f0, fmaf(h10, d0, fmaf(h01, f1, h11 * d1)));
+  }
+};
+
 struct SampleIn {
   float m1, m2, dl, lpe, lm1, lm2;   // detector-frame masses, distance, ln pi (natural),
                                      // log2 m1, log2 m2
@@ -129,20 +145,30 @@ __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int
 //   ln w = ln p_LOS(z) + (gamma - 3) ln u - softplus(r) + ln p_mix(m1) + beta ln m2 + ln S(m2)
 //          - ln C(m1) - ln D'(z) - ln pi,   u = 1 + z, r = (gamma + kappa) ln(u / (1 + z_p))
 // with every log1p term folded into one logarithm of a product.  row: the sample's LOS
-// row (or the pixel-averaged row for injections); pos/pc3/jtab/win: this Lambda's tables.
-// When L.lam_edge is set (lambda_peak = 0 or 1) the lambda derivative
-// e^(ln G - mix) - e^(ln P - mix) can exceed the float range for samples far from one
-// mixture component, although its product with the sample's weight does not; g[P_LAM]
-// then holds log2 P - mix2 and lam_lb holds log2 G - mix2, and the accumulator forms the
-// weighted difference in the exponent (lam_edge_term).  Returns false where w = 0.
-template <bool GRAD, typename RowT>
+// row (or the pixel-averaged row for injections); pos/aux/wval/wslp: this Lambda's tables.
+// When L.lam_edge is set (lambda_peak = 1 or 0) the mixture is one component and the
+// lambda derivative is sigma (1 - O/mix), where O is the other component's density
+// (P at lambda = 1, G at lambda = 0) and sigma = +1 / -1.  O/mix can exceed the float
+// range for samples far from the present component, so g[P_LAM] holds sigma and
+// lam_lb holds log2(O/mix); the accumulator keeps sum w O/mix as its own (max, sum) pair
+// and the FP64 merge subtracts it.  Returns false where w = 0.
+//
+// The gradient is not returned per sample: `sink` receives the sample's weight t
+// relative to the running maximum (after any rescaling) through sink.weight(lw2) and
+// then each derivative through sink.grad(i, value), so the 13 terms are folded into
+// their accumulators as soon as they exist (fewer live registers).  Samples whose lw2
+// falls more than 48 below the running maximum (which only grows) skip the derivative
+// work: their weight is below 2^-48 of the sum's largest.
+constexpr float GRAD_SKIP = 48.f;
+
+template <bool GRAD, typename RowT, typename Sink>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
                                            const float4* __restrict__ pos,
-                                           const float* __restrict__ pc3, int nx,
-                                           const float2* __restrict__ jtab,
-                                           const float2* __restrict__ win, float& lw2, float* g,
-                                           float& lam_lb) {
+                                           const float4* __restrict__ aux, int nx,
+                                           const float4* __restrict__ wval,
+                                           const float4* __restrict__ wslp, float& lw2,
+                                           Sink& sink) {
   // x = d_L H0 / c and the table coordinate x / dx carried with their rounding errors
   // (exact products by FMA), so the LOS-grid position keeps ~1e-7 of a cell
   const float x = s.dl * L.H0c;
@@ -156,7 +182,8 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const int n = min((int)sx, nx - 2);
   const float t = (sx - (float)n) + sx_lo;
   const float4 nd = __ldg(pos + n);
-  const float frac = nd.y + t * (nd.z + t * (nd.w + t * __ldg(pc3 + n)));
+  const float4 ax = __ldg(aux + n);
+  const float frac = nd.y + t * (nd.z + t * (nd.w + t * ax.x));
   int j = (int)floorf(nd.x + frac);
   float tl = (nd.x - (float)j) + frac;
   if (j > nz - 2) { tl += (float)(j - (nz - 2)); j = nz - 2; }
@@ -203,15 +230,15 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const bool win1 = m1s < L.mw;
   float Cx, mp1 = 0.f, Qc = 0.f, A = 0.f, dlm = 0.f, wt = 0.f;
   int wk = 0;
-  float2 wa = make_float2(0.f, 0.f), wb = wa;
   if (win1) {
     mp1 = m1s - L.mmin;
     const float ws = mp1 * L.inv_wh;
     wk = min((int)ws, NW_WIN - 1);
     wt = ws - (float)wk;
-    wa = __ldg(win + wk);
-    wb = __ldg(win + wk + 1);
-    Qc = hermite_val(wa, wb, wt);
+    const HermiteBasis hb(wt);
+    const float4 v0 = __ldg(wval + wk), v1 = __ldg(wval + wk + 1);
+    const float4 d0 = __ldg(wslp + wk), d1 = __ldg(wslp + wk + 1);
+    Qc = hb(v0.x, d0.x, v1.x, d1.x);
     Cx = Qc * (mp1 * mp1) * L.inv_dm;
     lin = fmaf(L.beta, lm2s2 - lm1s2, lin);
   } else {
@@ -243,8 +270,9 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   lw2 = fmaf(L.gam_m3, lu2, lin) + lg2(plos * (1.f + eab) * rcp(den));
   lw2 = fmaf(-s.lpe, LOG2EF, lw2);
   if (!(lw2 > -INFINITY)) return false;
+  const bool has_grad = sink.weight(lw2);
 
-  if (GRAD) {
+  if (GRAD && has_grad) {
     const float lu = lu2 * LN2F, lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
     const float inv1e = rcp(1.f + eab);
     const float pa = a2 >= b2 ? inv1e : eab * inv1e;   // mixture responsibilities
@@ -271,15 +299,20 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
       const float sf1 = f1 >= 0.f ? inv : ef1 * inv;
       dS1_dmin = -sf1 * L.dm * fmaf(j1, j1, j2 * j2);
       dS1_ddm = -sf1 * fmaf(mp1 * j2, j2, j1);
-      const float Qb = hermite_val(__ldg(win + (NW_WIN + 1) + wk), __ldg(win + (NW_WIN + 1) + wk + 1), wt);
-      const float Qj = hermite_val(__ldg(win + 2 * (NW_WIN + 1) + wk), __ldg(win + 2 * (NW_WIN + 1) + wk + 1), wt);
-      const float Qk = hermite_val(__ldg(win + 3 * (NW_WIN + 1) + wk), __ldg(win + 3 * (NW_WIN + 1) + wk + 1), wt);
+      // the four window tables share one Hermite basis (reloads hit L1)
+      const HermiteBasis hb(wt);
+      const float4 v0 = __ldg(wval + wk), v1 = __ldg(wval + wk + 1);
+      const float4 d0 = __ldg(wslp + wk), d1 = __ldg(wslp + wk + 1);
+      const float Qb = hb(v0.y, d0.y, v1.y, d1.y);
+      const float Qj = hb(v0.z, d0.z, v1.z, d1.z);
+      const float Qk = hb(v0.w, d0.w, v1.w, d1.w);
+      const float2 qa = make_float2(v0.x, d0.x), qb = make_float2(v1.x, d1.x);
       const float iQ = rcp(Qc);
       dlnC_db = Qb;                                      // R_beta / R_C
       dlnC_dmin = fmaf(L.beta, Qj, -rcp(Cx));            // (-1 + beta R_J) / R_C
       dlnC_ddm = Qk * iQ * j1;                           // R_K / R_C
       // -ln R_C(m1s) through m1s = m1/u:  m1s (Q_C'/Q_C + 2/m') / u
-      Gc = m1s * fmaf(hermite_dt(wa, wb, wt) * L.inv_wh, iQ, 2.f * j1);
+      Gc = m1s * fmaf(hermite_dt(qa, qb, wt) * L.inv_wh, iQ, 2.f * j1);
     } else {
       const float iC = rcp(Cx);
       float dC_db;
@@ -306,47 +339,76 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     Gz = fmaf(-D2, invDp, Gz);
 
     // z depends on H0 and Om through x and the inverted distance relation
-    const float J = hermite_val(__ldg(jtab + n), __ldg(jtab + n + 1), t);
-    g[P_H0] = Gz * x * L.invH0 * invDp;
-    g[P_OM] = fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp);
-    g[P_ALPHA] = pa * (-lm1s - L.dZPa);
-    g[P_BETA] = lm2s - dlnC_db;
-    g[P_MMIN] = -pa * L.dZPmin - pb * L.dZGmin + dS1_dmin - dS2_dm - dlnC_dmin;
-    g[P_MMAX] = -pa * L.dZPmax - pb * L.dZGmax;
-    g[P_DM] = dS1_ddm + dS2_ddm - dlnC_ddm;
-    g[P_MU] = pb * (zz * L.inv_sig - L.dZGmu);
-    g[P_SIG] = pb * (fmaf(zz, zz, -1.f) * L.inv_sig - L.dZGsig);
+    const float4 ax1 = __ldg(aux + n + 1);
+    const float J = hermite_val(make_float2(ax.y, ax.z), make_float2(ax1.y, ax1.z), t);
+    sink.grad(P_H0, Gz * x * L.invH0 * invDp);
+    sink.grad(P_OM, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
+    sink.grad(P_ALPHA, pa * (-lm1s - L.dZPa));
+    sink.grad(P_BETA, lm2s - dlnC_db);
+    sink.grad(P_MMIN, -pa * L.dZPmin - pb * L.dZGmin + dS1_dmin - dS2_dm - dlnC_dmin);
+    sink.grad(P_MMAX, -pa * L.dZPmax - pb * L.dZGmax);
+    sink.grad(P_DM, dS1_ddm + dS2_ddm - dlnC_ddm);
+    sink.grad(P_MU, pb * (zz * L.inv_sig - L.dZGmu));
+    sink.grad(P_SIG, pb * (fmaf(zz, zz, -1.f) * L.inv_sig - L.dZGsig));
     if (L.lam_edge == 0.f) {
-      g[P_LAM] = pb * L.inv_lam - pa * L.inv_1ml;
-    } else {
-      const float mix2 = mx + lg2(1.f + eab);
-      g[P_LAM] = fmaf(-L.alpha, lm1s2, L.la0_2) - mix2;           // log2 P - mix2
-      lam_lb = fmaf(-HALF_LOG2EF * zz, zz, L.lb0_2) - mix2;      // log2 G - mix2
+      sink.grad(P_LAM, pb * L.inv_lam - pa * L.inv_1ml);
+    } else if (L.lam >= 1.f) {                                    // mix = G: 1 - P/G
+      sink.lam_edge(1.f, lw2, fmaf(-L.alpha, lm1s2, L.la0_2) - b2);
+    } else {                                                      // mix = P: G/P - 1
+      sink.lam_edge(-1.f, lw2, fmaf(-HALF_LOG2EF * zz, zz, L.lb0_2) - a2);
     }
     const float dlu = (lu2 - L.lp2) * LN2F;
-    g[P_GAM] = lu - sr * dlu;
-    g[P_KAP] = -sr * dlu;
-    g[P_ZP] = sr * L.gpk * L.inv1zp;
+    sink.grad(P_GAM, lu - sr * dlu);
+    sink.grad(P_KAP, -sr * dlu);
+    sink.grad(P_ZP, sr * L.gpk * L.inv1zp);
   }
   return true;
 }
 
-// 2^d (2^lb - 2^la) without forming either power on its own
-__device__ __forceinline__ float lam_edge_term(float d, float la, float lb) {
-  return ex2(d + lb) - ex2(d + la);
-}
+// Sink that folds a sample into the online (max, sums) accumulator
+template <bool GRAD, bool KAHAN> struct Acc;
+template <bool GRAD, bool KAHAN>
+struct AccSink {
+  Acc<GRAD, KAHAN>& a;
+  float t = 0.f;
+  __device__ __forceinline__ explicit AccSink(Acc<GRAD, KAHAN>& acc) : a(acc) {}
+  __device__ __forceinline__ bool weight(float lw) {
+    t = a.take(lw);
+    return GRAD && !(lw < a.m - GRAD_SKIP);
+  }
+  __device__ __forceinline__ void grad(int i, float v) { a.g[i] = fmaf(t, v, a.g[i]); }
+  __device__ __forceinline__ void lam_edge(float sigma, float lw, float lo) { a.add_other(sigma, t, lw + lo); }
+};
 
-// Online (max, sum 2^(l-max), sum 2^(2(l-max)), sum 2^(l-max) dl) accumulator, l in log2 units.
+// Sink that keeps one sample's value and derivatives (per-sample outputs)
+struct TermSink {
+  float g[NP];
+  float lo = 0.f;
+  bool edge = false;
+  __device__ __forceinline__ bool weight(float) { return true; }
+  __device__ __forceinline__ void grad(int i, float v) { g[i] = v; }
+  __device__ __forceinline__ void lam_edge(float sigma, float, float l) {
+    g[P_LAM] = sigma;
+    lo = l;
+    edge = true;
+  }
+};
+
+// Online (max, sum 2^(l-max), sum 2^(2(l-max)), sum 2^(l-max) dl) accumulator, l in
+// log2 units, plus (mO, sO) = (max, sum 2^(l + lo - mO)) of the other-component weights
+// at lambda_peak = 0 or 1 (zero otherwise).
 template <bool GRAD, bool KAHAN>
 struct Acc {
   float m = -INFINITY, s1 = 0.f, s2 = 0.f, c1 = 0.f, c2 = 0.f;
+  float mO = -INFINITY, sO = 0.f;
   float g[GRAD ? NP : 1];
   __device__ __forceinline__ Acc() {
 #pragma unroll
     for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] = 0.f;
   }
-  __device__ __forceinline__ void add(float lw, const float* dg, bool lam_edge = false,
-                                      float lam_lb = 0.f) {
+  // add a sample of log2 weight lw to the value sums; returns its weight 2^(lw - m)
+  // relative to the (possibly new) running maximum m, rescaling what is already summed
+  __device__ __forceinline__ float take(float lw) {
     if (lw > m) {
       const float sc = ex2(m - lw);   // 0 on the first sample
       s1 = fmaf(s1, sc, 1.f);
@@ -354,43 +416,57 @@ struct Acc {
       c1 *= sc;
       c2 *= sc * sc;
       if (GRAD) {
-        const float dl = lam_edge ? lam_edge_term(0.f, dg[P_LAM], lam_lb) : dg[P_LAM];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) g[i] = fmaf(g[i], sc, i == P_LAM ? dl : dg[i]);
+        for (int i = 0; i < NP; ++i) g[i] *= sc;
       }
       m = lw;
+      return 1.f;
+    }
+    const float tt = ex2(lw - m);
+    if (KAHAN) {
+      float y1 = tt - c1, t1 = s1 + y1;
+      c1 = (t1 - s1) - y1;
+      s1 = t1;
+      float y2 = tt * tt - c2, t2 = s2 + y2;
+      c2 = (t2 - s2) - y2;
+      s2 = t2;
     } else {
-      const float tt = ex2(lw - m);
-      if (KAHAN) {
-        float y1 = tt - c1, t1 = s1 + y1;
-        c1 = (t1 - s1) - y1;
-        s1 = t1;
-        float y2 = tt * tt - c2, t2 = s2 + y2;
-        c2 = (t2 - s2) - y2;
-        s2 = t2;
-      } else {
-        s1 += tt;
-        s2 = fmaf(tt, tt, s2);
-      }
-      if (GRAD) {
-        const float cl = lam_edge ? lam_edge_term(lw - m, dg[P_LAM], lam_lb) : tt * dg[P_LAM];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) g[i] = i == P_LAM ? g[i] + cl : fmaf(tt, dg[i], g[i]);
-      }
+      s1 += tt;
+      s2 = fmaf(tt, tt, s2);
+    }
+    return tt;
+  }
+  // lambda_peak = 1 or 0: sigma t, and the other component's weight 2^l in (mO, sO)
+  __device__ __forceinline__ void add_other(float sigma, float tt, float l) {
+    g[P_LAM] = fmaf(sigma, tt, g[P_LAM]);
+    if (l > mO) {
+      sO = fmaf(sO, ex2(mO - l), 1.f);
+      mO = l;
+    } else {
+      sO += ex2(l - mO);
     }
   }
   // merge another lane's sums (fixed shuffle tree keeps the result deterministic)
-  __device__ __forceinline__ void merge(float om, float os1, float os2, const float* og) {
+  __device__ __forceinline__ void merge(float om, float os1, float os2, const float* og,
+                                        float omO = -INFINITY, float osO = 0.f) {
     const float M = fmaxf(m, om);
-    if (M == -INFINITY) return;
-    const float sa = ex2(m - M), sb = ex2(om - M);
-    s1 = s1 * sa + os1 * sb;
-    s2 = s2 * sa * sa + os2 * sb * sb;
-    if (GRAD) {
+    if (M > -INFINITY) {
+      const float sa = ex2(m - M), sb = ex2(om - M);
+      s1 = s1 * sa + os1 * sb;
+      s2 = s2 * sa * sa + os2 * sb * sb;
+      if (GRAD) {
 #pragma unroll
-      for (int i = 0; i < NP; ++i) g[i] = g[i] * sa + og[i] * sb;
+        for (int i = 0; i < NP; ++i) g[i] = g[i] * sa + og[i] * sb;
+      }
+      m = M;
     }
-    m = M;
+    if (GRAD) {
+      const float MO = fmaxf(mO, omO);
+      if (MO > -INFINITY) {
+        sO = sO * ex2(mO - MO) + osO * ex2(omO - MO);
+        mO = MO;
+      }
+    }
   }
 };
 

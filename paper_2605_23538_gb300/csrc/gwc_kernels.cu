@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       ld->c = 0.0;
       for (int i = 0; i < NP; ++i) ld->dc[i] = 0.0;
       ld->flag = 1;
+      ld->lam_sigma = 0;
     }
     return;
   }
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double pscale = (double)(nz - 1) / zmax;   // LOS grid units per unit z
 
   // ---- (2) inversion table on the uniform x grid
-  float2* jt = reinterpret_cast<float2*>(tb + 5 * nx);
+  float4* aux = reinterpret_cast<float4*>(tb + 4 * nx);
   for (int n = tid; n < nx; n += PRO_THREADS) {
     const double xn = (n == nx - 1) ? xmax : n * dx;
     double z = 0.0, Dp = 1.0, Jz = 0.0, jd = 0.0;
@@ -215,11 +216,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     }
     sdyn[2 * n] = z * pscale;                // P_n
     sdyn[2 * n + 1] = pscale / Dp * dx;      // dP/dx * dx
-    if (A.want_grad) jt[n] = make_float2((float)Jz, (float)(jd / Dp * dx));
+    aux[n] = make_float4(0.f, (float)Jz, (float)(jd / Dp * dx), 0.f);
   }
   __syncthreads();
   float4* pos = reinterpret_cast<float4*>(tb);
-  float* pc3 = tb + 4 * nx;
   for (int n = tid; n < nx; n += PRO_THREADS) {
     const double P0 = sdyn[2 * n], D0 = sdyn[2 * n + 1];
     double c2 = 0.0, c3 = 0.0;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     }
     const float hi = (float)P0;
     pos[n] = make_float4(hi, (float)(P0 - (double)hi), (float)D0, (float)c2);
-    pc3[n] = (float)c3;
+    aux[n].x = (float)c3;
   }
 
   // ---- (3) mass-model normalisations (thread 0), broadcast through shared memory
@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   //   Q_C = R_C dm / m'^2, Q_beta = R_beta / R_C, Q_J = R_J / R_C, Q_K = R_K dm / m'
   // and their m-derivatives (times hw).  Node 0 takes the m' -> 0 limits (1, ln mmin,
   // 1/mmin, -1) with secant slopes: weights there carry S(m1) < e^-127.
-  float2* win = reinterpret_cast<float2*>(tb + 7 * nx);
+  float4* wval = reinterpret_cast<float4*>(tb + 8 * nx);
+  float4* wslp = wval + (NW_WIN + 1);
   __shared__ double scum[4][NW_WIN + 1];
   __shared__ double sq[4][NW_WIN + 1];
   if (tid < NW_WIN)
@@ -345,8 +346,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   __syncthreads();
   if (tid == 0 && dm > 0.0)
     for (int i = 0; i < 4; ++i) qd[i] = (sq[i][1] - sq[i][0]) / hw;
-  if (tid <= NW_WIN)
-    for (int i = 0; i < 4; ++i) win[i * (NW_WIN + 1) + tid] = make_float2((float)qv[i], (float)(qd[i] * hw));
+  if (tid <= NW_WIN) {
+    wval[tid] = make_float4((float)qv[0], (float)qv[1], (float)qv[2], (float)qv[3]);
+    wslp[tid] = make_float4((float)(qd[0] * hw), (float)(qd[1] * hw), (float)(qd[2] * hw), (float)(qd[3] * hw));
+  }
 
   // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
   //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
@@ -457,12 +460,25 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     dc[P_ZP] = -sc[19];
     for (int i = 0; i < NP; ++i) ld->dc[i] = dc[i];
     ld->flag = 0;
+    ld->lam_sigma = lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0);
   }
 }
 
 // ---------------------------------------------------------------- fused kernel
+// A CTA owns one work item (a chunk of one event's samples, or of injections) and a
+// tile of Lambda points.  Its 8 warps form 8/G groups of G warps; a group sweeps one
+// Lambda at a time, each of its warps over 1/G of the staged samples, so the CTA's L1
+// working set is 8/G Lambda points' tables plus the chunk's few LOS rows, and each
+// lane amortises its per-Lambda work over chunk / (32 G) samples.  Every warp leaves
+// its (max, sums) for each of its Lambda points in shared memory; after the tile the
+// G entries of each Lambda are combined in warp order into one partial per
+// (item, Lambda).
+// Occupancy: the value kernel fits three CTAs per SM (<= 80 registers per thread), the
+// gradient kernel two (<= 128); three would force the 13 gradient sums to spill.
+constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
+
 template <bool GRAD, bool KAHAN, typename RowT>
-__global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
+__global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fused(FusedArgs A) {
   extern __shared__ __align__(16) float sm[];
   const int CH = A.chunk;
   float* s_m1 = sm;
@@ -472,8 +488,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
   float* s_lm1 = s_lpe + CH;
   float* s_lm2 = s_lm1 + CH;
   int* s_pix = reinterpret_cast<int*>(s_lm2 + CH);
+  float* s_part = reinterpret_cast<float*>(s_pix + CH);   // [slab][G][PSTRIDE]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = A.group, ngroups = WARPS / G;
+  const int gidx = warp / G, wg = warp - gidx * G;
   const int unit = blockIdx.x;
   const int ipos = unit / A.n_slabs, slab = unit - ipos * A.n_slabs;
   const int item = A.sched[ipos];
@@ -495,33 +514,30 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
 
   const int k0 = slab * A.slab;
   const int nk = min(A.slab, A.K - k0);
-  const int ntask = nk * A.P;
   const int nx = A.nx, nz = A.nz;
-  for (int task = warp; task < ntask; task += WARPS) {
-    const int k = k0 + task / A.P, part = task - (task / A.P) * A.P;
+  const int a = (int)((long long)it.count * wg / G);
+  const int b = (int)((long long)it.count * (wg + 1) / G);
+  for (int kk = gidx; kk < nk; kk += ngroups) {
+    const int k = k0 + kk;
     const LamF L = A.lf[k];
-    const bool lam_edge = L.lam_edge != 0.f;
     Acc<GRAD, KAHAN> acc;
     if (L.live != 0.f) {
       const float* tb = A.tables + (size_t)k * A.tstride;
       const float4* pos = reinterpret_cast<const float4*>(tb);
-      const float* pc3 = tb + 4 * nx;
-      const float2* jt = reinterpret_cast<const float2*>(tb + 5 * nx);
-      const float2* wt = reinterpret_cast<const float2*>(tb + 7 * nx);
-      const int a = (int)((long long)it.count * part / A.P);
-      const int b = (int)((long long)it.count * (part + 1) / A.P);
+      const float4* aux = reinterpret_cast<const float4*>(tb + 4 * nx);
+      const float4* wv = reinterpret_cast<const float4*>(tb + 8 * nx);
+      const float4* ws = wv + (NW_WIN + 1);
       for (int i = a + lane; i < b; i += 32) {
         SampleIn s;
         s.m1 = s_m1[i]; s.m2 = s_m2[i]; s.dl = s_dl[i]; s.lpe = s_lpe[i];
         s.lm1 = s_lm1[i]; s.lm2 = s_lm2[i];
-        float lw, g[GRAD ? NP : 1], lb = 0.f;
-        bool ok;
+        float lw;
+        AccSink<GRAD, KAHAN> sink(acc);
         if (inj)
-          ok = sample_lnw<GRAD>(L, s, A.pbar32, nz, pos, pc3, nx, jt, wt, lw, g, lb);
+          sample_lnw<GRAD>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
         else
-          ok = sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
-                                nz, pos, pc3, nx, jt, wt, lw, g, lb);
-        if (ok) acc.add(lw, g, GRAD && lam_edge, lb);
+          sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
+                           nz, pos, aux, nx, wv, ws, lw, sink);
       }
       if (KAHAN) { acc.s1 -= acc.c1; acc.s2 -= acc.c2; }
     }
@@ -531,24 +547,61 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused(FusedArgs A) {
       const float om_ = __shfl_xor_sync(0xffffffffu, acc.m, o);
       const float o1 = __shfl_xor_sync(0xffffffffu, acc.s1, o);
       const float o2 = __shfl_xor_sync(0xffffffffu, acc.s2, o);
-      float og[GRAD ? NP : 1];
+      float og[GRAD ? NP : 1], omO = -INFINITY, osO = 0.f;
       if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) og[i] = __shfl_xor_sync(0xffffffffu, acc.g[i], o);
+        for (int q = 0; q < NP; ++q) og[q] = __shfl_xor_sync(0xffffffffu, acc.g[q], o);
+        omO = __shfl_xor_sync(0xffffffffu, acc.mO, o);
+        osO = __shfl_xor_sync(0xffffffffu, acc.sO, o);
       }
-      acc.merge(om_, o1, o2, og);
+      acc.merge(om_, o1, o2, og, omO, osO);
     }
-    float* out = A.partials + (((size_t)k * A.n_items + item) * A.P + part) * PSTRIDE;
+    float* slot = s_part + ((size_t)kk * G + wg) * PSTRIDE;
     if (lane == 0) {
-      out[0] = acc.m;
-      out[1] = acc.s1;
-      out[2] = acc.s2;
+      slot[0] = acc.m;
+      slot[1] = acc.s1;
+      slot[2] = acc.s2;
+      slot[16] = acc.mO;
+      slot[17] = acc.sO;
     }
     if (GRAD && lane < NP) {
       float gv = 0.f;
 #pragma unroll
-      for (int i = 0; i < NP; ++i) gv = (lane == i) ? acc.g[i] : gv;
-      out[3 + lane] = gv;
+      for (int q = 0; q < NP; ++q) gv = (lane == q) ? acc.g[q] : gv;
+      slot[3 + lane] = gv;
+    }
+  }
+  __syncthreads();
+  // combine the G warps' sums of each Lambda in warp order: lane q owns component q
+  for (int kk = warp; kk < nk; kk += WARPS) {
+    const float* sl = s_part + (size_t)kk * G * PSTRIDE;
+    float M = -INFINITY;
+    for (int w = 0; w < G; ++w) M = fmaxf(M, sl[w * PSTRIDE]);
+    float* out = A.partials + ((size_t)(k0 + kk) * A.n_items + item) * PSTRIDE;
+    const int ncomp = GRAD ? 2 + NP : 2;   // s1, s2 (and g)
+    if (lane < ncomp) {
+      float acc = 0.f;
+      if (M > -INFINITY) {
+        for (int w = 0; w < G; ++w) {
+          const float mw = sl[w * PSTRIDE];
+          if (mw > -INFINITY) acc = fmaf(sl[w * PSTRIDE + 1 + lane], lane == 1 ? ex2(2.f * (mw - M)) : ex2(mw - M), acc);
+        }
+      }
+      out[1 + lane] = acc;
+    }
+    if (lane == 0) out[0] = M;
+    if (GRAD && lane == 15) {
+      float MO = -INFINITY;
+      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PSTRIDE + 16]);
+      float so = 0.f;
+      if (MO > -INFINITY) {
+        for (int w = 0; w < G; ++w) {
+          const float mo = sl[w * PSTRIDE + 16];
+          if (mo > -INFINITY) so = fmaf(sl[w * PSTRIDE + 17], ex2(mo - MO), so);
+        }
+      }
+      out[16] = MO;
+      out[17] = so;
     }
   }
 }
@@ -569,27 +622,29 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
   s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
   const float* tb = A.tables + (size_t)A.k * A.tstride;
   const int nx = A.nx;
-  float lw = -INFINITY, g[GRAD ? NP : 1], lb = 0.f;
+  const float4* pos = reinterpret_cast<const float4*>(tb);
+  const float4* aux = reinterpret_cast<const float4*>(tb + 4 * nx);
+  const float4* wv = reinterpret_cast<const float4*>(tb + 8 * nx);
+  const float4* ws = wv + (NW_WIN + 1);
+  // the gradient pass knows its item's final maximum from the value pass
+  const float m = GRAD ? A.partials[((size_t)A.k * A.n_items + A.sample_item[i]) * PSTRIDE] : -INFINITY;
+  float lw = -INFINITY;
+  TermSink ts;
   bool ok = false;
   if (L.live != 0.f) {
     if (inj)
-      ok = sample_lnw<GRAD>(L, s, A.pbar32, A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
-                            reinterpret_cast<const float2*>(tb + 5 * nx),
-                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
+      ok = sample_lnw<GRAD>(L, s, A.pbar32, A.nz, pos, aux, nx, wv, ws, lw, ts);
     else
       ok = sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
-                            A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
-                            reinterpret_cast<const float2*>(tb + 5 * nx),
-                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
+                            A.nz, pos, aux, nx, wv, ws, lw, ts);
   }
   if (!GRAD) {
     A.lw[i] = ok ? lw : -INFINITY;
   } else {
-    const float m = A.partials[((size_t)A.k * A.n_items + A.sample_item[i]) * PSTRIDE];
     const float t = ok ? ex2(lw - m) : 0.f;
-    for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * g[q] : 0.f;
-    if (ok && L.lam_edge != 0.f)
-      A.tg[(size_t)P_LAM * A.n_total + i] = lam_edge_term(lw - m, g[P_LAM], lb);
+    for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * ts.g[q] : 0.f;
+    if (ok && ts.edge)   // sigma (t - t O/mix): may overflow for extreme samples
+      A.tg[(size_t)P_LAM * A.n_total + i] = ts.g[P_LAM] * (t - ex2(lw - m + ts.lo));
   }
 }
 
@@ -631,6 +686,8 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
       out[0] = m;
       out[1] = a;
       out[2] = b;
+      out[16] = -INFINITY;   // the plain path folds the lambda-edge term into its g
+      out[17] = 0.f;
     }
   } else {
     float gs[NP];
@@ -655,9 +712,10 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
 constexpr double LN2D = 0.69314718055994530942;
 
 template <bool GRAD>
-__global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
+__global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   __shared__ double rs[8][2 + NP];
   __shared__ double rsel[8][3 + NP];
+  __shared__ double rO[8][2];
   __shared__ int rfail[8];
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const LamD D = A.ld[k];
@@ -701,6 +759,11 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
         if (GRAD)
           for (int i = 0; i < NP; ++i) G[i] += (double)p[3 + i] * r;
       }
+      if (GRAD && D.lam_sigma != 0)   // other-component sums at lambda_peak = 0 or 1
+        for (int s = s0; s < s1; ++s) {
+          const float* p = pk + (size_t)s * PSTRIDE;
+          if (p[16] > -INFINITY) G[P_LAM] -= D.lam_sigma * (double)p[17] * exp2((double)p[16] - M);
+        }
     }
     double lnL = -INFINITY, neff = 0.0;
     if (S1 > 0.0) {
@@ -724,10 +787,16 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
 
   // ---- injections: online merge of the injection partials
   double sM = -INFINITY, sS1 = 0.0, sS2 = 0.0, sG[GRAD ? NP : 1];
+  double oM = -INFINITY, oS = 0.0;   // other-component pair at lambda_peak = 0 or 1
   if (GRAD)
     for (int i = 0; i < NP; ++i) sG[i] = 0.0;
   for (int s = A.inj_item0 * P + tid; s < A.n_items * P; s += 256) {
     const float* p = pk + (size_t)s * PSTRIDE;
+    if (GRAD && D.lam_sigma != 0 && p[16] > -INFINITY) {
+      const double mo = p[16];
+      if (mo > oM) { oS = oS * exp2(oM - mo) + (double)p[17]; oM = mo; }
+      else oS += (double)p[17] * exp2(mo - oM);
+    }
     const double m = p[0];
     if (!(m > -INFINITY)) continue;
     if (m > sM) {
@@ -749,6 +818,11 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
   sumL += cmp;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
+    if (GRAD) {
+      const double x_m = __shfl_xor_sync(0xffffffffu, oM, o), x_s = __shfl_xor_sync(0xffffffffu, oS, o);
+      const double MO = fmax(oM, x_m);
+      if (MO > -INFINITY) { oS = oS * exp2(oM - MO) + x_s * exp2(x_m - MO); oM = MO; }
+    }
     sumL += __shfl_xor_sync(0xffffffffu, sumL, o);
     fail |= __shfl_xor_sync(0xffffffffu, fail, o);
     if (GRAD)
@@ -777,6 +851,8 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
     rsel[w][0] = sM;
     rsel[w][1] = sS1;
     rsel[w][2] = sS2;
+    rO[w][0] = oM;
+    rO[w][1] = oS;
     if (GRAD)
       for (int i = 0; i < NP; ++i) rsel[w][3 + i] = sG[i];
   }
@@ -792,7 +868,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
         for (int i = 0; i < NP; ++i) gt[i] += rs[q][2 + i];
       M = fmax(M, rsel[q][0]);
     }
-    if (M > -INFINITY)
+    if (M > -INFINITY) {
       for (int q = 0; q < 8; ++q) {
         if (!(rsel[q][0] > -INFINITY)) continue;
         const double r = exp2(rsel[q][0] - M);
@@ -801,6 +877,10 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs A) {
         if (GRAD)
           for (int i = 0; i < NP; ++i) G[i] += rsel[q][3 + i] * r;
       }
+      if (GRAD && D.lam_sigma != 0)
+        for (int q = 0; q < 8; ++q)
+          if (rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * exp2(rO[q][0] - M);
+    }
     int flag = (fl & 1) ? 2 : 0;
     const bool dead = (fl & 2) != 0;
     double lnxi = -INFINITY, neffs = 0.0;
@@ -839,23 +919,24 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
   s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
   const float* tb = A.tables;
   const int nx = A.nx;
-  float lw = -INFINITY, g[NP], lb = 0.f;
+  const float4* pos = reinterpret_cast<const float4*>(tb);
+  const float4* aux = reinterpret_cast<const float4*>(tb + 4 * nx);
+  const float4* wv = reinterpret_cast<const float4*>(tb + 8 * nx);
+  const float4* ws = wv + (NW_WIN + 1);
+  float lw = -INFINITY;
+  TermSink ts;
   bool ok = false;
   if (L.live != 0.f) {
     if (inj)
-      ok = sample_lnw<true>(L, s, A.pbar32, A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
-                            reinterpret_cast<const float2*>(tb + 5 * nx),
-                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
+      ok = sample_lnw<true>(L, s, A.pbar32, A.nz, pos, aux, nx, wv, ws, lw, ts);
     else
       ok = sample_lnw<true>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
-                            A.nz, reinterpret_cast<const float4*>(tb), tb + 4 * nx, nx,
-                            reinterpret_cast<const float2*>(tb + 5 * nx),
-                            reinterpret_cast<const float2*>(tb + 7 * nx), lw, g, lb);
-    if (ok && L.lam_edge != 0.f) g[P_LAM] = lam_edge_term(0.f, g[P_LAM], lb);   // may overflow
+                            A.nz, pos, aux, nx, wv, ws, lw, ts);
+    if (ok && ts.edge) ts.g[P_LAM] *= 1.f - ex2(ts.lo);   // sigma (1 - O/mix): may overflow
   }
   A.lnw[i] = ok ? lw * LN2F : -INFINITY;
   if (A.dlnw)
-    for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? g[q] : 0.f;
+    for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? ts.g[q] : 0.f;
 }
 
 cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s) {
@@ -899,11 +980,13 @@ static cudaError_t launch_fused_t(const FusedArgs& a, int grid, size_t smem, cud
   return cudaGetLastError();
 }
 
-size_t fused_smem_bytes(int chunk) { return (size_t)chunk * 7 * sizeof(float); }
-size_t fused_smem_max() { return fused_smem_bytes(4096); }
+size_t fused_smem_bytes(int chunk, int slab, int group) {
+  return (size_t)chunk * 7 * sizeof(float) + (size_t)slab * group * PSTRIDE * sizeof(float);
+}
+size_t fused_smem_max() { return fused_smem_bytes(4096, MAX_SLAB, WARPS); }
 
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s) {
-  const size_t smem = fused_smem_bytes(a.chunk);
+  const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
   if (grad) {
     if (kahan) return bf16 ? launch_fused_t<true, true, __nv_bfloat16>(a, grid, smem, s)
                            : launch_fused_t<true, true, float>(a, grid, smem, s);

@@ -35,14 +35,14 @@ struct FusedArgs {
   const int32_t* sched;   // launch order (largest items first)
   int n_items;
   int n_slabs;            // Lambda tiles per item
-  int slab;               // Lambda points per tile
-  int P;                  // sample parts per (item, Lambda) when K < WARPS
+  int slab;               // Lambda points per tile (<= MAX_SLAB)
+  int group;              // warps sharing one Lambda point: 1, 2, 4 or 8
   int K;
   int chunk;
   const LamF* lf;
   const float* tables;
   int tstride;
-  float* partials;        // [K][n_items][P][PSTRIDE]
+  float* partials;        // [K][n_items][PSTRIDE]
 };
 
 struct PlainArgs {
@@ -90,7 +90,8 @@ struct MergeArgs {
 
 cudaError_t set_gauss_legendre(const double* x, const double* w);
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s);
-size_t fused_smem_bytes(int chunk);
+constexpr int MAX_SLAB = 64;   // Lambda points per CTA tile at most
+size_t fused_smem_bytes(int chunk, int slab, int group);
 size_t fused_smem_max();
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s);
 cudaError_t launch_plain_sample(const PlainArgs& a, bool grad, bool bf16, cudaStream_t s);

@@ -41,14 +41,14 @@ def test_struct_sizes_match_header(g):
     assert ctypes.sizeof(g.Events) == 56
     assert ctypes.sizeof(g.Los) == 32
     assert ctypes.sizeof(g.Injections) == 48
-    assert ctypes.sizeof(g.Options) == 40
+    assert ctypes.sizeof(g.Options) == 40 + 8
     assert ctypes.sizeof(g.Info) == 56
 
 
 def test_defaults(g):
     o = g.default_options()
     assert (o.neff_min_event, o.neff_min_sel, o.accum, o.los_dtype) == (2.0, 0.0, 0, 0)
-    assert (o.n_x_table, o.max_K, o.chunk, o.lambda_tile) == (512, 256, 1024, 0)
+    assert (o.n_x_table, o.max_K, o.chunk, o.lambda_tile, o.lambda_group) == (512, 256, 2048, 0, 0)
 
 
 def test_invalid_inputs_rejected_before_any_device_work(g, synth):

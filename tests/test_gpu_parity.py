@@ -131,7 +131,7 @@ def test_sample_terms_elementwise(torch, g, orc, synth, cat_ragged, which):
         got = lnw.cpu().numpy().astype(np.float64) + c[0]
         gd = d.cpu().numpy().T.astype(np.float64) + c[None, 1:]
     ro, rg, rk = orc.ln_w_samples(lam, cat_ragged, "events", idx=order, grad=True)
-    io, ig, ik = orc.ln_w_samples(lam, cat_ragged, "inj", grad=True)
+    io, ig, ik = orc.ln_w_samples(lam, cat_ragged, "inj", idx=g.injection_order(cat_ragged), grad=True)
     ref, rgrad, rkink = np.concatenate([ro, io]), np.vstack([rg, ig]), np.vstack([rk, ik])
     # only samples whose weight is within e^-30 of the largest in their set (their event,
     # or the injections) can move any output; below that FP32 cannot resolve terms such
@@ -183,11 +183,11 @@ def test_batch_gradient_ragged(torch, g, orc, synth, cat_ragged):
         compare(got, ref, grad=True, label="ragged grad K=10")
 
 
-@pytest.mark.parametrize("chunk,tile", [(64, 1), (256, 3), (4096, 40)])
-def test_tiling_does_not_change_results(torch, g, synth, cat_ragged, chunk, tile):
+@pytest.mark.parametrize("chunk,tile,group", [(64, 1, 1), (256, 3, 8), (4096, 40, 4), (1024, 16, 1)])
+def test_tiling_does_not_change_results(torch, g, synth, cat_ragged, chunk, tile, group):
     lam = dev(torch, np.vstack([synth.FIDUCIAL, synth.lambda_batch(11, purpose=14)]))
     with g.Context(cat_ragged, max_K=16) as a, g.Context(cat_ragged, max_K=16, chunk=chunk,
-                                                         lambda_tile=tile) as b:
+                                                         lambda_tile=tile, lambda_group=group) as b:
         ra, rb = a.loglik_grad(lam), b.loglik_grad(lam)
         ea, eb = ra["lnL_event"].cpu().numpy(), rb["lnL_event"].cpu().numpy()
         fin = np.isfinite(ea)

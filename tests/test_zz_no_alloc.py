@@ -46,8 +46,9 @@ def test_noalloc_matches_context_twice(torch, synth):
             torch.cuda.synchronize()
             r_lnw, r_d, r_c = r_lnw.cpu().numpy(), r_d.cpu().numpy(), r_c.cpu().numpy()
             n_lnw, n_d, n_c = n_lnw.cpu().numpy(), n_d.cpu().numpy(), n_c.cpu().numpy()
-            # the context orders each event's samples by pixel; the caller's order is kept here
-            perm = np.concatenate([order, ns + np.arange(len(cat["inj_m1"]))])
+            # the context orders each event's samples by (pixel, d_L) and the injections by
+            # d_L; the caller's order is kept here
+            perm = np.concatenate([order, ns + g.injection_order(cat)])
             n_lnw, n_d = n_lnw[perm], n_d[:, perm]
             np.testing.assert_allclose(n_c, r_c, rtol=1e-12, atol=1e-12)
             fin = np.isfinite(r_lnw)
