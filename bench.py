@@ -191,6 +191,42 @@ def cpu_baseline(cat, lam, max_seconds=20.0):
                        f"+ the first {n_inj} injections), FP64 value+gradient, {dt:.1f} s")
 
 
+# HMC on the small workload (10 events x 1000 samples, 1e4 injection draws): one chain,
+# trajectories of 32 leapfrog steps recorded as one CUDA graph; M^-1 = diag(scale^2)
+HMC_SCALE = np.array([2.0, 0.1, 0.5, 0.5, 0.5, 5.0, 0.5, 2.0, 1.0, 0.02, 0.5, 2.0, 0.5])
+HMC_LEAPFROG, HMC_EPS, HMC_TRAJ, HMC_WARM = 32, 0.005, 20, 10
+
+
+def hmc_c1(g, synth, stream):
+    import torch
+    cat = synth.catalogue("c1")
+    n = len(cat["m1"]) + len(cat["inj_m1"])
+    r = np.random.default_rng(5)
+    with g.Context(cat, max_K=1) as ctx:
+        h = ctx.hmc(1, HMC_LEAPFROG, np.full(1, HMC_EPS), HMC_SCALE ** 2)
+        q = torch.tensor(synth.FIDUCIAL[None, :], device="cuda")
+        h.q.copy_(q)
+        p = torch.tensor(r.standard_normal((HMC_TRAJ + HMC_WARM, 1, 13)) / HMC_SCALE, device="cuda")
+        lu = torch.tensor(np.log(r.random((HMC_TRAJ + HMC_WARM, 1))), device="cuda")
+        for t in range(HMC_WARM):   # the first replays of a new graph are slow
+            h.run(None, p[t], lu[t], stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        e0.record(stream)
+        for t in range(HMC_TRAJ):
+            h.run(None, p[t + HMC_WARM], lu[t + HMC_WARM], stream)
+            acc += h.accept
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / HMC_TRAJ
+        h.close()
+    return {"workload": "c1 (10 events x 1000 samples, 1e4 draws), K = 1",
+            "leapfrog_steps": HMC_LEAPFROG, "ms_per_trajectory": ms,
+            "evals_per_s": (HMC_LEAPFROG + 1) * n / (ms / 1e3),
+            "acceptance": float(acc.item()) / HMC_TRAJ}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, one bounded sample per step."""
     world, rank, _ = dist_setup()
@@ -240,6 +276,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=["c2", "c3", "c5"],
                     help="catalogue size (c3 = the O5-scale headline; c2 for small profiling cases)")
     ap.add_argument("--K", type=int, default=K_LAMBDA, help="Lambda points per call")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the value+gradient step (no value-only, plain or e2e legs)")
     args = ap.parse_args()
@@ -279,6 +316,9 @@ def main():
     lam = torch.tensor(lam_np, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     out = g._outputs(K, ctx.n_events, lam.device, True)
+    # pick the launch shape (chunk, Lambda tile, warp group) on this batch, untimed
+    tune = None if args.no_tune else ctx.autotune(lam, grad=True, stream=stream)
+    info = ctx.info()
 
     def step():
         g.loglik_grad(ctx._ctx, lam, ctx.n_events, stream, out)
@@ -312,7 +352,7 @@ def main():
     roof = alu_roofline(evals_step, fused_ms / 1e3)
     roof["traffic"] = traffic_for(args.workload, K)
 
-    value_only = plain = e2e = None
+    value_only = plain = e2e = graph_line = hmc_line = None
     if not args.no_extras:
         # value-only throughput (same batch)
         outv = g._outputs(K, ctx.n_events, lam.device, False)
@@ -340,6 +380,21 @@ def main():
         barrier()
         plain = (n_s + n_i) * kp * psteps / (ev0.elapsed_time(ev1) / 1e3)
 
+        # the same call recorded once as a CUDA graph and replayed
+        lam_g = lam.clone()
+        graph = ctx.graph(lam_g, grad=True)
+        for _ in range(2):
+            graph.launch(stream)
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            graph.launch(stream)
+        ev1.record(stream)
+        barrier()
+        g_ms = ev0.elapsed_time(ev1) / args.steps
+        graph_line = {"value": evals_step / (g_ms / 1e3), "unit": "evals/s", "ms_per_step": g_ms}
+        graph.close()
+
         # end to end through the host-memory entry point (Lambda in, totals and gradient out)
         for _ in range(2):
             ctx.loglik_grad_host(lam_np)
@@ -351,6 +406,9 @@ def main():
         e2e = {"value": evals_step * args.steps / e2e_s, "unit": "evals/s",
                "h2d_bytes_per_step": K * 13 * 8,
                "d2h_bytes_per_step": K * 8 + K * 4 + K * 13 * 8}
+
+    if not args.no_extras:
+        hmc_line = hmc_c1(g, synth, stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
@@ -370,7 +428,10 @@ def main():
                        "evals_per_step": evals_step, "parallelism": f"lambda-batch x{world}",
                        "l2": "inputs larger than L2 (resident catalogue %.2f GB), no flush"
                              % (info["device_bytes"] / 1e9),
-                       "chunk": info["chunk"], "n_items": info["n_items"]},
+                       "chunk": info["chunk"], "n_items": info["n_items"],
+                       "lambda_tile": None if tune is None else tune["lambda_tile"],
+                       "lambda_group": None if tune is None else tune["lambda_group"],
+                       "autotuned": tune is not None},
             "roofline": roof,
             "stage_ms_per_step": {"prologue": stage_ms[0] / max(n_calls, 1), "fused": fused_ms,
                                   "merge": stage_ms[2] / max(n_calls, 1)},
@@ -384,6 +445,8 @@ def main():
             line["plain_gpu"] = {"value": plain, "unit": "evals/s", "K": kp,
                                  "speedup": value / world / plain}
             line["e2e"] = e2e
+            line["graph"] = graph_line
+            line["hmc_c1"] = hmc_line
         if clocks is not None:
             line["clocks"] = clocks
         if base is not None:

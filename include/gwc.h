@@ -164,6 +164,72 @@ gwc_status gwc_loglik_grad_host(gwc_ctx* ctx, int32_t K, const double* h_lambda,
                                 double* h_lnL_total, int32_t* h_flags, double* h_grad_total,
                                 void* stream);
 
+/* A recorded call.  gwc_graph_create records one gwc_loglik (want_grad = 0) or
+ * gwc_loglik_grad (want_grad = 1) call on the given device pointers as a CUDA graph --
+ * the prologue, the persistent fused kernel and the merge, three kernel nodes -- and
+ * gwc_graph_launch replays it on a stream.  A replay reads the current contents of
+ * d_lambda, so a sampler writes its next K points there and replays; the outputs are the
+ * same as a direct call's.  The paper has no counterpart: it serves callers that issue
+ * many calls of one shape (a sampler's steps), where the launch sequence is recorded
+ * once.  The graph uses the context's per-call scratch: replays of graphs of one context
+ * must not overlap (one stream at a time), and every graph must be destroyed before its
+ * context (a replay after gwc_destroy fails with GWC_E_INVALID).  Profiling events are
+ * not recorded inside graphs.  want_grad = 0 ignores d_grad_total. */
+typedef struct gwc_graph gwc_graph;
+gwc_status gwc_graph_create(gwc_ctx* ctx, int32_t K, const double* d_lambda, int32_t want_grad,
+                            double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
+                            double* d_neff_sel, double* d_lnL_total, int32_t* d_flags,
+                            double* d_grad_total, gwc_graph** out);
+gwc_status gwc_graph_launch(gwc_graph* graph, void* stream);
+void gwc_graph_destroy(gwc_graph* graph);   /* NULL is a no-op */
+
+/* One Hamiltonian Monte Carlo trajectory for K independent chains, recorded once as a
+ * CUDA graph and replayed by gwc_hmc_launch.  The paper samples with nested sampling
+ * and has no counterpart; this uses the gradient of gwc_loglik_grad for the leapfrog
+ * integrator of HMC (Duane et al. 1987; Neal 2011, "MCMC using Hamiltonian dynamics").
+ * With M^-1 = diag(d_inv_mass[13]) and step eps_k = d_eps[k], a replay evaluates lnL and
+ * its gradient at q, takes n_leapfrog leapfrog steps
+ *     p += eps/2 grad lnL(q);  q += eps M^-1 p;  p += eps/2 grad lnL(q)
+ * (n_leapfrog + 1 evaluations, the half kicks between steps merged into full ones), and
+ * accepts the end point when log_u_k < H(start) - H(end), H = -lnL + p.M^-1.p / 2.
+ * Device arrays, all caller-owned: d_q[K][13] (in: start; out: the accepted end point or
+ * the start again), d_p[K][13] (in: initial momenta, drawn by the caller from N(0, M);
+ * out: final momenta of the proposal), d_log_u[K] (in: log of uniform(0,1) numbers drawn
+ * by the caller), d_lnL[K] and d_grad[K][13] (out: at the returned point), d_accept[K]
+ * (out: 1 or 0), d_H[K][2] (out: H at the start and the end).  A chain whose path meets
+ * a flagged point (outside the domain, or an N_eff cut) stops moving and is rejected.
+ * The graph holds its own evaluation buffers (allocated here) and uses the context's
+ * per-call scratch: replays must not overlap other calls on the context, and the object
+ * must be destroyed before the context. */
+typedef struct gwc_hmc gwc_hmc;
+gwc_status gwc_hmc_create(gwc_ctx* ctx, int32_t K, int32_t n_leapfrog, const double* d_eps,
+                          const double* d_inv_mass, double* d_q, double* d_p,
+                          const double* d_log_u, double* d_lnL, double* d_grad,
+                          int32_t* d_accept, double* d_H, gwc_hmc** out);
+gwc_status gwc_hmc_launch(gwc_hmc* hmc, void* stream);
+void gwc_hmc_destroy(gwc_hmc* hmc);   /* NULL is a no-op */
+
+/* Launch-shape autotuner.  Times whole calls (gwc_loglik_grad when want_grad != 0,
+ * gwc_loglik otherwise) on the caller's K points d_lambda[K][13] (device) at every
+ * shape of chunk in {1024, 2048} x Lambda tile in {16, 32, 64} (clamped to K) x warp
+ * group in {1, 2, 4, 8}: one untimed call, then two timed with CUDA events on the
+ * stream.  The fastest shape becomes the context's chunk, lambda_tile and lambda_group
+ * for later calls (a new chunk re-splits the work items; results then differ from the
+ * old shape's only by FP32 rounding order).  Synchronises the device, allocates scratch
+ * for the trial outputs, and must not overlap other calls on the context.  Fails with
+ * GWC_E_INVALID while a graph or HMC object of the context exists (their recorded
+ * launches hold the work-item layout).  The paper has no counterpart.  *out (may be NULL) receives the chosen shape, its time per call
+ * and the number of shapes timed. */
+typedef struct {
+  int32_t chunk;
+  int32_t lambda_tile;
+  int32_t lambda_group;
+  int32_t n_tried;
+  double ms;
+} gwc_tune_result;
+gwc_status gwc_autotune(gwc_ctx* ctx, int32_t K, const double* d_lambda, int32_t want_grad,
+                        void* stream, gwc_tune_result* out);
+
 /* Release every resource of the context (NULL is a no-op). */
 void gwc_destroy(gwc_ctx* ctx);
 

@@ -70,10 +70,18 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32),
+                ("lambda_group", ctypes.c_int32), ("n_tried", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
 EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_loglik_plain", "gwc_loglik_grad_host", "gwc_destroy", "gwc_last_error",
            "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read",
-           "gwc_sample_terms", "gwc_sample_terms_noalloc")
+           "gwc_sample_terms", "gwc_sample_terms_noalloc", "gwc_graph_create", "gwc_graph_launch",
+           "gwc_graph_destroy", "gwc_hmc_create", "gwc_hmc_launch", "gwc_hmc_destroy",
+           "gwc_autotune")
 
 
 def lib():
@@ -118,6 +126,22 @@ def lib():
         L.gwc_profile_read.argtypes = [vp, vp, vp]
         L.gwc_los_cell_index.restype = ctypes.c_int
         L.gwc_los_cell_index.argtypes = [vp, i64, i32, d, vp, vp]
+        L.gwc_graph_create.restype = ctypes.c_int
+        L.gwc_graph_create.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(ctypes.c_void_p)]
+        L.gwc_graph_launch.restype = ctypes.c_int
+        L.gwc_graph_launch.argtypes = [vp, vp]
+        L.gwc_graph_destroy.restype = None
+        L.gwc_graph_destroy.argtypes = [vp]
+        L.gwc_hmc_create.restype = ctypes.c_int
+        L.gwc_hmc_create.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+        L.gwc_hmc_launch.restype = ctypes.c_int
+        L.gwc_hmc_launch.argtypes = [vp, vp]
+        L.gwc_hmc_destroy.restype = None
+        L.gwc_hmc_destroy.argtypes = [vp]
+        L.gwc_autotune.restype = ctypes.c_int
+        L.gwc_autotune.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(TuneResult)]
         _lib = L
         return L
 
@@ -334,6 +358,98 @@ def los_cell_index(z, n_z, z_max, stream=None):
     return cell
 
 
+class Graph:
+    """gwc_graph: one recorded gwc_loglik / gwc_loglik_grad call on fixed tensors.
+
+    ``lam`` [K, 13] (CUDA float64) is the input the replays read: write the next points
+    into it (``lam.copy_(...)``) and call ``launch()``; the results land in ``out``.
+    """
+
+    def __init__(self, context, lam, grad=True, out=None):
+        import torch
+        if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64
+                and lam.is_contiguous()):
+            raise TypeError("lam must be a contiguous CUDA float64 tensor of shape [K, 13]")
+        K = lam.shape[0]
+        self.context, self.lam, self.grad = context, lam, grad
+        self.out = out if out is not None else _outputs(K, context.n_events, lam.device, grad)
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        o = self.out
+        h = ctypes.c_void_p()
+        _check(lib().gwc_graph_create(context._ctx, K, p(lam), int(bool(grad)), p(o["lnL_event"]),
+                                      p(o["neff_event"]), p(o["ln_xi"]), p(o["neff_sel"]),
+                                      p(o["lnL_total"]), p(o["flags"]), p(o.get("grad_total")),
+                                      ctypes.byref(h)), context._ctx)
+        self._g = h
+
+    def launch(self, stream=None):
+        if self._g is None:
+            raise GwcError(-1, "graph destroyed")
+        _check(lib().gwc_graph_launch(self._g, _stream_ptr(stream)), None)
+        return self.out
+
+    def close(self):
+        if self._g is not None:
+            lib().gwc_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hmc:
+    """gwc_hmc: one recorded HMC trajectory of n_leapfrog steps for K chains.
+
+    The device tensors q, p, log_u (inputs) and lnL, grad, accept, H (outputs) are owned
+    here; ``run(q, p, log_u)`` copies the inputs in (any of them may be omitted to keep
+    the current contents) and replays the trajectory.  eps [K] and inv_mass [13] are
+    fixed at creation.
+    """
+
+    def __init__(self, context, K, n_leapfrog, eps, inv_mass, device="cuda"):
+        import torch
+        f64 = dict(dtype=torch.float64, device=device)
+        self.context = context
+        self.eps = torch.as_tensor(eps, **f64).reshape(-1).expand(K).contiguous()
+        self.inv_mass = torch.as_tensor(inv_mass, **f64).reshape(NUM_PARAMS).contiguous()
+        self.q = torch.zeros((K, NUM_PARAMS), **f64)
+        self.p = torch.zeros((K, NUM_PARAMS), **f64)
+        self.log_u = torch.zeros(K, **f64)
+        self.lnL = torch.zeros(K, **f64)
+        self.grad = torch.zeros((K, NUM_PARAMS), **f64)
+        self.accept = torch.zeros(K, dtype=torch.int32, device=device)
+        self.H = torch.zeros((K, 2), **f64)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        h = ctypes.c_void_p()
+        _check(lib().gwc_hmc_create(context._ctx, K, n_leapfrog, p(self.eps), p(self.inv_mass),
+                                    p(self.q), p(self.p), p(self.log_u), p(self.lnL), p(self.grad),
+                                    p(self.accept), p(self.H), ctypes.byref(h)), context._ctx)
+        self._h = h
+
+    def run(self, q=None, p=None, log_u=None, stream=None):
+        if self._h is None:
+            raise GwcError(-1, "hmc object destroyed")
+        for dst, src in ((self.q, q), (self.p, p), (self.log_u, log_u)):
+            if src is not None:
+                dst.copy_(src)
+        _check(lib().gwc_hmc_launch(self._h, _stream_ptr(stream)), None)
+        return self
+
+    def close(self):
+        if self._h is not None:
+            lib().gwc_hmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """A gwc_ctx: the catalogue resident on the device, evaluated at Lambda batches."""
 
@@ -362,6 +478,26 @@ class Context:
     def sample_terms(self, lam, grad=True, stream=None):
         info = get_info(self._ctx)
         return sample_terms(self._ctx, lam, info["n_samples"] + info["n_injections"], grad, stream)
+
+    def autotune(self, lam, grad=True, stream=None):
+        """gwc_autotune on the Lambda batch lam [K, 13]: returns the chosen shape."""
+        import torch
+        if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
+            raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
+        lam = lam.contiguous()
+        r = TuneResult()
+        _check(lib().gwc_autotune(self._ctx, lam.shape[0], ctypes.c_void_p(lam.data_ptr()),
+                                  int(bool(grad)), _stream_ptr(stream), ctypes.byref(r)), self._ctx)
+        return {"chunk": r.chunk, "lambda_tile": r.lambda_tile, "lambda_group": r.lambda_group,
+                "n_tried": r.n_tried, "ms": r.ms}
+
+    def hmc(self, K, n_leapfrog, eps, inv_mass):
+        """Record an HMC trajectory of n_leapfrog steps for K chains (see Hmc)."""
+        return Hmc(self, K, n_leapfrog, eps, inv_mass)
+
+    def graph(self, lam, grad=True, out=None):
+        """Record one call on these tensors as a CUDA graph (see Graph)."""
+        return Graph(self, lam, grad, out)
 
     def profile_enable(self, enable=True):
         profile_enable(self._ctx, enable)

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -64,6 +65,14 @@ struct gwc_ctx {
   LamD* ld = nullptr;
   float* tables = nullptr;
   float* partials = nullptr;
+  int32_t* counter = nullptr;   // work counter of the persistent fused kernel
+  int64_t items_cap = 0;        // work items the items/sched/partials buffers hold
+  int live_recordings = 0;      // graphs and HMC objects recorded on this context
+  uint64_t serial = 0;          // distinguishes contexts that reuse an address
+  std::vector<int64_t> h_offsets;   // event offsets (for re-splitting the work items)
+  int n_sms = 0;
+  std::map<uint64_t, int> occupancy;   // fused-kernel CTAs per SM by geometry
+  bool prof_off = false;               // recording a graph or autotuning: no profiling events
   // host-call staging
   double* d_lam = nullptr;
   double* d_out = nullptr;      // lnL_event, neff_event, ln_xi, neff_sel, lnL_total, grad
@@ -114,7 +123,7 @@ void free_all(gwc_ctx* c) {
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   c->prof_ev.clear();
   void* dev[] = {c->smp, c->pix, c->inj, c->los, c->pbar32, c->pbar64, c->items, c->sched,
-                 c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->d_lam, c->d_out,
+                 c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->d_lam, c->d_out,
                  c->d_flags, c->sample_item, c->plain_lw, c->plain_tg};
   for (void* p : dev)
     if (p) cudaFree(p);
@@ -150,7 +159,7 @@ cudaEvent_t prof_event(gwc_ctx* c, int b) {
 }
 
 cudaError_t prof_mark(gwc_ctx* c, int b, cudaStream_t s) {
-  if (c->prof_ev.empty()) return cudaSuccess;
+  if (c->prof_ev.empty() || c->prof_off) return cudaSuccess;
   if (b == 0 && c->prof_used == PROF_SLOTS) {
     cudaError_t r = prof_drain(c);
     if (r != cudaSuccess) return r;
@@ -209,6 +218,39 @@ void split_items(int64_t begin, int64_t count, int chunk, int32_t kind, std::vec
   }
 }
 
+// the work items of a chunk size: each event's samples split evenly into runs of at
+// most chunk, then the injections; the schedule lists them largest first
+struct ItemLayout {
+  std::vector<Item> items;
+  std::vector<int32_t> sched, ev_item0, sample_item;
+  int32_t inj_item0 = 0;
+};
+
+bool make_items(const int64_t* offsets, int32_t ne, int64_t ns, int64_t ni, int chunk, ItemLayout& L) {
+  L = ItemLayout();
+  L.ev_item0.assign((size_t)ne + 1, 0);
+  for (int32_t e = 0; e < ne; ++e) {
+    L.ev_item0[(size_t)e] = (int32_t)L.items.size();
+    split_items(offsets[e], offsets[e + 1] - offsets[e], chunk, 0, L.items);
+  }
+  L.ev_item0[(size_t)ne] = (int32_t)L.items.size();
+  L.inj_item0 = (int32_t)L.items.size();
+  split_items(0, ni, chunk, 1, L.items);
+  if (L.items.size() > 0x7fffffffu) return false;
+  const int32_t n = (int32_t)L.items.size();
+  L.sched.resize((size_t)n);
+  for (int32_t i = 0; i < n; ++i) L.sched[(size_t)i] = i;
+  std::stable_sort(L.sched.begin(), L.sched.end(),
+                   [&](int32_t a, int32_t b) { return L.items[(size_t)a].count > L.items[(size_t)b].count; });
+  L.sample_item.assign((size_t)(ns + ni), 0);
+  for (int32_t i = 0; i < n; ++i) {
+    const Item& it = L.items[(size_t)i];
+    const int64_t base = it.kind == 1 ? ns + it.begin : it.begin;
+    for (int32_t q = 0; q < it.count; ++q) L.sample_item[(size_t)(base + q)] = i;
+  }
+  return true;
+}
+
 // launch geometry of the fused kernel for a batch of K points
 void fused_geometry(const gwc_ctx* c, int K, int& slab, int& n_slabs) {
   slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : 64;
@@ -230,8 +272,10 @@ gwc_status check_call(gwc_ctx* c, int32_t K, const void* lam, const void* lnL_ev
   return GWC_OK;
 }
 
-gwc_status run_prologue(gwc_ctx* c, int K, const double* d_lambda, bool grad, cudaStream_t s) {
+gwc_status run_prologue(gwc_ctx* c, int K, const double* d_lambda, bool grad, cudaStream_t s,
+                        int32_t* counter = nullptr) {
   ProArgs pa;
+  pa.counter = counter;
   pa.lam = d_lambda;
   pa.nx = c->opt.n_x_table;
   pa.nz = c->n_z;
@@ -279,7 +323,7 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
                      int32_t* flags, double* grad_total, bool grad, cudaStream_t s) {
   cudaError_t pe = prof_mark(c, 0, s);
   if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
-  gwc_status st = run_prologue(c, K, d_lambda, grad, s);
+  gwc_status st = run_prologue(c, K, d_lambda, grad, s, c->counter);
   if (st != GWC_OK) return st;
   if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
   int slab, n_slabs;
@@ -304,15 +348,81 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   fa.tables = c->tables;
   fa.tstride = c->tstride;
   fa.partials = c->partials;
-  const long long grid = (long long)c->n_items * n_slabs;
-  if (grid > 0x7fffffffLL) return fail(c, GWC_E_INVALID, "work grid too large");
-  cudaError_t e = launch_fused(fa, grad, c->opt.accum == 1, c->bf16, (int)grid, s);
+  fa.counter = c->counter;
+  const long long units = (long long)c->n_items * n_slabs;
+  if (units > 0x7fffffffLL) return fail(c, GWC_E_INVALID, "work grid too large");
+  // persistent launch: as many CTAs as fit on the GPU at once, each taking units in
+  // schedule order (largest items first) from the counter
+  const bool kahan = c->opt.accum == 1;
+  const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
+                       ((uint64_t)grad << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;
+  auto oc = c->occupancy.find(key);
+  int bps = 0;
+  if (oc == c->occupancy.end()) {
+    cudaError_t oe = fused_blocks_per_sm(fa, grad, kahan, c->bf16, &bps);
+    if (oe != cudaSuccess) return cuda_fail(c, oe, "occupancy query");
+    if (bps < 1) return fail(c, GWC_E_UNSUPPORTED, "the fused kernel does not fit on an SM at this geometry");
+    c->occupancy[key] = bps;
+  } else {
+    bps = oc->second;
+  }
+  const long long grid = std::max(1LL, std::min(units, (long long)c->n_sms * bps));
+  cudaError_t e = launch_fused(fa, grad, kahan, c->bf16, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "sample kernel launch");
   if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
   st = run_merge(c, K, 1, grad, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, flags,
                  grad_total, s);
   if (st != GWC_OK) return st;
   if ((e = prof_mark(c, 3, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
+  return GWC_OK;
+}
+
+// Switch the context to another chunk size: re-split the work items and upload them
+// (growing the item and partial buffers when needed).  The caller has synchronised.
+gwc_status set_chunk(gwc_ctx* c, int chunk) {
+  if (chunk == c->opt.chunk) return GWC_OK;
+  ItemLayout lay;
+  if (!make_items(c->h_offsets.data(), c->n_events, c->n_samples, c->n_inj, chunk, lay))
+    return fail(c, GWC_E_INVALID, "too many work items");
+  const int64_t n = (int64_t)lay.items.size();
+  if (n > c->items_cap) {
+    Item* it = nullptr;
+    int32_t* sc = nullptr;
+    float* pa = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&it), sizeof(Item) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sc), sizeof(int32_t) * (size_t)n);
+    if (e == cudaSuccess)
+      e = cudaMalloc(reinterpret_cast<void**>(&pa), sizeof(float) * (size_t)c->opt.max_K * (size_t)n * PSTRIDE);
+    if (e != cudaSuccess) {
+      if (it) cudaFree(it);
+      if (sc) cudaFree(sc);
+      cudaGetLastError();
+      return fail(c, e == cudaErrorMemoryAllocation ? GWC_E_NOMEM : GWC_E_CUDA,
+                  std::string("work-item buffers: ") + cudaGetErrorString(e));
+    }
+    cudaFree(c->items);
+    cudaFree(c->sched);
+    cudaFree(c->partials);
+    c->device_bytes += (n - c->items_cap) * (int64_t)(sizeof(Item) + sizeof(int32_t) +
+                                                      sizeof(float) * (size_t)c->opt.max_K * PSTRIDE);
+    c->items = it;
+    c->sched = sc;
+    c->partials = pa;
+    c->items_cap = n;
+  }
+  cudaError_t e = cudaMemcpy(c->items, lay.items.data(), sizeof(Item) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->sched, lay.sched.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->ev_item0, lay.ev_item0.data(), sizeof(int32_t) * lay.ev_item0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->sample_item)
+    e = cudaMemcpy(c->sample_item, lay.sample_item.data(), sizeof(int32_t) * lay.sample_item.size(),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "work-item upload");
+  c->n_items = (int32_t)n;
+  c->inj_item0 = lay.inj_item0;
+  c->h_sample_item = std::move(lay.sample_item);
+  c->opt.chunk = chunk;
   return GWC_OK;
 }
 
@@ -455,29 +565,21 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
       h_inj[(size_t)q] = make_float4(inj->m1_det[k], inj->m2_det[k], inj->dl_mpc[k], inj->ln_p_draw[k]);
     }
   }
-  std::vector<Item> items;
-  std::vector<int32_t> ev_item0((size_t)ne + 1);
   std::vector<double> ev_n((size_t)std::max(ne, 1));
-  for (int32_t e = 0; e < ne; ++e) {
-    ev_item0[(size_t)e] = (int32_t)items.size();
-    split_items(ev->offsets[e], ev->offsets[e + 1] - ev->offsets[e], o.chunk, 0, items);
-    ev_n[(size_t)e] = (double)(ev->offsets[e + 1] - ev->offsets[e]);
+  for (int32_t e = 0; e < ne; ++e) ev_n[(size_t)e] = (double)(ev->offsets[e + 1] - ev->offsets[e]);
+  c->h_offsets.assign(ev->offsets, ev->offsets + (size_t)ne + 1);
+  ItemLayout lay;
+  if (!make_items(ev->offsets, ne, ns, ni, o.chunk, lay)) {
+    delete c;
+    return fail(nullptr, GWC_E_INVALID, "too many work items");
   }
-  ev_item0[(size_t)ne] = (int32_t)items.size();
-  c->inj_item0 = (int32_t)items.size();
-  split_items(0, ni, o.chunk, 1, items);
-  if (items.size() > 0x7fffffffu) { delete c; return fail(nullptr, GWC_E_INVALID, "too many work items"); }
-  c->n_items = (int32_t)items.size();
-  std::vector<int32_t> sched((size_t)c->n_items);
-  for (int32_t i = 0; i < c->n_items; ++i) sched[(size_t)i] = i;
-  std::stable_sort(sched.begin(), sched.end(),
-                   [&](int32_t a, int32_t b) { return items[(size_t)a].count > items[(size_t)b].count; });
-  c->h_sample_item.assign((size_t)(ns + ni), 0);
-  for (int32_t i = 0; i < c->n_items; ++i) {
-    const Item& it = items[(size_t)i];
-    const int64_t base = it.kind == 1 ? ns + it.begin : it.begin;
-    for (int32_t q = 0; q < it.count; ++q) c->h_sample_item[(size_t)(base + q)] = i;
-  }
+  c->n_items = (int32_t)lay.items.size();
+  c->items_cap = c->n_items;
+  c->inj_item0 = lay.inj_item0;
+  c->h_sample_item = std::move(lay.sample_item);
+  const std::vector<Item>& items = lay.items;
+  const std::vector<int32_t>& sched = lay.sched;
+  const std::vector<int32_t>& ev_item0 = lay.ev_item0;
   // pixel mean of the LOS rows (the selection term's redshift prior)
   std::vector<double> pbar((size_t)c->n_z, 0.0);
   for (int32_t p = 0; p < c->n_pix; ++p)
@@ -514,6 +616,8 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(dalloc(c, &c->ld, (size_t)o.max_K));
   chk(dalloc(c, &c->tables, (size_t)o.max_K * c->tstride));
   chk(dalloc(c, &c->partials, (size_t)kcap * c->n_items * PSTRIDE));
+  chk(dalloc(c, &c->counter, 1));
+  chk(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device));
   chk(dalloc(c, &c->d_lam, (size_t)o.max_K * NP));
   chk(dalloc(c, &c->d_out, (size_t)o.max_K * (2 * (size_t)std::max(ne, 1) + 3 + NP)));
   chk(dalloc(c, &c->d_flags, (size_t)o.max_K));
@@ -555,6 +659,8 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   }
   {
     std::lock_guard<std::mutex> g(g_mu);
+    static uint64_t next_serial = 0;
+    c->serial = ++next_serial;
     g_live.insert(c);
   }
   *out = c;
@@ -750,6 +856,389 @@ gwc_status gwc_sample_terms(gwc_ctx* c, const double* d_lambda, float* d_lnw, fl
   ta.c = d_c;
   cudaError_t e = launch_sample_terms(ta, c->bf16, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "sample-terms launch");
+  return GWC_OK;
+}
+
+struct gwc_graph {
+  uint32_t magic = 0x67776367u;   // "gwcg"
+  gwc_ctx* ctx = nullptr;
+  uint64_t serial = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+std::set<const gwc_graph*> g_graphs;
+bool graph_live(const gwc_graph* g) {
+  std::lock_guard<std::mutex> l(g_mu);
+  return g && g_graphs.count(g) && g->magic == 0x67776367u;
+}
+}  // namespace
+
+gwc_status gwc_graph_create(gwc_ctx* c, int32_t K, const double* d_lambda, int32_t want_grad,
+                            double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
+                            double* d_neff_sel, double* d_lnL_total, int32_t* d_flags,
+                            double* d_grad_total, gwc_graph** out) {
+  if (!out) return fail(c, GWC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  gwc_status st = check_call(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel,
+                             d_lnL_total, d_flags);
+  if (st != GWC_OK) return st;
+  if (want_grad && !d_grad_total) return fail(c, GWC_E_INVALID, "d_grad_total is NULL");
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+  // warm the occupancy cache outside the capture (it may set a kernel attribute)
+  {
+    int slab, n_slabs;
+    fused_geometry(c, K, slab, n_slabs);
+    FusedArgs fa{};
+    fa.chunk = c->opt.chunk;
+    fa.slab = slab;
+    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : 2;
+    const bool grad = want_grad != 0, kahan = c->opt.accum == 1;
+    const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
+                         ((uint64_t)grad << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;
+    if (!c->occupancy.count(key)) {
+      int bps = 0;
+      e = fused_blocks_per_sm(fa, grad, kahan, c->bf16, &bps);
+      if (e != cudaSuccess || bps < 1) {
+        cudaStreamDestroy(cs);
+        return e != cudaSuccess ? cuda_fail(c, e, "occupancy query")
+                                : fail(c, GWC_E_UNSUPPORTED, "the fused kernel does not fit on an SM");
+      }
+      c->occupancy[key] = bps;
+    }
+  }
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(c, e, "begin capture");
+  }
+  c->prof_off = true;
+  st = run_fused(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel, d_lnL_total,
+                 d_flags, want_grad ? d_grad_total : nullptr, want_grad != 0, cs);
+  c->prof_off = false;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (st != GWC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  gwc_graph* g = new (std::nothrow) gwc_graph;
+  if (!g) {
+    cudaGraphDestroy(graph);
+    return fail(c, GWC_E_NOMEM, "graph handle");
+  }
+  g->ctx = c;
+  g->serial = c->serial;
+  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(c, e, "graph instantiate");
+  }
+  {
+    std::lock_guard<std::mutex> l(g_mu);
+    g_graphs.insert(g);
+    ++c->live_recordings;
+  }
+  *out = g;
+  return GWC_OK;
+}
+
+gwc_status gwc_graph_launch(gwc_graph* g, void* stream) {
+  if (!graph_live(g)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed graph");
+  gwc_ctx* c = g->ctx;
+  if (!live(c) || c->serial != g->serial) return fail(nullptr, GWC_E_INVALID, "the graph's context was destroyed");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  return GWC_OK;
+}
+
+void gwc_graph_destroy(gwc_graph* g) {
+  {
+    std::lock_guard<std::mutex> l(g_mu);
+    if (!g || !g_graphs.count(g)) return;
+    g_graphs.erase(g);
+    if (g_live.count(g->ctx) && g->ctx->serial == g->serial) --g->ctx->live_recordings;
+  }
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->magic = 0;
+  delete g;
+}
+
+struct gwc_hmc {
+  uint32_t magic = 0x67776368u;   // "gwch"
+  gwc_ctx* ctx = nullptr;
+  uint64_t serial = 0;
+  cudaGraphExec_t exec = nullptr;
+  void* mem = nullptr;            // one device block: evaluation outputs and scratch
+};
+
+namespace {
+std::set<const gwc_hmc*> g_hmcs;
+bool hmc_live(const gwc_hmc* h) {
+  std::lock_guard<std::mutex> l(g_mu);
+  return h && g_hmcs.count(h) && h->magic == 0x67776368u;
+}
+}  // namespace
+
+gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const double* d_eps,
+                          const double* d_inv_mass, double* d_q, double* d_p,
+                          const double* d_log_u, double* d_lnL, double* d_grad,
+                          int32_t* d_accept, double* d_H, gwc_hmc** out) {
+  if (!out) return fail(c, GWC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
+  if (K < 1 || K > c->opt.max_K)
+    return fail(c, GWC_E_INVALID, "K must be in [1, max_K] (max_K = " + std::to_string(c->opt.max_K) + ")");
+  if (n_leapfrog < 1 || n_leapfrog > 4096) return fail(c, GWC_E_INVALID, "n_leapfrog must be in [1, 4096]");
+  if (!d_eps || !d_inv_mass || !d_q || !d_p || !d_log_u || !d_lnL || !d_grad || !d_accept || !d_H)
+    return fail(c, GWC_E_INVALID, "NULL device pointer");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  gwc_hmc* h = new (std::nothrow) gwc_hmc;
+  if (!h) return fail(c, GWC_E_NOMEM, "hmc handle");
+  h->ctx = c;
+  h->serial = c->serial;
+  // device block: lnL_event, neff_event [K][n_ev]; ln_xi, neff_sel, lnL_total, lnL0 [K];
+  // grad_total, q0, grad0 [K][13]; flags, div [K]
+  const size_t ne = (size_t)std::max(c->n_events, 1);
+  const size_t nd = 2 * (size_t)K * ne + 4 * (size_t)K + 3 * (size_t)K * NP;
+  cudaError_t e = cudaMalloc(&h->mem, nd * sizeof(double) + 2 * (size_t)K * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    delete h;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? GWC_E_NOMEM : GWC_E_CUDA,
+                std::string("hmc scratch: ") + cudaGetErrorString(e));
+  }
+  double* m = static_cast<double*>(h->mem);
+  double* lnL_event = m; m += (size_t)K * ne;
+  double* neff_event = m; m += (size_t)K * ne;
+  double* ln_xi = m; m += K;
+  double* neff_sel = m; m += K;
+  double* lnL_total = m; m += K;
+  double* lnL0 = m; m += K;
+  double* grad_total = m; m += (size_t)K * NP;
+  double* q0 = m; m += (size_t)K * NP;
+  double* grad0 = m; m += (size_t)K * NP;
+  int32_t* flags = reinterpret_cast<int32_t*>(m);
+  int32_t* div = flags + K;
+
+  HmcArgs ha;
+  ha.K = K;
+  ha.eps = d_eps;
+  ha.inv_mass = d_inv_mass;
+  ha.q = d_q;
+  ha.p = d_p;
+  ha.q0 = q0;
+  ha.lnL0 = lnL0;
+  ha.grad0 = grad0;
+  ha.div = div;
+  ha.lnL = lnL_total;
+  ha.grad = grad_total;
+  ha.flags = flags;
+  ha.log_u = d_log_u;
+  ha.H = d_H;
+  ha.accept = d_accept;
+  ha.lnL_out = d_lnL;
+  ha.grad_out = d_grad;
+
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(h->mem);
+    delete h;
+    return cuda_fail(c, e, "capture stream");
+  }
+  // occupancy of the gradient kernel, outside the capture
+  gwc_status st = GWC_OK;
+  {
+    int slab, n_slabs;
+    fused_geometry(c, K, slab, n_slabs);
+    FusedArgs fa{};
+    fa.chunk = c->opt.chunk;
+    fa.slab = slab;
+    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : 2;
+    const bool kahan = c->opt.accum == 1;
+    const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
+                         (1ull << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;
+    if (!c->occupancy.count(key)) {
+      int bps = 0;
+      e = fused_blocks_per_sm(fa, true, kahan, c->bf16, &bps);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "occupancy query");
+      else if (bps < 1) st = fail(c, GWC_E_UNSUPPORTED, "the fused kernel does not fit on an SM");
+      else c->occupancy[key] = bps;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  if (st == GWC_OK) {
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "begin capture");
+  }
+  if (st == GWC_OK) {
+    c->prof_off = true;
+    auto eval = [&]() {
+      return run_fused(c, K, d_q, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, flags,
+                       grad_total, true, cs);
+    };
+    auto stage = [&](int mode) {
+      ha.mode = mode;
+      cudaError_t r = launch_hmc(ha, cs);
+      return r == cudaSuccess ? GWC_OK : cuda_fail(c, r, "leapfrog launch");
+    };
+    st = stage(0);
+    if (st == GWC_OK) st = eval();
+    if (st == GWC_OK) st = stage(1);
+    for (int l = 1; l < n_leapfrog && st == GWC_OK; ++l) {
+      st = eval();
+      if (st == GWC_OK) st = stage(2);
+    }
+    if (st == GWC_OK) st = eval();
+    if (st == GWC_OK) st = stage(3);
+    c->prof_off = false;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (st == GWC_OK && e != cudaSuccess) st = cuda_fail(c, e, "end capture");
+  }
+  cudaStreamDestroy(cs);
+  if (st == GWC_OK) {
+    e = cudaGraphInstantiate(&h->exec, graph, 0);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "graph instantiate");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (st != GWC_OK) {
+    cudaFree(h->mem);
+    delete h;
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> l(g_mu);
+    g_hmcs.insert(h);
+    ++c->live_recordings;
+  }
+  *out = h;
+  return GWC_OK;
+}
+
+gwc_status gwc_hmc_launch(gwc_hmc* h, void* stream) {
+  if (!hmc_live(h)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed hmc object");
+  gwc_ctx* c = h->ctx;
+  if (!live(c) || c->serial != h->serial) return fail(nullptr, GWC_E_INVALID, "the hmc object's context was destroyed");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "trajectory launch");
+  return GWC_OK;
+}
+
+void gwc_hmc_destroy(gwc_hmc* h) {
+  {
+    std::lock_guard<std::mutex> l(g_mu);
+    if (!h || !g_hmcs.count(h)) return;
+    g_hmcs.erase(h);
+    if (g_live.count(h->ctx) && h->ctx->serial == h->serial) --h->ctx->live_recordings;
+  }
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->mem) cudaFree(h->mem);
+  h->magic = 0;
+  delete h;
+}
+
+gwc_status gwc_autotune(gwc_ctx* c, int32_t K, const double* d_lambda, int32_t want_grad,
+                        void* stream, gwc_tune_result* out) {
+  if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
+  if (K < 1 || K > c->opt.max_K)
+    return fail(c, GWC_E_INVALID, "K must be in [1, max_K] (max_K = " + std::to_string(c->opt.max_K) + ")");
+  if (!d_lambda) return fail(c, GWC_E_INVALID, "d_lambda is NULL");
+  {
+    std::lock_guard<std::mutex> l(g_mu);
+    if (c->live_recordings > 0)
+      return fail(c, GWC_E_INVALID, "destroy the context's graphs and HMC objects before tuning");
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronise before tuning");
+  const size_t ne = (size_t)std::max(c->n_events, 1);
+  double* tmp = nullptr;
+  int32_t* fl = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMalloc(reinterpret_cast<void**>(&tmp), sizeof(double) * (2 * (size_t)K * ne + 3 * (size_t)K + (size_t)K * NP));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&fl), sizeof(int32_t) * (size_t)K);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto release = [&]() {
+    if (tmp) cudaFree(tmp);
+    if (fl) cudaFree(fl);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (e != cudaSuccess) {
+    release();
+    cudaGetLastError();
+    return cuda_fail(c, e, "tuning scratch");
+  }
+  double* lnL_event = tmp;
+  double* neff_event = lnL_event + (size_t)K * ne;
+  double* ln_xi = neff_event + (size_t)K * ne;
+  double* neff_sel = ln_xi + K;
+  double* lnL_total = neff_sel + K;
+  double* grad = lnL_total + K;
+  const bool g = want_grad != 0;
+  const gwc_options keep = c->opt;
+  gwc_tune_result best{keep.chunk, keep.lambda_tile, keep.lambda_group, 0, INFINITY};
+  int n_tried = 0;
+  gwc_status st = GWC_OK;
+  c->prof_off = true;
+  const int chunks[] = {1024, 2048};
+  const int tiles[] = {16, 32, 64};
+  const int groups[] = {1, 2, 4, 8};
+  for (int chunk : chunks) {
+    if (st != GWC_OK) break;
+    st = set_chunk(c, chunk);
+    int last_tile = -1;
+    for (int tile : tiles) {
+      const int t = std::min(tile, (int)K);
+      if (st != GWC_OK || t == last_tile) continue;
+      last_tile = t;
+      for (int grp : groups) {
+        c->opt.lambda_tile = t;
+        c->opt.lambda_group = grp;
+        auto run = [&]() {
+          return run_fused(c, K, d_lambda, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, fl,
+                           g ? grad : nullptr, g, s);
+        };
+        st = run();
+        if (st == GWC_OK && (e = cudaEventRecord(e0, s)) != cudaSuccess) st = cuda_fail(c, e, "event");
+        if (st == GWC_OK) st = run();
+        if (st == GWC_OK) st = run();
+        if (st == GWC_OK && (e = cudaEventRecord(e1, s)) != cudaSuccess) st = cuda_fail(c, e, "event");
+        float ms = 0.f;
+        if (st == GWC_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(c, e, "tuning run");
+        if (st == GWC_OK && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) st = cuda_fail(c, e, "event");
+        if (st != GWC_OK) break;
+        ++n_tried;
+        if (0.5 * ms < best.ms) best = gwc_tune_result{chunk, t, grp, 0, 0.5 * (double)ms};
+      }
+    }
+  }
+  c->prof_off = false;
+  release();
+  if (st != GWC_OK) {
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    set_chunk(c, keep.chunk);
+    c->opt.lambda_tile = keep.lambda_tile;
+    c->opt.lambda_group = keep.lambda_group;
+    return st;
+  }
+  st = set_chunk(c, best.chunk);
+  if (st != GWC_OK) return st;
+  c->opt.lambda_tile = best.lambda_tile;
+  c->opt.lambda_group = best.lambda_group;
+  best.n_tried = n_tried;
+  if (out) *out = best;
   return GWC_OK;
 }
 

@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   __shared__ double sc[32];                      // scalar broadcast
 
   const int k = blockIdx.x, tid = threadIdx.x;
+  if (k == 0 && tid == 0 && A.counter) *A.counter = 0;
   const double* L = A.lam + (size_t)k * NP;
   LamF* lf = A.lf + k;
   LamD* ld = A.ld + k;
@@ -477,9 +478,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
 // gradient kernel two (<= 128); three would force the 13 gradient sums to spill.
 constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
 
+// One (item, Lambda-slab) unit: stage the item's samples, sweep them for the slab's
+// Lambda points, combine the warp groups' sums into the unit's partials.
 template <bool GRAD, bool KAHAN, typename RowT>
-__global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fused(FusedArgs A) {
-  extern __shared__ __align__(16) float sm[];
+__device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* sm) {
   const int CH = A.chunk;
   float* s_m1 = sm;
   float* s_m2 = s_m1 + CH;
@@ -493,7 +495,6 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = A.group, ngroups = WARPS / G;
   const int gidx = warp / G, wg = warp - gidx * G;
-  const int unit = blockIdx.x;
   const int ipos = unit / A.n_slabs, slab = unit - ipos * A.n_slabs;
   const int item = A.sched[ipos];
   const Item it = A.items[item];
@@ -603,6 +604,23 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
       out[16] = MO;
       out[17] = so;
     }
+  }
+}
+
+template <bool GRAD, bool KAHAN, typename RowT>
+__global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fused(const __grid_constant__ FusedArgs A) {
+  extern __shared__ __align__(16) float sm[];
+  // persistent: each CTA takes (item, Lambda-slab) units from the counter until none
+  // is left; the counter is zeroed by the prologue of the same call
+  __shared__ int s_unit;
+  const int n_units = A.n_items * A.n_slabs;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(A.counter, 1);
+    __syncthreads();
+    const int unit = s_unit;
+    if (unit >= n_units) break;
+    fused_unit<GRAD, KAHAN, RowT>(A, unit, sm);
+    __syncthreads();   // the combine has read s_part before the next unit restages
   }
 }
 
@@ -980,6 +998,14 @@ static cudaError_t launch_fused_t(const FusedArgs& a, int grid, size_t smem, cud
   return cudaGetLastError();
 }
 
+template <bool G, bool KH, typename RT>
+static cudaError_t occupancy_t(size_t smem, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(k_fused<G, KH, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fused_smem_max());
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_fused<G, KH, RT>, THREADS, smem);
+}
+
 size_t fused_smem_bytes(int chunk, int slab, int group) {
   return (size_t)chunk * 7 * sizeof(float) + (size_t)slab * group * PSTRIDE * sizeof(float);
 }
@@ -997,6 +1023,81 @@ cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, i
                          : launch_fused_t<false, true, float>(a, grid, smem, s);
   return bf16 ? launch_fused_t<false, false, __nv_bfloat16>(a, grid, smem, s)
               : launch_fused_t<false, false, float>(a, grid, smem, s);
+}
+
+cudaError_t fused_blocks_per_sm(const FusedArgs& a, bool grad, bool kahan, bool bf16, int* out) {
+  const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
+  if (grad) {
+    if (kahan) return bf16 ? occupancy_t<true, true, __nv_bfloat16>(smem, out) : occupancy_t<true, true, float>(smem, out);
+    return bf16 ? occupancy_t<true, false, __nv_bfloat16>(smem, out) : occupancy_t<true, false, float>(smem, out);
+  }
+  if (kahan) return bf16 ? occupancy_t<false, true, __nv_bfloat16>(smem, out) : occupancy_t<false, true, float>(smem, out);
+  return bf16 ? occupancy_t<false, false, __nv_bfloat16>(smem, out) : occupancy_t<false, false, float>(smem, out);
+}
+
+// ------------------------------------------------------------------ HMC leapfrog
+__global__ void __launch_bounds__(32) k_hmc(HmcArgs A) {
+  const int k = blockIdx.x, i = threadIdx.x;
+  const bool on = i < NP;
+  const size_t o = (size_t)k * NP + (on ? i : 0);
+  if (A.mode == 0) {
+    if (on) A.q0[o] = A.q[o];
+    if (i == 0) A.div[k] = 0;
+    return;
+  }
+  const bool bad = A.flags[k] != 0 || !(A.lnL[k] > -INFINITY);
+  int div = A.div[k] | (bad ? 1 : 0);
+  const double eps = A.eps[k];
+  const double im = on ? A.inv_mass[i] : 0.0;
+  double p = on ? A.p[o] : 0.0;
+  const double g = on ? A.grad[o] : 0.0;
+  auto kinetic = [&](double pv) {
+    double t = on ? 0.5 * im * pv * pv : 0.0;
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    return t;
+  };
+  if (A.mode == 1) {
+    if (on) A.grad0[o] = g;
+    const double ke = kinetic(p);
+    if (i == 0) {
+      A.lnL0[k] = A.lnL[k];
+      A.H[(size_t)k * 2] = div ? INFINITY : -A.lnL[k] + ke;
+    }
+  }
+  if (A.mode == 1 || A.mode == 2) {
+    if (!div && on) {
+      p += (A.mode == 1 ? 0.5 : 1.0) * eps * g;
+      A.p[o] = p;
+      A.q[o] += eps * im * p;
+    }
+    if (i == 0) A.div[k] = div;
+    return;
+  }
+  // mode 3: close the trajectory and accept or reject
+  if (!div && on) {
+    p += 0.5 * eps * g;
+    A.p[o] = p;
+  }
+  const double ke = kinetic(p);
+  const double H1 = div ? INFINITY : -A.lnL[k] + ke;
+  const double H0 = A.H[(size_t)k * 2];
+  const bool acc = !div && H0 < INFINITY && A.log_u[k] < H0 - H1;
+  if (on) {
+    if (!acc) A.q[o] = A.q0[o];
+    A.grad_out[o] = acc ? g : A.grad0[o];
+  }
+  if (i == 0) {
+    A.H[(size_t)k * 2 + 1] = H1;
+    A.accept[k] = acc ? 1 : 0;
+    A.lnL_out[k] = acc ? A.lnL[k] : A.lnL0[k];
+    A.div[k] = div;
+  }
+}
+
+cudaError_t launch_hmc(const HmcArgs& a, cudaStream_t s) {
+  if (a.K <= 0) return cudaSuccess;
+  k_hmc<<<a.K, 32, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_plain_sample(const PlainArgs& a, bool grad, bool bf16, cudaStream_t s) {

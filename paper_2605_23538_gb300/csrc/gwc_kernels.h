@@ -21,6 +21,7 @@ struct ProArgs {
   float* tables;          // [K][tstride]
   int tstride;
   int want_grad;
+  int* counter = nullptr;   // zeroed by CTA 0 when set (the fused kernel's work counter)
 };
 
 struct FusedArgs {
@@ -43,6 +44,7 @@ struct FusedArgs {
   const float* tables;
   int tstride;
   float* partials;        // [K][n_items][PSTRIDE]
+  int* counter;           // next (item, slab) unit; zero at launch
 };
 
 struct PlainArgs {
@@ -88,12 +90,40 @@ struct MergeArgs {
   double* grad_total;
 };
 
+// One leapfrog stage of K Hamiltonian Monte Carlo chains (one warp per chain, a lane
+// per parameter).  mode 0: save q0, clear the divergence mark.  1: after the evaluation
+// at q0: record lnL0, grad0 and H0 = -lnL + p.M^-1.p / 2, then half kick and drift.
+// 2: full kick and drift.  3: final half kick, H1, and the Metropolis decision.
+struct HmcArgs {
+  int K;
+  int mode;
+  const double* eps;        // [K] step sizes
+  const double* inv_mass;   // [13] diagonal inverse mass
+  double* q;                // [K][13] position (in/out)
+  double* p;                // [K][13] momentum (in/out)
+  double* q0;               // [K][13] scratch
+  double* lnL0;             // [K] scratch
+  double* grad0;            // [K][13] scratch
+  int32_t* div;             // [K] scratch: the chain met a flagged (invalid) point
+  const double* lnL;        // [K] the last evaluation
+  const double* grad;       // [K][13]
+  const int32_t* flags;     // [K]
+  const double* log_u;      // [K] log of a uniform(0, 1) number per chain
+  double* H;                // [K][2] Hamiltonian at the start and the end
+  int32_t* accept;          // [K]
+  double* lnL_out;          // [K] log-likelihood at the returned position
+  double* grad_out;         // [K][13]
+};
+cudaError_t launch_hmc(const HmcArgs& a, cudaStream_t s);
+
 cudaError_t set_gauss_legendre(const double* x, const double* w);
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s);
 constexpr int MAX_SLAB = 64;   // Lambda points per CTA tile at most
 size_t fused_smem_bytes(int chunk, int slab, int group);
 size_t fused_smem_max();
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s);
+// CTAs of the fused kernel that fit on one SM at this geometry (occupancy query)
+cudaError_t fused_blocks_per_sm(const FusedArgs& a, bool grad, bool kahan, bool bf16, int* out);
 cudaError_t launch_plain_sample(const PlainArgs& a, bool grad, bool bf16, cudaStream_t s);
 cudaError_t launch_plain_reduce(const PlainArgs& a, bool grad, cudaStream_t s);
 cudaError_t launch_merge(const MergeArgs& a, int K, bool grad, cudaStream_t s);

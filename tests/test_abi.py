@@ -43,6 +43,7 @@ def test_struct_sizes_match_header(g):
     assert ctypes.sizeof(g.Injections) == 48
     assert ctypes.sizeof(g.Options) == 40 + 8
     assert ctypes.sizeof(g.Info) == 56
+    assert ctypes.sizeof(g.TuneResult) == 24
 
 
 def test_defaults(g):
