@@ -298,7 +298,7 @@ def main():
         torch.cuda.synchronize()
 
     import paper_2605_23538_gb300 as g
-    from paper_2605_23538_gb300 import build, synth
+    from paper_2605_23538_gb300 import build, shard, synth
     if rank == 0:
         build.build()
     if dist is not None:
@@ -312,7 +312,8 @@ def main():
     ctx = g.Context(cat, max_K=K)
     info = ctx.info()
     # each rank evaluates its own Lambda batch over the full catalogue (weak scaling)
-    lam_np = synth.lambda_batch(K, purpose=4 + 100 * rank)
+    lam_np = shard.rank_rows(shard.world_batch(K, world, lambda n: synth.lambda_batch(n, purpose=4)),
+                             rank, world)
     lam = torch.tensor(lam_np, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     out = g._outputs(K, ctx.n_events, lam.device, True)
@@ -341,10 +342,7 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     stage_ms, n_calls = ctx.profile_read()
     ctx.profile_enable(False)
-    ms = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    ms_total = float(ms.item())
+    ms_total = shard.max_over_ranks(ms_total, device="cuda")
     evals_step = (n_s + n_i) * K
     value = evals_step * args.steps * world / (ms_total / 1e3)
     flags = out["flags"].cpu().numpy()

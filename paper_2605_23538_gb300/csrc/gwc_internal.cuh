@@ -40,7 +40,8 @@ struct __align__(16) LamF {
   float om, lp2, gam, gam_m3;             // log2(1+z_p); gamma; gamma - 3
   float gpk, alpha, beta, eps_b;          // gamma+kappa; 1+beta
   float mmin, mmax, dm, mw;               // mw = m_min + delta_m
-  float mu, inv_sig, la2, lb2;            // log2 of (1-lam)/Z_P and of lam/(sig sqrt(2 pi) Z_G)
+  float mu, inv_sig, la2, lb2;            // log2 of (1-lam)/Z_P and of lam/(sig sqrt(2 pi) Z_G),
+                                          // less the anchor R carried in FP64 by c
   float C0, inv_eps_b, Cw, mw1b;          // C above the window = C0 + m1^(1+beta)/(1+beta);
                                           // C(mw) = int_{m_min}^{mw} m^beta S; mw^(1+beta)
   float lmw, inv_wh, inv_dm, beta_small;  // ln mw; N_w/delta_m; 1/delta_m; 1 if |1+beta| < 1e-3
@@ -49,9 +50,11 @@ struct __align__(16) LamF {
   float dZGsig, dZGmin, dZGmax, Cwb;      // d ln Z_G / d(sig, m_min, m_max); int m^beta ln m S
   float Cmin, Kw, la0_2, lb0_2;           // dC/dm_min above the window; int m^beta dS/d delta_m;
                                           // log2 of 1/Z_P and of 1/(sig sqrt(2 pi) Z_G)
-  float inv_lam, inv_1ml, pad0, pad1;
+  float inv_lam, inv_1ml, dm_l2, zstep_lo;   // dm log2(e) formed in FP64; z_max/(n_z-1) - zstep
+  float alpha_lo, beta_lo, eps_b_lo, gpk_lo;   // alpha, beta, 1+beta, gamma+kappa less their
+                                               // float values (they multiply logs of up to ~8)
 };
-static_assert(sizeof(LamF) == 52 * 4, "LamF layout");
+static_assert(sizeof(LamF) == 56 * 4, "LamF layout");
 
 // FP64 constants of one Lambda point for the merge: ln w = (per-sample term) + c.
 // lam_sigma = +1 at lambda_peak = 1, -1 at lambda_peak = 0, else 0 (see Acc).
@@ -81,6 +84,11 @@ struct Item {          // one work item: a contiguous run of samples of one even
 constexpr float LN2F = 0.69314718055994530942f;
 constexpr float LOG2EF = 1.44269504088896340736f;
 constexpr float HALF_LOG2EF = 0.72134752044448170368f;
+// log2(e) as an unevaluated sum of two floats: x * log2(e) to about half an ulp, where the
+// single float constant (relative error -1.3e-8) would shift every ln pi of magnitude ~20
+// by the same ~3e-7, an error that grows with the number of events in the total
+constexpr float LOG2E_LO = 1.9259629911e-08f;
+__device__ __forceinline__ float to_log2(float x) { return fmaf(x, LOG2EF, x * LOG2E_LO); }
 
 // the special-function unit's approximations (PTX ex2/lg2/rcp .approx): relative errors
 // of a few 2^-23, which keeps every term of ln w at FP32 rounding level
@@ -89,11 +97,19 @@ __device__ __forceinline__ float ex2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// lg2: the special-function unit's approximation, for log2(1+z).  lg2_acc: the accurate
+// log2f, for the logarithm of the product of all ratio terms.  With the approximation in
+// both places the weighted mean error of ln w over 1e6 injections was +2e-7 to +5e-7, a
+// bias every sample shares and that reaches the total multiplied by the number of
+// events; with log2f for the product, ln xi at 5e7 injections is within 5e-8 of the FP64
+// value and the total at 10,000 events within 7.1e-4 (log2f in both places: 7.4e-4, and
+// about 2% slower).  ex2.approx and rcp.approx showed no comparable bias.
 __device__ __forceinline__ float lg2(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float lg2_acc(float x) { return log2f(x); }
 __device__ __forceinline__ float rcp(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -131,8 +147,8 @@ struct HermiteBasis {
 };
 
 struct SampleIn {
-  float m1, m2, dl, lpe, lm1, lm2;   // detector-frame masses, distance, ln pi (natural),
-                                     // log2 m1, log2 m2
+  float m1, m2, dl, npe2, lm1, lm2;  // detector-frame masses, distance, -log2 pi (the PE
+                                     // prior or draw density), log2 m1, log2 m2
 };
 
 __device__ __forceinline__ float ld_row(const float* __restrict__ r, int j) { return __ldg(r + j); }
@@ -188,7 +204,8 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   float tl = (nd.x - (float)j) + frac;
   if (j > nz - 2) { tl += (float)(j - (nz - 2)); j = nz - 2; }
   if (j < 0) { tl += (float)j; j = 0; }
-  const float z = ((float)j + tl) * L.zstep;
+  const float jt = (float)j + tl;
+  const float z = fmaf(jt, L.zstep, jt * L.zstep_lo);   // the step in two floats
   const float u = 1.f + z;
   const float ru = rcp(u);
   const float lu2 = lg2(u);
@@ -204,7 +221,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float lm1s2 = s.lm1 - lu2, lm2s2 = s.lm2 - lu2;
 
   // p(m1): (1-lam) m^-alpha / Z_P + lam N(m; mu, sig) / Z_G as max + log2(1 + e^-|a-b|)
-  const float a2 = fmaf(-L.alpha, lm1s2, L.la2);
+  const float a2 = fmaf(-L.alpha, lm1s2, fmaf(-L.alpha_lo, lm1s2, L.la2));
   const float zz = (m1s - L.mu) * L.inv_sig;
   const float b2 = fmaf(-HALF_LOG2EF * zz, zz, L.lb2);
   const float mx = fmaxf(a2, b2);
@@ -220,7 +237,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     if (!(mp2 > 0.f)) return false;
     i1 = rcp(mp2);
     i2 = rcp(mp2 - L.dm);
-    f2 = L.dm * (i1 + i2) * LOG2EF;
+    f2 = L.dm_l2 * (i1 + i2);
     ef2 = ex2(-fabsf(f2));
     lin -= fmaxf(f2, 0.f);
   }
@@ -240,10 +257,11 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     const float4 d0 = __ldg(wslp + wk), d1 = __ldg(wslp + wk + 1);
     Qc = hb(v0.x, d0.x, v1.x, d1.x);
     Cx = Qc * (mp1 * mp1) * L.inv_dm;
-    lin = fmaf(L.beta, lm2s2 - lm1s2, lin);
+    const float dl21 = lm2s2 - lm1s2;
+    lin = fmaf(L.beta, dl21, fmaf(L.beta_lo, dl21, lin));
   } else {
     if (L.beta_small == 0.f) {
-      A = ex2(L.eps_b * lm1s2);                       // m1s^(1+beta)
+      A = ex2(fmaf(L.eps_b, lm1s2, L.eps_b_lo * lm1s2));   // m1s^(1+beta)
       Cx = fmaf(A, L.inv_eps_b, L.C0);
     } else {                                          // |1+beta| < 1e-3: series in y
       dlm = fmaf(lm1s2, LN2F, -L.lmw);
@@ -252,12 +270,13 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
       A = L.mw1b * fmaf(y, phi1, 1.f);
       Cx = fmaf(L.mw1b * dlm, phi1, L.Cw);
     }
-    lin = fmaf(L.beta, lm2s2, lin);
+    lin = fmaf(L.beta, lm2s2, fmaf(L.beta_lo, lm2s2, lin));
   }
   den = win2 ? Cx * (1.f + ef2) : Cx;
 
   // rate psi(z)/(1+z) and the (1+z)^-2 mass Jacobian: (gam - 3) log2 u - softplus(r)/ln 2
-  const float r2 = L.gpk * (lu2 - L.lp2);
+  const float dlp = lu2 - L.lp2;
+  const float r2 = fmaf(L.gpk, dlp, L.gpk_lo * dlp);
   const float er = ex2(-fabsf(r2));
   lin -= fmaxf(r2, 0.f);
 
@@ -267,8 +286,8 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float Dp = fmaf(x, ru, u * rE);
   den *= Dp * (1.f + er);
 
-  lw2 = fmaf(L.gam_m3, lu2, lin) + lg2(plos * (1.f + eab) * rcp(den));
-  lw2 = fmaf(-s.lpe, LOG2EF, lw2);
+  lw2 = fmaf(L.gam_m3, lu2, lin) + lg2_acc(plos * (1.f + eab) * rcp(den));
+  lw2 += s.npe2;
   if (!(lw2 > -INFINITY)) return false;
   const bool has_grad = sink.weight(lw2);
 
@@ -293,7 +312,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     float dS1_dmin = 0.f, dS1_ddm = 0.f, dlnC_db, dlnC_dmin, dlnC_ddm, Gc;
     if (win1) {
       const float j1 = rcp(mp1), j2 = rcp(mp1 - L.dm);
-      const float f1 = L.dm * (j1 + j2) * LOG2EF;
+      const float f1 = L.dm_l2 * (j1 + j2);
       const float ef1 = ex2(-fabsf(f1));
       const float inv = rcp(1.f + ef1);
       const float sf1 = f1 >= 0.f ? inv : ef1 * inv;

@@ -397,23 +397,35 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.xmax = (float)xmax;
     f.live = 1.f;
     f.zstep = (float)(zmax / (nz - 1));
+    f.zstep_lo = (float)(zmax / (nz - 1) - (double)f.zstep);
     f.inv_zstep = (float)pscale;
     f.om = (float)om;
     f.lp2 = (float)(lp * LOG2E);
     f.gam = (float)gam;
     f.gam_m3 = (float)(gam - 3.0);
     f.gpk = (float)gpk;
+    f.gpk_lo = (float)(gpk - (double)f.gpk);
     f.alpha = (float)alpha;
     f.beta = (float)beta;
     f.eps_b = (float)eps;
+    f.alpha_lo = (float)(alpha - (double)f.alpha);
+    f.beta_lo = (float)(beta - (double)f.beta);
+    f.eps_b_lo = (float)(eps - (double)f.eps_b);
     f.mmin = (float)mmin;
     f.mmax = (float)mmax;
     f.dm = (float)dm;
+    f.dm_l2 = (float)(dm * LOG2E);
     f.mw = (float)mw;
     f.mu = (float)mu;
     f.inv_sig = (float)(1.0 / sig);
-    f.la2 = lam < 1.0 ? (float)((log1p(-lam) - lnZP) * LOG2E) : -INFINITY;
-    f.lb2 = lam > 0.0 ? (float)((log(lam) - lnsig2pi - lnZG) * LOG2E) : -INFINITY;
+    // the two components' log2 normalisations, less an anchor R (log2 units) that c
+    // carries in FP64: only their difference is rounded to FP32, so the rounding no
+    // longer shifts every sample's weight by the same amount
+    const double la2d = lam < 1.0 ? (log1p(-lam) - lnZP) * LOG2E : -INFINITY;
+    const double lb2d = lam > 0.0 ? (log(lam) - lnsig2pi - lnZG) * LOG2E : -INFINITY;
+    const double R = lam < 1.0 ? la2d : lb2d;
+    f.la2 = lam < 1.0 ? (float)(la2d - R) : -INFINITY;
+    f.lb2 = lam > 0.0 ? (float)(lb2d - R) : -INFINITY;
     const bool small = fabs(eps) < 1e-3;
     const double mw1b = exp(eps * log(mw));
     f.beta_small = small ? 1.f : 0.f;
@@ -438,13 +450,13 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.Cwb = (float)Cwb;
     f.Cmin = (float)(beta * Jw - mw1b / mw);
     f.Kw = (float)Kw;
-    f.la0_2 = (float)(-lnZP * LOG2E);
-    f.lb0_2 = (float)((-lnsig2pi - lnZG) * LOG2E);
+    f.la0_2 = (float)(-lnZP * LOG2E - R);
+    f.lb0_2 = (float)((-lnsig2pi - lnZG) * LOG2E - R);
     f.inv_lam = lam > 0.0 ? (float)(1.0 / lam) : 0.f;
     f.inv_1ml = lam < 1.0 ? (float)(1.0 / (1.0 - lam)) : 0.f;
     *lf = f;
-    // c = -ln N'_z - ln Z_m1 + ln(H0 / c)
-    ld->c = -log(Nz) - log(Zm1) + log(H0 / C_KMS);
+    // c = -ln N'_z - ln Z_m1 + ln(H0 / c) + R ln 2 (the anchor taken out of la2, lb2)
+    ld->c = -log(Nz) - log(Zm1) + log(H0 / C_KMS) + R * 0.69314718055994530942;
     double dc[NP];
     for (int i = 0; i < NP; ++i) dc[i] = 0.0;
     const double iZ = 1.0 / Zm1;   // -d ln Z_m1 = dW / Z_m1
@@ -506,7 +518,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     s_m1[i] = v.x;
     s_m2[i] = v.y;
     s_dl[i] = v.z;
-    s_lpe[i] = v.w;
+    s_lpe[i] = -to_log2(v.w);
     s_lm1[i] = log2f(v.x);
     s_lm2[i] = log2f(v.y);
     s_pix[i] = inj ? 0 : __ldg(A.pix + it.begin + i);
@@ -530,7 +542,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       const float4* ws = wv + (NW_WIN + 1);
       for (int i = a + lane; i < b; i += 32) {
         SampleIn s;
-        s.m1 = s_m1[i]; s.m2 = s_m2[i]; s.dl = s_dl[i]; s.lpe = s_lpe[i];
+        s.m1 = s_m1[i]; s.m2 = s_m2[i]; s.dl = s_dl[i]; s.npe2 = s_lpe[i];
         s.lm1 = s_lm1[i]; s.lm2 = s_lm2[i];
         float lw;
         AccSink<GRAD, KAHAN> sink(acc);
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
   const bool inj = i >= A.n_samples;
   float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
   SampleIn s;
-  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.lpe = v.w;
+  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.npe2 = -to_log2(v.w);
   s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
   const float* tb = A.tables + (size_t)A.k * A.tstride;
   const int nx = A.nx;
@@ -933,7 +945,7 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
   const bool inj = i >= A.n_samples;
   const float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
   SampleIn s;
-  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.lpe = v.w;
+  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.npe2 = -to_log2(v.w);
   s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
   const float* tb = A.tables;
   const int nx = A.nx;

@@ -1,0 +1,87 @@
+"""Precision study at the stress size: 10,000 events x 4,096 samples, 5e7 injections, K = 128.
+
+Four builds of the same catalogue are compared with the FP64 oracle: plain or
+compensated (Kahan) FP32 sums inside each work item, and the LOS table stored as FP32
+or as BF16 (interpolated in FP32 either way).  The oracle evaluates per-event ln L one
+event at a time, so sampled (event, Lambda) outputs are checked at full size; ln xi and
+the total need every injection and every event, which takes the oracle several minutes
+per Lambda point, so that comparison runs only with GWC_C5_FULL=1 set.  The printed
+table is the study's result; the FP32 builds must meet the per-event tolerance, the
+BF16 builds only a loose bound (their error is the storage rounding of the LOS table,
+about 2^-9 relative).
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+K = 128
+EVENTS = np.linspace(0, 9999, 48).astype(np.int64)     # sampled events
+LAMBDAS = [0, 1, 2, 3, 64, 127]                         # sampled Lambda points
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2605_23538_gb300 import build
+    build.build()
+    import paper_2605_23538_gb300 as g
+    return g
+
+
+def test_c5_precision_variants(torch, g, orc, synth):
+    cat = synth.catalogue("c5")
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(K - 1, purpose=41)])
+    sub = synth.subset_events(cat, EVENTS)
+    for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):     # per-event values ignore them
+        sub[k] = cat[k][:1000]
+    ref = orc.loglik(sub, lam[LAMBDAS])
+    full = os.environ.get("GWC_C5_FULL") == "1"
+    ref_full = orc.loglik(cat, lam[:1]) if full else None
+    lt = torch.tensor(lam, dtype=torch.float64, device="cuda")
+    rows, outs = [], {}
+    for name, accum, los in (("fp32 LOS, plain sums", 0, g.LOS_F32),
+                             ("fp32 LOS, compensated sums", 1, g.LOS_F32),
+                             ("bf16 LOS, plain sums", 0, g.LOS_BF16),
+                             ("bf16 LOS, compensated sums", 1, g.LOS_BF16)):
+        with g.Context(cat, max_K=K, accum=accum, los_dtype=los) as ctx:
+            out = ctx.loglik(lt)
+            torch.cuda.synchronize()
+            o = {k: v.cpu().numpy() for k, v in out.items()}
+        outs[name] = o
+        got = o["lnL_event"][LAMBDAS][:, EVENTS]
+        want = ref["lnL_event"]
+        fin = np.isfinite(want)
+        assert np.array_equal(np.isfinite(got), fin), name
+        d = np.abs(got[fin] - want[fin])
+        row = {"variant": name, "per_event_max": d.max(), "per_event_mean": d.mean()}
+        if full:
+            # the total before any N_eff flag: sum_i ln L_i - N ln xi, from each side's parts
+            raw = lambda r: np.sum(r["lnL_event"][0]) - len(r["lnL_event"][0]) * r["ln_xi"][0]
+            row["ln_xi"] = abs(o["ln_xi"][0] - ref_full["ln_xi"][0])
+            row["sum_events"] = abs(np.sum(o["lnL_event"][0]) - np.sum(ref_full["lnL_event"][0]))
+            row["total"] = abs(raw(o) - raw(ref_full))
+        rows.append(row)
+    base = outs["fp32 LOS, compensated sums"]
+    print("\nC5 precision (|GPU - FP64 oracle|; sampled", len(EVENTS), "events x", len(LAMBDAS), "Lambda)")
+    for r in rows:
+        o = outs[r["variant"]]
+        raw = lambda x: x["lnL_event"].sum(axis=1) - x["lnL_event"].shape[1] * x["ln_xi"]
+        r["ln_xi_vs_compensated"] = np.abs(o["ln_xi"] - base["ln_xi"]).max()
+        r["total_vs_compensated"] = np.nanmax(np.abs(raw(o) - raw(base)))
+        print("  " + ", ".join(f"{k} {v:.3e}" if isinstance(v, float) else f"{k} {v}" for k, v in r.items()))
+    for r in rows[:2]:
+        assert r["per_event_max"] <= 1e-5, r
+        if full:
+            assert r["total"] <= 1e-3, r
+    for r in rows[2:]:
+        assert r["per_event_max"] <= 2e-2, r

@@ -1,0 +1,72 @@
+"""The multi-rank path on CPU: world_size-2 gloo ranks shard a Lambda batch.
+
+Each rank evaluates its block of rows with the FP64 oracle (standing in for its GPU
+context: the sharding logic is the same), the blocks are gathered in rank order, and
+rank 0 checks the result against one process evaluating the whole batch.  Also checks
+the row split, the max over ranks used for the job's time, and a batch whose size is
+not a multiple of the world size.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, n_rows, result_file):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2605_23538_gb300 import shard, synth
+        cat = synth.catalogue(synth.scaled("shard", 4, ("fixed", 200), 4, 128, 2000, "found"))
+        lam_all = shard.world_batch(n_rows // world, world, lambda n: synth.lambda_batch(n, purpose=51)) \
+            if n_rows % world == 0 else synth.lambda_batch(n_rows, purpose=51)
+        mine = shard.rank_rows(lam_all, rank, world)
+        r = oracle.loglik(cat, mine, n_threads=1)
+        block = torch.tensor(np.column_stack([r["lnL_total"], r["ln_xi"]]), dtype=torch.float64)
+        allrows = shard.gather_rows(block, len(lam_all))
+        t = shard.max_over_ranks(10.0 + rank)
+        if rank == 0:
+            np.savez(result_file, gathered=allrows.numpy(), lam=lam_all, tmax=t)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("n_rows", [6, 5])
+def test_two_gloo_ranks_reproduce_one_process(tmp_path, n_rows):
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_2605_23538_gb300 import synth
+    out = str(tmp_path / "r.npz")
+    mp.start_processes(_rank_main, args=(2, _free_port(), n_rows, out), nprocs=2,
+                       start_method="spawn", join=True)
+    res = np.load(out)
+    cat = synth.catalogue(synth.scaled("shard", 4, ("fixed", 200), 4, 128, 2000, "found"))
+    ref = oracle.loglik(cat, res["lam"], n_threads=1)
+    assert res["gathered"].shape == (n_rows, 2)
+    np.testing.assert_array_equal(res["gathered"][:, 0], ref["lnL_total"])
+    np.testing.assert_array_equal(res["gathered"][:, 1], ref["ln_xi"])
+    assert res["tmax"] == 11.0
+
+
+def test_row_ranges_cover_the_batch_once():
+    from paper_2605_23538_gb300 import shard
+    for n in (0, 1, 5, 6, 256, 1001):
+        for world in (1, 2, 3, 8):
+            spans = [shard.row_range(n, r, world) for r in range(world)]
+            assert spans[0][0] == 0 and spans[-1][1] == n
+            assert all(spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+            sizes = [b - a for a, b in spans]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard.row_range(4, 2, 2)
