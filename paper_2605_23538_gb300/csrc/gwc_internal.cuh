@@ -31,6 +31,20 @@ constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the pr
 
 enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
 
+// The sample kernels do not sum the 13 derivatives of ln w themselves but 13 weighted
+// statistics they are linear in; the FP64 merge applies the Lambda-only coefficients
+// (stats_to_grad).  For one sample of weight t (pa, pb: mixture responsibilities,
+// zz = (m1s - mu)/sig, sr = sigmoid of the rate's turnover, lu2 = log2(1+z)):
+//   S_H0   t Gz x / D'            (d/dH0 = S_H0 / H0)
+//   S_OM   t d ln w / d Om
+//   S_A1   t pa                   S_LX  t pb  (at lambda_peak = 0, 1: t times the
+//                                             lambda-derivative before the other-component term)
+//   S_AL   t pa log2 m1s          S_BE  t d ln w / d beta
+//   S_MMIN t (smoothing and C(m1) parts of d/dm_min)   S_DM  t d ln w / d delta_m
+//   S_MU   t pb zz                S_SIG t pb zz^2
+//   S_LU   t lu2                  S_SRD t sr (lu2 - log2(1+z_p))      S_SR  t sr
+enum { S_H0, S_OM, S_A1, S_LX, S_AL, S_BE, S_MMIN, S_DM, S_MU, S_SIG, S_LU, S_SRD, S_SR };
+
 // FP32 constants of one Lambda point for the sample kernels (52 floats = 13 float4).
 // Fields ending in 2 are in log2 units (the value path works in log2 so that the
 // special-function unit's ex2/lg2 apply directly).
@@ -63,7 +77,36 @@ struct LamD {
   double dc[NP];
   int32_t flag;
   int32_t lam_sigma;
+  // coefficients of stats_to_grad
+  double invH0, dZPa, dZPmin, dZPmax, dZGmin, dZGmax, dZGmu, dZGsig;
+  double inv_sig, inv_lam, inv_1ml, gpk_inv1zp;
 };
+
+// The 13 derivative sums G (before division by the weight sum S1) from the statistics.
+template <typename T>
+__host__ __device__ inline void stats_to_grad(const T* st, T S1, const LamD& D, T* G) {
+  const T LN2 = (T)0.69314718055994530942;
+  T A1 = st[S_A1], B1 = st[S_LX];
+  if (D.lam_sigma != 0) {          // one component only: pa, pb are 0 or 1
+    A1 = D.lam_sigma < 0 ? S1 : (T)0;
+    B1 = D.lam_sigma > 0 ? S1 : (T)0;
+    G[P_LAM] = st[S_LX];
+  } else {
+    G[P_LAM] = (T)D.inv_lam * B1 - (T)D.inv_1ml * A1;
+  }
+  G[P_H0] = (T)D.invH0 * st[S_H0];
+  G[P_OM] = st[S_OM];
+  G[P_ALPHA] = -LN2 * st[S_AL] - (T)D.dZPa * A1;
+  G[P_BETA] = st[S_BE];
+  G[P_MMIN] = st[S_MMIN] - (T)D.dZPmin * A1 - (T)D.dZGmin * B1;
+  G[P_MMAX] = -(T)D.dZPmax * A1 - (T)D.dZGmax * B1;
+  G[P_DM] = st[S_DM];
+  G[P_MU] = (T)D.inv_sig * st[S_MU] - (T)D.dZGmu * B1;
+  G[P_SIG] = (T)D.inv_sig * (st[S_SIG] - B1) - (T)D.dZGsig * B1;
+  G[P_GAM] = LN2 * (st[S_LU] - st[S_SRD]);
+  G[P_KAP] = -LN2 * st[S_SRD];
+  G[P_ZP] = (T)D.gpk_inv1zp * st[S_SR];
+}
 
 // Per-Lambda table block (floats):
 //   [0, 4 NX)          float4 pos[NX]  {hi, lo, D, c2}: P(x_n) = hi + lo; cubic in t on
@@ -165,7 +208,7 @@ __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int
 // When L.lam_edge is set (lambda_peak = 1 or 0) the mixture is one component and the
 // lambda derivative is sigma (1 - O/mix), where O is the other component's density
 // (P at lambda = 1, G at lambda = 0) and sigma = +1 / -1.  O/mix can exceed the float
-// range for samples far from the present component, so g[P_LAM] holds sigma and
+// range for samples far from the present component, so statistic S_LX holds sigma and
 // lam_lb holds log2(O/mix); the accumulator keeps sum w O/mix as its own (max, sum) pair
 // and the FP64 merge subtracts it.  Returns false where w = 0.
 //
@@ -292,7 +335,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const bool has_grad = sink.weight(lw2);
 
   if (GRAD && has_grad) {
-    const float lu = lu2 * LN2F, lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
+    const float lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
     const float inv1e = rcp(1.f + eab);
     const float pa = a2 >= b2 ? inv1e : eab * inv1e;   // mixture responsibilities
     const float pb = 1.f - pa;
@@ -360,26 +403,26 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     // z depends on H0 and Om through x and the inverted distance relation
     const float4 ax1 = __ldg(aux + n + 1);
     const float J = hermite_val(make_float2(ax.y, ax.z), make_float2(ax1.y, ax1.z), t);
-    sink.grad(P_H0, Gz * x * L.invH0 * invDp);
-    sink.grad(P_OM, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
-    sink.grad(P_ALPHA, pa * (-lm1s - L.dZPa));
-    sink.grad(P_BETA, lm2s - dlnC_db);
-    sink.grad(P_MMIN, -pa * L.dZPmin - pb * L.dZGmin + dS1_dmin - dS2_dm - dlnC_dmin);
-    sink.grad(P_MMAX, -pa * L.dZPmax - pb * L.dZGmax);
-    sink.grad(P_DM, dS1_ddm + dS2_ddm - dlnC_ddm);
-    sink.grad(P_MU, pb * (zz * L.inv_sig - L.dZGmu));
-    sink.grad(P_SIG, pb * (fmaf(zz, zz, -1.f) * L.inv_sig - L.dZGsig));
+    sink.grad(S_H0, Gz * x * invDp);
+    sink.grad(S_OM, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
+    sink.grad(S_A1, pa);
+    sink.grad(S_AL, pa * lm1s2);
+    sink.grad(S_BE, lm2s - dlnC_db);
+    sink.grad(S_MMIN, dS1_dmin - dS2_dm - dlnC_dmin);
+    sink.grad(S_DM, dS1_ddm + dS2_ddm - dlnC_ddm);
+    const float pbz = pb * zz;
+    sink.grad(S_MU, pbz);
+    sink.grad(S_SIG, pbz * zz);
     if (L.lam_edge == 0.f) {
-      sink.grad(P_LAM, pb * L.inv_lam - pa * L.inv_1ml);
+      sink.grad(S_LX, pb);
     } else if (L.lam >= 1.f) {                                    // mix = G: 1 - P/G
       sink.lam_edge(1.f, lw2, fmaf(-L.alpha, lm1s2, L.la0_2) - b2);
     } else {                                                      // mix = P: G/P - 1
       sink.lam_edge(-1.f, lw2, fmaf(-HALF_LOG2EF * zz, zz, L.lb0_2) - a2);
     }
-    const float dlu = (lu2 - L.lp2) * LN2F;
-    sink.grad(P_GAM, lu - sr * dlu);
-    sink.grad(P_KAP, -sr * dlu);
-    sink.grad(P_ZP, sr * L.gpk * L.inv1zp);
+    sink.grad(S_LU, lu2);
+    sink.grad(S_SRD, sr * dlp);
+    sink.grad(S_SR, sr);
   }
   return true;
 }
@@ -407,7 +450,7 @@ struct TermSink {
   __device__ __forceinline__ bool weight(float) { return true; }
   __device__ __forceinline__ void grad(int i, float v) { g[i] = v; }
   __device__ __forceinline__ void lam_edge(float sigma, float, float l) {
-    g[P_LAM] = sigma;
+    g[S_LX] = sigma;
     lo = l;
     edge = true;
   }
@@ -457,7 +500,7 @@ struct Acc {
   }
   // lambda_peak = 1 or 0: sigma t, and the other component's weight 2^l in (mO, sO)
   __device__ __forceinline__ void add_other(float sigma, float tt, float l) {
-    g[P_LAM] = fmaf(sigma, tt, g[P_LAM]);
+    g[S_LX] = fmaf(sigma, tt, g[S_LX]);
     if (l > mO) {
       sO = fmaf(sO, ex2(mO - l), 1.f);
       mO = l;

@@ -474,6 +474,18 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     for (int i = 0; i < NP; ++i) ld->dc[i] = dc[i];
     ld->flag = 0;
     ld->lam_sigma = lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0);
+    ld->invH0 = 1.0 / H0;
+    ld->dZPa = dZPa;
+    ld->dZPmin = dZPmin;
+    ld->dZPmax = dZPmax;
+    ld->dZGmin = dZGmin;
+    ld->dZGmax = dZGmax;
+    ld->dZGmu = dZGmu;
+    ld->dZGsig = dZGsig;
+    ld->inv_sig = 1.0 / sig;
+    ld->inv_lam = lam > 0.0 ? 1.0 / lam : 0.0;
+    ld->inv_1ml = lam < 1.0 ? 1.0 / (1.0 - lam) : 0.0;
+    ld->gpk_inv1zp = gpk / (1.0 + zp);
   }
 }
 
@@ -488,7 +500,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
 // (item, Lambda).
 // Occupancy: the value kernel fits three CTAs per SM (<= 80 registers per thread), the
 // gradient kernel two (<= 128); three would force the 13 gradient sums to spill.
-constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
+#ifndef GWC_MINB_GRAD
+#define GWC_MINB_GRAD 2
+#endif
+constexpr int MINB_VALUE = 3, MINB_GRAD = GWC_MINB_GRAD;
 
 // One (item, Lambda-slab) unit: stage the item's samples, sweep them for the slab's
 // Lambda points, combine the warp groups' sums into the unit's partials.
@@ -674,7 +689,7 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
     const float t = ok ? ex2(lw - m) : 0.f;
     for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * ts.g[q] : 0.f;
     if (ok && ts.edge)   // sigma (t - t O/mix): may overflow for extreme samples
-      A.tg[(size_t)P_LAM * A.n_total + i] = ts.g[P_LAM] * (t - ex2(lw - m + ts.lo));
+      A.tg[(size_t)S_LX * A.n_total + i] = ts.g[S_LX] * (t - ex2(lw - m + ts.lo));
   }
 }
 
@@ -788,6 +803,11 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         S2 += (double)p[2] * r * r;
         if (GRAD)
           for (int i = 0; i < NP; ++i) G[i] += (double)p[3 + i] * r;
+      }
+      if (GRAD) {
+        double st[NP];
+        for (int i = 0; i < NP; ++i) st[i] = G[i];
+        stats_to_grad(st, S1, D, G);
       }
       if (GRAD && D.lam_sigma != 0)   // other-component sums at lambda_peak = 0 or 1
         for (int s = s0; s < s1; ++s) {
@@ -907,6 +927,11 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         if (GRAD)
           for (int i = 0; i < NP; ++i) G[i] += rsel[q][3 + i] * r;
       }
+      if (GRAD) {
+        double st[NP];
+        for (int i = 0; i < NP; ++i) st[i] = G[i];
+        stats_to_grad(st, S1, D, G);
+      }
       if (GRAD && D.lam_sigma != 0)
         for (int q = 0; q < 8; ++q)
           if (rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * exp2(rO[q][0] - M);
@@ -962,11 +987,15 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
     else
       ok = sample_lnw<true>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
                             A.nz, pos, aux, nx, wv, ws, lw, ts);
-    if (ok && ts.edge) ts.g[P_LAM] *= 1.f - ex2(ts.lo);   // sigma (1 - O/mix): may overflow
   }
   A.lnw[i] = ok ? lw * LN2F : -INFINITY;
-  if (A.dlnw)
-    for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? ts.g[q] : 0.f;
+  if (A.dlnw) {
+    double st[NP], G[NP];
+    for (int q = 0; q < NP; ++q) st[q] = ok ? (double)ts.g[q] : 0.0;
+    stats_to_grad(st, ok ? 1.0 : 0.0, *A.ld, G);
+    if (ok && ts.edge) G[P_LAM] *= 1.0 - exp2((double)ts.lo);   // sigma (1 - O/mix): may overflow
+    for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? (float)G[q] : 0.f;
+  }
 }
 
 cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s) {
