@@ -80,7 +80,15 @@ struct LamD {
   // coefficients of stats_to_grad
   double invH0, dZPa, dZPmin, dZPmax, dZGmin, dZGmax, dZGmu, dZGsig;
   double inv_sig, inv_lam, inv_1ml, gpk_inv1zp;
+  // -ln N'_z and its gamma, kappa, z_p derivatives, written by a prologue CTA of their own
+  double cz, dcz[3];
 };
+
+// the per-Lambda constant of ln w and its gradient: the parts in c, dc and in cz, dcz
+__host__ __device__ inline double lamd_c(const LamD& D) { return D.c + D.cz; }
+__host__ __device__ inline double lamd_dc(const LamD& D, int i) {
+  return D.dc[i] + (i == P_GAM ? D.dcz[0] : i == P_KAP ? D.dcz[1] : i == P_ZP ? D.dcz[2] : 0.0);
+}
 
 // The 13 derivative sums G (before division by the weight sum S1) from the statistics.
 template <typename T>

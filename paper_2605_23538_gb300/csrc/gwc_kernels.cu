@@ -115,14 +115,18 @@ __device__ bool lambda_ok(const double* L) {
 constexpr int PRO_THREADS = 256;
 constexpr int ZPANELS = 256;   // panels of the z quadrature (one per thread)
 
+// Three CTAs per Lambda point (blockIdx.y), run side by side: part 0 builds the d_L -> z
+// inversion table, part 1 the smoothing-window tables, the mass normalisations and the
+// constants, part 2 the redshift normalisation N'_z.  Parts 0 and 1 both need step (1),
+// which each computes.
 __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   extern __shared__ double sdyn[];               // 2 * nx doubles: P_n, D_n
-  __shared__ double sI[ZPANELS + 1], sJ[ZPANELS + 1], sD[ZPANELS + 1];
+  __shared__ double sI[ZPANELS + 1], sJ[ZPANELS + 1], sD[ZPANELS + 1], sDp[ZPANELS + 1];
   __shared__ double red[32 * 16];
   __shared__ double sc[32];                      // scalar broadcast
 
-  const int k = blockIdx.x, tid = threadIdx.x;
-  if (k == 0 && tid == 0 && A.counter) *A.counter = 0;
+  const int k = blockIdx.x, tid = threadIdx.x, part = blockIdx.y;
+  if (k == 0 && part == 0 && tid == 0 && A.counter) *A.counter = 0;
   const double* L = A.lam + (size_t)k * NP;
   LamF* lf = A.lf + k;
   LamD* ld = A.ld + k;
@@ -131,13 +135,15 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double zmax = A.zmax;
 
   if (!lambda_ok(L)) {
-    if (tid == 0) {
+    if (tid == 0 && part == 1) {
       LamF f;
       memset(&f, 0, sizeof(f));
       f.xmax = -1.f;
       *lf = f;
       ld->c = 0.0;
+      ld->cz = 0.0;
       for (int i = 0; i < NP; ++i) ld->dc[i] = 0.0;
+      for (int i = 0; i < 3; ++i) ld->dcz[i] = 0.0;
       ld->flag = 1;
       ld->lam_sigma = 0;
     }
@@ -146,6 +152,33 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double H0 = L[P_H0], om = L[P_OM], alpha = L[P_ALPHA], beta = L[P_BETA];
   const double mmin = L[P_MMIN], mmax = L[P_MMAX], dm = L[P_DM], mu = L[P_MU], sig = L[P_SIG];
   const double lam = L[P_LAM], gam = L[P_GAM], kap = L[P_KAP], zp = L[P_ZP];
+  const double gpk = gam + kap, lp = log1p(zp);
+
+  if (part == 2) {
+    // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
+    //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
+    const double dzg = zmax / (nz - 1);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < nz; j += PRO_THREADS) {
+      const double zj = j * dzg, l = log1p(zj);
+      const double r = gpk * (l - lp);
+      const double term = ((j == 0 || j == nz - 1) ? 0.5 : 1.0) * dzg * A.pbar64[j] *
+                          exp(gam * l - softplus_d(r) - l);
+      const double s = sigmoid_d(r);
+      v[0] += term;
+      v[1] += term * (l - s * (l - lp));
+      v[2] += term * (-s * (l - lp));
+      v[3] += term * (s * gpk / (1.0 + zp));
+    }
+    block_sum<4>(v, red);
+    if (tid == 0) {
+      ld->cz = -log(v[0]);
+      ld->dcz[0] = -v[1] / v[0];
+      ld->dcz[1] = -v[2] / v[0];
+      ld->dcz[2] = -v[3] / v[0];
+    }
+    return;
+  }
 
   // ---- (1) I(z) and J(z) = dI/dOm on panel edges of [0, zmax]
   const double hz = zmax / ZPANELS;
@@ -166,12 +199,17 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     sJ[tid + 1] = v[1];
     if (tid == 0) { sI[0] = 0.0; sJ[0] = 0.0; }
     __syncthreads();
-    for (int p = tid; p <= ZPANELS; p += PRO_THREADS) sD[p] = (1.0 + p * hz) * sI[p];
+    for (int p = tid; p <= ZPANELS; p += PRO_THREADS) {
+      const double zp_ = p * hz, u = 1.0 + zp_;
+      sD[p] = u * sI[p];
+      sDp[p] = sI[p] + u / sqrt(om * (zp_ * (3.0 + zp_ * (3.0 + zp_))) + 1.0);   // D'(z_p)
+    }
     __syncthreads();
   }
   const double xmax = sD[ZPANELS];
   const double dx = xmax / (nx - 1);
   const double pscale = (double)(nz - 1) / zmax;   // LOS grid units per unit z
+  if (part == 0) {
 
   // ---- (2) inversion table on the uniform x grid
   float4* aux = reinterpret_cast<float4*>(tb + 4 * nx);
@@ -186,34 +224,34 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       }
       const int p = lo;
       const double z0 = p * hz;
-      z = z0 + hz * (xn - sD[p]) / (sD[p + 1] - sD[p]);
-      double Iz = 0.0, E = 1.0;
-      for (int it = 0; it < 5; ++it) {
-        // I(z) = I(z0) + int_{z0}^{z} dz'/E by the Gauss-Legendre rule
-        const double h = z - z0;
-        double acc = 0.0;
-        for (int q = 0; q < NGL; ++q) {
-          const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
-          acc += c_glw[q] / sqrt(om * (zq * (3.0 + zq * (3.0 + zq))) + 1.0);
-        }
-        Iz = sI[p] + 0.5 * h * acc;
-        const double u = 1.0 + z;
-        E = sqrt(om * (z * (3.0 + z * (3.0 + z))) + 1.0);
-        Dp = Iz + u / E;
-        if (it == 4) break;
-        z -= (u * Iz - xn) / Dp;
-        z = fmin(fmax(z, z0), z0 + hz);
+      // start: invert the cubic Hermite interpolant of D on the panel (D and D' at its
+      // edges; ~1e-11 from the root), three Newton steps on that cubic in s = (z-z0)/hz
+      const double D0 = sD[p], D1 = sD[p + 1], d0 = sDp[p] * hz, d1 = sDp[p + 1] * hz;
+      const double c2 = 3.0 * (D1 - D0) - 2.0 * d0 - d1, c3 = 2.0 * (D0 - D1) + d0 + d1;
+      double sp = (xn - D0) / (D1 - D0);
+      for (int it = 0; it < 3; ++it) {
+        const double f = D0 + sp * (d0 + sp * (c2 + sp * c3)) - xn;
+        const double fd = d0 + sp * (2.0 * c2 + 3.0 * sp * c3);
+        sp = fmin(fmax(sp - f / fd, 0.0), 1.0);
       }
+      z = z0 + sp * hz;
+      // one Newton step on the exact D: I, J and E from one Gauss-Legendre pass; D' and
+      // J are kept from that pass (the step moves z by ~1e-11)
       const double h = z - z0;
-      double accj = 0.0;
+      double acc = 0.0, accj = 0.0;
       for (int q = 0; q < NGL; ++q) {
         const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
-        const double u3m1 = zq * (3.0 + zq * (3.0 + zq)), E2 = om * u3m1 + 1.0;
-        accj += c_glw[q] * (-0.5 * u3m1 / (E2 * sqrt(E2)));
+        const double u3m1 = zq * (3.0 + zq * (3.0 + zq)), E2 = om * u3m1 + 1.0, iE = 1.0 / sqrt(E2);
+        acc += c_glw[q] * iE;
+        accj += c_glw[q] * (-0.5 * u3m1 * iE * iE * iE);
       }
+      const double Iz = sI[p] + 0.5 * h * acc;
       Jz = sJ[p] + 0.5 * h * accj;
-      const double u3m1 = z * (3.0 + z * (3.0 + z)), E2 = om * u3m1 + 1.0;
-      jd = -0.5 * u3m1 / (E2 * sqrt(E2));
+      const double u = 1.0 + z;
+      const double u3m1 = z * (3.0 + z * (3.0 + z)), E2 = om * u3m1 + 1.0, iE = 1.0 / sqrt(E2);
+      Dp = Iz + u * iE;
+      z = fmin(fmax(z - (u * Iz - xn) / Dp, z0), z0 + hz);
+      jd = -0.5 * u3m1 * iE * iE * iE;
     }
     sdyn[2 * n] = z * pscale;                // P_n
     sdyn[2 * n + 1] = pscale / Dp * dx;      // dP/dx * dx
@@ -233,8 +271,11 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     pos[n] = make_float4(hi, (float)(P0 - (double)hi), (float)D0, (float)c2);
     aux[n].x = (float)c3;
   }
+  return;
+  }   // part 0
 
-  // ---- (3) mass-model normalisations (thread 0), broadcast through shared memory
+  // ---- (3) mass-model normalisations (Z_P on thread 0, Z_G on thread 32, so the two
+  //          serial chains run in different warps), broadcast through shared memory
   if (tid == 0) {
     // Z_P = int_{mmin}^{mmax} m^-alpha dm = e^{t a} (b - a) phi1(t (b - a)), t = 1 - alpha
     const double t = 1.0 - alpha, a = log(mmin), b = log(mmax), Lr = b - a, y = t * Lr;
@@ -245,6 +286,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     sc[1] = -(a + Lr * gy);                          // d ln Z_P / d alpha
     sc[2] = -exp(-alpha * a - lnZP);                 // d ln Z_P / d m_min
     sc[3] = exp(-alpha * b - lnZP);                  // d ln Z_P / d m_max
+  } else if (tid == 32) {
     // Z_G = Phi(B) - Phi(A)
     const double A_ = (mmin - mu) / sig, B_ = (mmax - mu) / sig, r2 = 0.70710678118654752440;
     double ZG;
@@ -269,9 +311,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double hw = dm / NW_WIN;
   double cum[4] = {0.0, 0.0, 0.0, 0.0};   // C, C_beta, J, K over this thread's panel
   double wv[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (tid < NW_WIN && dm > 0.0) {
-    const double ma = mmin + tid * hw;
-    for (int q = 0; q < NGL; ++q) {
+  static_assert(2 * NW_WIN <= PRO_THREADS, "two threads per window panel");
+  if (tid < 2 * NW_WIN && dm > 0.0) {   // panel tid / 2, half of its nodes each
+    const double ma = mmin + (tid >> 1) * hw;
+    for (int q = (tid & 1) * (NGL / 2); q < ((tid & 1) + 1) * (NGL / 2); ++q) {
       const double m = ma + 0.5 * hw * (1.0 + c_glx[q]);
       const double mp = m - mmin, lm = log(m);
       double S, oneS, dSddm;
@@ -298,7 +341,13 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     }
   }
   block_sum<9>(wv, red);
-  block_scan<4>(cum, red);   // inclusive: cum at node tid + 1
+  // each panel's sums to its even thread, then an inclusive scan: the even thread 2p
+  // holds the cumulative integrals at node p + 1
+  for (int i = 0; i < 4; ++i) {
+    cum[i] += __shfl_xor_sync(0xffffffffu, cum[i], 1);
+    if (tid & 1) cum[i] = 0.0;
+  }
+  block_scan<4>(cum, red);
   const double W = wv[0];
   const double Zm1 = 1.0 - W;
   // d ln Z_m1 / d theta = -dW/d theta / Z_m1
@@ -314,8 +363,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   float4* wslp = wval + (NW_WIN + 1);
   __shared__ double scum[4][NW_WIN + 1];
   __shared__ double sq[4][NW_WIN + 1];
-  if (tid < NW_WIN)
-    for (int i = 0; i < 4; ++i) scum[i][tid + 1] = cum[i];
+  if (tid < 2 * NW_WIN && !(tid & 1))
+    for (int i = 0; i < 4; ++i) scum[i][(tid >> 1) + 1] = cum[i];
   if (tid == 0)
     for (int i = 0; i < 4; ++i) scum[i][0] = 0.0;
   __syncthreads();
@@ -352,36 +401,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     wslp[tid] = make_float4((float)(qd[0] * hw), (float)(qd[1] * hw), (float)(qd[2] * hw), (float)(qd[3] * hw));
   }
 
-  // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
-  //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
-  const double gpk = gam + kap, lp = log1p(zp);
-  {
-    const double dzg = zmax / (nz - 1);
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < nz; j += PRO_THREADS) {
-      const double zj = j * dzg, l = log1p(zj);
-      const double r = gpk * (l - lp);
-      const double term = ((j == 0 || j == nz - 1) ? 0.5 : 1.0) * dzg * A.pbar64[j] *
-                          exp(gam * l - softplus_d(r) - l);
-      const double s = sigmoid_d(r);
-      v[0] += term;
-      v[1] += term * (l - s * (l - lp));
-      v[2] += term * (-s * (l - lp));
-      v[3] += term * (s * gpk / (1.0 + zp));
-    }
-    block_sum<4>(v, red);
-    if (tid == 0) {
-      sc[16] = v[0];
-      sc[17] = v[1] / v[0];
-      sc[18] = v[2] / v[0];
-      sc[19] = v[3] / v[0];
-    }
-  }
-  __syncthreads();
-
   // ---- (6) constants
   if (tid == 0) {
-    const double Nz = sc[16];
     const double Cw = dm > 0.0 ? scum[0][NW_WIN] : 0.0;
     const double Cwb = dm > 0.0 ? scum[1][NW_WIN] : 0.0;
     const double Jw = dm > 0.0 ? scum[2][NW_WIN] : 0.0;
@@ -455,8 +476,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.inv_lam = lam > 0.0 ? (float)(1.0 / lam) : 0.f;
     f.inv_1ml = lam < 1.0 ? (float)(1.0 / (1.0 - lam)) : 0.f;
     *lf = f;
-    // c = -ln N'_z - ln Z_m1 + ln(H0 / c) + R ln 2 (the anchor taken out of la2, lb2)
-    ld->c = -log(Nz) - log(Zm1) + log(H0 / C_KMS) + R * 0.69314718055994530942;
+    // c = -ln Z_m1 + ln(H0 / c) + R ln 2 (the anchor taken out of la2, lb2); -ln N'_z
+    // and its derivatives are in cz, dcz
+    ld->c = -log(Zm1) + log(H0 / C_KMS) + R * 0.69314718055994530942;
     double dc[NP];
     for (int i = 0; i < NP; ++i) dc[i] = 0.0;
     const double iZ = 1.0 / Zm1;   // -d ln Z_m1 = dW / Z_m1
@@ -468,9 +490,6 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     dc[P_MU] = dWmu * iZ;
     dc[P_SIG] = dWsig * iZ;
     dc[P_LAM] = dWl * iZ;
-    dc[P_GAM] = -sc[17];
-    dc[P_KAP] = -sc[18];
-    dc[P_ZP] = -sc[19];
     for (int i = 0; i < NP; ++i) ld->dc[i] = dc[i];
     ld->flag = 0;
     ld->lam_sigma = lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0);
@@ -499,11 +518,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
 // G entries of each Lambda are combined in warp order into one partial per
 // (item, Lambda).
 // Occupancy: the value kernel fits three CTAs per SM (<= 80 registers per thread), the
-// gradient kernel two (<= 128); three would force the 13 gradient sums to spill.
-#ifndef GWC_MINB_GRAD
-#define GWC_MINB_GRAD 2
-#endif
-constexpr int MINB_VALUE = 3, MINB_GRAD = GWC_MINB_GRAD;
+// gradient kernel two (<= 128): at three it spills ~340 bytes per thread and runs at
+// half the speed.
+constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
 
 // One (item, Lambda-slab) unit: stage the item's samples, sweep them for the slab's
 // Lambda points, combine the warp groups' sums into the unit's partials.
@@ -817,10 +834,10 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     }
     double lnL = -INFINITY, neff = 0.0;
     if (S1 > 0.0) {
-      lnL = M * LN2D + log(S1) - log(A.ev_n[e]) + D.c;
+      lnL = M * LN2D + log(S1) - log(A.ev_n[e]) + lamd_c(D);
       neff = S1 * S1 / S2;
       if (GRAD)
-        for (int i = 0; i < NP; ++i) sg[i] += G[i] / S1 + D.dc[i];
+        for (int i = 0; i < NP; ++i) sg[i] += G[i] / S1 + lamd_dc(D, i);
     }
     A.lnL_event[(size_t)k * ne + e] = lnL;
     A.neff_event[(size_t)k * ne + e] = neff;
@@ -940,7 +957,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     const bool dead = (fl & 2) != 0;
     double lnxi = -INFINITY, neffs = 0.0;
     if (S1 > 0.0) {
-      lnxi = M * LN2D + log(S1) - log(A.n_draw) + D.c;
+      lnxi = M * LN2D + log(S1) - log(A.n_draw) + lamd_c(D);
       neffs = S1 * S1 / S2;
     } else {
       flag |= 8;
@@ -953,7 +970,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     if (GRAD)
       for (int i = 0; i < NP; ++i)
         A.grad_total[(size_t)k * NP + i] =
-            (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + D.dc[i]);
+            (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + lamd_dc(D, i));
   }
 }
 
@@ -962,8 +979,8 @@ template <typename RowT>
 __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
-    A.c[0] = A.ld->c;
-    for (int q = 0; q < NP; ++q) A.c[1 + q] = A.ld->dc[q];
+    A.c[0] = lamd_c(*A.ld);
+    for (int q = 0; q < NP; ++q) A.c[1 + q] = lamd_dc(*A.ld, q);
   }
   if (i >= A.n_total) return;
   const LamF L = A.lf[0];
@@ -1026,7 +1043,7 @@ cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_prologue<<<K, PRO_THREADS, smem, s>>>(a);
+  k_prologue<<<dim3(K, 3), PRO_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
