@@ -77,6 +77,11 @@ def lib():
             L.orc_ln_w_samples.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp]
             L.orc_ln_w_row.restype = ctypes.c_int
             L.orc_ln_w_row.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, d, vp, vp]
+            L.orc_loglik_kde.restype = ctypes.c_int
+            L.orc_loglik_kde.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, i32, d, d, i32,
+                                         vp, vp, vp, vp, vp, vp]
+            L.orc_bandwidth.restype = d
+            L.orc_bandwidth.argtypes = [vp, i64, i32]
         return _lib
 
 
@@ -151,6 +156,54 @@ def ln_w_samples(lam, cat, which="events", idx=None, grad=False):
     if rc != 0:
         raise ValueError("Lambda outside its domain")
     return (out, g, kink) if grad else out
+
+
+BW_RULES = {"scott": 0, "silverman": 1, "biweight": 2}
+
+
+def bandwidth(z, rule="scott"):
+    """KDE bandwidth of the values z by the named rule (see bandwidth() in the C++)."""
+    a = np.ascontiguousarray(z, dtype=np.float64)
+    return lib().orc_bandwidth(_ptr(a), len(a), BW_RULES[rule])
+
+
+def _inputs(cat, keep):
+    def arr(key, dt):
+        a = np.ascontiguousarray(cat[key], dtype=dt)
+        keep[key] = a
+        return _ptr(a)
+
+    los = np.ascontiguousarray(cat["los"], dtype=np.float32)
+    keep["los"] = los
+    n_ev = len(cat["offsets"]) - 1
+    return n_ev, Inputs(n_events=n_ev, pad0=0, offsets=arr("offsets", np.int64),
+                        m1=arr("m1", np.float32), m2=arr("m2", np.float32), dl=arr("dl", np.float32),
+                        lnpe=arr("lnpe", np.float32), pix=arr("pix", np.int32),
+                        n_pix=los.shape[0], n_z=los.shape[1], z_max=float(cat["z_max"]),
+                        los=_ptr(los), n_inj=len(cat["inj_m1"]), n_draw=float(cat["n_draw"]),
+                        im1=arr("inj_m1", np.float32), im2=arr("inj_m2", np.float32),
+                        idl=arr("inj_dl", np.float32), ilnpd=arr("inj_lnpd", np.float32))
+
+
+def loglik_kde(cat, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, neff_min_sel=0.0, n_threads=0):
+    """The KDE form of the likelihood (Eqs. 5-7): per-pixel weighted Gaussian KDE in z on
+    an n_grid-point grid over [0, z_max], times the pixel's LOS prior, trapezoid rule,
+    pixels below neff_min_pixel dropped.  neff_event is the effective number of kept
+    pixels.  Value only."""
+    lam = np.atleast_2d(_lam(lam))
+    K = lam.shape[0]
+    keep = {}
+    n_ev, inp = _inputs(cat, keep)
+    out = dict(lnL_event=np.empty((K, n_ev)), neff_event=np.empty((K, n_ev)),
+               ln_xi=np.empty(K), neff_sel=np.empty(K), lnL_total=np.empty(K),
+               flags=np.empty(K, np.int32))
+    rc = lib().orc_loglik_kde(ctypes.byref(inp), K, _ptr(lam), BW_RULES[bw], n_grid, neff_min_pixel,
+                              neff_min_sel, n_threads, _ptr(out["lnL_event"]), _ptr(out["neff_event"]),
+                              _ptr(out["ln_xi"]), _ptr(out["neff_sel"]), _ptr(out["lnL_total"]),
+                              _ptr(out["flags"]))
+    if rc != 0:
+        raise ValueError("oracle rejected the inputs")
+    return out
 
 
 def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads=0):

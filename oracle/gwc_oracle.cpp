@@ -19,6 +19,8 @@
 //     kernel of Eq. 5 is taken in its zero-width limit, so each event term is the
 //     Monte-Carlo mean of w over the event's samples.
 //   * Eq. 7: effective sample size (sum w)^2 / sum w^2, applied per event.
+//   * The KDE form of Eqs. 5-7 (per-pixel Gaussian KDE on a redshift grid, per-pixel
+//     N_eff cut, bandwidth rules of the appendix) is evaluated by orc_loglik_kde.
 // The mass model (power law + Gaussian peak, low-mass smoothing) and the
 // Madau-Dickinson rate are named but not written out in the paper; the standard
 // population-literature definitions are used (see the functions below).
@@ -447,16 +449,20 @@ inline void kink_parts(const Dual& z, double jump, double* kink) {
   for (int i = 0; i < NP; ++i) kink[i] = jump * std::fabs(z.d[i]);
 }
 
+// row == NULL leaves out the LOS factor (the weight w' of the KDE form, Eq. 6); *z_out
+// (when given) receives z whenever d_L maps into [0, zmax], whatever the weight.
 template <class T>
 bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, double m2d,
-          double dl, double lnpi, T& out, double* kink = nullptr) {
+          double dl, double lnpi, T& out, double* kink = nullptr, double* z_out = nullptr) {
+  if (z_out) *z_out = NEG_INF;
   if (!(dl > 0.0)) return false;
   const T x = dl * P.H0 / C_KMS;
   if (val(x) > P.xmax) return false;
   const double z0 = z_root(val(x), val(P.om), zmax);
   const T z = z_of_x(x, P.om, z0);
-  T plos;
-  if (!los_interp(row, nz, zmax, z, plos)) return false;
+  if (z_out) *z_out = val(z);
+  T plos = T(1.0);
+  if (row && !los_interp(row, nz, zmax, z, plos)) return false;
   const T u = 1.0 + z;
   const T m1s = m1d / u;
   const T m2s = m2d / u;
@@ -465,8 +471,9 @@ bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, d
   if (!ln_p_m2(m2s, m1s, P, lp2)) return false;
   const T ddl_dz = (C_KMS / P.H0) * Dprime_of(z, P.om);
   const T lu = flog(u);
-  out = flog(plos) + ln_psi(z, P) - lu - P.lnNz + lp1 + lp2 - 2.0 * lu - flog(ddl_dz) - lnpi;
-  if (kink) kink_parts(z, los_kink(row, nz, zmax, val(z), val(plos), 2e-5), kink);
+  out = ln_psi(z, P) - lu - P.lnNz + lp1 + lp2 - 2.0 * lu - flog(ddl_dz) - lnpi;
+  if (row) out = out + flog(plos);
+  if (kink && row) kink_parts(z, los_kink(row, nz, zmax, val(z), val(plos), 2e-5), kink);
   return true;
 }
 
@@ -703,6 +710,153 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
   }
 }
 
+// ------------------------------------------------------------ KDE numerator
+// The paper's own per-event term (Eqs. 5-7): in each sky pixel j of event i, a Gaussian
+// KDE in z of the pixel's samples weighted by w' = p_pop(z, theta'|Lambda) / pi_PE (the
+// weight of Eq. 6, i.e. the Monte-Carlo weight without its LOS factor), evaluated on a
+// uniform grid of n_grid points over [0, zmax], multiplied by the pixel's LOS prior and
+// integrated by the trapezoid rule:
+//     L_ij = sum_g c_g p_LOS(z_g | j) sum_k w'_k K_h(z_g - z_k),   K_h = N(0, h^2) density
+//     L_i  = (1 / N_i) sum_{j kept} L_ij
+// A pixel is kept when its N_eff = (sum w')^2 / sum w'^2 (Eq. 7) reaches the threshold
+// and its bandwidth is positive.  With a LOS prior linear in z and every sample more
+// than a few h inside the grid, L_i equals the Monte-Carlo term exactly; that is the
+// kernel's zero-width limit for any h.
+enum { BW_SCOTT = 0, BW_SILVERMAN = 1, BW_BIWEIGHT = 2 };
+
+// quantile of sorted values, linear between order statistics at position q (n - 1)
+double quantile_sorted(const std::vector<double>& s, double q) {
+  const double pos = q * (double)(s.size() - 1);
+  const size_t i = (size_t)std::floor(pos);
+  if (i + 1 >= s.size()) return s.back();
+  return s[i] + (pos - (double)i) * (s[i + 1] - s[i]);
+}
+
+// Bandwidth of one pixel's z samples (unweighted), by the rules of the paper's appendix:
+//   Scott      1.06 sigma n^-1/5 (sigma: sample standard deviation, n - 1 in the divisor)
+//   Silverman  0.9 min(sigma, IQR / 1.34) n^-1/5
+//   biweight   1.06 s_bi n^-1/5 with s_bi^2 the biweight midvariance (the expression the
+//              appendix prints, about the median Q with u = (z - Q) / (9 MAD))
+// 0 when it is undefined (n < 2, or a zero scale).
+double bandwidth(std::vector<double> z, int rule) {
+  const size_t n = z.size();
+  if (n < 2) return 0.0;
+  const double nf = (double)n, shrink = std::pow(nf, -0.2);
+  double mean = 0.0;
+  for (double v : z) mean += v;
+  mean /= nf;
+  double ss = 0.0;
+  for (double v : z) ss += (v - mean) * (v - mean);
+  const double sigma = std::sqrt(ss / (nf - 1.0));
+  if (rule == BW_SCOTT) return 1.06 * sigma * shrink;
+  std::sort(z.begin(), z.end());
+  if (rule == BW_SILVERMAN) {
+    const double iqr = quantile_sorted(z, 0.75) - quantile_sorted(z, 0.25);
+    return 0.9 * std::min(sigma, iqr / 1.34) * shrink;
+  }
+  const double Q = quantile_sorted(z, 0.5);
+  std::vector<double> dev(n);
+  for (size_t i = 0; i < n; ++i) dev[i] = std::fabs(z[i] - Q);
+  std::sort(dev.begin(), dev.end());
+  const double mad = quantile_sorted(dev, 0.5);
+  if (!(mad > 0.0)) return 0.0;
+  double num = 0.0, den = 0.0;
+  for (double v : z) {
+    const double u = (v - Q) / (9.0 * mad);
+    if (std::fabs(u) < 1.0) {
+      const double a = 1.0 - u * u;
+      num += (v - Q) * (v - Q) * a * a * a * a;
+      den += a * (1.0 - 5.0 * u * u);
+    }
+  }
+  if (!(den != 0.0) || !(num > 0.0)) return 0.0;
+  return 1.06 * std::sqrt(nf * num / (den * den)) * shrink;
+}
+
+// ln L_i and the effective number of kept pixels (sum_j L_ij)^2 / sum_j L_ij^2 of one event
+void kde_event(const Inputs& in, const Pop<double>& P, int e, int rule, int n_grid,
+               double neff_min_pixel, double* lnL, double* neff) {
+  const int nz = in.n_z;
+  const double zmax = in.z_max;
+  const double dzg = zmax / (n_grid - 1);
+  std::vector<int> pixels;
+  for (int64_t k = in.offsets[e]; k < in.offsets[e + 1]; ++k)
+    if (std::find(pixels.begin(), pixels.end(), in.pix[k]) == pixels.end()) pixels.push_back(in.pix[k]);
+  std::vector<double> lnLj;   // ln L_ij of the kept pixels
+  for (int pj : pixels) {
+    std::vector<double> zs, zw, lw;   // valid z of the pixel; z and ln w' of positive weights
+    for (int64_t k = in.offsets[e]; k < in.offsets[e + 1]; ++k) {
+      if (in.pix[k] != pj) continue;
+      double l, z;
+      const bool pos = ln_w(P, nullptr, nz, zmax, in.m1[k], in.m2[k], in.dl[k], in.lnpe[k], l,
+                            nullptr, &z);
+      if (z == NEG_INF) continue;   // d_L outside the distance range
+      zs.push_back(z);
+      if (pos) { zw.push_back(z); lw.push_back(l); }
+    }
+    if (lw.empty()) continue;
+    double m = NEG_INF;
+    for (double v : lw) m = std::max(m, v);
+    double s1 = 0.0, s2 = 0.0;
+    for (double v : lw) { const double t = std::exp(v - m); s1 += t; s2 += t * t; }
+    if (!(s1 * s1 / s2 >= neff_min_pixel)) continue;
+    const double h = bandwidth(zs, rule);
+    if (!(h > 0.0)) continue;
+    std::vector<double> row((size_t)nz);
+    for (int j = 0; j < nz; ++j) row[(size_t)j] = (double)in.los[(size_t)pj * nz + j];
+    // the grid sum of Eq. 5 times the LOS prior, in the paper's order: the KDE at each
+    // grid point, then the trapezoid over the grid
+    const double norm = 1.0 / (h * std::sqrt(2.0 * M_PI));
+    double Lj = 0.0;
+    for (int g = 0; g < n_grid; ++g) {
+      const double zg = g * dzg;
+      double p;
+      if (!los_interp(row.data(), nz, zmax, zg, p)) continue;
+      double f = 0.0;
+      for (size_t k = 0; k < zw.size(); ++k) {
+        const double u = (zg - zw[k]) / h;
+        f += std::exp(lw[k] - m - 0.5 * u * u) * norm;
+      }
+      Lj += ((g == 0 || g == n_grid - 1) ? 0.5 : 1.0) * dzg * p * f;
+    }
+    if (Lj > 0.0) lnLj.push_back(m + std::log(Lj));
+  }
+  const double n_i = (double)(in.offsets[e + 1] - in.offsets[e]);
+  if (lnLj.empty()) { *lnL = NEG_INF; *neff = 0.0; return; }
+  double M = NEG_INF;
+  for (double v : lnLj) M = std::max(M, v);
+  double a = 0.0, b = 0.0;
+  for (double v : lnLj) { const double t = std::exp(v - M); a += t; b += t * t; }
+  *lnL = M + std::log(a) - std::log(n_i);
+  *neff = a * a / b;
+}
+
+void eval_lambda_kde(const Inputs& in, const std::vector<double>& pbar, const double* L,
+                     int rule, int n_grid, double neff_min_pixel, double neff_min_sel,
+                     double* lnL_event, double* neff_event, double* ln_xi, double* neff_sel,
+                     double* lnL_total, int32_t* flag) {
+  const int ne = in.n_events;
+  // the selection term is the Monte-Carlo one; the event terms are replaced below
+  eval_lambda<double>(in, pbar, L, 0.0, neff_min_sel, lnL_event, neff_event, ln_xi, neff_sel,
+                      lnL_total, flag, nullptr, nullptr, nullptr);
+  if (*flag & 1) return;
+  const Pop<double> P = make_pop<double>(L, pbar, in.z_max);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < ne; ++e)
+    kde_event(in, P, e, rule, n_grid, neff_min_pixel, lnL_event + e, neff_event + e);
+  bool dead = false;
+  double sum = 0.0, comp_ = 0.0;
+  for (int e = 0; e < ne; ++e) {
+    if (lnL_event[e] == NEG_INF) { dead = true; continue; }
+    const double v = lnL_event[e];
+    const double t = sum + v;
+    if (std::fabs(sum) >= std::fabs(v)) comp_ += (sum - t) + v; else comp_ += (v - t) + sum;
+    sum = t;
+  }
+  *flag &= ~2;   // the per-pixel cut replaces the per-event one
+  *lnL_total = (*flag || dead) ? NEG_INF : (sum + comp_) - (double)ne * (*ln_xi);
+}
+
 std::vector<double> row_to_double(const float* row, int nz) {
   std::vector<double> r((size_t)nz);
   for (int j = 0; j < nz; ++j) r[(size_t)j] = (double)row[j];
@@ -749,6 +903,34 @@ int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad
                           neff_sel + k, lnL_total + k, flags + k, nullptr, nullptr, nullptr);
   }
   return 0;
+}
+
+// The KDE form of the likelihood (Eqs. 5-7; see kde_event): bw_rule 0 Scott, 1
+// Silverman, 2 biweight; n_grid KDE grid points on [0, zmax]; pixels below
+// neff_min_pixel are dropped.  neff_event receives the effective number of kept pixels.
+// Flags as orc_loglik, without bit 1 (there is no per-event N_eff cut).
+int orc_loglik_kde(const Inputs* in, int32_t K, const double* lam, int32_t bw_rule,
+                   int32_t n_grid, double neff_min_pixel, double neff_min_sel, int32_t n_threads,
+                   double* lnL_event, double* neff_event, double* ln_xi, double* neff_sel,
+                   double* lnL_total, int32_t* flags) {
+  if (!in || K < 0 || !inputs_valid(*in) || n_grid < 2 || bw_rule < 0 || bw_rule > 2) return -1;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+  const std::vector<double> pbar = pixel_mean(*in);
+  const int ne = in->n_events;
+  for (int k = 0; k < K; ++k)
+    eval_lambda_kde(*in, pbar, lam + (size_t)k * NP, bw_rule, n_grid, neff_min_pixel, neff_min_sel,
+                    lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
+                    neff_sel + k, lnL_total + k, flags + k);
+  return 0;
+}
+
+// bandwidth of n values by rule bw_rule (as above)
+double orc_bandwidth(const double* z, int64_t n, int32_t bw_rule) {
+  return bandwidth(std::vector<double>(z, z + n), bw_rule);
 }
 
 int orc_num_params(void) { return NP; }
