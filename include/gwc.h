@@ -147,6 +147,38 @@ gwc_status gwc_loglik_grad(gwc_ctx* ctx, int32_t K, const double* d_lambda, doub
                            double* d_lnL_total, int32_t* d_flags, double* d_grad_total,
                            void* stream);
 
+/* The paper's KDE form of the event term (Eqs. 5-7; value only).  For each event and
+ * each sky pixel j holding its samples: a Gaussian kernel density estimate in z of the
+ * pixel's samples, weighted by w' = p_pop(z, m1, m2 | Lambda) / pi_PE (Eq. 6: the
+ * Monte-Carlo weight without its LOS factor), evaluated on n_grid points uniform on
+ * [0, z_max], multiplied by the pixel's LOS prior there and integrated by the trapezoid
+ * rule; L_i = (1/N_i) sum over the pixels whose N_eff = (sum w')^2 / sum w'^2 (Eq. 7)
+ * reaches neff_min_pixel.  The bandwidth of each pixel comes from its samples' z
+ * (unweighted), by the appendix's rules: Scott 1.06 sigma n^-1/5 (sample sigma with an
+ * n-1 divisor), Silverman 0.9 min(sigma, IQR/1.34) n^-1/5 (quartiles linear between
+ * order statistics), biweight 1.06 s_bi n^-1/5 (s_bi^2 the printed biweight
+ * midvariance about the median, u = (z - Q)/(9 MAD)); a pixel with fewer than two
+ * samples in [0, z_max] or a zero bandwidth is dropped.  Kernels are summed over the
+ * grid points within 7 h of each sample (the rest weigh less than e^-24.5).  The
+ * selection term is the Monte-Carlo sum of gwc_loglik.  Outputs as gwc_loglik, except
+ * that d_neff_event[K][n_events] receives the effective number of kept pixels,
+ * (sum_j L_ij)^2 / sum_j L_ij^2, and flag bit 1 is never set (no per-event cut); an
+ * event with no kept pixel makes the total -inf.  kopt may be NULL (defaults).  The
+ * first call (and a call with another n_grid) allocates the form's device buffers:
+ * about max_K x (groups + work items) x 72 bytes plus n_pix x n_grid floats.  Needs the
+ * LOS table stored as FP32 (GWC_E_UNSUPPORTED otherwise). */
+enum { GWC_BW_SCOTT = 0, GWC_BW_SILVERMAN = 1, GWC_BW_BIWEIGHT = 2 };
+typedef struct {
+  int32_t bw_rule;        /* GWC_BW_* (default Scott) */
+  int32_t n_grid;         /* KDE grid points on [0, z_max] (default 256) */
+  double neff_min_pixel;  /* per-pixel N_eff threshold (default 2) */
+} gwc_kde_options;
+void gwc_default_kde_options(gwc_kde_options* o);
+gwc_status gwc_loglik_kde(gwc_ctx* ctx, int32_t K, const double* d_lambda,
+                          const gwc_kde_options* kopt, double* d_lnL_event, double* d_neff_event,
+                          double* d_ln_xi, double* d_neff_sel, double* d_lnL_total,
+                          int32_t* d_flags, void* stream);
+
 /* The plain single-Lambda path, kept as the speed-up baseline: the same per-sample
  * arithmetic, one Lambda per launch sequence, every sample re-read from memory for each
  * Lambda, per-sample weights (and, for the gradient, per-sample weighted derivatives)

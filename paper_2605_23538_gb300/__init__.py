@@ -70,6 +70,14 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class KdeOptions(ctypes.Structure):
+    _fields_ = [("bw_rule", ctypes.c_int32), ("n_grid", ctypes.c_int32),
+                ("neff_min_pixel", ctypes.c_double)]
+
+
+BW_RULES = {"scott": 0, "silverman": 1, "biweight": 2}
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32),
                 ("lambda_group", ctypes.c_int32), ("n_tried", ctypes.c_int32),
@@ -81,7 +89,7 @@ EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read",
            "gwc_sample_terms", "gwc_sample_terms_noalloc", "gwc_graph_create", "gwc_graph_launch",
            "gwc_graph_destroy", "gwc_hmc_create", "gwc_hmc_launch", "gwc_hmc_destroy",
-           "gwc_autotune")
+           "gwc_autotune", "gwc_default_kde_options", "gwc_loglik_kde")
 
 
 def lib():
@@ -140,6 +148,10 @@ def lib():
         L.gwc_hmc_launch.argtypes = [vp, vp]
         L.gwc_hmc_destroy.restype = None
         L.gwc_hmc_destroy.argtypes = [vp]
+        L.gwc_default_kde_options.restype = None
+        L.gwc_default_kde_options.argtypes = [ctypes.POINTER(KdeOptions)]
+        L.gwc_loglik_kde.restype = ctypes.c_int
+        L.gwc_loglik_kde.argtypes = [vp, i32, vp, ctypes.POINTER(KdeOptions), vp, vp, vp, vp, vp, vp, vp]
         L.gwc_autotune.restype = ctypes.c_int
         L.gwc_autotune.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(TuneResult)]
         _lib = L
@@ -250,6 +262,34 @@ def loglik(ctx, lam, n_events, stream=None, out=None):
 def loglik_grad(ctx, lam, n_events, stream=None, out=None):
     """gwc_loglik_grad: as loglik, plus grad_total [K, 13]."""
     return _call(lib().gwc_loglik_grad, ctx, lam, n_events, True, stream, out)
+
+
+def default_kde_options(**kw):
+    o = KdeOptions()
+    lib().gwc_default_kde_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "bw":
+            k, v = "bw_rule", BW_RULES[v]
+        setattr(o, k, v)
+    return o
+
+
+def loglik_kde(ctx, lam, n_events, bw="scott", n_grid=256, neff_min_pixel=2.0, stream=None, out=None):
+    """gwc_loglik_kde: the paper's KDE form of the event terms (value only); neff_event
+    holds the effective number of kept pixels of each event."""
+    import torch
+    if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
+        raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
+    lam = lam.contiguous()
+    K = lam.shape[0]
+    if out is None:
+        out = _outputs(K, n_events, lam.device, False)
+    o = default_kde_options(bw=bw, n_grid=n_grid, neff_min_pixel=neff_min_pixel)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(lib().gwc_loglik_kde(ctx, K, p(lam), ctypes.byref(o), p(out["lnL_event"]), p(out["neff_event"]),
+                                p(out["ln_xi"]), p(out["neff_sel"]), p(out["lnL_total"]), p(out["flags"]),
+                                _stream_ptr(stream)), ctx)
+    return out
 
 
 def loglik_plain(ctx, lam, n_events, grad=True, stream=None, out=None):
@@ -465,6 +505,9 @@ class Context:
 
     def loglik_grad(self, lam, stream=None):
         return loglik_grad(self._ctx, lam, self.n_events, stream)
+
+    def loglik_kde(self, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, stream=None):
+        return loglik_kde(self._ctx, lam, self.n_events, bw, n_grid, neff_min_pixel, stream)
 
     def loglik_plain(self, lam, grad=True, stream=None):
         return loglik_plain(self._ctx, lam, self.n_events, grad, stream)

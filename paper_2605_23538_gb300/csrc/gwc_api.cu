@@ -68,6 +68,17 @@ struct gwc_ctx {
   int32_t* counter = nullptr;   // work counter of the persistent fused kernel
   int64_t items_cap = 0;        // work items the items/sched/partials buffers hold
   int live_recordings = 0;      // graphs and HMC objects recorded on this context
+  // KDE form of the event term: (event, pixel) groups, built at create; device copies,
+  // the LOS prior on the KDE grid and the partial buffer made on first use
+  std::vector<KdeGroup> h_groups;
+  std::vector<int32_t> h_ev_group0;
+  KdeGroup* kde_groups = nullptr;
+  int32_t* kde_ev_group0 = nullptr;
+  int32_t* kde_sched_inj = nullptr;
+  float* kde_pgrid = nullptr;
+  int kde_G = 0;
+  float* kde_partials = nullptr;
+  int64_t kde_stride = 0;
   uint64_t serial = 0;          // distinguishes contexts that reuse an address
   std::vector<int64_t> h_offsets;   // event offsets (for re-splitting the work items)
   int n_sms = 0;
@@ -124,6 +135,7 @@ void free_all(gwc_ctx* c) {
   c->prof_ev.clear();
   void* dev[] = {c->smp, c->pix, c->inj, c->los, c->pbar32, c->pbar64, c->items, c->sched,
                  c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->d_lam, c->d_out,
+                 c->kde_groups, c->kde_ev_group0, c->kde_sched_inj, c->kde_pgrid, c->kde_partials,
                  c->d_flags, c->sample_item, c->plain_lw, c->plain_tg};
   for (void* p : dev)
     if (p) cudaFree(p);
@@ -318,14 +330,10 @@ gwc_status run_merge(gwc_ctx* c, int K, int P, bool grad, double* lnL_event, dou
   return GWC_OK;
 }
 
-gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_event,
-                     double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
-                     int32_t* flags, double* grad_total, bool grad, cudaStream_t s) {
-  cudaError_t pe = prof_mark(c, 0, s);
-  if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
-  gwc_status st = run_prologue(c, K, d_lambda, grad, s, c->counter);
-  if (st != GWC_OK) return st;
-  if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
+// the persistent fused kernel over the n_sched items listed in sched, writing partial
+// slot slot0 + item of a [K][stride][PSTRIDE] buffer
+gwc_status launch_fused_items(gwc_ctx* c, int32_t K, bool grad, const int32_t* sched, int n_sched,
+                              float* partials, int64_t stride, int64_t slot0, cudaStream_t s) {
   int slab, n_slabs;
   fused_geometry(c, K, slab, n_slabs);
   FusedArgs fa;
@@ -337,7 +345,7 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   fa.nz = c->n_z;
   fa.nx = c->opt.n_x_table;
   fa.items = c->items;
-  fa.sched = c->sched;
+  fa.sched = sched;
   fa.n_items = c->n_items;
   fa.n_slabs = n_slabs;
   fa.slab = slab;
@@ -347,9 +355,12 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   fa.lf = c->lf;
   fa.tables = c->tables;
   fa.tstride = c->tstride;
-  fa.partials = c->partials;
+  fa.partials = partials;
   fa.counter = c->counter;
-  const long long units = (long long)c->n_items * n_slabs;
+  fa.n_sched = n_sched;
+  fa.stride = (int)stride;
+  fa.slot0 = (int)slot0;
+  const long long units = (long long)n_sched * n_slabs;
   if (units > 0x7fffffffLL) return fail(c, GWC_E_INVALID, "work grid too large");
   // persistent launch: as many CTAs as fit on the GPU at once, each taking units in
   // schedule order (largest items first) from the counter
@@ -369,6 +380,20 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   const long long grid = std::max(1LL, std::min(units, (long long)c->n_sms * bps));
   cudaError_t e = launch_fused(fa, grad, kahan, c->bf16, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "sample kernel launch");
+  return GWC_OK;
+}
+
+gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_event,
+                     double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
+                     int32_t* flags, double* grad_total, bool grad, cudaStream_t s) {
+  cudaError_t pe = prof_mark(c, 0, s);
+  if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
+  gwc_status st = run_prologue(c, K, d_lambda, grad, s, c->counter);
+  if (st != GWC_OK) return st;
+  if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
+  st = launch_fused_items(c, K, grad, c->sched, c->n_items, c->partials, c->n_items, 0, s);
+  if (st != GWC_OK) return st;
+  cudaError_t e;
   if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
   st = run_merge(c, K, 1, grad, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, flags,
                  grad_total, s);
@@ -423,6 +448,59 @@ gwc_status set_chunk(gwc_ctx* c, int chunk) {
   c->inj_item0 = lay.inj_item0;
   c->h_sample_item = std::move(lay.sample_item);
   c->opt.chunk = chunk;
+  // the KDE form's injection schedule and partial buffer follow the item layout
+  if (c->kde_sched_inj) { cudaFree(c->kde_sched_inj); c->kde_sched_inj = nullptr; }
+  if (c->kde_partials) { cudaFree(c->kde_partials); c->kde_partials = nullptr; }
+  return GWC_OK;
+}
+
+// Device resources of the KDE form, made on first use (and the LOS grid table again when
+// the grid size changes).
+gwc_status kde_prepare(gwc_ctx* c, int G, cudaStream_t s) {
+  auto oom = [&](cudaError_t e, const char* what) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? GWC_E_NOMEM : GWC_E_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaSuccess;
+  const size_t ng = c->h_groups.size();
+  if (!c->kde_groups && ng > 0) {
+    e = dalloc(c, &c->kde_groups, ng);
+    if (e == cudaSuccess) e = cudaMemcpy(c->kde_groups, c->h_groups.data(), sizeof(KdeGroup) * ng, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return oom(e, "KDE groups");
+  }
+  if (!c->kde_ev_group0) {
+    e = dalloc(c, &c->kde_ev_group0, c->h_ev_group0.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->kde_ev_group0, c->h_ev_group0.data(), sizeof(int32_t) * c->h_ev_group0.size(),
+                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return oom(e, "KDE group offsets");
+  }
+  if (!c->kde_sched_inj) {
+    ItemLayout lay;
+    if (!make_items(c->h_offsets.data(), c->n_events, c->n_samples, c->n_inj, c->opt.chunk, lay))
+      return fail(c, GWC_E_INVALID, "too many work items");
+    std::vector<int32_t> si;
+    for (int32_t q : lay.sched)
+      if (q >= lay.inj_item0) si.push_back(q);
+    e = dalloc(c, &c->kde_sched_inj, std::max<size_t>(si.size(), 1));
+    if (e == cudaSuccess && !si.empty())
+      e = cudaMemcpy(c->kde_sched_inj, si.data(), sizeof(int32_t) * si.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return oom(e, "KDE injection schedule");
+  }
+  if (!c->kde_partials) {
+    c->kde_stride = (int64_t)ng + c->n_items;
+    e = dalloc(c, &c->kde_partials, (size_t)c->opt.max_K * (size_t)c->kde_stride * PSTRIDE);
+    if (e != cudaSuccess) return oom(e, "KDE partials");
+  }
+  if (c->kde_G != G) {
+    if (c->kde_pgrid) { cudaFree(c->kde_pgrid); c->kde_pgrid = nullptr; c->kde_G = 0; }
+    e = dalloc(c, &c->kde_pgrid, (size_t)c->n_pix * G);
+    if (e != cudaSuccess) return oom(e, "KDE grid table");
+    e = launch_los_grid(static_cast<const float*>(c->los), c->n_pix, c->n_z, c->z_max, G, c->kde_pgrid, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "KDE grid table");
+    c->kde_G = G;
+  }
   return GWC_OK;
 }
 
@@ -547,6 +625,18 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
       }
     }
   }
+  // (event, pixel) groups of the sorted samples, for the KDE form
+  c->h_ev_group0.assign((size_t)ne + 1, 0);
+  for (int32_t e = 0; e < ne; ++e) {
+    c->h_ev_group0[(size_t)e] = (int32_t)c->h_groups.size();
+    for (int64_t q = ev->offsets[e]; q < ev->offsets[e + 1];) {
+      int64_t r = q;
+      while (r < ev->offsets[e + 1] && h_pix[(size_t)r] == h_pix[(size_t)q]) ++r;
+      c->h_groups.push_back(KdeGroup{q, (int32_t)(r - q), h_pix[(size_t)q]});
+      q = r;
+    }
+  }
+  c->h_ev_group0[(size_t)ne] = (int32_t)c->h_groups.size();
   // injections by d_L, for the same reason (their sum does not depend on the order), then
   // each block of INJ_BLOCK by m1_det: a block spans so little d_L that z is almost the
   // same for all of it, so the injections above m_max (1 + z) -- often 40% of a broad
@@ -687,6 +777,85 @@ gwc_status gwc_loglik_grad(gwc_ctx* c, int32_t K, const double* d_lambda, double
   if (!d_grad_total) return fail(c, GWC_E_INVALID, "d_grad_total is NULL");
   return run_fused(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel, d_lnL_total,
                    d_flags, d_grad_total, true, static_cast<cudaStream_t>(stream));
+}
+
+void gwc_default_kde_options(gwc_kde_options* o) {
+  if (!o) return;
+  o->bw_rule = GWC_BW_SCOTT;
+  o->n_grid = 256;
+  o->neff_min_pixel = 2.0;
+}
+
+gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const gwc_kde_options* kopt,
+                          double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
+                          double* d_neff_sel, double* d_lnL_total, int32_t* d_flags, void* stream) {
+  gwc_status st = check_call(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel,
+                             d_lnL_total, d_flags);
+  if (st != GWC_OK) return st;
+  gwc_kde_options ko;
+  gwc_default_kde_options(&ko);
+  if (kopt) ko = *kopt;
+  if (ko.bw_rule < GWC_BW_SCOTT || ko.bw_rule > GWC_BW_BIWEIGHT)
+    return fail(c, GWC_E_INVALID, "bw_rule must be GWC_BW_SCOTT, GWC_BW_SILVERMAN or GWC_BW_BIWEIGHT");
+  if (ko.n_grid < 2 || ko.n_grid > 65536) return fail(c, GWC_E_INVALID, "n_grid must be in [2, 65536]");
+  if (!(ko.neff_min_pixel >= 0.0)) return fail(c, GWC_E_INVALID, "neff_min_pixel must be >= 0");
+  if (c->bf16) return fail(c, GWC_E_UNSUPPORTED, "the KDE form needs the LOS table stored as FP32");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = kde_prepare(c, ko.n_grid, s);
+  if (st != GWC_OK) return st;
+  cudaError_t pe = prof_mark(c, 0, s);
+  if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
+  st = run_prologue(c, K, d_lambda, false, s, c->counter);
+  if (st != GWC_OK) return st;
+  if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
+  const int64_t ng = (int64_t)c->h_groups.size();
+  // the selection term: the Monte-Carlo sum over the injections only
+  st = launch_fused_items(c, K, false, c->kde_sched_inj, c->n_items - c->inj_item0, c->kde_partials,
+                          c->kde_stride, ng, s);
+  if (st != GWC_OK) return st;
+  KdeArgs ka;
+  ka.smp = c->smp;
+  ka.groups = c->kde_groups;
+  ka.n_groups = (int)ng;
+  ka.pgrid = c->kde_pgrid;
+  ka.G = ko.n_grid;
+  ka.dzg = (float)(c->z_max / (ko.n_grid - 1));
+  ka.rule = ko.bw_rule;
+  ka.neff_min = (float)ko.neff_min_pixel;
+  ka.K = K;
+  ka.nx = c->opt.n_x_table;
+  ka.nz = c->n_z;
+  ka.lf = c->lf;
+  ka.tables = c->tables;
+  ka.tstride = c->tstride;
+  ka.partials = c->kde_partials;
+  ka.stride = (int)c->kde_stride;
+  cudaError_t e = launch_kde(ka, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "KDE launch");
+  if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
+  MergeArgs ma;
+  ma.partials = c->kde_partials;
+  ma.n_items = (int)c->kde_stride;
+  ma.P = 1;
+  ma.ev_item0 = c->kde_ev_group0;
+  ma.n_events = c->n_events;
+  ma.inj_item0 = (int)(ng + c->inj_item0);
+  ma.ev_n = c->ev_n;
+  ma.n_draw = c->n_draw;
+  ma.ld = c->ld;
+  ma.neff_min_event = 0.0;   // the per-pixel cut replaces the per-event one
+  ma.neff_min_sel = c->opt.neff_min_sel;
+  ma.lnL_event = d_lnL_event;
+  ma.neff_event = d_neff_event;
+  ma.ln_xi = d_ln_xi;
+  ma.neff_sel = d_neff_sel;
+  ma.lnL_total = d_lnL_total;
+  ma.flags = d_flags;
+  ma.grad_total = nullptr;
+  e = launch_merge(ma, K, false, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "merge launch");
+  if ((e = prof_mark(c, 3, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
+  return GWC_OK;
 }
 
 gwc_status gwc_loglik_plain(gwc_ctx* c, int32_t K, const double* d_lambda, double* d_lnL_event,

@@ -228,7 +228,10 @@ __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int
 // work: their weight is below 2^-48 of the sum's largest.
 constexpr float GRAD_SKIP = 48.f;
 
-template <bool GRAD, typename RowT, typename Sink>
+// WITH_LOS = false leaves out the LOS factor (the weight w' of the KDE form, whose LOS
+// prior enters through the grid integral instead).  Every sample whose d_L maps into
+// [0, z_max] reports its z through sink.position(z), whatever its weight.
+template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
                                            const float4* __restrict__ pos,
@@ -240,7 +243,6 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   // (exact products by FMA), so the LOS-grid position keeps ~1e-7 of a cell
   const float x = s.dl * L.H0c;
   if (!(x > 0.f) || x > L.xmax) return false;
-  if (s.m2 > s.m1) return false;
   const float x_lo = fmaf(s.dl, L.H0c, -x) + s.dl * L.H0c_lo;
   const float sx = x * L.inv_dx;
   const float sx_lo = fmaf(x, L.inv_dx, -sx) + fmaf(x, L.inv_dx_lo, x_lo * L.inv_dx);
@@ -257,14 +259,20 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   if (j < 0) { tl += (float)j; j = 0; }
   const float jt = (float)j + tl;
   const float z = fmaf(jt, L.zstep, jt * L.zstep_lo);   // the step in two floats
+  sink.position(z);
+  if (s.m2 > s.m1) return false;
   const float u = 1.f + z;
   const float ru = rcp(u);
   const float lu2 = lg2(u);
 
   // --- LOS prior of the sample's pixel, linear in z (convex form: no cancellation)
-  const float p0 = ld_row(row, j), p1 = ld_row(row, j + 1);
-  const float plos = fmaf(tl, p1, (1.f - tl) * p0);
-  if (!(plos > 0.f)) return false;
+  float p0 = 1.f, p1 = 1.f, plos = 1.f;
+  if (WITH_LOS) {
+    p0 = ld_row(row, j);
+    p1 = ld_row(row, j + 1);
+    plos = fmaf(tl, p1, (1.f - tl) * p0);
+    if (!(plos > 0.f)) return false;
+  }
 
   // --- source-frame masses
   const float m1s = s.m1 * ru, m2s = s.m2 * ru;
@@ -447,6 +455,7 @@ struct AccSink {
     return GRAD && !(lw < a.m - GRAD_SKIP);
   }
   __device__ __forceinline__ void grad(int i, float v) { a.g[i] = fmaf(t, v, a.g[i]); }
+  __device__ __forceinline__ void position(float) {}
   __device__ __forceinline__ void lam_edge(float sigma, float lw, float lo) { a.add_other(sigma, t, lw + lo); }
 };
 
@@ -457,6 +466,7 @@ struct TermSink {
   bool edge = false;
   __device__ __forceinline__ bool weight(float) { return true; }
   __device__ __forceinline__ void grad(int i, float v) { g[i] = v; }
+  __device__ __forceinline__ void position(float) {}
   __device__ __forceinline__ void lam_edge(float sigma, float, float l) {
     g[S_LX] = sigma;
     lo = l;

@@ -622,7 +622,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     const float* sl = s_part + (size_t)kk * G * PSTRIDE;
     float M = -INFINITY;
     for (int w = 0; w < G; ++w) M = fmaxf(M, sl[w * PSTRIDE]);
-    float* out = A.partials + ((size_t)(k0 + kk) * A.n_items + item) * PSTRIDE;
+    float* out = A.partials + ((size_t)(k0 + kk) * A.stride + A.slot0 + item) * PSTRIDE;
     const int ncomp = GRAD ? 2 + NP : 2;   // s1, s2 (and g)
     if (lane < ncomp) {
       float acc = 0.f;
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
   // persistent: each CTA takes (item, Lambda-slab) units from the counter until none
   // is left; the counter is zeroed by the prologue of the same call
   __shared__ int s_unit;
-  const int n_units = A.n_items * A.n_slabs;
+  const int n_units = A.n_sched * A.n_slabs;
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(A.counter, 1);
     __syncthreads();
@@ -666,6 +666,283 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
     fused_unit<GRAD, KAHAN, RowT>(A, unit, sm);
     __syncthreads();   // the combine has read s_part before the next unit restages
   }
+}
+
+// ------------------------------------------------------------------ KDE form
+// The paper's own event term (Eqs. 5-7): for each (event, pixel) group, a Gaussian KDE
+// in z of the group's samples weighted by w' (the weight without its LOS factor) on a
+// uniform grid of G points over [0, z_max], times the pixel's LOS prior at the grid
+// points, trapezoid rule.  One warp per (group, Lambda); the 8 warps of a CTA take 8
+// Lambda points of one group, so the group's samples are read from L1 after the first.
+// Pass 1: z and w' of every sample -> the pixel's N_eff and the moments (and, for the
+// Silverman and biweight rules, order statistics: within a group the samples are sorted
+// by d_L, so by z, and the samples with a z form a contiguous index range).  Pass 2:
+// each sample adds w' times its kernel's trapezoid sum over the grid points within 7 h
+// (beyond, the kernel is below e^-24.5 of its peak).
+namespace {
+
+struct KdeSink {
+  float z = -INFINITY;
+  __device__ __forceinline__ bool weight(float) { return false; }
+  __device__ __forceinline__ void grad(int, float) {}
+  __device__ __forceinline__ void lam_edge(float, float, float) {}
+  __device__ __forceinline__ void position(float zz) { z = zz; }
+};
+
+struct KdeCtx {
+  const LamF& L;
+  const float4* pos;
+  const float4* aux;
+  const float4* wv;
+  const float4* ws;
+  int nx, nz;
+};
+
+// z and log2 w' of sample i of the group (z = -inf when d_L has no z; lw = -inf when w' = 0)
+__device__ __forceinline__ void kde_sample(const KdeCtx& C, const float4 v, float& z, float& lw) {
+  SampleIn s;
+  s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.npe2 = -to_log2(v.w);
+  s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
+  KdeSink sk;
+  float l = -INFINITY;
+  const bool ok = sample_lnw<false, float, KdeSink, false>(C.L, s, static_cast<const float*>(nullptr),
+                                                          C.nz, C.pos, C.aux, C.nx, C.wv, C.ws, l, sk);
+  z = sk.z;
+  lw = ok ? l : -INFINITY;
+}
+
+__device__ __forceinline__ float kde_z(const KdeCtx& C, const float4* smp, int64_t i) {
+  float z, lw;
+  kde_sample(C, __ldg(smp + i), z, lw);
+  return z;
+}
+
+// quantile q of the n z values starting at index v0 (sorted): linear between order statistics
+__device__ float kde_quantile(const KdeCtx& C, const float4* smp, int64_t v0, int n, float q) {
+  const float pos = q * (float)(n - 1);
+  const int i = min((int)floorf(pos), n - 1);
+  const float z0 = kde_z(C, smp, v0 + i);
+  if (i + 1 >= n) return z0;
+  return fmaf(pos - (float)i, kde_z(C, smp, v0 + i + 1) - z0, z0);
+}
+
+// k-th smallest (0-based) of |z_i - Q| over the n sorted values from v0, where the first
+// `nl` values are <= Q (their deviations fall with i) and the rest are > Q (rise with i)
+__device__ float kde_kth_dev(const KdeCtx& C, const float4* smp, int64_t v0, int n, int nl, float Q, int k) {
+  // A[a] = Q - z[nl - 1 - a] (a < nl, ascending), B[b] = z[nl + b] - Q (b < n - nl, ascending)
+  const int na = nl, nb = n - nl;
+  int lo = max(0, k + 1 - nb), hi = min(k + 1, na);   // number taken from A
+  for (int it = 0; it < 40 && lo < hi; ++it) {
+    const int ta = (lo + hi) >> 1, tb = k + 1 - ta;
+    // need A[ta-1] <= B[tb] and B[tb-1] <= A[ta]
+    const float a_next = ta < na ? Q - kde_z(C, smp, v0 + nl - 1 - ta) : INFINITY;
+    const float b_prev = tb > 0 ? kde_z(C, smp, v0 + nl + tb - 1) - Q : -INFINITY;
+    if (b_prev > a_next) lo = ta + 1; else hi = ta;
+  }
+  const int ta = lo, tb = k + 1 - ta;
+  const float a_last = ta > 0 ? Q - kde_z(C, smp, v0 + nl - ta) : -INFINITY;
+  const float b_last = tb > 0 ? kde_z(C, smp, v0 + nl + tb - 1) - Q : -INFINITY;
+  return fmaxf(a_last, b_last);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = blockIdx.x, k = blockIdx.y * WARPS + warp;
+  if (k >= A.K) return;
+  const KdeGroup grp = A.groups[g];
+  float* out = A.partials + ((size_t)k * A.stride + g) * PSTRIDE;
+  const LamF L = A.lf[k];
+  if (L.live == 0.f) {
+    if (lane == 0) { out[0] = -INFINITY; out[1] = 0.f; out[2] = 0.f; }
+    return;
+  }
+  const float* tb = A.tables + (size_t)k * A.tstride;
+  const float4* pos = reinterpret_cast<const float4*>(tb);
+  const float4* aux = reinterpret_cast<const float4*>(tb + 4 * A.nx);
+  const float4* wv = reinterpret_cast<const float4*>(tb + 8 * A.nx);
+  const KdeCtx C{L, pos, aux, wv, wv + (NW_WIN + 1), A.nx, A.nz};
+  const float4* smp = A.smp + grp.begin;
+  const int n = grp.count;
+
+  // ---- pass 1: weights (max, sum, sum of squares), Welford moments of z, valid range
+  float m = -INFINITY, s1 = 0.f, s2 = 0.f;
+  double wn = 0.0, wmean = 0.0, wM2 = 0.0;
+  int vmin = INT_MAX, vmax = -1;
+  for (int i = lane; i < n; i += 32) {
+    float z, lw;
+    kde_sample(C, __ldg(smp + i), z, lw);
+    if (z > -INFINITY) {
+      vmin = min(vmin, i);
+      vmax = max(vmax, i);
+      wn += 1.0;
+      const double d = (double)z - wmean;
+      wmean += d / wn;
+      wM2 += d * ((double)z - wmean);
+    }
+    if (lw > -INFINITY) {
+      if (lw > m) {
+        const float sc = ex2(m - lw);
+        s1 = fmaf(s1, sc, 1.f);
+        s2 = fmaf(s2, sc * sc, 1.f);
+        m = lw;
+      } else {
+        const float t = ex2(lw - m);
+        s1 += t;
+        s2 = fmaf(t, t, s2);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float om = __shfl_xor_sync(0xffffffffu, m, o);
+    const float o1 = __shfl_xor_sync(0xffffffffu, s1, o);
+    const float o2 = __shfl_xor_sync(0xffffffffu, s2, o);
+    const float M = fmaxf(m, om);
+    if (M > -INFINITY) {
+      const float ra = ex2(m - M), rb = ex2(om - M);
+      s1 = s1 * ra + o1 * rb;
+      s2 = s2 * ra * ra + o2 * rb * rb;
+      m = M;
+    }
+    const double bn = __shfl_xor_sync(0xffffffffu, wn, o);
+    const double bmean = __shfl_xor_sync(0xffffffffu, wmean, o);
+    const double bM2 = __shfl_xor_sync(0xffffffffu, wM2, o);
+    const double nn = wn + bn;
+    if (nn > 0.0) {   // Chan et al.'s pairwise update of (n, mean, M2)
+      const double d = bmean - wmean;
+      wM2 = wM2 + bM2 + d * d * wn * bn / nn;
+      wmean = wmean + d * bn / nn;
+      wn = nn;
+    }
+    vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
+  const int nv = (int)wn;
+  bool keep = m > -INFINITY && nv >= 2 && s1 * s1 >= A.neff_min * s2;
+
+  // ---- bandwidth (every lane computes the same value; the order statistics by lane 0)
+  float h = 0.f;
+  if (keep) {
+    const float shrink = exp2f(-0.2f * log2f((float)nv));
+    const float sigma = (float)sqrt(wM2 / (wn - 1.0));
+    if (A.rule == 0) {
+      h = 1.06f * sigma * shrink;
+    } else {
+      float hv = 0.f;
+      if (lane == 0) {
+        if (A.rule == 1) {
+          const float iqr = kde_quantile(C, smp, vmin, nv, 0.75f) - kde_quantile(C, smp, vmin, nv, 0.25f);
+          hv = 0.9f * fminf(sigma, iqr / 1.34f) * shrink;
+        } else {
+          const float Q = kde_quantile(C, smp, vmin, nv, 0.5f);
+          // values <= Q: binary search on the sorted z
+          int lo = 0, hi = nv;
+          for (int it = 0; it < 40 && lo < hi; ++it) {
+            const int mid = (lo + hi) >> 1;
+            if (kde_z(C, smp, vmin + mid) <= Q) lo = mid + 1; else hi = mid;
+          }
+          const float pos = 0.5f * (float)(nv - 1);
+          const int i0 = (int)floorf(pos);
+          const float d0 = kde_kth_dev(C, smp, vmin, nv, lo, Q, i0);
+          const float d1 = i0 + 1 < nv ? kde_kth_dev(C, smp, vmin, nv, lo, Q, i0 + 1) : d0;
+          const float mad = fmaf(pos - (float)i0, d1 - d0, d0);
+          hv = mad > 0.f ? Q : NAN;   // Q passed on; the sums below need every lane
+          h = mad;
+        }
+      }
+      if (A.rule == 1) {
+        h = __shfl_sync(0xffffffffu, hv, 0);
+      } else {
+        const float Q = __shfl_sync(0xffffffffu, hv, 0);
+        const float mad = __shfl_sync(0xffffffffu, h, 0);
+        h = 0.f;
+        if (mad > 0.f) {
+          const float inv9 = 1.f / (9.f * mad);
+          double num = 0.0, den = 0.0;
+          for (int i = vmin + lane; i <= vmax; i += 32) {
+            const float dz = kde_z(C, smp, i) - Q;
+            const float u = dz * inv9;
+            if (fabsf(u) < 1.f) {
+              const double a = 1.0 - (double)u * u;
+              num += (double)dz * dz * a * a * a * a;
+              den += a * (1.0 - 5.0 * (double)u * u);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+          }
+          if (den != 0.0 && num > 0.0) h = 1.06f * (float)sqrt((double)nv * num / (den * den)) * shrink;
+        }
+      }
+    }
+    keep = h > 0.f;
+  }
+  if (!keep) {
+    if (lane == 0) { out[0] = -INFINITY; out[1] = 0.f; out[2] = 0.f; }
+    return;
+  }
+
+  // ---- pass 2: sum_k w'_k sum_g c_g p_LOS(z_g) K_h(z_g - z_k), scaled by 2^-m
+  const float* pg = A.pgrid + (size_t)grp.pix * A.G;
+  const float dzg = A.dzg, inv_dzg = 1.f / dzg, reach = 7.f * h;
+  const float cexp = -0.5f * LOG2EF / (h * h);
+  float acc = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    float z, lw;
+    kde_sample(C, __ldg(smp + i), z, lw);
+    if (!(lw > -INFINITY)) continue;
+    const int g0 = max(0, (int)ceilf((z - reach) * inv_dzg));
+    const int g1 = min(A.G - 1, (int)floorf((z + reach) * inv_dzg));
+    float T = 0.f;
+    for (int gg = g0; gg <= g1; ++gg) {
+      const float d = fmaf((float)gg, dzg, -z);
+      const float c = (gg == 0 || gg == A.G - 1) ? 0.5f : 1.f;
+      T = fmaf(c * __ldg(pg + gg), ex2(cexp * d * d), T);
+    }
+    acc = fmaf(ex2(lw - m), T, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const float S = acc * dzg / (h * 2.50662827463100050242f);   // h sqrt(2 pi)
+    out[0] = S > 0.f ? m : -INFINITY;
+    out[1] = S;
+    out[2] = S * S;
+  }
+}
+
+__global__ void k_los_grid(const float* __restrict__ los, int n_pix, int nz, double zmax, int G,
+                           float* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_pix * G) return;
+  const int p = (int)(t / G), gq = (int)(t - (long long)p * G);
+  const double zg = gq * (zmax / (G - 1));
+  const double sc = (double)(nz - 1) / zmax;
+  int j = (int)floor(zg * sc);
+  if (j > nz - 2) j = nz - 2;
+  if (j < 0) j = 0;
+  const double tt = zg * sc - (double)j;
+  const float* row = los + (size_t)p * nz;
+  const double a = row[j], b = row[j + 1];
+  out[t] = (float)(a + tt * (b - a));
+}
+
+cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s) {
+  if (a.n_groups <= 0 || a.K <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)a.n_groups, (unsigned)((a.K + WARPS - 1) / WARPS));
+  k_kde<<<grid, THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_los_grid(const float* los, int n_pix, int nz, double zmax, int G, float* out,
+                            cudaStream_t s) {
+  const long long n = (long long)n_pix * G;
+  k_los_grid<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(los, n_pix, nz, zmax, G, out);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ plain path

@@ -43,9 +43,40 @@ struct FusedArgs {
   const LamF* lf;
   const float* tables;
   int tstride;
-  float* partials;        // [K][n_items][PSTRIDE]
+  float* partials;        // [K][stride][PSTRIDE], slot slot0 + item
   int* counter;           // next (item, slab) unit; zero at launch
+  int n_sched;            // schedule entries (units = n_sched * n_slabs)
+  int stride;             // partial slots per Lambda
+  int slot0;              // slot of item 0
 };
+
+// KDE form of the event term: one (event, pixel) group of samples
+struct KdeGroup {
+  int64_t begin;
+  int32_t count;
+  int32_t pix;
+};
+
+struct KdeArgs {
+  const float4* smp;
+  const KdeGroup* groups;
+  int n_groups;
+  const float* pgrid;     // [n_pix][G]: the LOS prior at the KDE grid points
+  int G;
+  float dzg;              // grid step z_max / (G - 1)
+  int rule;               // 0 Scott, 1 Silverman, 2 biweight
+  float neff_min;         // per-pixel N_eff threshold
+  int K;
+  int nx, nz;
+  const LamF* lf;
+  const float* tables;
+  int tstride;
+  float* partials;        // [K][stride][PSTRIDE], slot = group index
+  int stride;
+};
+cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s);
+cudaError_t launch_los_grid(const float* los, int n_pix, int nz, double zmax, int G, float* out,
+                            cudaStream_t s);
 
 struct PlainArgs {
   const float4* smp;

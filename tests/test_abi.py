@@ -44,6 +44,7 @@ def test_struct_sizes_match_header(g):
     assert ctypes.sizeof(g.Options) == 40 + 8
     assert ctypes.sizeof(g.Info) == 56
     assert ctypes.sizeof(g.TuneResult) == 24
+    assert ctypes.sizeof(g.KdeOptions) == 16
 
 
 def test_defaults(g):
