@@ -54,15 +54,16 @@ def load_peaks():
 
 # Algorithmic work per (sample, Lambda) evaluation of the fused value+gradient kernel,
 # counted from its formula (one transcendental = one special-function-unit op):
-#   value: ln(1+z), 1/(1+z), e^-|a-b| (mass mixture), e^-|r| (rate), 1/sqrt(E^2),
-#          ln(product), the product's reciprocal, (1+beta)-power above the smoothing
-#          window, the logsumexp exponential                                  -> 9 SFU
-#   gradient adds 1/(1+e^-|a-b|), 1/(1+e^-|r|), 1/D', 1/C                      -> 4 SFU
-# and about 190 FP32 operations in all (value ~75: Hermite position, LOS lerp, masses,
-# mixture, rate, Jacobian, online logsumexp; gradient ~115: the z-chain and 13
-# derivative terms with their accumulation).
+#   value, 8 SFU: 1/(1+z), log2(1+z), 2^-|a-b| (mass mixture), m1^(1+beta) above the
+#          smoothing window, 2^-|r| (rate), 1/sqrt(E^2), 1/(product's denominator), the
+#          logsumexp power; ~85 FP32: distance-to-position with its compensation terms
+#          (~20), LOS lerp, source masses, mixture, smoothing, C(m1), rate, E(z) and D'(z),
+#          the accurate log2 of the product (~12), accumulation
+#   gradient, 5 SFU: 1/(1+2^-|a-b|), 1/(1+2^-|r|), 1/D', 1/C, 1/p_LOS; ~81 FP32: the
+#          z-chain G_z (~25), J(x), window or closed-form C derivatives, and the 13
+#          statistics with their accumulation (~36)
 SFU_PER_EVAL = 13
-FP32_PER_EVAL = 190
+FP32_PER_EVAL = 166
 SMS, FP32_LANES, SFU_LANES, SM_MAX_GHZ = 152, 128, 16, 2.07
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fused value+gradient
@@ -225,6 +226,31 @@ def hmc_c1(g, synth, stream):
             "leapfrog_steps": HMC_LEAPFROG, "ms_per_trajectory": ms,
             "evals_per_s": (HMC_LEAPFROG + 1) * n / (ms / 1e3),
             "acceptance": float(acc.item()) / HMC_TRAJ}
+
+
+# The paper's KDE form of the event term (value only), on the bench's catalogue with the
+# first KDE_K points of the batch: Scott bandwidth, 256-point grid, per-pixel N_eff >= 2
+KDE_K = 16
+
+
+def kde_timing(g, ctx, lam, n_evals, stream):
+    import torch
+    k = max(1, min(KDE_K, lam.shape[0]))
+    lk = lam[:k].contiguous()
+    out = g._outputs(k, ctx.n_events, lk.device, False)
+    for _ in range(2):
+        g.loglik_kde(ctx._ctx, lk, ctx.n_events, stream=stream, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        g.loglik_kde(ctx._ctx, lk, ctx.n_events, stream=stream, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"K": k, "bandwidth": "scott", "n_grid": 256, "ms_per_call": ms,
+            "value": n_evals * k / (ms / 1e3), "unit": "evals/s (value only)"}
 
 
 def run_reference(args):
@@ -405,8 +431,10 @@ def main():
                "h2d_bytes_per_step": K * 13 * 8,
                "d2h_bytes_per_step": K * 8 + K * 4 + K * 13 * 8}
 
+    kde_line = None
     if not args.no_extras:
         hmc_line = hmc_c1(g, synth, stream)
+        kde_line = kde_timing(g, ctx, lam, n_s + n_i, stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
@@ -445,6 +473,7 @@ def main():
             line["e2e"] = e2e
             line["graph"] = graph_line
             line["hmc_c1"] = hmc_line
+            line["kde"] = kde_line
         if clocks is not None:
             line["clocks"] = clocks
         if base is not None:
