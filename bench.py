@@ -283,8 +283,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "c3: 2000 events x log-uniform 1k-16k samples, nside-64 x 2048 LOS, "
-                                   "1e7 injections, K=256", "sample": sample},
+            "config": {"workload": WORKLOAD_NAMES[WORKLOAD], "K": K_LAMBDA, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
