@@ -49,7 +49,8 @@ enum { S_H0, S_OM, S_A1, S_LX, S_AL, S_BE, S_MMIN, S_DM, S_MU, S_SIG, S_LU, S_SR
 // Fields ending in 2 are in log2 units (the value path works in log2 so that the
 // special-function unit's ex2/lg2 apply directly).
 struct __align__(16) LamF {
-  float H0c, H0c_lo, inv_dx, inv_dx_lo;  // H0/c and (nx-1)/xmax, each as a hi + lo pair
+  float H0c, H0c_lo, sxa, sxa_lo;        // H0/c as a hi + lo pair; H0/(c dx) (the table
+                                         // coordinate per Mpc) as a hi + lo pair
   float xmax, live, zstep, inv_zstep;     // live = 0: skip this Lambda; z_max/(n_z-1) and inverse
   float om, lp2, gam, gam_m3;             // log2(1+z_p); gamma; gamma - 3
   float gpk, alpha, beta, eps_b;          // gamma+kappa; 1+beta
@@ -239,13 +240,13 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const float4* __restrict__ wval,
                                            const float4* __restrict__ wslp, float& lw2,
                                            Sink& sink) {
-  // x = d_L H0 / c and the table coordinate x / dx carried with their rounding errors
-  // (exact products by FMA), so the LOS-grid position keeps ~1e-7 of a cell
+  // x = d_L H0 / c, and the table coordinate d_L H0 / (c dx) carried with its rounding
+  // error (an exact product by FMA and the constant's own low part), so the LOS-grid
+  // position keeps ~1e-7 of a cell
   const float x = s.dl * L.H0c;
   if (!(x > 0.f) || x > L.xmax) return false;
-  const float x_lo = fmaf(s.dl, L.H0c, -x) + s.dl * L.H0c_lo;
-  const float sx = x * L.inv_dx;
-  const float sx_lo = fmaf(x, L.inv_dx, -sx) + fmaf(x, L.inv_dx_lo, x_lo * L.inv_dx);
+  const float sx = s.dl * L.sxa;
+  const float sx_lo = fmaf(s.dl, L.sxa, -sx) + s.dl * L.sxa_lo;
 
   // --- d_L -> z: position on the LOS grid from the Hermite table (split precision)
   const int n = min((int)sx, nx - 2);
@@ -263,7 +264,12 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   if (s.m2 > s.m1) return false;
   const float u = 1.f + z;
   const float ru = rcp(u);
+
+  // --- source-frame masses (the support cuts first: samples outside skip the rest)
+  const float m1s = s.m1 * ru, m2s = s.m2 * ru;
+  if (m1s > L.mmax || m2s < L.mmin) return false;
   const float lu2 = lg2(u);
+  const float lm1s2 = s.lm1 - lu2, lm2s2 = s.lm2 - lu2;
 
   // --- LOS prior of the sample's pixel, linear in z (convex form: no cancellation)
   float p0 = 1.f, p1 = 1.f, plos = 1.f;
@@ -273,11 +279,6 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     plos = fmaf(tl, p1, (1.f - tl) * p0);
     if (!(plos > 0.f)) return false;
   }
-
-  // --- source-frame masses
-  const float m1s = s.m1 * ru, m2s = s.m2 * ru;
-  if (m1s > L.mmax || m2s < L.mmin) return false;
-  const float lm1s2 = s.lm1 - lu2, lm2s2 = s.lm2 - lu2;
 
   // p(m1): (1-lam) m^-alpha / Z_P + lam N(m; mu, sig) / Z_G as max + log2(1 + e^-|a-b|)
   const float a2 = fmaf(-L.alpha, lm1s2, fmaf(-L.alpha_lo, lm1s2, L.la2));

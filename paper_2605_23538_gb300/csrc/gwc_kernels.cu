@@ -413,8 +413,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     memset(&f, 0, sizeof(f));
     f.H0c = (float)(H0 / C_KMS);
     f.H0c_lo = (float)(H0 / C_KMS - (double)f.H0c);
-    f.inv_dx = (float)(1.0 / dx);
-    f.inv_dx_lo = (float)(1.0 / dx - (double)f.inv_dx);
+    const double sxa = H0 / C_KMS / dx;
+    f.sxa = (float)sxa;
+    f.sxa_lo = (float)(sxa - (double)f.sxa);
     f.xmax = (float)xmax;
     f.live = 1.f;
     f.zstep = (float)(zmax / (nz - 1));
