@@ -159,7 +159,7 @@ gwc_status gwc_loglik_grad(gwc_ctx* ctx, int32_t K, const double* d_lambda, doub
  * order statistics), biweight 1.06 s_bi n^-1/5 (s_bi^2 the printed biweight
  * midvariance about the median, u = (z - Q)/(9 MAD)); a pixel with fewer than two
  * samples in [0, z_max] or a zero bandwidth is dropped.  Kernels are summed over the
- * grid points within 7 h of each sample (the rest weigh less than e^-24.5).  The
+ * grid points within 6 h of each sample (the kernel's mass beyond is 2e-9).  The
  * selection term is the Monte-Carlo sum of gwc_loglik.  Outputs as gwc_loglik, except
  * that d_neff_event[K][n_events] receives the effective number of kept pixels,
  * (sum_j L_ij)^2 / sum_j L_ij^2, and flag bit 1 is never set (no per-event cut); an

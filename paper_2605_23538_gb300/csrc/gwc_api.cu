@@ -79,6 +79,7 @@ struct gwc_ctx {
   int kde_G = 0;
   float* kde_partials = nullptr;
   int64_t kde_stride = 0;
+  float2* kde_lm = nullptr;     // log2 masses of every sample
   uint64_t serial = 0;          // distinguishes contexts that reuse an address
   std::vector<int64_t> h_offsets;   // event offsets (for re-splitting the work items)
   int n_sms = 0;
@@ -135,7 +136,7 @@ void free_all(gwc_ctx* c) {
   c->prof_ev.clear();
   void* dev[] = {c->smp, c->pix, c->inj, c->los, c->pbar32, c->pbar64, c->items, c->sched,
                  c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->d_lam, c->d_out,
-                 c->kde_groups, c->kde_ev_group0, c->kde_sched_inj, c->kde_pgrid, c->kde_partials,
+                 c->kde_groups, c->kde_ev_group0, c->kde_sched_inj, c->kde_pgrid, c->kde_partials, c->kde_lm,
                  c->d_flags, c->sample_item, c->plain_lw, c->plain_tg};
   for (void* p : dev)
     if (p) cudaFree(p);
@@ -493,6 +494,12 @@ gwc_status kde_prepare(gwc_ctx* c, int G, cudaStream_t s) {
     e = dalloc(c, &c->kde_partials, (size_t)c->opt.max_K * (size_t)c->kde_stride * PSTRIDE);
     if (e != cudaSuccess) return oom(e, "KDE partials");
   }
+  if (!c->kde_lm && c->n_samples > 0) {
+    e = dalloc(c, &c->kde_lm, (size_t)c->n_samples);
+    if (e != cudaSuccess) return oom(e, "KDE log2 masses");
+    e = launch_log2_masses(c->smp, c->n_samples, c->kde_lm, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "KDE log2 masses");
+  }
   if (c->kde_G != G) {
     if (c->kde_pgrid) { cudaFree(c->kde_pgrid); c->kde_pgrid = nullptr; c->kde_G = 0; }
     e = dalloc(c, &c->kde_pgrid, (size_t)c->n_pix * G);
@@ -815,6 +822,7 @@ gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const g
   if (st != GWC_OK) return st;
   KdeArgs ka;
   ka.smp = c->smp;
+  ka.lm = c->kde_lm;
   ka.groups = c->kde_groups;
   ka.n_groups = (int)ng;
   ka.pgrid = c->kde_pgrid;

@@ -678,8 +678,8 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
 // Pass 1: z and w' of every sample -> the pixel's N_eff and the moments (and, for the
 // Silverman and biweight rules, order statistics: within a group the samples are sorted
 // by d_L, so by z, and the samples with a z form a contiguous index range).  Pass 2:
-// each sample adds w' times its kernel's trapezoid sum over the grid points within 7 h
-// (beyond, the kernel is below e^-24.5 of its peak).
+// each sample adds w' times its kernel's trapezoid sum over the grid points within 6 h
+// (the kernel's mass beyond is 2e-9).
 namespace {
 
 struct KdeSink {
@@ -697,13 +697,15 @@ struct KdeCtx {
   const float4* wv;
   const float4* ws;
   int nx, nz;
+  const float2* lm;   // the group's log2 masses
 };
 
-// z and log2 w' of sample i of the group (z = -inf when d_L has no z; lw = -inf when w' = 0)
-__device__ __forceinline__ void kde_sample(const KdeCtx& C, const float4 v, float& z, float& lw) {
+// z and log2 w' of a sample (z = -inf when d_L has no z; lw = -inf when w' = 0)
+__device__ __forceinline__ void kde_sample(const KdeCtx& C, const float4 v, const float2 lm, float& z,
+                                           float& lw) {
   SampleIn s;
   s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.npe2 = -to_log2(v.w);
-  s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
+  s.lm1 = lm.x; s.lm2 = lm.y;
   KdeSink sk;
   float l = -INFINITY;
   const bool ok = sample_lnw<false, float, KdeSink, false>(C.L, s, static_cast<const float*>(nullptr),
@@ -714,7 +716,7 @@ __device__ __forceinline__ void kde_sample(const KdeCtx& C, const float4 v, floa
 
 __device__ __forceinline__ float kde_z(const KdeCtx& C, const float4* smp, int64_t i) {
   float z, lw;
-  kde_sample(C, __ldg(smp + i), z, lw);
+  kde_sample(C, __ldg(smp + i), C.lm[i], z, lw);
   return z;
 }
 
@@ -763,24 +765,24 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   const float4* pos = reinterpret_cast<const float4*>(tb);
   const float4* aux = reinterpret_cast<const float4*>(tb + 4 * A.nx);
   const float4* wv = reinterpret_cast<const float4*>(tb + 8 * A.nx);
-  const KdeCtx C{L, pos, aux, wv, wv + (NW_WIN + 1), A.nx, A.nz};
+  const KdeCtx C{L, pos, aux, wv, wv + (NW_WIN + 1), A.nx, A.nz, A.lm + grp.begin};
   const float4* smp = A.smp + grp.begin;
   const int n = grp.count;
 
   // ---- pass 1: weights (max, sum, sum of squares), Welford moments of z, valid range
   float m = -INFINITY, s1 = 0.f, s2 = 0.f;
-  double wn = 0.0, wmean = 0.0, wM2 = 0.0;
+  float fn = 0.f, fmean = 0.f, fM2 = 0.f;   // Welford per lane in FP32, merged in FP64
   int vmin = INT_MAX, vmax = -1;
   for (int i = lane; i < n; i += 32) {
     float z, lw;
-    kde_sample(C, __ldg(smp + i), z, lw);
+    kde_sample(C, __ldg(smp + i), C.lm[i], z, lw);
     if (z > -INFINITY) {
       vmin = min(vmin, i);
       vmax = max(vmax, i);
-      wn += 1.0;
-      const double d = (double)z - wmean;
-      wmean += d / wn;
-      wM2 += d * ((double)z - wmean);
+      fn += 1.f;
+      const float d = z - fmean;
+      fmean = fmaf(d, 1.f / fn, fmean);
+      fM2 = fmaf(d, z - fmean, fM2);
     }
     if (lw > -INFINITY) {
       if (lw > m) {
@@ -795,6 +797,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
       }
     }
   }
+  double wn = fn, wmean = fmean, wM2 = fM2;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float om = __shfl_xor_sync(0xffffffffu, m, o);
@@ -887,22 +890,28 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
     return;
   }
 
-  // ---- pass 2: sum_k w'_k sum_g c_g p_LOS(z_g) K_h(z_g - z_k), scaled by 2^-m
+  // ---- pass 2: sum_k w'_k sum_g c_g p_LOS(z_g) K_h(z_g - z_k), scaled by 2^-m; each
+  //      kernel over the grid points within 6 h (its mass beyond is 2e-9)
   const float* pg = A.pgrid + (size_t)grp.pix * A.G;
-  const float dzg = A.dzg, inv_dzg = 1.f / dzg, reach = 7.f * h;
+  const float dzg = A.dzg, inv_dzg = 1.f / dzg, reach = 6.f * h;
   const float cexp = -0.5f * LOG2EF / (h * h);
   float acc = 0.f;
   for (int i = lane; i < n; i += 32) {
     float z, lw;
-    kde_sample(C, __ldg(smp + i), z, lw);
+    kde_sample(C, __ldg(smp + i), C.lm[i], z, lw);
     if (!(lw > -INFINITY)) continue;
     const int g0 = max(0, (int)ceilf((z - reach) * inv_dzg));
     const int g1 = min(A.G - 1, (int)floorf((z + reach) * inv_dzg));
-    float T = 0.f;
-    for (int gg = g0; gg <= g1; ++gg) {
-      const float d = fmaf((float)gg, dzg, -z);
-      const float c = (gg == 0 || gg == A.G - 1) ? 0.5f : 1.f;
-      T = fmaf(c * __ldg(pg + gg), ex2(cexp * d * d), T);
+    float T = 0.f, gf = (float)g0;
+    for (int gg = g0; gg <= g1; ++gg, gf += 1.f) {
+      const float d = fmaf(gf, dzg, -z);
+      T = fmaf(__ldg(pg + gg), ex2((cexp * d) * d), T);
+    }
+    // trapezoid: the two end points of the grid weigh half
+    if (g0 == 0 && g1 >= 0) T = fmaf(-0.5f * __ldg(pg), ex2((cexp * z) * z), T);
+    if (g1 == A.G - 1 && g0 <= g1) {
+      const float d = fmaf((float)(A.G - 1), dzg, -z);
+      T = fmaf(-0.5f * __ldg(pg + A.G - 1), ex2((cexp * d) * d), T);
     }
     acc = fmaf(ex2(lw - m), T, acc);
   }
@@ -930,6 +939,19 @@ __global__ void k_los_grid(const float* __restrict__ los, int n_pix, int nz, dou
   const float* row = los + (size_t)p * nz;
   const double a = row[j], b = row[j + 1];
   out[t] = (float)(a + tt * (b - a));
+}
+
+__global__ void k_log2_masses(const float4* __restrict__ smp, long long n, float2* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 v = __ldg(smp + i);
+  out[i] = make_float2(log2f(v.x), log2f(v.y));
+}
+
+cudaError_t launch_log2_masses(const float4* smp, long long n, float2* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_log2_masses<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(smp, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s) {

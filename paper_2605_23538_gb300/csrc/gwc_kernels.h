@@ -59,6 +59,7 @@ struct KdeGroup {
 
 struct KdeArgs {
   const float4* smp;
+  const float2* lm;       // log2 m1_det, log2 m2_det of every sample
   const KdeGroup* groups;
   int n_groups;
   const float* pgrid;     // [n_pix][G]: the LOS prior at the KDE grid points
@@ -75,6 +76,7 @@ struct KdeArgs {
   int stride;
 };
 cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s);
+cudaError_t launch_log2_masses(const float4* smp, long long n, float2* out, cudaStream_t s);
 cudaError_t launch_los_grid(const float* los, int n_pix, int nz, double zmax, int G, float* out,
                             cudaStream_t s);
 
