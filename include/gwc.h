@@ -122,6 +122,15 @@ typedef struct {
   int32_t chunk;         /* samples per work item, 64..4096 (default 2048) */
   int32_t lambda_tile;   /* Lambda points per CTA tile, 0..64 (0 = default 64) */
   int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 2) */
+  int32_t cap_per_pixel; /* > 0: keep at most this many samples of each (event, pixel), chosen
+                            at random as the paper's memory option does (it quotes 2500);
+                            0 = keep all (default).  The kept samples of a group are those
+                            with the smallest key, the (k+1)-th output of the SplitMix64
+                            generator (Steele, Lea and Flood 2014) started at cap_seed for
+                            input sample k, so a caller can reproduce the choice; N_i
+                            counts the kept samples, and every later output (per-sample
+                            terms included) refers to the kept samples only. */
+  uint64_t cap_seed;     /* seed of that choice (default 0) */
 } gwc_options;
 
 /* Fill *o with the defaults listed above. */

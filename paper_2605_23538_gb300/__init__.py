@@ -59,7 +59,8 @@ class Options(ctypes.Structure):
                 ("accum", ctypes.c_int32), ("los_dtype", ctypes.c_int32),
                 ("n_x_table", ctypes.c_int32), ("max_K", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32),
-                ("lambda_group", ctypes.c_int32)]
+                ("lambda_group", ctypes.c_int32), ("cap_per_pixel", ctypes.c_int32),
+                ("cap_seed", ctypes.c_uint64)]
 
 
 class Info(ctypes.Structure):
@@ -346,6 +347,46 @@ def sample_terms_noalloc(lam, samples, pix, injections, los, z_max, n_x_table=51
                                         _stream_ptr(stream))
     _check(st)
     return lnw, d, c
+
+
+def _splitmix64_outputs(seed, k):
+    """The (k+1)-th outputs of the SplitMix64 generator started at `seed` (uint64 arrays)."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(k, dtype=np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def cap_selection(cat, cap, seed=0):
+    """Input indices of the samples kept by the cap_per_pixel option (see include/gwc.h):
+    in each (event, pixel) group larger than `cap`, the `cap` samples with the smallest
+    SplitMix64 key; per event in input order.  Returns (indices, new offsets)."""
+    off = np.asarray(cat["offsets"], dtype=np.int64)
+    pix = np.asarray(cat["pix"])
+    keep, counts = [], []
+    for e in range(len(off) - 1):
+        idx = np.arange(off[e], off[e + 1])
+        sel = []
+        for p in np.unique(pix[idx]):
+            run = idx[pix[idx] == p]
+            if cap > 0 and len(run) > cap:
+                run = run[np.argsort(_splitmix64_outputs(seed, run), kind="stable")[:cap]]
+            sel.append(run)
+        sel = np.sort(np.concatenate(sel))
+        keep.append(sel)
+        counts.append(len(sel))
+    return np.concatenate(keep), np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+
+
+def capped(cat, cap, seed=0):
+    """The catalogue as the library holds it under cap_per_pixel = cap, cap_seed = seed."""
+    idx, off = cap_selection(cat, cap, seed)
+    out = dict(cat)
+    for k in ("m1", "m2", "dl", "lnpe", "pix"):
+        out[k] = np.asarray(cat[k])[idx]
+    out["offsets"] = off
+    return out
 
 
 def sample_order(cat):

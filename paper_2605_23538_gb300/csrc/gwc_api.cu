@@ -526,6 +526,8 @@ void gwc_default_options(gwc_options* o) {
   o->chunk = 2048;
   o->lambda_tile = 0;
   o->lambda_group = 0;
+  o->cap_per_pixel = 0;
+  o->cap_seed = 0;
 }
 
 gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_injections* inj,
@@ -548,6 +550,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   if (o.lambda_tile < 0 || o.lambda_tile > MAX_SLAB)
     return fail(nullptr, GWC_E_INVALID, "lambda_tile must be in [0, " + std::to_string(MAX_SLAB) + "]");
   if (!(o.neff_min_event >= 0.0) || !(o.neff_min_sel >= 0.0)) return fail(nullptr, GWC_E_INVALID, "N_eff thresholds must be >= 0");
+  if (o.cap_per_pixel < 0) return fail(nullptr, GWC_E_INVALID, "cap_per_pixel must be >= 0");
 
   // ---- validate the events
   const int32_t ne = ev->n_events;
@@ -557,7 +560,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   for (int32_t e = 0; e < ne; ++e)
     if (ev->offsets[e + 1] <= ev->offsets[e])
       return fail(nullptr, GWC_E_INVALID, "offsets must be strictly increasing (event " + std::to_string(e) + ")");
-  const int64_t ns = ev->offsets[ne];
+  int64_t ns = ev->offsets[ne];
   if (ns > 0 && (!ev->m1_det || !ev->m2_det || !ev->dl_mpc || !ev->ln_pe_prior || !ev->pix))
     return fail(nullptr, GWC_E_INVALID, "NULL sample array");
   if (!finite_all(ev->m1_det, ns) || !finite_all(ev->m2_det, ns) || !finite_all(ev->dl_mpc, ns) ||
@@ -571,6 +574,60 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   for (int64_t k = 0; k < ns; ++k)
     if (ev->pix[k] < 0 || ev->pix[k] >= los->n_pix)
       return fail(nullptr, GWC_E_INVALID, "pixel id out of range at sample " + std::to_string(k));
+  // ---- per-pixel cap (the paper's memory option): in each (event, pixel) group larger
+  //      than the cap keep the cap samples with the smallest key, the (k+1)-th output of
+  //      SplitMix64 started at cap_seed for input sample k
+  gwc_events evc{};
+  std::vector<float> cm1, cm2, cdl, clp;
+  std::vector<int32_t> cpx;
+  std::vector<int64_t> coff;
+  if (o.cap_per_pixel > 0) {
+    auto key = [&](int64_t k) {
+      uint64_t z = o.cap_seed + (uint64_t)(k + 1) * 0x9e3779b97f4a7c15ull;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      return z ^ (z >> 31);
+    };
+    coff.assign((size_t)ne + 1, 0);
+    std::vector<int64_t> idx, kept;
+    for (int32_t e = 0; e < ne; ++e) {
+      idx.clear();
+      for (int64_t k = ev->offsets[e]; k < ev->offsets[e + 1]; ++k) idx.push_back(k);
+      std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return ev->pix[a] < ev->pix[b]; });
+      kept.clear();
+      for (size_t a = 0; a < idx.size();) {
+        size_t b = a;
+        while (b < idx.size() && ev->pix[idx[b]] == ev->pix[idx[a]]) ++b;
+        if ((int64_t)(b - a) > o.cap_per_pixel) {
+          std::vector<int64_t> run(idx.begin() + a, idx.begin() + b);
+          std::nth_element(run.begin(), run.begin() + o.cap_per_pixel, run.end(),
+                           [&](int64_t x, int64_t y) { return key(x) < key(y); });
+          kept.insert(kept.end(), run.begin(), run.begin() + o.cap_per_pixel);
+        } else {
+          kept.insert(kept.end(), idx.begin() + a, idx.begin() + b);
+        }
+        a = b;
+      }
+      std::sort(kept.begin(), kept.end());   // input order within the event
+      for (int64_t k : kept) {
+        cm1.push_back(ev->m1_det[k]);
+        cm2.push_back(ev->m2_det[k]);
+        cdl.push_back(ev->dl_mpc[k]);
+        clp.push_back(ev->ln_pe_prior[k]);
+        cpx.push_back(ev->pix[k]);
+      }
+      coff[(size_t)e + 1] = (int64_t)cm1.size();
+    }
+    evc.n_events = ne;
+    evc.offsets = coff.data();
+    evc.m1_det = cm1.data();
+    evc.m2_det = cm2.data();
+    evc.dl_mpc = cdl.data();
+    evc.ln_pe_prior = clp.data();
+    evc.pix = cpx.data();
+    ev = &evc;
+    ns = coff[(size_t)ne];
+  }
   const int64_t nlos = (int64_t)los->n_pix * los->n_z;
   std::vector<float> los_f((size_t)nlos);
   if (los->dtype == GWC_LOS_F32) {

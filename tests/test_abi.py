@@ -41,7 +41,7 @@ def test_struct_sizes_match_header(g):
     assert ctypes.sizeof(g.Events) == 56
     assert ctypes.sizeof(g.Los) == 32
     assert ctypes.sizeof(g.Injections) == 48
-    assert ctypes.sizeof(g.Options) == 40 + 8
+    assert ctypes.sizeof(g.Options) == 56
     assert ctypes.sizeof(g.Info) == 56
     assert ctypes.sizeof(g.TuneResult) == 24
     assert ctypes.sizeof(g.KdeOptions) == 16
@@ -51,6 +51,7 @@ def test_defaults(g):
     o = g.default_options()
     assert (o.neff_min_event, o.neff_min_sel, o.accum, o.los_dtype) == (2.0, 0.0, 0, 0)
     assert (o.n_x_table, o.max_K, o.chunk, o.lambda_tile, o.lambda_group) == (512, 256, 2048, 0, 0)
+    assert (o.cap_per_pixel, o.cap_seed) == (0, 0)
 
 
 def test_invalid_inputs_rejected_before_any_device_work(g, synth):
@@ -94,3 +95,26 @@ def test_null_context_calls_fail_cleanly(g):
     lib.gwc_destroy(None)
     info = g.Info()
     assert lib.gwc_get_info(None, ctypes.byref(info)) == -1
+
+
+def test_cap_selection_keeps_the_smallest_keys(g, synth):
+    # SplitMix64 reference values (generator started at 1234567): its first outputs
+    first = g._splitmix64_outputs(1234567, np.arange(3))
+    assert [int(v) for v in first] == [6457827717110365317, 3203168211198807973, 9817491932198370423]
+    w = synth.scaled("cap", 6, ("uniform", 300, 900), 8, 128, 1000, "found")
+    cat = synth.catalogue(w)
+    idx, off = g.cap_selection(cat, 20, seed=99)
+    for e in range(6):
+        a, b = cat["offsets"][e], cat["offsets"][e + 1]
+        sel = idx[off[e]:off[e + 1]]
+        assert np.all(np.diff(sel) > 0) and sel.min() >= a and sel.max() < b
+        for p in np.unique(cat["pix"][a:b]):
+            run = np.arange(a, b)[cat["pix"][a:b] == p]
+            kept = sel[cat["pix"][sel] == p]
+            assert len(kept) == min(len(run), 20)
+            if len(run) > 20:   # exactly the 20 smallest keys of the run
+                keys = g._splitmix64_outputs(99, run)
+                assert set(kept) == set(run[np.argsort(keys)[:20]])
+    other, _ = g.cap_selection(cat, 20, seed=100)
+    assert not np.array_equal(idx, other)
+    assert len(g.cap_selection(cat, 0)[0]) == len(cat["m1"])

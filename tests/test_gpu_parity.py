@@ -327,3 +327,22 @@ def test_invalid_calls(torch, g, synth, cat_c1):
             ctx.loglik(dev(torch, np.vstack([synth.FIDUCIAL] * 3)))   # K > max_K
         with pytest.raises(TypeError):
             ctx.loglik(torch.zeros((1, 13), dtype=torch.float32, device="cuda"))
+
+
+def test_cap_per_pixel_matches_the_oracle_on_the_capped_catalogue(torch, g, orc, synth, cat_ragged):
+    # the library's random per-pixel cap and the same choice made in numpy must give the
+    # same catalogue: compare both paths against the oracle on the capped catalogue
+    cap, seed = 40, 2024
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(5, purpose=81)])
+    small = g.capped(cat_ragged, cap, seed)
+    assert len(small["m1"]) < len(cat_ragged["m1"])
+    ref = orc.loglik(small, lam, grad=True)
+    with g.Context(cat_ragged, max_K=6, cap_per_pixel=cap, cap_seed=seed) as ctx:
+        assert ctx.info()["n_samples"] == len(small["m1"])
+        got = ctx.loglik_grad(dev(torch, lam))
+        kde = ctx.loglik_kde(dev(torch, lam))
+    compare(got, ref, grad=True, label=f"cap {cap}")
+    kref = orc.loglik_kde(small, lam)
+    fin = np.isfinite(kref["lnL_event"])
+    d = np.abs(kde["lnL_event"].cpu().numpy()[fin] - kref["lnL_event"][fin]).max()
+    assert d <= 1e-5, d
