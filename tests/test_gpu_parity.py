@@ -346,3 +346,21 @@ def test_cap_per_pixel_matches_the_oracle_on_the_capped_catalogue(torch, g, orc,
     fin = np.isfinite(kref["lnL_event"])
     d = np.abs(kde["lnL_event"].cpu().numpy()[fin] - kref["lnL_event"][fin]).max()
     assert d <= 1e-5, d
+
+
+def test_spectral_siren_single_uniform_row(torch, g, orc, synth, cat_c1):
+    # spectral-siren mode: one LOS row, uniform in comoving volume, for every sample
+    z_max = float(cat_c1["z_max"])
+    z = np.linspace(0.0, z_max, 512)
+    E = np.sqrt(0.3 * (1 + z) ** 3 + 0.7)
+    dc = np.concatenate([[0.0], np.cumsum(0.5 * (1 / E[1:] + 1 / E[:-1]) * np.diff(z))])
+    row = dc ** 2 / E
+    row /= np.sum(0.5 * (row[1:] + row[:-1]) * np.diff(z))
+    cat = dict(cat_c1)
+    cat["los"] = row[None, :].astype(np.float32)
+    cat["pix"] = np.zeros_like(cat_c1["pix"])
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(3, purpose=82)])
+    ref = orc.loglik(cat, lam, grad=True)
+    with g.Context(cat, max_K=4) as ctx:
+        got = ctx.loglik_grad(dev(torch, lam))
+    compare(got, ref, grad=True, label="spectral siren")
