@@ -528,13 +528,10 @@ constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
 template <bool GRAD, bool KAHAN, typename RowT>
 __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* sm) {
   const int CH = A.chunk;
-  float* s_m1 = sm;
-  float* s_m2 = s_m1 + CH;
-  float* s_dl = s_m2 + CH;
-  float* s_lpe = s_dl + CH;
-  float* s_lm1 = s_lpe + CH;
-  float* s_lm2 = s_lm1 + CH;
-  int* s_pix = reinterpret_cast<int*>(s_lm2 + CH);
+  // staged samples: {m1, m2, d_L, -log2 pi}, {log2 m1, log2 m2}, pixel (3 loads a sample)
+  float4* s_a = reinterpret_cast<float4*>(sm);
+  float2* s_b = reinterpret_cast<float2*>(s_a + CH);
+  int* s_pix = reinterpret_cast<int*>(s_b + CH);
   float* s_part = reinterpret_cast<float*>(s_pix + CH);   // [slab][G][PSTRIDE]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -548,12 +545,8 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
   const float4* src = inj ? A.inj : A.smp;
   for (int i = tid; i < it.count; i += THREADS) {
     const float4 v = __ldg(src + it.begin + i);
-    s_m1[i] = v.x;
-    s_m2[i] = v.y;
-    s_dl[i] = v.z;
-    s_lpe[i] = -to_log2(v.w);
-    s_lm1[i] = log2f(v.x);
-    s_lm2[i] = log2f(v.y);
+    s_a[i] = make_float4(v.x, v.y, v.z, -to_log2(v.w));
+    s_b[i] = make_float2(log2f(v.x), log2f(v.y));
     s_pix[i] = inj ? 0 : __ldg(A.pix + it.begin + i);
   }
   __syncthreads();
@@ -575,8 +568,10 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       const float4* ws = wv + (NW_WIN + 1);
       for (int i = a + lane; i < b; i += 32) {
         SampleIn s;
-        s.m1 = s_m1[i]; s.m2 = s_m2[i]; s.dl = s_dl[i]; s.npe2 = s_lpe[i];
-        s.lm1 = s_lm1[i]; s.lm2 = s_lm2[i];
+        const float4 va = s_a[i];
+        const float2 vb = s_b[i];
+        s.m1 = va.x; s.m2 = va.y; s.dl = va.z; s.npe2 = va.w;
+        s.lm1 = vb.x; s.lm2 = vb.y;
         float lw;
         AccSink<GRAD, KAHAN> sink(acc);
         if (inj)
