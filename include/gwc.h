@@ -188,6 +188,23 @@ gwc_status gwc_loglik_kde(gwc_ctx* ctx, int32_t K, const double* d_lambda,
                           double* d_ln_xi, double* d_neff_sel, double* d_lnL_total,
                           int32_t* d_flags, void* stream);
 
+/* The parts of the likelihood that shards of a catalogue combine (the survey's event
+ * sharding: one exchange of ~K (3 + 26) numbers).  A context built from a subset of the
+ * events and a subset of the found injections, with n_draw of the whole injection set,
+ * gives for its share: d_lnL_event, d_neff_event, d_ln_xi (ln of its injections' sum
+ * over the whole n_draw), d_neff_sel and d_flags as gwc_loglik; d_sum_events[K] = the sum
+ * of its events' ln L_i (-inf if one has no weight); and, when both are non-NULL,
+ * d_grad_events[K][13] (gradient of that sum) and d_grad_ln_xi[K][13] (gradient of its
+ * ln xi).  Shards combine exactly: xi = sum over shards of xi_r, so
+ *   ln L = sum_r sum_events_r - N_det ln(sum_r xi_r)
+ *   grad = sum_r grad_events_r - N_det sum_r (xi_r / xi) grad_ln_xi_r
+ * with N_det the number of events over all shards, and N_eff,sel = (sum xi_r)^2 /
+ * sum (xi_r^2 / N_eff,sel,r).  No total is formed here. */
+gwc_status gwc_loglik_parts(gwc_ctx* ctx, int32_t K, const double* d_lambda, double* d_lnL_event,
+                            double* d_neff_event, double* d_ln_xi, double* d_neff_sel,
+                            double* d_sum_events, int32_t* d_flags, double* d_grad_events,
+                            double* d_grad_ln_xi, void* stream);
+
 /* The plain single-Lambda path, kept as the speed-up baseline: the same per-sample
  * arithmetic, one Lambda per launch sequence, every sample re-read from memory for each
  * Lambda, per-sample weights (and, for the gradient, per-sample weighted derivatives)

@@ -90,7 +90,7 @@ EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read",
            "gwc_sample_terms", "gwc_sample_terms_noalloc", "gwc_graph_create", "gwc_graph_launch",
            "gwc_graph_destroy", "gwc_hmc_create", "gwc_hmc_launch", "gwc_hmc_destroy",
-           "gwc_autotune", "gwc_default_kde_options", "gwc_loglik_kde")
+           "gwc_autotune", "gwc_default_kde_options", "gwc_loglik_kde", "gwc_loglik_parts")
 
 
 def lib():
@@ -153,6 +153,8 @@ def lib():
         L.gwc_default_kde_options.argtypes = [ctypes.POINTER(KdeOptions)]
         L.gwc_loglik_kde.restype = ctypes.c_int
         L.gwc_loglik_kde.argtypes = [vp, i32, vp, ctypes.POINTER(KdeOptions), vp, vp, vp, vp, vp, vp, vp]
+        L.gwc_loglik_parts.restype = ctypes.c_int
+        L.gwc_loglik_parts.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.gwc_autotune.restype = ctypes.c_int
         L.gwc_autotune.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(TuneResult)]
         _lib = L
@@ -549,6 +551,28 @@ class Context:
 
     def loglik_kde(self, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, stream=None):
         return loglik_kde(self._ctx, lam, self.n_events, bw, n_grid, neff_min_pixel, stream)
+
+    def loglik_parts(self, lam, grad=True, stream=None):
+        """gwc_loglik_parts: this context's share of a sharded catalogue (see shard.merge_parts)."""
+        import torch
+        if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
+            raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
+        lam = lam.contiguous()
+        K = lam.shape[0]
+        f64 = dict(dtype=torch.float64, device=lam.device)
+        out = _outputs(K, self.n_events, lam.device, False)
+        del out["lnL_total"]
+        out["sum_events"] = torch.empty(K, **f64)
+        if grad:
+            out["grad_events"] = torch.empty((K, NUM_PARAMS), **f64)
+            out["grad_ln_xi"] = torch.empty((K, NUM_PARAMS), **f64)
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(lib().gwc_loglik_parts(self._ctx, K, p(lam), p(out["lnL_event"]), p(out["neff_event"]),
+                                      p(out["ln_xi"]), p(out["neff_sel"]), p(out["sum_events"]),
+                                      p(out["flags"]), p(out.get("grad_events")), p(out.get("grad_ln_xi")),
+                                      _stream_ptr(stream)), self._ctx)
+        out["n_events"] = self.n_events
+        return out
 
     def loglik_plain(self, lam, grad=True, stream=None):
         return loglik_plain(self._ctx, lam, self.n_events, grad, stream)

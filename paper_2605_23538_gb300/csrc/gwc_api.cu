@@ -306,8 +306,12 @@ gwc_status run_prologue(gwc_ctx* c, int K, const double* d_lambda, bool grad, cu
 
 gwc_status run_merge(gwc_ctx* c, int K, int P, bool grad, double* lnL_event, double* neff_event,
                      double* ln_xi, double* neff_sel, double* lnL_total, int32_t* flags,
-                     double* grad_total, cudaStream_t s) {
+                     double* grad_total, cudaStream_t s, double* sum_events = nullptr,
+                     double* grad_events = nullptr, double* grad_ln_xi = nullptr) {
   MergeArgs ma;
+  ma.sum_events = sum_events;
+  ma.grad_events = grad_events;
+  ma.grad_ln_xi = grad_ln_xi;
   ma.partials = c->partials;
   ma.n_items = c->n_items;
   ma.P = P;
@@ -386,7 +390,9 @@ gwc_status launch_fused_items(gwc_ctx* c, int32_t K, bool grad, const int32_t* s
 
 gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_event,
                      double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
-                     int32_t* flags, double* grad_total, bool grad, cudaStream_t s) {
+                     int32_t* flags, double* grad_total, bool grad, cudaStream_t s,
+                     double* sum_events = nullptr, double* grad_events = nullptr,
+                     double* grad_ln_xi = nullptr) {
   cudaError_t pe = prof_mark(c, 0, s);
   if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
   gwc_status st = run_prologue(c, K, d_lambda, grad, s, c->counter);
@@ -397,7 +403,7 @@ gwc_status run_fused(gwc_ctx* c, int32_t K, const double* d_lambda, double* lnL_
   cudaError_t e;
   if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
   st = run_merge(c, K, 1, grad, lnL_event, neff_event, ln_xi, neff_sel, lnL_total, flags,
-                 grad_total, s);
+                 grad_total, s, sum_events, grad_events, grad_ln_xi);
   if (st != GWC_OK) return st;
   if ((e = prof_mark(c, 3, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
   return GWC_OK;
@@ -921,6 +927,23 @@ gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const g
   if (e != cudaSuccess) return cuda_fail(c, e, "merge launch");
   if ((e = prof_mark(c, 3, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
   return GWC_OK;
+}
+
+gwc_status gwc_loglik_parts(gwc_ctx* c, int32_t K, const double* d_lambda, double* d_lnL_event,
+                            double* d_neff_event, double* d_ln_xi, double* d_neff_sel,
+                            double* d_sum_events, int32_t* d_flags, double* d_grad_events,
+                            double* d_grad_ln_xi, void* stream) {
+  if (!d_sum_events) return fail(c, GWC_E_INVALID, "d_sum_events is NULL");
+  if ((d_grad_events == nullptr) != (d_grad_ln_xi == nullptr))
+    return fail(c, GWC_E_INVALID, "give both gradient parts or neither");
+  // check_call requires a non-NULL total pointer; d_sum_events stands in for it
+  gwc_status st = check_call(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel,
+                             d_sum_events, d_flags);
+  if (st != GWC_OK) return st;
+  const bool grad = d_grad_events != nullptr;
+  return run_fused(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel, nullptr, d_flags,
+                   nullptr, grad, static_cast<cudaStream_t>(stream), d_sum_events, d_grad_events,
+                   d_grad_ln_xi);
 }
 
 gwc_status gwc_loglik_plain(gwc_ctx* c, int32_t K, const double* d_lambda, double* d_lnL_event,

@@ -1085,10 +1085,14 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     if (tid == 0) {
       A.ln_xi[k] = -INFINITY;
       A.neff_sel[k] = 0.0;
-      A.lnL_total[k] = -INFINITY;
+      if (A.lnL_total) A.lnL_total[k] = -INFINITY;
+      if (A.sum_events) A.sum_events[k] = -INFINITY;
       A.flags[k] = 1;
-      if (GRAD)
-        for (int i = 0; i < NP; ++i) A.grad_total[(size_t)k * NP + i] = 0.0;
+      for (int i = 0; i < NP; ++i) {
+        if (GRAD && A.grad_total) A.grad_total[(size_t)k * NP + i] = 0.0;
+        if (GRAD && A.grad_events) A.grad_events[(size_t)k * NP + i] = 0.0;
+        if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NP + i] = 0.0;
+      }
     }
     return;
   }
@@ -1261,11 +1265,16 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     A.ln_xi[k] = lnxi;
     A.neff_sel[k] = neffs;
     A.flags[k] = flag;
-    A.lnL_total[k] = (flag || dead) ? -INFINITY : tot - (double)ne * lnxi;
-    if (GRAD)
+    if (A.lnL_total) A.lnL_total[k] = (flag || dead) ? -INFINITY : tot - (double)ne * lnxi;
+    if (GRAD && A.grad_total)
       for (int i = 0; i < NP; ++i)
         A.grad_total[(size_t)k * NP + i] =
             (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + lamd_dc(D, i));
+    if (A.sum_events) A.sum_events[k] = dead ? -INFINITY : tot;
+    for (int i = 0; i < NP; ++i) {
+      if (GRAD && A.grad_events) A.grad_events[(size_t)k * NP + i] = dead ? 0.0 : gt[i];
+      if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NP + i] = S1 > 0.0 ? G[i] / S1 + lamd_dc(D, i) : 0.0;
+    }
   }
 }
 

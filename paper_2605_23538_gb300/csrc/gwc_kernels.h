@@ -121,6 +121,11 @@ struct MergeArgs {
   double* lnL_total;
   int32_t* flags;
   double* grad_total;
+  // optional parts for merging shards of a catalogue (may be null): sum_i ln L_i [K],
+  // its gradient [K][13], and the gradient of ln xi [K][13]
+  double* sum_events = nullptr;
+  double* grad_events = nullptr;
+  double* grad_ln_xi = nullptr;
 };
 
 // One leapfrog stage of K Hamiltonian Monte Carlo chains (one warp per chain, a lane

@@ -364,3 +364,29 @@ def test_spectral_siren_single_uniform_row(torch, g, orc, synth, cat_c1):
     with g.Context(cat, max_K=4) as ctx:
         got = ctx.loglik_grad(dev(torch, lam))
     compare(got, ref, grad=True, label="spectral siren")
+
+
+def test_event_shards_merge_to_the_full_likelihood(torch, g, orc, synth, cat_ragged):
+    # two contexts on one GPU, each with half of the events and half of the injections
+    # (and the whole n_draw), combined by shard.merge_parts; compared with the oracle on the
+    # whole catalogue exactly as a single context would be
+    from paper_2605_23538_gb300 import shard
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(5, purpose=83)])
+    ref = orc.loglik(cat_ragged, lam, grad=True)
+    ne, ni = len(cat_ragged["offsets"]) - 1, len(cat_ragged["inj_m1"])
+    halves = []
+    for ev, (a, b) in (([*range(0, ne // 2)], (0, ni // 2)), ([*range(ne // 2, ne)], (ni // 2, ni))):
+        part = synth.subset_events(cat_ragged, ev)
+        for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
+            part[k] = cat_ragged[k][a:b]
+        halves.append(part)
+    parts = []
+    for part in halves:
+        with g.Context(part, max_K=6, neff_min_sel=0.0) as ctx:
+            parts.append(ctx.loglik_parts(dev(torch, lam)))
+    merged = shard.merge_parts(parts)
+    got = {"lnL_event": torch.cat([p["lnL_event"] for p in parts], dim=1),
+           "neff_event": torch.cat([p["neff_event"] for p in parts], dim=1)}
+    for k in ("lnL_total", "ln_xi", "neff_sel", "flags", "grad_total"):
+        got[k] = torch.as_tensor(merged[k])
+    compare(got, ref, grad=True, label="two event shards")
