@@ -121,7 +121,7 @@ typedef struct {
   int32_t max_K;         /* largest Lambda batch a call may pass (default 256) */
   int32_t chunk;         /* samples per work item, 64..4096 (default 2048) */
   int32_t lambda_tile;   /* Lambda points per CTA tile, 0..64 (0 = default 64) */
-  int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 2) */
+  int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 1) */
   int32_t cap_per_pixel; /* > 0: keep at most this many samples of each (event, pixel), chosen
                             at random as the paper's memory option does (it quotes 2500);
                             0 = keep all (default).  The kept samples of a group are those

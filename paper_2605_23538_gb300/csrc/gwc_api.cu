@@ -146,6 +146,9 @@ void free_all(gwc_ctx* c) {
 }
 
 constexpr int PROF_SLOTS = 256;
+// one warp per Lambda point: warps then claim points from a shared counter, so uneven
+// per-point work (cuts, early rejections) leaves no warp idle at the unit's barrier
+constexpr int DEFAULT_LAMBDA_GROUP = 1;
 
 // fold the recorded quadruples into the sums (waits for them)
 cudaError_t prof_drain(gwc_ctx* c) {
@@ -354,7 +357,7 @@ gwc_status launch_fused_items(gwc_ctx* c, int32_t K, bool grad, const int32_t* s
   fa.n_items = c->n_items;
   fa.n_slabs = n_slabs;
   fa.slab = slab;
-  fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : 2;
+  fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
   fa.K = K;
   fa.chunk = c->opt.chunk;
   fa.lf = c->lf;
@@ -1151,7 +1154,7 @@ gwc_status gwc_graph_create(gwc_ctx* c, int32_t K, const double* d_lambda, int32
     FusedArgs fa{};
     fa.chunk = c->opt.chunk;
     fa.slab = slab;
-    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : 2;
+    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
     const bool grad = want_grad != 0, kahan = c->opt.accum == 1;
     const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
                          ((uint64_t)grad << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;
@@ -1318,7 +1321,7 @@ gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const doubl
     FusedArgs fa{};
     fa.chunk = c->opt.chunk;
     fa.slab = slab;
-    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : 2;
+    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
     const bool kahan = c->opt.accum == 1;
     const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
                          (1ull << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;

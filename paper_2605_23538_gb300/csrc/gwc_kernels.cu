@@ -526,7 +526,7 @@ constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
 // One (item, Lambda-slab) unit: stage the item's samples, sweep them for the slab's
 // Lambda points, combine the warp groups' sums into the unit's partials.
 template <bool GRAD, bool KAHAN, typename RowT>
-__device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* sm) {
+__device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* sm, int* s_next) {
   const int CH = A.chunk;
   // staged samples: {m1, m2, d_L, -log2 pi}, {log2 m1, log2 m2}, pixel (3 loads a sample)
   float4* s_a = reinterpret_cast<float4*>(sm);
@@ -549,6 +549,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     s_b[i] = make_float2(log2f(v.x), log2f(v.y));
     s_pix[i] = inj ? 0 : __ldg(A.pix + it.begin + i);
   }
+  if (tid == 0) *s_next = 0;
   __syncthreads();
 
   const int k0 = slab * A.slab;
@@ -556,7 +557,18 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
   const int nx = A.nx, nz = A.nz;
   const int a = (int)((long long)it.count * wg / G);
   const int b = (int)((long long)it.count * (wg + 1) / G);
-  for (int kk = gidx; kk < nk; kk += ngroups) {
+  // With one warp per group each warp takes the next Lambda point of the tile from a
+  // counter (the work per point varies, e.g. with how many samples fall outside the mass
+  // support); a point's sums are still formed by one warp in one order, so the result
+  // does not depend on which warp took it.  Groups of several warps take every
+  // ngroups-th point.
+  auto next_k = [&](int prev) {
+    if (G != 1) return prev + ngroups;
+    int v = 0;
+    if (lane == 0) v = atomicAdd(s_next, 1);
+    return __shfl_sync(0xffffffffu, v, 0);
+  };
+  for (int kk = (G == 1) ? next_k(0) : gidx; kk < nk; kk = next_k(kk)) {
     const int k = k0 + kk;
     const LamF L = A.lf[k];
     Acc<GRAD, KAHAN> acc;
@@ -652,14 +664,14 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
   extern __shared__ __align__(16) float sm[];
   // persistent: each CTA takes (item, Lambda-slab) units from the counter until none
   // is left; the counter is zeroed by the prologue of the same call
-  __shared__ int s_unit;
+  __shared__ int s_unit, s_next;
   const int n_units = A.n_sched * A.n_slabs;
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(A.counter, 1);
     __syncthreads();
     const int unit = s_unit;
     if (unit >= n_units) break;
-    fused_unit<GRAD, KAHAN, RowT>(A, unit, sm);
+    fused_unit<GRAD, KAHAN, RowT>(A, unit, sm, &s_next);
     __syncthreads();   // the combine has read s_part before the next unit restages
   }
 }
