@@ -778,7 +778,10 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
 
   // ---- pass 1: weights (max, sum, sum of squares), Welford moments of z, valid range
   float m = -INFINITY, s1 = 0.f, s2 = 0.f;
-  float fn = 0.f, fmean = 0.f, fM2 = 0.f;   // Welford per lane in FP32, merged in FP64
+  // Welford per lane and Chan's pairwise merge across lanes, all in FP32: this GPU's
+  // FP64 pipe runs at 1/64 of the FP32 rate, and a few FP64 divisions per warp kept it
+  // half busy for the whole kernel
+  float fn = 0.f, fmean = 0.f, fM2 = 0.f;
   int vmin = INT_MAX, vmax = -1;
   for (int i = lane; i < n; i += 32) {
     float z, lw;
@@ -804,7 +807,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
       }
     }
   }
-  double wn = fn, wmean = fmean, wM2 = fM2;
+  float wn = fn, wmean = fmean, wM2 = fM2;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float om = __shfl_xor_sync(0xffffffffu, m, o);
@@ -817,19 +820,21 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
       s2 = s2 * ra * ra + o2 * rb * rb;
       m = M;
     }
-    const double bn = __shfl_xor_sync(0xffffffffu, wn, o);
-    const double bmean = __shfl_xor_sync(0xffffffffu, wmean, o);
-    const double bM2 = __shfl_xor_sync(0xffffffffu, wM2, o);
-    const double nn = wn + bn;
-    if (nn > 0.0) {   // Chan et al.'s pairwise update of (n, mean, M2)
-      const double d = bmean - wmean;
-      wM2 = wM2 + bM2 + d * d * wn * bn / nn;
-      wmean = wmean + d * bn / nn;
+    const float bn = __shfl_xor_sync(0xffffffffu, wn, o);
+    const float bmean = __shfl_xor_sync(0xffffffffu, wmean, o);
+    const float bM2 = __shfl_xor_sync(0xffffffffu, wM2, o);
+    const float nn = wn + bn;   // exact: counts stay below 2^24
+    if (nn > 0.f) {   // Chan et al.'s pairwise update of (n, mean, M2)
+      const float d = bmean - wmean, r = bn / nn;
+      wM2 = wM2 + bM2 + (d * d) * (wn * r);
+      wmean = fmaf(d, r, wmean);
       wn = nn;
     }
     vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
     vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
   }
+  // the two partners of a butterfly round differently; every lane takes lane 0's M2
+  wM2 = __shfl_sync(0xffffffffu, wM2, 0);
   const int nv = (int)wn;
   bool keep = m > -INFINITY && nv >= 2 && s1 * s1 >= A.neff_min * s2;
 
@@ -837,7 +842,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   float h = 0.f;
   if (keep) {
     const float shrink = exp2f(-0.2f * log2f((float)nv));
-    const float sigma = (float)sqrt(wM2 / (wn - 1.0));
+    const float sigma = sqrtf(wM2 / (wn - 1.f));
     if (A.rule == 0) {
       h = 1.06f * sigma * shrink;
     } else {
@@ -871,14 +876,14 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
         h = 0.f;
         if (mad > 0.f) {
           const float inv9 = 1.f / (9.f * mad);
-          double num = 0.0, den = 0.0;
+          float num = 0.f, den = 0.f;
           for (int i = vmin + lane; i <= vmax; i += 32) {
             const float dz = kde_z(C, smp, i) - Q;
             const float u = dz * inv9;
             if (fabsf(u) < 1.f) {
-              const double a = 1.0 - (double)u * u;
-              num += (double)dz * dz * a * a * a * a;
-              den += a * (1.0 - 5.0 * (double)u * u);
+              const float u2 = u * u, a = 1.f - u2, a2 = a * a;
+              num = fmaf((dz * dz) * a2, a2, num);
+              den = fmaf(a, fmaf(-5.f, u2, 1.f), den);
             }
           }
 #pragma unroll
@@ -886,7 +891,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
             num += __shfl_xor_sync(0xffffffffu, num, o);
             den += __shfl_xor_sync(0xffffffffu, den, o);
           }
-          if (den != 0.0 && num > 0.0) h = 1.06f * (float)sqrt((double)nv * num / (den * den)) * shrink;
+          if (den != 0.f && num > 0.f) h = 1.06f * sqrtf((float)nv * num / (den * den)) * shrink;
         }
       }
     }
