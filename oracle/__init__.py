@@ -19,7 +19,8 @@ import threading
 
 import numpy as np
 
-NP = 13
+NP = 13       # hyperparameters of the power law + peak mass model
+NP_MP = 16    # of the multi-peak model: [..., mu_high, sigma_high, lambda_low]
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gwc_oracle.cpp")
 _LIB = os.path.join(_HERE, "liborc.so")
@@ -60,26 +61,28 @@ def lib():
             d, i32, i64, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
             L = _lib
             L.orc_loglik.restype = ctypes.c_int
-            L.orc_loglik.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, d, d, i32,
+            L.orc_loglik.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, i32, d, d, i32,
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp]
             for name, args in [("orc_E", [d, d]), ("orc_I", [d, d]), ("orc_D", [d, d]),
                                ("orc_Dprime", [d, d]), ("orc_z_of_x", [d, d, d]),
-                               ("orc_S", [d, d, d]), ("orc_ln_p_m1", [d, vp]),
-                               ("orc_ln_p_m2", [d, d, vp]), ("orc_C", [d, vp]),
-                               ("orc_ln_Zm1", [vp]), ("orc_ln_psi", [d, vp]),
-                               ("orc_ln_Nz", [vp, vp, i32, d]), ("orc_rule_poly", [i32, i32])]:
+                               ("orc_S", [d, d, d]), ("orc_ln_p_m1", [d, vp, i32]),
+                               ("orc_ln_p_m2", [d, d, vp, i32]), ("orc_C", [d, vp, i32]),
+                               ("orc_ln_Zm1", [vp, i32]), ("orc_ln_psi", [d, vp, i32]),
+                               ("orc_ln_Nz", [vp, i32, vp, i32, d]), ("orc_rule_poly", [i32, i32])]:
                 fn = getattr(L, name)
                 fn.restype = d
                 fn.argtypes = args
             L.orc_los_cell.restype = i32
             L.orc_los_cell.argtypes = [ctypes.c_float, i32, d]
             L.orc_ln_w_samples.restype = ctypes.c_int
-            L.orc_ln_w_samples.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp]
+            L.orc_ln_w_samples.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp]
             L.orc_ln_w_row.restype = ctypes.c_int
-            L.orc_ln_w_row.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, d, vp, vp]
+            L.orc_ln_w_row.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, i32, d, vp, vp]
             L.orc_loglik_kde.restype = ctypes.c_int
-            L.orc_loglik_kde.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, i32, d, d, i32,
+            L.orc_loglik_kde.argtypes = [ctypes.POINTER(Inputs), i32, vp, i32, i32, i32, d, d, i32,
                                          vp, vp, vp, vp, vp, vp]
+            L.orc_num_params.restype = i32
+            L.orc_num_params.argtypes = [i32]
             L.orc_bandwidth.restype = d
             L.orc_bandwidth.argtypes = [vp, i64, i32]
         return _lib
@@ -90,8 +93,10 @@ def _ptr(a):
 
 
 def _lam(lam):
+    """Lambda as float64; its width selects the mass model (13: power law + peak,
+    16: multi-peak)."""
     a = np.ascontiguousarray(lam, dtype=np.float64)
-    assert a.shape[-1] == NP
+    assert a.shape[-1] in (NP, NP_MP), "Lambda rows have 13 or 16 entries"
     return a
 
 
@@ -101,18 +106,18 @@ def D(z, om): return lib().orc_D(z, om)
 def Dprime(z, om): return lib().orc_Dprime(z, om)
 def z_of_x(x, om, zmax=10.0): return lib().orc_z_of_x(x, om, zmax)
 def S(m, mmin, dm): return lib().orc_S(m, mmin, dm)
-def ln_p_m1(m1, lam): a = _lam(lam); return lib().orc_ln_p_m1(m1, _ptr(a))
-def ln_p_m2(m2, m1, lam): a = _lam(lam); return lib().orc_ln_p_m2(m2, m1, _ptr(a))
-def C(m1, lam): a = _lam(lam); return lib().orc_C(m1, _ptr(a))
-def ln_Zm1(lam): a = _lam(lam); return lib().orc_ln_Zm1(_ptr(a))
-def ln_psi(z, lam): a = _lam(lam); return lib().orc_ln_psi(z, _ptr(a))
+def ln_p_m1(m1, lam): a = _lam(lam); return lib().orc_ln_p_m1(m1, _ptr(a), a.shape[-1])
+def ln_p_m2(m2, m1, lam): a = _lam(lam); return lib().orc_ln_p_m2(m2, m1, _ptr(a), a.shape[-1])
+def C(m1, lam): a = _lam(lam); return lib().orc_C(m1, _ptr(a), a.shape[-1])
+def ln_Zm1(lam): a = _lam(lam); return lib().orc_ln_Zm1(_ptr(a), a.shape[-1])
+def ln_psi(z, lam): a = _lam(lam); return lib().orc_ln_psi(z, _ptr(a), a.shape[-1])
 def rule_poly(k, which): return lib().orc_rule_poly(k, which)
 
 
 def ln_Nz(lam, pbar, zmax):
     a = _lam(lam)
     p = np.ascontiguousarray(pbar, dtype=np.float64)
-    return lib().orc_ln_Nz(_ptr(a), _ptr(p), len(p), zmax)
+    return lib().orc_ln_Nz(_ptr(a), a.shape[-1], _ptr(p), len(p), zmax)
 
 
 def los_cell(z, nz, zmax):
@@ -127,8 +132,8 @@ def ln_w_row(lam, m1, m2, dl, lnpi, row, zmax, grad=False):
     m1, m2, dl, lnpi, row = f32(m1), f32(m2), f32(dl), f32(lnpi), f32(row)
     n = len(m1)
     out = np.empty(n, np.float64)
-    g = np.empty((n, NP), np.float64) if grad else None
-    rc = lib().orc_ln_w_row(_ptr(a), n, _ptr(m1), _ptr(m2), _ptr(dl), _ptr(lnpi), _ptr(row),
+    g = np.empty((n, a.shape[-1]), np.float64) if grad else None
+    rc = lib().orc_ln_w_row(_ptr(a), a.shape[-1], n, _ptr(m1), _ptr(m2), _ptr(dl), _ptr(lnpi), _ptr(row),
                             len(row), zmax, _ptr(out), _ptr(g))
     if rc != 0:
         raise ValueError("Lambda outside its domain")
@@ -147,9 +152,9 @@ def ln_w_samples(lam, cat, which="events", idx=None, grad=False):
     los = f32(cat["los"])
     n = len(m1)
     out = np.empty(n, np.float64)
-    g = np.empty((n, NP), np.float64) if grad else None
-    kink = np.empty((n, NP), np.float64) if grad else None
-    rc = lib().orc_ln_w_samples(_ptr(a), n, _ptr(m1), _ptr(m2), _ptr(dl), _ptr(lp),
+    g = np.empty((n, a.shape[-1]), np.float64) if grad else None
+    kink = np.empty((n, a.shape[-1]), np.float64) if grad else None
+    rc = lib().orc_ln_w_samples(_ptr(a), a.shape[-1], n, _ptr(m1), _ptr(m2), _ptr(dl), _ptr(lp),
                                 _ptr(pix) if pix is not None else None, _ptr(los), los.shape[0],
                                 los.shape[1], float(cat["z_max"]), _ptr(out), _ptr(g),
                                 _ptr(kink) if grad else None)
@@ -197,7 +202,7 @@ def loglik_kde(cat, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, neff_min_se
     out = dict(lnL_event=np.empty((K, n_ev)), neff_event=np.empty((K, n_ev)),
                ln_xi=np.empty(K), neff_sel=np.empty(K), lnL_total=np.empty(K),
                flags=np.empty(K, np.int32))
-    rc = lib().orc_loglik_kde(ctypes.byref(inp), K, _ptr(lam), BW_RULES[bw], n_grid, neff_min_pixel,
+    rc = lib().orc_loglik_kde(ctypes.byref(inp), K, _ptr(lam), lam.shape[1], BW_RULES[bw], n_grid, neff_min_pixel,
                               neff_min_sel, n_threads, _ptr(out["lnL_event"]), _ptr(out["neff_event"]),
                               _ptr(out["ln_xi"]), _ptr(out["neff_sel"]), _ptr(out["lnL_total"]),
                               _ptr(out["flags"]))
@@ -207,7 +212,8 @@ def loglik_kde(cat, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, neff_min_se
 
 
 def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads=0):
-    """Evaluate the whole likelihood for a Lambda batch ``lam`` [K, 13].
+    """Evaluate the whole likelihood for a Lambda batch ``lam`` [K, 13] (power law +
+    peak) or [K, 16] (multi-peak); gradients have the same width.
 
     ``cat`` is a dict of numpy arrays with the keys produced by
     ``paper_2605_23538_gb300.synth`` (offsets, m1, m2, dl, lnpe, pix, los, z_max,
@@ -232,12 +238,13 @@ def loglik(cat, lam, grad=False, neff_min_event=2.0, neff_min_sel=0.0, n_threads
                  los=_ptr(los), n_inj=len(cat["inj_m1"]), n_draw=float(cat["n_draw"]),
                  im1=arr("inj_m1", np.float32), im2=arr("inj_m2", np.float32),
                  idl=arr("inj_dl", np.float32), ilnpd=arr("inj_lnpd", np.float32))
+    P = lam.shape[1]
     out = dict(lnL_event=np.empty((K, n_ev)), neff_event=np.empty((K, n_ev)),
                ln_xi=np.empty(K), neff_sel=np.empty(K), lnL_total=np.empty(K),
-               flags=np.empty(K, np.int32), grad_total=np.zeros((K, NP)) if grad else None,
-               grad_scale=np.zeros((K, NP)) if grad else None,
-               grad_kink=np.zeros((K, NP)) if grad else None)
-    rc = lib().orc_loglik(ctypes.byref(inp), K, _ptr(lam), int(bool(grad)), neff_min_event,
+               flags=np.empty(K, np.int32), grad_total=np.zeros((K, P)) if grad else None,
+               grad_scale=np.zeros((K, P)) if grad else None,
+               grad_kink=np.zeros((K, P)) if grad else None)
+    rc = lib().orc_loglik(ctypes.byref(inp), K, _ptr(lam), P, int(bool(grad)), neff_min_event,
                           neff_min_sel, n_threads, _ptr(out["lnL_event"]), _ptr(out["neff_event"]),
                           _ptr(out["ln_xi"]), _ptr(out["neff_sel"]), _ptr(out["lnL_total"]),
                           _ptr(out["flags"]), _ptr(out["grad_total"]), _ptr(out["grad_scale"]),

@@ -21,9 +21,11 @@
 //   * Eq. 7: effective sample size (sum w)^2 / sum w^2, applied per event.
 //   * The KDE form of Eqs. 5-7 (per-pixel Gaussian KDE on a redshift grid, per-pixel
 //     N_eff cut, bandwidth rules of the appendix) is evaluated by orc_loglik_kde.
-// The mass model (power law + Gaussian peak, low-mass smoothing) and the
+// The mass models (power law + Gaussian peak, and the multi-peak model of the paper's
+// simulated catalogue, App. A, Table 2, both with low-mass smoothing) and the
 // Madau-Dickinson rate are named but not written out in the paper; the standard
-// population-literature definitions are used (see the functions below).
+// population-literature definitions are used (see the functions below).  A Lambda row of
+// 13 entries selects the first mass model, one of 16 the second.
 //
 // Numerics are deliberately direct: every integral is an adaptive Gauss-Kronrod
 // quadrature of its own definition, z(d_L) is a safeguarded Newton root of
@@ -48,68 +50,81 @@
 
 namespace {
 
-constexpr int NP = 13;                       // hyperparameters per Lambda point
+constexpr int NP = 13;                       // hyperparameters, power law + peak
+constexpr int NP_MP = 16;                    // hyperparameters, multi-peak
+constexpr int NP_MAX = 16;
 constexpr double C_KMS = 299792.458;         // speed of light [km/s]
 constexpr double NEG_INF = -std::numeric_limits<double>::infinity();
 constexpr double LN_SQRT_2PI = 0.91893853320467274178032973640562;
 
 // Lambda layout: [H0, Om, alpha, beta, m_min, m_max, delta_m, mu_g, sigma_g,
 //                 lambda_peak, gamma, kappa, z_p]
-enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
+// and for the multi-peak mass model three more, the second (higher-mass) Gaussian and
+// the share of the Gaussian fraction in the first (lower-mass) one:
+//                 [..., mu_high, sigma_high, lambda_low]
+// (mu_g, sigma_g, lambda_peak are then mu_low, sigma_low and lambda_g of Table 2).
+enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP,
+       P_MU2, P_SIG2, P_LAM1 };
+enum { MODEL_PLP = 0, MODEL_MP = 1 };
+inline int n_params(int model) { return model == MODEL_MP ? NP_MP : NP; }
+inline int model_of(int n_par) { return n_par == NP ? MODEL_PLP : n_par == NP_MP ? MODEL_MP : -1; }
 
 // ---------------------------------------------------------------- dual numbers
-struct Dual {
+// value and N first derivatives (N = 13 or 16: one per hyperparameter of the model)
+template <int N> struct DualT {
   double v;
-  double d[NP];
-  Dual() : v(0.0) { for (int i = 0; i < NP; ++i) d[i] = 0.0; }
-  Dual(double c) : v(c) { for (int i = 0; i < NP; ++i) d[i] = 0.0; }  // NOLINT: implicit on purpose
+  double d[N];
+  DualT() : v(0.0) { for (int i = 0; i < N; ++i) d[i] = 0.0; }
+  DualT(double c) : v(c) { for (int i = 0; i < N; ++i) d[i] = 0.0; }  // NOLINT: implicit on purpose
 };
+using Dual = DualT<NP>;
+using DualM = DualT<NP_MP>;
 
 inline double val(double x) { return x; }
-inline double val(const Dual& x) { return x.v; }
+template <int N> double val(const DualT<N>& x) { return x.v; }
 
-inline Dual operator+(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v + b.v;
-  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] + b.d[i];
+template <int N> DualT<N> operator+(const DualT<N>& a, const DualT<N>& b) {
+  DualT<N> r; r.v = a.v + b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
 }
-inline Dual operator-(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v - b.v;
-  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] - b.d[i];
+template <int N> DualT<N> operator-(const DualT<N>& a, const DualT<N>& b) {
+  DualT<N> r; r.v = a.v - b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
 }
-inline Dual operator-(const Dual& a) {
-  Dual r; r.v = -a.v;
-  for (int i = 0; i < NP; ++i) r.d[i] = -a.d[i];
+template <int N> DualT<N> operator-(const DualT<N>& a) {
+  DualT<N> r; r.v = -a.v;
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
   return r;
 }
-inline Dual operator*(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v * b.v;
-  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+template <int N> DualT<N> operator*(const DualT<N>& a, const DualT<N>& b) {
+  DualT<N> r; r.v = a.v * b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
   return r;
 }
-inline Dual operator/(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v / b.v;
-  for (int i = 0; i < NP; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+template <int N> DualT<N> operator/(const DualT<N>& a, const DualT<N>& b) {
+  DualT<N> r; r.v = a.v / b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
   return r;
 }
-inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
-inline Dual operator+(double a, const Dual& b) { Dual r = b; r.v += a; return r; }
-inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
-inline Dual operator-(double a, const Dual& b) { Dual r = -b; r.v += a; return r; }
-inline Dual operator*(const Dual& a, double b) {
-  Dual r; r.v = a.v * b;
-  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] * b;
+template <int N> DualT<N> operator+(const DualT<N>& a, double b) { DualT<N> r = a; r.v += b; return r; }
+template <int N> DualT<N> operator+(double a, const DualT<N>& b) { DualT<N> r = b; r.v += a; return r; }
+template <int N> DualT<N> operator-(const DualT<N>& a, double b) { DualT<N> r = a; r.v -= b; return r; }
+template <int N> DualT<N> operator-(double a, const DualT<N>& b) { DualT<N> r = -b; r.v += a; return r; }
+template <int N> DualT<N> operator*(const DualT<N>& a, double b) {
+  DualT<N> r; r.v = a.v * b;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
   return r;
 }
-inline Dual operator*(double a, const Dual& b) { return b * a; }
-inline Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
-inline Dual operator/(double a, const Dual& b) { return Dual(a) / b; }
+template <int N> DualT<N> operator*(double a, const DualT<N>& b) { return b * a; }
+template <int N> DualT<N> operator/(const DualT<N>& a, double b) { return a * (1.0 / b); }
+template <int N> DualT<N> operator/(double a, const DualT<N>& b) { return DualT<N>(a) / b; }
 
 // f(a) with f(a.v) = fv and f'(a.v) = dfv
-inline Dual chain(const Dual& a, double fv, double dfv) {
-  Dual r; r.v = fv;
-  for (int i = 0; i < NP; ++i) r.d[i] = dfv * a.d[i];
+template <int N> DualT<N> chain(const DualT<N>& a, double fv, double dfv) {
+  DualT<N> r; r.v = fv;
+  for (int i = 0; i < N; ++i) r.d[i] = dfv * a.d[i];
   return r;
 }
 
@@ -118,11 +133,14 @@ inline double flog(double x) { return std::log(x); }
 inline double flog1p(double x) { return std::log1p(x); }
 inline double fsqrt(double x) { return std::sqrt(x); }
 inline double ferf(double x) { return std::erf(x); }
-inline Dual fexp(const Dual& a) { const double e = std::exp(a.v); return chain(a, e, e); }
-inline Dual flog(const Dual& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
-inline Dual flog1p(const Dual& a) { return chain(a, std::log1p(a.v), 1.0 / (1.0 + a.v)); }
-inline Dual fsqrt(const Dual& a) { const double s = std::sqrt(a.v); return chain(a, s, 0.5 / s); }
-inline Dual ferf(const Dual& a) {
+template <int N> DualT<N> fexp(const DualT<N>& a) { const double e = std::exp(a.v); return chain(a, e, e); }
+template <int N> DualT<N> flog(const DualT<N>& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
+template <int N> DualT<N> flog1p(const DualT<N>& a) { return chain(a, std::log1p(a.v), 1.0 / (1.0 + a.v)); }
+template <int N> DualT<N> fsqrt(const DualT<N>& a) {
+  const double s = std::sqrt(a.v);
+  return chain(a, s, 0.5 / s);
+}
+template <int N> DualT<N> ferf(const DualT<N>& a) {
   return chain(a, std::erf(a.v), 1.12837916709551257389615890312154 * std::exp(-a.v * a.v));
 }
 // ln(1 + e^a), stable for either sign of a
@@ -133,11 +151,18 @@ template <class T> T softplus(const T& a) {
 
 // component access used by the quadrature's convergence test
 inline int ncomp(double) { return 1; }
-inline int ncomp(const Dual&) { return NP + 1; }
+template <int N> int ncomp(const DualT<N>&) { return N + 1; }
 inline double comp(double x, int) { return x; }
-inline double comp(const Dual& x, int i) { return i == 0 ? x.v : x.d[i - 1]; }
+template <int N> double comp(const DualT<N>& x, int i) { return i == 0 ? x.v : x.d[i - 1]; }
 inline double cabs_comp(double x, int) { return std::fabs(x); }
-inline double cabs_comp(const Dual& x, int i) { return std::fabs(comp(x, i)); }
+template <int N> double cabs_comp(const DualT<N>& x, int i) { return std::fabs(comp(x, i)); }
+
+// the variable for hyperparameter i: its value, with unit derivative in slot i
+inline void seed(double& v, double x, int) { v = x; }
+template <int N> void seed(DualT<N>& v, double x, int i) {
+  v = DualT<N>(x);
+  if (i < N) v.d[i] = 1.0;
+}
 
 // ------------------------------------------------------ adaptive Gauss-Kronrod
 // Kronrod's 15-point extension of the 7-point Gauss-Legendre rule on [-1, 1]
@@ -156,7 +181,7 @@ const double WG[4] = {
     0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
     0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
 
-constexpr int NC_MAX = NP + 1;
+constexpr int NC_MAX = NP_MAX + 1;
 
 template <class T, class F>
 void gk15(const F& f, const T& a, const T& b, T& K, T& G, double* kabs) {
@@ -270,9 +295,12 @@ template <class T> T z_of_x(const T& x, const T& om, double z0) {
 
 // ----------------------------------------------------------------- population
 template <class T> struct Pop {
+  int model = MODEL_PLP;
   T H0, om, alpha, beta, mmin, mmax, dm, mu, sig, lam, gam, kap, zp;
+  T mu2, sig2, lam1;   // multi-peak only: the second Gaussian, the first one's share
   T lnZP;    // ln int_{mmin}^{mmax} m^-alpha dm
   T lnZG;    // ln of the Gaussian's mass inside [mmin, mmax]
+  T lnZG2;   // the same for the second Gaussian (multi-peak)
   T lnZm1;   // ln int p_unnormalised(m1) dm1
   T lnNz;    // ln of the redshift-prior normalisation over the pixel-averaged LOS prior
   double xmax;  // D(z_max; Om)
@@ -291,12 +319,24 @@ template <class T> bool ln_S(const T& m, const T& mmin, const T& dm, T& out) {
   return true;
 }
 
-// unnormalised primary-mass density: (1-lam) m^-alpha/Z_P + lam N(m; mu, sig)/Z_G
+// N(m; mu, sig) / Z, Z its mass inside [mmin, mmax] (a Gaussian truncated to the range)
+template <class T> T gauss_trunc(const T& m, const T& mu, const T& sig, const T& lnZ) {
+  const T zg = (m - mu) / sig;
+  return fexp(-0.5 * zg * zg - flog(sig) - LN_SQRT_2PI - lnZ);
+}
+
+// unnormalised primary-mass density before smoothing:
+//   power law + peak:  (1-lam) m^-alpha/Z_P + lam G(m; mu, sig)
+//   multi-peak:        (1-lam) m^-alpha/Z_P + lam [lam1 G(m; mu, sig) + (1-lam1) G(m; mu2, sig2)]
+// with G truncated Gaussians; the multi-peak model is the power law with two peaks of the
+// population literature (Abbott et al. 2021, ApJL 913 L7), mixed and smoothed like the
+// single peak.  At lam1 = 1 it is the power law + peak model with the first Gaussian.
 template <class T> T m1_mixture(const T& m, const Pop<T>& P) {
   const T pl = fexp(-P.alpha * flog(m) - P.lnZP);
-  const T zg = (m - P.mu) / P.sig;
-  const T ga = fexp(-0.5 * zg * zg - flog(P.sig) - LN_SQRT_2PI - P.lnZG);
-  return (1.0 - P.lam) * pl + P.lam * ga;
+  const T ga = gauss_trunc(m, P.mu, P.sig, P.lnZG);
+  if (P.model != MODEL_MP) return (1.0 - P.lam) * pl + P.lam * ga;
+  const T ga2 = gauss_trunc(m, P.mu2, P.sig2, P.lnZG2);
+  return (1.0 - P.lam) * pl + P.lam * (P.lam1 * ga + (1.0 - P.lam1) * ga2);
 }
 
 template <class T> T m1_unnormalised(const T& m, const Pop<T>& P) {
@@ -365,6 +405,8 @@ template <class T> void set_norms(Pop<T>& P, const std::vector<double>& pbar, do
   P.lnZP = flog(integrate(fpl, P.mmin, P.mmax, 1e-14));
   const double r2 = 0.70710678118654752440084436210485;
   P.lnZG = flog(0.5 * (ferf((P.mmax - P.mu) / P.sig * r2) - ferf((P.mmin - P.mu) / P.sig * r2)));
+  if (P.model == MODEL_MP)
+    P.lnZG2 = flog(0.5 * (ferf((P.mmax - P.mu2) / P.sig2 * r2) - ferf((P.mmin - P.mu2) / P.sig2 * r2)));
   // Z_m1 over [mmin, mmin+dm] and [mmin+dm, mmax]; the upper piece is split around the
   // peak (fixed split points do not change the integral, only help the adaptivity)
   auto fm = [&P](const T& m) { return m1_unnormalised(m, P); };
@@ -374,7 +416,12 @@ template <class T> void set_norms(Pop<T>& P, const std::vector<double>& pbar, do
   for (double k : {-5.0, 0.0, 5.0}) {
     const double c = val(P.mu) + k * val(P.sig);
     if (c > val(mw) && c < val(P.mmax)) cuts.push_back(c);
+    if (P.model == MODEL_MP) {
+      const double c2 = val(P.mu2) + k * val(P.sig2);
+      if (c2 > val(mw) && c2 < val(P.mmax)) cuts.push_back(c2);
+    }
   }
+  std::sort(cuts.begin(), cuts.end());
   T lo = mw;
   for (double c : cuts) { Z = Z + integrate(fm, lo, T(c), 1e-14); lo = T(c); }
   Z = Z + integrate(fm, lo, P.mmax, 1e-14);
@@ -383,29 +430,26 @@ template <class T> void set_norms(Pop<T>& P, const std::vector<double>& pbar, do
   P.xmax = D_of(zmax, val(P.om));
 }
 
-bool lambda_in_domain(const double* L) {
-  for (int i = 0; i < NP; ++i) if (!std::isfinite(L[i])) return false;
-  return L[P_H0] > 0.0 && L[P_OM] >= 0.0 && L[P_OM] <= 1.0 && L[P_MMIN] > 0.0 &&
-         L[P_MMAX] > L[P_MMIN] && L[P_DM] >= 0.0 && L[P_MMIN] + L[P_DM] < L[P_MMAX] &&
-         L[P_SIG] > 0.0 && L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0 && L[P_ZP] > -1.0;
+bool lambda_in_domain(const double* L, int model = MODEL_PLP) {
+  for (int i = 0; i < n_params(model); ++i) if (!std::isfinite(L[i])) return false;
+  const bool base = L[P_H0] > 0.0 && L[P_OM] >= 0.0 && L[P_OM] <= 1.0 && L[P_MMIN] > 0.0 &&
+                    L[P_MMAX] > L[P_MMIN] && L[P_DM] >= 0.0 && L[P_MMIN] + L[P_DM] < L[P_MMAX] &&
+                    L[P_SIG] > 0.0 && L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0 && L[P_ZP] > -1.0;
+  if (model != MODEL_MP) return base;
+  return base && L[P_SIG2] > 0.0 && L[P_LAM1] >= 0.0 && L[P_LAM1] <= 1.0;
 }
 
-template <class T> Pop<T> make_pop(const double* L, const std::vector<double>& pbar, double zmax);
-
-template <> Pop<double> make_pop<double>(const double* L, const std::vector<double>& pbar, double zmax) {
-  Pop<double> P;
-  P.H0 = L[0]; P.om = L[1]; P.alpha = L[2]; P.beta = L[3]; P.mmin = L[4]; P.mmax = L[5];
-  P.dm = L[6]; P.mu = L[7]; P.sig = L[8]; P.lam = L[9]; P.gam = L[10]; P.kap = L[11]; P.zp = L[12];
-  set_norms(P, pbar, zmax);
-  return P;
-}
-
-template <> Pop<Dual> make_pop<Dual>(const double* L, const std::vector<double>& pbar, double zmax) {
-  Dual v[NP];
-  for (int i = 0; i < NP; ++i) { v[i] = Dual(L[i]); v[i].d[i] = 1.0; }
-  Pop<Dual> P;
+// The population at Lambda; with T a dual number, hyperparameter i carries the unit
+// derivative in slot i (all n_params(model) of them, so T must be wide enough)
+template <class T>
+Pop<T> make_pop(const double* L, int model, const std::vector<double>& pbar, double zmax) {
+  T v[NP_MAX];
+  for (int i = 0; i < n_params(model); ++i) seed(v[i], L[i], i);
+  Pop<T> P;
+  P.model = model;
   P.H0 = v[0]; P.om = v[1]; P.alpha = v[2]; P.beta = v[3]; P.mmin = v[4]; P.mmax = v[5];
   P.dm = v[6]; P.mu = v[7]; P.sig = v[8]; P.lam = v[9]; P.gam = v[10]; P.kap = v[11]; P.zp = v[12];
+  if (model == MODEL_MP) { P.mu2 = v[P_MU2]; P.sig2 = v[P_SIG2]; P.lam1 = v[P_LAM1]; }
   set_norms(P, pbar, zmax);
   return P;
 }
@@ -445,8 +489,8 @@ double los_kink(const double* row, int nz, double zmax, double zv, double p, dou
 //        - ln pi_PE                                              (Eq. 6)
 // with z solving D(z) = d_L H0 / c and m_s = m_d / (1+z).  Returns false where w = 0.
 inline void kink_parts(const double&, double, double*) {}
-inline void kink_parts(const Dual& z, double jump, double* kink) {
-  for (int i = 0; i < NP; ++i) kink[i] = jump * std::fabs(z.d[i]);
+template <int N> void kink_parts(const DualT<N>& z, double jump, double* kink) {
+  for (int i = 0; i < N; ++i) kink[i] = jump * std::fabs(z.d[i]);
 }
 
 // row == NULL leaves out the LOS factor (the weight w' of the KDE form, Eq. 6); *z_out
@@ -481,21 +525,22 @@ bool ln_w(const Pop<T>& P, const double* row, int nz, double zmax, double m1d, d
 // (max, sum e^(l - max), sum e^(2(l - max)), sum e^(l - max) dl/dLambda) over a set
 template <class T> struct Sums {
   double m = NEG_INF, s1 = 0.0, s2 = 0.0;
-  double g[NP] = {0};      // sum e^(l - m) dl/dLambda
-  double gabs[NP] = {0};   // sum e^(l - m) |dl/dLambda| (a magnitude scale for tests)
-  double gkink[NP] = {0};  // sum e^(l - m) (one-sided derivative ambiguity at LOS nodes)
+  double g[NP_MAX] = {0};      // sum e^(l - m) dl/dLambda
+  double gabs[NP_MAX] = {0};   // sum e^(l - m) |dl/dLambda| (a magnitude scale for tests)
+  double gkink[NP_MAX] = {0};  // sum e^(l - m) (one-sided derivative ambiguity at LOS nodes)
   long n_pos = 0;
 };
 
 inline void grad_parts(const double&, double*, double*, double) {}
-inline void grad_parts(const Dual& l, double* g, double* gabs, double t) {
-  for (int i = 0; i < NP; ++i) {
+template <int N> void grad_parts(const DualT<N>& l, double* g, double* gabs, double t) {
+  for (int i = 0; i < N; ++i) {
     g[i] += t * l.d[i];
     gabs[i] += t * std::fabs(l.d[i]);
   }
 }
 
-template <class T> Sums<T> sums_of(const std::vector<T>& ls, const std::vector<double>& kinks) {
+// kinks: np values per entry of ls (or none)
+template <class T> Sums<T> sums_of(const std::vector<T>& ls, const std::vector<double>& kinks, int np) {
   Sums<T> S;
   for (const T& l : ls) S.m = std::max(S.m, val(l));
   for (size_t q = 0; q < ls.size(); ++q) {
@@ -505,7 +550,7 @@ template <class T> Sums<T> sums_of(const std::vector<T>& ls, const std::vector<d
     S.s2 += t * t;
     grad_parts(l, S.g, S.gabs, t);
     if (!kinks.empty())
-      for (int i = 0; i < NP; ++i) S.gkink[i] += t * kinks[q * NP + i];
+      for (int i = 0; i < np; ++i) S.gkink[i] += t * kinks[q * np + i];
     ++S.n_pos;
   }
   return S;
@@ -520,7 +565,7 @@ template <class T> Sums<T> merge(const std::vector<Sums<T>>& parts) {
     const double r = std::exp(p.m - S.m);
     S.s1 += p.s1 * r;
     S.s2 += p.s2 * r * r;
-    for (int i = 0; i < NP; ++i) {
+    for (int i = 0; i < NP_MAX; ++i) {
       S.g[i] += p.g[i] * r;
       S.gabs[i] += p.gabs[i] * r;
       S.gkink[i] += p.gkink[i] * r;
@@ -572,28 +617,29 @@ bool inputs_valid(const Inputs& in) {
 }
 
 template <class T>
-void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double* L,
+void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double* L, int model,
                  double neff_min_event, double neff_min_sel, double* lnL_event, double* neff_event,
                  double* ln_xi, double* neff_sel, double* lnL_total, int32_t* flag, double* grad,
                  double* gscale, double* gkink) {
   const int ne = in.n_events;
   const double zmax = in.z_max;
   const int nz = in.n_z;
+  const int np = n_params(model);
   *flag = 0;
-  if (grad) for (int i = 0; i < NP; ++i) grad[i] = 0.0;
-  if (gscale) for (int i = 0; i < NP; ++i) gscale[i] = 0.0;
-  if (gkink) for (int i = 0; i < NP; ++i) gkink[i] = 0.0;
-  if (!lambda_in_domain(L)) {
+  if (grad) for (int i = 0; i < np; ++i) grad[i] = 0.0;
+  if (gscale) for (int i = 0; i < np; ++i) gscale[i] = 0.0;
+  if (gkink) for (int i = 0; i < np; ++i) gkink[i] = 0.0;
+  if (!lambda_in_domain(L, model)) {
     *flag = 1;
     for (int e = 0; e < ne; ++e) { lnL_event[e] = NEG_INF; neff_event[e] = 0.0; }
     *ln_xi = NEG_INF; *neff_sel = 0.0; *lnL_total = NEG_INF;
     return;
   }
-  const Pop<T> P = make_pop<T>(L, pbar, zmax);
+  const Pop<T> P = make_pop<T>(L, model, pbar, zmax);
 
   // ---- numerator: one event at a time
-  std::vector<double> ev_grad((size_t)ne * NP, 0.0), ev_gabs((size_t)ne * NP, 0.0),
-      ev_gkink((size_t)ne * NP, 0.0);
+  std::vector<double> ev_grad((size_t)ne * np, 0.0), ev_gabs((size_t)ne * np, 0.0),
+      ev_gkink((size_t)ne * np, 0.0);
   const bool want_kink = gkink != nullptr;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int e = 0; e < ne; ++e) {
@@ -601,7 +647,7 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
     std::vector<double> kinks;
     std::vector<double> row((size_t)nz);
     int cur_pix = -1;
-    double kk[NP];
+    double kk[NP_MAX];
     for (int64_t k = in.offsets[e]; k < in.offsets[e + 1]; ++k) {
       if (in.pix[k] != cur_pix) {
         cur_pix = in.pix[k];
@@ -611,10 +657,10 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
       if (ln_w(P, row.data(), nz, zmax, in.m1[k], in.m2[k], in.dl[k], in.lnpe[k], l,
                want_kink ? kk : nullptr)) {
         ls.push_back(l);
-        if (want_kink) kinks.insert(kinks.end(), kk, kk + NP);
+        if (want_kink) kinks.insert(kinks.end(), kk, kk + np);
       }
     }
-    const Sums<T> S = sums_of(ls, kinks);
+    const Sums<T> S = sums_of(ls, kinks, np);
     const double n_i = (double)(in.offsets[e + 1] - in.offsets[e]);
     if (S.n_pos == 0) {
       lnL_event[e] = NEG_INF;
@@ -622,10 +668,10 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
     } else {
       lnL_event[e] = S.m + std::log(S.s1) - std::log(n_i);
       neff_event[e] = S.s1 * S.s1 / S.s2;
-      for (int i = 0; i < NP; ++i) {
-        ev_grad[(size_t)e * NP + i] = S.g[i] / S.s1;
-        ev_gabs[(size_t)e * NP + i] = S.gabs[i] / S.s1;
-        ev_gkink[(size_t)e * NP + i] = S.gkink[i] / S.s1;
+      for (int i = 0; i < np; ++i) {
+        ev_grad[(size_t)e * np + i] = S.g[i] / S.s1;
+        ev_gabs[(size_t)e * np + i] = S.gabs[i] / S.s1;
+        ev_gkink[(size_t)e * np + i] = S.gkink[i] / S.s1;
       }
     }
   }
@@ -638,27 +684,27 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
   for (int64_t c = 0; c < nchunk; ++c) {
     std::vector<T> ls;
     std::vector<double> kinks;
-    double kk[NP];
+    double kk[NP_MAX];
     const int64_t a = c * chunk, b = std::min(in.n_inj, a + chunk);
     for (int64_t k = a; k < b; ++k) {
       T l;
       if (ln_w(P, pbar.data(), nz, zmax, in.im1[k], in.im2[k], in.idl[k], in.ilnpd[k], l,
                want_kink ? kk : nullptr)) {
         ls.push_back(l);
-        if (want_kink) kinks.insert(kinks.end(), kk, kk + NP);
+        if (want_kink) kinks.insert(kinks.end(), kk, kk + np);
       }
     }
-    parts[(size_t)c] = sums_of(ls, kinks);
+    parts[(size_t)c] = sums_of(ls, kinks, np);
   }
   const Sums<T> Ssel = merge(parts);
-  double sel_grad[NP] = {0}, sel_gabs[NP] = {0}, sel_gkink[NP] = {0};
+  double sel_grad[NP_MAX] = {0}, sel_gabs[NP_MAX] = {0}, sel_gkink[NP_MAX] = {0};
   if (Ssel.n_pos == 0) {
     *ln_xi = NEG_INF;
     *neff_sel = 0.0;
   } else {
     *ln_xi = Ssel.m + std::log(Ssel.s1) - std::log(in.n_draw);
     *neff_sel = Ssel.s1 * Ssel.s1 / Ssel.s2;
-    for (int i = 0; i < NP; ++i) {
+    for (int i = 0; i < np; ++i) {
       sel_grad[i] = Ssel.g[i] / Ssel.s1;
       sel_gabs[i] = Ssel.gabs[i] / Ssel.s1;
       sel_gkink[i] = Ssel.gkink[i] / Ssel.s1;
@@ -688,23 +734,23 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
   }
   *lnL_total = (sum + comp_) - (double)ne * (*ln_xi);
   if (grad) {
-    for (int i = 0; i < NP; ++i) {
+    for (int i = 0; i < np; ++i) {
       double g = 0.0;
-      for (int e = 0; e < ne; ++e) g += ev_grad[(size_t)e * NP + i];
+      for (int e = 0; e < ne; ++e) g += ev_grad[(size_t)e * np + i];
       grad[i] = g - (double)ne * sel_grad[i];
     }
   }
   if (gscale) {
-    for (int i = 0; i < NP; ++i) {
+    for (int i = 0; i < np; ++i) {
       double a = 0.0;
-      for (int e = 0; e < ne; ++e) a += ev_gabs[(size_t)e * NP + i];
+      for (int e = 0; e < ne; ++e) a += ev_gabs[(size_t)e * np + i];
       gscale[i] = a + (double)ne * sel_gabs[i];
     }
   }
   if (gkink) {
-    for (int i = 0; i < NP; ++i) {
+    for (int i = 0; i < np; ++i) {
       double a = 0.0;
-      for (int e = 0; e < ne; ++e) a += ev_gkink[(size_t)e * NP + i];
+      for (int e = 0; e < ne; ++e) a += ev_gkink[(size_t)e * np + i];
       gkink[i] = a + (double)ne * sel_gkink[i];
     }
   }
@@ -831,16 +877,16 @@ void kde_event(const Inputs& in, const Pop<double>& P, int e, int rule, int n_gr
   *neff = a * a / b;
 }
 
-void eval_lambda_kde(const Inputs& in, const std::vector<double>& pbar, const double* L,
+void eval_lambda_kde(const Inputs& in, const std::vector<double>& pbar, const double* L, int model,
                      int rule, int n_grid, double neff_min_pixel, double neff_min_sel,
                      double* lnL_event, double* neff_event, double* ln_xi, double* neff_sel,
                      double* lnL_total, int32_t* flag) {
   const int ne = in.n_events;
   // the selection term is the Monte-Carlo one; the event terms are replaced below
-  eval_lambda<double>(in, pbar, L, 0.0, neff_min_sel, lnL_event, neff_event, ln_xi, neff_sel,
+  eval_lambda<double>(in, pbar, L, model, 0.0, neff_min_sel, lnL_event, neff_event, ln_xi, neff_sel,
                       lnL_total, flag, nullptr, nullptr, nullptr);
   if (*flag & 1) return;
-  const Pop<double> P = make_pop<double>(L, pbar, in.z_max);
+  const Pop<double> P = make_pop<double>(L, model, pbar, in.z_max);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int e = 0; e < ne; ++e)
     kde_event(in, P, e, rule, n_grid, neff_min_pixel, lnL_event + e, neff_event + e);
@@ -863,25 +909,73 @@ std::vector<double> row_to_double(const float* row, int nz) {
   return r;
 }
 
+// ln w of n samples with gradient slots of type D (Dual or DualM): out_grad[n][np] and,
+// when non-NULL, out_kink[n][np]; row_of(k, row) fills sample k's LOS row
+template <class D, class RowOf>
+void ln_w_grad(const double* L, int model, const std::vector<double>& norm_row, double zmax,
+               int64_t n, const float* m1, const float* m2, const float* dl, const float* lnpi,
+               int nz, const RowOf& row_of, double* out, double* out_grad, double* out_kink) {
+  const int np = n_params(model);
+  const Pop<D> P = make_pop<D>(L, model, norm_row, zmax);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < n; ++k) {
+    std::vector<double> row((size_t)nz);
+    row_of(k, row);
+    D l;
+    double kk[NP_MAX] = {0};
+    const bool ok = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l, kk);
+    out[k] = ok ? l.v : NEG_INF;
+    for (int i = 0; i < np; ++i) {
+      out_grad[(size_t)k * np + i] = ok ? l.d[i] : 0.0;
+      if (out_kink) out_kink[(size_t)k * np + i] = ok ? kk[i] : 0.0;
+    }
+  }
+}
+
+template <class RowOf>
+int ln_w_any(const double* L, int32_t n_par, const std::vector<double>& norm_row, double zmax,
+             int64_t n, const float* m1, const float* m2, const float* dl, const float* lnpi, int nz,
+             const RowOf& row_of, double* out, double* out_grad, double* out_kink) {
+  const int model = model_of(n_par);
+  if (model < 0 || !lambda_in_domain(L, model)) return -1;
+  if (!out_grad) {
+    const Pop<double> P = make_pop<double>(L, model, norm_row, zmax);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+      std::vector<double> row((size_t)nz);
+      row_of(k, row);
+      double l;
+      out[k] = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l) ? l : NEG_INF;
+    }
+  } else if (model == MODEL_MP) {
+    ln_w_grad<DualM>(L, model, norm_row, zmax, n, m1, m2, dl, lnpi, nz, row_of, out, out_grad, out_kink);
+  } else {
+    ln_w_grad<Dual>(L, model, norm_row, zmax, n, m1, m2, dl, lnpi, nz, row_of, out, out_grad, out_kink);
+  }
+  return 0;
+}
+
 }  // namespace
 
 // ============================================================== C entry points
 extern "C" {
 
-// Full likelihood for K Lambda points.  Arrays are host memory; outputs are
+// Full likelihood for K Lambda points lam[K][n_par]; n_par = 13 selects the power law +
+// peak mass model, 16 the multi-peak model.  Arrays are host memory; outputs are
 // lnL_event[K][n_events], neff_event[K][n_events], ln_xi[K], neff_sel[K],
-// lnL_total[K], flags[K] and, if grad_total != NULL, grad_total[K][13]
-// (want_grad != 0 selects the dual-number pass).  grad_scale[K][13] (may be NULL)
+// lnL_total[K], flags[K] and, if grad_total != NULL, grad_total[K][n_par]
+// (want_grad != 0 selects the dual-number pass).  grad_scale[K][n_par] (may be NULL)
 // receives sum_i sum_k p_ik |d ln w_ik| + N_det sum_m q_m |d ln w_m|, the size of the
-// terms whose difference is the gradient.  grad_kink[K][13] (may be NULL) receives the
+// terms whose difference is the gradient.  grad_kink[K][n_par] (may be NULL) receives the
 // same weighted sum of the one-sided-derivative ambiguity of samples lying within 2e-5
 // LOS cells of a grid node (where either one-sided derivative is correct).  Returns 0,
 // or -1 on invalid inputs.
-int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad,
+int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t n_par, int32_t want_grad,
                double neff_min_event, double neff_min_sel, int32_t n_threads, double* lnL_event,
                double* neff_event, double* ln_xi, double* neff_sel, double* lnL_total,
                int32_t* flags, double* grad_total, double* grad_scale, double* grad_kink) {
-  if (!in || K < 0 || !inputs_valid(*in)) return -1;
+  const int model = model_of(n_par);
+  if (!in || K < 0 || model < 0 || !inputs_valid(*in)) return -1;
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #else
@@ -890,16 +984,20 @@ int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad
   const std::vector<double> pbar = pixel_mean(*in);
   const int ne = in->n_events;
   for (int k = 0; k < K; ++k) {
-    double* g = (want_grad && grad_total) ? grad_total + (size_t)k * NP : nullptr;
-    double* gs = (want_grad && grad_scale) ? grad_scale + (size_t)k * NP : nullptr;
-    double* gk = (want_grad && grad_kink) ? grad_kink + (size_t)k * NP : nullptr;
-    if (want_grad)
-      eval_lambda<Dual>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
-                        lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
+    double* g = (want_grad && grad_total) ? grad_total + (size_t)k * n_par : nullptr;
+    double* gs = (want_grad && grad_scale) ? grad_scale + (size_t)k * n_par : nullptr;
+    double* gk = (want_grad && grad_kink) ? grad_kink + (size_t)k * n_par : nullptr;
+    const double* Lk = lam + (size_t)k * n_par;
+    double* le = lnL_event + (size_t)k * ne;
+    double* nf = neff_event + (size_t)k * ne;
+    if (want_grad && model == MODEL_MP)
+      eval_lambda<DualM>(*in, pbar, Lk, model, neff_min_event, neff_min_sel, le, nf, ln_xi + k,
+                         neff_sel + k, lnL_total + k, flags + k, g, gs, gk);
+    else if (want_grad)
+      eval_lambda<Dual>(*in, pbar, Lk, model, neff_min_event, neff_min_sel, le, nf, ln_xi + k,
                         neff_sel + k, lnL_total + k, flags + k, g, gs, gk);
     else
-      eval_lambda<double>(*in, pbar, lam + (size_t)k * NP, neff_min_event, neff_min_sel,
-                          lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
+      eval_lambda<double>(*in, pbar, Lk, model, neff_min_event, neff_min_sel, le, nf, ln_xi + k,
                           neff_sel + k, lnL_total + k, flags + k, nullptr, nullptr, nullptr);
   }
   return 0;
@@ -909,11 +1007,13 @@ int orc_loglik(const Inputs* in, int32_t K, const double* lam, int32_t want_grad
 // Silverman, 2 biweight; n_grid KDE grid points on [0, zmax]; pixels below
 // neff_min_pixel are dropped.  neff_event receives the effective number of kept pixels.
 // Flags as orc_loglik, without bit 1 (there is no per-event N_eff cut).
-int orc_loglik_kde(const Inputs* in, int32_t K, const double* lam, int32_t bw_rule,
+int orc_loglik_kde(const Inputs* in, int32_t K, const double* lam, int32_t n_par, int32_t bw_rule,
                    int32_t n_grid, double neff_min_pixel, double neff_min_sel, int32_t n_threads,
                    double* lnL_event, double* neff_event, double* ln_xi, double* neff_sel,
                    double* lnL_total, int32_t* flags) {
-  if (!in || K < 0 || !inputs_valid(*in) || n_grid < 2 || bw_rule < 0 || bw_rule > 2) return -1;
+  const int model = model_of(n_par);
+  if (!in || K < 0 || model < 0 || !inputs_valid(*in) || n_grid < 2 || bw_rule < 0 || bw_rule > 2)
+    return -1;
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #else
@@ -922,7 +1022,7 @@ int orc_loglik_kde(const Inputs* in, int32_t K, const double* lam, int32_t bw_ru
   const std::vector<double> pbar = pixel_mean(*in);
   const int ne = in->n_events;
   for (int k = 0; k < K; ++k)
-    eval_lambda_kde(*in, pbar, lam + (size_t)k * NP, bw_rule, n_grid, neff_min_pixel, neff_min_sel,
+    eval_lambda_kde(*in, pbar, lam + (size_t)k * n_par, model, bw_rule, n_grid, neff_min_pixel, neff_min_sel,
                     lnL_event + (size_t)k * ne, neff_event + (size_t)k * ne, ln_xi + k,
                     neff_sel + k, lnL_total + k, flags + k);
   return 0;
@@ -933,7 +1033,8 @@ double orc_bandwidth(const double* z, int64_t n, int32_t bw_rule) {
   return bandwidth(std::vector<double>(z, z + n), bw_rule);
 }
 
-int orc_num_params(void) { return NP; }
+// hyperparameters of mass model 0 (power law + peak) or 1 (multi-peak)
+int orc_num_params(int32_t model) { return model == MODEL_MP ? NP_MP : model == MODEL_PLP ? NP : -1; }
 
 // --- pieces, exposed for the pin tests ---------------------------------------
 double orc_E(double z, double om) { return E_of(z, om); }
@@ -947,28 +1048,40 @@ double orc_S(double m, double mmin, double dm) {
   return ln_S(m, mmin, dm, ls) ? std::exp(ls) : 0.0;
 }
 
-static Pop<double> pop_from(const double* L) {
+// The pieces below take Lambda as L[n_par] (13: power law + peak, 16: multi-peak) and
+// return NaN for any other n_par.
+static Pop<double> pop_from(const double* L, int model) {
   std::vector<double> pbar(2, 1.0);  // N_z is not needed by the mass and rate pieces
-  return make_pop<double>(L, pbar, 1.0);
+  return make_pop<double>(L, model, pbar, 1.0);
 }
+constexpr double NaN_ = std::numeric_limits<double>::quiet_NaN();
 
-double orc_ln_p_m1(double m1, const double* L) {
-  const Pop<double> P = pop_from(L);
+double orc_ln_p_m1(double m1, const double* L, int32_t n_par) {
+  if (model_of(n_par) < 0) return NaN_;
+  const Pop<double> P = pop_from(L, model_of(n_par));
   double o;
   return ln_p_m1(m1, P, o) ? o : NEG_INF;
 }
-double orc_ln_p_m2(double m2, double m1, const double* L) {
-  const Pop<double> P = pop_from(L);
+double orc_ln_p_m2(double m2, double m1, const double* L, int32_t n_par) {
+  if (model_of(n_par) < 0) return NaN_;
+  const Pop<double> P = pop_from(L, model_of(n_par));
   double o;
   return ln_p_m2(m2, m1, P, o) ? o : NEG_INF;
 }
-double orc_C(double m1, const double* L) { return C_of(m1, pop_from(L)); }
-double orc_ln_Zm1(const double* L) { return pop_from(L).lnZm1; }
-double orc_ln_psi(double z, const double* L) { return ln_psi(z, pop_from(L)); }
+double orc_C(double m1, const double* L, int32_t n_par) {
+  return model_of(n_par) < 0 ? NaN_ : C_of(m1, pop_from(L, model_of(n_par)));
+}
+double orc_ln_Zm1(const double* L, int32_t n_par) {
+  return model_of(n_par) < 0 ? NaN_ : pop_from(L, model_of(n_par)).lnZm1;
+}
+double orc_ln_psi(double z, const double* L, int32_t n_par) {
+  return model_of(n_par) < 0 ? NaN_ : ln_psi(z, pop_from(L, model_of(n_par)));
+}
 
-double orc_ln_Nz(const double* L, const double* pbar, int32_t nz, double zmax) {
+double orc_ln_Nz(const double* L, int32_t n_par, const double* pbar, int32_t nz, double zmax) {
+  if (model_of(n_par) < 0) return NaN_;
   std::vector<double> pb(pbar, pbar + nz);
-  return flog(Nz_of(pb, zmax, pop_from(L)));
+  return flog(Nz_of(pb, zmax, pop_from(L, model_of(n_par))));
 }
 
 // The LOS grid cell of z, as used by los_interp above and as the CUDA library documents
@@ -984,46 +1097,26 @@ int32_t orc_los_cell(float zf, int32_t nz, double zmax) {
   return j;
 }
 
-// ln w for n samples against one LOS row that also defines N_z (as the pixel
-// average does for injections).  out_grad[n][13] is filled when non-NULL.
-// Samples with w = 0 get -inf (and a zero gradient).
-int orc_ln_w_row(const double* L, int64_t n, const float* m1, const float* m2, const float* dl,
-                 const float* lnpi, const float* row_f32, int32_t nz, double zmax, double* out,
-                 double* out_grad) {
-  if (!lambda_in_domain(L)) return -1;
+// ln w for n samples against one LOS row that also defines N_z (as the pixel average
+// does for injections).  out_grad[n][n_par] is filled when non-NULL.  Samples with
+// w = 0 get -inf (and a zero gradient).
+int orc_ln_w_row(const double* L, int32_t n_par, int64_t n, const float* m1, const float* m2,
+                 const float* dl, const float* lnpi, const float* row_f32, int32_t nz, double zmax,
+                 double* out, double* out_grad) {
   const std::vector<double> row = row_to_double(row_f32, nz);
-  if (!out_grad) {
-    const Pop<double> P = make_pop<double>(L, row, zmax);
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t k = 0; k < n; ++k) {
-      double l;
-      out[k] = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l) ? l : NEG_INF;
-    }
-    return 0;
-  }
-  const Pop<Dual> P = make_pop<Dual>(L, row, zmax);
-#pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t k = 0; k < n; ++k) {
-    Dual l;
-    if (ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l)) {
-      out[k] = l.v;
-      for (int i = 0; i < NP; ++i) out_grad[(size_t)k * NP + i] = l.d[i];
-    } else {
-      out[k] = NEG_INF;
-      for (int i = 0; i < NP; ++i) out_grad[(size_t)k * NP + i] = 0.0;
-    }
-  }
-  return 0;
+  auto row_of = [&row](int64_t, std::vector<double>& r) { r = row; };
+  return ln_w_any(L, n_par, row, zmax, n, m1, m2, dl, lnpi, nz, row_of, out, out_grad, nullptr);
 }
 
 // ln w of n samples as the likelihood uses them: event samples (pix != NULL) against their
 // pixel's LOS row, injections (pix == NULL) against the pixel mean; N_z from the pixel
-// mean in both cases.  -inf where w = 0; out_grad[n][13] when non-NULL, and out_kink[n][13]
-// (with out_grad) the one-sided-derivative ambiguity of samples near a LOS grid node.
-int orc_ln_w_samples(const double* L, int64_t n, const float* m1, const float* m2, const float* dl,
-                     const float* lnpi, const int32_t* pix, const float* los, int32_t n_pix,
-                     int32_t nz, double zmax, double* out, double* out_grad, double* out_kink) {
-  if (!lambda_in_domain(L)) return -1;
+// mean in both cases.  -inf where w = 0; out_grad[n][n_par] when non-NULL, and
+// out_kink[n][n_par] (with out_grad) the one-sided-derivative ambiguity of samples near a
+// LOS grid node.
+int orc_ln_w_samples(const double* L, int32_t n_par, int64_t n, const float* m1, const float* m2,
+                     const float* dl, const float* lnpi, const int32_t* pix, const float* los,
+                     int32_t n_pix, int32_t nz, double zmax, double* out, double* out_grad,
+                     double* out_kink) {
   std::vector<double> pbar((size_t)nz, 0.0);
   for (int p = 0; p < n_pix; ++p)
     for (int j = 0; j < nz; ++j) pbar[(size_t)j] += (double)los[(size_t)p * nz + j];
@@ -1032,32 +1125,7 @@ int orc_ln_w_samples(const double* L, int64_t n, const float* m1, const float* m
     if (!pix) { row = pbar; return; }
     for (int j = 0; j < nz; ++j) row[(size_t)j] = (double)los[(size_t)pix[k] * nz + j];
   };
-  if (!out_grad) {
-    const Pop<double> P = make_pop<double>(L, pbar, zmax);
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t k = 0; k < n; ++k) {
-      std::vector<double> row((size_t)nz);
-      row_of(k, row);
-      double l;
-      out[k] = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l) ? l : NEG_INF;
-    }
-    return 0;
-  }
-  const Pop<Dual> P = make_pop<Dual>(L, pbar, zmax);
-#pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t k = 0; k < n; ++k) {
-    std::vector<double> row((size_t)nz);
-    row_of(k, row);
-    Dual l;
-    double kk[NP] = {0};
-    const bool ok = ln_w(P, row.data(), nz, zmax, m1[k], m2[k], dl[k], lnpi[k], l, kk);
-    out[k] = ok ? l.v : NEG_INF;
-    for (int i = 0; i < NP; ++i) {
-      out_grad[(size_t)k * NP + i] = ok ? l.d[i] : 0.0;
-      if (out_kink) out_kink[(size_t)k * NP + i] = ok ? kk[i] : 0.0;
-    }
-  }
-  return 0;
+  return ln_w_any(L, n_par, pbar, zmax, n, m1, m2, dl, lnpi, nz, row_of, out, out_grad, out_kink);
 }
 
 // single application of the 15-point Kronrod (which = 0) or 7-point Gauss

@@ -32,6 +32,15 @@ LAMBDA_NAMES = ("H0", "Om", "alpha", "beta", "m_min", "m_max", "delta_m", "mu_g"
                 "sigma_g", "lambda_peak", "gamma", "kappa", "z_p")
 FIDUCIAL = np.array([70.0, 0.3, 3.4, 1.1, 5.0, 90.0, 4.0, 34.0, 4.0, 0.04, 2.7, 3.0, 2.0])
 
+# The multi-peak mass model takes 16: the first Gaussian is the lower-mass peak, and
+# three more entries give the higher-mass peak and the low peak's share of lambda_g.
+# Its reference point is the paper's Table 2 (the injected values of its simulated O5
+# catalogue).
+LAMBDA_NAMES_MP = LAMBDA_NAMES[:7] + ("mu_low", "sigma_low", "lambda_g") + LAMBDA_NAMES[10:] + \
+    ("mu_high", "sigma_high", "lambda_low")
+FIDUCIAL_MP = np.array([67.4, 0.315, 2.9, 1.0, 4.6, 86.3, 4.8, 9.7, 0.7, 0.4, 3.3, 2.9, 2.5,
+                        30.7, 6.3, 0.8])
+
 _D0_MPC = 8000.0      # SNR normalisation distance of the toy detector
 _SNR_THRESHOLD = 12.0
 _INJ_DLMAX = 20000.0  # injections: p(dL) = 2 dL / dLmax^2 on (0, dLmax]
@@ -278,10 +287,14 @@ def injections(w: Workload, seed: int = SEED_BASE, chunk: int = 1 << 22) -> dict
                 n_draw=float(n_draw))
 
 
-def lambda_batch(K: int, seed: int = SEED_BASE, purpose: int = 4) -> np.ndarray:
-    """K Lambda points: H0 ~ U(20, 140), Om ~ U(0.1, 0.5), the rest within +-20% of FIDUCIAL."""
+def lambda_batch(K: int, seed: int = SEED_BASE, purpose: int = 4, model: str = "plp") -> np.ndarray:
+    """K Lambda points: H0 ~ U(20, 140), Om ~ U(0.1, 0.5), the rest within +-20% of
+    FIDUCIAL (model "plp", 13 columns) or of FIDUCIAL_MP (model "multipeak", 16)."""
     g = rng(purpose, seed)
-    lam = FIDUCIAL[None, :] * g.uniform(0.8, 1.2, size=(K, 13))
+    fid = FIDUCIAL_MP if model == "multipeak" else FIDUCIAL
+    if model not in ("plp", "multipeak"):
+        raise ValueError("model is 'plp' or 'multipeak'")
+    lam = fid[None, :] * g.uniform(0.8, 1.2, size=(K, len(fid)))
     lam[:, 0] = g.uniform(20.0, 140.0, size=K)
     lam[:, 1] = g.uniform(0.1, 0.5, size=K)
     return lam
