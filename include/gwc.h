@@ -14,14 +14,26 @@
  *   N_eff,i      = (sum_k w_ik)^2 / sum_k w_ik^2                          (Eq. 7, applied per event)
  *
  * z solves d_L = (c/H0)(1+z) int_0^z dz'/E(z'), E = sqrt(Om (1+z)^3 + 1 - Om) (Eq. 1, flat).
- * The mass model is a power law plus a Gaussian peak with a low-mass smoothing window,
- * and psi is the Madau-Dickinson rate shape with psi(0) = 1.
+ * The mass model is a power law plus a Gaussian peak with a low-mass smoothing window
+ * (GWC_MASS_PLP), or the multi-peak model of the paper's simulated catalogue (App. A,
+ * Table 2; GWC_MASS_MULTIPEAK): a power law plus two Gaussian peaks, mixed as
+ * (1 - lambda_g) P + lambda_g [lambda_low G_low + (1 - lambda_low) G_high], every
+ * component normalised on [m_min, m_max], with the same smoothing.  psi is the
+ * Madau-Dickinson rate shape with psi(0) = 1.
  *
- * Lambda layout (13 doubles, in this order):
+ * Lambda layout: P doubles per point, in this order, where P = GWC_NUM_PARAMS (13) for
+ * GWC_MASS_PLP and GWC_NUM_PARAMS_MULTIPEAK (16) for GWC_MASS_MULTIPEAK (the context's
+ * options.mass_model; gwc_get_info reports P):
  *   [H0 (km/s/Mpc), Om, alpha, beta, m_min, m_max, delta_m, mu_g, sigma_g, lambda_peak,
  *    gamma, kappa, z_p]
+ * and for the multi-peak model, where (mu_g, sigma_g, lambda_peak) are the low peak's
+ * (mu_low, sigma_low) and lambda_g, three more: [..., mu_high, sigma_high, lambda_low].
+ * Every [K][P] array below (Lambda points, gradients, HMC states) has this width.
  * Domain: H0 > 0, 0 <= Om <= 1, m_min > 0, m_max > m_min, delta_m >= 0,
- * m_min + delta_m < m_max, sigma_g > 0, 0 <= lambda_peak <= 1, z_p > -1, all finite.
+ * m_min + delta_m < m_max, sigma_g > 0, 0 <= lambda_peak <= 1, z_p > -1, all finite; the
+ * multi-peak model adds sigma_high > 0 and 0 <= lambda_low <= 1.  Its gradient is the
+ * interior derivative: at lambda_g or lambda_low equal to 0 or 1 the two components
+ * d/d lambda_g and d/d lambda_low are NaN (the other components stay exact).
  * A point outside the domain is not an error: its flags bit 0 is set and its
  * log-likelihood outputs are -inf.
  *
@@ -47,7 +59,10 @@
 extern "C" {
 #endif
 
-#define GWC_NUM_PARAMS 13
+#define GWC_NUM_PARAMS 13              /* Lambda entries, power law + peak */
+#define GWC_NUM_PARAMS_MULTIPEAK 16    /* Lambda entries, multi-peak */
+#define GWC_MASS_PLP 0
+#define GWC_MASS_MULTIPEAK 1
 
 typedef enum {
   GWC_OK = 0,
@@ -131,6 +146,7 @@ typedef struct {
                             counts the kept samples, and every later output (per-sample
                             terms included) refers to the kept samples only. */
   uint64_t cap_seed;     /* seed of that choice (default 0) */
+  int32_t mass_model;    /* GWC_MASS_PLP (default) or GWC_MASS_MULTIPEAK; sets the Lambda width */
 } gwc_options;
 
 /* Fill *o with the defaults listed above. */
@@ -142,14 +158,14 @@ gwc_status gwc_create(const gwc_events* events, const gwc_los* los,
                       const gwc_injections* inj, const gwc_options* opts, gwc_ctx** out);
 
 /* Log-likelihood for K Lambda points (1 <= K <= max_K).  Device pointers:
- *   d_lambda[K][13] (in), d_lnL_event[K][n_events], d_neff_event[K][n_events],
+ *   d_lambda[K][P] (in), d_lnL_event[K][n_events], d_neff_event[K][n_events],
  *   d_ln_xi[K], d_neff_sel[K], d_lnL_total[K], d_flags[K] (out).
  * d_lnL_event and d_neff_event may be NULL when n_events == 0. */
 gwc_status gwc_loglik(gwc_ctx* ctx, int32_t K, const double* d_lambda, double* d_lnL_event,
                       double* d_neff_event, double* d_ln_xi, double* d_neff_sel,
                       double* d_lnL_total, int32_t* d_flags, void* stream);
 
-/* As gwc_loglik, plus d_grad_total[K][13] = d lnL_total / d Lambda (zero where a flag
+/* As gwc_loglik, plus d_grad_total[K][P] = d lnL_total / d Lambda (zero where a flag
  * is set).  Each sample's derivative is recomputed in the same pass as its weight. */
 gwc_status gwc_loglik_grad(gwc_ctx* ctx, int32_t K, const double* d_lambda, double* d_lnL_event,
                            double* d_neff_event, double* d_ln_xi, double* d_neff_sel,
@@ -194,7 +210,7 @@ gwc_status gwc_loglik_kde(gwc_ctx* ctx, int32_t K, const double* d_lambda,
  * gives for its share: d_lnL_event, d_neff_event, d_ln_xi (ln of its injections' sum
  * over the whole n_draw), d_neff_sel and d_flags as gwc_loglik; d_sum_events[K] = the sum
  * of its events' ln L_i (-inf if one has no weight); and, when both are non-NULL,
- * d_grad_events[K][13] (gradient of that sum) and d_grad_ln_xi[K][13] (gradient of its
+ * d_grad_events[K][P] (gradient of that sum) and d_grad_ln_xi[K][P] (gradient of its
  * ln xi).  Shards combine exactly: xi = sum over shards of xi_r, so
  *   ln L = sum_r sum_events_r - N_det ln(sum_r xi_r)
  *   grad = sum_r grad_events_r - N_det sum_r (xi_r / xi) grad_ln_xi_r
@@ -209,14 +225,15 @@ gwc_status gwc_loglik_parts(gwc_ctx* ctx, int32_t K, const double* d_lambda, dou
  * arithmetic, one Lambda per launch sequence, every sample re-read from memory for each
  * Lambda, per-sample weights (and, for the gradient, per-sample weighted derivatives)
  * written to device memory and reduced in separate passes.  Same outputs as
- * gwc_loglik_grad (d_grad_total may be NULL for the value only). */
+ * gwc_loglik_grad (d_grad_total may be NULL for the value only).  Power law + peak
+ * contexts only (GWC_E_UNSUPPORTED for the multi-peak model). */
 gwc_status gwc_loglik_plain(gwc_ctx* ctx, int32_t K, const double* d_lambda,
                             double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
                             double* d_neff_sel, double* d_lnL_total, int32_t* d_flags,
                             double* d_grad_total, void* stream);
 
-/* Host-memory convenience form of gwc_loglik_grad: h_lambda[K][13] in; h_lnL_total[K],
- * h_flags[K] and h_grad_total[K][13] out (h_grad_total may be NULL for the value only).
+/* Host-memory convenience form of gwc_loglik_grad: h_lambda[K][P] in; h_lnL_total[K],
+ * h_flags[K] and h_grad_total[K][P] out (h_grad_total may be NULL for the value only).
  * Copies through the context's pinned staging buffers and synchronises the stream. */
 gwc_status gwc_loglik_grad_host(gwc_ctx* ctx, int32_t K, const double* h_lambda,
                                 double* h_lnL_total, int32_t* h_flags, double* h_grad_total,
@@ -245,15 +262,15 @@ void gwc_graph_destroy(gwc_graph* graph);   /* NULL is a no-op */
  * CUDA graph and replayed by gwc_hmc_launch.  The paper samples with nested sampling
  * and has no counterpart; this uses the gradient of gwc_loglik_grad for the leapfrog
  * integrator of HMC (Duane et al. 1987; Neal 2011, "MCMC using Hamiltonian dynamics").
- * With M^-1 = diag(d_inv_mass[13]) and step eps_k = d_eps[k], a replay evaluates lnL and
+ * With M^-1 = diag(d_inv_mass[P]) and step eps_k = d_eps[k], a replay evaluates lnL and
  * its gradient at q, takes n_leapfrog leapfrog steps
  *     p += eps/2 grad lnL(q);  q += eps M^-1 p;  p += eps/2 grad lnL(q)
  * (n_leapfrog + 1 evaluations, the half kicks between steps merged into full ones), and
  * accepts the end point when log_u_k < H(start) - H(end), H = -lnL + p.M^-1.p / 2.
- * Device arrays, all caller-owned: d_q[K][13] (in: start; out: the accepted end point or
- * the start again), d_p[K][13] (in: initial momenta, drawn by the caller from N(0, M);
+ * Device arrays, all caller-owned: d_q[K][P] (in: start; out: the accepted end point or
+ * the start again), d_p[K][P] (in: initial momenta, drawn by the caller from N(0, M);
  * out: final momenta of the proposal), d_log_u[K] (in: log of uniform(0,1) numbers drawn
- * by the caller), d_lnL[K] and d_grad[K][13] (out: at the returned point), d_accept[K]
+ * by the caller), d_lnL[K] and d_grad[K][P] (out: at the returned point), d_accept[K]
  * (out: 1 or 0), d_H[K][2] (out: H at the start and the end).  A chain whose path meets
  * a flagged point (outside the domain, or an N_eff cut) stops moving and is rejected.
  * The graph holds its own evaluation buffers (allocated here) and uses the context's
@@ -268,7 +285,7 @@ gwc_status gwc_hmc_launch(gwc_hmc* hmc, void* stream);
 void gwc_hmc_destroy(gwc_hmc* hmc);   /* NULL is a no-op */
 
 /* Launch-shape autotuner.  Times whole calls (gwc_loglik_grad when want_grad != 0,
- * gwc_loglik otherwise) on the caller's K points d_lambda[K][13] (device) at every
+ * gwc_loglik otherwise) on the caller's K points d_lambda[K][P] (device) at every
  * shape of chunk in {1024, 2048} x Lambda tile in {16, 32, 64} (clamped to K) x warp
  * group in {1, 2, 4, 8}: one untimed call, then two timed with CUDA events on the
  * stream.  The fastest shape becomes the context's chunk, lambda_tile and lambda_group
@@ -306,6 +323,8 @@ typedef struct {
   int32_t n_x_table;
   int32_t max_K;
   int64_t device_bytes;  /* device memory held by the context */
+  int32_t n_params;      /* P: Lambda entries of the context's mass model (13 or 16) */
+  int32_t mass_model;
 } gwc_info;
 
 gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
@@ -316,9 +335,9 @@ gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
  * context's order (stably sorted by dl_mpc, then each consecutive block of 256 stably
  * sorted by m1_det):
  *   d_lnw[n_samples + n_found]          ln w minus the per-Lambda constant c (-inf where w = 0)
- *   d_dlnw[13][n_samples + n_found]     (optional, may be NULL) d(ln w - c)/d Lambda
- *   d_c[14]                             c and dc/d Lambda, so ln w = d_lnw + c
- * d_lambda points to 13 doubles on the device.  Uses the context's per-call scratch. */
+ *   d_dlnw[P][n_samples + n_found]      (optional, may be NULL) d(ln w - c)/d Lambda
+ *   d_c[1 + P]                          c and dc/d Lambda, so ln w = d_lnw + c
+ * d_lambda points to P doubles on the device.  Uses the context's per-call scratch. */
 gwc_status gwc_sample_terms(gwc_ctx* ctx, const double* d_lambda, float* d_lnw, float* d_dlnw,
                             double* d_c, void* stream);
 
@@ -331,7 +350,7 @@ gwc_status gwc_sample_terms(gwc_ctx* ctx, const double* d_lambda, float* d_lnw, 
  * a gwc_ctx.  It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
  * (one Lambda point's constants and tables and the pixel-mean LOS row, about 80 KB) is a
  * fixed device array inside the library, held by every GPU that loads the library until
- * the process exits.
+ * the process exits.  It evaluates the power law + peak model (13-entry Lambda).
  *   d_lambda[13]                      Lambda (device, doubles)
  *   d_samples[n_samples][4]           {m1_det, m2_det, d_L, ln pi_PE} (device, 16-byte aligned)
  *   d_pix[n_samples]                  pixel of each sample, in [0, n_pix)

@@ -18,7 +18,10 @@ import threading
 
 import numpy as np
 
-NUM_PARAMS = 13
+NUM_PARAMS = 13               # Lambda entries, power law + peak mass model
+NUM_PARAMS_MULTIPEAK = 16     # Lambda entries, multi-peak mass model
+MASS_PLP, MASS_MULTIPEAK = 0, 1
+MASS_MODELS = {"plp": MASS_PLP, "multipeak": MASS_MULTIPEAK}
 FLAG_DOMAIN, FLAG_NEFF_EVENT, FLAG_NEFF_SEL, FLAG_XI_ZERO = 1, 2, 4, 8
 LOS_F32, LOS_BF16 = 0, 1
 STATUS = {0: "GWC_OK", -1: "GWC_E_INVALID", -2: "GWC_E_CUDA", -3: "GWC_E_NOMEM",
@@ -60,7 +63,7 @@ class Options(ctypes.Structure):
                 ("n_x_table", ctypes.c_int32), ("max_K", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("lambda_tile", ctypes.c_int32),
                 ("lambda_group", ctypes.c_int32), ("cap_per_pixel", ctypes.c_int32),
-                ("cap_seed", ctypes.c_uint64)]
+                ("cap_seed", ctypes.c_uint64), ("mass_model", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -68,7 +71,8 @@ class Info(ctypes.Structure):
                 ("n_injections", ctypes.c_int64), ("n_pix", ctypes.c_int32),
                 ("n_z", ctypes.c_int32), ("n_items", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("n_x_table", ctypes.c_int32), ("max_K", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("n_params", ctypes.c_int32),
+                ("mass_model", ctypes.c_int32)]
 
 
 class KdeOptions(ctypes.Structure):
@@ -162,11 +166,34 @@ def lib():
 
 
 def default_options(**kw) -> Options:
+    """gwc_default_options with fields overridden by keyword (mass_model may be given by
+    name, "plp" or "multipeak")."""
     o = Options()
     lib().gwc_default_options(ctypes.byref(o))
     for k, v in kw.items():
+        if k == "mass_model" and isinstance(v, str):
+            v = MASS_MODELS[v]
         setattr(o, k, v)
     return o
+
+
+def _lam_batch(lam):
+    """Check a CUDA float64 Lambda batch [K, P], P = 13 or 16; returns it contiguous."""
+    import torch
+    if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64
+            and lam.dim() == 2 and lam.shape[1] in (NUM_PARAMS, NUM_PARAMS_MULTIPEAK)):
+        raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13] (or [K, 16] for "
+                        "the multi-peak model)")
+    return lam.contiguous()
+
+
+def _check_width(ctx, P):
+    """The library reads P doubles per Lambda point from the context's mass model: refuse
+    a batch of another width before it can read past the caller's tensor."""
+    info = Info()
+    _check(lib().gwc_get_info(ctx, ctypes.byref(info)), ctx)
+    if P != info.n_params:
+        raise TypeError(f"this context's mass model takes Lambda rows of {info.n_params} entries, not {P}")
 
 
 def last_error(ctx=None) -> str:
@@ -227,7 +254,7 @@ def get_info(ctx) -> dict:
     return {f: getattr(info, f) for f, _ in Info._fields_}
 
 
-def _outputs(K, n_ev, device, grad):
+def _outputs(K, n_ev, device, grad, P=NUM_PARAMS):
     import torch
     f64 = dict(dtype=torch.float64, device=device)
     out = dict(lnL_event=torch.empty((K, n_ev), **f64), neff_event=torch.empty((K, n_ev), **f64),
@@ -235,18 +262,16 @@ def _outputs(K, n_ev, device, grad):
                lnL_total=torch.empty(K, **f64),
                flags=torch.empty(K, dtype=torch.int32, device=device))
     if grad:
-        out["grad_total"] = torch.empty((K, NUM_PARAMS), **f64)
+        out["grad_total"] = torch.empty((K, P), **f64)
     return out
 
 
 def _call(fn, ctx, lam, n_events, grad, stream, out, plain=False):
-    import torch
-    if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
-        raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
-    lam = lam.contiguous()
+    lam = _lam_batch(lam)
+    _check_width(ctx, lam.shape[1])
     K = lam.shape[0]
     if out is None:
-        out = _outputs(K, n_events, lam.device, grad)
+        out = _outputs(K, n_events, lam.device, grad, lam.shape[1])
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     args = [ctx, K, p(lam), p(out["lnL_event"]), p(out["neff_event"]), p(out["ln_xi"]),
             p(out["neff_sel"]), p(out["lnL_total"]), p(out["flags"])]
@@ -258,12 +283,13 @@ def _call(fn, ctx, lam, n_events, grad, stream, out, plain=False):
 
 
 def loglik(ctx, lam, n_events, stream=None, out=None):
-    """gwc_loglik: lam is a CUDA float64 tensor [K, 13]; returns a dict of tensors."""
+    """gwc_loglik: lam is a CUDA float64 tensor [K, P] (P = 13, or 16 for the multi-peak
+    model, matching the context); returns a dict of tensors."""
     return _call(lib().gwc_loglik, ctx, lam, n_events, False, stream, out)
 
 
 def loglik_grad(ctx, lam, n_events, stream=None, out=None):
-    """gwc_loglik_grad: as loglik, plus grad_total [K, 13]."""
+    """gwc_loglik_grad: as loglik, plus grad_total [K, P]."""
     return _call(lib().gwc_loglik_grad, ctx, lam, n_events, True, stream, out)
 
 
@@ -280,10 +306,8 @@ def default_kde_options(**kw):
 def loglik_kde(ctx, lam, n_events, bw="scott", n_grid=256, neff_min_pixel=2.0, stream=None, out=None):
     """gwc_loglik_kde: the paper's KDE form of the event terms (value only); neff_event
     holds the effective number of kept pixels of each event."""
-    import torch
-    if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
-        raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
-    lam = lam.contiguous()
+    lam = _lam_batch(lam)
+    _check_width(ctx, lam.shape[1])
     K = lam.shape[0]
     if out is None:
         out = _outputs(K, n_events, lam.device, False)
@@ -299,7 +323,7 @@ def loglik_plain(ctx, lam, n_events, grad=True, stream=None, out=None):
     """gwc_loglik_plain: the single-Lambda baseline path (same outputs)."""
     if out is None:
         import torch
-        out = _outputs(lam.shape[0], n_events, lam.device, grad)
+        out = _outputs(lam.shape[0], n_events, lam.device, grad, lam.shape[-1])
         if not grad:
             out["grad_total"] = None
     return _call(lib().gwc_loglik_plain, ctx, lam, n_events, False, stream, out, plain=True)
@@ -308,10 +332,11 @@ def loglik_plain(ctx, lam, n_events, grad=True, stream=None, out=None):
 def loglik_grad_host(ctx, lam: np.ndarray, grad=True, stream=None):
     """gwc_loglik_grad_host: host Lambda in, host total / flags / gradient out."""
     lam = np.ascontiguousarray(np.atleast_2d(lam), dtype=np.float64)
+    _check_width(ctx, lam.shape[1])
     K = lam.shape[0]
     tot = np.empty(K, np.float64)
     flags = np.empty(K, np.int32)
-    g = np.empty((K, NUM_PARAMS), np.float64) if grad else None
+    g = np.empty((K, lam.shape[1]), np.float64) if grad else None
     st = lib().gwc_loglik_grad_host(ctx, K, _np_ptr(lam), _np_ptr(tot), _np_ptr(flags),
                                     _np_ptr(g) if grad else None, _stream_ptr(stream))
     _check(st, ctx)
@@ -319,12 +344,14 @@ def loglik_grad_host(ctx, lam: np.ndarray, grad=True, stream=None):
 
 
 def sample_terms(ctx, lam, n_total, grad=True, stream=None):
-    """gwc_sample_terms for one Lambda (CUDA float64 tensor [13]): (ln w - c, d, c[14])."""
+    """gwc_sample_terms for one Lambda (CUDA float64 tensor [P]): (ln w - c, d [P, n], c[1 + P])."""
     import torch
     lam = lam.contiguous()
+    P = lam.numel()
+    _check_width(ctx, P)
     lnw = torch.empty(n_total, dtype=torch.float32, device=lam.device)
-    d = torch.empty((13, n_total), dtype=torch.float32, device=lam.device) if grad else None
-    c = torch.empty(14, dtype=torch.float64, device=lam.device)
+    d = torch.empty((P, n_total), dtype=torch.float32, device=lam.device) if grad else None
+    c = torch.empty(1 + P, dtype=torch.float64, device=lam.device)
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     _check(lib().gwc_sample_terms(ctx, p(lam), p(lnw), p(d), p(c), _stream_ptr(stream)), ctx)
     return lnw, d, c
@@ -444,18 +471,19 @@ def los_cell_index(z, n_z, z_max, stream=None):
 class Graph:
     """gwc_graph: one recorded gwc_loglik / gwc_loglik_grad call on fixed tensors.
 
-    ``lam`` [K, 13] (CUDA float64) is the input the replays read: write the next points
+    ``lam`` [K, P] (CUDA float64) is the input the replays read: write the next points
     into it (``lam.copy_(...)``) and call ``launch()``; the results land in ``out``.
     """
 
     def __init__(self, context, lam, grad=True, out=None):
         import torch
-        if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64
-                and lam.is_contiguous()):
-            raise TypeError("lam must be a contiguous CUDA float64 tensor of shape [K, 13]")
+        if not (isinstance(lam, torch.Tensor) and lam.is_contiguous()):
+            raise TypeError("lam must be a contiguous CUDA float64 tensor of shape [K, P]")
+        lam = _lam_batch(lam)
+        _check_width(context._ctx, lam.shape[1])
         K = lam.shape[0]
         self.context, self.lam, self.grad = context, lam, grad
-        self.out = out if out is not None else _outputs(K, context.n_events, lam.device, grad)
+        self.out = out if out is not None else _outputs(K, context.n_events, lam.device, grad, lam.shape[1])
         p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
         o = self.out
         h = ctypes.c_void_p()
@@ -488,21 +516,22 @@ class Hmc:
 
     The device tensors q, p, log_u (inputs) and lnL, grad, accept, H (outputs) are owned
     here; ``run(q, p, log_u)`` copies the inputs in (any of them may be omitted to keep
-    the current contents) and replays the trajectory.  eps [K] and inv_mass [13] are
-    fixed at creation.
+    the current contents) and replays the trajectory.  eps [K] and inv_mass [P] are
+    fixed at creation (P: the context's Lambda width).
     """
 
     def __init__(self, context, K, n_leapfrog, eps, inv_mass, device="cuda"):
         import torch
         f64 = dict(dtype=torch.float64, device=device)
         self.context = context
+        P = context.n_params
         self.eps = torch.as_tensor(eps, **f64).reshape(-1).expand(K).contiguous()
-        self.inv_mass = torch.as_tensor(inv_mass, **f64).reshape(NUM_PARAMS).contiguous()
-        self.q = torch.zeros((K, NUM_PARAMS), **f64)
-        self.p = torch.zeros((K, NUM_PARAMS), **f64)
+        self.inv_mass = torch.as_tensor(inv_mass, **f64).reshape(P).contiguous()
+        self.q = torch.zeros((K, P), **f64)
+        self.p = torch.zeros((K, P), **f64)
         self.log_u = torch.zeros(K, **f64)
         self.lnL = torch.zeros(K, **f64)
-        self.grad = torch.zeros((K, NUM_PARAMS), **f64)
+        self.grad = torch.zeros((K, P), **f64)
         self.accept = torch.zeros(K, dtype=torch.int32, device=device)
         self.H = torch.zeros((K, 2), **f64)
         p = lambda t: ctypes.c_void_p(t.data_ptr())
@@ -542,6 +571,7 @@ class Context:
         self.options = options
         self.n_events = len(cat["offsets"]) - 1
         self._ctx = create(cat, options)
+        self.n_params = NUM_PARAMS_MULTIPEAK if options.mass_model == MASS_MULTIPEAK else NUM_PARAMS
 
     def loglik(self, lam, stream=None):
         return loglik(self._ctx, lam, self.n_events, stream)
@@ -555,17 +585,16 @@ class Context:
     def loglik_parts(self, lam, grad=True, stream=None):
         """gwc_loglik_parts: this context's share of a sharded catalogue (see shard.merge_parts)."""
         import torch
-        if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
-            raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
-        lam = lam.contiguous()
-        K = lam.shape[0]
+        lam = _lam_batch(lam)
+        _check_width(self._ctx, lam.shape[1])
+        K, P = lam.shape
         f64 = dict(dtype=torch.float64, device=lam.device)
         out = _outputs(K, self.n_events, lam.device, False)
         del out["lnL_total"]
         out["sum_events"] = torch.empty(K, **f64)
         if grad:
-            out["grad_events"] = torch.empty((K, NUM_PARAMS), **f64)
-            out["grad_ln_xi"] = torch.empty((K, NUM_PARAMS), **f64)
+            out["grad_events"] = torch.empty((K, P), **f64)
+            out["grad_ln_xi"] = torch.empty((K, P), **f64)
         p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
         _check(lib().gwc_loglik_parts(self._ctx, K, p(lam), p(out["lnL_event"]), p(out["neff_event"]),
                                       p(out["ln_xi"]), p(out["neff_sel"]), p(out["sum_events"]),
@@ -588,11 +617,9 @@ class Context:
         return sample_terms(self._ctx, lam, info["n_samples"] + info["n_injections"], grad, stream)
 
     def autotune(self, lam, grad=True, stream=None):
-        """gwc_autotune on the Lambda batch lam [K, 13]: returns the chosen shape."""
-        import torch
-        if not (isinstance(lam, torch.Tensor) and lam.is_cuda and lam.dtype == torch.float64):
-            raise TypeError("lam must be a CUDA float64 tensor of shape [K, 13]")
-        lam = lam.contiguous()
+        """gwc_autotune on the Lambda batch lam [K, P]: returns the chosen shape."""
+        lam = _lam_batch(lam)
+        _check_width(self._ctx, lam.shape[1])
         r = TuneResult()
         _check(lib().gwc_autotune(self._ctx, lam.shape[0], ctypes.c_void_p(lam.data_ptr()),
                                   int(bool(grad)), _stream_ptr(stream), ctypes.byref(r)), self._ctx)

@@ -47,6 +47,8 @@ struct gwc_ctx {
   int32_t n_pix = 0, n_z = 0;
   double z_max = 0.0;
   bool bf16 = false;
+  bool mp = false;      // multi-peak mass model
+  int np = NP;          // Lambda entries per point of the mass model (13 or 16)
   int32_t n_items = 0, inj_item0 = 0;
   int tstride = 0;
   int64_t device_bytes = 0;
@@ -302,6 +304,7 @@ gwc_status run_prologue(gwc_ctx* c, int K, const double* d_lambda, bool grad, cu
   pa.tables = c->tables;
   pa.tstride = c->tstride;
   pa.want_grad = grad ? 1 : 0;
+  pa.mp = c->mp ? 1 : 0;
   cudaError_t e = launch_prologue(pa, K, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "prologue launch");
   return GWC_OK;
@@ -312,6 +315,7 @@ gwc_status run_merge(gwc_ctx* c, int K, int P, bool grad, double* lnL_event, dou
                      double* grad_total, cudaStream_t s, double* sum_events = nullptr,
                      double* grad_events = nullptr, double* grad_ln_xi = nullptr) {
   MergeArgs ma;
+  ma.mp = c->mp ? 1 : 0;
   ma.sum_events = sum_events;
   ma.grad_events = grad_events;
   ma.grad_ln_xi = grad_ln_xi;
@@ -368,6 +372,7 @@ gwc_status launch_fused_items(gwc_ctx* c, int32_t K, bool grad, const int32_t* s
   fa.n_sched = n_sched;
   fa.stride = (int)stride;
   fa.slot0 = (int)slot0;
+  fa.mp = c->mp ? 1 : 0;
   const long long units = (long long)n_sched * n_slabs;
   if (units > 0x7fffffffLL) return fail(c, GWC_E_INVALID, "work grid too large");
   // persistent launch: as many CTAs as fit on the GPU at once, each taking units in
@@ -537,6 +542,7 @@ void gwc_default_options(gwc_options* o) {
   o->lambda_group = 0;
   o->cap_per_pixel = 0;
   o->cap_seed = 0;
+  o->mass_model = GWC_MASS_PLP;
 }
 
 gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_injections* inj,
@@ -560,6 +566,8 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
     return fail(nullptr, GWC_E_INVALID, "lambda_tile must be in [0, " + std::to_string(MAX_SLAB) + "]");
   if (!(o.neff_min_event >= 0.0) || !(o.neff_min_sel >= 0.0)) return fail(nullptr, GWC_E_INVALID, "N_eff thresholds must be >= 0");
   if (o.cap_per_pixel < 0) return fail(nullptr, GWC_E_INVALID, "cap_per_pixel must be >= 0");
+  if (o.mass_model != GWC_MASS_PLP && o.mass_model != GWC_MASS_MULTIPEAK)
+    return fail(nullptr, GWC_E_INVALID, "mass_model must be GWC_MASS_PLP or GWC_MASS_MULTIPEAK");
 
   // ---- validate the events
   const int32_t ne = ev->n_events;
@@ -674,6 +682,8 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   c->n_z = los->n_z;
   c->z_max = los->z_max;
   c->bf16 = o.los_dtype == GWC_LOS_BF16;
+  c->mp = o.mass_model == GWC_MASS_MULTIPEAK;
+  c->np = n_params(c->mp);
   c->tstride = (table_floats(o.n_x_table) + 3) & ~3;
 
   // ---- host layout: samples sorted by pixel inside each event, work items
@@ -781,11 +791,11 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(dalloc(c, &c->partials, (size_t)kcap * c->n_items * PSTRIDE));
   chk(dalloc(c, &c->counter, 1));
   chk(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device));
-  chk(dalloc(c, &c->d_lam, (size_t)o.max_K * NP));
-  chk(dalloc(c, &c->d_out, (size_t)o.max_K * (2 * (size_t)std::max(ne, 1) + 3 + NP)));
+  chk(dalloc(c, &c->d_lam, (size_t)o.max_K * NP_MAX));
+  chk(dalloc(c, &c->d_out, (size_t)o.max_K * (2 * (size_t)std::max(ne, 1) + 3 + NP_MAX)));
   chk(dalloc(c, &c->d_flags, (size_t)o.max_K));
-  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->h_lam), sizeof(double) * o.max_K * NP);
-  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->h_out), sizeof(double) * o.max_K * (1 + NP));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->h_lam), sizeof(double) * o.max_K * NP_MAX);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->h_out), sizeof(double) * o.max_K * (1 + NP_MAX));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->h_flags), sizeof(int32_t) * o.max_K);
   if (e != cudaSuccess) {
     const bool oom = e == cudaErrorMemoryAllocation;
@@ -904,6 +914,7 @@ gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const g
   ka.tstride = c->tstride;
   ka.partials = c->kde_partials;
   ka.stride = (int)c->kde_stride;
+  ka.mp = c->mp ? 1 : 0;
   cudaError_t e = launch_kde(ka, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "KDE launch");
   if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
@@ -956,6 +967,7 @@ gwc_status gwc_loglik_plain(gwc_ctx* c, int32_t K, const double* d_lambda, doubl
   gwc_status st = check_call(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel,
                              d_lnL_total, d_flags);
   if (st != GWC_OK) return st;
+  if (c->mp) return fail(c, GWC_E_UNSUPPORTED, "the plain path evaluates the power law + peak model only");
   const bool grad = d_grad_total != nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long ntot = c->n_samples + c->n_inj;
@@ -1032,8 +1044,8 @@ gwc_status gwc_loglik_grad_host(gwc_ctx* c, int32_t K, const double* h_lambda,
   double* neff_sel = ln_xi + c->opt.max_K;
   double* lnL_total = neff_sel + c->opt.max_K;
   double* grad = lnL_total + c->opt.max_K;
-  std::memcpy(c->h_lam, h_lambda, sizeof(double) * (size_t)K * NP);
-  cudaError_t e = cudaMemcpyAsync(c->d_lam, c->h_lam, sizeof(double) * (size_t)K * NP, cudaMemcpyHostToDevice, s);
+  std::memcpy(c->h_lam, h_lambda, sizeof(double) * (size_t)K * c->np);
+  cudaError_t e = cudaMemcpyAsync(c->d_lam, c->h_lam, sizeof(double) * (size_t)K * c->np, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "H2D copy");
   gwc_status st = (h_grad_total ? gwc_loglik_grad(c, K, c->d_lam, lnL_event, neff_event, ln_xi, neff_sel,
                                                   lnL_total, c->d_flags, grad, stream)
@@ -1042,14 +1054,14 @@ gwc_status gwc_loglik_grad_host(gwc_ctx* c, int32_t K, const double* h_lambda,
   if (st != GWC_OK) return st;
   e = cudaMemcpyAsync(c->h_out, lnL_total, sizeof(double) * (size_t)K, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && h_grad_total)
-    e = cudaMemcpyAsync(c->h_out + K, grad, sizeof(double) * (size_t)K * NP, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(c->h_out + K, grad, sizeof(double) * (size_t)K * c->np, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "D2H copy");
   std::memcpy(h_lnL_total, c->h_out, sizeof(double) * (size_t)K);
   std::memcpy(h_flags, c->h_flags, sizeof(int32_t) * (size_t)K);
-  if (h_grad_total) std::memcpy(h_grad_total, c->h_out + K, sizeof(double) * (size_t)K * NP);
+  if (h_grad_total) std::memcpy(h_grad_total, c->h_out + K, sizeof(double) * (size_t)K * c->np);
   return GWC_OK;
 }
 
@@ -1087,6 +1099,8 @@ gwc_status gwc_get_info(const gwc_ctx* c, gwc_info* out) {
   out->n_x_table = c->opt.n_x_table;
   out->max_K = c->opt.max_K;
   out->device_bytes = c->device_bytes;
+  out->n_params = c->np;
+  out->mass_model = c->opt.mass_model;
   return GWC_OK;
 }
 
@@ -1114,6 +1128,7 @@ gwc_status gwc_sample_terms(gwc_ctx* c, const double* d_lambda, float* d_lnw, fl
   ta.lnw = d_lnw;
   ta.dlnw = d_dlnw;
   ta.c = d_c;
+  ta.mp = c->mp ? 1 : 0;
   cudaError_t e = launch_sample_terms(ta, c->bf16, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "sample-terms launch");
   return GWC_OK;
@@ -1155,6 +1170,7 @@ gwc_status gwc_graph_create(gwc_ctx* c, int32_t K, const double* d_lambda, int32
     fa.chunk = c->opt.chunk;
     fa.slab = slab;
     fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+    fa.mp = c->mp ? 1 : 0;
     const bool grad = want_grad != 0, kahan = c->opt.accum == 1;
     const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
                          ((uint64_t)grad << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;
@@ -1266,7 +1282,7 @@ gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const doubl
   // device block: lnL_event, neff_event [K][n_ev]; ln_xi, neff_sel, lnL_total, lnL0 [K];
   // grad_total, q0, grad0 [K][13]; flags, div [K]
   const size_t ne = (size_t)std::max(c->n_events, 1);
-  const size_t nd = 2 * (size_t)K * ne + 4 * (size_t)K + 3 * (size_t)K * NP;
+  const size_t nd = 2 * (size_t)K * ne + 4 * (size_t)K + 3 * (size_t)K * c->np;
   cudaError_t e = cudaMalloc(&h->mem, nd * sizeof(double) + 2 * (size_t)K * sizeof(int32_t));
   if (e != cudaSuccess) {
     delete h;
@@ -1281,14 +1297,15 @@ gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const doubl
   double* neff_sel = m; m += K;
   double* lnL_total = m; m += K;
   double* lnL0 = m; m += K;
-  double* grad_total = m; m += (size_t)K * NP;
-  double* q0 = m; m += (size_t)K * NP;
-  double* grad0 = m; m += (size_t)K * NP;
+  double* grad_total = m; m += (size_t)K * c->np;
+  double* q0 = m; m += (size_t)K * c->np;
+  double* grad0 = m; m += (size_t)K * c->np;
   int32_t* flags = reinterpret_cast<int32_t*>(m);
   int32_t* div = flags + K;
 
   HmcArgs ha;
   ha.K = K;
+  ha.np = c->np;
   ha.eps = d_eps;
   ha.inv_mass = d_inv_mass;
   ha.q = d_q;
@@ -1322,6 +1339,7 @@ gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const doubl
     fa.chunk = c->opt.chunk;
     fa.slab = slab;
     fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+    fa.mp = c->mp ? 1 : 0;
     const bool kahan = c->opt.accum == 1;
     const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
                          (1ull << 2) | ((uint64_t)kahan << 1) | (uint64_t)c->bf16;
@@ -1424,7 +1442,7 @@ gwc_status gwc_autotune(gwc_ctx* c, int32_t K, const double* d_lambda, int32_t w
   double* tmp = nullptr;
   int32_t* fl = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  e = cudaMalloc(reinterpret_cast<void**>(&tmp), sizeof(double) * (2 * (size_t)K * ne + 3 * (size_t)K + (size_t)K * NP));
+  e = cudaMalloc(reinterpret_cast<void**>(&tmp), sizeof(double) * (2 * (size_t)K * ne + 3 * (size_t)K + (size_t)K * c->np));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&fl), sizeof(int32_t) * (size_t)K);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);

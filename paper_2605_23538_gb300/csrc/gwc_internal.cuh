@@ -21,15 +21,23 @@
 
 namespace gwc {
 
-constexpr int NP = 13;
+constexpr int NP = 13;               // hyperparameters of the power law + peak mass model
+constexpr int NP_MP = 16;            // of the multi-peak model
+constexpr int NP_MAX = 16;
+__host__ __device__ constexpr int n_params(bool mp) { return mp ? NP_MP : NP; }
 constexpr double C_KMS = 299792.458;
 constexpr int WARPS = 8;             // warps per CTA of the sample kernels
 constexpr int THREADS = WARPS * 32;
 constexpr int NW_WIN = 128;          // panels of the smoothing-window tables
-constexpr int PSTRIDE = 18;          // floats per partial sum: m, s1, s2, g[13], mO, sO
+constexpr int PSTRIDE = 21;          // floats per partial sum: m, s1, s2, g[16], mO, sO
+constexpr int PART_MO = 3 + NP_MAX, PART_SO = 4 + NP_MAX;   // where mO, sO sit
 constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the prologue
 
-enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP };
+// The multi-peak model appends the higher-mass Gaussian and the lower one's share of
+// the Gaussian fraction; (mu_g, sigma_g, lambda_peak) are then the low peak's
+// (mu_low, sigma_low) and lambda_g.
+enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP,
+       P_MU2, P_SIG2, P_LAM1 };
 
 // The sample kernels do not sum the 13 derivatives of ln w themselves but 13 weighted
 // statistics they are linear in; the FP64 merge applies the Lambda-only coefficients
@@ -43,9 +51,13 @@ enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_
 //   S_MMIN t (smoothing and C(m1) parts of d/dm_min)   S_DM  t d ln w / d delta_m
 //   S_MU   t pb zz                S_SIG t pb zz^2
 //   S_LU   t lu2                  S_SRD t sr (lu2 - log2(1+z_p))      S_SR  t sr
-enum { S_H0, S_OM, S_A1, S_LX, S_AL, S_BE, S_MMIN, S_DM, S_MU, S_SIG, S_LU, S_SRD, S_SR };
+// and for the multi-peak model (pb then being the low peak's responsibility, pb2 the
+// high peak's, zz2 = (m1s - mu2)/sig2):
+//   S_MU2  t pb2 zz2              S_SIG2 t pb2 zz2^2                  S_LX2 t pb2
+enum { S_H0, S_OM, S_A1, S_LX, S_AL, S_BE, S_MMIN, S_DM, S_MU, S_SIG, S_LU, S_SRD, S_SR,
+       S_MU2, S_SIG2, S_LX2 };
 
-// FP32 constants of one Lambda point for the sample kernels (52 floats = 13 float4).
+// FP32 constants of one Lambda point for the sample kernels (60 floats = 15 float4).
 // Fields ending in 2 are in log2 units (the value path works in log2 so that the
 // special-function unit's ex2/lg2 apply directly).
 struct __align__(16) LamF {
@@ -68,19 +80,26 @@ struct __align__(16) LamF {
   float inv_lam, inv_1ml, dm_l2, zstep_lo;   // dm log2(e) formed in FP64; z_max/(n_z-1) - zstep
   float alpha_lo, beta_lo, eps_b_lo, gpk_lo;   // alpha, beta, 1+beta, gamma+kappa less their
                                                // float values (they multiply logs of up to ~8)
+  float mu2, inv_sig2, lc2, pad0;         // multi-peak: the high peak, log2 of its weight
+                                          // lam (1-lam1)/(sig2 sqrt(2 pi) Z_G2) less R
 };
-static_assert(sizeof(LamF) == 56 * 4, "LamF layout");
+static_assert(sizeof(LamF) == 60 * 4, "LamF layout");
 
 // FP64 constants of one Lambda point for the merge: ln w = (per-sample term) + c.
 // lam_sigma = +1 at lambda_peak = 1, -1 at lambda_peak = 0, else 0 (see Acc).
 struct LamD {
   double c;
-  double dc[NP];
+  double dc[NP_MAX];
   int32_t flag;
   int32_t lam_sigma;
   // coefficients of stats_to_grad
   double invH0, dZPa, dZPmin, dZPmax, dZGmin, dZGmax, dZGmu, dZGsig;
   double inv_sig, inv_lam, inv_1ml, gpk_inv1zp;
+  // multi-peak (mp = 1): the high peak's d ln Z_G2 / d(m_min, m_max, mu2, sig2), 1/sig2,
+  // 1/lam1, 1/(1 - lam1); lam_bound = 1 when lam or lam1 sits at 0 or 1, where the
+  // multi-peak gradient leaves their two components undefined (NaN)
+  int32_t mp, lam_bound;
+  double dZG2min, dZG2max, dZG2mu, dZG2sig, inv_sig2, inv_lam1, inv_1ml1;
   // -ln N'_z and its gamma, kappa, z_p derivatives, written by a prologue CTA of their own
   double cz, dcz[3];
 };
@@ -91,10 +110,32 @@ __host__ __device__ inline double lamd_dc(const LamD& D, int i) {
   return D.dc[i] + (i == P_GAM ? D.dcz[0] : i == P_KAP ? D.dcz[1] : i == P_ZP ? D.dcz[2] : 0.0);
 }
 
-// The 13 derivative sums G (before division by the weight sum S1) from the statistics.
+// The derivative sums G (before division by the weight sum S1; 13, or 16 for the
+// multi-peak model) from the statistics.
 template <typename T>
 __host__ __device__ inline void stats_to_grad(const T* st, T S1, const LamD& D, T* G) {
   const T LN2 = (T)0.69314718055994530942;
+  if (D.mp) {
+    const T A1 = st[S_A1], B1 = st[S_LX], B2 = st[S_LX2];
+    G[P_H0] = (T)D.invH0 * st[S_H0];
+    G[P_OM] = st[S_OM];
+    G[P_ALPHA] = -LN2 * st[S_AL] - (T)D.dZPa * A1;
+    G[P_BETA] = st[S_BE];
+    G[P_MMIN] = st[S_MMIN] - (T)D.dZPmin * A1 - (T)D.dZGmin * B1 - (T)D.dZG2min * B2;
+    G[P_MMAX] = -(T)D.dZPmax * A1 - (T)D.dZGmax * B1 - (T)D.dZG2max * B2;
+    G[P_DM] = st[S_DM];
+    G[P_MU] = (T)D.inv_sig * st[S_MU] - (T)D.dZGmu * B1;
+    G[P_SIG] = (T)D.inv_sig * (st[S_SIG] - B1) - (T)D.dZGsig * B1;
+    G[P_MU2] = (T)D.inv_sig2 * st[S_MU2] - (T)D.dZG2mu * B2;
+    G[P_SIG2] = (T)D.inv_sig2 * (st[S_SIG2] - B2) - (T)D.dZG2sig * B2;
+    // d ln mix / d lam = (pb + pb2)/lam - pa/(1-lam); d / d lam1 = pb/lam1 - pb2/(1-lam1)
+    G[P_LAM] = D.lam_bound ? (T)NAN : (T)D.inv_lam * (B1 + B2) - (T)D.inv_1ml * A1;
+    G[P_LAM1] = D.lam_bound ? (T)NAN : (T)D.inv_lam1 * B1 - (T)D.inv_1ml1 * B2;
+    G[P_GAM] = LN2 * (st[S_LU] - st[S_SRD]);
+    G[P_KAP] = -LN2 * st[S_SRD];
+    G[P_ZP] = (T)D.gpk_inv1zp * st[S_SR];
+    return;
+  }
   T A1 = st[S_A1], B1 = st[S_LX];
   if (D.lam_sigma != 0) {          // one component only: pa, pb are 0 or 1
     A1 = D.lam_sigma < 0 ? S1 : (T)0;
@@ -231,8 +272,9 @@ constexpr float GRAD_SKIP = 48.f;
 
 // WITH_LOS = false leaves out the LOS factor (the weight w' of the KDE form, whose LOS
 // prior enters through the grid integral instead).  Every sample whose d_L maps into
-// [0, z_max] reports its z through sink.position(z), whatever its weight.
-template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true>
+// [0, z_max] reports its z through sink.position(z), whatever its weight.  MP selects
+// the multi-peak mass model (a second Gaussian in the primary-mass mixture).
+template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
                                            const float4* __restrict__ pos,
@@ -280,12 +322,26 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     if (!(plos > 0.f)) return false;
   }
 
-  // p(m1): (1-lam) m^-alpha / Z_P + lam N(m; mu, sig) / Z_G as max + log2(1 + e^-|a-b|)
+  // p(m1): (1-lam) m^-alpha / Z_P + lam N(m; mu, sig) / Z_G as max + log2(1 + e^-|a-b|);
+  // multi-peak: the three components' log2 weights a2, b2, c2 as max + log2 of the sum of
+  // their powers relative to it (mixf in [1, 3])
   const float a2 = fmaf(-L.alpha, lm1s2, fmaf(-L.alpha_lo, lm1s2, L.la2));
   const float zz = (m1s - L.mu) * L.inv_sig;
   const float b2 = fmaf(-HALF_LOG2EF * zz, zz, L.lb2);
-  const float mx = fmaxf(a2, b2);
-  const float eab = ex2(fminf(a2, b2) - mx);
+  float mx, eab = 0.f, mixf, zz2 = 0.f, ea = 0.f, eb = 0.f, ec = 0.f;
+  if (!MP) {
+    mx = fmaxf(a2, b2);
+    eab = ex2(fminf(a2, b2) - mx);
+    mixf = 1.f + eab;
+  } else {
+    zz2 = (m1s - L.mu2) * L.inv_sig2;
+    const float c2 = fmaf(-HALF_LOG2EF * zz2, zz2, L.lc2);
+    mx = fmaxf(fmaxf(a2, b2), c2);
+    ea = ex2(a2 - mx);
+    eb = ex2(b2 - mx);
+    ec = ex2(c2 - mx);
+    mixf = ea + eb + ec;
+  }
   float lin = mx;     // log2 terms outside the product
   float den;          // denominators of the product
 
@@ -346,16 +402,24 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float Dp = fmaf(x, ru, u * rE);
   den *= Dp * (1.f + er);
 
-  lw2 = fmaf(L.gam_m3, lu2, lin) + lg2_acc(plos * (1.f + eab) * rcp(den));
+  lw2 = fmaf(L.gam_m3, lu2, lin) + lg2_acc(plos * mixf * rcp(den));
   lw2 += s.npe2;
   if (!(lw2 > -INFINITY)) return false;
   const bool has_grad = sink.weight(lw2);
 
   if (GRAD && has_grad) {
     const float lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
-    const float inv1e = rcp(1.f + eab);
-    const float pa = a2 >= b2 ? inv1e : eab * inv1e;   // mixture responsibilities
-    const float pb = 1.f - pa;
+    float pa, pb, pb2 = 0.f;                           // mixture responsibilities
+    if (!MP) {
+      const float inv1e = rcp(mixf);
+      pa = a2 >= b2 ? inv1e : eab * inv1e;
+      pb = 1.f - pa;
+    } else {
+      const float inv = rcp(mixf);
+      pa = ea * inv;
+      pb = eb * inv;
+      pb2 = ec * inv;
+    }
     const float invr = rcp(1.f + er);
     const float sr = r2 >= 0.f ? invr : er * invr;     // sigmoid(r)
     const float invDp = rcp(Dp);
@@ -411,8 +475,8 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     }
     // total z-derivative of ln w at fixed detector-frame data
     float Gz = (p1 - p0) * L.inv_zstep * rcp(plos);
-    const float inner = L.gam - 3.f - L.gpk * sr + fmaf(pa, L.alpha, pb * zz * m1s * L.inv_sig) -
-                        m2s * dS2_dm + Gc;
+    const float gpeak = MP ? fmaf(pb * zz, L.inv_sig, pb2 * zz2 * L.inv_sig2) * m1s : pb * zz * m1s * L.inv_sig;
+    const float inner = L.gam - 3.f - L.gpk * sr + fmaf(pa, L.alpha, gpeak) - m2s * dS2_dm + Gc;
     Gz = fmaf(inner, ru, Gz);
     const float D2 = fmaf(-1.5f * L.om * (u3m1 + 1.f), rE3, 2.f * rE);
     Gz = fmaf(-D2, invDp, Gz);
@@ -430,7 +494,13 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     const float pbz = pb * zz;
     sink.grad(S_MU, pbz);
     sink.grad(S_SIG, pbz * zz);
-    if (L.lam_edge == 0.f) {
+    if (MP) {
+      sink.grad(S_LX, pb);
+      const float pbz2 = pb2 * zz2;
+      sink.grad(S_MU2, pbz2);
+      sink.grad(S_SIG2, pbz2 * zz2);
+      sink.grad(S_LX2, pb2);
+    } else if (L.lam_edge == 0.f) {
       sink.grad(S_LX, pb);
     } else if (L.lam >= 1.f) {                                    // mix = G: 1 - P/G
       sink.lam_edge(1.f, lw2, fmaf(-L.alpha, lm1s2, L.la0_2) - b2);
@@ -445,12 +515,12 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
 }
 
 // Sink that folds a sample into the online (max, sums) accumulator
-template <bool GRAD, bool KAHAN> struct Acc;
-template <bool GRAD, bool KAHAN>
+template <bool GRAD, bool KAHAN, int NS = NP> struct Acc;
+template <bool GRAD, bool KAHAN, int NS = NP>
 struct AccSink {
-  Acc<GRAD, KAHAN>& a;
+  Acc<GRAD, KAHAN, NS>& a;
   float t = 0.f;
-  __device__ __forceinline__ explicit AccSink(Acc<GRAD, KAHAN>& acc) : a(acc) {}
+  __device__ __forceinline__ explicit AccSink(Acc<GRAD, KAHAN, NS>& acc) : a(acc) {}
   __device__ __forceinline__ bool weight(float lw) {
     t = a.take(lw);
     return GRAD && !(lw < a.m - GRAD_SKIP);
@@ -462,7 +532,7 @@ struct AccSink {
 
 // Sink that keeps one sample's value and derivatives (per-sample outputs)
 struct TermSink {
-  float g[NP];
+  float g[NP_MAX];
   float lo = 0.f;
   bool edge = false;
   __device__ __forceinline__ bool weight(float) { return true; }
@@ -477,15 +547,15 @@ struct TermSink {
 
 // Online (max, sum 2^(l-max), sum 2^(2(l-max)), sum 2^(l-max) dl) accumulator, l in
 // log2 units, plus (mO, sO) = (max, sum 2^(l + lo - mO)) of the other-component weights
-// at lambda_peak = 0 or 1 (zero otherwise).
-template <bool GRAD, bool KAHAN>
+// at lambda_peak = 0 or 1 (zero otherwise).  NS statistics (13, or 16 multi-peak).
+template <bool GRAD, bool KAHAN, int NS>
 struct Acc {
   float m = -INFINITY, s1 = 0.f, s2 = 0.f, c1 = 0.f, c2 = 0.f;
   float mO = -INFINITY, sO = 0.f;
-  float g[GRAD ? NP : 1];
+  float g[GRAD ? NS : 1];
   __device__ __forceinline__ Acc() {
 #pragma unroll
-    for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] = 0.f;
+    for (int i = 0; i < (GRAD ? NS : 1); ++i) g[i] = 0.f;
   }
   // add a sample of log2 weight lw to the value sums; returns its weight 2^(lw - m)
   // relative to the (possibly new) running maximum m, rescaling what is already summed
@@ -498,7 +568,7 @@ struct Acc {
       c2 *= sc * sc;
       if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) g[i] *= sc;
+        for (int i = 0; i < NS; ++i) g[i] *= sc;
       }
       m = lw;
       return 1.f;
@@ -537,7 +607,7 @@ struct Acc {
       s2 = s2 * sa * sa + os2 * sb * sb;
       if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) g[i] = g[i] * sa + og[i] * sb;
+        for (int i = 0; i < NS; ++i) g[i] = g[i] * sa + og[i] * sb;
       }
       m = M;
     }

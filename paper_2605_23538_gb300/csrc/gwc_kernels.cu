@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <type_traits>
 
 namespace gwc {
 
@@ -103,12 +104,30 @@ __device__ __forceinline__ void smooth_d(double mp, double dm, double& S, double
   dSddm = -S * oneS * dfddm;
 }
 
-__device__ bool lambda_ok(const double* L) {
-  for (int i = 0; i < NP; ++i)
+__device__ bool lambda_ok(const double* L, bool mp) {
+  for (int i = 0; i < n_params(mp); ++i)
     if (!isfinite(L[i])) return false;
-  return L[P_H0] > 0.0 && L[P_OM] >= 0.0 && L[P_OM] <= 1.0 && L[P_MMIN] > 0.0 &&
-         L[P_MMAX] > L[P_MMIN] && L[P_DM] >= 0.0 && L[P_MMIN] + L[P_DM] < L[P_MMAX] &&
-         L[P_SIG] > 0.0 && L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0 && L[P_ZP] > -1.0;
+  const bool base = L[P_H0] > 0.0 && L[P_OM] >= 0.0 && L[P_OM] <= 1.0 && L[P_MMIN] > 0.0 &&
+                    L[P_MMAX] > L[P_MMIN] && L[P_DM] >= 0.0 && L[P_MMIN] + L[P_DM] < L[P_MMAX] &&
+                    L[P_SIG] > 0.0 && L[P_LAM] >= 0.0 && L[P_LAM] <= 1.0 && L[P_ZP] > -1.0;
+  return base && (!mp || (L[P_SIG2] > 0.0 && L[P_LAM1] >= 0.0 && L[P_LAM1] <= 1.0));
+}
+
+// ln Z_G = ln of the mass of N(mu, sig) inside [mmin, mmax] (erfc forms without
+// cancellation on either side) and d ln Z_G / d(mu, sig, mmin, mmax) into out[0..4]
+__device__ void gauss_mass(double mu, double sig, double mmin, double mmax, double* out) {
+  const double A_ = (mmin - mu) / sig, B_ = (mmax - mu) / sig, r2 = 0.70710678118654752440;
+  double ZG;
+  if (A_ > 0.0) ZG = 0.5 * (erfc(A_ * r2) - erfc(B_ * r2));
+  else if (B_ < 0.0) ZG = 0.5 * (erfc(-B_ * r2) - erfc(-A_ * r2));
+  else ZG = 1.0 - 0.5 * (erfc(B_ * r2) + erfc(-A_ * r2));
+  const double phA = 0.39894228040143267794 * exp(-0.5 * A_ * A_);
+  const double phB = 0.39894228040143267794 * exp(-0.5 * B_ * B_);
+  out[0] = log(ZG);
+  out[1] = (phA - phB) / (sig * ZG);                // d ln Z_G / d mu
+  out[2] = (A_ * phA - B_ * phB) / (sig * ZG);      // d ln Z_G / d sigma
+  out[3] = -phA / (sig * ZG);                       // d ln Z_G / d m_min
+  out[4] = phB / (sig * ZG);                        // d ln Z_G / d m_max
 }
 
 // ---------------------------------------------------------------------- prologue
@@ -127,14 +146,15 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
 
   const int k = blockIdx.x, tid = threadIdx.x, part = blockIdx.y;
   if (k == 0 && part == 0 && tid == 0 && A.counter) *A.counter = 0;
-  const double* L = A.lam + (size_t)k * NP;
+  const bool mp = A.mp != 0;
+  const double* L = A.lam + (size_t)k * n_params(mp);
   LamF* lf = A.lf + k;
   LamD* ld = A.ld + k;
   float* tb = A.tables + (size_t)k * A.tstride;
   const int nx = A.nx, nz = A.nz;
   const double zmax = A.zmax;
 
-  if (!lambda_ok(L)) {
+  if (!lambda_ok(L, mp)) {
     if (tid == 0 && part == 1) {
       LamF f;
       memset(&f, 0, sizeof(f));
@@ -142,7 +162,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       *lf = f;
       ld->c = 0.0;
       ld->cz = 0.0;
-      for (int i = 0; i < NP; ++i) ld->dc[i] = 0.0;
+      for (int i = 0; i < NP_MAX; ++i) ld->dc[i] = 0.0;
+      ld->mp = mp ? 1 : 0;
+      ld->lam_bound = 0;
       for (int i = 0; i < 3; ++i) ld->dcz[i] = 0.0;
       ld->flag = 1;
       ld->lam_sigma = 0;
@@ -153,6 +175,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double mmin = L[P_MMIN], mmax = L[P_MMAX], dm = L[P_DM], mu = L[P_MU], sig = L[P_SIG];
   const double lam = L[P_LAM], gam = L[P_GAM], kap = L[P_KAP], zp = L[P_ZP];
   const double gpk = gam + kap, lp = log1p(zp);
+  // multi-peak: the high peak and the low peak's share (lam1 = 1 leaves one Gaussian)
+  const double mu2 = mp ? L[P_MU2] : 0.0, sig2 = mp ? L[P_SIG2] : 1.0, lam1 = mp ? L[P_LAM1] : 1.0;
 
   if (part == 2) {
     // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
@@ -274,8 +298,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   return;
   }   // part 0
 
-  // ---- (3) mass-model normalisations (Z_P on thread 0, Z_G on thread 32, so the two
-  //          serial chains run in different warps), broadcast through shared memory
+  // ---- (3) mass-model normalisations (Z_P on thread 0, Z_G on thread 32, Z_G2 on
+  //          thread 64, so the serial chains run in different warps), broadcast through
+  //          shared memory
   if (tid == 0) {
     // Z_P = int_{mmin}^{mmax} m^-alpha dm = e^{t a} (b - a) phi1(t (b - a)), t = 1 - alpha
     const double t = 1.0 - alpha, a = log(mmin), b = log(mmax), Lr = b - a, y = t * Lr;
@@ -287,30 +312,25 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     sc[2] = -exp(-alpha * a - lnZP);                 // d ln Z_P / d m_min
     sc[3] = exp(-alpha * b - lnZP);                  // d ln Z_P / d m_max
   } else if (tid == 32) {
-    // Z_G = Phi(B) - Phi(A)
-    const double A_ = (mmin - mu) / sig, B_ = (mmax - mu) / sig, r2 = 0.70710678118654752440;
-    double ZG;
-    if (A_ > 0.0) ZG = 0.5 * (erfc(A_ * r2) - erfc(B_ * r2));
-    else if (B_ < 0.0) ZG = 0.5 * (erfc(-B_ * r2) - erfc(-A_ * r2));
-    else ZG = 1.0 - 0.5 * (erfc(B_ * r2) + erfc(-A_ * r2));
-    const double phA = 0.39894228040143267794 * exp(-0.5 * A_ * A_);
-    const double phB = 0.39894228040143267794 * exp(-0.5 * B_ * B_);
-    sc[4] = log(ZG);
-    sc[5] = (phA - phB) / (sig * ZG);                // d ln Z_G / d mu
-    sc[6] = (A_ * phA - B_ * phB) / (sig * ZG);      // d ln Z_G / d sigma
-    sc[7] = -phA / (sig * ZG);                       // d ln Z_G / d m_min
-    sc[8] = phB / (sig * ZG);                        // d ln Z_G / d m_max
+    gauss_mass(mu, sig, mmin, mmax, sc + 4);         // Z_G = Phi(B) - Phi(A)
+  } else if (tid == 64 && mp) {
+    gauss_mass(mu2, sig2, mmin, mmax, sc + 9);
   }
   __syncthreads();
   const double lnZP = sc[0], dZPa = sc[1], dZPmin = sc[2], dZPmax = sc[3];
   const double lnZG = sc[4], dZGmu = sc[5], dZGsig = sc[6], dZGmin = sc[7], dZGmax = sc[8];
+  const double lnZG2 = mp ? sc[9] : 0.0, dZG2mu = mp ? sc[10] : 0.0, dZG2sig = mp ? sc[11] : 0.0;
+  const double dZG2min = mp ? sc[12] : 0.0, dZG2max = mp ? sc[13] : 0.0;
   const double lnsig2pi = log(sig) + 0.91893853320467274178;
+  const double lnsig2pi2 = log(sig2) + 0.91893853320467274178;
 
   // ---- (4) smoothing window [mmin, mmin + dm]: W = int h (1 - S), its derivatives,
   //          and the cumulative C-family integrals at the table nodes
   const double hw = dm / NW_WIN;
+  //          (multi-peak: the Gaussian part is lam1 G + (1 - lam1) G2, and four more sums
+  //          give the mu2, sig2, lam1 derivatives and the G2 part of the m_max one)
   double cum[4] = {0.0, 0.0, 0.0, 0.0};   // C, C_beta, J, K over this thread's panel
-  double wv[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double wv[13] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   static_assert(2 * NW_WIN <= PRO_THREADS, "two threads per window panel");
   if (tid < 2 * NW_WIN && dm > 0.0) {   // panel tid / 2, half of its nodes each
     const double ma = mmin + (tid >> 1) * hw;
@@ -327,20 +347,30 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       cum[3] += w * mb * dSddm;
       const double P = exp(-alpha * lm - lnZP);
       const double zg = (m - mu) / sig;
-      const double G = exp(-0.5 * zg * zg - lnsig2pi - lnZG);
-      const double h = (1.0 - lam) * P + lam * G;
+      const double G1 = exp(-0.5 * zg * zg - lnsig2pi - lnZG);
+      const double zg2 = (m - mu2) / sig2;
+      const double G2 = mp ? exp(-0.5 * zg2 * zg2 - lnsig2pi2 - lnZG2) : 0.0;
+      const double G = lam1 * G1, Gb = (1.0 - lam1) * G2;   // the two peaks' shares
+      const double h = (1.0 - lam) * P + lam * (G + Gb);
       wv[0] += w * h * oneS;
       wv[1] += w * (1.0 - lam) * P * (-lm - dZPa) * oneS;
-      wv[2] += w * (G - P) * oneS;
+      wv[2] += w * (G + Gb - P) * oneS;
       wv[3] += w * lam * G * (zg / sig - dZGmu) * oneS;
       wv[4] += w * lam * G * ((zg * zg - 1.0) / sig - dZGsig) * oneS;
       wv[5] += w * P * oneS;
       wv[6] += w * G * oneS;
-      wv[7] += w * ((1.0 - lam) * P * (-alpha / m - dZPmin) + lam * G * (-zg / sig - dZGmin)) * oneS;
+      wv[7] += w * ((1.0 - lam) * P * (-alpha / m - dZPmin) + lam * G * (-zg / sig - dZGmin) +
+                    lam * Gb * (-zg2 / sig2 - dZG2min)) * oneS;
       wv[8] += w * (-h * dSddm);
+      if (mp) {
+        wv[9] += w * lam * Gb * (zg2 / sig2 - dZG2mu) * oneS;
+        wv[10] += w * lam * Gb * ((zg2 * zg2 - 1.0) / sig2 - dZG2sig) * oneS;
+        wv[11] += w * lam * (G1 - G2) * oneS;
+        wv[12] += w * Gb * oneS;
+      }
     }
   }
-  block_sum<9>(wv, red);
+  block_sum<13>(wv, red);
   // each panel's sums to its even thread, then an inclusive scan: the even thread 2p
   // holds the cumulative integrals at node p + 1
   for (int i = 0; i < 4; ++i) {
@@ -352,8 +382,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double Zm1 = 1.0 - W;
   // d ln Z_m1 / d theta = -dW/d theta / Z_m1
   const double dWa = wv[1], dWl = wv[2], dWmu = wv[3], dWsig = wv[4];
-  const double dWmax = -(1.0 - lam) * dZPmax * wv[5] - lam * dZGmax * wv[6];
+  const double dWmax = -(1.0 - lam) * dZPmax * wv[5] - lam * dZGmax * wv[6] - lam * dZG2max * wv[12];
   const double dWmin = wv[7], dWdm = wv[8];
+  const double dWmu2 = wv[9], dWsig2 = wv[10], dWl1 = wv[11];
 
   // window tables at nodes m_k = mmin + k hw: with R_X = X / (m^beta S(m)),
   //   Q_C = R_C dm / m'^2, Q_beta = R_beta / R_C, Q_J = R_J / R_C, Q_K = R_K dm / m'
@@ -443,11 +474,17 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     // the two components' log2 normalisations, less an anchor R (log2 units) that c
     // carries in FP64: only their difference is rounded to FP32, so the rounding no
     // longer shifts every sample's weight by the same amount
+    // (multi-peak: the low peak carries lam lam1, the high one lam (1 - lam1))
     const double la2d = lam < 1.0 ? (log1p(-lam) - lnZP) * LOG2E : -INFINITY;
-    const double lb2d = lam > 0.0 ? (log(lam) - lnsig2pi - lnZG) * LOG2E : -INFINITY;
-    const double R = lam < 1.0 ? la2d : lb2d;
+    const double lb2d = lam > 0.0 && lam1 > 0.0 ? (log(lam * lam1) - lnsig2pi - lnZG) * LOG2E : -INFINITY;
+    const double lc2d = mp && lam > 0.0 && lam1 < 1.0 ? (log(lam) + log1p(-lam1) - lnsig2pi2 - lnZG2) * LOG2E
+                                                     : -INFINITY;
+    const double R = lam < 1.0 ? la2d : (lb2d > -INFINITY ? lb2d : lc2d);
     f.la2 = lam < 1.0 ? (float)(la2d - R) : -INFINITY;
-    f.lb2 = lam > 0.0 ? (float)(lb2d - R) : -INFINITY;
+    f.lb2 = lb2d > -INFINITY ? (float)(lb2d - R) : -INFINITY;
+    f.lc2 = lc2d > -INFINITY ? (float)(lc2d - R) : -INFINITY;
+    f.mu2 = (float)mu2;
+    f.inv_sig2 = (float)(1.0 / sig2);
     const bool small = fabs(eps) < 1e-3;
     const double mw1b = exp(eps * log(mw));
     f.beta_small = small ? 1.f : 0.f;
@@ -460,7 +497,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.inv_dm = dm > 0.0 ? (float)(1.0 / dm) : 0.f;
     f.invH0 = (float)(1.0 / H0);
     f.inv1zp = (float)(1.0 / (1.0 + zp));
-    f.lam_edge = (lam > 0.0 && lam < 1.0) ? 0.f : 1.f;
+    f.lam_edge = (mp || (lam > 0.0 && lam < 1.0)) ? 0.f : 1.f;
     f.lam = (float)lam;
     f.dZPa = (float)dZPa;
     f.dZPmin = (float)dZPmin;
@@ -480,8 +517,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     // c = -ln Z_m1 + ln(H0 / c) + R ln 2 (the anchor taken out of la2, lb2); -ln N'_z
     // and its derivatives are in cz, dcz
     ld->c = -log(Zm1) + log(H0 / C_KMS) + R * 0.69314718055994530942;
-    double dc[NP];
-    for (int i = 0; i < NP; ++i) dc[i] = 0.0;
+    double dc[NP_MAX];
+    for (int i = 0; i < NP_MAX; ++i) dc[i] = 0.0;
     const double iZ = 1.0 / Zm1;   // -d ln Z_m1 = dW / Z_m1
     dc[P_H0] = 1.0 / H0;
     dc[P_ALPHA] = dWa * iZ;
@@ -491,9 +528,23 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     dc[P_MU] = dWmu * iZ;
     dc[P_SIG] = dWsig * iZ;
     dc[P_LAM] = dWl * iZ;
-    for (int i = 0; i < NP; ++i) ld->dc[i] = dc[i];
+    if (mp) {
+      dc[P_MU2] = dWmu2 * iZ;
+      dc[P_SIG2] = dWsig2 * iZ;
+      dc[P_LAM1] = dWl1 * iZ;
+    }
+    for (int i = 0; i < NP_MAX; ++i) ld->dc[i] = dc[i];
     ld->flag = 0;
-    ld->lam_sigma = lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0);
+    ld->lam_sigma = mp ? 0 : (lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0));
+    ld->mp = mp ? 1 : 0;
+    ld->lam_bound = mp && !(lam > 0.0 && lam < 1.0 && lam1 > 0.0 && lam1 < 1.0) ? 1 : 0;
+    ld->dZG2min = dZG2min;
+    ld->dZG2max = dZG2max;
+    ld->dZG2mu = dZG2mu;
+    ld->dZG2sig = dZG2sig;
+    ld->inv_sig2 = 1.0 / sig2;
+    ld->inv_lam1 = lam1 > 0.0 ? 1.0 / lam1 : 0.0;
+    ld->inv_1ml1 = lam1 < 1.0 ? 1.0 / (1.0 - lam1) : 0.0;
     ld->invH0 = 1.0 / H0;
     ld->dZPa = dZPa;
     ld->dZPmin = dZPmin;
@@ -525,8 +576,10 @@ constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
 
 // One (item, Lambda-slab) unit: stage the item's samples, sweep them for the slab's
 // Lambda points, combine the warp groups' sums into the unit's partials.
-template <bool GRAD, bool KAHAN, typename RowT>
+template <bool GRAD, bool KAHAN, typename RowT, bool MP>
 __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* sm, int* s_next) {
+  constexpr int NS = n_params(MP);   // gradient statistics of the mass model
+  using Sink = AccSink<GRAD, KAHAN, NS>;
   const int CH = A.chunk;
   // staged samples: {m1, m2, d_L, -log2 pi}, {log2 m1, log2 m2}, pixel (3 loads a sample)
   float4* s_a = reinterpret_cast<float4*>(sm);
@@ -571,7 +624,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
   for (int kk = (G == 1) ? next_k(0) : gidx; kk < nk; kk = next_k(kk)) {
     const int k = k0 + kk;
     const LamF L = A.lf[k];
-    Acc<GRAD, KAHAN> acc;
+    Acc<GRAD, KAHAN, NS> acc;
     if (L.live != 0.f) {
       const float* tb = A.tables + (size_t)k * A.tstride;
       const float4* pos = reinterpret_cast<const float4*>(tb);
@@ -585,12 +638,12 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
         s.m1 = va.x; s.m2 = va.y; s.dl = va.z; s.npe2 = va.w;
         s.lm1 = vb.x; s.lm2 = vb.y;
         float lw;
-        AccSink<GRAD, KAHAN> sink(acc);
+        Sink sink(acc);
         if (inj)
-          sample_lnw<GRAD>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
+          sample_lnw<GRAD, float, Sink, true, MP>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
         else
-          sample_lnw<GRAD>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
-                           nz, pos, aux, nx, wv, ws, lw, sink);
+          sample_lnw<GRAD, RowT, Sink, true, MP>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
+                                                 nz, pos, aux, nx, wv, ws, lw, sink);
       }
       if (KAHAN) { acc.s1 -= acc.c1; acc.s2 -= acc.c2; }
     }
@@ -600,10 +653,10 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       const float om_ = __shfl_xor_sync(0xffffffffu, acc.m, o);
       const float o1 = __shfl_xor_sync(0xffffffffu, acc.s1, o);
       const float o2 = __shfl_xor_sync(0xffffffffu, acc.s2, o);
-      float og[GRAD ? NP : 1], omO = -INFINITY, osO = 0.f;
+      float og[GRAD ? NS : 1], omO = -INFINITY, osO = 0.f;
       if (GRAD) {
 #pragma unroll
-        for (int q = 0; q < NP; ++q) og[q] = __shfl_xor_sync(0xffffffffu, acc.g[q], o);
+        for (int q = 0; q < NS; ++q) og[q] = __shfl_xor_sync(0xffffffffu, acc.g[q], o);
         omO = __shfl_xor_sync(0xffffffffu, acc.mO, o);
         osO = __shfl_xor_sync(0xffffffffu, acc.sO, o);
       }
@@ -614,13 +667,13 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       slot[0] = acc.m;
       slot[1] = acc.s1;
       slot[2] = acc.s2;
-      slot[16] = acc.mO;
-      slot[17] = acc.sO;
+      slot[PART_MO] = acc.mO;
+      slot[PART_SO] = acc.sO;
     }
-    if (GRAD && lane < NP) {
+    if (GRAD && lane < NS) {
       float gv = 0.f;
 #pragma unroll
-      for (int q = 0; q < NP; ++q) gv = (lane == q) ? acc.g[q] : gv;
+      for (int q = 0; q < NS; ++q) gv = (lane == q) ? acc.g[q] : gv;
       slot[3 + lane] = gv;
     }
   }
@@ -631,7 +684,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     float M = -INFINITY;
     for (int w = 0; w < G; ++w) M = fmaxf(M, sl[w * PSTRIDE]);
     float* out = A.partials + ((size_t)(k0 + kk) * A.stride + A.slot0 + item) * PSTRIDE;
-    const int ncomp = GRAD ? 2 + NP : 2;   // s1, s2 (and g)
+    const int ncomp = GRAD ? 2 + NS : 2;   // s1, s2 (and g)
     if (lane < ncomp) {
       float acc = 0.f;
       if (M > -INFINITY) {
@@ -643,23 +696,23 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       out[1 + lane] = acc;
     }
     if (lane == 0) out[0] = M;
-    if (GRAD && lane == 15) {
+    if (GRAD && lane == ncomp) {   // the first lane past the sums
       float MO = -INFINITY;
-      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PSTRIDE + 16]);
+      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PSTRIDE + PART_MO]);
       float so = 0.f;
       if (MO > -INFINITY) {
         for (int w = 0; w < G; ++w) {
-          const float mo = sl[w * PSTRIDE + 16];
-          if (mo > -INFINITY) so = fmaf(sl[w * PSTRIDE + 17], ex2(mo - MO), so);
+          const float mo = sl[w * PSTRIDE + PART_MO];
+          if (mo > -INFINITY) so = fmaf(sl[w * PSTRIDE + PART_SO], ex2(mo - MO), so);
         }
       }
-      out[16] = MO;
-      out[17] = so;
+      out[PART_MO] = MO;
+      out[PART_SO] = so;
     }
   }
 }
 
-template <bool GRAD, bool KAHAN, typename RowT>
+template <bool GRAD, bool KAHAN, typename RowT, bool MP>
 __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fused(const __grid_constant__ FusedArgs A) {
   extern __shared__ __align__(16) float sm[];
   // persistent: each CTA takes (item, Lambda-slab) units from the counter until none
@@ -671,7 +724,7 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
     __syncthreads();
     const int unit = s_unit;
     if (unit >= n_units) break;
-    fused_unit<GRAD, KAHAN, RowT>(A, unit, sm, &s_next);
+    fused_unit<GRAD, KAHAN, RowT, MP>(A, unit, sm, &s_next);
     __syncthreads();   // the combine has read s_part before the next unit restages
   }
 }
@@ -698,6 +751,7 @@ struct KdeSink {
 };
 
 struct KdeCtx {
+  bool mp;            // multi-peak mass model
   const LamF& L;
   const float4* pos;
   const float4* aux;
@@ -715,8 +769,11 @@ __device__ __forceinline__ void kde_sample(const KdeCtx& C, const float4 v, cons
   s.lm1 = lm.x; s.lm2 = lm.y;
   KdeSink sk;
   float l = -INFINITY;
-  const bool ok = sample_lnw<false, float, KdeSink, false>(C.L, s, static_cast<const float*>(nullptr),
-                                                          C.nz, C.pos, C.aux, C.nx, C.wv, C.ws, l, sk);
+  const float* none = nullptr;
+  const bool ok = C.mp ? sample_lnw<false, float, KdeSink, false, true>(C.L, s, none, C.nz, C.pos, C.aux, C.nx,
+                                                                        C.wv, C.ws, l, sk)
+                       : sample_lnw<false, float, KdeSink, false, false>(C.L, s, none, C.nz, C.pos, C.aux, C.nx,
+                                                                         C.wv, C.ws, l, sk);
   z = sk.z;
   lw = ok ? l : -INFINITY;
 }
@@ -772,7 +829,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   const float4* pos = reinterpret_cast<const float4*>(tb);
   const float4* aux = reinterpret_cast<const float4*>(tb + 4 * A.nx);
   const float4* wv = reinterpret_cast<const float4*>(tb + 8 * A.nx);
-  const KdeCtx C{L, pos, aux, wv, wv + (NW_WIN + 1), A.nx, A.nz, A.lm + grp.begin};
+  const KdeCtx C{A.mp != 0, L, pos, aux, wv, wv + (NW_WIN + 1), A.nx, A.nz, A.lm + grp.begin};
   const float4* smp = A.smp + grp.begin;
   const int n = grp.count;
 
@@ -1060,8 +1117,8 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
       out[0] = m;
       out[1] = a;
       out[2] = b;
-      out[16] = -INFINITY;   // the plain path folds the lambda-edge term into its g
-      out[17] = 0.f;
+      out[PART_MO] = -INFINITY;   // the plain path folds the lambda-edge term into its g
+      out[PART_SO] = 0.f;
     }
   } else {
     float gs[NP];
@@ -1087,13 +1144,14 @@ constexpr double LN2D = 0.69314718055994530942;
 
 template <bool GRAD>
 __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
-  __shared__ double rs[8][2 + NP];
-  __shared__ double rsel[8][3 + NP];
+  __shared__ double rs[8][2 + NP_MAX];
+  __shared__ double rsel[8][3 + NP_MAX];
   __shared__ double rO[8][2];
   __shared__ int rfail[8];
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const LamD D = A.ld[k];
   const int ne = A.n_events;
+  const int NPK = n_params(A.mp != 0);   // gradient width of the mass model
   if (D.flag & 1) {
     for (int e = tid; e < ne; e += 256) {
       A.lnL_event[(size_t)k * ne + e] = -INFINITY;
@@ -1105,10 +1163,10 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       if (A.lnL_total) A.lnL_total[k] = -INFINITY;
       if (A.sum_events) A.sum_events[k] = -INFINITY;
       A.flags[k] = 1;
-      for (int i = 0; i < NP; ++i) {
-        if (GRAD && A.grad_total) A.grad_total[(size_t)k * NP + i] = 0.0;
-        if (GRAD && A.grad_events) A.grad_events[(size_t)k * NP + i] = 0.0;
-        if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NP + i] = 0.0;
+      for (int i = 0; i < NPK; ++i) {
+        if (GRAD && A.grad_total) A.grad_total[(size_t)k * NPK + i] = 0.0;
+        if (GRAD && A.grad_events) A.grad_events[(size_t)k * NPK + i] = 0.0;
+        if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NPK + i] = 0.0;
       }
     }
     return;
@@ -1117,16 +1175,16 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   const float* pk = A.partials + (size_t)k * A.n_items * P * PSTRIDE;
 
   // ---- events: thread-strided, each event merged in item order
-  double sumL = 0.0, cmp = 0.0, sg[NP];
-  for (int i = 0; i < NP; ++i) sg[i] = 0.0;
+  double sumL = 0.0, cmp = 0.0, sg[NP_MAX];
+  for (int i = 0; i < NPK; ++i) sg[i] = 0.0;
   int fail = 0;   // bit 0: an event below the N_eff threshold; bit 1: an event with no weight
   for (int e = tid; e < ne; e += 256) {
     const int s0 = A.ev_item0[e] * P, s1 = A.ev_item0[e + 1] * P;
     double M = -INFINITY;
     for (int s = s0; s < s1; ++s) M = fmax(M, (double)pk[(size_t)s * PSTRIDE]);
-    double S1 = 0.0, S2 = 0.0, G[GRAD ? NP : 1];
+    double S1 = 0.0, S2 = 0.0, G[GRAD ? NP_MAX : 1];
     if (GRAD)
-      for (int i = 0; i < NP; ++i) G[i] = 0.0;
+      for (int i = 0; i < NPK; ++i) G[i] = 0.0;
     if (M > -INFINITY) {
       for (int s = s0; s < s1; ++s) {
         const float* p = pk + (size_t)s * PSTRIDE;
@@ -1135,17 +1193,17 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         S1 += (double)p[1] * r;
         S2 += (double)p[2] * r * r;
         if (GRAD)
-          for (int i = 0; i < NP; ++i) G[i] += (double)p[3 + i] * r;
+          for (int i = 0; i < NPK; ++i) G[i] += (double)p[3 + i] * r;
       }
       if (GRAD) {
-        double st[NP];
-        for (int i = 0; i < NP; ++i) st[i] = G[i];
+        double st[NP_MAX];
+        for (int i = 0; i < NPK; ++i) st[i] = G[i];
         stats_to_grad(st, S1, D, G);
       }
       if (GRAD && D.lam_sigma != 0)   // other-component sums at lambda_peak = 0 or 1
         for (int s = s0; s < s1; ++s) {
           const float* p = pk + (size_t)s * PSTRIDE;
-          if (p[16] > -INFINITY) G[P_LAM] -= D.lam_sigma * (double)p[17] * exp2((double)p[16] - M);
+          if (p[PART_MO] > -INFINITY) G[P_LAM] -= D.lam_sigma * (double)p[PART_SO] * exp2((double)p[PART_MO] - M);
         }
     }
     double lnL = -INFINITY, neff = 0.0;
@@ -1153,7 +1211,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       lnL = M * LN2D + log(S1) - log(A.ev_n[e]) + lamd_c(D);
       neff = S1 * S1 / S2;
       if (GRAD)
-        for (int i = 0; i < NP; ++i) sg[i] += G[i] / S1 + lamd_dc(D, i);
+        for (int i = 0; i < NPK; ++i) sg[i] += G[i] / S1 + lamd_dc(D, i);
     }
     A.lnL_event[(size_t)k * ne + e] = lnL;
     A.neff_event[(size_t)k * ne + e] = neff;
@@ -1169,16 +1227,16 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   }
 
   // ---- injections: online merge of the injection partials
-  double sM = -INFINITY, sS1 = 0.0, sS2 = 0.0, sG[GRAD ? NP : 1];
+  double sM = -INFINITY, sS1 = 0.0, sS2 = 0.0, sG[GRAD ? NP_MAX : 1];
   double oM = -INFINITY, oS = 0.0;   // other-component pair at lambda_peak = 0 or 1
   if (GRAD)
-    for (int i = 0; i < NP; ++i) sG[i] = 0.0;
+    for (int i = 0; i < NPK; ++i) sG[i] = 0.0;
   for (int s = A.inj_item0 * P + tid; s < A.n_items * P; s += 256) {
     const float* p = pk + (size_t)s * PSTRIDE;
-    if (GRAD && D.lam_sigma != 0 && p[16] > -INFINITY) {
-      const double mo = p[16];
-      if (mo > oM) { oS = oS * exp2(oM - mo) + (double)p[17]; oM = mo; }
-      else oS += (double)p[17] * exp2(mo - oM);
+    if (GRAD && D.lam_sigma != 0 && p[PART_MO] > -INFINITY) {
+      const double mo = p[PART_MO];
+      if (mo > oM) { oS = oS * exp2(oM - mo) + (double)p[PART_SO]; oM = mo; }
+      else oS += (double)p[PART_SO] * exp2(mo - oM);
     }
     const double m = p[0];
     if (!(m > -INFINITY)) continue;
@@ -1187,14 +1245,14 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       sS1 *= r;
       sS2 *= r * r;
       if (GRAD)
-        for (int i = 0; i < NP; ++i) sG[i] *= r;
+        for (int i = 0; i < NPK; ++i) sG[i] *= r;
       sM = m;
     }
     const double r = exp2(m - sM);
     sS1 += (double)p[1] * r;
     sS2 += (double)p[2] * r * r;
     if (GRAD)
-      for (int i = 0; i < NP; ++i) sG[i] += (double)p[3 + i] * r;
+      for (int i = 0; i < NPK; ++i) sG[i] += (double)p[3 + i] * r;
   }
 
   // ---- fixed-order reductions: butterfly within warps, then warps in order
@@ -1209,27 +1267,27 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     sumL += __shfl_xor_sync(0xffffffffu, sumL, o);
     fail |= __shfl_xor_sync(0xffffffffu, fail, o);
     if (GRAD)
-      for (int i = 0; i < NP; ++i) sg[i] += __shfl_xor_sync(0xffffffffu, sg[i], o);
+      for (int i = 0; i < NPK; ++i) sg[i] += __shfl_xor_sync(0xffffffffu, sg[i], o);
     const double oM = __shfl_xor_sync(0xffffffffu, sM, o);
     const double o1 = __shfl_xor_sync(0xffffffffu, sS1, o);
     const double o2 = __shfl_xor_sync(0xffffffffu, sS2, o);
-    double oG[GRAD ? NP : 1];
+    double oG[GRAD ? NP_MAX : 1];
     if (GRAD)
-      for (int i = 0; i < NP; ++i) oG[i] = __shfl_xor_sync(0xffffffffu, sG[i], o);
+      for (int i = 0; i < NPK; ++i) oG[i] = __shfl_xor_sync(0xffffffffu, sG[i], o);
     const double M = fmax(sM, oM);
     if (M > -INFINITY) {
       const double ra = exp2(sM - M), rb = exp2(oM - M);
       sS1 = sS1 * ra + o1 * rb;
       sS2 = sS2 * ra * ra + o2 * rb * rb;
       if (GRAD)
-        for (int i = 0; i < NP; ++i) sG[i] = sG[i] * ra + oG[i] * rb;
+        for (int i = 0; i < NPK; ++i) sG[i] = sG[i] * ra + oG[i] * rb;
       sM = M;
     }
   }
   if (lane == 0) {
     rs[w][0] = sumL;
     if (GRAD)
-      for (int i = 0; i < NP; ++i) rs[w][2 + i] = sg[i];
+      for (int i = 0; i < NPK; ++i) rs[w][2 + i] = sg[i];
     rfail[w] = fail;
     rsel[w][0] = sM;
     rsel[w][1] = sS1;
@@ -1237,18 +1295,18 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     rO[w][0] = oM;
     rO[w][1] = oS;
     if (GRAD)
-      for (int i = 0; i < NP; ++i) rsel[w][3 + i] = sG[i];
+      for (int i = 0; i < NPK; ++i) rsel[w][3 + i] = sG[i];
   }
   __syncthreads();
   if (tid == 0) {
-    double tot = 0.0, gt[NP], M = -INFINITY, S1 = 0.0, S2 = 0.0, G[NP];
+    double tot = 0.0, gt[NP_MAX], M = -INFINITY, S1 = 0.0, S2 = 0.0, G[NP_MAX];
     int fl = 0;
-    for (int i = 0; i < NP; ++i) { gt[i] = 0.0; G[i] = 0.0; }
+    for (int i = 0; i < NPK; ++i) { gt[i] = 0.0; G[i] = 0.0; }
     for (int q = 0; q < 8; ++q) {
       tot += rs[q][0];
       fl |= rfail[q];
       if (GRAD)
-        for (int i = 0; i < NP; ++i) gt[i] += rs[q][2 + i];
+        for (int i = 0; i < NPK; ++i) gt[i] += rs[q][2 + i];
       M = fmax(M, rsel[q][0]);
     }
     if (M > -INFINITY) {
@@ -1258,11 +1316,11 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         S1 += rsel[q][1] * r;
         S2 += rsel[q][2] * r * r;
         if (GRAD)
-          for (int i = 0; i < NP; ++i) G[i] += rsel[q][3 + i] * r;
+          for (int i = 0; i < NPK; ++i) G[i] += rsel[q][3 + i] * r;
       }
       if (GRAD) {
-        double st[NP];
-        for (int i = 0; i < NP; ++i) st[i] = G[i];
+        double st[NP_MAX];
+        for (int i = 0; i < NPK; ++i) st[i] = G[i];
         stats_to_grad(st, S1, D, G);
       }
       if (GRAD && D.lam_sigma != 0)
@@ -1284,24 +1342,25 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     A.flags[k] = flag;
     if (A.lnL_total) A.lnL_total[k] = (flag || dead) ? -INFINITY : tot - (double)ne * lnxi;
     if (GRAD && A.grad_total)
-      for (int i = 0; i < NP; ++i)
-        A.grad_total[(size_t)k * NP + i] =
+      for (int i = 0; i < NPK; ++i)
+        A.grad_total[(size_t)k * NPK + i] =
             (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + lamd_dc(D, i));
     if (A.sum_events) A.sum_events[k] = dead ? -INFINITY : tot;
-    for (int i = 0; i < NP; ++i) {
-      if (GRAD && A.grad_events) A.grad_events[(size_t)k * NP + i] = dead ? 0.0 : gt[i];
-      if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NP + i] = S1 > 0.0 ? G[i] / S1 + lamd_dc(D, i) : 0.0;
+    for (int i = 0; i < NPK; ++i) {
+      if (GRAD && A.grad_events) A.grad_events[(size_t)k * NPK + i] = dead ? 0.0 : gt[i];
+      if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NPK + i] = S1 > 0.0 ? G[i] / S1 + lamd_dc(D, i) : 0.0;
     }
   }
 }
 
 // --------------------------------------------------------- per-sample terms (tests)
-template <typename RowT>
+template <typename RowT, bool MP>
 __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
+  constexpr int NS = n_params(MP);
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     A.c[0] = lamd_c(*A.ld);
-    for (int q = 0; q < NP; ++q) A.c[1 + q] = lamd_dc(*A.ld, q);
+    for (int q = 0; q < NS; ++q) A.c[1 + q] = lamd_dc(*A.ld, q);
   }
   if (i >= A.n_total) return;
   const LamF L = A.lf[0];
@@ -1321,25 +1380,31 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
   bool ok = false;
   if (L.live != 0.f) {
     if (inj)
-      ok = sample_lnw<true>(L, s, A.pbar32, A.nz, pos, aux, nx, wv, ws, lw, ts);
+      ok = sample_lnw<true, float, TermSink, true, MP>(L, s, A.pbar32, A.nz, pos, aux, nx, wv, ws, lw, ts);
     else
-      ok = sample_lnw<true>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz,
-                            A.nz, pos, aux, nx, wv, ws, lw, ts);
+      ok = sample_lnw<true, RowT, TermSink, true, MP>(
+          L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz, A.nz, pos, aux, nx,
+          wv, ws, lw, ts);
   }
   A.lnw[i] = ok ? lw * LN2F : -INFINITY;
   if (A.dlnw) {
-    double st[NP], G[NP];
-    for (int q = 0; q < NP; ++q) st[q] = ok ? (double)ts.g[q] : 0.0;
+    double st[NP_MAX], G[NP_MAX];
+    for (int q = 0; q < NS; ++q) st[q] = ok ? (double)ts.g[q] : 0.0;
     stats_to_grad(st, ok ? 1.0 : 0.0, *A.ld, G);
     if (ok && ts.edge) G[P_LAM] *= 1.0 - exp2((double)ts.lo);   // sigma (1 - O/mix): may overflow
-    for (int q = 0; q < NP; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? (float)G[q] : 0.f;
+    for (int q = 0; q < NS; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? (float)G[q] : 0.f;
   }
 }
 
 cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s) {
   const int grid = (int)std::max(1LL, (a.n_total + 255) / 256);
-  if (bf16) k_sample_terms<__nv_bfloat16><<<grid, 256, 0, s>>>(a);
-  else k_sample_terms<float><<<grid, 256, 0, s>>>(a);
+  if (a.mp) {
+    if (bf16) k_sample_terms<__nv_bfloat16, true><<<grid, 256, 0, s>>>(a);
+    else k_sample_terms<float, true><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (bf16) k_sample_terms<__nv_bfloat16, false><<<grid, 256, 0, s>>>(a);
+    else k_sample_terms<float, false><<<grid, 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -1368,22 +1433,48 @@ cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool G, bool KH, typename RT>
+template <bool G, bool KH, typename RT, bool MP>
 static cudaError_t launch_fused_t(const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_fused<G, KH, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fused<G, KH, RT, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fused_smem_max());
   if (e != cudaSuccess) return e;
-  k_fused<G, KH, RT><<<grid, THREADS, smem, s>>>(a);
+  k_fused<G, KH, RT, MP><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool G, bool KH, typename RT>
+template <bool G, bool KH, typename RT, bool MP>
 static cudaError_t occupancy_t(size_t smem, int* out) {
-  cudaError_t e = cudaFuncSetAttribute(k_fused<G, KH, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fused<G, KH, RT, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fused_smem_max());
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_fused<G, KH, RT>, THREADS, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_fused<G, KH, RT, MP>, THREADS, smem);
 }
+
+// the instance for (gradient, compensated sums, bf16 LOS rows, multi-peak)
+template <template <bool, bool, typename, bool> class F, typename... Args>
+static cudaError_t fused_dispatch(bool grad, bool kahan, bool bf16, bool mp, Args... args) {
+#define GWC_FUSED_CASE(G_, K_, B_, M_)                                                           \
+  if (grad == G_ && kahan == K_ && bf16 == B_ && mp == M_)                                      \
+    return F<G_, K_, std::conditional_t<B_, __nv_bfloat16, float>, M_>::run(args...);
+  GWC_FUSED_CASE(true, false, false, false) GWC_FUSED_CASE(true, true, false, false)
+  GWC_FUSED_CASE(true, false, true, false) GWC_FUSED_CASE(true, true, true, false)
+  GWC_FUSED_CASE(false, false, false, false) GWC_FUSED_CASE(false, true, false, false)
+  GWC_FUSED_CASE(false, false, true, false) GWC_FUSED_CASE(false, true, true, false)
+  GWC_FUSED_CASE(true, false, false, true) GWC_FUSED_CASE(true, true, false, true)
+  GWC_FUSED_CASE(true, false, true, true) GWC_FUSED_CASE(true, true, true, true)
+  GWC_FUSED_CASE(false, false, false, true) GWC_FUSED_CASE(false, true, false, true)
+  GWC_FUSED_CASE(false, false, true, true) GWC_FUSED_CASE(false, true, true, true)
+#undef GWC_FUSED_CASE
+  return cudaErrorInvalidValue;
+}
+template <bool G, bool KH, typename RT, bool MP> struct FusedLaunch {
+  static cudaError_t run(const FusedArgs& a, int grid, size_t smem, cudaStream_t s) {
+    return launch_fused_t<G, KH, RT, MP>(a, grid, smem, s);
+  }
+};
+template <bool G, bool KH, typename RT, bool MP> struct FusedOccupancy {
+  static cudaError_t run(size_t smem, int* out) { return occupancy_t<G, KH, RT, MP>(smem, out); }
+};
 
 size_t fused_smem_bytes(int chunk, int slab, int group) {
   return (size_t)chunk * 7 * sizeof(float) + (size_t)slab * group * PSTRIDE * sizeof(float);
@@ -1392,33 +1483,19 @@ size_t fused_smem_max() { return fused_smem_bytes(4096, MAX_SLAB, WARPS); }
 
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s) {
   const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
-  if (grad) {
-    if (kahan) return bf16 ? launch_fused_t<true, true, __nv_bfloat16>(a, grid, smem, s)
-                           : launch_fused_t<true, true, float>(a, grid, smem, s);
-    return bf16 ? launch_fused_t<true, false, __nv_bfloat16>(a, grid, smem, s)
-                : launch_fused_t<true, false, float>(a, grid, smem, s);
-  }
-  if (kahan) return bf16 ? launch_fused_t<false, true, __nv_bfloat16>(a, grid, smem, s)
-                         : launch_fused_t<false, true, float>(a, grid, smem, s);
-  return bf16 ? launch_fused_t<false, false, __nv_bfloat16>(a, grid, smem, s)
-              : launch_fused_t<false, false, float>(a, grid, smem, s);
+  return fused_dispatch<FusedLaunch>(grad, kahan, bf16, a.mp != 0, a, grid, smem, s);
 }
 
 cudaError_t fused_blocks_per_sm(const FusedArgs& a, bool grad, bool kahan, bool bf16, int* out) {
   const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
-  if (grad) {
-    if (kahan) return bf16 ? occupancy_t<true, true, __nv_bfloat16>(smem, out) : occupancy_t<true, true, float>(smem, out);
-    return bf16 ? occupancy_t<true, false, __nv_bfloat16>(smem, out) : occupancy_t<true, false, float>(smem, out);
-  }
-  if (kahan) return bf16 ? occupancy_t<false, true, __nv_bfloat16>(smem, out) : occupancy_t<false, true, float>(smem, out);
-  return bf16 ? occupancy_t<false, false, __nv_bfloat16>(smem, out) : occupancy_t<false, false, float>(smem, out);
+  return fused_dispatch<FusedOccupancy>(grad, kahan, bf16, a.mp != 0, smem, out);
 }
 
 // ------------------------------------------------------------------ HMC leapfrog
 __global__ void __launch_bounds__(32) k_hmc(HmcArgs A) {
   const int k = blockIdx.x, i = threadIdx.x;
-  const bool on = i < NP;
-  const size_t o = (size_t)k * NP + (on ? i : 0);
+  const bool on = i < A.np;
+  const size_t o = (size_t)k * A.np + (on ? i : 0);
   if (A.mode == 0) {
     if (on) A.q0[o] = A.q[o];
     if (i == 0) A.div[k] = 0;

@@ -11,7 +11,8 @@
 namespace gwc {
 
 struct ProArgs {
-  const double* lam;      // [K][13]
+  const double* lam;      // [K][13], or [K][16] for the multi-peak model
+  int mp = 0;             // mass model: 0 power law + peak, 1 multi-peak
   int nx;                 // nodes of the inversion table
   int nz;                 // LOS grid nodes
   double zmax;
@@ -48,6 +49,7 @@ struct FusedArgs {
   int n_sched;            // schedule entries (units = n_sched * n_slabs)
   int stride;             // partial slots per Lambda
   int slot0;              // slot of item 0
+  int mp = 0;             // multi-peak mass model
 };
 
 // KDE form of the event term: one (event, pixel) group of samples
@@ -74,6 +76,7 @@ struct KdeArgs {
   int tstride;
   float* partials;        // [K][stride][PSTRIDE], slot = group index
   int stride;
+  int mp = 0;             // multi-peak mass model
 };
 cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s);
 cudaError_t launch_log2_masses(const float4* smp, long long n, float2* out, cudaStream_t s);
@@ -103,6 +106,7 @@ struct PlainArgs {
 };
 
 struct MergeArgs {
+  int mp = 0;               // multi-peak mass model: 16 gradient components, else 13
   const float* partials;
   int n_items;
   int P;
@@ -122,7 +126,7 @@ struct MergeArgs {
   int32_t* flags;
   double* grad_total;
   // optional parts for merging shards of a catalogue (may be null): sum_i ln L_i [K],
-  // its gradient [K][13], and the gradient of ln xi [K][13]
+  // its gradient [K][P], and the gradient of ln xi [K][P] (P = 13, or 16 multi-peak)
   double* sum_events = nullptr;
   double* grad_events = nullptr;
   double* grad_ln_xi = nullptr;
@@ -135,22 +139,23 @@ struct MergeArgs {
 struct HmcArgs {
   int K;
   int mode;
+  int np;                   // parameters per chain (13, or 16 multi-peak): P below
   const double* eps;        // [K] step sizes
-  const double* inv_mass;   // [13] diagonal inverse mass
-  double* q;                // [K][13] position (in/out)
-  double* p;                // [K][13] momentum (in/out)
-  double* q0;               // [K][13] scratch
+  const double* inv_mass;   // [P] diagonal inverse mass
+  double* q;                // [K][P] position (in/out)
+  double* p;                // [K][P] momentum (in/out)
+  double* q0;               // [K][P] scratch
   double* lnL0;             // [K] scratch
-  double* grad0;            // [K][13] scratch
+  double* grad0;            // [K][P] scratch
   int32_t* div;             // [K] scratch: the chain met a flagged (invalid) point
   const double* lnL;        // [K] the last evaluation
-  const double* grad;       // [K][13]
+  const double* grad;       // [K][P]
   const int32_t* flags;     // [K]
   const double* log_u;      // [K] log of a uniform(0, 1) number per chain
   double* H;                // [K][2] Hamiltonian at the start and the end
   int32_t* accept;          // [K]
   double* lnL_out;          // [K] log-likelihood at the returned position
-  double* grad_out;         // [K][13]
+  double* grad_out;         // [K][P]
 };
 cudaError_t launch_hmc(const HmcArgs& a, cudaStream_t s);
 
@@ -179,8 +184,9 @@ struct TermsArgs {
   const LamD* ld;
   const float* tables;
   float* lnw;       // [n_total]
-  float* dlnw;      // [13][n_total] or nullptr
-  double* c;        // [14]
+  float* dlnw;      // [P][n_total] or nullptr (P = 13, or 16 multi-peak)
+  double* c;        // [1 + P]
+  int mp = 0;       // multi-peak mass model
 };
 cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s);
 // the calling thread's message for gwc_last_error(NULL) (defined with the C ABI)

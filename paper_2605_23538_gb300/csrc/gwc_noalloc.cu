@@ -34,7 +34,7 @@ constexpr int MAX_DEVICES = 64;
 // scratch layout (bytes): LamF | LamD | per-Lambda tables | pixel mean (float) | (double)
 constexpr size_t OFF_LF = 0;
 constexpr size_t OFF_LD = 256;
-constexpr size_t OFF_TB = 512;
+constexpr size_t OFF_TB = 768;
 constexpr size_t TB_BYTES = ((size_t)table_floats(MAX_NX) + 3) / 4 * 4 * sizeof(float);
 constexpr size_t OFF_P32 = OFF_TB + (TB_BYTES + 255) / 256 * 256;
 constexpr size_t OFF_P64 = OFF_P32 + (MAX_NZ * sizeof(float) + 255) / 256 * 256;

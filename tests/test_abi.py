@@ -35,23 +35,42 @@ def test_exports_every_declared_function(g):
     assert sorted(g.EXPORTS) == declared
 
 
-def test_struct_sizes_match_header(g):
+STRUCTS = {"Events": "gwc_events", "Los": "gwc_los", "Injections": "gwc_injections",
+           "Options": "gwc_options", "Info": "gwc_info", "TuneResult": "gwc_tune_result",
+           "KdeOptions": "gwc_kde_options"}
+
+
+def test_struct_layouts_match_the_compiled_header(g, tmp_path):
+    # a C program compiled against include/gwc.h prints each struct's size and the offset
+    # of every field the binding declares; the ctypes layouts must agree exactly
     import ctypes
-    # sizes from the header's field lists (x86-64 / aarch64 LP64 ABI)
-    assert ctypes.sizeof(g.Events) == 56
-    assert ctypes.sizeof(g.Los) == 32
-    assert ctypes.sizeof(g.Injections) == 48
-    assert ctypes.sizeof(g.Options) == 56
-    assert ctypes.sizeof(g.Info) == 56
-    assert ctypes.sizeof(g.TuneResult) == 24
-    assert ctypes.sizeof(g.KdeOptions) == 16
+    import subprocess
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gwc.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        cls = getattr(g, py)
+        lines.append(f'  printf("{py} size %zu\\n", sizeof({c}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{py} {f} %zu\\n", offsetof({c}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_side = {(a, b): int(n) for a, b, n in (ln.split() for ln in got if ln.strip())}
+    for py in STRUCTS:
+        cls = getattr(g, py)
+        assert c_side[(py, "size")] == ctypes.sizeof(cls), py
+        for f, _ in cls._fields_:
+            assert c_side[(py, f)] == getattr(cls, f).offset, (py, f)
 
 
 def test_defaults(g):
     o = g.default_options()
     assert (o.neff_min_event, o.neff_min_sel, o.accum, o.los_dtype) == (2.0, 0.0, 0, 0)
     assert (o.n_x_table, o.max_K, o.chunk, o.lambda_tile, o.lambda_group) == (512, 256, 2048, 0, 0)
-    assert (o.cap_per_pixel, o.cap_seed) == (0, 0)
+    assert (o.cap_per_pixel, o.cap_seed, o.mass_model) == (0, 0, g.MASS_PLP)
+    assert g.default_options(mass_model="multipeak").mass_model == g.MASS_MULTIPEAK
 
 
 def test_invalid_inputs_rejected_before_any_device_work(g, synth):
