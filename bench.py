@@ -255,6 +255,27 @@ def kde_timing(g, ctx, lam, n_evals, stream):
             "value": n_evals * k / (ms / 1e3), "unit": "evals/s (value only)"}
 
 
+def multipeak_timing(g, synth, cat, K, n_evals, stream, steps=3):
+    """The multi-peak mass model (16-entry Lambda) on the same catalogue: value+gradient
+    calls at K points drawn around the paper's Table 2 values, default launch shape."""
+    import torch
+    lam = torch.tensor(synth.lambda_batch(K, purpose=4, model="multipeak"), device="cuda")
+    with g.Context(cat, max_K=K, mass_model="multipeak") as ctx:
+        out = g._outputs(K, ctx.n_events, lam.device, True, lam.shape[1])
+        for _ in range(2):
+            g.loglik_grad(ctx._ctx, lam, ctx.n_events, stream, out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            g.loglik_grad(ctx._ctx, lam, ctx.n_events, stream, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    return {"K": K, "n_params": 16, "ms_per_call": ms, "value": n_evals * K / (ms / 1e3),
+            "unit": "evals/s (value+gradient)"}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, one bounded sample per step."""
     world, rank, _ = dist_setup()
@@ -432,10 +453,11 @@ def main():
                "h2d_bytes_per_step": K * 13 * 8,
                "d2h_bytes_per_step": K * 8 + K * 4 + K * 13 * 8}
 
-    kde_line = None
+    kde_line = mp_line = None
     if not args.no_extras:
         hmc_line = hmc_c1(g, synth, stream)
         kde_line = kde_timing(g, ctx, lam, n_s + n_i, stream)
+        mp_line = multipeak_timing(g, synth, cat, K, n_s + n_i, stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
@@ -475,6 +497,7 @@ def main():
             line["graph"] = graph_line
             line["hmc_c1"] = hmc_line
             line["kde"] = kde_line
+            line["multipeak"] = mp_line
         if clocks is not None:
             line["clocks"] = clocks
         if base is not None:
