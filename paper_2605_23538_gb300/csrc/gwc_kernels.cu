@@ -20,6 +20,8 @@
 #include <cfloat>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 namespace gwc {
 
 __constant__ double c_glx[NGL];   // Gauss-Legendre nodes on [-1, 1]
@@ -134,18 +136,83 @@ __device__ void gauss_mass(double mu, double sig, double mmin, double mmax, doub
 constexpr int PRO_THREADS = 256;
 constexpr int ZPANELS = 256;   // panels of the z quadrature (one per thread)
 
-// Three CTAs per Lambda point (blockIdx.y), run side by side: part 0 builds the d_L -> z
-// inversion table, part 1 the smoothing-window tables, the mass normalisations and the
-// constants, part 2 the redshift normalisation N'_z.  Parts 0 and 1 both need step (1),
-// which each computes.
+// (1) I(z) and J(z) = dI/dOm on the ZPANELS + 1 panel edges of [0, zmax] (an 8-point
+// Gauss-Legendre rule per panel, one panel per thread, then a block scan), and D(z),
+// D'(z) = I + (1+z)/E there.
+__device__ void z_panels(double om, double zmax, double* sI, double* sJ, double* sD, double* sDp,
+                         double* red) {
+  const int tid = threadIdx.x;
+  const double hz = zmax / ZPANELS;
+  double v[2] = {0.0, 0.0};
+  const double za = tid * hz;
+  for (int q = 0; q < NGL; ++q) {
+    const double zq = za + 0.5 * hz * (1.0 + c_glx[q]);
+    const double u3m1 = zq * (3.0 + zq * (3.0 + zq));   // (1+z)^3 - 1
+    const double iE = rsqrt(om * u3m1 + 1.0);            // 1/E
+    v[0] += c_glw[q] * iE;
+    v[1] += c_glw[q] * (-0.5 * u3m1 * (iE * iE * iE));
+  }
+  v[0] *= 0.5 * hz;
+  v[1] *= 0.5 * hz;
+  block_scan<2>(v, red);
+  sI[tid + 1] = v[0];
+  sJ[tid + 1] = v[1];
+  if (tid == 0) { sI[0] = 0.0; sJ[0] = 0.0; }
+  __syncthreads();
+  for (int p = tid; p <= ZPANELS; p += PRO_THREADS) {
+    const double zp_ = p * hz, u = 1.0 + zp_;
+    sD[p] = u * sI[p];
+    sDp[p] = sI[p] + u * rsqrt(om * (zp_ * (3.0 + zp_ * (3.0 + zp_))) + 1.0);
+  }
+  __syncthreads();
+}
+
+// The prologue's CTAs per Lambda point and their roles, in two shapes.  CL (small
+// batches, whose few CTAs would leave most SMs idle): a thread-block cluster of eight
+// CTAs, so that the FP64 work, which this GPU runs at 1/64 of its FP32 rate, is spread
+// over eight SMs -- ranks 0 and 1 build the two halves of the d_L -> z inversion table
+// (each after step (1)), rank 2 the redshift normalisation N'_z, ranks 3..7 each
+// integrate a share of the smoothing window's panels; after a cluster barrier rank 3
+// gathers the window CTAs' sums and panel integrals from their shared memory in rank
+// order, scans them, and writes the window tables and the constants (xmax it reads from
+// rank 0's shared memory), and a second barrier keeps every CTA's shared memory alive
+// until rank 3 is done.  Every CTA passes both barriers, except that all of them return
+// at once for a Lambda outside the domain.  Not CL (large batches, where every SM has
+// work anyway): three CTAs, no redundant work -- rank 0 the whole inversion table, rank 1
+// N'_z, rank 2 step (1), the whole window, the tables and the constants.
+template <bool CL> struct ProShape {
+  static constexpr int CTAS = CL ? 8 : 3;
+  static constexpr int INV = CL ? 2 : 1;   // ranks [0, INV) build the inversion table
+  static constexpr int NZR = INV;          // the N'_z rank
+  static constexpr int WIN0 = NZR + 1;     // ranks [WIN0, CTAS) integrate the window; WIN0 gathers
+  static constexpr int NWIN = CTAS - WIN0;
+};
+constexpr int PRO_CLUSTER_MAX_K = 32;      // batches up to this size use the cluster shape
+
+template <bool CL>
 __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
+  namespace cg = cooperative_groups;
+  using Sh = ProShape<CL>;
   extern __shared__ double sdyn[];               // 2 * nx doubles: P_n, D_n
   __shared__ double sI[ZPANELS + 1], sJ[ZPANELS + 1], sD[ZPANELS + 1], sDp[ZPANELS + 1];
   __shared__ double red[32 * 16];
   __shared__ double sc[32];                      // scalar broadcast
+  __shared__ double s_wv[16];                    // a window CTA's share of the window sums
+  __shared__ double s_pan[4][NW_WIN];            // and its panels' C-family integrals
 
-  const int k = blockIdx.x, tid = threadIdx.x, part = blockIdx.y;
-  if (k == 0 && part == 0 && tid == 0 && A.counter) *A.counter = 0;
+  const int k = blockIdx.x, tid = threadIdx.x, rank = blockIdx.y;
+  // the barrier across a Lambda point's CTAs (the cluster); without CL the roles exchange
+  // nothing and only the CTA's own barrier is needed
+  auto pro_sync = [&]() {
+    if constexpr (CL) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+  // a rank's shared memory (without CL only the CTA's own is ever asked for)
+  auto peer = [&](double* p, int r) -> const double* {
+    if constexpr (CL) return cg::this_cluster().map_shared_rank(p, r);
+    else return p;
+  };
+  if (k == 0 && rank == 0 && tid == 0 && A.counter) *A.counter = 0;
   const bool mp = A.mp != 0;
   const double* L = A.lam + (size_t)k * n_params(mp);
   LamF* lf = A.lf + k;
@@ -154,8 +221,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const int nx = A.nx, nz = A.nz;
   const double zmax = A.zmax;
 
-  if (!lambda_ok(L, mp)) {
-    if (tid == 0 && part == 1) {
+  if (!lambda_ok(L, mp)) {   // the same for every rank: the whole cluster returns
+    if (tid == 0 && rank == Sh::WIN0) {
       LamF f;
       memset(&f, 0, sizeof(f));
       f.xmax = -1.f;
@@ -178,7 +245,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   // multi-peak: the high peak and the low peak's share (lam1 = 1 leaves one Gaussian)
   const double mu2 = mp ? L[P_MU2] : 0.0, sig2 = mp ? L[P_SIG2] : 1.0, lam1 = mp ? L[P_LAM1] : 1.0;
 
-  if (part == 2) {
+  if (rank == Sh::NZR) {
     // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
     //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
     const double dzg = zmax / (nz - 1);
@@ -201,43 +268,25 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       ld->dcz[1] = -v[2] / v[0];
       ld->dcz[2] = -v[3] / v[0];
     }
+    if constexpr (CL) { pro_sync(); pro_sync(); }
     return;
   }
+  const double pscale = (double)(nz - 1) / zmax;   // LOS grid units per unit z
 
-  // ---- (1) I(z) and J(z) = dI/dOm on panel edges of [0, zmax]
+  if (rank < Sh::INV) {
+  z_panels(om, zmax, sI, sJ, sD, sDp, red);
   const double hz = zmax / ZPANELS;
-  {
-    double v[2] = {0.0, 0.0};
-    const double za = tid * hz;
-    for (int q = 0; q < NGL; ++q) {
-      const double zq = za + 0.5 * hz * (1.0 + c_glx[q]);
-      const double u3m1 = zq * (3.0 + zq * (3.0 + zq));   // (1+z)^3 - 1
-      const double E2 = om * u3m1 + 1.0, E = sqrt(E2);
-      v[0] += c_glw[q] / E;
-      v[1] += c_glw[q] * (-0.5 * u3m1 / (E2 * E));
-    }
-    v[0] *= 0.5 * hz;
-    v[1] *= 0.5 * hz;
-    block_scan<2>(v, red);
-    sI[tid + 1] = v[0];
-    sJ[tid + 1] = v[1];
-    if (tid == 0) { sI[0] = 0.0; sJ[0] = 0.0; }
-    __syncthreads();
-    for (int p = tid; p <= ZPANELS; p += PRO_THREADS) {
-      const double zp_ = p * hz, u = 1.0 + zp_;
-      sD[p] = u * sI[p];
-      sDp[p] = sI[p] + u / sqrt(om * (zp_ * (3.0 + zp_ * (3.0 + zp_))) + 1.0);   // D'(z_p)
-    }
-    __syncthreads();
-  }
   const double xmax = sD[ZPANELS];
   const double dx = xmax / (nx - 1);
-  const double pscale = (double)(nz - 1) / zmax;   // LOS grid units per unit z
-  if (part == 0) {
 
-  // ---- (2) inversion table on the uniform x grid
+  // ---- (2) inversion table on the uniform x grid: each of the INV ranks owns nodes
+  //          [own0, own1) and also evaluates node own1 (when there is one), the right
+  //          neighbour that its last Hermite segment needs, leaving that node's table
+  //          entries to the next rank
+  const int own0 = rank * nx / Sh::INV, own1 = (rank + 1) * nx / Sh::INV;
+  const int eval1 = own1 < nx ? own1 + 1 : nx;
   float4* aux = reinterpret_cast<float4*>(tb + 4 * nx);
-  for (int n = tid; n < nx; n += PRO_THREADS) {
+  for (int n = own0 + tid; n < eval1; n += PRO_THREADS) {
     const double xn = (n == nx - 1) ? xmax : n * dx;
     double z = 0.0, Dp = 1.0, Jz = 0.0, jd = 0.0;
     if (n > 0) {
@@ -265,25 +314,25 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       double acc = 0.0, accj = 0.0;
       for (int q = 0; q < NGL; ++q) {
         const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
-        const double u3m1 = zq * (3.0 + zq * (3.0 + zq)), E2 = om * u3m1 + 1.0, iE = 1.0 / sqrt(E2);
+        const double u3m1 = zq * (3.0 + zq * (3.0 + zq)), iE = rsqrt(om * u3m1 + 1.0);
         acc += c_glw[q] * iE;
         accj += c_glw[q] * (-0.5 * u3m1 * iE * iE * iE);
       }
       const double Iz = sI[p] + 0.5 * h * acc;
       Jz = sJ[p] + 0.5 * h * accj;
       const double u = 1.0 + z;
-      const double u3m1 = z * (3.0 + z * (3.0 + z)), E2 = om * u3m1 + 1.0, iE = 1.0 / sqrt(E2);
+      const double u3m1 = z * (3.0 + z * (3.0 + z)), iE = rsqrt(om * u3m1 + 1.0);
       Dp = Iz + u * iE;
       z = fmin(fmax(z - (u * Iz - xn) / Dp, z0), z0 + hz);
       jd = -0.5 * u3m1 * iE * iE * iE;
     }
     sdyn[2 * n] = z * pscale;                // P_n
     sdyn[2 * n + 1] = pscale / Dp * dx;      // dP/dx * dx
-    aux[n] = make_float4(0.f, (float)Jz, (float)(jd / Dp * dx), 0.f);
+    if (n < own1) aux[n] = make_float4(0.f, (float)Jz, (float)(jd / Dp * dx), 0.f);
   }
   __syncthreads();
   float4* pos = reinterpret_cast<float4*>(tb);
-  for (int n = tid; n < nx; n += PRO_THREADS) {
+  for (int n = own0 + tid; n < own1; n += PRO_THREADS) {
     const double P0 = sdyn[2 * n], D0 = sdyn[2 * n + 1];
     double c2 = 0.0, c3 = 0.0;
     if (n < nx - 1) {
@@ -295,8 +344,12 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     pos[n] = make_float4(hi, (float)(P0 - (double)hi), (float)D0, (float)c2);
     aux[n].x = (float)c3;
   }
+  if constexpr (CL) { pro_sync(); pro_sync(); }   // rank WIN0 reads xmax from rank 0 in between
   return;
-  }   // part 0
+  }   // the inversion ranks
+
+  // ---- the window ranks; without CL the single window rank also needs step (1) for xmax
+  if constexpr (!CL) z_panels(om, zmax, sI, sJ, sD, sDp, red);
 
   // ---- (3) mass-model normalisations (Z_P on thread 0, Z_G on thread 32, Z_G2 on
   //          thread 64, so the serial chains run in different warps), broadcast through
@@ -329,12 +382,17 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double hw = dm / NW_WIN;
   //          (multi-peak: the Gaussian part is lam1 G + (1 - lam1) G2, and four more sums
   //          give the mu2, sig2, lam1 derivatives and the G2 part of the m_max one)
-  double cum[4] = {0.0, 0.0, 0.0, 0.0};   // C, C_beta, J, K over this thread's panel
+  //          The window ranks share the panels; a thread takes one Gauss-Legendre node at
+  //          a time (eight consecutive threads one panel).
+  const int wr = rank - Sh::WIN0;
+  const int pa0 = wr * NW_WIN / Sh::NWIN, pa1 = (wr + 1) * NW_WIN / Sh::NWIN;   // this CTA's panels
   double wv[13] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  static_assert(2 * NW_WIN <= PRO_THREADS, "two threads per window panel");
-  if (tid < 2 * NW_WIN && dm > 0.0) {   // panel tid / 2, half of its nodes each
-    const double ma = mmin + (tid >> 1) * hw;
-    for (int q = (tid & 1) * (NGL / 2); q < ((tid & 1) + 1) * (NGL / 2); ++q) {
+  for (int base = 0; base < (pa1 - pa0) * NGL; base += PRO_THREADS) {   // uniform trip count
+  const int pl = (base + tid) / NGL, q = tid % NGL;                        // panel (local), node
+  double cum[4] = {0.0, 0.0, 0.0, 0.0};   // C, C_beta, J, K at this thread's node
+  if (pa0 + pl < pa1 && dm > 0.0) {
+    const double ma = mmin + (pa0 + pl) * hw;
+    {
       const double m = ma + 0.5 * hw * (1.0 + c_glx[q]);
       const double mp = m - mmin, lm = log(m);
       double S, oneS, dSddm;
@@ -370,14 +428,35 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       }
     }
   }
+  // each panel's integrals: the sum over its NGL node threads (a fixed xor tree)
+  for (int i = 0; i < 4; ++i)
+    for (int o = 1; o < NGL; o <<= 1) cum[i] += __shfl_xor_sync(0xffffffffu, cum[i], o);
+  if (q == 0 && pa0 + pl < pa1)
+    for (int i = 0; i < 4; ++i) s_pan[i][pl] = cum[i];
+  }
   block_sum<13>(wv, red);
-  // each panel's sums to its even thread, then an inclusive scan: the even thread 2p
-  // holds the cumulative integrals at node p + 1
-  for (int i = 0; i < 4; ++i) {
-    cum[i] += __shfl_xor_sync(0xffffffffu, cum[i], 1);
-    if (tid & 1) cum[i] = 0.0;
+  if (tid < 13) s_wv[tid] = wv[tid];
+  pro_sync();
+  if (rank == Sh::WIN0) {
+  // ---- rank WIN0 gathers the shares in rank order (the window sums, and each panel's
+  //      integrals from the CTA that owns it), then an inclusive scan over the panels:
+  //      thread p holds the cumulative integrals at node p + 1
+  for (int i = 0; i < 13; ++i) wv[i] = 0.0;
+  for (int r = 0; r < Sh::NWIN; ++r) {
+    const double* o = peer(s_wv, Sh::WIN0 + r);
+    for (int i = 0; i < 13; ++i) wv[i] += o[i];
+  }
+  double cum[4] = {0.0, 0.0, 0.0, 0.0};
+  if (tid < NW_WIN) {
+    int r = 0;
+    while ((r + 1) * NW_WIN / Sh::NWIN <= tid) ++r;
+    const double* o = peer(&s_pan[0][0], Sh::WIN0 + r);
+    const int loc = tid - r * NW_WIN / Sh::NWIN;
+    for (int i = 0; i < 4; ++i) cum[i] = o[i * NW_WIN + loc];
   }
   block_scan<4>(cum, red);
+  const double xmax = *peer(&sD[ZPANELS], 0);   // D(z_max): rank 0's with CL, else this CTA's
+  const double dx = xmax / (nx - 1);
   const double W = wv[0];
   const double Zm1 = 1.0 - W;
   // d ln Z_m1 / d theta = -dW/d theta / Z_m1
@@ -394,8 +473,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   float4* wslp = wval + (NW_WIN + 1);
   __shared__ double scum[4][NW_WIN + 1];
   __shared__ double sq[4][NW_WIN + 1];
-  if (tid < 2 * NW_WIN && !(tid & 1))
-    for (int i = 0; i < 4; ++i) scum[i][(tid >> 1) + 1] = cum[i];
+  if (tid < NW_WIN)
+    for (int i = 0; i < 4; ++i) scum[i][tid + 1] = cum[i];
   if (tid == 0)
     for (int i = 0; i < 4; ++i) scum[i][0] = 0.0;
   __syncthreads();
@@ -558,6 +637,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     ld->inv_1ml = lam < 1.0 ? 1.0 / (1.0 - lam) : 0.0;
     ld->gpk_inv1zp = gpk / (1.0 + zp);
   }
+  }   // rank WIN0
+  if constexpr (CL) pro_sync();   // the window CTAs' shared memory stays until rank WIN0 has read it
 }
 
 // ---------------------------------------------------------------- fused kernel
@@ -1425,12 +1506,30 @@ __global__ void k_los_cell(const float* z, long long n, int nz, double zmax, int
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s) {
   const size_t smem = sizeof(double) * 2 * (size_t)a.nx;
+  const bool cl = K <= PRO_CLUSTER_MAX_K;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cl ? cudaFuncSetAttribute(k_prologue<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(k_prologue<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_prologue<<<dim3(K, 3), PRO_THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  if (!cl) {
+    k_prologue<false><<<dim3(K, ProShape<false>::CTAS), PRO_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  // one cluster of ProShape<true>::CTAS CTAs per Lambda point (grid y = cluster y)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(K, ProShape<true>::CTAS, 1);
+  cfg.blockDim = dim3(PRO_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = ProShape<true>::CTAS;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_prologue<true>, a);
 }
 
 template <bool G, bool KH, typename RT, bool MP>
