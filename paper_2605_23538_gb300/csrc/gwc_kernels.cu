@@ -1230,11 +1230,12 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   __shared__ double rO[8][2];
   __shared__ int rfail[8];
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nt = blockDim.x, nw = nt >> 5;   // sized to the work by launch_merge
   const LamD D = A.ld[k];
   const int ne = A.n_events;
   const int NPK = n_params(A.mp != 0);   // gradient width of the mass model
   if (D.flag & 1) {
-    for (int e = tid; e < ne; e += 256) {
+    for (int e = tid; e < ne; e += nt) {
       A.lnL_event[(size_t)k * ne + e] = -INFINITY;
       A.neff_event[(size_t)k * ne + e] = 0.0;
     }
@@ -1259,7 +1260,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   double sumL = 0.0, cmp = 0.0, sg[NP_MAX];
   for (int i = 0; i < NPK; ++i) sg[i] = 0.0;
   int fail = 0;   // bit 0: an event below the N_eff threshold; bit 1: an event with no weight
-  for (int e = tid; e < ne; e += 256) {
+  for (int e = tid; e < ne; e += nt) {
     const int s0 = A.ev_item0[e] * P, s1 = A.ev_item0[e + 1] * P;
     double M = -INFINITY;
     for (int s = s0; s < s1; ++s) M = fmax(M, (double)pk[(size_t)s * PSTRIDE]);
@@ -1312,7 +1313,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   double oM = -INFINITY, oS = 0.0;   // other-component pair at lambda_peak = 0 or 1
   if (GRAD)
     for (int i = 0; i < NPK; ++i) sG[i] = 0.0;
-  for (int s = A.inj_item0 * P + tid; s < A.n_items * P; s += 256) {
+  for (int s = A.inj_item0 * P + tid; s < A.n_items * P; s += nt) {
     const float* p = pk + (size_t)s * PSTRIDE;
     if (GRAD && D.lam_sigma != 0 && p[PART_MO] > -INFINITY) {
       const double mo = p[PART_MO];
@@ -1383,7 +1384,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     double tot = 0.0, gt[NP_MAX], M = -INFINITY, S1 = 0.0, S2 = 0.0, G[NP_MAX];
     int fl = 0;
     for (int i = 0; i < NPK; ++i) { gt[i] = 0.0; G[i] = 0.0; }
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < nw; ++q) {
       tot += rs[q][0];
       fl |= rfail[q];
       if (GRAD)
@@ -1391,7 +1392,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       M = fmax(M, rsel[q][0]);
     }
     if (M > -INFINITY) {
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < nw; ++q) {
         if (!(rsel[q][0] > -INFINITY)) continue;
         const double r = exp2(rsel[q][0] - M);
         S1 += rsel[q][1] * r;
@@ -1405,7 +1406,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         stats_to_grad(st, S1, D, G);
       }
       if (GRAD && D.lam_sigma != 0)
-        for (int q = 0; q < 8; ++q)
+        for (int q = 0; q < nw; ++q)
           if (rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * exp2(rO[q][0] - M);
     }
     int flag = (fl & 1) ? 2 : 0;
@@ -1673,9 +1674,14 @@ cudaError_t launch_plain_reduce(const PlainArgs& a, bool grad, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One CTA per Lambda point, with one thread per event or injection partial up to 256: a
+// small catalogue (an HMC chain's) then reduces over one or two warps, whose FP64
+// butterflies (1/64 of the FP32 rate on this GPU) would otherwise run in all eight.
 cudaError_t launch_merge(const MergeArgs& a, int K, bool grad, cudaStream_t s) {
-  if (grad) k_merge<true><<<K, 256, 0, s>>>(a);
-  else k_merge<false><<<K, 256, 0, s>>>(a);
+  const long long work = std::max<long long>(a.n_events, (long long)(a.n_items - a.inj_item0) * a.P);
+  const int threads = (int)std::min<long long>(256, std::max<long long>(32, (work + 31) / 32 * 32));
+  if (grad) k_merge<true><<<K, threads, 0, s>>>(a);
+  else k_merge<false><<<K, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
