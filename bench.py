@@ -69,7 +69,7 @@ SMS, FP32_LANES, SFU_LANES, SM_MAX_GHZ = 152, 128, 16, 2.07
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fused value+gradient
 # launch on the default workload and batch, from an ncu capture of the kernel and layout
 # sources whose digest is recorded here; reported only while the sources still have it.
-TRAFFIC = {"digest": "84331e6c70a06da3", "workload": "c3", "K": 256, "bytes_per_launch": 886.12e6}
+TRAFFIC = {"digest": "c5365ca631255f91", "workload": "c3", "K": 256, "bytes_per_launch": 1031.00e6}
 KERNEL_SOURCES = ("gwc_kernels.cu", "gwc_internal.cuh", "gwc_kernels.h", "gwc_api.cu")
 
 
