@@ -92,7 +92,7 @@ struct gwc_ctx {
   double* d_out = nullptr;      // lnL_event, neff_event, ln_xi, neff_sel, lnL_total, grad
   int32_t* d_flags = nullptr;
   double* h_lam = nullptr;      // pinned
-  double* h_out = nullptr;      // pinned: lnL_total[K], grad[K][13]
+  double* h_out = nullptr;      // pinned: lnL_total[K], grad[K][np]
   int32_t* h_flags = nullptr;   // pinned
   // plain path scratch (allocated on first use)
   int32_t* sample_item = nullptr;
@@ -1280,7 +1280,7 @@ gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const doubl
   h->ctx = c;
   h->serial = c->serial;
   // device block: lnL_event, neff_event [K][n_ev]; ln_xi, neff_sel, lnL_total, lnL0 [K];
-  // grad_total, q0, grad0 [K][13]; flags, div [K]
+  // grad_total, q0, grad0 [K][np]; flags, div [K]
   const size_t ne = (size_t)std::max(c->n_events, 1);
   const size_t nd = 2 * (size_t)K * ne + 4 * (size_t)K + 3 * (size_t)K * c->np;
   cudaError_t e = cudaMalloc(&h->mem, nd * sizeof(double) + 2 * (size_t)K * sizeof(int32_t));

@@ -39,8 +39,8 @@ constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the pr
 enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_GAM, P_KAP, P_ZP,
        P_MU2, P_SIG2, P_LAM1 };
 
-// The sample kernels do not sum the 13 derivatives of ln w themselves but 13 weighted
-// statistics they are linear in; the FP64 merge applies the Lambda-only coefficients
+// The sample kernels do not sum the 13 derivatives of ln w (16 for the multi-peak model)
+// themselves but as many weighted statistics that they are linear in; the FP64 merge applies the Lambda-only coefficients
 // (stats_to_grad).  For one sample of weight t (pa, pb: mixture responsibilities,
 // zz = (m1s - mu)/sig, sr = sigmoid of the rate's turnover, lu2 = log2(1+z)):
 //   S_H0   t Gz x / D'            (d/dH0 = S_H0 / H0)
