@@ -14,7 +14,7 @@ evaluates its parts with gwc_loglik_parts; `merge_parts` combines the shards exa
 because the selection integral is a sum over injections, xi = sum_r xi_r:
     ln L = sum_r sum_events_r - N_det ln(sum_r xi_r)
     d ln L = sum_r d sum_events_r - N_det sum_r (xi_r / xi) d ln xi_r
-`merge_parts_distributed` does the one exchange (an all_gather of K (4 + 26) numbers).
+`merge_parts_distributed` does the one exchange (an all_gather of K (5 + 2P) numbers).
 """
 from __future__ import annotations
 
@@ -117,7 +117,8 @@ def merge_parts(parts):
 
 def merge_parts_distributed(part):
     """merge_parts over all ranks of the process group: one all_gather of every rank's
-    K (4 + 26) numbers, then the same exact combination on every rank."""
+    K (5 + 2P) numbers (P = 13, or 16 for the multi-peak model, taken from the
+    gradients' width), then the same exact combination on every rank."""
     import torch
     dist = _dist()
     if dist is None:
@@ -131,8 +132,11 @@ def merge_parts_distributed(part):
     K = int(t(part["ln_xi"]).shape[0])
     cols = [t(part["sum_events"])[:, None], t(part["ln_xi"])[:, None], t(part["neff_sel"])[:, None],
             t(part["flags"])[:, None], torch.full((K, 1), float(part["n_events"]), dtype=torch.float64)]
+    P = 0
     if grad:
-        cols += [t(part["grad_events"]), t(part["grad_ln_xi"])]
+        ge, gx = t(part["grad_events"]).reshape(K, -1), t(part["grad_ln_xi"]).reshape(K, -1)
+        P = ge.shape[1]
+        cols += [ge, gx]
     mine = torch.cat(cols, dim=1)
     every = [torch.empty_like(mine) for _ in range(world)]
     dist.all_gather(every, mine)
@@ -142,7 +146,7 @@ def merge_parts_distributed(part):
         p = {"sum_events": m[:, 0], "ln_xi": m[:, 1], "neff_sel": m[:, 2],
              "flags": m[:, 3].astype(np.int64), "n_events": int(m[0, 4])}
         if grad:
-            p["grad_events"] = m[:, 5:18]
-            p["grad_ln_xi"] = m[:, 18:31]
+            p["grad_events"] = m[:, 5:5 + P]
+            p["grad_ln_xi"] = m[:, 5 + P:5 + 2 * P]
         parts.append(p)
     return merge_parts(parts)

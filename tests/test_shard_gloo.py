@@ -113,3 +113,54 @@ def test_event_shards_on_two_gloo_ranks(tmp_path):
     np.testing.assert_allclose(res["ln_xi"], ref["ln_xi"], rtol=0, atol=1e-12)
     np.testing.assert_allclose(res["neff_sel"], ref["neff_sel"], rtol=1e-12)
     np.testing.assert_allclose(res["total"], ref["lnL_total"], rtol=0, atol=1e-10)
+
+
+def _parts_rank_grad(rank, world, port, result_file):
+    # multi-peak (16-entry) Lambda with gradients: the oracle gives this shard's total
+    # gradient; its parts are rebuilt from the definition of ln xi
+    # (d ln xi = sum_m softmax(ln w)_m d ln w_m) and grad_total = grad_events - n_r d ln xi_r
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2605_23538_gb300 import shard, synth
+        cat = synth.catalogue(synth.scaled("shard", 4, ("fixed", 200), 4, 128, 2000, "found"))
+        lam = synth.lambda_batch(2, purpose=53, model="multipeak")
+        ne, ni = len(cat["offsets"]) - 1, len(cat["inj_m1"])
+        ev = list(range(rank * ne // world, (rank + 1) * ne // world))
+        part = synth.subset_events(cat, ev)
+        a, b = rank * ni // world, (rank + 1) * ni // world
+        for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
+            part[k] = cat[k][a:b]
+        r = oracle.loglik(part, lam, grad=True, neff_min_event=0.0)
+        gx = []
+        for q in lam:
+            lw, dlw, _ = oracle.ln_w_samples(q, part, "inj", grad=True)
+            fin = np.isfinite(lw)
+            w = np.exp(lw[fin] - lw[fin].max())
+            gx.append((w[:, None] * dlw[fin]).sum(axis=0) / w.sum())
+        gx = np.array(gx)
+        mine = {"sum_events": r["lnL_event"].sum(axis=1), "ln_xi": r["ln_xi"], "neff_sel": r["neff_sel"],
+                "flags": r["flags"], "n_events": len(ev),
+                "grad_events": r["grad_total"] + len(ev) * gx, "grad_ln_xi": gx}
+        merged = shard.merge_parts_distributed(mine)
+        if rank == 0:
+            np.savez(result_file, total=merged["lnL_total"], grad=merged["grad_total"], lam=lam)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_event_shards_merge_multipeak_gradients_on_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_2605_23538_gb300 import synth
+    out = str(tmp_path / "pg.npz")
+    mp.start_processes(_parts_rank_grad, args=(2, _free_port(), out), nprocs=2, start_method="spawn", join=True)
+    res = np.load(out)
+    cat = synth.catalogue(synth.scaled("shard", 4, ("fixed", 200), 4, 128, 2000, "found"))
+    ref = oracle.loglik(cat, res["lam"], grad=True, neff_min_event=0.0)
+    assert res["grad"].shape == (2, 16)
+    np.testing.assert_allclose(res["total"], ref["lnL_total"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(res["grad"], ref["grad_total"], rtol=1e-8, atol=1e-8 * np.abs(ref["grad_total"]).max())
