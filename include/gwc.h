@@ -204,8 +204,8 @@ gwc_status gwc_loglik_kde(gwc_ctx* ctx, int32_t K, const double* d_lambda,
                           double* d_ln_xi, double* d_neff_sel, double* d_lnL_total,
                           int32_t* d_flags, void* stream);
 
-/* The parts of the likelihood that shards of a catalogue combine (the survey's event
- * sharding: one exchange of ~K (3 + 26) numbers).  A context built from a subset of the
+/* The parts of the likelihood that shards of a catalogue combine (event sharding or
+ * batching: one exchange of K (5 + 2P) numbers).  A context built from a subset of the
  * events and a subset of the found injections, with n_draw of the whole injection set,
  * gives for its share: d_lnL_event, d_neff_event, d_ln_xi (ln of its injections' sum
  * over the whole n_draw), d_neff_sel and d_flags as gwc_loglik; d_sum_events[K] = the sum
