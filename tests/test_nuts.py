@@ -79,3 +79,26 @@ def test_invalid_start_is_rejected():
         return np.full(len(q), -np.inf), np.zeros_like(q)
     with pytest.raises(ValueError):
         nuts.sample(wall, np.zeros((2, 2)), 5, 0.1)
+
+
+def test_walkers_on_the_oracle_likelihood(orc, synth):
+    # the sampler over a real 16-entry target: the FP64 oracle on a tiny catalogue, with a
+    # point outside the Lambda domain (-inf) possible along the way; every recorded point
+    # is in the domain and its recorded log-likelihood is the oracle's there
+    from conftest import smooth_row, tiny_catalogue
+    r = np.random.default_rng(6)
+    ev = [[(m1, m1 * 0.7, dl, 2.0 * np.log(dl), 0) for m1, dl in zip(r.uniform(20, 40, 30), r.uniform(800, 3000, 30))]
+          for _ in range(2)]
+    inj = [(m1, m1 * r.uniform(0.3, 1.0), r.uniform(200, 6000), -16.0) for m1 in np.exp(r.uniform(np.log(6), np.log(120), 200))]
+    cat = tiny_catalogue(smooth_row(257)[None, :], ev, inj, 800.0)
+
+    def logp_grad(q):
+        out = orc.loglik(cat, q, grad=True, neff_min_event=0.0)
+        return out["lnL_total"], out["grad_total"]
+
+    fid = synth.FIDUCIAL_MP
+    res = nuts.sample(logp_grad, np.vstack([fid, fid * 1.001]), 4, 0.02,
+                      inv_mass=(0.05 * np.maximum(np.abs(fid), 0.1)) ** 2, seed=1, max_depth=4)
+    last = res["samples"][-1]
+    assert last.shape == (2, 16) and np.all(np.isfinite(res["lnL"]))
+    np.testing.assert_allclose(res["lnL"][-1], logp_grad(last)[0], rtol=0, atol=1e-12)

@@ -80,9 +80,13 @@ def _linear_los_catalogue(synth, seed=3, n_pix=3, per_pix=(40, 60, 25), z_max=2.
 
 
 @pytest.mark.parametrize("rule", ["scott", "silverman", "biweight"])
-def test_linear_los_kde_equals_monte_carlo(orc, synth, rule):
+@pytest.mark.parametrize("model", ["plp", "multipeak"])
+def test_linear_los_kde_equals_monte_carlo(orc, synth, rule, model):
     cat = _linear_los_catalogue(synth)
-    lam = np.vstack([synth.FIDUCIAL, synth.FIDUCIAL * [1.1, 0.9, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1]])
+    fid = synth.FIDUCIAL if model == "plp" else synth.FIDUCIAL_MP
+    shift = np.ones(len(fid))
+    shift[:2] = [1.1, 0.9]
+    lam = np.vstack([fid, fid * shift])
     kde = orc.loglik_kde(cat, lam, bw=rule, n_grid=256, neff_min_pixel=0.0)
     mc = orc.loglik(cat, lam, neff_min_event=0.0)
     assert np.all(np.isfinite(kde["lnL_event"]))
