@@ -74,6 +74,8 @@ def lib():
                 fn.argtypes = args
             L.orc_los_cell.restype = i32
             L.orc_los_cell.argtypes = [ctypes.c_float, i32, d]
+            L.orc_sample_cells.restype = ctypes.c_int
+            L.orc_sample_cells.argtypes = [vp, i32, i64, vp, i32, d, vp, vp]
             L.orc_ln_w_samples.restype = ctypes.c_int
             L.orc_ln_w_samples.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp]
             L.orc_ln_w_row.restype = ctypes.c_int
@@ -123,6 +125,18 @@ def ln_Nz(lam, pbar, zmax):
 def los_cell(z, nz, zmax):
     """LOS grid cell of the float32 value z (-1 outside [0, zmax])."""
     return lib().orc_los_cell(ctypes.c_float(float(np.float32(z))), nz, zmax)
+
+
+def sample_cells(lam, dl, nz, zmax):
+    """LOS grid cell (int32, -1 where d_L maps outside [0, zmax]) and exact grid position
+    z (nz - 1) / zmax (NaN there) of each sample's redshift at Lambda, as ln_w uses them."""
+    a = _lam(lam)
+    dl = np.ascontiguousarray(dl, dtype=np.float32)
+    cell = np.empty(len(dl), np.int32)
+    pos = np.empty(len(dl), np.float64)
+    if lib().orc_sample_cells(_ptr(a), a.shape[-1], len(dl), _ptr(dl), nz, zmax, _ptr(cell), _ptr(pos)) != 0:
+        raise ValueError("Lambda outside its domain")
+    return cell, pos
 
 
 def ln_w_row(lam, m1, m2, dl, lnpi, row, zmax, grad=False):

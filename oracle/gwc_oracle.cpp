@@ -455,15 +455,24 @@ Pop<T> make_pop(const double* L, int model, const std::vector<double>& pbar, dou
 }
 
 // ---------------------------------------------------------------------- LOS
-// linear interpolation of a row tabulated at z_j = j * zmax / (nz - 1); zero outside
-// [0, zmax].  The cell index is the exact floor of z (nz - 1) / zmax.
-template <class T> bool los_interp(const double* row, int nz, double zmax, const T& z, T& p) {
-  const double zv = val(z);
-  if (zv < 0.0 || zv > zmax) return false;
+// The grid cell of z on z_j = j * zmax / (nz - 1): the exact floor of z (nz - 1) / zmax,
+// clamped to [0, nz - 2] (z = zmax lies in the last cell); -1 outside [0, zmax].
+int los_cell_of(double zv, int nz, double zmax) {
+  if (zv < 0.0 || zv > zmax) return -1;
   const double s = (double)(nz - 1) / zmax;
   int j = (int)std::floor(zv * s);
   if (j > nz - 2) j = nz - 2;
   if (j < 0) j = 0;
+  return j;
+}
+
+// linear interpolation of a row tabulated at z_j = j * zmax / (nz - 1); zero outside
+// [0, zmax], in the cell los_cell_of gives.
+template <class T> bool los_interp(const double* row, int nz, double zmax, const T& z, T& p) {
+  const double zv = val(z);
+  const int j = los_cell_of(zv, nz, zmax);
+  if (j < 0) return false;
+  const double s = (double)(nz - 1) / zmax;
   const T t = z * s - (double)j;
   p = row[j] + t * (row[j + 1] - row[j]);
   return val(p) > 0.0;
@@ -676,8 +685,15 @@ void eval_lambda(const Inputs& in, const std::vector<double>& pbar, const double
     }
   }
 
-  // ---- selection: injections against the pixel-averaged LOS prior, in fixed chunks
-  const int64_t chunk = 65536;
+  // ---- selection: injections against the pixel-averaged LOS prior, in chunks small
+  // enough that every thread gets several (the chunk size changes only the order of
+  // the FP64 sums)
+#ifdef _OPENMP
+  const int64_t nthreads = omp_get_max_threads();
+#else
+  const int64_t nthreads = 1;
+#endif
+  const int64_t chunk = std::min<int64_t>(65536, std::max<int64_t>(1024, in.n_inj / (4 * nthreads) + 1));
   const int64_t nchunk = (in.n_inj + chunk - 1) / chunk;
   std::vector<Sums<T>> parts((size_t)nchunk);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -1087,14 +1103,32 @@ double orc_ln_Nz(const double* L, int32_t n_par, const double* pbar, int32_t nz,
 // The LOS grid cell of z, as used by los_interp above and as the CUDA library documents
 // it: floor(z * ((nz - 1) / zmax)) in double precision, clamped to [0, nz - 2]; -1 for
 // z outside [0, zmax].
-int32_t orc_los_cell(float zf, int32_t nz, double zmax) {
-  const double z = (double)zf;
-  if (z < 0.0 || z > zmax) return -1;
+int32_t orc_los_cell(float zf, int32_t nz, double zmax) { return los_cell_of((double)zf, nz, zmax); }
+
+// For n samples of distance dl (Mpc) at Lambda L: the LOS grid cell that ln_w
+// interpolates in (los_cell_of of the sample's exact redshift; -1 where d_L does not map
+// into [0, zmax], i.e. d_L <= 0 or x > D(zmax)) and, in pos (may be NULL), the exact grid
+// position z (nz - 1) / zmax (NaN where the cell is -1).
+int orc_sample_cells(const double* L, int32_t n_par, int64_t n, const float* dl, int32_t nz,
+                     double zmax, int32_t* cell, double* pos) {
+  const int model = model_of(n_par);
+  if (model < 0 || !lambda_in_domain(L, model)) return 1;
+  const double H0 = L[P_H0], om = L[P_OM];
+  const double xmax = D_of(zmax, om);
   const double s = (double)(nz - 1) / zmax;
-  int j = (int)std::floor(z * s);
-  if (j > nz - 2) j = nz - 2;
-  if (j < 0) j = 0;
-  return j;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t k = 0; k < n; ++k) {
+    const double d = (double)dl[k];
+    cell[k] = -1;
+    if (pos) pos[k] = NaN_;
+    if (!(d > 0.0)) continue;
+    const double x = d * H0 / C_KMS;
+    if (x > xmax) continue;
+    const double z = z_of_x(x, om, z_root(x, om, zmax));
+    cell[k] = los_cell_of(z, nz, zmax);
+    if (pos && cell[k] >= 0) pos[k] = z * s;
+  }
+  return 0;
 }
 
 // ln w for n samples against one LOS row that also defines N_z (as the pixel average

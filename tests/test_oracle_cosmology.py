@@ -76,3 +76,34 @@ def test_distance_monotone_and_bounded(orc):
         d = np.array([orc.D(z, om) for z in zs])
         assert np.all(np.diff(d) > 0)
         assert np.all(d <= zs * (1 + zs) + 1e-15)   # E >= 1 for z >= 0
+
+
+@pytest.mark.parametrize("om", [0.0, 1.0])
+def test_sample_cells_closed_forms(orc, synth, om):
+    # the per-sample grid cell and position come from the closed-form inverses at
+    # Om = 0 (z = (sqrt(1 + 4x) - 1)/2) and Om = 1 (z = ((1 + sqrt(1 + 2x))/2)^2 - 1),
+    # with x = d_L H0 / c; cells are the floor of the position, -1 where d_L <= 0 or
+    # z > z_max, and z = z_max lies in the last cell
+    lam = synth.FIDUCIAL.copy()
+    lam[1] = om
+    nz, zmax, c = 512, 2.0, 299792.458
+    rng = np.random.default_rng(3)
+    dl = rng.uniform(-500.0, 4.0e4, 4000).astype(np.float32)
+    x = dl.astype(np.float64) * lam[0] / c
+    if om == 0.0:
+        z = 0.5 * (np.sqrt(1.0 + 4.0 * np.maximum(x, 0.0)) - 1.0)
+    else:
+        z = ((1.0 + np.sqrt(1.0 + 2.0 * np.maximum(x, 0.0))) / 2.0) ** 2 - 1.0
+    pos_cf = z * (nz - 1) / zmax
+    cell, pos = orc.sample_cells(lam, dl, nz, zmax)
+    inside = (dl > 0) & (z <= zmax)
+    assert np.array_equal(cell >= 0, inside)
+    assert np.all(np.isnan(pos[~inside]))
+    np.testing.assert_allclose(pos[inside], pos_cf[inside], rtol=1e-12, atol=1e-10)
+    want = np.minimum(np.floor(pos_cf[inside]), nz - 2).astype(np.int32)
+    near = np.abs(pos_cf[inside] - np.round(pos_cf[inside])) < 1e-8   # no claim at the node itself
+    assert np.array_equal(cell[inside][~near], want[~near])
+    # a distance that maps exactly to z_max lies in the last cell
+    d_max = orc.D(zmax, om) * c / lam[0]
+    cm, _ = orc.sample_cells(lam, np.array([np.nextafter(np.float32(d_max), np.float32(0))], np.float32), nz, zmax)
+    assert cm[0] == nz - 2
