@@ -53,19 +53,112 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# Algorithmic work per (sample, Lambda) evaluation of the fused value+gradient kernel,
-# counted from its formula (one transcendental = one special-function-unit op):
-#   value, 8 SFU: 1/(1+z), log2(1+z), 2^-|a-b| (mass mixture), m1^(1+beta) above the
-#          smoothing window, 2^-|r| (rate), 1/sqrt(E^2), 1/(product's denominator), the
-#          logsumexp power; ~85 FP32: distance-to-position with its compensation terms
-#          (~20), LOS lerp, source masses, mixture, smoothing, C(m1), rate, E(z) and D'(z),
-#          the accurate log2 of the product (~12), accumulation
-#   gradient, 5 SFU: 1/(1+2^-|a-b|), 1/(1+2^-|r|), 1/D', 1/C, 1/p_LOS; ~81 FP32: the
-#          z-chain G_z (~25), J(x), window or closed-form C derivatives, and the 13
-#          statistics with their accumulation (~36)
-SFU_PER_EVAL = 13
-FP32_PER_EVAL = 166
-SMS, FP32_LANES, SFU_LANES, SM_MAX_GHZ = 152, 128, 16, 2.07
+# Algorithmic work per (sample, Lambda) evaluation of the fused kernel, counted by hand
+# from its source (sample_lnw and the accumulator), per stage that an evaluation reaches
+# (the stages of gwc_path_census).  Each entry: (FP32 operations of the method, FP32
+# operations that exist only for precision, {special-function op: count}).  FP32
+# operations are adds, multiplies and fused multiply-adds (compares, min/max, selects and
+# conversions are not counted); the accurate log2f of the product counts as one lg2
+# (its extra accuracy work is not counted).  "Precision" is the compensation the FP32
+# path carries against shared biases: the split table coordinate (x hi + lo, 6 ops), the
+# low parts of alpha, beta, 1+beta and gamma+kappa (one FMA each where used).  Stages
+# named *_nowin1 are charged to the evaluations of the parent stage outside the m1
+# smoothing window (the closed-form C(m1)); the weight_* stages are the gradient's and
+# are charged to every evaluation with a positive weight (an upper bound: the kernel
+# skips the derivatives of weights below 2^-48 of the running maximum).
+WORK = {
+    "live": (1, 0, {}),                                         # x = d_L H0/c, range test
+    "in_range": (9, 6, {}),                                     # table position, cell, z
+    "mass_order": (3, 0, {"rcp": 1}),                           # 1+z, source masses
+    "support": (5, 0, {"lg2": 1}),                              # log2(1+z), LOS lerp
+    "value": (27, 2, {"ex2": 3, "rsqrt": 1, "rcp": 1, "lg2": 1}),  # mixture, rate, Jacobian, log, accumulate
+    "value_nowin1": (3, 2, {"ex2": 1}),                         # C(m1) above the window
+    "value_win1": (20, 1, {}),                                  # C(m1) from the window table
+    "value_win2": (7, 0, {"rcp": 2, "ex2": 1}),                 # smoothing of m2
+    "weight": (67, 0, {"rcp": 4}),                              # z-chain, J(x), 13 statistics
+    "weight_nowin1": (8, 0, {"rcp": 1}),
+    "weight_win1": (48, 0, {"rcp": 5, "ex2": 1}),
+    "weight_win2": (9, 0, {"rcp": 1}),
+}
+SFU_TYPES = ("ex2", "lg2", "rcp", "rsqrt")
+SMS = 152
+
+
+def work_from_census(census, grad=True):
+    """FP32 (method, precision) and special-function op counts of one call, from the
+    stage counts of gwc_path_census and the WORK table."""
+    n = dict(census)
+    n["value_nowin1"] = n["value"] - n["value_win1"]
+    n["weight_nowin1"] = n["weight"] - n["weight_win1"]
+    stages = [k for k in WORK if grad or not k.startswith("weight")]
+    meth = sum(n[k] * WORK[k][0] for k in stages)
+    prec = sum(n[k] * WORK[k][1] for k in stages)
+    sfu = {t: sum(n[k] * WORK[k][2].get(t, 0) for k in stages) for t in SFU_TYPES}
+    return {"fp32_method": meth, "fp32_precision": prec, "sfu": sfu}
+
+
+# Throughput probes (gwc_alu_probe): CTAs per launch and iterations per chain, sized so
+# that each launch takes ~10-40 ms
+PROBES = {"ffma": 320_000, "ffma2": 160_000, "ex2": 40_000, "lg2": 40_000, "rcp": 40_000,
+          "rsqrt": 40_000, "dfma": 5_000}
+PROBE_BLOCKS = SMS * 8
+
+
+def measure_alu_peaks(g, stream, clock_index):
+    """Operations per second of each arithmetic unit (best of three timed launches after
+    one untimed), with the SM clock sampled meanwhile; per SM per clock as well."""
+    import torch
+    sampler = ClockSampler(clock_index)
+    sampler.start()
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for unit, iters in PROBES.items():
+        g.alu_probe(unit, PROBE_BLOCKS, iters, stream)
+        best = float("inf")
+        for _ in range(3):
+            e0.record(stream)
+            ops = g.alu_probe(unit, PROBE_BLOCKS, iters, stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[unit] = {"ops_per_s": ops / best, "ms": best * 1e3}
+    clocks = sampler.stop()
+    mhz = clocks["sm_mhz"] if clocks else None
+    for unit in out:
+        out[unit]["per_sm_per_clk"] = (out[unit]["ops_per_s"] / (SMS * mhz * 1e6)) if mhz else None
+    return {"units": out, "clocks": clocks,
+            "how": f"gwc_alu_probe: {PROBE_BLOCKS} CTAs x 256 threads x 8 independent chains, "
+                   "best of 3 CUDA-event-timed launches after 1 untimed; per_sm_per_clk uses the "
+                   "median SM clock sampled during the probes"}
+
+
+def alu_roofline(work, seconds, peaks, kernel_mhz):
+    """The binding arithmetic unit of one launch: the slower of the FP32 pipe (the better
+    of scalar and packed FMA) and the special-function unit (each op type at its own
+    measured rate), with the probes' rates scaled from their clock to the kernel's."""
+    u = peaks["units"]
+    probe_mhz = (peaks.get("clocks") or {}).get("sm_mhz")
+    scale = (kernel_mhz / probe_mhz) if (kernel_mhz and probe_mhz) else 1.0
+    fp32_peak = max(u["ffma"]["ops_per_s"], u["ffma2"]["ops_per_s"]) * scale
+    t_fp32 = work["fp32_method"] / fp32_peak
+    t_fp32_all = (work["fp32_method"] + work["fp32_precision"]) / fp32_peak
+    sfu_ops = sum(work["sfu"].values())
+    t_sfu = sum(work["sfu"][t] / (u[t]["ops_per_s"] * scale) for t in SFU_TYPES)
+    common = {"bound": "alu", "peak_source": "measured (gwc_alu_probe on this GPU)",
+              "clock_scale": scale, "t_fp32_ms": t_fp32 * 1e3, "t_sfu_ms": t_sfu * 1e3,
+              "t_fp32_with_precision_ms": t_fp32_all * 1e3, "kernel_ms": seconds * 1e3,
+              "fp32_method_ops": work["fp32_method"], "fp32_precision_ops": work["fp32_precision"],
+              "sfu_ops": work["sfu"]}
+    if t_fp32 >= t_sfu:
+        ach = work["fp32_method"] / seconds / 1e12
+        return dict(common, unit="Tops/s (FP32 pipe, method ops)", achieved=ach, peak=fp32_peak / 1e12,
+                    frac=ach / (fp32_peak / 1e12),
+                    frac_with_precision=t_fp32_all / seconds)
+    sfu_peak = sfu_ops / t_sfu
+    ach = sfu_ops / seconds / 1e12
+    return dict(common, unit="Tops/s (SFU, this op mix)", achieved=ach, peak=sfu_peak / 1e12,
+                frac=ach / (sfu_peak / 1e12), frac_fp32_with_precision=t_fp32_all / seconds)
+
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fused value+gradient
 # launch on the default workload and batch, from an ncu capture of the kernel and layout
@@ -101,21 +194,6 @@ def traffic_for(workload, K):
             and TRAFFIC["K"] == K):
         return TRAFFIC["bytes_per_launch"]
     return None
-
-
-def alu_roofline(evals, seconds):
-    """Binding ALU unit for evals evaluations in `seconds` (peaks at the maximum SM clock)."""
-    sfu_peak = SMS * SFU_LANES * SM_MAX_GHZ * 1e9          # SFU ops/s
-    fp32_peak = SMS * FP32_LANES * SM_MAX_GHZ * 1e9        # FP32 instructions/s
-    t_sfu = evals * SFU_PER_EVAL / sfu_peak
-    t_fp32 = evals * FP32_PER_EVAL / fp32_peak
-    if t_fp32 >= t_sfu:
-        ach = evals * FP32_PER_EVAL / seconds / 1e12
-        return dict(bound="alu", unit="Tinst/s (FP32 pipe)", achieved=ach, peak=fp32_peak / 1e12,
-                    frac=ach / (fp32_peak / 1e12), peak_source="152 SMs x 128 FP32 lanes x 2.07 GHz")
-    ach = evals * SFU_PER_EVAL / seconds / 1e12
-    return dict(bound="alu", unit="Top/s (SFU)", achieved=ach, peak=sfu_peak / 1e12,
-                frac=ach / (sfu_peak / 1e12), peak_source="152 SMs x 16 SFU lanes x 2.07 GHz")
 
 
 class ClockSampler:
@@ -181,19 +259,41 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(cat, lam, max_seconds=20.0):
-    """The FP64 oracle (value + gradient) on a bounded sample of the workload."""
-    import oracle
+def host_description():
+    """nproc and the CPU model lines of lscpu (the host the oracle runs on)."""
+    desc = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Architecture", "Model name", "CPU(s)", "Thread(s) per core", "Socket(s)"):
+                desc[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return desc
+
+
+def oracle_sample(cat, n_ev, n_inj):
+    """The first n_ev events and the first n_inj injections of the workload."""
     from paper_2605_23538_gb300 import synth
+    sub = synth.subset_events(cat, range(n_ev))
+    for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
+        sub[k] = cat[k][:n_inj]
+    return sub, int(sub["offsets"][-1]) + n_inj
+
+
+def cpu_baseline(cat, lam, max_seconds=20.0):
+    """The FP64 oracle (value + gradient) on a bounded sample of the workload, on all host
+    cores and on one core."""
+    import oracle
     cores = os.cpu_count() or 1
-    # grow the sample until one timed pass takes about half of max_seconds or more
-    n_ev, n_inj = 4, 20_000
     n_ev_max = len(cat["offsets"]) - 1
+    # all cores: at least four events per core (the oracle runs events in parallel, and
+    # injections in chunks of about n_inj / (4 cores)); grow the sample until one timed
+    # pass takes about half of max_seconds or more
+    n_ev, n_inj = min(n_ev_max, 4 * cores), 20_000
     while True:
-        sub = synth.subset_events(cat, range(n_ev))
-        for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
-            sub[k] = cat[k][:n_inj]
-        evals = int(sub["offsets"][-1]) + n_inj
+        sub, evals = oracle_sample(cat, n_ev, n_inj)
         t0 = time.perf_counter()
         oracle.loglik(sub, lam[:1], grad=True, n_threads=cores)
         dt = time.perf_counter() - t0
@@ -202,9 +302,21 @@ def cpu_baseline(cat, lam, max_seconds=20.0):
         grow = max(1.5, min(8.0, 0.7 * max_seconds / max(dt, 1e-3)))
         n_ev = min(n_ev_max, int(n_ev * grow))
         n_inj = min(len(cat["inj_m1"]), int(n_inj * grow))
-    return dict(value=evals / dt, unit="evals/s", cores=cores, kind="oracle",
+    value = evals / dt
+    # one core: a slice of the same sample sized to take about a quarter of max_seconds
+    frac = min(1.0, 0.25 * max_seconds / max(dt * cores, 1e-3))
+    n1_ev, n1_inj = max(1, int(n_ev * frac)), max(1000, int(n_inj * frac))
+    sub1, evals1 = oracle_sample(cat, n1_ev, n1_inj)
+    t0 = time.perf_counter()
+    oracle.loglik(sub1, lam[:1], grad=True, n_threads=1)
+    dt1 = time.perf_counter() - t0
+    return dict(value=value, unit="evals/s", cores=cores, kind="oracle",
                 sample=f"1 Lambda x ({int(sub['offsets'][-1])} samples of the first {n_ev} events "
-                       f"+ the first {n_inj} injections), FP64 value+gradient, {dt:.1f} s")
+                       f"+ the first {n_inj} injections), FP64 value+gradient, {dt:.1f} s on {cores} threads",
+                one_core={"value": evals1 / dt1, "unit": "evals/s", "cores": 1,
+                          "sample": f"1 Lambda x ({int(sub1['offsets'][-1])} samples of the first {n1_ev} "
+                                    f"events + the first {n1_inj} injections), {dt1:.1f} s"},
+                host=host_description())
 
 
 # HMC on the small workload (10 events x 1000 samples, 1e4 injection draws): one chain,
@@ -291,6 +403,12 @@ def multipeak_timing(g, synth, cat, K, n_evals, stream, steps=3):
             "unit": "evals/s (value+gradient)"}
 
 
+# The reference arm's sample per step: enough events that every core has several (the
+# oracle runs events in parallel, and injections in chunks of about n_inj / (4 cores)),
+# about 3 s of work per step on 16 cores
+REF_EVENTS, REF_INJECTIONS = 64, 400_000
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, one bounded sample per step."""
     world, rank, _ = dist_setup()
@@ -300,13 +418,10 @@ def run_reference(args):
     from paper_2605_23538_gb300 import synth
     oracle.build()
     cat = synth.catalogue(WORKLOAD)
-    lam = synth.lambda_batch(K_LAMBDA)
+    lam = synth.lambda_batch(K_LAMBDA, purpose=4)
     cores = os.cpu_count() or 1
-    n_ev, n_inj = 6, 40_000
-    sub = synth.subset_events(cat, range(n_ev))
-    for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
-        sub[k] = cat[k][:n_inj]
-    evals = int(sub["offsets"][-1]) + n_inj
+    n_ev = max(REF_EVENTS, 4 * cores)
+    sub, evals = oracle_sample(cat, n_ev, REF_INJECTIONS)
     for w in range(args.warmup):
         oracle.loglik(sub, lam[w % K_LAMBDA:w % K_LAMBDA + 1], grad=True, n_threads=cores)
     t0 = time.perf_counter()
@@ -315,15 +430,15 @@ def run_reference(args):
         oracle.loglik(sub, lam[k:k + 1], grad=True, n_threads=cores)
     dt = time.perf_counter() - t0
     value = evals * args.steps / dt
-    sample = (f"per step 1 Lambda x ({int(sub['offsets'][-1])} samples of the first {n_ev} events "
-              f"+ the first {n_inj} injections)")
+    sample = (f"per step 1 Lambda of the bench's batch x ({int(sub['offsets'][-1])} samples of the first "
+              f"{n_ev} events + the first {REF_INJECTIONS} injections), FP64 value+gradient")
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD_NAMES[WORKLOAD], "K": K_LAMBDA, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_description()},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -410,8 +525,14 @@ def main():
     value = evals_step * args.steps * world / (ms_total / 1e3)
     flags = out["flags"].cpu().numpy()
     fused_ms = stage_ms[1] / max(n_calls, 1)
-    roof = alu_roofline(evals_step, fused_ms / 1e3)
+    # untimed: which stages the batch's evaluations reach (to charge each only its work),
+    # and the arithmetic units' measured rates
+    census = ctx.path_census(lam, stream)
+    work = work_from_census(census, grad=True)
+    peaks = measure_alu_peaks(g, stream, local)
+    roof = alu_roofline(work, fused_ms / 1e3, peaks, (clocks or {}).get("sm_mhz"))
     roof["traffic"] = traffic_for(args.workload, K)
+    roof["census"] = census
 
     value_only = plain = e2e = graph_line = hmc_line = None
     if not args.no_extras:
@@ -481,7 +602,7 @@ def main():
         base = cpu_baseline(cat, lam_np)
 
     if rank == 0:
-        peaks, src = load_peaks()
+        mpeaks, src = load_peaks()
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps,
@@ -497,12 +618,13 @@ def main():
                        "lambda_group": None if tune is None else tune["lambda_group"],
                        "autotuned": tune is not None},
             "roofline": roof,
+            "alu_peaks": peaks,
             "stage_ms_per_step": {"prologue": stage_ms[0] / max(n_calls, 1), "fused": fused_ms,
                                   "merge": stage_ms[2] / max(n_calls, 1)},
             "gpu_launches": 3 * args.steps,
             "kernel_digest": kernel_digest(),
             "flags_nonzero": int(np.count_nonzero(flags)),
-            "peaks": {"source": src, "hbm_gbs": peaks.get("hbm_gbs")},
+            "peaks": {"source": src, "hbm_gbs": mpeaks.get("hbm_gbs")},
         }
         if value_only is not None:
             line["value_only"] = {"value": value_only, "unit": "evals/s"}

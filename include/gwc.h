@@ -337,23 +337,34 @@ gwc_status gwc_get_info(const gwc_ctx* ctx, gwc_info* out);
  *   d_lnw[n_samples + n_found]          ln w minus the per-Lambda constant c (-inf where w = 0)
  *   d_dlnw[P][n_samples + n_found]      (optional, may be NULL) d(ln w - c)/d Lambda
  *   d_c[1 + P]                          c and dc/d Lambda, so ln w = d_lnw + c
+ *   d_cell[n_samples + n_found]         (optional, may be NULL) the LOS grid cell j whose
+ *                                       nodes z_j, z_j+1 the sample's prior is interpolated
+ *                                       between (Sec. 2.1's pixelised LOS prior), from the same
+ *                                       arithmetic as the likelihood kernels: the floor of the
+ *                                       sample's grid position z (n_z - 1) / z_max, clamped to
+ *                                       [0, n_z - 2]; -1 where d_L maps outside [0, z_max]
  * d_lambda points to P doubles on the device.  Uses the context's per-call scratch. */
 gwc_status gwc_sample_terms(gwc_ctx* ctx, const double* d_lambda, float* d_lnw, float* d_dlnw,
-                            double* d_c, void* stream);
+                            double* d_c, int32_t* d_cell, void* stream);
 
-/* Per-sample terms without allocating: the same outputs as gwc_sample_terms, computed
- * from caller-owned device arrays instead of a context.  The paper has no counterpart;
+/* Per-sample terms without allocating: the outputs d_lnw, d_dlnw and d_c of
+ * gwc_sample_terms, computed from caller-owned device arrays instead of a context.  The paper has no counterpart;
  * this entry point serves callers that cannot allocate device memory when they need an
  * evaluation -- code running while a CUDA graph is being captured (cudaMalloc is not
  * allowed then), code inside a framework whose caching allocator owns the device's
  * memory, or callbacks that must leave the memory state untouched -- and so cannot hold
  * a gwc_ctx.  It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
- * (one Lambda point's constants and tables and the pixel-mean LOS row, about 80 KB) is a
+ * (one Lambda point's constants and tables, the pixel-mean LOS row and its partial sums
+ * over 8 slabs of pixels, about 340 KB) is a
  * fixed device array inside the library, held by every GPU that loads the library until
  * the process exits.  It evaluates the power law + peak model (13-entry Lambda).
  *   d_lambda[13]                      Lambda (device, doubles)
  *   d_samples[n_samples][4]           {m1_det, m2_det, d_L, ln pi_PE} (device, 16-byte aligned)
- *   d_pix[n_samples]                  pixel of each sample, in [0, n_pix)
+ *   d_pix[n_samples]                  pixel of each sample, in [0, n_pix); the library does
+ *                                     not read these on the host, so it cannot reject a bad
+ *                                     one up front: a sample whose pixel lies outside the
+ *                                     range reads no LOS row and gets w = 0 (d_lnw = -inf,
+ *                                     d_dlnw = 0)
  *   d_injections[n_inj][4]            {m1_det, m2_det, d_L, ln p_draw} (device, 16-byte aligned)
  *   d_los[n_pix][n_z]                 LOS priors on z_j = j z_max / (n_z - 1) (device, float)
  *   n_x_table                         inversion-table nodes, a multiple of 4 in [16, 1024]
@@ -388,6 +399,35 @@ gwc_status gwc_profile_read(gwc_ctx* ctx, double* ms, int64_t* n_calls);
  * their split-precision position tables. */
 gwc_status gwc_los_cell_index(const float* d_z, int64_t n, int32_t n_z, double z_max,
                               int32_t* d_cell, void* stream);
+
+/* Path census of the likelihood kernels' per-(sample, Lambda) arithmetic (measurement
+ * only; the paper has no counterpart).  For the K points d_lambda[K][P] (device) and
+ * every event sample and injection of the context, the value arithmetic of the fused
+ * kernel is run once and d_counts[GWC_CENSUS_N] (device, uint64, overwritten) receives
+ * how many (sample, Lambda) evaluations reached each stage, so that a roofline can
+ * charge each evaluation only the work it did:
+ *   [0] evaluations at a live (in-domain) Lambda       [1] d_L maps into [0, z_max]
+ *   [2] of those, m2_det <= m1_det                     [3] of those, inside the mass support
+ *   [4] the whole value computed (LOS prior > 0)       [5] of [4], m1 inside the smoothing window
+ *   [6] of [4], m2 inside the smoothing window         [7] weight > 0 (the gradient's share)
+ *   [8] of [7], m1 inside the window                   [9] of [7], m2 inside the window
+ * Uses the context's per-call scratch and must not overlap other calls on it. */
+#define GWC_CENSUS_N 10
+gwc_status gwc_path_census(gwc_ctx* ctx, int32_t K, const double* d_lambda, uint64_t* d_counts,
+                           void* stream);
+
+/* Throughput probes of the arithmetic units (measurement only; the paper has no
+ * counterpart): one kernel of `blocks` CTAs x 256 threads on the stream, each thread
+ * running `iters` iterations of 8 independent dependency chains of one operation:
+ *   GWC_UNIT_FFMA   FP32 fused multiply-add           GWC_UNIT_FFMA2  packed f32x2 FMA
+ *   GWC_UNIT_EX2, GWC_UNIT_LG2, GWC_UNIT_RCP, GWC_UNIT_RSQRT   special-function unit
+ *                   approximations (each chain also adds a constant in FP32)
+ *   GWC_UNIT_DFMA   FP64 fused multiply-add
+ * *ops (host, may be NULL) receives the operations the launch performs (a packed FMA
+ * counts as two); the caller times the launch, e.g. with CUDA events on the stream. */
+enum { GWC_UNIT_FFMA = 0, GWC_UNIT_FFMA2 = 1, GWC_UNIT_EX2 = 2, GWC_UNIT_LG2 = 3,
+       GWC_UNIT_RCP = 4, GWC_UNIT_RSQRT = 5, GWC_UNIT_DFMA = 6 };
+gwc_status gwc_alu_probe(int32_t unit, int32_t blocks, int32_t iters, double* ops, void* stream);
 
 #ifdef __cplusplus
 }

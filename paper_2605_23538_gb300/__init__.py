@@ -94,7 +94,8 @@ EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_get_info", "gwc_los_cell_index", "gwc_profile_enable", "gwc_profile_read",
            "gwc_sample_terms", "gwc_sample_terms_noalloc", "gwc_graph_create", "gwc_graph_launch",
            "gwc_graph_destroy", "gwc_hmc_create", "gwc_hmc_launch", "gwc_hmc_destroy",
-           "gwc_autotune", "gwc_default_kde_options", "gwc_loglik_kde", "gwc_loglik_parts")
+           "gwc_autotune", "gwc_default_kde_options", "gwc_loglik_kde", "gwc_loglik_parts",
+           "gwc_path_census", "gwc_alu_probe")
 
 
 def lib():
@@ -129,7 +130,7 @@ def lib():
         L.gwc_get_info.restype = ctypes.c_int
         L.gwc_get_info.argtypes = [vp, ctypes.POINTER(Info)]
         L.gwc_sample_terms.restype = ctypes.c_int
-        L.gwc_sample_terms.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gwc_sample_terms.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.gwc_sample_terms_noalloc.restype = ctypes.c_int
         L.gwc_sample_terms_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, i32, i32, d, vp, i32,
                                                vp, vp, vp, vp]
@@ -159,6 +160,10 @@ def lib():
         L.gwc_loglik_kde.argtypes = [vp, i32, vp, ctypes.POINTER(KdeOptions), vp, vp, vp, vp, vp, vp, vp]
         L.gwc_loglik_parts.restype = ctypes.c_int
         L.gwc_loglik_parts.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gwc_path_census.restype = ctypes.c_int
+        L.gwc_path_census.argtypes = [vp, i32, vp, vp, vp]
+        L.gwc_alu_probe.restype = ctypes.c_int
+        L.gwc_alu_probe.argtypes = [i32, i32, i32, ctypes.POINTER(d), vp]
         L.gwc_autotune.restype = ctypes.c_int
         L.gwc_autotune.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(TuneResult)]
         _lib = L
@@ -343,8 +348,10 @@ def loglik_grad_host(ctx, lam: np.ndarray, grad=True, stream=None):
     return (tot, flags, g) if grad else (tot, flags)
 
 
-def sample_terms(ctx, lam, n_total, grad=True, stream=None):
-    """gwc_sample_terms for one Lambda (CUDA float64 tensor [P]): (ln w - c, d [P, n], c[1 + P])."""
+def sample_terms(ctx, lam, n_total, grad=True, stream=None, cells=False):
+    """gwc_sample_terms for one Lambda (CUDA float64 tensor [P]): (ln w - c, d [P, n], c[1 + P]),
+    and with cells=True a fourth tensor, the int32 LOS grid cell of each sample (-1 where
+    d_L maps outside [0, z_max])."""
     import torch
     lam = lam.contiguous()
     P = lam.numel()
@@ -352,30 +359,71 @@ def sample_terms(ctx, lam, n_total, grad=True, stream=None):
     lnw = torch.empty(n_total, dtype=torch.float32, device=lam.device)
     d = torch.empty((P, n_total), dtype=torch.float32, device=lam.device) if grad else None
     c = torch.empty(1 + P, dtype=torch.float64, device=lam.device)
+    cell = torch.empty(n_total, dtype=torch.int32, device=lam.device) if cells else None
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
-    _check(lib().gwc_sample_terms(ctx, p(lam), p(lnw), p(d), p(c), _stream_ptr(stream)), ctx)
-    return lnw, d, c
+    _check(lib().gwc_sample_terms(ctx, p(lam), p(lnw), p(d), p(c), p(cell), _stream_ptr(stream)), ctx)
+    return (lnw, d, c, cell) if cells else (lnw, d, c)
 
 
 def sample_terms_noalloc(lam, samples, pix, injections, los, z_max, n_x_table=512, grad=True,
                          stream=None):
     """gwc_sample_terms_noalloc on caller-owned CUDA tensors (no context, no allocation in
     the library): samples [n, 4] and injections [m, 4] float32, pix [n] int32, los
-    [n_pix, n_z] float32, lam [13] float64.  Returns (ln w - c, d, c) like sample_terms;
-    the output tensors are allocated here by PyTorch, not by the library."""
+    [n_pix, n_z] float32, lam [13] float64, all contiguous and on the current CUDA device
+    (the library reads them asynchronously on `stream`, so no temporary copy is made
+    here).  Returns (ln w - c, d, c) like sample_terms; the output tensors are allocated
+    here by PyTorch, not by the library."""
     import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def need(t, name, dtype, dim, width=None):
+        if not (isinstance(t, torch.Tensor) and t.device == dev and t.dtype == dtype and t.dim() == dim
+                and (width is None or t.shape[-1] == width) and t.is_contiguous()):
+            shape = f"[..., {width}]" if width else f"{dim}-D"
+            raise TypeError(f"{name} must be a contiguous {dtype} {shape} tensor on {dev}")
+
+    need(lam, "lam", torch.float64, 1, NUM_PARAMS)
+    need(samples, "samples", torch.float32, 2, 4)
+    need(pix, "pix", torch.int32, 1)
+    need(injections, "injections", torch.float32, 2, 4)
+    need(los, "los", torch.float32, 2)
     n, m = samples.shape[0], injections.shape[0]
-    lnw = torch.empty(n + m, dtype=torch.float32, device=lam.device)
-    d = torch.empty((13, n + m), dtype=torch.float32, device=lam.device) if grad else None
-    c = torch.empty(14, dtype=torch.float64, device=lam.device)
+    if pix.shape[0] != n:
+        raise TypeError("pix must have one entry per sample")
+    lnw = torch.empty(n + m, dtype=torch.float32, device=dev)
+    d = torch.empty((NUM_PARAMS, n + m), dtype=torch.float32, device=dev) if grad else None
+    c = torch.empty(1 + NUM_PARAMS, dtype=torch.float64, device=dev)
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
-    st = lib().gwc_sample_terms_noalloc(p(lam.contiguous()), n, p(samples.contiguous()),
-                                        p(pix.contiguous()), m, p(injections.contiguous()),
-                                        los.shape[0], los.shape[1], float(z_max),
-                                        p(los.contiguous()), n_x_table, p(lnw), p(d), p(c),
-                                        _stream_ptr(stream))
+    st = lib().gwc_sample_terms_noalloc(p(lam), n, p(samples), p(pix), m, p(injections),
+                                        los.shape[0], los.shape[1], float(z_max), p(los), n_x_table,
+                                        p(lnw), p(d), p(c), _stream_ptr(stream))
     _check(st)
     return lnw, d, c
+
+
+CENSUS_SLOTS = ("live", "in_range", "mass_order", "support", "value", "value_win1", "value_win2",
+                "weight", "weight_win1", "weight_win2")
+UNITS = {"ffma": 0, "ffma2": 1, "ex2": 2, "lg2": 3, "rcp": 4, "rsqrt": 5, "dfma": 6}
+
+
+def path_census(ctx, lam, stream=None):
+    """gwc_path_census: how many (sample, Lambda) evaluations of the batch lam [K, P]
+    reach each stage of the value arithmetic; returns a dict keyed by CENSUS_SLOTS."""
+    import torch
+    lam = _lam_batch(lam)
+    _check_width(ctx, lam.shape[1])
+    counts = torch.zeros(len(CENSUS_SLOTS), dtype=torch.int64, device=lam.device)
+    _check(lib().gwc_path_census(ctx, lam.shape[0], ctypes.c_void_p(lam.data_ptr()),
+                                 ctypes.c_void_p(counts.data_ptr()), _stream_ptr(stream)), ctx)
+    return dict(zip(CENSUS_SLOTS, (int(v) for v in counts.cpu().numpy())))
+
+
+def alu_probe(unit, blocks, iters, stream=None):
+    """gwc_alu_probe: launch one throughput probe of an arithmetic unit (a key of UNITS)
+    on the stream; returns the number of operations it performs (the caller times it)."""
+    ops = ctypes.c_double(0.0)
+    _check(lib().gwc_alu_probe(UNITS[unit], blocks, iters, ctypes.byref(ops), _stream_ptr(stream)))
+    return ops.value
 
 
 def _splitmix64_outputs(seed, k):
@@ -612,9 +660,12 @@ class Context:
     def info(self):
         return get_info(self._ctx)
 
-    def sample_terms(self, lam, grad=True, stream=None):
+    def sample_terms(self, lam, grad=True, stream=None, cells=False):
         info = get_info(self._ctx)
-        return sample_terms(self._ctx, lam, info["n_samples"] + info["n_injections"], grad, stream)
+        return sample_terms(self._ctx, lam, info["n_samples"] + info["n_injections"], grad, stream, cells)
+
+    def path_census(self, lam, stream=None):
+        return path_census(self._ctx, lam, stream)
 
     def autotune(self, lam, grad=True, stream=None):
         """gwc_autotune on the Lambda batch lam [K, P]: returns the chosen shape."""

@@ -1,4 +1,4 @@
-"""Build libgwc.so in-tree with nvcc for sm_103a (no cmake, three translation units)."""
+"""Build libgwc.so in-tree with nvcc for sm_103a (no cmake; the translation units compile in parallel)."""
 from __future__ import annotations
 
 import os
@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgwc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["gwc_kernels.cu", "gwc_api.cu", "gwc_noalloc.cu"]
+SOURCES = ["gwc_kernels.cu", "gwc_api.cu", "gwc_noalloc.cu", "gwc_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

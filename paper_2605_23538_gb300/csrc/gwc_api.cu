@@ -187,27 +187,6 @@ cudaError_t prof_mark(gwc_ctx* c, int b, cudaStream_t s) {
   return r;
 }
 
-void gauss_legendre(int n, double* x, double* w) {
-  const double pi = 3.14159265358979323846;
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int j = 2; j <= n; ++j) {
-        const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-  }
-}
-
 uint16_t to_bf16(float f) {   // round to nearest even
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -821,9 +800,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(cudaMemcpy(c->sched, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(c->ev_item0, ev_item0.data(), sizeof(int32_t) * ev_item0.size(), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(c->ev_n, ev_n.data(), sizeof(double) * ev_n.size(), cudaMemcpyHostToDevice));
-  double glx[NGL], glw[NGL];
-  gauss_legendre(NGL, glx, glw);
-  chk(set_gauss_legendre(glx, glw));
+  chk(ensure_gauss_legendre());
   if (e != cudaSuccess) {
     std::string msg = std::string("device upload failed: ") + cudaGetErrorString(e);
     free_all(c);
@@ -1105,7 +1082,7 @@ gwc_status gwc_get_info(const gwc_ctx* c, gwc_info* out) {
 }
 
 gwc_status gwc_sample_terms(gwc_ctx* c, const double* d_lambda, float* d_lnw, float* d_dlnw,
-                            double* d_c, void* stream) {
+                            double* d_c, int32_t* d_cell, void* stream) {
   if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
   if (!d_lambda || !d_lnw || !d_c) return fail(c, GWC_E_INVALID, "NULL pointer");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
@@ -1129,8 +1106,40 @@ gwc_status gwc_sample_terms(gwc_ctx* c, const double* d_lambda, float* d_lnw, fl
   ta.dlnw = d_dlnw;
   ta.c = d_c;
   ta.mp = c->mp ? 1 : 0;
+  ta.n_pix = c->n_pix;
+  ta.cell = d_cell;
   cudaError_t e = launch_sample_terms(ta, c->bf16, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "sample-terms launch");
+  return GWC_OK;
+}
+
+gwc_status gwc_path_census(gwc_ctx* c, int32_t K, const double* d_lambda, uint64_t* d_counts, void* stream) {
+  static_assert(GWC_CENSUS_N == GWC_CENSUS_SLOTS, "census slots");
+  if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
+  if (K < 1 || K > c->opt.max_K) return fail(c, GWC_E_INVALID, "K must be in [1, max_K]");
+  if (!d_lambda || !d_counts) return fail(c, GWC_E_INVALID, "NULL pointer");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gwc_status st = run_prologue(c, K, d_lambda, false, s);
+  if (st != GWC_OK) return st;
+  CensusArgs ca;
+  ca.smp = c->smp;
+  ca.pix = c->pix;
+  ca.inj = c->inj;
+  ca.los = c->los;
+  ca.pbar32 = c->pbar32;
+  ca.nz = c->n_z;
+  ca.nx = c->opt.n_x_table;
+  ca.n_samples = c->n_samples;
+  ca.n_total = c->n_samples + c->n_inj;
+  ca.K = K;
+  ca.lf = c->lf;
+  ca.tables = c->tables;
+  ca.tstride = c->tstride;
+  ca.counts = reinterpret_cast<unsigned long long*>(d_counts);
+  ca.mp = c->mp ? 1 : 0;
+  cudaError_t e = launch_census(ca, c->bf16, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "census launch");
   return GWC_OK;
 }
 

@@ -272,7 +272,10 @@ constexpr float GRAD_SKIP = 48.f;
 
 // WITH_LOS = false leaves out the LOS factor (the weight w' of the KDE form, whose LOS
 // prior enters through the grid integral instead).  Every sample whose d_L maps into
-// [0, z_max] reports its z through sink.position(z), whatever its weight.  MP selects
+// [0, z_max] reports its z and the LOS cell j it interpolates in through
+// sink.position(z, j), whatever its weight; sink.reached(2) and sink.reached(3) mark the
+// mass-order and mass-support cuts passed, and sink.windows(win1, win2) the whole value
+// about to be formed, with the smoothing-window branches taken (a path census uses them).  MP selects
 // the multi-peak mass model (a second Gaussian in the primary-mass mixture).
 template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
@@ -298,18 +301,24 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float frac = nd.y + t * (nd.z + t * (nd.w + t * ax.x));
   int j = (int)floorf(nd.x + frac);
   float tl = (nd.x - (float)j) + frac;
+  // The rounded sum hi + lo can land on the other side of a node when the position lies
+  // within half an ulp of it (1.2e-4 cells near the end of a 2048-node grid); the
+  // in-cell fraction tl is accurate to ~1e-7, so the cell follows its sign.
+  if (tl < 0.f) { --j; tl += 1.f; } else if (tl >= 1.f) { ++j; tl -= 1.f; }
   if (j > nz - 2) { tl += (float)(j - (nz - 2)); j = nz - 2; }
   if (j < 0) { tl += (float)j; j = 0; }
   const float jt = (float)j + tl;
   const float z = fmaf(jt, L.zstep, jt * L.zstep_lo);   // the step in two floats
-  sink.position(z);
+  sink.position(z, j);
   if (s.m2 > s.m1) return false;
+  sink.reached(2);
   const float u = 1.f + z;
   const float ru = rcp(u);
 
   // --- source-frame masses (the support cuts first: samples outside skip the rest)
   const float m1s = s.m1 * ru, m2s = s.m2 * ru;
   if (m1s > L.mmax || m2s < L.mmin) return false;
+  sink.reached(3);
   const float lu2 = lg2(u);
   const float lm1s2 = s.lm1 - lu2, lm2s2 = s.lm2 - lu2;
 
@@ -402,6 +411,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float Dp = fmaf(x, ru, u * rE);
   den *= Dp * (1.f + er);
 
+  sink.windows(win1, win2);
   lw2 = fmaf(L.gam_m3, lu2, lin) + lg2_acc(plos * mixf * rcp(den));
   lw2 += s.npe2;
   if (!(lw2 > -INFINITY)) return false;
@@ -526,7 +536,9 @@ struct AccSink {
     return GRAD && !(lw < a.m - GRAD_SKIP);
   }
   __device__ __forceinline__ void grad(int i, float v) { a.g[i] = fmaf(t, v, a.g[i]); }
-  __device__ __forceinline__ void position(float) {}
+  __device__ __forceinline__ void position(float, int) {}
+  __device__ __forceinline__ void reached(int) {}
+  __device__ __forceinline__ void windows(bool, bool) {}
   __device__ __forceinline__ void lam_edge(float sigma, float lw, float lo) { a.add_other(sigma, t, lw + lo); }
 };
 
@@ -535,9 +547,12 @@ struct TermSink {
   float g[NP_MAX];
   float lo = 0.f;
   bool edge = false;
+  int cell = -1;      // the LOS cell the sample interpolates in (-1: d_L outside [0, z_max])
   __device__ __forceinline__ bool weight(float) { return true; }
   __device__ __forceinline__ void grad(int i, float v) { g[i] = v; }
-  __device__ __forceinline__ void position(float) {}
+  __device__ __forceinline__ void position(float, int j) { cell = j; }
+  __device__ __forceinline__ void reached(int) {}
+  __device__ __forceinline__ void windows(bool, bool) {}
   __device__ __forceinline__ void lam_edge(float sigma, float, float l) {
     g[S_LX] = sigma;
     lo = l;

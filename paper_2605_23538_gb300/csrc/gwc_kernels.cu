@@ -18,6 +18,8 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include <cooperative_groups.h>
@@ -27,10 +29,47 @@ namespace gwc {
 __constant__ double c_glx[NGL];   // Gauss-Legendre nodes on [-1, 1]
 __constant__ double c_glw[NGL];   // and weights
 
-cudaError_t set_gauss_legendre(const double* x, const double* w) {
-  cudaError_t e = cudaMemcpyToSymbol(c_glx, x, sizeof(double) * NGL);
+// n-point Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on the Legendre
+// polynomial from the three-term recurrence, started at the usual cosine estimate.
+static void gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// One upload per device for the life of the process (the values never change), shared by
+// gwc_create and the context-free entry point.
+cudaError_t ensure_gauss_legendre() {
+  constexpr int MAX_DEV = 64;
+  static std::mutex mu;
+  static bool done[MAX_DEV] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_glw, w, sizeof(double) * NGL);
+  if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (done[dev]) return cudaSuccess;
+  double x[NGL], w[NGL];
+  gauss_legendre(NGL, x, w);
+  e = cudaMemcpyToSymbol(c_glx, x, sizeof(double) * NGL);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, w, sizeof(double) * NGL);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
 }
 
 // ------------------------------------------------------------------ FP64 helpers
@@ -828,7 +867,9 @@ struct KdeSink {
   __device__ __forceinline__ bool weight(float) { return false; }
   __device__ __forceinline__ void grad(int, float) {}
   __device__ __forceinline__ void lam_edge(float, float, float) {}
-  __device__ __forceinline__ void position(float zz) { z = zz; }
+  __device__ __forceinline__ void position(float zz, int) { z = zz; }
+  __device__ __forceinline__ void reached(int) {}
+  __device__ __forceinline__ void windows(bool, bool) {}
 };
 
 struct KdeCtx {
@@ -1461,13 +1502,16 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
   TermSink ts;
   bool ok = false;
   if (L.live != 0.f) {
-    if (inj)
+    if (inj) {
       ok = sample_lnw<true, float, TermSink, true, MP>(L, s, A.pbar32, A.nz, pos, aux, nx, wv, ws, lw, ts);
-    else
-      ok = sample_lnw<true, RowT, TermSink, true, MP>(
-          L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz, A.nz, pos, aux, nx,
-          wv, ws, lw, ts);
+    } else {
+      const int px = __ldg(A.pix + i);
+      if (px >= 0 && px < A.n_pix)   // a pixel outside the table reads nothing and gets w = 0
+        ok = sample_lnw<true, RowT, TermSink, true, MP>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)px * A.nz,
+                                                        A.nz, pos, aux, nx, wv, ws, lw, ts);
+    }
   }
+  if (A.cell) A.cell[i] = ts.cell;
   A.lnw[i] = ok ? lw * LN2F : -INFINITY;
   if (A.dlnw) {
     double st[NP_MAX], G[NP_MAX];
@@ -1486,6 +1530,80 @@ cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s) {
   } else {
     if (bf16) k_sample_terms<__nv_bfloat16, false><<<grid, 256, 0, s>>>(a);
     else k_sample_terms<float, false><<<grid, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ path census (measurement)
+// The value arithmetic of the fused kernel, once per (sample, Lambda), counting which
+// stages each evaluation reaches (see gwc_path_census in gwc.h for the slots).
+struct CensusSink {
+  unsigned c[GWC_CENSUS_SLOTS] = {0};
+  __device__ __forceinline__ bool weight(float) { ++c[7]; w = true; return false; }
+  __device__ __forceinline__ void grad(int, float) {}
+  __device__ __forceinline__ void lam_edge(float, float, float) {}
+  __device__ __forceinline__ void position(float, int) { ++c[1]; }
+  __device__ __forceinline__ void reached(int st) { ++c[st]; }
+  __device__ __forceinline__ void windows(bool a, bool b) {
+    ++c[4];
+    w1 = a;
+    w2 = b;
+    c[5] += a;
+    c[6] += b;
+  }
+  bool w = false, w1 = false, w2 = false;
+};
+
+template <typename RowT, bool MP>
+__global__ void __launch_bounds__(256) k_census(CensusArgs A) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  CensusSink cs;
+  if (i < A.n_total) {
+    const bool inj = i >= A.n_samples;
+    const float4 v = inj ? __ldg(A.inj + (i - A.n_samples)) : __ldg(A.smp + i);
+    SampleIn s;
+    s.m1 = v.x; s.m2 = v.y; s.dl = v.z; s.npe2 = -to_log2(v.w);
+    s.lm1 = log2f(v.x); s.lm2 = log2f(v.y);
+    const RowT* row = inj ? nullptr : reinterpret_cast<const RowT*>(A.los) + (size_t)__ldg(A.pix + i) * A.nz;
+    const int nx = A.nx;
+    for (int k = 0; k < A.K; ++k) {
+      const LamF L = A.lf[k];
+      if (L.live == 0.f) continue;
+      ++cs.c[0];
+      const float* tb = A.tables + (size_t)k * A.tstride;
+      const float4* pos = reinterpret_cast<const float4*>(tb);
+      const float4* aux = reinterpret_cast<const float4*>(tb + 4 * nx);
+      const float4* wv = reinterpret_cast<const float4*>(tb + 8 * nx);
+      const float4* ws = wv + (NW_WIN + 1);
+      float lw;
+      cs.w = false;
+      if (inj)
+        sample_lnw<false, float, CensusSink, true, MP>(L, s, A.pbar32, A.nz, pos, aux, nx, wv, ws, lw, cs);
+      else
+        sample_lnw<false, RowT, CensusSink, true, MP>(L, s, row, A.nz, pos, aux, nx, wv, ws, lw, cs);
+      if (cs.w) {
+        cs.c[8] += cs.w1;
+        cs.c[9] += cs.w2;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < GWC_CENSUS_SLOTS; ++q) {
+    const unsigned t = __reduce_add_sync(0xffffffffu, cs.c[q]);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(A.counts + q, (unsigned long long)t);
+  }
+}
+
+cudaError_t launch_census(const CensusArgs& a, bool bf16, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(unsigned long long) * GWC_CENSUS_SLOTS, s);
+  if (e != cudaSuccess || a.n_total <= 0) return e;
+  const unsigned grid = (unsigned)((a.n_total + 255) / 256);
+  if (a.mp) {
+    if (bf16) k_census<__nv_bfloat16, true><<<grid, 256, 0, s>>>(a);
+    else k_census<float, true><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (bf16) k_census<__nv_bfloat16, false><<<grid, 256, 0, s>>>(a);
+    else k_census<float, false><<<grid, 256, 0, s>>>(a);
   }
   return cudaGetLastError();
 }

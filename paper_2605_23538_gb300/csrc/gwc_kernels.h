@@ -159,7 +159,8 @@ struct HmcArgs {
 };
 cudaError_t launch_hmc(const HmcArgs& a, cudaStream_t s);
 
-cudaError_t set_gauss_legendre(const double* x, const double* w);
+// upload the prologue's Gauss-Legendre constants to the current device (once per device)
+cudaError_t ensure_gauss_legendre();
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s);
 constexpr int MAX_SLAB = 64;   // Lambda points per CTA tile at most
 size_t fused_smem_bytes(int chunk, int slab, int group);
@@ -187,8 +188,29 @@ struct TermsArgs {
   float* dlnw;      // [P][n_total] or nullptr (P = 13, or 16 multi-peak)
   double* c;        // [1 + P]
   int mp = 0;       // multi-peak mass model
+  int n_pix = 0;    // rows of los: a sample whose pixel lies outside [0, n_pix) gets w = 0
+  int32_t* cell = nullptr;   // [n_total] or nullptr: the LOS cell each sample interpolates in
 };
 cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s);
+constexpr int GWC_CENSUS_SLOTS = 10;
+struct CensusArgs {
+  const float4* smp;
+  const int32_t* pix;
+  const float4* inj;
+  const void* los;
+  const float* pbar32;
+  int nz;
+  int nx;
+  long long n_samples;
+  long long n_total;
+  int K;
+  const LamF* lf;
+  const float* tables;
+  int tstride;
+  unsigned long long* counts;   // [GWC_CENSUS_SLOTS], zeroed by the launcher
+  int mp = 0;
+};
+cudaError_t launch_census(const CensusArgs& a, bool bf16, cudaStream_t s);
 // the calling thread's message for gwc_last_error(NULL) (defined with the C ABI)
 void set_thread_error(const std::string& msg);
 cudaError_t launch_los_cell(const float* z, long long n, int nz, double zmax, int* cell, cudaStream_t s);

@@ -11,8 +11,8 @@
 //
 // The scratch array is shared by every call in the process on a given device and keeps
 // the last call's contents.  Each call first overwrites everything it later reads (the
-// pixel mean, the per-Lambda constants and the tables), so nothing needs to start at
-// zero, but calls whose kernels overlap on the GPU (concurrent streams, or host threads
+// pixel slabs' partial sums, the pixel mean, the per-Lambda constants and the tables), so
+// nothing needs to start at zero, but calls whose kernels overlap on the GPU (concurrent streams, or host threads
 // issuing in parallel) race on the array and must be serialised by the caller.
 #include <cmath>
 #include <cstdint>
@@ -30,15 +30,18 @@ namespace {
 constexpr int MAX_NZ = 4096;      // LOS redshift nodes
 constexpr int MAX_NX = 1024;      // nodes of the inversion table
 constexpr int MAX_DEVICES = 64;
+constexpr int PM_SLABS = 8;       // pixel slabs summed in parallel for the pixel mean
 
 // scratch layout (bytes): LamF | LamD | per-Lambda tables | pixel mean (float) | (double)
+// | the pixel slabs' partial sums (double, [PM_SLABS][n_z])
 constexpr size_t OFF_LF = 0;
 constexpr size_t OFF_LD = 256;
 constexpr size_t OFF_TB = 768;
 constexpr size_t TB_BYTES = ((size_t)table_floats(MAX_NX) + 3) / 4 * 4 * sizeof(float);
 constexpr size_t OFF_P32 = OFF_TB + (TB_BYTES + 255) / 256 * 256;
 constexpr size_t OFF_P64 = OFF_P32 + (MAX_NZ * sizeof(float) + 255) / 256 * 256;
-constexpr size_t SCRATCH_BYTES = OFF_P64 + MAX_NZ * sizeof(double);   // about 80 KB
+constexpr size_t OFF_PART = OFF_P64 + MAX_NZ * sizeof(double);
+constexpr size_t SCRATCH_BYTES = OFF_PART + (size_t)PM_SLABS * MAX_NZ * sizeof(double);   // about 340 KB
 static_assert(sizeof(LamF) <= OFF_LD - OFF_LF && sizeof(LamD) <= OFF_TB - OFF_LD, "scratch layout");
 
 // Held by every device that loads the library, for the life of the process.
@@ -53,41 +56,35 @@ gwc_status err(gwc_status s, const std::string& m) {
   return s;
 }
 
-// pixel mean of the LOS rows, accumulated in double
-__global__ void k_pixel_mean(const float* __restrict__ los, int n_pix, int nz, float* p32, double* p64) {
+// Pixel mean of the LOS rows in two passes, every sum in FP64 and in a fixed order.  Pass
+// 1: block (z tile, slab) has one thread per z node sum the slab's rows in row order, so
+// PM_SLABS x n_z threads share the n_pix x n_z reads (coalesced along z).  Pass 2: one
+// thread per z node adds the slabs' sums in slab order and divides by n_pix.
+constexpr int PM_THREADS = 64;
+__global__ void __launch_bounds__(PM_THREADS) k_pixel_mean_part(const float* __restrict__ los, int n_pix, int nz,
+                                                                double* part) {
+  const int j = blockIdx.x * PM_THREADS + threadIdx.x;
+  if (j >= nz) return;
+  const int slab = blockIdx.y;
+  const int p0 = (int)((long long)n_pix * slab / PM_SLABS), p1 = (int)((long long)n_pix * (slab + 1) / PM_SLABS);
+  double s = 0.0;
+  for (int p = p0; p < p1; ++p) s += (double)__ldg(los + (size_t)p * nz + j);
+  part[(size_t)slab * nz + j] = s;
+}
+
+__global__ void k_pixel_mean_combine(const double* __restrict__ part, int n_pix, int nz, float* p32, double* p64) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nz) return;
   double s = 0.0;
-  for (int p = 0; p < n_pix; ++p) s += (double)__ldg(los + (size_t)p * nz + j);
+  for (int q = 0; q < PM_SLABS; ++q) s += part[(size_t)q * nz + j];
   s /= (double)n_pix;
   p64[j] = s;
   p32[j] = (float)s;
 }
 
-void gauss_legendre8(double* x, double* w) {
-  const int n = NGL;
-  const double pi = 3.14159265358979323846;
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int j = 2; j <= n; ++j) {
-        const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-  }
-}
-
 // One-time set-up on the current device: look up the device address of the scratch
-// array (its host-side name is only a stand-in) and upload the quadrature constants.
+// array (its host-side name is only a stand-in) and make sure the prologue's quadrature
+// constants are on the device.
 gwc_status setup(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> g(g_setup_mu);
   if (g_scratch_ptr[dev]) {
@@ -97,9 +94,7 @@ gwc_status setup(int dev, unsigned char** out) {
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) return err(GWC_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  double x[NGL], w[NGL];
-  gauss_legendre8(x, w);
-  e = set_gauss_legendre(x, w);
+  e = ensure_gauss_legendre();
   if (e != cudaSuccess) return err(GWC_E_CUDA, std::string("constant upload: ") + cudaGetErrorString(e));
   g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
   *out = g_scratch_ptr[dev];
@@ -140,8 +135,13 @@ extern "C" gwc_status gwc_sample_terms_noalloc(const double* d_lambda, int64_t n
   LamD* ld = reinterpret_cast<LamD*>(base + OFF_LD);
   float* tables = reinterpret_cast<float*>(base + OFF_TB);
 
-  k_pixel_mean<<<(n_z + 255) / 256, 256, 0, s>>>(d_los, n_pix, n_z, p32, p64);
+  double* part = reinterpret_cast<double*>(base + OFF_PART);
+  k_pixel_mean_part<<<dim3((n_z + PM_THREADS - 1) / PM_THREADS, PM_SLABS), PM_THREADS, 0, s>>>(d_los, n_pix, n_z, part);
   e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    k_pixel_mean_combine<<<(n_z + 255) / 256, 256, 0, s>>>(part, n_pix, n_z, p32, p64);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return err(GWC_E_CUDA, std::string("pixel-mean launch: ") + cudaGetErrorString(e));
   ProArgs pa;
   pa.lam = d_lambda;
@@ -172,6 +172,7 @@ extern "C" gwc_status gwc_sample_terms_noalloc(const double* d_lambda, int64_t n
   ta.lnw = d_lnw;
   ta.dlnw = d_dlnw;
   ta.c = d_c;
+  ta.n_pix = n_pix;
   e = launch_sample_terms(ta, false, s);
   if (e != cudaSuccess) return err(GWC_E_CUDA, std::string("sample-terms launch: ") + cudaGetErrorString(e));
   return GWC_OK;

@@ -115,7 +115,10 @@ def sample(logp_grad, q0, n_samples, eps, inv_mass=None, seed=0, n_adapt=0, targ
     eps: initial step size (scalar or [K]); inv_mass: diagonal of M^-1 ([P], default ones).
     Returns a dict: samples [n_samples, K, P], lnL [n_samples, K], depth and n_leapfrog
     [n_samples, K], accept_stat [n_samples, K], eps [K] (the step sizes used for the
-    recorded transitions) and n_calls (batched evaluations made)."""
+    recorded transitions), n_calls (batched evaluations made in all) and calls
+    [n_samples] (those of each recorded transition: every call serves each walker still
+    building its tree, so a transition takes as many calls as its longest walker takes
+    leapfrog steps)."""
     q0 = np.atleast_2d(np.asarray(q0, dtype=np.float64))
     K, P = q0.shape
     inv_mass = np.ones(P) if inv_mass is None else np.asarray(inv_mass, dtype=np.float64).reshape(P)
@@ -133,12 +136,13 @@ def sample(logp_grad, q0, n_samples, eps, inv_mass=None, seed=0, n_adapt=0, targ
     log_eps_bar = np.zeros(K)
     out = dict(samples=np.empty((n_samples, K, P)), lnL=np.empty((n_samples, K)),
                depth=np.empty((n_samples, K), np.int32), n_leapfrog=np.empty((n_samples, K), np.int32),
-               accept_stat=np.empty((n_samples, K)))
+               accept_stat=np.empty((n_samples, K)), calls=np.empty(n_samples, np.int64))
     n_calls = 1
     for it in range(n_adapt + n_samples):
         gens = [w.iterate() for w in walkers]
         pending = {k: next(g) for k, g in enumerate(gens)}   # every transition takes a step
         results = {}
+        calls_before = n_calls
         while pending:
             ks = sorted(pending)
             L, G = logp_grad(np.stack([pending[k] for k in ks]))
@@ -162,6 +166,7 @@ def sample(logp_grad, q0, n_samples, eps, inv_mass=None, seed=0, n_adapt=0, targ
                     w.eps = float(np.exp(log_eps_bar[k]))
             continue
         r = it - n_adapt
+        out["calls"][r] = n_calls - calls_before
         for k, w in enumerate(walkers):
             out["samples"][r, k] = w.q
             out["lnL"][r, k] = w.lnL

@@ -58,3 +58,30 @@ def tiny_catalogue(rows, events, injections, n_draw, z_max=2.0):
                 inj_m1=inj[:, 0].astype(np.float32), inj_m2=inj[:, 1].astype(np.float32),
                 inj_dl=inj[:, 2].astype(np.float32), inj_lnpd=inj[:, 3].astype(np.float32),
                 n_draw=float(n_draw))
+
+
+# Grid positions closer than this (in cells) to a node: the library's FP32 position,
+# accurate to ~1e-7 of a cell, may put such a sample on either side of the node, and the
+# two cells then give the same interpolated value (the prior is continuous there).
+NODE_WINDOW = 2e-5
+
+
+def cell_mismatches(got, ref_cell, ref_pos):
+    """Compare the library's per-sample LOS cells with the oracle's (cell and exact grid
+    position from oracle.sample_cells).  Returns (n_checked, n_near, n_diff_near); raises
+    AssertionError for any difference away from a node, or a difference near a node other
+    than the neighbouring cell."""
+    got = np.asarray(got)
+    assert np.array_equal(got >= 0, ref_cell >= 0), "samples inside / outside [0, z_max] differ"
+    inside = ref_cell >= 0
+    pos = ref_pos[inside]
+    near = np.abs(pos - np.round(pos)) < NODE_WINDOW
+    g, r = got[inside], ref_cell[inside]
+    far_bad = (g != r) & ~near
+    assert not far_bad.any(), (f"{far_bad.sum()} cells differ away from any node, e.g. position "
+                               f"{pos[far_bad][:3]}, library {g[far_bad][:3]}, oracle {r[far_bad][:3]}")
+    node = np.round(pos[near]).astype(np.int64)
+    gn = g[near]
+    ok_near = (gn == node) | (gn == node - 1)
+    assert ok_near.all(), "a cell near a node is neither of the node's two cells"
+    return int(inside.sum()), int(near.sum()), int((g[near] != r[near]).sum())

@@ -2,12 +2,15 @@
 with the bench's batch of K = 256 Lambda points and its launch configuration (the
 default chunk, tile and one warp per point).
 
-The oracle cannot evaluate the whole batch in test time, so it checks what it can
-compute piece by piece: per-event ln L and N_eff at sampled (event, Lambda) pairs, from
-the oracle on those events alone (an event's value does not depend on the others), and
-ln xi at one Lambda over all 1e7 injections.  The gradient at full size is checked
-against central differences of the library's own total at the fiducial point (a
-property that holds at any size) along the directions in which the total is smooth.
+The whole-catalogue oracle runs at two points of the batch (the fiducial point and one
+bench point): the total ln L = sum_i ln L_i - N_det ln xi (Eq. 3), ln xi, every per-event
+ln L_i and all 13 gradient components are compared with it, analytic against analytic
+(the oracle's forward-mode derivative).  The N_eff cut is off (neff_min_event = 0) so the
+total is finite wherever no event has zero weight.  The other points are checked
+through what the oracle computes piece by piece: per-event ln L and N_eff at sampled
+(event, Lambda) pairs, from the oracle on those events alone, and the LOS cells of the
+sampled events' samples and of a stride of the injections.  Central differences of the
+library's own total along directions that leave every z alone are a further property.
 """
 import numpy as np
 import pytest
@@ -68,6 +71,75 @@ def test_c3_sampled_events_and_selection(torch, g, orc, synth, cat_c3):
     print(f"c3 ln xi |d| {abs(o['ln_xi'][0] - r['ln_xi'][0]):.2e}")
     assert abs(o["ln_xi"][0] - r["ln_xi"][0]) <= 1e-5
     np.testing.assert_allclose(o["neff_sel"][0], r["neff_sel"][0], rtol=1e-4)
+
+
+TOL_EVENT, TOL_TOTAL, TOL_XI, TOL_NEFF, TOL_GRAD = 1e-5, 1e-3, 1e-5, 1e-4, 1e-4
+
+
+def test_c3_total_and_gradient_against_whole_catalogue_oracle(torch, g, orc, synth, cat_c3):
+    lam = synth.lambda_batch(K, purpose=4)           # the bench's batch
+    lam[1] = synth.FIDUCIAL
+    with g.Context(cat_c3, max_K=K, neff_min_event=0.0) as ctx:
+        out = ctx.loglik_grad(torch.tensor(lam, device="cuda"))
+        torch.cuda.synchronize()
+        o = {k: v.cpu().numpy() for k, v in out.items()}
+    # the fiducial point and the first bench point whose total is finite on the GPU (a point
+    # with an event of zero weight has no finite total to compare)
+    ok = np.flatnonzero((o["flags"] == 0) & np.isfinite(o["lnL_total"]))
+    rows = [1, int(ok[ok != 1][0])]
+    assert 1 in ok
+    ref = orc.loglik(cat_c3, lam[rows], grad=True, neff_min_event=0.0)
+    for n, k in enumerate(rows):
+        assert o["flags"][k] == ref["flags"][n] == 0
+        ge, re_ = o["lnL_event"][k], ref["lnL_event"][n]
+        assert np.all(np.isfinite(ge)) and np.all(np.isfinite(re_))
+        d_ev = np.abs(ge - re_).max()
+        d_xi = abs(o["ln_xi"][k] - ref["ln_xi"][n])
+        d_tot = abs(o["lnL_total"][k] - ref["lnL_total"][n])
+        d_sum = abs(ge.sum() - re_.sum())
+        r_neff = np.max(np.abs(o["neff_event"][k] - ref["neff_event"][n]) / ref["neff_event"][n])
+        r_neffs = abs(o["neff_sel"][k] - ref["neff_sel"][n]) / ref["neff_sel"][n]
+        gg, gr = o["grad_total"][k], ref["grad_total"][n]
+        sc, kink = ref["grad_scale"][n], ref["grad_kink"][n]
+        den = np.maximum(np.maximum(np.abs(gr), 1e-2 * sc), 1e-9)
+        rel = np.maximum(np.abs(gg - gr) - kink, 0.0) / den
+        plain = np.abs(gg - gr) / np.abs(gr)
+        floor_used = (np.abs(gr) < 1e-2 * sc) & (np.abs(gg - gr) > TOL_GRAD * np.abs(gr))
+        print(f"\nc3 whole catalogue, Lambda row {k}: total {ref['lnL_total'][n]:.6f} |d| {d_tot:.2e}; "
+              f"sum ln L_i |d| {d_sum:.2e}; ln xi |d| {d_xi:.2e}; per-event max |d| {d_ev:.2e}; "
+              f"N_eff rel {r_neff:.2e}, sel {r_neffs:.2e}")
+        for i in range(len(gg)):
+            print(f"  grad[{i:2d}] oracle {gr[i]: .8e} gpu {gg[i]: .8e} |d|/|g| {plain[i]:.2e} "
+                  f"|d|/max(|g|, 1e-2 scale) {rel[i]:.2e}{'  (floor)' if floor_used[i] else ''}"
+                  f"{'  (kink %.1e)' % kink[i] if kink[i] > 0 else ''}")
+        print(f"  components that needed the 1e-2 scale floor: {int(floor_used.sum())} of {len(gg)}")
+        assert d_ev <= TOL_EVENT
+        assert d_xi <= TOL_XI
+        assert d_tot <= TOL_TOTAL
+        assert r_neff <= TOL_NEFF and r_neffs <= TOL_NEFF
+        assert np.all(rel <= TOL_GRAD), rel
+
+
+def test_c3_sampled_cells(torch, g, orc, synth, cat_c3):
+    # the LOS cell of each sample of the sampled events and of every 50th injection, from
+    # the likelihood kernels' position arithmetic, against the oracle's exact floor
+    from conftest import cell_mismatches
+    lam = synth.lambda_batch(K, purpose=4)
+    order = g.sample_order(cat_c3)
+    inj_order = g.injection_order(cat_c3)
+    off = cat_c3["offsets"]
+    idx = np.concatenate([np.arange(off[e], off[e + 1]) for e in EVENTS])
+    ns = len(order)
+    inj_idx = np.arange(0, len(inj_order), 50)
+    with g.Context(cat_c3, max_K=1) as ctx:
+        for k in LAMBDAS:
+            *_, cell = ctx.sample_terms(torch.tensor(lam[k], device="cuda"), grad=False, cells=True)
+            cell = cell.cpu().numpy()
+            got = np.concatenate([cell[idx], cell[ns + inj_idx]])
+            dl = np.concatenate([np.asarray(cat_c3["dl"])[order[idx]], np.asarray(cat_c3["inj_dl"])[inj_order[inj_idx]]])
+            rc, rp = orc.sample_cells(lam[k], dl, cat_c3["los"].shape[1], float(cat_c3["z_max"]))
+            n, near, diff = cell_mismatches(got, rc, rp)
+            print(f"c3 cells Lambda#{k}: {n} samples in range, {near} near a node, {diff} in the neighbouring cell")
 
 
 def test_c3_gradient_against_differences_of_the_total(torch, g, synth, cat_c3):

@@ -246,6 +246,29 @@ def test_los_cell_index_bit_exact(torch, g, orc):
         np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_fused_kernel_cell_index_against_oracle(torch, g, orc, synth, cat_ragged, which):
+    # The LOS cell each sample is interpolated in, as the likelihood kernels compute it
+    # (their own position arithmetic, reported through gwc_sample_terms), against the
+    # oracle's floor of the exact grid position z (n_z - 1) / z_max: equal for every sample
+    # except within NODE_WINDOW cells of a node, where either neighbouring cell gives the
+    # same value; those are counted.
+    from conftest import cell_mismatches
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(9, purpose=13)[:1],
+                     synth.lambda_batch(1, purpose=16)])[which]
+    nz, zmax = cat_ragged["los"].shape[1], float(cat_ragged["z_max"])
+    with g.Context(cat_ragged, max_K=1) as ctx:
+        *_, cell = ctx.sample_terms(torch.tensor(lam, device="cuda"), grad=False, cells=True)
+        cell = cell.cpu().numpy()
+    dl = np.concatenate([np.asarray(cat_ragged["dl"])[g.sample_order(cat_ragged)],
+                         np.asarray(cat_ragged["inj_dl"])[g.injection_order(cat_ragged)]])
+    rc, rp = orc.sample_cells(lam, dl, nz, zmax)
+    n, near, diff = cell_mismatches(cell, rc, rp)
+    print(f"cells Lambda#{which}: {n} samples in range, {near} within {2e-5} cells of a node, "
+          f"{diff} of those in the neighbouring cell")
+    assert n > 20_000
+
+
 def test_pixel_ids_used_verbatim(torch, g, orc, synth, cat_c1):
     # shifting every sample to another block of pixels changes results exactly as the
     # oracle says (a pixel mix-up would not)

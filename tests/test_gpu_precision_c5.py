@@ -2,16 +2,15 @@
 
 Four builds of the same catalogue are compared with the FP64 oracle: plain or
 compensated (Kahan) FP32 sums inside each work item, and the LOS table stored as FP32
-or as BF16 (interpolated in FP32 either way).  The oracle evaluates per-event ln L one
-event at a time, so sampled (event, Lambda) outputs are checked at full size; ln xi and
-the total need every injection and every event, which takes the oracle several minutes
-per Lambda point, so that comparison runs only with GWC_C5_FULL=1 set.  The printed
-table is the study's result; the FP32 builds must meet the per-event tolerance, the
-BF16 builds only a loose bound (their error is the storage rounding of the LOS table,
-about 2^-9 relative).
+or as BF16 (interpolated in FP32 either way).  Per-event ln L is checked
+at sampled (event, Lambda) pairs against the oracle on those events alone, and ln xi,
+the sum of the per-event terms and the total at the fiducial point against the oracle on
+the whole catalogue (the total before any N_eff flag: at this point some of the 10,000
+events fall below the default threshold).  The printed table is the study's result; the
+FP32 builds must meet the per-event, ln xi and total tolerances, the BF16 builds only a
+loose per-event bound (their error is the storage rounding of the LOS table, about 2^-9
+relative).
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -45,8 +44,8 @@ def test_c5_precision_variants(torch, g, orc, synth):
     for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):     # per-event values ignore them
         sub[k] = cat[k][:1000]
     ref = orc.loglik(sub, lam[LAMBDAS])
-    full = os.environ.get("GWC_C5_FULL") == "1"
-    ref_full = orc.loglik(cat, lam[:1]) if full else None
+    full = True
+    ref_full = orc.loglik(cat, lam[:1])
     lt = torch.tensor(lam, dtype=torch.float64, device="cuda")
     rows, outs = [], {}
     for name, accum, los in (("fp32 LOS, plain sums", 0, g.LOS_F32),
@@ -81,7 +80,7 @@ def test_c5_precision_variants(torch, g, orc, synth):
         print("  " + ", ".join(f"{k} {v:.3e}" if isinstance(v, float) else f"{k} {v}" for k, v in r.items()))
     for r in rows[:2]:
         assert r["per_event_max"] <= 1e-5, r
-        if full:
-            assert r["total"] <= 1e-3, r
+        assert r["ln_xi"] <= 1e-5, r
+        assert r["total"] <= 1e-3, r
     for r in rows[2:]:
         assert r["per_event_max"] <= 2e-2, r

@@ -30,7 +30,10 @@ def test_independent_gaussian_moments_and_adaptation():
     z = (x[:, 0] - mean[0]) / sd[0]
     assert np.mean(z < 1.0) == pytest.approx(0.8413, abs=0.03)
     assert 0.65 < r["accept_stat"].mean() < 0.95
-    assert r["n_calls"] < r["n_leapfrog"].sum()           # the walkers shared their batches
+    # the walkers shared their batches: each recorded transition took as many calls as its
+    # longest walker took leapfrog steps
+    np.testing.assert_array_equal(r["calls"], r["n_leapfrog"].max(axis=1))
+    assert r["calls"].sum() < r["n_leapfrog"].sum()
     assert np.all(np.isfinite(r["lnL"]))
 
 

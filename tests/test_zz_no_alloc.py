@@ -72,3 +72,34 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(torch):
     with pytest.raises(g.GwcError) as e:
         g.sample_terms_noalloc(lam, z, p, z, big, 2.0)
     assert e.value.status == -1 and "scratch limit" in str(e.value)
+
+
+def test_noalloc_out_of_range_pixel_gets_zero_weight(torch, synth):
+    # The entry point never reads the caller's pixel ids on the host, so the kernel checks
+    # them: a sample whose pixel is n_pix (one past the table) or negative reads no LOS row
+    # and gets w = 0, and every other sample keeps its value.
+    import paper_2605_23538_gb300 as g
+    w = synth.scaled("noalloc_pix", 3, ("uniform", 200, 400), 4, 256, 2000, "found")
+    cat = synth.catalogue(w)
+    dev = "cuda"
+    samples = torch.tensor(np.stack([cat["m1"], cat["m2"], cat["dl"], cat["lnpe"]], axis=1), device=dev)
+    inj = torch.tensor(np.stack([cat["inj_m1"], cat["inj_m2"], cat["inj_dl"], cat["inj_lnpd"]], axis=1),
+                       device=dev)
+    los = torch.tensor(cat["los"], device=dev)
+    lam = torch.tensor(synth.FIDUCIAL, dtype=torch.float64, device=dev)
+    pix_np = np.asarray(cat["pix"], dtype=np.int32)
+    a_lnw, a_d, _ = g.sample_terms_noalloc(lam, samples, torch.tensor(pix_np, device=dev), inj, los, cat["z_max"])
+    a_lnw, a_d = a_lnw.cpu().numpy(), a_d.cpu().numpy()
+    fin = np.flatnonzero(np.isfinite(a_lnw[:len(pix_np)]))
+    bad = fin[[0, len(fin) // 2]]
+    pix_bad = pix_np.copy()
+    pix_bad[bad[0]] = cat["los"].shape[0]
+    pix_bad[bad[1]] = -1
+    b_lnw, b_d, _ = g.sample_terms_noalloc(lam, samples, torch.tensor(pix_bad, device=dev), inj, los, cat["z_max"])
+    torch.cuda.synchronize()
+    b_lnw, b_d = b_lnw.cpu().numpy(), b_d.cpu().numpy()
+    assert np.all(np.isneginf(b_lnw[bad])) and np.all(b_d[:, bad] == 0.0)
+    rest = np.ones(len(a_lnw), bool)
+    rest[bad] = False
+    np.testing.assert_array_equal(b_lnw[rest], a_lnw[rest])
+    np.testing.assert_array_equal(b_d[:, rest], a_d[:, rest])
