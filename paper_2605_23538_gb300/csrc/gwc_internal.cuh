@@ -161,7 +161,9 @@ __host__ __device__ inline void stats_to_grad(const T* st, T S1, const LamD& D, 
 // Per-Lambda table block (floats):
 //   [0, 4 NX)          float4 pos[NX]  {hi, lo, D, c2}: P(x_n) = hi + lo; cubic in t on
 //                      segment n: P = P_n + t (D + t (c2 + t c3)), t in [0, 1)
-//   [4 NX, 8 NX)       float4 aux[NX]  {c3, J, dJ/dx * dx, 0} (J Hermite in x)
+//   [4 NX, 8 NX)       float4 aux[NX]  {c3, J_n, d - c, c}: J = J_n + t (d - c) + t^2 c on
+//                      segment n, d = J_{n+1} - J_n, c half the difference of the nodes'
+//                      slopes dJ/dx dx
 //   [8 NX, 8 NX + 4 (NW_WIN + 1))   float4 wval[NW_WIN + 1] {Q_C, Q_beta, Q_J, Q_K}
 //   [.., + 4 (NW_WIN + 1))           float4 wslp[NW_WIN + 1] the same times dQ/dm * h
 //                      (Hermite in m over [m_min, m_min + delta_m])
@@ -209,13 +211,6 @@ __device__ __forceinline__ float rcp(float x) {
   return y;
 }
 
-__device__ __forceinline__ float hermite_val(float2 a, float2 b, float t) {
-  // a = {f0, f0' h}, b = {f1, f1' h}: f0 + t (f0' h + t (c2 + t c3))
-  const float d = b.x - a.x;
-  const float c2 = fmaf(3.f, d, -fmaf(2.f, a.y, b.y));
-  const float c3 = fmaf(-2.f, d, a.y + b.y);
-  return fmaf(t, fmaf(t, fmaf(t, c3, c2), a.y), a.x);
-}
 // derivative with respect to t (multiply by 1/h for d/dm)
 __device__ __forceinline__ float hermite_dt(float2 a, float2 b, float t) {
   const float d = b.x - a.x;
@@ -242,12 +237,26 @@ struct HermiteBasis {
 struct SampleIn {
   float m1, m2, dl, npe2, lm1, lm2;  // detector-frame masses, distance, -log2 pi (the PE
                                      // prior or draw density), log2 m1, log2 m2
+  bool valid = true;                 // false: a lane past the end of its run (its fields
+                                     // hold another sample of the run; it adds nothing)
 };
 
 __device__ __forceinline__ float ld_row(const float* __restrict__ r, int j) { return __ldg(r + j); }
 __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int j) {
   return __bfloat162float(r[j]);
 }
+
+// floor(v) for |v| < 2^22 without a float-to-int conversion (those share the
+// special-function unit's quarter-rate pipe): v + 1.5*2^23 lies in [2^23, 2^24), where
+// the floats are exactly the integers, so the exact sum rounded down is floor(v) +
+// 1.5*2^23.  floor_biased returns that sum; biased_int its integer, biased_float its value
+// (both exact).  Outside |v| < 2^22 (and for NaN) the integer is meaningless but finite;
+// every caller clamps it to a table.
+constexpr float FLOOR_BIAS = 12582912.f;          // 1.5 * 2^23
+constexpr unsigned FLOOR_BIAS_BITS = 0x4B400000u;
+__device__ __forceinline__ float floor_biased(float v) { return __fadd_rd(v, FLOOR_BIAS); }
+__device__ __forceinline__ int biased_int(float f) { return (int)((unsigned)__float_as_int(f) - FLOOR_BIAS_BITS); }
+__device__ __forceinline__ float biased_float(float f) { return f - FLOOR_BIAS; }
 
 // lw2 = log2 of w without the per-Lambda constant c (ln w = lw2 ln 2 + c) and, for GRAD,
 // g = d ln w / d Lambda (natural units, without dc).
@@ -262,21 +271,31 @@ __device__ __forceinline__ float ld_row(const __nv_bfloat16* __restrict__ r, int
 // lam_lb holds log2(O/mix); the accumulator keeps sum w O/mix as its own (max, sum) pair
 // and the FP64 merge subtracts it.  Returns false where w = 0.
 //
+// Control flow.  The sample's cuts (d_L outside the distance table, m2 > m1, source
+// masses outside [m_min, m_max], a zero LOS prior, m2 on the lower mass edge, w = 0) clear
+// a per-lane flag `live` instead of returning, and the function returns early only where
+// sink.any(live) is false: for the warp-wide sinks that is a vote over the warp (one
+// uniform branch, no divergent exits), for per-thread sinks the thread's own flag.  A lane
+// that is not live keeps computing on its own, possibly meaningless, values; every table
+// index is clamped, the smoothing-window branches are taken only by live lanes, its weight
+// is zero and the sink adds none of its derivatives.
+//
 // The gradient is not returned per sample: `sink` receives the sample's weight t
-// relative to the running maximum (after any rescaling) through sink.weight(lw2) and
-// then each derivative through sink.grad(i, value), so the 13 terms are folded into
+// relative to the running reference (after any rescaling) through sink.weight(lw2, live)
+// and then each derivative through sink.grad(i, value), so the 13 terms are folded into
 // their accumulators as soon as they exist (fewer live registers).  Samples whose lw2
-// falls more than 48 below the running maximum (which only grows) skip the derivative
-// work: their weight is below 2^-48 of the sum's largest.
+// falls more than 48 below the reference skip the derivative work: their weight is below
+// 2^-48 of the sum's largest.
 constexpr float GRAD_SKIP = 48.f;
 
 // WITH_LOS = false leaves out the LOS factor (the weight w' of the KDE form, whose LOS
 // prior enters through the grid integral instead).  Every sample whose d_L maps into
 // [0, z_max] reports its z and the LOS cell j it interpolates in through
-// sink.position(z, j), whatever its weight; sink.reached(2) and sink.reached(3) mark the
-// mass-order and mass-support cuts passed, and sink.windows(win1, win2) the whole value
-// about to be formed, with the smoothing-window branches taken (a path census uses them).  MP selects
-// the multi-peak mass model (a second Gaussian in the primary-mass mixture).
+// sink.position(z, j, ok), whatever its weight; sink.reached(2, ok) and sink.reached(3, ok)
+// mark the mass-order and mass-support cuts passed, and sink.windows(win1, win2, ok) the
+// whole value about to be formed, with the smoothing-window branches taken (a path census
+// uses them).  MP selects the multi-peak mass model (a second Gaussian in the
+// primary-mass mixture).
 template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
@@ -289,36 +308,44 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   // error (an exact product by FMA and the constant's own low part), so the LOS-grid
   // position keeps ~1e-7 of a cell
   const float x = s.dl * L.H0c;
-  if (!(x > 0.f) || x > L.xmax) return false;
+  bool live = s.valid && x > 0.f && !(x > L.xmax);
+  if (!sink.any(live)) return false;
   const float sx = s.dl * L.sxa;
   const float sx_lo = fmaf(s.dl, L.sxa, -sx) + s.dl * L.sxa_lo;
 
   // --- d_L -> z: position on the LOS grid from the Hermite table (split precision)
-  const int n = min((int)sx, nx - 2);
+  const int n = min(max(biased_int(floor_biased(sx)), 0), nx - 2);   // floor(sx), in the table
   const float t = (sx - (float)n) + sx_lo;
   const float4 nd = __ldg(pos + n);
   const float4 ax = __ldg(aux + n);
   const float frac = nd.y + t * (nd.z + t * (nd.w + t * ax.x));
-  int j = (int)floorf(nd.x + frac);
-  float tl = (nd.x - (float)j) + frac;
+  const float fj = floor_biased(nd.x + frac);
+  int j = biased_int(fj);
+  float tl = (nd.x - biased_float(fj)) + frac;
   // The rounded sum hi + lo can land on the other side of a node when the position lies
   // within half an ulp of it (1.2e-4 cells near the end of a 2048-node grid); the
   // in-cell fraction tl is accurate to ~1e-7, so the cell follows its sign.
-  if (tl < 0.f) { --j; tl += 1.f; } else if (tl >= 1.f) { ++j; tl -= 1.f; }
-  if (j > nz - 2) { tl += (float)(j - (nz - 2)); j = nz - 2; }
-  if (j < 0) { tl += (float)j; j = 0; }
+  const int dj = tl < 0.f ? -1 : (tl >= 1.f ? 1 : 0);
+  j += dj;
+  tl -= (float)dj;
+  {  // the last cell extends to the end of the grid, the first to its start
+    const int jc = min(max(j, 0), nz - 2);
+    tl += (float)(j - jc);
+    j = jc;
+  }
   const float jt = (float)j + tl;
   const float z = fmaf(jt, L.zstep, jt * L.zstep_lo);   // the step in two floats
-  sink.position(z, j);
-  if (s.m2 > s.m1) return false;
-  sink.reached(2);
+  sink.position(z, j, live);
+  live = live && !(s.m2 > s.m1);
+  sink.reached(2, live);
   const float u = 1.f + z;
   const float ru = rcp(u);
 
-  // --- source-frame masses (the support cuts first: samples outside skip the rest)
+  // --- source-frame masses (the support cuts first: warps with no sample inside skip the rest)
   const float m1s = s.m1 * ru, m2s = s.m2 * ru;
-  if (m1s > L.mmax || m2s < L.mmin) return false;
-  sink.reached(3);
+  live = live && !(m1s > L.mmax || m2s < L.mmin);
+  sink.reached(3, live);
+  if (!sink.any(live)) return false;
   const float lu2 = lg2(u);
   const float lm1s2 = s.lm1 - lu2, lm2s2 = s.lm2 - lu2;
 
@@ -328,7 +355,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     p0 = ld_row(row, j);
     p1 = ld_row(row, j + 1);
     plos = fmaf(tl, p1, (1.f - tl) * p0);
-    if (!(plos > 0.f)) return false;
+    live = live && plos > 0.f;
   }
 
   // p(m1): (1-lam) m^-alpha / Z_P + lam N(m; mu, sig) / Z_G as max + log2(1 + e^-|a-b|);
@@ -355,11 +382,11 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   float den;          // denominators of the product
 
   // smoothing of m2: ln S = -softplus(f), f = dm/m' + dm/(m' - dm)
-  const bool win2 = m2s < L.mw;
+  const bool win2 = live && m2s < L.mw;
   float mp2 = 0.f, i1 = 0.f, i2 = 0.f, f2 = 0.f, ef2 = 0.f;
   if (win2) {
     mp2 = m2s - L.mmin;
-    if (!(mp2 > 0.f)) return false;
+    live = mp2 > 0.f;              // S(m_min) = 0
     i1 = rcp(mp2);
     i2 = rcp(mp2 - L.dm);
     f2 = L.dm_l2 * (i1 + i2);
@@ -369,13 +396,14 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
 
   // normaliser of p(m2 | m1): in the window C(m1) = m1^beta S(m1) Q_C m'^2 / dm, whose
   // S(m1) cancels against p(m1); above it C = C0 + m1^(1+beta) / (1+beta)
-  const bool win1 = m1s < L.mw;
+  const bool win1 = live && m1s < L.mw;
   float Cx, mp1 = 0.f, Qc = 0.f, A = 0.f, dlm = 0.f, wt = 0.f;
   int wk = 0;
   if (win1) {
     mp1 = m1s - L.mmin;
     const float ws = mp1 * L.inv_wh;
-    wk = min((int)ws, NW_WIN - 1);
+    const float fw = floor_biased(ws);
+    wk = min(biased_int(fw), NW_WIN - 1);
     wt = ws - (float)wk;
     const HermiteBasis hb(wt);
     const float4 v0 = __ldg(wval + wk), v1 = __ldg(wval + wk + 1);
@@ -411,13 +439,13 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const float Dp = fmaf(x, ru, u * rE);
   den *= Dp * (1.f + er);
 
-  sink.windows(win1, win2);
+  sink.windows(win1, win2, live);
   lw2 = fmaf(L.gam_m3, lu2, lin) + lg2_acc(plos * mixf * rcp(den));
   lw2 += s.npe2;
-  if (!(lw2 > -INFINITY)) return false;
-  const bool has_grad = sink.weight(lw2);
+  live = live && lw2 > -INFINITY;
+  const bool has_grad = sink.weight(lw2, live);
 
-  if (GRAD && has_grad) {
+  if (GRAD && sink.any(has_grad)) {
     const float lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
     float pa, pb, pb2 = 0.f;                           // mixture responsibilities
     if (!MP) {
@@ -491,9 +519,9 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     const float D2 = fmaf(-1.5f * L.om * (u3m1 + 1.f), rE3, 2.f * rE);
     Gz = fmaf(-D2, invDp, Gz);
 
-    // z depends on H0 and Om through x and the inverted distance relation
-    const float4 ax1 = __ldg(aux + n + 1);
-    const float J = hermite_val(make_float2(ax.y, ax.z), make_float2(ax1.y, ax1.z), t);
+    // z depends on H0 and Om through x and the inverted distance relation; J = dI/dOm at
+    // z(x), a quadratic on the table segment
+    const float J = fmaf(t, fmaf(t, ax.w, ax.z), ax.y);
     sink.grad(S_H0, Gz * x * invDp);
     sink.grad(S_OM, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
     sink.grad(S_A1, pa);
@@ -521,38 +549,47 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     sink.grad(S_SRD, sr * dlp);
     sink.grad(S_SR, sr);
   }
-  return true;
+  return live;
 }
 
-// Sink that folds a sample into the online (max, sums) accumulator
+// Sink that folds a sample into the online (reference, sums) accumulator of its lane;
+// any() votes over the warp, so every lane of the warp must call sample_lnw together
 template <bool GRAD, bool KAHAN, int NS = NP> struct Acc;
 template <bool GRAD, bool KAHAN, int NS = NP>
 struct AccSink {
   Acc<GRAD, KAHAN, NS>& a;
   float t = 0.f;
+  bool hg = false;    // this lane's derivatives are summed
   __device__ __forceinline__ explicit AccSink(Acc<GRAD, KAHAN, NS>& acc) : a(acc) {}
-  __device__ __forceinline__ bool weight(float lw) {
-    t = a.take(lw);
-    return GRAD && !(lw < a.m - GRAD_SKIP);
+  __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
+  __device__ __forceinline__ bool weight(float lw, bool live) {
+    t = a.take(lw, live);
+    hg = GRAD && live && !(lw < a.m - GRAD_SKIP);
+    return hg;
   }
-  __device__ __forceinline__ void grad(int i, float v) { a.g[i] = fmaf(t, v, a.g[i]); }
-  __device__ __forceinline__ void position(float, int) {}
-  __device__ __forceinline__ void reached(int) {}
-  __device__ __forceinline__ void windows(bool, bool) {}
-  __device__ __forceinline__ void lam_edge(float sigma, float lw, float lo) { a.add_other(sigma, t, lw + lo); }
+  __device__ __forceinline__ void grad(int i, float v) {
+    if (hg) a.g[i] = fmaf(t, v, a.g[i]);
+  }
+  __device__ __forceinline__ void position(float, int, bool) {}
+  __device__ __forceinline__ void reached(int, bool) {}
+  __device__ __forceinline__ void windows(bool, bool, bool) {}
+  __device__ __forceinline__ void lam_edge(float sigma, float lw, float lo) {
+    if (hg) a.add_other(sigma, t, lw + lo);
+  }
 };
 
-// Sink that keeps one sample's value and derivatives (per-sample outputs)
+// Sink that keeps one sample's value and derivatives (per-sample outputs; one thread each)
 struct TermSink {
   float g[NP_MAX];
   float lo = 0.f;
   bool edge = false;
   int cell = -1;      // the LOS cell the sample interpolates in (-1: d_L outside [0, z_max])
-  __device__ __forceinline__ bool weight(float) { return true; }
+  __device__ __forceinline__ bool any(bool p) { return p; }
+  __device__ __forceinline__ bool weight(float, bool live) { return live; }
   __device__ __forceinline__ void grad(int i, float v) { g[i] = v; }
-  __device__ __forceinline__ void position(float, int j) { cell = j; }
-  __device__ __forceinline__ void reached(int) {}
-  __device__ __forceinline__ void windows(bool, bool) {}
+  __device__ __forceinline__ void position(float, int j, bool ok) { cell = ok ? j : -1; }
+  __device__ __forceinline__ void reached(int, bool) {}
+  __device__ __forceinline__ void windows(bool, bool, bool) {}
   __device__ __forceinline__ void lam_edge(float sigma, float, float l) {
     g[S_LX] = sigma;
     lo = l;
@@ -560,9 +597,15 @@ struct TermSink {
   }
 };
 
-// Online (max, sum 2^(l-max), sum 2^(2(l-max)), sum 2^(l-max) dl) accumulator, l in
-// log2 units, plus (mO, sO) = (max, sum 2^(l + lo - mO)) of the other-component weights
-// at lambda_peak = 0 or 1 (zero otherwise).  NS statistics (13, or 16 multi-peak).
+// Online accumulator of one lane, l in log2 units: a reference m and the sums
+// s1 = sum 2^(l-m), s2 = sum 2^(2(l-m)), g = sum 2^(l-m) dl, plus (mO, sO) = (max,
+// sum 2^(l + lo - mO)) of the other-component weights at lambda_peak = 0 or 1 (zero
+// otherwise).  NS statistics (13, or 16 multi-peak).  The reference is the value of some
+// summed sample and is raised (rescaling the sums) only when a sample exceeds it by more
+// than RESCALE_HEADROOM, so every term is at most 2^32 and s2 at most 2^64 a term (float
+// holds 2^127); s1 >= 1 once a sample is in.  Partials and merges only use m as a common
+// reference, never as the maximum.
+constexpr float RESCALE_HEADROOM = 32.f;
 template <bool GRAD, bool KAHAN, int NS>
 struct Acc {
   float m = -INFINITY, s1 = 0.f, s2 = 0.f, c1 = 0.f, c2 = 0.f;
@@ -572,13 +615,13 @@ struct Acc {
 #pragma unroll
     for (int i = 0; i < (GRAD ? NS : 1); ++i) g[i] = 0.f;
   }
-  // add a sample of log2 weight lw to the value sums; returns its weight 2^(lw - m)
-  // relative to the (possibly new) running maximum m, rescaling what is already summed
-  __device__ __forceinline__ float take(float lw) {
-    if (lw > m) {
+  // add a sample of log2 weight lw (when live) to the value sums; returns its weight
+  // 2^(lw - m) relative to the (possibly new) reference m, 0 when not live
+  __device__ __forceinline__ float take(float lw, bool live) {
+    if (live && lw > m + RESCALE_HEADROOM) {
       const float sc = ex2(m - lw);   // 0 on the first sample
-      s1 = fmaf(s1, sc, 1.f);
-      s2 = fmaf(s2, sc * sc, 1.f);
+      s1 *= sc;
+      s2 *= sc * sc;
       c1 *= sc;
       c2 *= sc * sc;
       if (GRAD) {
@@ -586,9 +629,8 @@ struct Acc {
         for (int i = 0; i < NS; ++i) g[i] *= sc;
       }
       m = lw;
-      return 1.f;
     }
-    const float tt = ex2(lw - m);
+    const float tt = live ? ex2(lw - m) : 0.f;
     if (KAHAN) {
       float y1 = tt - c1, t1 = s1 + y1;
       c1 = (t1 - s1) - y1;

@@ -232,7 +232,7 @@ template <bool CL>
 __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   namespace cg = cooperative_groups;
   using Sh = ProShape<CL>;
-  extern __shared__ double sdyn[];               // 2 * nx doubles: P_n, D_n
+  extern __shared__ double sdyn[];               // 4 * nx doubles: P_n, D_n, then J_n, J'_n
   __shared__ double sI[ZPANELS + 1], sJ[ZPANELS + 1], sD[ZPANELS + 1], sDp[ZPANELS + 1];
   __shared__ double red[32 * 16];
   __shared__ double sc[32];                      // scalar broadcast
@@ -367,7 +367,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     }
     sdyn[2 * n] = z * pscale;                // P_n
     sdyn[2 * n + 1] = pscale / Dp * dx;      // dP/dx * dx
-    if (n < own1) aux[n] = make_float4(0.f, (float)Jz, (float)(jd / Dp * dx), 0.f);
+    sdyn[2 * nx + n] = Jz;                   // J and dJ/dx * dx at the node
+    sdyn[3 * nx + n] = jd / Dp * dx;
   }
   __syncthreads();
   float4* pos = reinterpret_cast<float4*>(tb);
@@ -381,7 +382,15 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     }
     const float hi = (float)P0;
     pos[n] = make_float4(hi, (float)(P0 - (double)hi), (float)D0, (float)c2);
-    aux[n].x = (float)c3;
+    // J on the segment: the quadratic through J_n and J_{n+1} whose curvature is the mean
+    // of the two nodes' slopes' difference, J = J_n + t (d - c) + t^2 c (error O(dx^3))
+    const double J0 = sdyn[2 * nx + n];
+    double dJ = 0.0, cJ = 0.0;
+    if (n < nx - 1) {
+      dJ = sdyn[2 * nx + n + 1] - J0;
+      cJ = 0.5 * (sdyn[3 * nx + n + 1] - sdyn[3 * nx + n]);
+    }
+    aux[n] = make_float4((float)c3, (float)J0, (float)(dJ - cJ), (float)cJ);
   }
   if constexpr (CL) { pro_sync(); pro_sync(); }   // rank WIN0 reads xmax from rank 0 in between
   return;
@@ -751,12 +760,17 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       const float4* aux = reinterpret_cast<const float4*>(tb + 4 * nx);
       const float4* wv = reinterpret_cast<const float4*>(tb + 8 * nx);
       const float4* ws = wv + (NW_WIN + 1);
-      for (int i = a + lane; i < b; i += 32) {
+      // every lane of the warp runs the same number of iterations (the per-sample
+      // arithmetic votes over the warp); lanes past the end repeat the run's last sample
+      // with valid = false
+      for (int base = a; base < b; base += 32) {
+        const int i = min(base + lane, b - 1);
         SampleIn s;
         const float4 va = s_a[i];
         const float2 vb = s_b[i];
         s.m1 = va.x; s.m2 = va.y; s.dl = va.z; s.npe2 = va.w;
         s.lm1 = vb.x; s.lm2 = vb.y;
+        s.valid = base + lane < b;
         float lw;
         Sink sink(acc);
         if (inj)
@@ -864,12 +878,15 @@ namespace {
 
 struct KdeSink {
   float z = -INFINITY;
-  __device__ __forceinline__ bool weight(float) { return false; }
+  __device__ __forceinline__ bool any(bool p) { return p; }
+  __device__ __forceinline__ bool weight(float, bool) { return false; }
   __device__ __forceinline__ void grad(int, float) {}
   __device__ __forceinline__ void lam_edge(float, float, float) {}
-  __device__ __forceinline__ void position(float zz, int) { z = zz; }
-  __device__ __forceinline__ void reached(int) {}
-  __device__ __forceinline__ void windows(bool, bool) {}
+  __device__ __forceinline__ void position(float zz, int, bool ok) {
+    if (ok) z = zz;
+  }
+  __device__ __forceinline__ void reached(int, bool) {}
+  __device__ __forceinline__ void windows(bool, bool, bool) {}
 };
 
 struct KdeCtx {
@@ -1539,12 +1556,18 @@ cudaError_t launch_sample_terms(const TermsArgs& a, bool bf16, cudaStream_t s) {
 // stages each evaluation reaches (see gwc_path_census in gwc.h for the slots).
 struct CensusSink {
   unsigned c[GWC_CENSUS_SLOTS] = {0};
-  __device__ __forceinline__ bool weight(float) { ++c[7]; w = true; return false; }
+  __device__ __forceinline__ bool any(bool p) { return p; }
+  __device__ __forceinline__ bool weight(float, bool live) {
+    c[7] += live;
+    w = live;
+    return false;
+  }
   __device__ __forceinline__ void grad(int, float) {}
   __device__ __forceinline__ void lam_edge(float, float, float) {}
-  __device__ __forceinline__ void position(float, int) { ++c[1]; }
-  __device__ __forceinline__ void reached(int st) { ++c[st]; }
-  __device__ __forceinline__ void windows(bool a, bool b) {
+  __device__ __forceinline__ void position(float, int, bool ok) { c[1] += ok; }
+  __device__ __forceinline__ void reached(int st, bool ok) { c[st] += ok; }
+  __device__ __forceinline__ void windows(bool a, bool b, bool ok) {
+    if (!ok) return;
     ++c[4];
     w1 = a;
     w2 = b;
@@ -1624,7 +1647,7 @@ __global__ void k_los_cell(const float* z, long long n, int nz, double zmax, int
 
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 2 * (size_t)a.nx;
+  const size_t smem = sizeof(double) * 4 * (size_t)a.nx;
   const bool cl = K <= PRO_CLUSTER_MAX_K;
   if (smem > 48 * 1024) {
     cudaError_t e = cl ? cudaFuncSetAttribute(k_prologue<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
