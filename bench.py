@@ -75,7 +75,7 @@ WORK = {
     "value_nowin1": (3, 2, {"ex2": 1}),                         # C(m1) above the window
     "value_win1": (20, 1, {}),                                  # C(m1) from the window table
     "value_win2": (7, 0, {"rcp": 2, "ex2": 1}),                 # smoothing of m2
-    "weight": (67, 0, {"rcp": 4}),                              # z-chain, J(x), 13 statistics
+    "weight": (61, 0, {"rcp": 4}),                              # z-chain, J(x) quadratic, 13 statistics
     "weight_nowin1": (8, 0, {"rcp": 1}),
     "weight_win1": (48, 0, {"rcp": 5, "ex2": 1}),
     "weight_win2": (9, 0, {"rcp": 1}),
@@ -362,7 +362,18 @@ def hmc_c1(g, synth, stream):
 KDE_K = 16
 
 
-def kde_timing(g, ctx, lam, n_evals, stream):
+# Work of the KDE kernel, counted from its source as lower bounds (gwc_kde_census): one
+# evaluation of the weight w' (the value arithmetic without the LOS factor: the live,
+# in_range, mass_order, support and value stages of WORK less the LOS interpolation, with
+# the closed-form C(m1)) per second-pass sample with a weight, and per grid term d = z_g - z,
+# (c d) d, and the accumulation T += p_LOS(z_g) 2^((c d) d): 4 FP32 operations and one ex2.
+# The first pass's evaluations (which repeat the second's for kept samples) and the
+# bandwidths' order statistics are not charged.
+KDE_WORK_EVAL = (46, {"ex2": 4, "lg2": 2, "rcp": 2, "rsqrt": 1})
+KDE_WORK_TERM = (4, {"ex2": 1})
+
+
+def kde_timing(g, ctx, lam, n_evals, stream, peaks):
     import torch
     k = max(1, min(KDE_K, lam.shape[0]))
     lk = lam[:k].contiguous()
@@ -372,14 +383,26 @@ def kde_timing(g, ctx, lam, n_evals, stream):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     reps = 3
+    ctx.profile_enable(True)
+    ctx.profile_read()
     e0.record(stream)
     for _ in range(reps):
         g.loglik_kde(ctx._ctx, lk, ctx.n_events, stream=stream, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
+    stage_ms, n_calls = ctx.profile_read()
+    ctx.profile_enable(False)
     ms = e0.elapsed_time(e1) / reps
-    return {"K": k, "bandwidth": "scott", "n_grid": 256, "ms_per_call": ms,
-            "value": n_evals * k / (ms / 1e3), "unit": "evals/s (value only)"}
+    kde_ms = stage_ms[1] / max(n_calls, 1)
+    census = ctx.kde_census(lk, stream=stream)
+    fp32 = census["pass2"] * KDE_WORK_EVAL[0] + census["terms"] * KDE_WORK_TERM[0]
+    sfu = {t: census["pass2"] * KDE_WORK_EVAL[1].get(t, 0) + census["terms"] * KDE_WORK_TERM[1].get(t, 0)
+           for t in SFU_TYPES}
+    roof = alu_roofline({"fp32_method": fp32, "fp32_precision": 0, "sfu": sfu}, kde_ms / 1e3, peaks, None)
+    roof["census"] = census
+    roof["work"] = "lower bound: w' once per weighted second-pass sample, 4 FP32 + 1 ex2 per grid term"
+    return {"K": k, "bandwidth": "scott", "n_grid": 256, "ms_per_call": ms, "kde_kernel_ms": kde_ms,
+            "value": n_evals * k / (ms / 1e3), "unit": "evals/s (value only)", "roofline": roof}
 
 
 def multipeak_timing(g, synth, cat, K, n_evals, stream, steps=3):
@@ -592,7 +615,7 @@ def main():
     kde_line = mp_line = None
     if not args.no_extras:
         hmc_line = hmc_c1(g, synth, stream)
-        kde_line = kde_timing(g, ctx, lam, n_s + n_i, stream)
+        kde_line = kde_timing(g, ctx, lam, n_s + n_i, stream, peaks)
         mp_line = multipeak_timing(g, synth, cat, K, n_s + n_i, stream)
 
     base = None

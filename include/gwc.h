@@ -221,6 +221,25 @@ gwc_status gwc_loglik_parts(gwc_ctx* ctx, int32_t K, const double* d_lambda, dou
                             double* d_sum_events, int32_t* d_flags, double* d_grad_events,
                             double* d_grad_ln_xi, void* stream);
 
+/* Combination of event shards (Eq. 3 with the selection function of Eq. 4 as a
+ * Monte-Carlo sum over injections, which splits into the shards' sums): the exchange step
+ * of event sharding.  parts[R][K][5 + 2P] (FP64, row-major) holds, for shard r and point
+ * k, the outputs of that shard's gwc_loglik_parts: d_sum_events, d_ln_xi, d_neff_sel,
+ * d_flags (as a double), the shard's number of events, then (P = 13 or 16) its
+ * d_grad_events and d_grad_ln_xi rows; P = 0 leaves the gradients out.  Receives
+ * lnL_total[K], ln_xi[K] (of the whole injection set), neff_sel[K], flags[K] and, when
+ * P > 0 and grad_total is not NULL, grad_total[K][P], with the formulas of
+ * gwc_loglik_parts; flag bits 0 and 1 carry over, bit 3 follows the merged ln xi, bit 2
+ * (a shard's own selection cut) is dropped (apply a threshold to the merged neff_sel).
+ * on_device = 1: every pointer is device memory and one kernel runs on `stream`
+ * (asynchronous, no allocation); on_device = 0: every pointer is host memory and the
+ * same FP64 arithmetic runs on the calling thread (no CUDA call; stream is ignored).
+ * Shards are combined in index order, so the result does not depend on the device.
+ * GWC_E_INVALID for R < 1, K < 1, P not in {0, 13, 16} or a NULL output. */
+gwc_status gwc_merge_parts(int32_t R, int32_t K, int32_t P, const double* parts, int32_t on_device,
+                           double* lnL_total, double* ln_xi, double* neff_sel, int32_t* flags,
+                           double* grad_total, void* stream);
+
 /* The plain single-Lambda path, kept as the speed-up baseline: the same per-sample
  * arithmetic, one Lambda per launch sequence, every sample re-read from memory for each
  * Lambda, per-sample weights (and, for the gradient, per-sample weighted derivatives)
@@ -385,7 +404,9 @@ gwc_status gwc_sample_terms_noalloc(const double* d_lambda, int64_t n_samples,
 
 /* Per-kernel timing.  While enabled, every call records CUDA events on its stream around
  * its three stages (the prologue kernel, the sample kernel or the plain path's sample
- * passes, and the merge kernel).  gwc_profile_read waits for the recorded events,
+ * passes, and the merge kernel; for gwc_loglik_kde the first stage also holds the
+ * injections' Monte-Carlo sum and the second is the KDE kernel alone).  gwc_profile_read
+ * waits for the recorded events,
  * returns ms[0..2] = summed stage times in milliseconds and *n_calls = calls recorded
  * since the last read, then resets the sums.  Enabling creates the events (no per-call
  * allocation); disabling destroys them.  Not for use inside stream capture. */
@@ -415,6 +436,20 @@ gwc_status gwc_los_cell_index(const float* d_z, int64_t n, int32_t n_z, double z
 #define GWC_CENSUS_N 10
 gwc_status gwc_path_census(gwc_ctx* ctx, int32_t K, const double* d_lambda, uint64_t* d_counts,
                            void* stream);
+
+/* Path census of the KDE form's kernel (measurement only; the paper has no counterpart):
+ * for the K points d_lambda[K][P] (device) and the options kopt (NULL: defaults), runs the
+ * KDE kernel of gwc_loglik_kde once and d_counts[GWC_KDE_CENSUS_N] (device, uint64,
+ * overwritten) receives
+ *   [0] (sample, Lambda) evaluations of the first pass (weights, moments, bandwidth)
+ *   [1] (event, pixel group, Lambda) pairs kept (N_eff and bandwidth tests passed)
+ *   [2] (sample, Lambda) evaluations of the second pass with a weight
+ *   [3] kernel terms summed on the grid (the grid points within 6 h of each of [2])
+ * so that a roofline can charge the kernel its work.  Errors as gwc_loglik_kde; uses the
+ * context's per-call scratch and must not overlap other calls on it. */
+#define GWC_KDE_CENSUS_N 4
+gwc_status gwc_kde_census(gwc_ctx* ctx, int32_t K, const double* d_lambda, const gwc_kde_options* kopt,
+                          uint64_t* d_counts, void* stream);
 
 /* Throughput probes of the arithmetic units (measurement only; the paper has no
  * counterpart): one kernel of `blocks` CTAs x 256 threads on the stream, each thread

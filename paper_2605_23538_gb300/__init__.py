@@ -95,7 +95,7 @@ EXPORTS = ("gwc_default_options", "gwc_create", "gwc_loglik", "gwc_loglik_grad",
            "gwc_sample_terms", "gwc_sample_terms_noalloc", "gwc_graph_create", "gwc_graph_launch",
            "gwc_graph_destroy", "gwc_hmc_create", "gwc_hmc_launch", "gwc_hmc_destroy",
            "gwc_autotune", "gwc_default_kde_options", "gwc_loglik_kde", "gwc_loglik_parts",
-           "gwc_path_census", "gwc_alu_probe")
+           "gwc_path_census", "gwc_kde_census", "gwc_alu_probe", "gwc_merge_parts")
 
 
 def lib():
@@ -162,6 +162,10 @@ def lib():
         L.gwc_loglik_parts.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.gwc_path_census.restype = ctypes.c_int
         L.gwc_path_census.argtypes = [vp, i32, vp, vp, vp]
+        L.gwc_merge_parts.restype = ctypes.c_int
+        L.gwc_merge_parts.argtypes = [i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, vp]
+        L.gwc_kde_census.restype = ctypes.c_int
+        L.gwc_kde_census.argtypes = [vp, i32, vp, ctypes.POINTER(KdeOptions), vp, vp]
         L.gwc_alu_probe.restype = ctypes.c_int
         L.gwc_alu_probe.argtypes = [i32, i32, i32, ctypes.POINTER(d), vp]
         L.gwc_autotune.restype = ctypes.c_int
@@ -418,6 +422,23 @@ def path_census(ctx, lam, stream=None):
     return dict(zip(CENSUS_SLOTS, (int(v) for v in counts.cpu().numpy())))
 
 
+KDE_CENSUS_SLOTS = ("pass1", "kept", "pass2", "terms")
+
+
+def kde_census(ctx, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, stream=None):
+    """gwc_kde_census: the KDE kernel's work for the batch lam [K, P] (first-pass sample
+    evaluations, kept groups, second-pass evaluations, grid terms); a dict keyed by
+    KDE_CENSUS_SLOTS."""
+    import torch
+    lam = _lam_batch(lam)
+    _check_width(ctx, lam.shape[1])
+    counts = torch.zeros(len(KDE_CENSUS_SLOTS), dtype=torch.int64, device=lam.device)
+    o = default_kde_options(bw=bw, n_grid=n_grid, neff_min_pixel=neff_min_pixel)
+    _check(lib().gwc_kde_census(ctx, lam.shape[0], ctypes.c_void_p(lam.data_ptr()), ctypes.byref(o),
+                                ctypes.c_void_p(counts.data_ptr()), _stream_ptr(stream)), ctx)
+    return dict(zip(KDE_CENSUS_SLOTS, (int(v) for v in counts.cpu().numpy())))
+
+
 def alu_probe(unit, blocks, iters, stream=None):
     """gwc_alu_probe: launch one throughput probe of an arithmetic unit (a key of UNITS)
     on the stream; returns the number of operations it performs (the caller times it)."""
@@ -666,6 +687,9 @@ class Context:
 
     def path_census(self, lam, stream=None):
         return path_census(self._ctx, lam, stream)
+
+    def kde_census(self, lam, bw="scott", n_grid=256, neff_min_pixel=2.0, stream=None):
+        return kde_census(self._ctx, lam, bw, n_grid, neff_min_pixel, stream)
 
     def autotune(self, lam, grad=True, stream=None):
         """gwc_autotune on the Lambda batch lam [K, P]: returns the chosen shape."""

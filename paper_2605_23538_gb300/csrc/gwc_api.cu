@@ -846,38 +846,24 @@ void gwc_default_kde_options(gwc_kde_options* o) {
   o->neff_min_pixel = 2.0;
 }
 
-gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const gwc_kde_options* kopt,
-                          double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
-                          double* d_neff_sel, double* d_lnL_total, int32_t* d_flags, void* stream) {
-  gwc_status st = check_call(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel,
-                             d_lnL_total, d_flags);
-  if (st != GWC_OK) return st;
-  gwc_kde_options ko;
-  gwc_default_kde_options(&ko);
-  if (kopt) ko = *kopt;
-  if (ko.bw_rule < GWC_BW_SCOTT || ko.bw_rule > GWC_BW_BIWEIGHT)
+namespace {
+gwc_status kde_options_check(gwc_ctx* c, const gwc_kde_options* kopt, gwc_kde_options* ko) {
+  gwc_default_kde_options(ko);
+  if (kopt) *ko = *kopt;
+  if (ko->bw_rule < GWC_BW_SCOTT || ko->bw_rule > GWC_BW_BIWEIGHT)
     return fail(c, GWC_E_INVALID, "bw_rule must be GWC_BW_SCOTT, GWC_BW_SILVERMAN or GWC_BW_BIWEIGHT");
-  if (ko.n_grid < 2 || ko.n_grid > 65536) return fail(c, GWC_E_INVALID, "n_grid must be in [2, 65536]");
-  if (!(ko.neff_min_pixel >= 0.0)) return fail(c, GWC_E_INVALID, "neff_min_pixel must be >= 0");
+  if (ko->n_grid < 2 || ko->n_grid > 65536) return fail(c, GWC_E_INVALID, "n_grid must be in [2, 65536]");
+  if (!(ko->neff_min_pixel >= 0.0)) return fail(c, GWC_E_INVALID, "neff_min_pixel must be >= 0");
   if (c->bf16) return fail(c, GWC_E_UNSUPPORTED, "the KDE form needs the LOS table stored as FP32");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = kde_prepare(c, ko.n_grid, s);
-  if (st != GWC_OK) return st;
-  cudaError_t pe = prof_mark(c, 0, s);
-  if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
-  st = run_prologue(c, K, d_lambda, false, s, c->counter);
-  if (st != GWC_OK) return st;
-  if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
-  const int64_t ng = (int64_t)c->h_groups.size();
-  // the selection term: the Monte-Carlo sum over the injections only
-  st = launch_fused_items(c, K, false, c->kde_sched_inj, c->n_items - c->inj_item0, c->kde_partials,
-                          c->kde_stride, ng, s);
-  if (st != GWC_OK) return st;
+  return GWC_OK;
+}
+
+KdeArgs kde_args(gwc_ctx* c, const gwc_kde_options& ko, int32_t K) {
   KdeArgs ka;
   ka.smp = c->smp;
   ka.lm = c->kde_lm;
   ka.groups = c->kde_groups;
-  ka.n_groups = (int)ng;
+  ka.n_groups = (int)c->h_groups.size();
   ka.pgrid = c->kde_pgrid;
   ka.G = ko.n_grid;
   ka.dzg = (float)(c->z_max / (ko.n_grid - 1));
@@ -892,6 +878,33 @@ gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const g
   ka.partials = c->kde_partials;
   ka.stride = (int)c->kde_stride;
   ka.mp = c->mp ? 1 : 0;
+  return ka;
+}
+}  // namespace
+
+gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const gwc_kde_options* kopt,
+                          double* d_lnL_event, double* d_neff_event, double* d_ln_xi,
+                          double* d_neff_sel, double* d_lnL_total, int32_t* d_flags, void* stream) {
+  gwc_status st = check_call(c, K, d_lambda, d_lnL_event, d_neff_event, d_ln_xi, d_neff_sel,
+                             d_lnL_total, d_flags);
+  if (st != GWC_OK) return st;
+  gwc_kde_options ko;
+  if ((st = kde_options_check(c, kopt, &ko)) != GWC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = kde_prepare(c, ko.n_grid, s);
+  if (st != GWC_OK) return st;
+  cudaError_t pe = prof_mark(c, 0, s);
+  if (pe != cudaSuccess) return cuda_fail(c, pe, "profile event");
+  st = run_prologue(c, K, d_lambda, false, s, c->counter);
+  if (st != GWC_OK) return st;
+  const int64_t ng = (int64_t)c->h_groups.size();
+  // the selection term: the Monte-Carlo sum over the injections only (profiled with the
+  // prologue, so that the second stage is the KDE kernel alone)
+  st = launch_fused_items(c, K, false, c->kde_sched_inj, c->n_items - c->inj_item0, c->kde_partials,
+                          c->kde_stride, ng, s);
+  if (st != GWC_OK) return st;
+  if ((pe = prof_mark(c, 1, s)) != cudaSuccess) return cuda_fail(c, pe, "profile event");
+  const KdeArgs ka = kde_args(c, ko, K);
   cudaError_t e = launch_kde(ka, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "KDE launch");
   if ((e = prof_mark(c, 2, s)) != cudaSuccess) return cuda_fail(c, e, "profile event");
@@ -1140,6 +1153,43 @@ gwc_status gwc_path_census(gwc_ctx* c, int32_t K, const double* d_lambda, uint64
   ca.mp = c->mp ? 1 : 0;
   cudaError_t e = launch_census(ca, c->bf16, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "census launch");
+  return GWC_OK;
+}
+
+gwc_status gwc_merge_parts(int32_t R, int32_t K, int32_t P, const double* parts, int32_t on_device,
+                           double* lnL_total, double* ln_xi, double* neff_sel, int32_t* flags,
+                           double* grad_total, void* stream) {
+  if (R < 1 || K < 1) return fail(nullptr, GWC_E_INVALID, "R and K must be >= 1");
+  if (P != 0 && P != NP && P != NP_MP) return fail(nullptr, GWC_E_INVALID, "P must be 0, 13 or 16");
+  if (!parts || !lnL_total || !ln_xi || !neff_sel || !flags) return fail(nullptr, GWC_E_INVALID, "NULL pointer");
+  if (!on_device) {
+    for (int k = 0; k < K; ++k) merge_parts_point(R, K, P, parts, k, lnL_total, ln_xi, neff_sel, flags, grad_total);
+    return GWC_OK;
+  }
+  const cudaError_t e = launch_merge_parts(R, K, P, parts, lnL_total, ln_xi, neff_sel, flags, grad_total,
+                                           static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, GWC_E_CUDA, std::string("merge_parts launch: ") + cudaGetErrorString(e));
+  return GWC_OK;
+}
+
+gwc_status gwc_kde_census(gwc_ctx* c, int32_t K, const double* d_lambda, const gwc_kde_options* kopt,
+                          uint64_t* d_counts, void* stream) {
+  static_assert(GWC_KDE_CENSUS_N == KDE_CENSUS_SLOTS, "KDE census slots");
+  if (!live(c)) return fail(nullptr, GWC_E_INVALID, "invalid or destroyed context");
+  if (K < 1 || K > c->opt.max_K) return fail(c, GWC_E_INVALID, "K must be in [1, max_K]");
+  if (!d_lambda || !d_counts) return fail(c, GWC_E_INVALID, "NULL pointer");
+  gwc_kde_options ko;
+  gwc_status st = kde_options_check(c, kopt, &ko);
+  if (st != GWC_OK) return st;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GWC_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = kde_prepare(c, ko.n_grid, s)) != GWC_OK) return st;
+  if ((st = run_prologue(c, K, d_lambda, false, s)) != GWC_OK) return st;
+  cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * GWC_KDE_CENSUS_N, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "census reset");
+  KdeArgs ka = kde_args(c, ko, K);
+  ka.census = reinterpret_cast<unsigned long long*>(d_counts);
+  if ((e = launch_kde(ka, s)) != cudaSuccess) return cuda_fail(c, e, "KDE census launch");
   return GWC_OK;
 }
 

@@ -29,8 +29,9 @@ constexpr double C_KMS = 299792.458;
 constexpr int WARPS = 8;             // warps per CTA of the sample kernels
 constexpr int THREADS = WARPS * 32;
 constexpr int NW_WIN = 128;          // panels of the smoothing-window tables
-constexpr int PSTRIDE = 21;          // floats per partial sum: m, s1, s2, g[16], mO, sO
-constexpr int PART_MO = 3 + NP_MAX, PART_SO = 4 + NP_MAX;   // where mO, sO sit
+constexpr int PSTRIDE = 23;          // floats per partial sum: m, s1, s2, g[16], mO, sO, mO2, sO2
+constexpr int PART_MO = 3 + NP_MAX, PART_SO = 4 + NP_MAX;     // where mO, sO sit
+constexpr int PART_MO2 = 5 + NP_MAX, PART_SO2 = 6 + NP_MAX;   // the second pair (multi-peak)
 constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the prologue
 
 // The multi-peak model appends the higher-mass Gaussian and the lower one's share of
@@ -80,13 +81,21 @@ struct __align__(16) LamF {
   float inv_lam, inv_1ml, dm_l2, zstep_lo;   // dm log2(e) formed in FP64; z_max/(n_z-1) - zstep
   float alpha_lo, beta_lo, eps_b_lo, gpk_lo;   // alpha, beta, 1+beta, gamma+kappa less their
                                                // float values (they multiply logs of up to ~8)
-  float mu2, inv_sig2, lc2, pad0;         // multi-peak: the high peak, log2 of its weight
-                                          // lam (1-lam1)/(sig2 sqrt(2 pi) Z_G2) less R
+  float mu2, inv_sig2, lc2, lam_sig;      // multi-peak: the high peak, log2 of its weight
+                                          // lam (1-lam1)/(sig2 sqrt(2 pi) Z_G2) less R;
+                                          // lam_sig = +1 / -1 at lambda_peak = 1 / 0, else 0
+  float lam1_edge, o2_hi, o2_l2, lb1_2;   // multi-peak, lam1 at 0 or 1 with lam > 0: the
+                                          // other peak's log2 weight o2_l2 = log2(lam /
+                                          // (sig sqrt(2 pi) Z_G)) less R of the high (o2_hi
+                                          // = 1, lam1 = 1) or the low peak; at lam = 0 the
+                                          // peaks' log2 weights without lam: lb1_2, lc1_2
+  float lc1_2, pad1, pad2, pad3;
 };
-static_assert(sizeof(LamF) == 60 * 4, "LamF layout");
+static_assert(sizeof(LamF) == 68 * 4, "LamF layout");
 
 // FP64 constants of one Lambda point for the merge: ln w = (per-sample term) + c.
-// lam_sigma = +1 at lambda_peak = 1, -1 at lambda_peak = 0, else 0 (see Acc).
+// lam_sigma = +1 at lambda_peak = 1, -1 at lambda_peak = 0, else 0 (see Acc); for the
+// multi-peak model lam1_sigma the same for lambda_low (0 when lambda_peak = 0).
 struct LamD {
   double c;
   double dc[NP_MAX];
@@ -96,9 +105,8 @@ struct LamD {
   double invH0, dZPa, dZPmin, dZPmax, dZGmin, dZGmax, dZGmu, dZGsig;
   double inv_sig, inv_lam, inv_1ml, gpk_inv1zp;
   // multi-peak (mp = 1): the high peak's d ln Z_G2 / d(m_min, m_max, mu2, sig2), 1/sig2,
-  // 1/lam1, 1/(1 - lam1); lam_bound = 1 when lam or lam1 sits at 0 or 1, where the
-  // multi-peak gradient leaves their two components undefined (NaN)
-  int32_t mp, lam_bound;
+  // 1/lam1, 1/(1 - lam1) (a reciprocal is 0 where its weight is 0)
+  int32_t mp, lam1_sigma;
   double dZG2min, dZG2max, dZG2mu, dZG2sig, inv_sig2, inv_lam1, inv_1ml1;
   // -ln N'_z and its gamma, kappa, z_p derivatives, written by a prologue CTA of their own
   double cz, dcz[3];
@@ -128,9 +136,14 @@ __host__ __device__ inline void stats_to_grad(const T* st, T S1, const LamD& D, 
     G[P_SIG] = (T)D.inv_sig * (st[S_SIG] - B1) - (T)D.dZGsig * B1;
     G[P_MU2] = (T)D.inv_sig2 * st[S_MU2] - (T)D.dZG2mu * B2;
     G[P_SIG2] = (T)D.inv_sig2 * (st[S_SIG2] - B2) - (T)D.dZG2sig * B2;
-    // d ln mix / d lam = (pb + pb2)/lam - pa/(1-lam); d / d lam1 = pb/lam1 - pb2/(1-lam1)
-    G[P_LAM] = D.lam_bound ? (T)NAN : (T)D.inv_lam * (B1 + B2) - (T)D.inv_1ml * A1;
-    G[P_LAM1] = D.lam_bound ? (T)NAN : (T)D.inv_lam1 * B1 - (T)D.inv_1ml1 * B2;
+    // d ln mix / d lam = (pb + pb2)/lam - pa/(1-lam); d / d lam1 = pb/lam1 - pb2/(1-lam1).
+    // At a bound the term whose weight is 0 has 0 responsibility and a 0 reciprocal, and
+    // what remains is the one-sided derivative less the other component's share, which
+    // the caller subtracts (sigma times the other-component sum, see Acc): at lam = 1,
+    // S1 - sum t P/mix; at lam = 0, sum t (lam1 G + (1-lam1) G2)/P - S1; at lam1 = 1,
+    // sum t pb - sum t lam G2/mix; at lam1 = 0, sum t lam G/mix - sum t pb2
+    G[P_LAM] = (T)D.inv_lam * (B1 + B2) - (T)D.inv_1ml * A1;
+    G[P_LAM1] = (T)D.inv_lam1 * B1 - (T)D.inv_1ml1 * B2;
     G[P_GAM] = LN2 * (st[S_LU] - st[S_SRD]);
     G[P_KAP] = -LN2 * st[S_SRD];
     G[P_ZP] = (T)D.gpk_inv1zp * st[S_SR];
@@ -295,8 +308,10 @@ constexpr float GRAD_SKIP = 48.f;
 // mark the mass-order and mass-support cuts passed, and sink.windows(win1, win2, ok) the
 // whole value about to be formed, with the smoothing-window branches taken (a path census
 // uses them).  MP selects the multi-peak mass model (a second Gaussian in the
-// primary-mass mixture).
-template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false>
+// primary-mass mixture).  EDGE = false leaves out the mixture-bound code (the other-
+// component sums and sigma in S_LX); a caller may pass it only for Lambda points with
+// L.lam_edge = 0 (and L.lam1_edge = 0 for the multi-peak model).
+template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false, bool EDGE = true>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
                                            const float4* __restrict__ pos,
@@ -444,8 +459,32 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   lw2 += s.npe2;
   live = live && lw2 > -INFINITY;
   const bool has_grad = sink.weight(lw2, live);
+  // at a mixture bound every live sample adds to the other-component sum, whatever its
+  // weight (its weight under the absent component can be large)
+  const bool edge = EDGE && (L.lam_edge != 0.f || (MP && L.lam1_edge != 0.f));
 
-  if (GRAD && sink.any(has_grad)) {
+  if (GRAD && sink.any(has_grad || (edge && live))) {
+    // other-component sums at the mixture's bounds (the same branch for every lane of a
+    // Lambda point): log2 of O/mix for the component whose weight is 0
+    if (EDGE && L.lam_edge != 0.f) {
+      float lo;
+      if (!MP) {
+        lo = L.lam >= 1.f ? fmaf(-L.alpha, lm1s2, L.la0_2) - b2             // mix = G: P/G
+                          : fmaf(-HALF_LOG2EF * zz, zz, L.lb0_2) - a2;      // mix = P: G/P
+      } else if (L.lam >= 1.f) {                                            // P/mix
+        lo = fmaf(-L.alpha, lm1s2, L.la0_2) - (mx + lg2(mixf));
+      } else {                                          // mix = P: (lam1 G + (1-lam1) G2)/P
+        const float q1 = fmaf(-HALF_LOG2EF * zz, zz, L.lb1_2);
+        const float q2 = fmaf(-HALF_LOG2EF * zz2, zz2, L.lc1_2);
+        const float qm = fmaxf(q1, q2);
+        lo = qm + lg2(ex2(q1 - qm) + ex2(q2 - qm)) - (mx + lg2(mixf));
+      }
+      sink.other(0, lw2, lo);
+    }
+    if (EDGE && MP && L.lam1_edge != 0.f) {             // lam G2/mix (lam1 = 1) or lam G/mix
+      const float zo = L.o2_hi != 0.f ? zz2 : zz;
+      sink.other(1, lw2, fmaf(-HALF_LOG2EF * zo, zo, L.o2_l2) - (mx + lg2(mixf)));
+    }
     const float lm1s = lm1s2 * LN2F, lm2s = lm2s2 * LN2F;
     float pa, pb, pb2 = 0.f;                           // mixture responsibilities
     if (!MP) {
@@ -520,34 +559,22 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     Gz = fmaf(-D2, invDp, Gz);
 
     // z depends on H0 and Om through x and the inverted distance relation; J = dI/dOm at
-    // z(x), a quadratic on the table segment
+    // z(x), a quadratic on the table segment.  The statistics go to the sink in pairs
+    // (packed FP32 pairs in the accumulator).
     const float J = fmaf(t, fmaf(t, ax.w, ax.z), ax.y);
-    sink.grad(S_H0, Gz * x * invDp);
-    sink.grad(S_OM, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
-    sink.grad(S_A1, pa);
-    sink.grad(S_AL, pa * lm1s2);
-    sink.grad(S_BE, lm2s - dlnC_db);
-    sink.grad(S_MMIN, dS1_dmin - dS2_dm - dlnC_dmin);
-    sink.grad(S_DM, dS1_ddm + dS2_ddm - dlnC_ddm);
+    sink.grad2(S_H0, Gz * x * invDp, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
+    // S_LX: pb, or sigma at lambda_peak = 1 / 0 for the single-peak model (the merge takes
+    // the lambda derivative from it and the other-component sum)
+    sink.grad2(S_A1, pa, (EDGE && !MP && L.lam_edge != 0.f) ? L.lam_sig : pb);
+    sink.grad2(S_AL, pa * lm1s2, lm2s - dlnC_db);
+    sink.grad2(S_MMIN, dS1_dmin - dS2_dm - dlnC_dmin, dS1_ddm + dS2_ddm - dlnC_ddm);
     const float pbz = pb * zz;
-    sink.grad(S_MU, pbz);
-    sink.grad(S_SIG, pbz * zz);
-    if (MP) {
-      sink.grad(S_LX, pb);
-      const float pbz2 = pb2 * zz2;
-      sink.grad(S_MU2, pbz2);
-      sink.grad(S_SIG2, pbz2 * zz2);
-      sink.grad(S_LX2, pb2);
-    } else if (L.lam_edge == 0.f) {
-      sink.grad(S_LX, pb);
-    } else if (L.lam >= 1.f) {                                    // mix = G: 1 - P/G
-      sink.lam_edge(1.f, lw2, fmaf(-L.alpha, lm1s2, L.la0_2) - b2);
-    } else {                                                      // mix = P: G/P - 1
-      sink.lam_edge(-1.f, lw2, fmaf(-HALF_LOG2EF * zz, zz, L.lb0_2) - a2);
-    }
-    sink.grad(S_LU, lu2);
-    sink.grad(S_SRD, sr * dlp);
-    sink.grad(S_SR, sr);
+    sink.grad2(S_MU, pbz, pbz * zz);
+    sink.grad2(S_LU, lu2, sr * dlp);
+    const float pbz2 = pb2 * zz2;                      // 0 for the single-peak model
+    sink.grad2(S_SR, sr, pbz2);                        // S_SR, S_MU2
+    if (MP) sink.grad2(S_SIG2, pbz2 * zz2, pb2);       // S_SIG2, S_LX2
+
   }
   return live;
 }
@@ -560,61 +587,72 @@ struct AccSink {
   Acc<GRAD, KAHAN, NS>& a;
   float t = 0.f;
   bool hg = false;    // this lane's derivatives are summed
+  bool lv = false;    // this lane's sample has a weight
   __device__ __forceinline__ explicit AccSink(Acc<GRAD, KAHAN, NS>& acc) : a(acc) {}
   __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
   __device__ __forceinline__ bool weight(float lw, bool live) {
     t = a.take(lw, live);
+    lv = live;
     hg = GRAD && live && !(lw < a.m - GRAD_SKIP);
     return hg;
   }
-  __device__ __forceinline__ void grad(int i, float v) {
-    if (hg) a.g[i] = fmaf(t, v, a.g[i]);
+  // statistics i and i + 1 (i even) as one packed FP32 pair
+  __device__ __forceinline__ void grad2(int i, float v0, float v1) {
+    if (hg) a.g2[i >> 1] = __ffma2_rn(make_float2(t, t), make_float2(v0, v1), a.g2[i >> 1]);
   }
   __device__ __forceinline__ void position(float, int, bool) {}
   __device__ __forceinline__ void reached(int, bool) {}
   __device__ __forceinline__ void windows(bool, bool, bool) {}
-  __device__ __forceinline__ void lam_edge(float sigma, float lw, float lo) {
-    if (hg) a.add_other(sigma, t, lw + lo);
+  __device__ __forceinline__ void other(int q, float lw, float lo) {
+    if (lv) a.add_other(q, lw + lo);
   }
 };
 
 // Sink that keeps one sample's value and derivatives (per-sample outputs; one thread each)
 struct TermSink {
   float g[NP_MAX];
-  float lo = 0.f;
-  bool edge = false;
+  float lo[2] = {0.f, 0.f};     // log2 of O/mix at the mixture's bounds (see sample_lnw)
+  bool edge[2] = {false, false};
   int cell = -1;      // the LOS cell the sample interpolates in (-1: d_L outside [0, z_max])
   __device__ __forceinline__ bool any(bool p) { return p; }
   __device__ __forceinline__ bool weight(float, bool live) { return live; }
-  __device__ __forceinline__ void grad(int i, float v) { g[i] = v; }
+  __device__ __forceinline__ void grad2(int i, float v0, float v1) {
+    g[i] = v0;
+    g[i + 1] = v1;
+  }
   __device__ __forceinline__ void position(float, int j, bool ok) { cell = ok ? j : -1; }
   __device__ __forceinline__ void reached(int, bool) {}
   __device__ __forceinline__ void windows(bool, bool, bool) {}
-  __device__ __forceinline__ void lam_edge(float sigma, float, float l) {
-    g[S_LX] = sigma;
-    lo = l;
-    edge = true;
+  __device__ __forceinline__ void other(int q, float, float l) {
+    lo[q] = l;
+    edge[q] = true;
   }
 };
 
 // Online accumulator of one lane, l in log2 units: a reference m and the sums
-// s1 = sum 2^(l-m), s2 = sum 2^(2(l-m)), g = sum 2^(l-m) dl, plus (mO, sO) = (max,
-// sum 2^(l + lo - mO)) of the other-component weights at lambda_peak = 0 or 1 (zero
-// otherwise).  NS statistics (13, or 16 multi-peak).  The reference is the value of some
-// summed sample and is raised (rescaling the sums) only when a sample exceeds it by more
-// than RESCALE_HEADROOM, so every term is at most 2^32 and s2 at most 2^64 a term (float
-// holds 2^127); s1 >= 1 once a sample is in.  Partials and merges only use m as a common
+// s1 = sum 2^(l-m), s2 = sum 2^(2(l-m)), g = sum 2^(l-m) dl (as packed pairs g2), plus
+// (mO, sO) = (max, sum 2^(l + lo - mO)) of the other-component weights at a mixture bound
+// (one pair, two for the multi-peak model's lambda_peak and lambda_low; zero otherwise).
+// NS statistics (13, or 16 multi-peak).  The reference is the value of some summed sample
+// and is raised (rescaling the sums) only when a sample exceeds it by more than
+// RESCALE_HEADROOM, so every term is at most 2^32 and s2 at most 2^64 a term (float holds
+// 2^127); s1 >= 1 once a sample is in.  Partials and merges only use m as a common
 // reference, never as the maximum.
 constexpr float RESCALE_HEADROOM = 32.f;
 template <bool GRAD, bool KAHAN, int NS>
 struct Acc {
+  static constexpr int NG2 = GRAD ? (NS + 1) / 2 : 1;   // packed statistic pairs
+  static constexpr int NO = NS > NP ? 2 : 1;            // other-component pairs
   float m = -INFINITY, s1 = 0.f, s2 = 0.f, c1 = 0.f, c2 = 0.f;
-  float mO = -INFINITY, sO = 0.f;
-  float g[GRAD ? NS : 1];
+  float mO[NO], sO[NO];
+  float2 g2[NG2];
   __device__ __forceinline__ Acc() {
 #pragma unroll
-    for (int i = 0; i < (GRAD ? NS : 1); ++i) g[i] = 0.f;
+    for (int i = 0; i < NG2; ++i) g2[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NO; ++q) { mO[q] = -INFINITY; sO[q] = 0.f; }
   }
+  __device__ __forceinline__ float g(int i) const { return (i & 1) ? g2[i >> 1].y : g2[i >> 1].x; }
   // add a sample of log2 weight lw (when live) to the value sums; returns its weight
   // 2^(lw - m) relative to the (possibly new) reference m, 0 when not live
   __device__ __forceinline__ float take(float lw, bool live) {
@@ -626,7 +664,7 @@ struct Acc {
       c2 *= sc * sc;
       if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < NS; ++i) g[i] *= sc;
+        for (int i = 0; i < NG2; ++i) g2[i] = __fmul2_rn(g2[i], make_float2(sc, sc));
       }
       m = lw;
     }
@@ -644,19 +682,18 @@ struct Acc {
     }
     return tt;
   }
-  // lambda_peak = 1 or 0: sigma t, and the other component's weight 2^l in (mO, sO)
-  __device__ __forceinline__ void add_other(float sigma, float tt, float l) {
-    g[S_LX] = fmaf(sigma, tt, g[S_LX]);
-    if (l > mO) {
-      sO = fmaf(sO, ex2(mO - l), 1.f);
-      mO = l;
+  // the other component's weight 2^l at a mixture bound, into pair q
+  __device__ __forceinline__ void add_other(int q, float l) {
+    if (l > mO[q]) {
+      sO[q] = fmaf(sO[q], ex2(mO[q] - l), 1.f);
+      mO[q] = l;
     } else {
-      sO += ex2(l - mO);
+      sO[q] += ex2(l - mO[q]);
     }
   }
   // merge another lane's sums (fixed shuffle tree keeps the result deterministic)
-  __device__ __forceinline__ void merge(float om, float os1, float os2, const float* og,
-                                        float omO = -INFINITY, float osO = 0.f) {
+  __device__ __forceinline__ void merge(float om, float os1, float os2, const float2* og2,
+                                        const float* omO, const float* osO) {
     const float M = fmaxf(m, om);
     if (M > -INFINITY) {
       const float sa = ex2(m - M), sb = ex2(om - M);
@@ -664,15 +701,19 @@ struct Acc {
       s2 = s2 * sa * sa + os2 * sb * sb;
       if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < NS; ++i) g[i] = g[i] * sa + og[i] * sb;
+        for (int i = 0; i < NG2; ++i)
+          g2[i] = __ffma2_rn(g2[i], make_float2(sa, sa), __fmul2_rn(og2[i], make_float2(sb, sb)));
       }
       m = M;
     }
     if (GRAD) {
-      const float MO = fmaxf(mO, omO);
-      if (MO > -INFINITY) {
-        sO = sO * ex2(mO - MO) + osO * ex2(omO - MO);
-        mO = MO;
+#pragma unroll
+      for (int q = 0; q < NO; ++q) {
+        const float MO = fmaxf(mO[q], omO[q]);
+        if (MO > -INFINITY) {
+          sO[q] = sO[q] * ex2(mO[q] - MO) + osO[q] * ex2(omO[q] - MO);
+          mO[q] = MO;
+        }
       }
     }
   }

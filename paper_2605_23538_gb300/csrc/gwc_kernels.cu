@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       ld->cz = 0.0;
       for (int i = 0; i < NP_MAX; ++i) ld->dc[i] = 0.0;
       ld->mp = mp ? 1 : 0;
-      ld->lam_bound = 0;
+      ld->lam1_sigma = 0;
       for (int i = 0; i < 3; ++i) ld->dcz[i] = 0.0;
       ld->flag = 1;
       ld->lam_sigma = 0;
@@ -624,8 +624,18 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.inv_dm = dm > 0.0 ? (float)(1.0 / dm) : 0.f;
     f.invH0 = (float)(1.0 / H0);
     f.inv1zp = (float)(1.0 / (1.0 + zp));
-    f.lam_edge = (mp || (lam > 0.0 && lam < 1.0)) ? 0.f : 1.f;
+    f.lam_edge = (lam > 0.0 && lam < 1.0) ? 0.f : 1.f;
     f.lam = (float)lam;
+    f.lam_sig = lam >= 1.0 ? 1.f : (lam <= 0.0 ? -1.f : 0.f);
+    // multi-peak bounds: lam1 at 0 or 1 (with lam > 0) takes the other peak's weight lam G2
+    // (lam1 = 1) or lam G (lam1 = 0); at lam = 0 the mixture of the two peaks without lam
+    const bool e1 = mp && lam > 0.0 && !(lam1 > 0.0 && lam1 < 1.0);
+    f.lam1_edge = e1 ? 1.f : 0.f;
+    f.o2_hi = lam1 >= 1.0 ? 1.f : 0.f;
+    f.o2_l2 = !e1 ? 0.f
+                  : (float)((log(lam) - (lam1 >= 1.0 ? lnsig2pi2 + lnZG2 : lnsig2pi + lnZG)) * LOG2E - R);
+    f.lb1_2 = mp && lam1 > 0.0 ? (float)((log(lam1) - lnsig2pi - lnZG) * LOG2E - R) : -INFINITY;
+    f.lc1_2 = mp && lam1 < 1.0 ? (float)((log1p(-lam1) - lnsig2pi2 - lnZG2) * LOG2E - R) : -INFINITY;
     f.dZPa = (float)dZPa;
     f.dZPmin = (float)dZPmin;
     f.dZPmax = (float)dZPmax;
@@ -662,9 +672,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     }
     for (int i = 0; i < NP_MAX; ++i) ld->dc[i] = dc[i];
     ld->flag = 0;
-    ld->lam_sigma = mp ? 0 : (lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0));
+    ld->lam_sigma = lam >= 1.0 ? 1 : (lam <= 0.0 ? -1 : 0);
     ld->mp = mp ? 1 : 0;
-    ld->lam_bound = mp && !(lam > 0.0 && lam < 1.0 && lam1 > 0.0 && lam1 < 1.0) ? 1 : 0;
+    ld->lam1_sigma = e1 ? (lam1 >= 1.0 ? 1 : -1) : 0;
     ld->dZG2min = dZG2min;
     ld->dZG2max = dZG2max;
     ld->dZG2mu = dZG2mu;
@@ -762,37 +772,51 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       const float4* ws = wv + (NW_WIN + 1);
       // every lane of the warp runs the same number of iterations (the per-sample
       // arithmetic votes over the warp); lanes past the end repeat the run's last sample
-      // with valid = false
-      for (int base = a; base < b; base += 32) {
-        const int i = min(base + lane, b - 1);
-        SampleIn s;
-        const float4 va = s_a[i];
-        const float2 vb = s_b[i];
-        s.m1 = va.x; s.m2 = va.y; s.dl = va.z; s.npe2 = va.w;
-        s.lm1 = vb.x; s.lm2 = vb.y;
-        s.valid = base + lane < b;
-        float lw;
-        Sink sink(acc);
-        if (inj)
-          sample_lnw<GRAD, float, Sink, true, MP>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
-        else
-          sample_lnw<GRAD, RowT, Sink, true, MP>(L, s, reinterpret_cast<const RowT*>(A.los) + (size_t)s_pix[i] * nz,
-                                                 nz, pos, aux, nx, wv, ws, lw, sink);
-      }
+      // with valid = false.  Points on a mixture bound take their own instance of the loop.
+      auto sweep = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        for (int base = a; base < b; base += 32) {
+          const int i = min(base + lane, b - 1);
+          SampleIn s;
+          const float4 va = s_a[i];
+          const float2 vb = s_b[i];
+          s.m1 = va.x; s.m2 = va.y; s.dl = va.z; s.npe2 = va.w;
+          s.lm1 = vb.x; s.lm2 = vb.y;
+          s.valid = base + lane < b;
+          float lw;
+          Sink sink(acc);
+          if (inj)
+            sample_lnw<GRAD, float, Sink, true, MP, EDGE>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
+          else
+            sample_lnw<GRAD, RowT, Sink, true, MP, EDGE>(L, s, reinterpret_cast<const RowT*>(A.los) +
+                                                           (size_t)s_pix[i] * nz, nz, pos, aux, nx, wv, ws, lw, sink);
+        }
+      };
+      if (GRAD && (L.lam_edge != 0.f || (MP && L.lam1_edge != 0.f)))
+        sweep(std::true_type{});
+      else
+        sweep(std::false_type{});
       if (KAHAN) { acc.s1 -= acc.c1; acc.s2 -= acc.c2; }
     }
     // butterfly reduction across the warp (every lane ends with the same sums)
+    using AccT = Acc<GRAD, KAHAN, NS>;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float om_ = __shfl_xor_sync(0xffffffffu, acc.m, o);
       const float o1 = __shfl_xor_sync(0xffffffffu, acc.s1, o);
       const float o2 = __shfl_xor_sync(0xffffffffu, acc.s2, o);
-      float og[GRAD ? NS : 1], omO = -INFINITY, osO = 0.f;
+      float2 og[AccT::NG2];
+      float omO[AccT::NO], osO[AccT::NO];
       if (GRAD) {
 #pragma unroll
-        for (int q = 0; q < NS; ++q) og[q] = __shfl_xor_sync(0xffffffffu, acc.g[q], o);
-        omO = __shfl_xor_sync(0xffffffffu, acc.mO, o);
-        osO = __shfl_xor_sync(0xffffffffu, acc.sO, o);
+        for (int q = 0; q < AccT::NG2; ++q)
+          og[q] = make_float2(__shfl_xor_sync(0xffffffffu, acc.g2[q].x, o),
+                              __shfl_xor_sync(0xffffffffu, acc.g2[q].y, o));
+#pragma unroll
+        for (int q = 0; q < AccT::NO; ++q) {
+          omO[q] = __shfl_xor_sync(0xffffffffu, acc.mO[q], o);
+          osO[q] = __shfl_xor_sync(0xffffffffu, acc.sO[q], o);
+        }
       }
       acc.merge(om_, o1, o2, og, omO, osO);
     }
@@ -801,13 +825,15 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       slot[0] = acc.m;
       slot[1] = acc.s1;
       slot[2] = acc.s2;
-      slot[PART_MO] = acc.mO;
-      slot[PART_SO] = acc.sO;
+      slot[PART_MO] = acc.mO[0];
+      slot[PART_SO] = acc.sO[0];
+      slot[PART_MO2] = AccT::NO > 1 ? acc.mO[AccT::NO - 1] : -INFINITY;
+      slot[PART_SO2] = AccT::NO > 1 ? acc.sO[AccT::NO - 1] : 0.f;
     }
     if (GRAD && lane < NS) {
       float gv = 0.f;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) gv = (lane == q) ? acc.g[q] : gv;
+      for (int q = 0; q < NS; ++q) gv = (lane == q) ? acc.g(q) : gv;
       slot[3 + lane] = gv;
     }
   }
@@ -830,18 +856,19 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       out[1 + lane] = acc;
     }
     if (lane == 0) out[0] = M;
-    if (GRAD && lane == ncomp) {   // the first lane past the sums
+    if (GRAD && (lane == ncomp || lane == ncomp + 1)) {   // the lanes past the sums: one other pair each
+      const int pm = lane == ncomp ? PART_MO : PART_MO2;
       float MO = -INFINITY;
-      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PSTRIDE + PART_MO]);
+      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PSTRIDE + pm]);
       float so = 0.f;
       if (MO > -INFINITY) {
         for (int w = 0; w < G; ++w) {
-          const float mo = sl[w * PSTRIDE + PART_MO];
-          if (mo > -INFINITY) so = fmaf(sl[w * PSTRIDE + PART_SO], ex2(mo - MO), so);
+          const float mo = sl[w * PSTRIDE + pm];
+          if (mo > -INFINITY) so = fmaf(sl[w * PSTRIDE + pm + 1], ex2(mo - MO), so);
         }
       }
-      out[PART_MO] = MO;
-      out[PART_SO] = so;
+      out[pm] = MO;
+      out[pm + 1] = so;
     }
   }
 }
@@ -880,8 +907,8 @@ struct KdeSink {
   float z = -INFINITY;
   __device__ __forceinline__ bool any(bool p) { return p; }
   __device__ __forceinline__ bool weight(float, bool) { return false; }
-  __device__ __forceinline__ void grad(int, float) {}
-  __device__ __forceinline__ void lam_edge(float, float, float) {}
+  __device__ __forceinline__ void grad2(int, float, float) {}
+  __device__ __forceinline__ void other(int, float, float) {}
   __device__ __forceinline__ void position(float zz, int, bool ok) {
     if (ok) z = zz;
   }
@@ -971,6 +998,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   const KdeCtx C{A.mp != 0, L, pos, aux, wv, wv + (NW_WIN + 1), A.nx, A.nz, A.lm + grp.begin};
   const float4* smp = A.smp + grp.begin;
   const int n = grp.count;
+  if (A.census && lane == 0) atomicAdd(A.census + 0, (unsigned long long)n);
 
   // ---- pass 1: weights (max, sum, sum of squares), Welford moments of z, valid range
   float m = -INFINITY, s1 = 0.f, s2 = 0.f;
@@ -1097,6 +1125,7 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
     if (lane == 0) { out[0] = -INFINITY; out[1] = 0.f; out[2] = 0.f; }
     return;
   }
+  unsigned n_w = 0, n_terms = 0;   // census counts of this lane (measurement only)
 
   // ---- pass 2: sum_k w'_k sum_g c_g p_LOS(z_g) K_h(z_g - z_k), scaled by 2^-m; each
   //      kernel over the grid points within 6 h (its mass beyond is 2e-9)
@@ -1110,6 +1139,10 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
     if (!(lw > -INFINITY)) continue;
     const int g0 = max(0, (int)ceilf((z - reach) * inv_dzg));
     const int g1 = min(A.G - 1, (int)floorf((z + reach) * inv_dzg));
+    if (A.census) {
+      ++n_w;
+      n_terms += (unsigned)max(g1 - g0 + 1, 0);
+    }
     float T = 0.f, gf = (float)g0;
     for (int gg = g0; gg <= g1; ++gg, gf += 1.f) {
       const float d = fmaf(gf, dzg, -z);
@@ -1125,6 +1158,14 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (A.census) {
+    const unsigned a = __reduce_add_sync(0xffffffffu, n_w), b = __reduce_add_sync(0xffffffffu, n_terms);
+    if (lane == 0) {
+      atomicAdd(A.census + 1, 1ull);
+      atomicAdd(A.census + 2, (unsigned long long)a);
+      atomicAdd(A.census + 3, (unsigned long long)b);
+    }
+  }
   if (lane == 0) {
     const float S = acc * dzg / (h * 2.50662827463100050242f);   // h sqrt(2 pi)
     out[0] = S > 0.f ? m : -INFINITY;
@@ -1213,8 +1254,8 @@ __global__ void __launch_bounds__(256) k_plain_sample(PlainArgs A) {
   } else {
     const float t = ok ? ex2(lw - m) : 0.f;
     for (int q = 0; q < NP; ++q) A.tg[(size_t)q * A.n_total + i] = ok ? t * ts.g[q] : 0.f;
-    if (ok && ts.edge)   // sigma (t - t O/mix): may overflow for extreme samples
-      A.tg[(size_t)S_LX * A.n_total + i] = ts.g[S_LX] * (t - ex2(lw - m + ts.lo));
+    if (ok && ts.edge[0])   // sigma (t - t O/mix): may overflow for extreme samples
+      A.tg[(size_t)S_LX * A.n_total + i] = ts.g[S_LX] * (t - ex2(lw - m + ts.lo[0]));
   }
 }
 
@@ -1258,6 +1299,8 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
       out[2] = b;
       out[PART_MO] = -INFINITY;   // the plain path folds the lambda-edge term into its g
       out[PART_SO] = 0.f;
+      out[PART_MO2] = -INFINITY;
+      out[PART_SO2] = 0.f;
     }
   } else {
     float gs[NP];
@@ -1285,7 +1328,7 @@ template <bool GRAD>
 __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   __shared__ double rs[8][2 + NP_MAX];
   __shared__ double rsel[8][3 + NP_MAX];
-  __shared__ double rO[8][2];
+  __shared__ double rO[8][4];
   __shared__ int rfail[8];
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int nt = blockDim.x, nw = nt >> 5;   // sized to the work by launch_merge
@@ -1340,10 +1383,13 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         for (int i = 0; i < NPK; ++i) st[i] = G[i];
         stats_to_grad(st, S1, D, G);
       }
-      if (GRAD && D.lam_sigma != 0)   // other-component sums at lambda_peak = 0 or 1
+      if (GRAD && (D.lam_sigma != 0 || D.lam1_sigma != 0))   // other-component sums at the bounds
         for (int s = s0; s < s1; ++s) {
           const float* p = pk + (size_t)s * PSTRIDE;
-          if (p[PART_MO] > -INFINITY) G[P_LAM] -= D.lam_sigma * (double)p[PART_SO] * exp2((double)p[PART_MO] - M);
+          if (D.lam_sigma != 0 && p[PART_MO] > -INFINITY)
+            G[P_LAM] -= D.lam_sigma * (double)p[PART_SO] * exp2((double)p[PART_MO] - M);
+          if (D.lam1_sigma != 0 && p[PART_MO2] > -INFINITY)
+            G[P_LAM1] -= D.lam1_sigma * (double)p[PART_SO2] * exp2((double)p[PART_MO2] - M);
         }
     }
     double lnL = -INFINITY, neff = 0.0;
@@ -1368,15 +1414,19 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
 
   // ---- injections: online merge of the injection partials
   double sM = -INFINITY, sS1 = 0.0, sS2 = 0.0, sG[GRAD ? NP_MAX : 1];
-  double oM = -INFINITY, oS = 0.0;   // other-component pair at lambda_peak = 0 or 1
+  double oM[2] = {-INFINITY, -INFINITY}, oS[2] = {0.0, 0.0};   // other-component pairs at the bounds
   if (GRAD)
     for (int i = 0; i < NPK; ++i) sG[i] = 0.0;
   for (int s = A.inj_item0 * P + tid; s < A.n_items * P; s += nt) {
     const float* p = pk + (size_t)s * PSTRIDE;
-    if (GRAD && D.lam_sigma != 0 && p[PART_MO] > -INFINITY) {
-      const double mo = p[PART_MO];
-      if (mo > oM) { oS = oS * exp2(oM - mo) + (double)p[PART_SO]; oM = mo; }
-      else oS += (double)p[PART_SO] * exp2(mo - oM);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int pm = q == 0 ? PART_MO : PART_MO2;
+      if (GRAD && (q == 0 ? D.lam_sigma : D.lam1_sigma) != 0 && p[pm] > -INFINITY) {
+        const double mo = p[pm];
+        if (mo > oM[q]) { oS[q] = oS[q] * exp2(oM[q] - mo) + (double)p[pm + 1]; oM[q] = mo; }
+        else oS[q] += (double)p[pm + 1] * exp2(mo - oM[q]);
+      }
     }
     const double m = p[0];
     if (!(m > -INFINITY)) continue;
@@ -1399,11 +1449,13 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   sumL += cmp;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    if (GRAD) {
-      const double x_m = __shfl_xor_sync(0xffffffffu, oM, o), x_s = __shfl_xor_sync(0xffffffffu, oS, o);
-      const double MO = fmax(oM, x_m);
-      if (MO > -INFINITY) { oS = oS * exp2(oM - MO) + x_s * exp2(x_m - MO); oM = MO; }
-    }
+    if (GRAD)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const double x_m = __shfl_xor_sync(0xffffffffu, oM[q], o), x_s = __shfl_xor_sync(0xffffffffu, oS[q], o);
+        const double MO = fmax(oM[q], x_m);
+        if (MO > -INFINITY) { oS[q] = oS[q] * exp2(oM[q] - MO) + x_s * exp2(x_m - MO); oM[q] = MO; }
+      }
     sumL += __shfl_xor_sync(0xffffffffu, sumL, o);
     fail |= __shfl_xor_sync(0xffffffffu, fail, o);
     if (GRAD)
@@ -1432,8 +1484,10 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     rsel[w][0] = sM;
     rsel[w][1] = sS1;
     rsel[w][2] = sS2;
-    rO[w][0] = oM;
-    rO[w][1] = oS;
+    rO[w][0] = oM[0];
+    rO[w][1] = oS[0];
+    rO[w][2] = oM[1];
+    rO[w][3] = oS[1];
     if (GRAD)
       for (int i = 0; i < NPK; ++i) rsel[w][3 + i] = sG[i];
   }
@@ -1463,9 +1517,11 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         for (int i = 0; i < NPK; ++i) st[i] = G[i];
         stats_to_grad(st, S1, D, G);
       }
-      if (GRAD && D.lam_sigma != 0)
-        for (int q = 0; q < nw; ++q)
-          if (rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * exp2(rO[q][0] - M);
+      if (GRAD)
+        for (int q = 0; q < nw; ++q) {
+          if (D.lam_sigma != 0 && rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * exp2(rO[q][0] - M);
+          if (D.lam1_sigma != 0 && rO[q][2] > -INFINITY) G[P_LAM1] -= D.lam1_sigma * rO[q][3] * exp2(rO[q][2] - M);
+        }
     }
     int flag = (fl & 1) ? 2 : 0;
     const bool dead = (fl & 2) != 0;
@@ -1534,7 +1590,10 @@ __global__ void __launch_bounds__(256) k_sample_terms(TermsArgs A) {
     double st[NP_MAX], G[NP_MAX];
     for (int q = 0; q < NS; ++q) st[q] = ok ? (double)ts.g[q] : 0.0;
     stats_to_grad(st, ok ? 1.0 : 0.0, *A.ld, G);
-    if (ok && ts.edge) G[P_LAM] *= 1.0 - exp2((double)ts.lo);   // sigma (1 - O/mix): may overflow
+    // at a mixture bound: sigma (1 - O/mix) (may overflow), and for the multi-peak
+    // model's lambda_low the other peak's share taken off
+    if (ok && ts.edge[0]) G[P_LAM] *= 1.0 - exp2((double)ts.lo[0]);
+    if (ok && ts.edge[1]) G[P_LAM1] -= A.ld->lam1_sigma * exp2((double)ts.lo[1]);
     for (int q = 0; q < NS; ++q) A.dlnw[(size_t)q * A.n_total + i] = ok ? (float)G[q] : 0.f;
   }
 }
@@ -1562,8 +1621,8 @@ struct CensusSink {
     w = live;
     return false;
   }
-  __device__ __forceinline__ void grad(int, float) {}
-  __device__ __forceinline__ void lam_edge(float, float, float) {}
+  __device__ __forceinline__ void grad2(int, float, float) {}
+  __device__ __forceinline__ void other(int, float, float) {}
   __device__ __forceinline__ void position(float, int, bool ok) { c[1] += ok; }
   __device__ __forceinline__ void reached(int st, bool ok) { c[st] += ok; }
   __device__ __forceinline__ void windows(bool a, bool b, bool ok) {
@@ -1730,6 +1789,20 @@ cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, i
 cudaError_t fused_blocks_per_sm(const FusedArgs& a, bool grad, bool kahan, bool bf16, int* out) {
   const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
   return fused_dispatch<FusedOccupancy>(grad, kahan, bf16, a.mp != 0, smem, out);
+}
+
+// ------------------------------------------------------------ event-shard merge
+__global__ void k_merge_parts(int R, int K, int P, const double* __restrict__ parts, double* lnL_total,
+                              double* ln_xi, double* neff_sel, int32_t* flags, double* grad_total) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < K) merge_parts_point(R, K, P, parts, k, lnL_total, ln_xi, neff_sel, flags, grad_total);
+}
+
+cudaError_t launch_merge_parts(int R, int K, int P, const double* parts, double* lnL_total, double* ln_xi,
+                               double* neff_sel, int32_t* flags, double* grad_total, cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
+  k_merge_parts<<<(K + 127) / 128, 128, 0, s>>>(R, K, P, parts, lnL_total, ln_xi, neff_sel, flags, grad_total);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ HMC leapfrog

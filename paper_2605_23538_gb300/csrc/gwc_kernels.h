@@ -77,7 +77,11 @@ struct KdeArgs {
   float* partials;        // [K][stride][PSTRIDE], slot = group index
   int stride;
   int mp = 0;             // multi-peak mass model
+  // measurement only (null otherwise): [0] pass-1 sample evaluations, [1] (group, Lambda)
+  // pairs kept, [2] pass-2 sample evaluations with a weight, [3] grid terms summed
+  unsigned long long* census = nullptr;
 };
+constexpr int KDE_CENSUS_SLOTS = 4;
 cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s);
 cudaError_t launch_log2_masses(const float4* smp, long long n, float2* out, cudaStream_t s);
 cudaError_t launch_los_grid(const float* los, int n_pix, int nz, double zmax, int G, float* out,
@@ -211,6 +215,60 @@ struct CensusArgs {
   int mp = 0;
 };
 cudaError_t launch_census(const CensusArgs& a, bool bf16, cudaStream_t s);
+// Combination of event shards' parts for one Lambda point k (host or device, FP64, ranks
+// in order).  parts[R][K][5 + 2P]: sum of the shard's ln L_i, its ln xi_r, N_eff,sel r,
+// flags, number of events, then (P > 0) the gradients of the first two.  xi = sum_r xi_r
+// (the selection integral is a sum over injections), so
+//   ln L = sum_r S_r - N ln xi,  grad = sum_r dS_r - N sum_r (xi_r / xi) d ln xi_r,
+//   N_eff,sel = xi^2 / sum_r (xi_r^2 / N_eff,sel r)
+// with N the events of all shards.  Flag bits 0 and 1 carry over; bit 3 (no injection
+// weight) follows the merged xi; bit 2 (a shard's own selection cut) is dropped.
+__host__ __device__ inline void merge_parts_point(int R, int K, int P, const double* parts, int k,
+                                                  double* lnL_total, double* ln_xi, double* neff_sel,
+                                                  int32_t* flags, double* grad_total) {
+  const int W = 5 + 2 * P;
+  double M = -INFINITY, ndet = 0.0;
+  int fl = 0;
+  bool dead = false;
+  for (int r = 0; r < R; ++r) {
+    const double* q = parts + ((size_t)r * K + k) * W;
+    if (q[1] > M) M = q[1];
+    ndet += q[4];
+    fl |= (int)q[3];
+    if (!(q[0] > -INFINITY && q[0] < INFINITY)) dead = true;
+  }
+  const bool fin = M > -INFINITY && M < INFINITY;
+  double sw = 0.0, s2 = 0.0, se = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const double* q = parts + ((size_t)r * K + k) * W;
+    const double w = (fin && q[1] > -INFINITY) ? exp(q[1] - M) : 0.0;
+    sw += w;
+    if (q[2] > 0.0) s2 += w * w / q[2];
+    se += q[0];
+  }
+  const double lx = (fin && sw > 0.0) ? M + log(sw) : -INFINITY;
+  const int f = (fl & ~(4 | 8)) | (lx > -INFINITY ? 0 : 8);
+  const bool bad = f != 0 || dead;
+  lnL_total[k] = bad ? -INFINITY : se - ndet * lx;
+  ln_xi[k] = lx;
+  neff_sel[k] = s2 > 0.0 ? sw * sw / s2 : 0.0;
+  flags[k] = f;
+  if (P > 0 && grad_total) {
+    for (int i = 0; i < P; ++i) {
+      double ge = 0.0, gx = 0.0;
+      for (int r = 0; r < R; ++r) {
+        const double* q = parts + ((size_t)r * K + k) * W;
+        const double w = (fin && q[1] > -INFINITY) ? exp(q[1] - M) : 0.0;
+        ge += q[5 + i];
+        gx += (sw > 0.0 ? w / sw : 0.0) * q[5 + P + i];
+      }
+      grad_total[(size_t)k * P + i] = bad ? 0.0 : ge - ndet * gx;
+    }
+  }
+}
+cudaError_t launch_merge_parts(int R, int K, int P, const double* parts, double* lnL_total, double* ln_xi,
+                               double* neff_sel, int32_t* flags, double* grad_total, cudaStream_t s);
+
 // the calling thread's message for gwc_last_error(NULL) (defined with the C ABI)
 void set_thread_error(const std::string& msg);
 cudaError_t launch_los_cell(const float* z, long long n, int nz, double zmax, int* cell, cudaStream_t s);

@@ -35,8 +35,8 @@ constexpr int PM_SLABS = 8;       // pixel slabs summed in parallel for the pixe
 // scratch layout (bytes): LamF | LamD | per-Lambda tables | pixel mean (float) | (double)
 // | the pixel slabs' partial sums (double, [PM_SLABS][n_z])
 constexpr size_t OFF_LF = 0;
-constexpr size_t OFF_LD = 256;
-constexpr size_t OFF_TB = 768;
+constexpr size_t OFF_LD = 512;
+constexpr size_t OFF_TB = 1024;
 constexpr size_t TB_BYTES = ((size_t)table_floats(MAX_NX) + 3) / 4 * 4 * sizeof(float);
 constexpr size_t OFF_P32 = OFF_TB + (TB_BYTES + 255) / 256 * 256;
 constexpr size_t OFF_P64 = OFF_P32 + (MAX_NZ * sizeof(float) + 255) / 256 * 256;

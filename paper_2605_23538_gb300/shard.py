@@ -14,7 +14,9 @@ evaluates its parts with gwc_loglik_parts; `merge_parts` combines the shards exa
 because the selection integral is a sum over injections, xi = sum_r xi_r:
     ln L = sum_r sum_events_r - N_det ln(sum_r xi_r)
     d ln L = sum_r d sum_events_r - N_det sum_r (xi_r / xi) d ln xi_r
-`merge_parts_distributed` does the one exchange (an all_gather of K (5 + 2P) numbers).
+`merge_parts_distributed` does the one exchange (an all_gather of K (5 + 2P) numbers,
+on the GPU with NCCL) and the combination (gwc_merge_parts: a kernel for device rows, the
+same FP64 arithmetic on the host for gloo's host rows).
 """
 from __future__ import annotations
 
@@ -77,76 +79,76 @@ def world_batch(K: int, world: int, make_batch) -> np.ndarray:
     return np.asarray(make_batch(K * world))
 
 
-def merge_parts(parts):
-    """Combine the gwc_loglik_parts outputs of every shard (a list of dicts of tensors or
-    arrays with keys sum_events, ln_xi, neff_sel, flags, n_events and, for the gradient,
-    grad_events, grad_ln_xi) into lnL_total, ln_xi, neff_sel, flags and grad_total."""
-    def a(x):
-        return np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x, dtype=np.float64)
-    n_det = float(sum(int(p["n_events"]) for p in parts))
-    lx = np.stack([a(p["ln_xi"]) for p in parts])               # [R, K]
-    ns = np.stack([a(p["neff_sel"]) for p in parts])
-    se = np.stack([a(p["sum_events"]) for p in parts])
-    fl = np.bitwise_or.reduce(np.stack([np.asarray(a(p["flags"]), np.int64) for p in parts]), axis=0)
-    M = np.max(lx, axis=0)
-    fin = np.isfinite(M)
-    w = np.where(fin[None, :] & np.isfinite(lx), np.exp(lx - np.where(fin, M, 0.0)[None, :]), 0.0)
-    sw = w.sum(axis=0)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        ln_xi = np.where(fin & (sw > 0), M + np.log(sw), -np.inf)
-        # sum of squared injection weights of shard r, in units of exp(2 M): w_r^2 / N_eff,r
-        s2 = np.where(ns > 0, w * w / np.where(ns > 0, ns, 1.0), 0.0).sum(axis=0)
-        neff = np.where(s2 > 0, sw * sw / s2, 0.0)
-    # bits 0 (domain) and 1 (an event's N_eff) carry over; bit 3 (no injection weight) is
-    # decided by the merged sum; a shard's own selection N_eff cut (bit 2) says nothing
-    # about the merged one -- shards are built with neff_min_sel = 0 and a caller applies
-    # its threshold to the merged neff_sel
-    flags = (fl & ~np.int64(4 | 8)) | np.where(np.isfinite(ln_xi), 0, 8)
-    dead = ~np.all(np.isfinite(se), axis=0)
-    total = np.where((flags != 0) | dead, -np.inf, se.sum(axis=0) - n_det * ln_xi)
-    out = {"lnL_total": total, "ln_xi": ln_xi, "neff_sel": neff, "flags": flags.astype(np.int32)}
-    if all("grad_events" in p for p in parts):
-        ge = np.stack([a(p["grad_events"]) for p in parts]).sum(axis=0)          # [K, 13]
-        gx = np.stack([a(p["grad_ln_xi"]) for p in parts])                      # [R, K, 13]
-        with np.errstate(divide="ignore", invalid="ignore"):
-            q = np.where(sw > 0, w / np.where(sw > 0, sw, 1.0), 0.0)             # xi_r / xi
-        grad = ge - n_det * np.einsum("rk,rki->ki", q, gx)
-        out["grad_total"] = np.where(((flags != 0) | dead)[:, None], 0.0, grad)
+def pack_parts(part, device=None):
+    """One shard's gwc_loglik_parts outputs (a dict of tensors or arrays with keys
+    sum_events, ln_xi, neff_sel, flags, n_events and, for the gradient, grad_events,
+    grad_ln_xi) as the [K, 5 + 2P] FP64 rows that gwc_merge_parts reads, on `device`
+    (default: where the part's tensors are; host for numpy arrays)."""
+    import torch
+
+    def t(x):
+        x = x if isinstance(x, torch.Tensor) else torch.as_tensor(np.asarray(x))
+        return x.to(dtype=torch.float64, device=device) if device is not None else x.to(torch.float64)
+    se = t(part["sum_events"])
+    if device is None:
+        device = se.device
+    K = int(se.shape[0])
+    cols = [se[:, None], t(part["ln_xi"]).to(device)[:, None], t(part["neff_sel"]).to(device)[:, None],
+            t(part["flags"]).to(device)[:, None],
+            torch.full((K, 1), float(part["n_events"]), dtype=torch.float64, device=device)]
+    if "grad_events" in part:
+        cols += [t(part["grad_events"]).to(device).reshape(K, -1), t(part["grad_ln_xi"]).to(device).reshape(K, -1)]
+    return torch.cat(cols, dim=1).contiguous()
+
+
+def merge_packed(rows):
+    """gwc_merge_parts on the packed rows [R, K, 5 + 2P] of R shards: a kernel on the
+    current stream when rows is a CUDA tensor, the same FP64 arithmetic on the host for a
+    CPU tensor.  Returns lnL_total, ln_xi, neff_sel, flags (and grad_total when P > 0) as
+    tensors on the rows' device."""
+    import ctypes
+    import torch
+    from . import _check, _stream_ptr, lib
+    rows = rows.to(torch.float64).contiguous()
+    R, K, W = (int(v) for v in rows.shape)
+    P = (W - 5) // 2
+    dev = rows.device
+    out = {"lnL_total": torch.empty(K, dtype=torch.float64, device=dev),
+           "ln_xi": torch.empty(K, dtype=torch.float64, device=dev),
+           "neff_sel": torch.empty(K, dtype=torch.float64, device=dev),
+           "flags": torch.empty(K, dtype=torch.int32, device=dev)}
+    if P > 0:
+        out["grad_total"] = torch.empty((K, P), dtype=torch.float64, device=dev)
+    p = lambda x: ctypes.c_void_p(x.data_ptr())
+    _check(lib().gwc_merge_parts(R, K, P, p(rows), 1 if rows.is_cuda else 0, p(out["lnL_total"]),
+                                 p(out["ln_xi"]), p(out["neff_sel"]), p(out["flags"]),
+                                 p(out["grad_total"]) if P > 0 else None,
+                                 _stream_ptr(None) if rows.is_cuda else None))
     return out
+
+
+def merge_parts(parts):
+    """Combine the gwc_loglik_parts outputs of every shard (a list of dicts, see
+    pack_parts) into lnL_total, ln_xi, neff_sel, flags and grad_total (gwc_merge_parts, on
+    the device of the first part's tensors)."""
+    import torch
+    first = pack_parts(parts[0])
+    return merge_packed(torch.stack([first] + [pack_parts(q, first.device) for q in parts[1:]]))
 
 
 def merge_parts_distributed(part):
     """merge_parts over all ranks of the process group: one all_gather of every rank's
     K (5 + 2P) numbers (P = 13, or 16 for the multi-peak model, taken from the
-    gradients' width), then the same exact combination on every rank."""
+    gradients' width), then the same exact combination on every rank.  With NCCL the
+    exchange and the combination stay on this rank's GPU; with gloo they run on the host."""
     import torch
     dist = _dist()
     if dist is None:
         return merge_parts([part])
     world = dist.get_world_size()
-    grad = "grad_events" in part
-
-    def t(x):
-        return torch.as_tensor(np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x,
-                                          dtype=np.float64))
-    K = int(t(part["ln_xi"]).shape[0])
-    cols = [t(part["sum_events"])[:, None], t(part["ln_xi"])[:, None], t(part["neff_sel"])[:, None],
-            t(part["flags"])[:, None], torch.full((K, 1), float(part["n_events"]), dtype=torch.float64)]
-    P = 0
-    if grad:
-        ge, gx = t(part["grad_events"]).reshape(K, -1), t(part["grad_ln_xi"]).reshape(K, -1)
-        P = ge.shape[1]
-        cols += [ge, gx]
-    mine = torch.cat(cols, dim=1)
+    on_gpu = dist.get_backend() == "nccl"
+    device = torch.device("cuda", torch.cuda.current_device()) if on_gpu else torch.device("cpu")
+    mine = pack_parts(part, device)
     every = [torch.empty_like(mine) for _ in range(world)]
     dist.all_gather(every, mine)
-    parts = []
-    for m in every:
-        m = m.numpy()
-        p = {"sum_events": m[:, 0], "ln_xi": m[:, 1], "neff_sel": m[:, 2],
-             "flags": m[:, 3].astype(np.int64), "n_events": int(m[0, 4])}
-        if grad:
-            p["grad_events"] = m[:, 5:5 + P]
-            p["grad_ln_xi"] = m[:, 5 + P:5 + 2 * P]
-        parts.append(p)
-    return merge_parts(parts)
+    return merge_packed(torch.stack(every))

@@ -174,3 +174,33 @@ def test_c3_gradient_against_differences_of_the_total(torch, g, synth, cat_c3):
         print(f"component {i}: gradient {grad[0, i]:.6e}, central difference {fd:.6e}")
         # the FP32 total's rounding (~1e-4 absolute at this size) limits the difference
         assert abs(fd - grad[0, i]) <= 2e-2 * abs(grad[0, i]) + 2e-4 / h
+
+
+def test_c3_kde_sampled_events(torch, g, orc, synth, cat_c3):
+    # The KDE form (Eqs. 5-7) at full size, for the three bandwidth rules on the paper's
+    # 256-point grid: per-event ln L and the effective number of kept pixels at the 24
+    # sampled events x 4 bench points, the library on the whole catalogue against the
+    # oracle on those events alone.  Here the (event, pixel) groups hold hundreds of
+    # samples, so the order statistics of the robust bandwidths range over long runs.
+    lam = synth.lambda_batch(K, purpose=4)[LAMBDAS]
+    off, pix = cat_c3["offsets"], np.asarray(cat_c3["pix"])
+    biggest = max(np.bincount(pix[off[e]:off[e + 1]]).max() for e in EVENTS)
+    sub = synth.subset_events(cat_c3, EVENTS)
+    for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):  # per-event values ignore them
+        sub[k] = cat_c3[k][:1000]
+    with g.Context(cat_c3, max_K=len(LAMBDAS)) as ctx:
+        for rule in ("scott", "silverman", "biweight"):
+            got = ctx.loglik_kde(torch.tensor(lam, device="cuda"), bw=rule)
+            torch.cuda.synchronize()
+            ge = got["lnL_event"].cpu().numpy()[:, EVENTS]
+            gn = got["neff_event"].cpu().numpy()[:, EVENTS]
+            ref = orc.loglik_kde(sub, lam, bw=rule)
+            fin = np.isfinite(ref["lnL_event"])
+            assert np.array_equal(np.isfinite(ge), fin), rule
+            d = np.abs(ge[fin] - ref["lnL_event"][fin])
+            pos = ref["neff_event"] > 0
+            dn = np.abs(gn[pos] - ref["neff_event"][pos]) / ref["neff_event"][pos]
+            print(f"c3 KDE {rule}: {fin.sum()} finite (event, Lambda) pairs, largest group {biggest} "
+                  f"samples; per-event |d| max {d.max():.2e}, kept-pixel N_eff rel {dn.max():.2e}")
+            assert d.max() <= 1e-5
+            assert dn.max() <= 1e-4

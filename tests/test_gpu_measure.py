@@ -72,3 +72,30 @@ def test_alu_probe_runs(torch, g, unit):
     print(f"{unit}: {ops / (ms / 1e3) / 1e12:.2f} Tops/s on a small launch")
     with pytest.raises(g.GwcError):
         g.alu_probe(unit, 0, 1, s)
+
+
+@pytest.mark.parametrize("rule", ["scott", "biweight"])
+def test_kde_census_counts(torch, g, synth, rule):
+    # the KDE kernel's work counts: every event sample is evaluated once per live point in
+    # the first pass; kept groups, second-pass evaluations and grid terms are bounded by
+    # what they count; a batch counts what its points count one at a time
+    w = synth.scaled("kde_census", 10, ("uniform", 300, 3000), 8, 512, 5_000, "found")
+    cat = synth.catalogue(w)
+    lam = np.vstack([synth.FIDUCIAL, synth.lambda_batch(3, purpose=32)])
+    n_s = len(cat["m1"])
+    off, pix = cat["offsets"], np.asarray(cat["pix"])
+    n_groups = sum(len(np.unique(pix[off[e]:off[e + 1]])) for e in range(len(off) - 1))
+    n_grid = 256
+    with g.Context(cat, max_K=len(lam)) as ctx:
+        whole = ctx.kde_census(torch.tensor(lam, device="cuda"), bw=rule, n_grid=n_grid)
+        total = {k: 0 for k in whole}
+        for row in lam:
+            one = ctx.kde_census(torch.tensor(row[None, :], device="cuda"), bw=rule, n_grid=n_grid)
+            assert one["pass1"] == n_s
+            assert 0 < one["kept"] <= n_groups
+            assert 0 < one["pass2"] <= n_s
+            assert one["pass2"] <= one["terms"] <= one["pass2"] * n_grid
+            for k in total:
+                total[k] += one[k]
+    assert whole == total
+    print(f"KDE census ({rule}):", whole, f"{whole['terms'] / whole['pass2']:.1f} grid terms per sample")

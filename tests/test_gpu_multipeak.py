@@ -3,8 +3,8 @@
 The same tolerances as the power law + peak path (see test_gpu_parity.py): per-event
 ln L within 1e-5, ln xi within 1e-5, total within 1e-3, the 16-component gradient within
 1e-4 of its scale, flags exact; plus per-sample ln w and derivatives element by element,
-the KDE form, the reduction to the single-peak context at lambda_low = 1, the NaN
-components at the mixture-weight bounds, and the width and option checks.
+the KDE form, the reduction to the single-peak context at lambda_low = 1, the one-sided
+derivatives at the mixture-weight bounds, and the width and option checks.
 """
 import numpy as np
 import pytest
@@ -75,17 +75,50 @@ def test_lambda_low_one_is_the_single_peak_context(torch, g, synth, cat_c1):
     for key in ("lnL_event", "ln_xi"):
         np.testing.assert_allclose(a[key].cpu().numpy(), b[key].cpu().numpy(), rtol=0, atol=1e-5)
     ga, gb = a["grad_total"].cpu().numpy(), b["grad_total"].cpu().numpy()
-    # at the bound lambda_low = 1 the two mixture-weight components are left undefined
-    assert np.all(np.isnan(ga[:, [P_LAM, P_LAM1]]))
-    keep = [i for i in range(13) if i != P_LAM]
+    # every component of the single-peak model, lambda_g (= lambda_peak there) included;
+    # d/d lambda_low at the bound is one-sided (checked against the oracle below)
+    assert np.all(np.isfinite(ga))
+    keep = list(range(13))
     scale = np.abs(gb[:, keep]).max(axis=0)
     np.testing.assert_allclose(ga[:, keep], gb[:, keep], rtol=1e-3, atol=1e-4 * scale.max())
     np.testing.assert_array_equal(ga[:, 13:15], 0.0)   # the absent peak's parameters
 
 
-def test_sample_terms_elementwise(torch, g, orc, synth, cat_ragged):
+# the lambda_g and lambda_low derivatives at the mixture's bounds are one-sided: the
+# oracle's forward-mode derivative of the mixture polynomial, which its tests pin
+# against one-sided differences
+BOUNDS = [(1.0, None), (0.0, None), (None, 1.0), (None, 0.0), (1.0, 0.0), (0.0, 1.0)]
+
+
+def test_mixture_bounds_one_sided_gradient(torch, g, orc, synth, cat_c1):
+    lam = np.repeat(synth.FIDUCIAL_MP[None, :], len(BOUNDS), axis=0)
+    for k, (lg, ll) in enumerate(BOUNDS):
+        if lg is not None:
+            lam[k, P_LAM] = lg
+        if ll is not None:
+            lam[k, P_LAM1] = ll
+    with g.Context(cat_c1, max_K=len(BOUNDS), mass_model="multipeak", neff_min_event=0.0) as ctx:
+        got = ctx.loglik_grad(dev(torch, lam))
+        torch.cuda.synchronize()
+    ref = orc.loglik(cat_c1, lam, grad=True, neff_min_event=0.0)
+    assert np.all(np.isfinite(ref["lnL_total"])) and np.all(np.isfinite(got["grad_total"].cpu().numpy()))
+    out = compare(got, ref, grad=True, label="multipeak bounds")
+    gg, gr = got["grad_total"].cpu().numpy(), ref["grad_total"]
+    for k, b in enumerate(BOUNDS):
+        print(f"bounds {b}: d/d lambda_g {gg[k, P_LAM]:.6e} (oracle {gr[k, P_LAM]:.6e}), "
+              f"d/d lambda_low {gg[k, P_LAM1]:.6e} (oracle {gr[k, P_LAM1]:.6e})")
+    # at lambda_g = 0 the mixture does not depend on lambda_low
+    assert gg[1, P_LAM1] == 0.0 and gg[5, P_LAM1] == 0.0
+    assert out["d_total"] <= 1e-3
+
+
+@pytest.mark.parametrize("bound", [None, (1.0, 0.0), (0.0, 1.0)])
+def test_sample_terms_elementwise(torch, g, orc, synth, cat_ragged, bound):
     # every sample's ln w and its 16 derivatives against the oracle, element by element
+    # (inside the domain, and at two corners of the mixture weights)
     lam = synth.lambda_batch(1, purpose=84, model="multipeak")[0]
+    if bound is not None:
+        lam[P_LAM], lam[P_LAM1] = bound
     order = g.sample_order(cat_ragged)
     with g.Context(cat_ragged, max_K=1, mass_model="multipeak") as ctx:
         lnw, d, c = ctx.sample_terms(torch.tensor(lam, device="cuda"))

@@ -8,7 +8,8 @@ already-pinned power law + peak model with the low (or high) Gaussian; exchangin
 two Gaussians together with lam_low <-> 1 - lam_low changes nothing; without smoothing
 (delta_m = 0) the density is the textbook mixture of a normalised power law and two
 scipy truncated normals; the density integrates to one under an independent
-quadrature; the 16-component gradient matches central finite differences.
+quadrature; the 16-component gradient matches central finite differences inside the
+domain and one-sided differences (taken into the domain) at the mixture weights' bounds.
 """
 import os
 
@@ -145,6 +146,33 @@ def test_gradient_matches_finite_differences(orc, small):
         assert abs(fd - g[i]) <= 1e-5 * abs(g[i]) + 2e-7 / scale[i], (LAMBDA_NAMES_MP[i], fd, g[i])
     # the three new parameters do move the likelihood at this point
     assert np.all(np.abs(g[[P_MU2, P_SIG2, P_LAM1]]) > 1e-3)
+
+
+@pytest.mark.parametrize("bound", [(1.0, None), (0.0, None), (None, 1.0), (None, 0.0), (1.0, 0.0), (0.0, 1.0)])
+def test_gradient_at_the_mixture_bounds_is_one_sided(orc, small, bound):
+    # at lambda_g or lambda_low = 0 or 1 only one side of the point is in the domain: the
+    # oracle's derivative of those two components must equal the one-sided difference
+    # taken into the domain (second order: three points)
+    lam = FIDUCIAL_MP.copy()
+    if bound[0] is not None:
+        lam[P_LAM] = bound[0]
+    if bound[1] is not None:
+        lam[P_LAM1] = bound[1]
+    g = orc.loglik(small, lam, grad=True, neff_min_event=0.0)["grad_total"][0]
+    assert np.all(np.isfinite(g))
+    f0 = orc.loglik(small, lam, neff_min_event=0.0)["lnL_total"][0]
+    for i in (P_LAM, P_LAM1):
+        d = -1.0 if lam[i] >= 1.0 else 1.0             # the direction into the domain
+        h = 1e-5
+        l1, l2 = lam.copy(), lam.copy()
+        l1[i] += d * h
+        l2[i] += 2 * d * h
+        f1 = orc.loglik(small, l1, neff_min_event=0.0)["lnL_total"][0]
+        f2 = orc.loglik(small, l2, neff_min_event=0.0)["lnL_total"][0]
+        fd = d * (-3.0 * f0 + 4.0 * f1 - f2) / (2.0 * h)
+        assert abs(fd - g[i]) <= 1e-5 * abs(g[i]) + 1e-5, (bound, LAMBDA_NAMES_MP[i], fd, g[i])
+    if lam[P_LAM] == 0.0:                              # no lambda_low dependence without the peaks
+        assert g[P_LAM1] == 0.0
 
 
 @pytest.mark.parametrize("bad", [dict(sigma_high=0.0), dict(sigma_high=-1.0), dict(lambda_low=1.01),

@@ -4,13 +4,21 @@ Each rank evaluates its block of rows with the FP64 oracle (standing in for its 
 context: the sharding logic is the same), the blocks are gathered in rank order, and
 rank 0 checks the result against one process evaluating the whole batch.  Also checks
 the row split, the max over ranks used for the job's time, and a batch whose size is
-not a multiple of the world size.
+not a multiple of the world size.  Event shards exchange their parts in one all_gather
+and combine them with the library's gwc_merge_parts (its host arithmetic, as on gloo).
 """
 import os
 import socket
 
 import numpy as np
 import pytest
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    # the event-shard merge runs in libgwc.so (host arithmetic for host rows)
+    from paper_2605_23538_gb300 import build
+    build.build()
 
 
 def _free_port():
@@ -164,3 +172,40 @@ def test_event_shards_merge_multipeak_gradients_on_two_gloo_ranks(tmp_path):
     assert res["grad"].shape == (2, 16)
     np.testing.assert_allclose(res["total"], ref["lnL_total"], rtol=0, atol=1e-9)
     np.testing.assert_allclose(res["grad"], ref["grad_total"], rtol=1e-8, atol=1e-8 * np.abs(ref["grad_total"]).max())
+
+
+def test_merge_entry_on_host_rows_matches_the_whole_catalogue(orc):
+    # the same entry gloo ranks use, called in one process on three shards' host rows
+    # (events and injections split unevenly), against the oracle on the whole catalogue
+    from paper_2605_23538_gb300 import shard, synth
+    cat = synth.catalogue(synth.scaled("shard", 6, ("fixed", 150), 4, 128, 3000, "found"))
+    lam = synth.lambda_batch(3, purpose=54)
+    ne, ni = len(cat["offsets"]) - 1, len(cat["inj_m1"])
+    cuts_e, cuts_i = [0, 1, 4, ne], [0, ni // 5, ni // 2, ni]
+    parts = []
+    for r in range(3):
+        ev = list(range(cuts_e[r], cuts_e[r + 1]))
+        part = synth.subset_events(cat, ev)
+        for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
+            part[k] = cat[k][cuts_i[r]:cuts_i[r + 1]]
+        o = orc.loglik(part, lam, n_threads=1, neff_min_event=0.0)
+        parts.append({"sum_events": o["lnL_event"].sum(axis=1), "ln_xi": o["ln_xi"], "neff_sel": o["neff_sel"],
+                      "flags": o["flags"], "n_events": len(ev)})
+    merged = shard.merge_parts(parts)
+    assert merged["lnL_total"].device.type == "cpu"
+    ref = orc.loglik(cat, lam, n_threads=1, neff_min_event=0.0)
+    np.testing.assert_allclose(merged["ln_xi"].numpy(), ref["ln_xi"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(merged["neff_sel"].numpy(), ref["neff_sel"], rtol=1e-12)
+    np.testing.assert_allclose(merged["lnL_total"].numpy(), ref["lnL_total"], rtol=0, atol=1e-10)
+    np.testing.assert_array_equal(merged["flags"].numpy(), ref["flags"])
+
+
+def test_merge_entry_rejects_bad_shapes():
+    import ctypes
+    import paper_2605_23538_gb300 as g
+    buf = np.zeros(64)
+    outs = [np.zeros(4) for _ in range(3)] + [np.zeros(4, np.int32)]
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert g.lib().gwc_merge_parts(2, 1, 7, p(buf), 0, *[p(o) for o in outs], None, None) != 0
+    assert g.lib().gwc_merge_parts(0, 1, 0, p(buf), 0, *[p(o) for o in outs], None, None) != 0
+    assert g.lib().gwc_merge_parts(1, 1, 0, p(buf), 0, None, *[p(o) for o in outs[1:]], None, None) != 0
