@@ -135,7 +135,8 @@ typedef struct {
                             in [16, 4096] (default 512) */
   int32_t max_K;         /* largest Lambda batch a call may pass (default 256) */
   int32_t chunk;         /* samples per work item, 64..4096 (default 2048) */
-  int32_t lambda_tile;   /* Lambda points per CTA tile, 0..64 (0 = default 64) */
+  int32_t lambda_tile;   /* Lambda points per CTA tile, 0..256 (0 = default 64); a tile holds
+                            at most 512 / lambda_group points */
   int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 1) */
   int32_t cap_per_pixel; /* > 0: keep at most this many samples of each (event, pixel), chosen
                             at random as the paper's memory option does (it quotes 2500);
@@ -305,8 +306,9 @@ void gwc_hmc_destroy(gwc_hmc* hmc);   /* NULL is a no-op */
 
 /* Launch-shape autotuner.  Times whole calls (gwc_loglik_grad when want_grad != 0,
  * gwc_loglik otherwise) on the caller's K points d_lambda[K][P] (device) at every
- * shape of chunk in {1024, 2048} x Lambda tile in {16, 32, 64} (clamped to K) x warp
- * group in {1, 2, 4, 8}: one untimed call, then two timed with CUDA events on the
+ * shape of chunk in {1024, 2048} x Lambda tile in {16, 32, 64, 128, 256} (clamped to K)
+ * x warp group in {1, 2, 4, 8} with tile x group <= 512: one untimed call, then two
+ * timed with CUDA events on the
  * stream.  The fastest shape becomes the context's chunk, lambda_tile and lambda_group
  * for later calls (a new chunk re-splits the work items; results then differ from the
  * old shape's only by FP32 rounding order).  Synchronises the device, allocates scratch

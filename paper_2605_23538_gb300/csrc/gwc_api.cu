@@ -251,7 +251,8 @@ bool make_items(const int64_t* offsets, int32_t ne, int64_t ns, int64_t ni, int 
 // launch geometry of the fused kernel for a batch of K points
 void fused_geometry(const gwc_ctx* c, int K, int& slab, int& n_slabs) {
   slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : 64;
-  slab = std::max(1, std::min(std::min(slab, K), MAX_SLAB));
+  const int group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+  slab = std::max(1, std::min(std::min(slab, K), std::min(MAX_SLAB, MAX_SLAB_GROUP / group)));
   n_slabs = (K + slab - 1) / slab;
 }
 
@@ -1529,7 +1530,7 @@ gwc_status gwc_autotune(gwc_ctx* c, int32_t K, const double* d_lambda, int32_t w
   gwc_status st = GWC_OK;
   c->prof_off = true;
   const int chunks[] = {1024, 2048};
-  const int tiles[] = {16, 32, 64};
+  const int tiles[] = {16, 32, 64, 128, 256};
   const int groups[] = {1, 2, 4, 8};
   for (int chunk : chunks) {
     if (st != GWC_OK) break;
@@ -1540,6 +1541,7 @@ gwc_status gwc_autotune(gwc_ctx* c, int32_t K, const double* d_lambda, int32_t w
       if (st != GWC_OK || t == last_tile) continue;
       last_tile = t;
       for (int grp : groups) {
+        if (t * grp > MAX_SLAB_GROUP) continue;   // the geometry would cut the tile
         c->opt.lambda_tile = t;
         c->opt.lambda_group = grp;
         auto run = [&]() {

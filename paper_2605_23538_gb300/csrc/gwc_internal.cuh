@@ -300,6 +300,8 @@ __device__ __forceinline__ float biased_float(float f) { return f - FLOOR_BIAS; 
 // falls more than 48 below the reference skip the derivative work: their weight is below
 // 2^-48 of the sum's largest.
 constexpr float GRAD_SKIP = 48.f;
+// how far above an accumulator's reference a sample may lie before the reference is raised
+constexpr float RESCALE_HEADROOM = 32.f;
 
 // WITH_LOS = false leaves out the LOS factor (the weight w' of the KDE form, whose LOS
 // prior enters through the grid integral instead).  Every sample whose d_L maps into
@@ -308,10 +310,11 @@ constexpr float GRAD_SKIP = 48.f;
 // mark the mass-order and mass-support cuts passed, and sink.windows(win1, win2, ok) the
 // whole value about to be formed, with the smoothing-window branches taken (a path census
 // uses them).  MP selects the multi-peak mass model (a second Gaussian in the
-// primary-mass mixture).  EDGE = false leaves out the mixture-bound code (the other-
-// component sums and sigma in S_LX); a caller may pass it only for Lambda points with
-// L.lam_edge = 0 (and L.lam1_edge = 0 for the multi-peak model).
-template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false, bool EDGE = true>
+// primary-mass mixture).  RARE = false leaves out the code of two rare kinds of Lambda
+// point: a mixture weight on a bound (the other-component sums and sigma in S_LX) and
+// |1 + beta| < 1e-3 (the series form of C(m1)); a caller may pass it only for points with
+// L.lam_edge = 0, L.lam1_edge = 0 (multi-peak model) and L.beta_small = 0.
+template <bool GRAD, typename RowT, typename Sink, bool WITH_LOS = true, bool MP = false, bool RARE = true>
 __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
                                            const RowT* __restrict__ row, int nz,
                                            const float4* __restrict__ pos,
@@ -428,7 +431,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     const float dl21 = lm2s2 - lm1s2;
     lin = fmaf(L.beta, dl21, fmaf(L.beta_lo, dl21, lin));
   } else {
-    if (L.beta_small == 0.f) {
+    if (!(RARE && L.beta_small != 0.f)) {
       A = ex2(fmaf(L.eps_b, lm1s2, L.eps_b_lo * lm1s2));   // m1s^(1+beta)
       Cx = fmaf(A, L.inv_eps_b, L.C0);
     } else {                                          // |1+beta| < 1e-3: series in y
@@ -461,12 +464,12 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
   const bool has_grad = sink.weight(lw2, live);
   // at a mixture bound every live sample adds to the other-component sum, whatever its
   // weight (its weight under the absent component can be large)
-  const bool edge = EDGE && (L.lam_edge != 0.f || (MP && L.lam1_edge != 0.f));
+  const bool edge = RARE && (L.lam_edge != 0.f || (MP && L.lam1_edge != 0.f));
 
   if (GRAD && sink.any(has_grad || (edge && live))) {
     // other-component sums at the mixture's bounds (the same branch for every lane of a
     // Lambda point): log2 of O/mix for the component whose weight is 0
-    if (EDGE && L.lam_edge != 0.f) {
+    if (RARE && L.lam_edge != 0.f) {
       float lo;
       if (!MP) {
         lo = L.lam >= 1.f ? fmaf(-L.alpha, lm1s2, L.la0_2) - b2             // mix = G: P/G
@@ -481,7 +484,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
       }
       sink.other(0, lw2, lo);
     }
-    if (EDGE && MP && L.lam1_edge != 0.f) {             // lam G2/mix (lam1 = 1) or lam G/mix
+    if (RARE && MP && L.lam1_edge != 0.f) {             // lam G2/mix (lam1 = 1) or lam G/mix
       const float zo = L.o2_hi != 0.f ? zz2 : zz;
       sink.other(1, lw2, fmaf(-HALF_LOG2EF * zo, zo, L.o2_l2) - (mx + lg2(mixf)));
     }
@@ -536,7 +539,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     } else {
       const float iC = rcp(Cx);
       float dC_db;
-      if (L.beta_small == 0.f) {
+      if (!(RARE && L.beta_small != 0.f)) {
         // dC/dbeta = C_beta(mw) + (A ln m1s - mw^(1+beta) ln mw - (C - C(mw))) / (1+beta)
         dC_db = fmaf(fmaf(A, lm1s, -fmaf(L.mw1b, L.lmw, Cx - L.Cw)), L.inv_eps_b, L.Cwb);
       } else {
@@ -565,7 +568,7 @@ __device__ __forceinline__ bool sample_lnw(const LamF& L, const SampleIn& s,
     sink.grad2(S_H0, Gz * x * invDp, fmaf(Gz, -u * J * invDp, -fmaf(-0.5f * u * u3m1, rE3, J) * invDp));
     // S_LX: pb, or sigma at lambda_peak = 1 / 0 for the single-peak model (the merge takes
     // the lambda derivative from it and the other-component sum)
-    sink.grad2(S_A1, pa, (EDGE && !MP && L.lam_edge != 0.f) ? L.lam_sig : pb);
+    sink.grad2(S_A1, pa, (RARE && !MP && L.lam_edge != 0.f) ? L.lam_sig : pb);
     sink.grad2(S_AL, pa * lm1s2, lm2s - dlnC_db);
     sink.grad2(S_MMIN, dS1_dmin - dS2_dm - dlnC_dmin, dS1_ddm + dS2_ddm - dlnC_ddm);
     const float pbz = pb * zz;
@@ -591,7 +594,10 @@ struct AccSink {
   __device__ __forceinline__ explicit AccSink(Acc<GRAD, KAHAN, NS>& acc) : a(acc) {}
   __device__ __forceinline__ bool any(bool p) { return __any_sync(0xffffffffu, p); }
   __device__ __forceinline__ bool weight(float lw, bool live) {
-    t = a.take(lw, live);
+    // the rescale is rare: one warp-uniform branch, each lane's own part selected inside
+    const bool up = live && lw > a.m + RESCALE_HEADROOM;
+    if (__any_sync(0xffffffffu, up)) a.rescale(lw, up);
+    t = a.add(lw, live);
     lv = live;
     hg = GRAD && live && !(lw < a.m - GRAD_SKIP);
     return hg;
@@ -638,7 +644,6 @@ struct TermSink {
 // RESCALE_HEADROOM, so every term is at most 2^32 and s2 at most 2^64 a term (float holds
 // 2^127); s1 >= 1 once a sample is in.  Partials and merges only use m as a common
 // reference, never as the maximum.
-constexpr float RESCALE_HEADROOM = 32.f;
 template <bool GRAD, bool KAHAN, int NS>
 struct Acc {
   static constexpr int NG2 = GRAD ? (NS + 1) / 2 : 1;   // packed statistic pairs
@@ -653,21 +658,22 @@ struct Acc {
     for (int q = 0; q < NO; ++q) { mO[q] = -INFINITY; sO[q] = 0.f; }
   }
   __device__ __forceinline__ float g(int i) const { return (i & 1) ? g2[i >> 1].y : g2[i >> 1].x; }
-  // add a sample of log2 weight lw (when live) to the value sums; returns its weight
-  // 2^(lw - m) relative to the (possibly new) reference m, 0 when not live
-  __device__ __forceinline__ float take(float lw, bool live) {
-    if (live && lw > m + RESCALE_HEADROOM) {
-      const float sc = ex2(m - lw);   // 0 on the first sample
-      s1 *= sc;
-      s2 *= sc * sc;
-      c1 *= sc;
-      c2 *= sc * sc;
-      if (GRAD) {
+  // raise the reference to lw where up is set (the sums rescaled; 0 on the first sample)
+  __device__ __forceinline__ void rescale(float lw, bool up) {
+    const float sc = up ? ex2(m - lw) : 1.f;
+    s1 *= sc;
+    s2 *= sc * sc;
+    c1 *= sc;
+    c2 *= sc * sc;
+    if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < NG2; ++i) g2[i] = __fmul2_rn(g2[i], make_float2(sc, sc));
-      }
-      m = lw;
+      for (int i = 0; i < NG2; ++i) g2[i] = __fmul2_rn(g2[i], make_float2(sc, sc));
     }
+    m = up ? lw : m;
+  }
+  // add a sample of log2 weight lw (when live) to the value sums, once the reference
+  // admits it (lw <= m + RESCALE_HEADROOM); returns its weight 2^(lw - m), 0 when not live
+  __device__ __forceinline__ float add(float lw, bool live) {
     const float tt = live ? ex2(lw - m) : 0.f;
     if (KAHAN) {
       float y1 = tt - c1, t1 = s1 + y1;

@@ -720,11 +720,12 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
   constexpr int NS = n_params(MP);   // gradient statistics of the mass model
   using Sink = AccSink<GRAD, KAHAN, NS>;
   const int CH = A.chunk;
-  // staged samples: {m1, m2, d_L, -log2 pi}, {log2 m1, log2 m2}, pixel (3 loads a sample)
+  // staged samples: {m1, m2, d_L, -log2 pi}, {log2 m1, log2 m2, pixel, 0} (two loads a
+  // sample); the value kernel's partials need only (m, s1, s2)
+  constexpr int PS = GRAD ? PSTRIDE : 4;
   float4* s_a = reinterpret_cast<float4*>(sm);
-  float2* s_b = reinterpret_cast<float2*>(s_a + CH);
-  int* s_pix = reinterpret_cast<int*>(s_b + CH);
-  float* s_part = reinterpret_cast<float*>(s_pix + CH);   // [slab][G][PSTRIDE]
+  float4* s_b = s_a + CH;
+  float* s_part = reinterpret_cast<float*>(s_b + CH);   // [slab][G][PS]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = A.group, ngroups = WARPS / G;
@@ -738,8 +739,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
   for (int i = tid; i < it.count; i += THREADS) {
     const float4 v = __ldg(src + it.begin + i);
     s_a[i] = make_float4(v.x, v.y, v.z, -to_log2(v.w));
-    s_b[i] = make_float2(log2f(v.x), log2f(v.y));
-    s_pix[i] = inj ? 0 : __ldg(A.pix + it.begin + i);
+    s_b[i] = make_float4(log2f(v.x), log2f(v.y), __int_as_float(inj ? 0 : __ldg(A.pix + it.begin + i)), 0.f);
   }
   if (tid == 0) *s_next = 0;
   __syncthreads();
@@ -772,27 +772,29 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       const float4* ws = wv + (NW_WIN + 1);
       // every lane of the warp runs the same number of iterations (the per-sample
       // arithmetic votes over the warp); lanes past the end repeat the run's last sample
-      // with valid = false.  Points on a mixture bound take their own instance of the loop.
-      auto sweep = [&](auto edge_tag) {
-        constexpr bool EDGE = decltype(edge_tag)::value;
+      // with valid = false.  Rare points (a mixture weight on a bound, |1+beta| < 1e-3) take
+      // their own instance of the loop.
+      auto sweep = [&](auto rare_tag) {
+        constexpr bool RARE = decltype(rare_tag)::value;
         for (int base = a; base < b; base += 32) {
           const int i = min(base + lane, b - 1);
           SampleIn s;
           const float4 va = s_a[i];
-          const float2 vb = s_b[i];
+          const float4 vb = s_b[i];
           s.m1 = va.x; s.m2 = va.y; s.dl = va.z; s.npe2 = va.w;
           s.lm1 = vb.x; s.lm2 = vb.y;
           s.valid = base + lane < b;
           float lw;
           Sink sink(acc);
           if (inj)
-            sample_lnw<GRAD, float, Sink, true, MP, EDGE>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
+            sample_lnw<GRAD, float, Sink, true, MP, RARE>(L, s, A.pbar32, nz, pos, aux, nx, wv, ws, lw, sink);
           else
-            sample_lnw<GRAD, RowT, Sink, true, MP, EDGE>(L, s, reinterpret_cast<const RowT*>(A.los) +
-                                                           (size_t)s_pix[i] * nz, nz, pos, aux, nx, wv, ws, lw, sink);
+            sample_lnw<GRAD, RowT, Sink, true, MP, RARE>(L, s, reinterpret_cast<const RowT*>(A.los) +
+                                                           (size_t)__float_as_int(vb.z) * nz, nz, pos, aux, nx, wv, ws,
+                                                           lw, sink);
         }
       };
-      if (GRAD && (L.lam_edge != 0.f || (MP && L.lam1_edge != 0.f)))
+      if ((GRAD && (L.lam_edge != 0.f || (MP && L.lam1_edge != 0.f))) || L.beta_small != 0.f)
         sweep(std::true_type{});
       else
         sweep(std::false_type{});
@@ -820,15 +822,17 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       }
       acc.merge(om_, o1, o2, og, omO, osO);
     }
-    float* slot = s_part + ((size_t)kk * G + wg) * PSTRIDE;
+    float* slot = s_part + ((size_t)kk * G + wg) * PS;
     if (lane == 0) {
       slot[0] = acc.m;
       slot[1] = acc.s1;
       slot[2] = acc.s2;
-      slot[PART_MO] = acc.mO[0];
-      slot[PART_SO] = acc.sO[0];
-      slot[PART_MO2] = AccT::NO > 1 ? acc.mO[AccT::NO - 1] : -INFINITY;
-      slot[PART_SO2] = AccT::NO > 1 ? acc.sO[AccT::NO - 1] : 0.f;
+      if (GRAD) {
+        slot[PART_MO] = acc.mO[0];
+        slot[PART_SO] = acc.sO[0];
+        slot[PART_MO2] = AccT::NO > 1 ? acc.mO[AccT::NO - 1] : -INFINITY;
+        slot[PART_SO2] = AccT::NO > 1 ? acc.sO[AccT::NO - 1] : 0.f;
+      }
     }
     if (GRAD && lane < NS) {
       float gv = 0.f;
@@ -838,19 +842,22 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     }
   }
   __syncthreads();
-  // combine the G warps' sums of each Lambda in warp order: lane q owns component q
+  // combine the G warps' sums of each Lambda in warp order: lane q owns component q.
+  // The partial's reference is the warps' largest rounded up to an integer (the FP64
+  // merge then rescales by exact powers of two).
   for (int kk = warp; kk < nk; kk += WARPS) {
-    const float* sl = s_part + (size_t)kk * G * PSTRIDE;
+    const float* sl = s_part + (size_t)kk * G * PS;
     float M = -INFINITY;
-    for (int w = 0; w < G; ++w) M = fmaxf(M, sl[w * PSTRIDE]);
+    for (int w = 0; w < G; ++w) M = fmaxf(M, sl[w * PS]);
+    M = ceilf(M);
     float* out = A.partials + ((size_t)(k0 + kk) * A.stride + A.slot0 + item) * PSTRIDE;
     const int ncomp = GRAD ? 2 + NS : 2;   // s1, s2 (and g)
     if (lane < ncomp) {
       float acc = 0.f;
       if (M > -INFINITY) {
         for (int w = 0; w < G; ++w) {
-          const float mw = sl[w * PSTRIDE];
-          if (mw > -INFINITY) acc = fmaf(sl[w * PSTRIDE + 1 + lane], lane == 1 ? ex2(2.f * (mw - M)) : ex2(mw - M), acc);
+          const float mw = sl[w * PS];
+          if (mw > -INFINITY) acc = fmaf(sl[w * PS + 1 + lane], lane == 1 ? ex2(2.f * (mw - M)) : ex2(mw - M), acc);
         }
       }
       out[1 + lane] = acc;
@@ -859,12 +866,13 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     if (GRAD && (lane == ncomp || lane == ncomp + 1)) {   // the lanes past the sums: one other pair each
       const int pm = lane == ncomp ? PART_MO : PART_MO2;
       float MO = -INFINITY;
-      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PSTRIDE + pm]);
+      for (int w = 0; w < G; ++w) MO = fmaxf(MO, sl[w * PS + pm]);
+      MO = ceilf(MO);
       float so = 0.f;
       if (MO > -INFINITY) {
         for (int w = 0; w < G; ++w) {
-          const float mo = sl[w * PSTRIDE + pm];
-          if (mo > -INFINITY) so = fmaf(sl[w * PSTRIDE + pm + 1], ex2(mo - MO), so);
+          const float mo = sl[w * PS + pm];
+          if (mo > -INFINITY) so = fmaf(sl[w * PS + pm + 1], ex2(mo - MO), so);
         }
       }
       out[pm] = MO;
@@ -1167,8 +1175,10 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
     }
   }
   if (lane == 0) {
-    const float S = acc * dzg / (h * 2.50662827463100050242f);   // h sqrt(2 pi)
-    out[0] = S > 0.f ? m : -INFINITY;
+    // the reference rounded up to an integer for the merge, the sum scaled to it
+    const float mi = ceilf(m);
+    const float S = acc * dzg / (h * 2.50662827463100050242f) * ex2(m - mi);   // h sqrt(2 pi)
+    out[0] = S > 0.f ? mi : -INFINITY;
     out[1] = S;
     out[2] = S * S;
   }
@@ -1277,6 +1287,7 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
     __syncthreads();
     m = red[0][0];
     for (int q = 1; q < 8; ++q) m = fmaxf(m, red[0][q]);
+    m = ceilf(m);   // an integer reference for the merge (and the gradient pass)
     float s1 = 0.f, s2 = 0.f;
     if (m > -INFINITY)
       for (int i = tid; i < it.count; i += 256) {
@@ -1321,7 +1332,17 @@ __global__ void __launch_bounds__(256) k_plain_reduce(PlainArgs A) {
 }
 
 // -------------------------------------------------------------------- merge
-// Partial maxima arrive in log2 units; the FP64 sums scale by powers of two.
+// Partial references arrive in log2 units and are integers (every producer rounds its
+// reference up to one and scales its sums to it), so every rescale of the FP64 sums is
+// an exact power of two: 2^k from the exponent field, without the FP64 exp2 sequence
+// (GB300's FP64 pipe runs at 1/64 of the FP32 rate, and the merge of a small batch is
+// a chain of such rescales).  Below the FP64 range the term is dropped (it is below
+// 2^-1022 of the largest), above it the result is infinite.
+__device__ __forceinline__ double pow2i(double k) {
+  if (!(k >= -1022.0)) return 0.0;
+  if (k > 1023.0) return INFINITY;
+  return __longlong_as_double((long long)(1023 + (int)k) << 52);
+}
 constexpr double LN2D = 0.69314718055994530942;
 
 template <bool GRAD>
@@ -1372,7 +1393,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       for (int s = s0; s < s1; ++s) {
         const float* p = pk + (size_t)s * PSTRIDE;
         if (!(p[0] > -INFINITY)) continue;
-        const double r = exp2((double)p[0] - M);
+        const double r = pow2i((double)p[0] - M);
         S1 += (double)p[1] * r;
         S2 += (double)p[2] * r * r;
         if (GRAD)
@@ -1387,17 +1408,19 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         for (int s = s0; s < s1; ++s) {
           const float* p = pk + (size_t)s * PSTRIDE;
           if (D.lam_sigma != 0 && p[PART_MO] > -INFINITY)
-            G[P_LAM] -= D.lam_sigma * (double)p[PART_SO] * exp2((double)p[PART_MO] - M);
+            G[P_LAM] -= D.lam_sigma * (double)p[PART_SO] * pow2i((double)p[PART_MO] - M);
           if (D.lam1_sigma != 0 && p[PART_MO2] > -INFINITY)
-            G[P_LAM1] -= D.lam1_sigma * (double)p[PART_SO2] * exp2((double)p[PART_MO2] - M);
+            G[P_LAM1] -= D.lam1_sigma * (double)p[PART_SO2] * pow2i((double)p[PART_MO2] - M);
         }
     }
     double lnL = -INFINITY, neff = 0.0;
     if (S1 > 0.0) {
       lnL = M * LN2D + log(S1) - log(A.ev_n[e]) + lamd_c(D);
       neff = S1 * S1 / S2;
-      if (GRAD)
-        for (int i = 0; i < NPK; ++i) sg[i] += G[i] / S1 + lamd_dc(D, i);
+      if (GRAD) {
+        const double iS1 = 1.0 / S1;
+        for (int i = 0; i < NPK; ++i) sg[i] += G[i] * iS1 + lamd_dc(D, i);
+      }
     }
     A.lnL_event[(size_t)k * ne + e] = lnL;
     A.neff_event[(size_t)k * ne + e] = neff;
@@ -1424,21 +1447,21 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       const int pm = q == 0 ? PART_MO : PART_MO2;
       if (GRAD && (q == 0 ? D.lam_sigma : D.lam1_sigma) != 0 && p[pm] > -INFINITY) {
         const double mo = p[pm];
-        if (mo > oM[q]) { oS[q] = oS[q] * exp2(oM[q] - mo) + (double)p[pm + 1]; oM[q] = mo; }
-        else oS[q] += (double)p[pm + 1] * exp2(mo - oM[q]);
+        if (mo > oM[q]) { oS[q] = oS[q] * pow2i(oM[q] - mo) + (double)p[pm + 1]; oM[q] = mo; }
+        else oS[q] += (double)p[pm + 1] * pow2i(mo - oM[q]);
       }
     }
     const double m = p[0];
     if (!(m > -INFINITY)) continue;
     if (m > sM) {
-      const double r = exp2(sM - m);
+      const double r = pow2i(sM - m);
       sS1 *= r;
       sS2 *= r * r;
       if (GRAD)
         for (int i = 0; i < NPK; ++i) sG[i] *= r;
       sM = m;
     }
-    const double r = exp2(m - sM);
+    const double r = pow2i(m - sM);
     sS1 += (double)p[1] * r;
     sS2 += (double)p[2] * r * r;
     if (GRAD)
@@ -1454,7 +1477,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       for (int q = 0; q < 2; ++q) {
         const double x_m = __shfl_xor_sync(0xffffffffu, oM[q], o), x_s = __shfl_xor_sync(0xffffffffu, oS[q], o);
         const double MO = fmax(oM[q], x_m);
-        if (MO > -INFINITY) { oS[q] = oS[q] * exp2(oM[q] - MO) + x_s * exp2(x_m - MO); oM[q] = MO; }
+        if (MO > -INFINITY) { oS[q] = oS[q] * pow2i(oM[q] - MO) + x_s * pow2i(x_m - MO); oM[q] = MO; }
       }
     sumL += __shfl_xor_sync(0xffffffffu, sumL, o);
     fail |= __shfl_xor_sync(0xffffffffu, fail, o);
@@ -1468,7 +1491,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       for (int i = 0; i < NPK; ++i) oG[i] = __shfl_xor_sync(0xffffffffu, sG[i], o);
     const double M = fmax(sM, oM);
     if (M > -INFINITY) {
-      const double ra = exp2(sM - M), rb = exp2(oM - M);
+      const double ra = pow2i(sM - M), rb = pow2i(oM - M);
       sS1 = sS1 * ra + o1 * rb;
       sS2 = sS2 * ra * ra + o2 * rb * rb;
       if (GRAD)
@@ -1506,7 +1529,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     if (M > -INFINITY) {
       for (int q = 0; q < nw; ++q) {
         if (!(rsel[q][0] > -INFINITY)) continue;
-        const double r = exp2(rsel[q][0] - M);
+        const double r = pow2i(rsel[q][0] - M);
         S1 += rsel[q][1] * r;
         S2 += rsel[q][2] * r * r;
         if (GRAD)
@@ -1519,8 +1542,8 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       }
       if (GRAD)
         for (int q = 0; q < nw; ++q) {
-          if (D.lam_sigma != 0 && rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * exp2(rO[q][0] - M);
-          if (D.lam1_sigma != 0 && rO[q][2] > -INFINITY) G[P_LAM1] -= D.lam1_sigma * rO[q][3] * exp2(rO[q][2] - M);
+          if (D.lam_sigma != 0 && rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * pow2i(rO[q][0] - M);
+          if (D.lam1_sigma != 0 && rO[q][2] > -INFINITY) G[P_LAM1] -= D.lam1_sigma * rO[q][3] * pow2i(rO[q][2] - M);
         }
     }
     int flag = (fl & 1) ? 2 : 0;
@@ -1776,18 +1799,18 @@ template <bool G, bool KH, typename RT, bool MP> struct FusedOccupancy {
   static cudaError_t run(size_t smem, int* out) { return occupancy_t<G, KH, RT, MP>(smem, out); }
 };
 
-size_t fused_smem_bytes(int chunk, int slab, int group) {
-  return (size_t)chunk * 7 * sizeof(float) + (size_t)slab * group * PSTRIDE * sizeof(float);
+size_t fused_smem_bytes(int chunk, int slab, int group, bool grad) {
+  return (size_t)chunk * 8 * sizeof(float) + (size_t)slab * group * (grad ? PSTRIDE : 4) * sizeof(float);
 }
-size_t fused_smem_max() { return fused_smem_bytes(4096, MAX_SLAB, WARPS); }
+size_t fused_smem_max() { return fused_smem_bytes(4096, MAX_SLAB_GROUP, 1, true); }
 
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s) {
-  const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
+  const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group, grad);
   return fused_dispatch<FusedLaunch>(grad, kahan, bf16, a.mp != 0, a, grid, smem, s);
 }
 
 cudaError_t fused_blocks_per_sm(const FusedArgs& a, bool grad, bool kahan, bool bf16, int* out) {
-  const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group);
+  const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group, grad);
   return fused_dispatch<FusedOccupancy>(grad, kahan, bf16, a.mp != 0, smem, out);
 }
 

@@ -166,8 +166,10 @@ cudaError_t launch_hmc(const HmcArgs& a, cudaStream_t s);
 // upload the prologue's Gauss-Legendre constants to the current device (once per device)
 cudaError_t ensure_gauss_legendre();
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s);
-constexpr int MAX_SLAB = 64;   // Lambda points per CTA tile at most
-size_t fused_smem_bytes(int chunk, int slab, int group);
+constexpr int MAX_SLAB = 256;        // Lambda points per CTA tile at most
+constexpr int MAX_SLAB_GROUP = 512;  // tile points x warps per point at most (the combine's
+                                     // shared memory: this many partials of PSTRIDE floats)
+size_t fused_smem_bytes(int chunk, int slab, int group, bool grad);
 size_t fused_smem_max();
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s);
 // CTAs of the fused kernel that fit on one SM at this geometry (occupancy query)
