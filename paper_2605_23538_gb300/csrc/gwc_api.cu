@@ -68,6 +68,7 @@ struct gwc_ctx {
   float* tables = nullptr;
   float* partials = nullptr;
   int32_t* counter = nullptr;   // work counter of the persistent fused kernel
+  int32_t* order = nullptr;     // [max_K] the batch's points ordered by H0 (the prologue writes it)
   int64_t items_cap = 0;        // work items the items/sched/partials buffers hold
   int live_recordings = 0;      // graphs and HMC objects recorded on this context
   // KDE form of the event term: (event, pixel) groups, built at create; device copies,
@@ -137,7 +138,7 @@ void free_all(gwc_ctx* c) {
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   c->prof_ev.clear();
   void* dev[] = {c->smp, c->pix, c->inj, c->los, c->pbar32, c->pbar64, c->items, c->sched,
-                 c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->d_lam, c->d_out,
+                 c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->order, c->d_lam, c->d_out,
                  c->kde_groups, c->kde_ev_group0, c->kde_sched_inj, c->kde_pgrid, c->kde_partials, c->kde_lm,
                  c->d_flags, c->sample_item, c->plain_lw, c->plain_tg};
   for (void* p : dev)
@@ -274,6 +275,7 @@ gwc_status run_prologue(gwc_ctx* c, int K, const double* d_lambda, bool grad, cu
                         int32_t* counter = nullptr) {
   ProArgs pa;
   pa.counter = counter;
+  pa.order = c->order;
   pa.lam = d_lambda;
   pa.nx = c->opt.n_x_table;
   pa.nz = c->n_z;
@@ -349,6 +351,7 @@ gwc_status launch_fused_items(gwc_ctx* c, int32_t K, bool grad, const int32_t* s
   fa.tstride = c->tstride;
   fa.partials = partials;
   fa.counter = c->counter;
+  fa.order = c->order;
   fa.n_sched = n_sched;
   fa.stride = (int)stride;
   fa.slot0 = (int)slot0;
@@ -770,6 +773,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(dalloc(c, &c->tables, (size_t)o.max_K * c->tstride));
   chk(dalloc(c, &c->partials, (size_t)kcap * c->n_items * PSTRIDE));
   chk(dalloc(c, &c->counter, 1));
+  chk(dalloc(c, &c->order, (size_t)o.max_K));
   chk(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device));
   chk(dalloc(c, &c->d_lam, (size_t)o.max_K * NP_MAX));
   chk(dalloc(c, &c->d_out, (size_t)o.max_K * (2 * (size_t)std::max(ne, 1) + 3 + NP_MAX)));

@@ -252,6 +252,22 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     else return p;
   };
   if (k == 0 && rank == 0 && tid == 0 && A.counter) *A.counter = 0;
+  if (A.order && rank == 0 && tid < 32) {
+    // this point's rank in the batch ordered by H0 (ties and NaN by index): the fused
+    // kernel takes points in that order, so the warps of a CTA work on points whose
+    // distance-redshift relations, and hence LOS cells, are alike
+    const int np = n_params(A.mp != 0);
+    const double hk = A.lam[(size_t)k * np + P_H0];
+    const double kk = hk == hk ? hk : INFINITY;
+    int r = 0;
+    for (int j = tid; j < (int)gridDim.x; j += 32) {
+      const double hj0 = A.lam[(size_t)j * np + P_H0];
+      const double hj = hj0 == hj0 ? hj0 : INFINITY;
+      r += (hj < kk || (hj == kk && j < k)) ? 1 : 0;
+    }
+    r = __reduce_add_sync(0xffffffffu, r);
+    if (tid == 0) A.order[r] = k;
+  }
   const bool mp = A.mp != 0;
   const double* L = A.lam + (size_t)k * n_params(mp);
   LamF* lf = A.lf + k;
@@ -761,7 +777,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     return __shfl_sync(0xffffffffu, v, 0);
   };
   for (int kk = (G == 1) ? next_k(0) : gidx; kk < nk; kk = next_k(kk)) {
-    const int k = k0 + kk;
+    const int k = A.order ? A.order[k0 + kk] : k0 + kk;
     const LamF L = A.lf[k];
     Acc<GRAD, KAHAN, NS> acc;
     if (L.live != 0.f) {
@@ -822,6 +838,33 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       }
       acc.merge(om_, o1, o2, og, omO, osO);
     }
+    if (G == 1) {
+      // one warp per point: the warp's sums are the partial; written straight to global
+      // memory with the reference rounded up to an integer (the FP64 merge then rescales
+      // by exact powers of two), no shared-memory combine
+      float* out = A.partials + ((size_t)k * A.stride + A.slot0 + item) * PSTRIDE;
+      const float M = ceilf(acc.m);
+      const float sc = M > -INFINITY ? ex2(acc.m - M) : 0.f;
+      if (lane == 0) {
+        out[0] = M;
+        out[1] = acc.s1 * sc;
+        out[2] = acc.s2 * (sc * sc);
+      }
+      if (GRAD && lane < NS) {
+        float gv = 0.f;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) gv = (lane == q) ? acc.g(q) : gv;
+        out[3 + lane] = gv * sc;
+      }
+      if (GRAD && lane < 2) {   // the other-component pairs
+        const float mo = lane == 0 ? acc.mO[0] : (AccT::NO > 1 ? acc.mO[AccT::NO - 1] : -INFINITY);
+        const float so = lane == 0 ? acc.sO[0] : (AccT::NO > 1 ? acc.sO[AccT::NO - 1] : 0.f);
+        const float MO = ceilf(mo);
+        out[lane == 0 ? PART_MO : PART_MO2] = MO;
+        out[lane == 0 ? PART_SO : PART_SO2] = MO > -INFINITY ? so * ex2(mo - MO) : 0.f;
+      }
+      continue;
+    }
     float* slot = s_part + ((size_t)kk * G + wg) * PS;
     if (lane == 0) {
       slot[0] = acc.m;
@@ -841,6 +884,7 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
       slot[3 + lane] = gv;
     }
   }
+  if (G == 1) return;   // the caller's barrier precedes the next unit's staging
   __syncthreads();
   // combine the G warps' sums of each Lambda in warp order: lane q owns component q.
   // The partial's reference is the warps' largest rounded up to an integer (the FP64
@@ -850,7 +894,8 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     float M = -INFINITY;
     for (int w = 0; w < G; ++w) M = fmaxf(M, sl[w * PS]);
     M = ceilf(M);
-    float* out = A.partials + ((size_t)(k0 + kk) * A.stride + A.slot0 + item) * PSTRIDE;
+    const int kq = A.order ? A.order[k0 + kk] : k0 + kk;
+    float* out = A.partials + ((size_t)kq * A.stride + A.slot0 + item) * PSTRIDE;
     const int ncomp = GRAD ? 2 + NS : 2;   // s1, s2 (and g)
     if (lane < ncomp) {
       float acc = 0.f;
@@ -894,7 +939,7 @@ __global__ void __launch_bounds__(THREADS, GRAD ? MINB_GRAD : MINB_VALUE) k_fuse
     const int unit = s_unit;
     if (unit >= n_units) break;
     fused_unit<GRAD, KAHAN, RowT, MP>(A, unit, sm, &s_next);
-    __syncthreads();   // the combine has read s_part before the next unit restages
+    __syncthreads();   // every warp is done with the staged samples (and the combine with s_part)
   }
 }
 
@@ -1800,9 +1845,11 @@ template <bool G, bool KH, typename RT, bool MP> struct FusedOccupancy {
 };
 
 size_t fused_smem_bytes(int chunk, int slab, int group, bool grad) {
-  return (size_t)chunk * 8 * sizeof(float) + (size_t)slab * group * (grad ? PSTRIDE : 4) * sizeof(float);
+  // one warp per point writes its partials directly: no combine buffer
+  const size_t part = group == 1 ? 0 : (size_t)slab * group * (grad ? PSTRIDE : 4) * sizeof(float);
+  return (size_t)chunk * 8 * sizeof(float) + part;
 }
-size_t fused_smem_max() { return fused_smem_bytes(4096, MAX_SLAB_GROUP, 1, true); }
+size_t fused_smem_max() { return fused_smem_bytes(4096, MAX_SLAB_GROUP / 2, 2, true); }   // the largest shape
 
 cudaError_t launch_fused(const FusedArgs& a, bool grad, bool kahan, bool bf16, int grid, cudaStream_t s) {
   const size_t smem = fused_smem_bytes(a.chunk, a.slab, a.group, grad);

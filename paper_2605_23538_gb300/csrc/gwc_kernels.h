@@ -23,6 +23,8 @@ struct ProArgs {
   int tstride;
   int want_grad;
   int* counter = nullptr;   // zeroed by CTA 0 when set (the fused kernel's work counter)
+  int32_t* order = nullptr; // when set: order[r] = the Lambda point of rank r by H0 (the
+                            // order in which the fused kernel takes points)
 };
 
 struct FusedArgs {
@@ -46,6 +48,7 @@ struct FusedArgs {
   int tstride;
   float* partials;        // [K][stride][PSTRIDE], slot slot0 + item
   int* counter;           // next (item, slab) unit; zero at launch
+  const int32_t* order;   // Lambda points in the order taken (by H0), or null (index order)
   int n_sched;            // schedule entries (units = n_sched * n_slabs)
   int stride;             // partial slots per Lambda
   int slot0;              // slot of item 0

@@ -75,6 +75,11 @@ def compare(got, ref, grad=False, label=""):
         assert np.all(rel <= TOL_GRAD), f"{label}: grad rel err {rel.max()} at {np.unravel_index(rel.argmax(), rel.shape)}"
         out["grad_rel"] = float(rel.max())
         out["kink_used"] = int(np.count_nonzero((np.abs(gg - gr) > 1e-4 * np.maximum(np.abs(gr), 1e-2 * sc)) & (kink > 0)))
+        # the plain relative error of each finite component, and how many components pass
+        # only through the 1e-2 x scale floor (|d| > 1e-4 |g| where |g| < 1e-2 scale)
+        plain = np.abs(gg - gr)[ft] / np.maximum(np.abs(gr[ft]), 1e-300)
+        out["grad_plain_rel_max"] = float(plain.max()) if plain.size else 0.0
+        out["floor_used"] = int(np.count_nonzero(((np.abs(gr) < 1e-2 * sc) & (np.abs(gg - gr) > TOL_GRAD * np.abs(gr)))[ft]))
     print(label, out)
     return out
 
