@@ -273,10 +273,15 @@ def host_description():
     return desc
 
 
-def oracle_sample(cat, n_ev, n_inj):
-    """The first n_ev events and the first n_inj injections of the workload."""
+def oracle_sample(cat, n_ev, n_inj=None):
+    """The first n_ev events and the first n_inj injections of the workload; by default
+    as many injections per event sample as the whole workload has (the two kinds of
+    evaluation cost differently: many injections leave at the mass cut)."""
     from paper_2605_23538_gb300 import synth
     sub = synth.subset_events(cat, range(n_ev))
+    if n_inj is None:
+        n_inj = int(round(int(sub["offsets"][-1]) * len(cat["inj_m1"]) / len(cat["m1"])))
+    n_inj = max(1, min(n_inj, len(cat["inj_m1"])))
     for k in ("inj_m1", "inj_m2", "inj_dl", "inj_lnpd"):
         sub[k] = cat[k][:n_inj]
     return sub, int(sub["offsets"][-1]) + n_inj
@@ -291,9 +296,10 @@ def cpu_baseline(cat, lam, max_seconds=20.0):
     # all cores: at least four events per core (the oracle runs events in parallel, and
     # injections in chunks of about n_inj / (4 cores)); grow the sample until one timed
     # pass takes about half of max_seconds or more
-    n_ev, n_inj = min(n_ev_max, 4 * cores), 20_000
+    n_ev = min(n_ev_max, 4 * cores)
     while True:
-        sub, evals = oracle_sample(cat, n_ev, n_inj)
+        sub, evals = oracle_sample(cat, n_ev)
+        n_inj = len(sub["inj_m1"])
         t0 = time.perf_counter()
         oracle.loglik(sub, lam[:1], grad=True, n_threads=cores)
         dt = time.perf_counter() - t0
@@ -301,12 +307,12 @@ def cpu_baseline(cat, lam, max_seconds=20.0):
             break
         grow = max(1.5, min(8.0, 0.7 * max_seconds / max(dt, 1e-3)))
         n_ev = min(n_ev_max, int(n_ev * grow))
-        n_inj = min(len(cat["inj_m1"]), int(n_inj * grow))
     value = evals / dt
     # one core: a slice of the same sample sized to take about a quarter of max_seconds
     frac = min(1.0, 0.25 * max_seconds / max(dt * cores, 1e-3))
-    n1_ev, n1_inj = max(1, int(n_ev * frac)), max(1000, int(n_inj * frac))
-    sub1, evals1 = oracle_sample(cat, n1_ev, n1_inj)
+    n1_ev = max(1, int(n_ev * frac))
+    sub1, evals1 = oracle_sample(cat, n1_ev)
+    n1_inj = len(sub1["inj_m1"])
     t0 = time.perf_counter()
     oracle.loglik(sub1, lam[:1], grad=True, n_threads=1)
     dt1 = time.perf_counter() - t0
@@ -351,10 +357,24 @@ def hmc_c1(g, synth, stream):
         # be rising, so the first ones can be slow
         ms = float(np.median([ev[t].elapsed_time(ev[t + 1]) for t in range(HMC_TRAJ)]))
         h.close()
+        # where a K = 1 evaluation's time goes: direct value+gradient calls with the
+        # library's per-stage events (not inside a graph)
+        out = g._outputs(1, ctx.n_events, q.device, True)
+        for _ in range(10):
+            g.loglik_grad(ctx._ctx, q, ctx.n_events, stream, out)
+        torch.cuda.synchronize()
+        ctx.profile_enable(True)
+        ctx.profile_read()
+        for _ in range(50):
+            g.loglik_grad(ctx._ctx, q, ctx.n_events, stream, out)
+        stage_ms, n_calls = ctx.profile_read()
+        ctx.profile_enable(False)
+    stages = {name: stage_ms[i] / max(n_calls, 1) for i, name in enumerate(("prologue", "fused", "merge"))}
     return {"workload": "c1 (10 events x 1000 samples, 1e4 draws), K = 1",
             "leapfrog_steps": HMC_LEAPFROG, "ms_per_trajectory": ms, "statistic": "median of 30",
             "evals_per_s": (HMC_LEAPFROG + 1) * n / (ms / 1e3),
-            "acceptance": float(acc.item()) / HMC_TRAJ}
+            "acceptance": float(acc.item()) / HMC_TRAJ,
+            "stage_ms_per_call": stages}
 
 
 # The paper's KDE form of the event term (value only), on the bench's catalogue with the
@@ -365,12 +385,14 @@ KDE_K = 16
 # Work of the KDE kernel, counted from its source as lower bounds (gwc_kde_census): one
 # evaluation of the weight w' (the value arithmetic without the LOS factor: the live,
 # in_range, mass_order, support and value stages of WORK less the LOS interpolation, with
-# the closed-form C(m1)) per second-pass sample with a weight, and per grid term d = z_g - z,
-# (c d) d, and the accumulation T += p_LOS(z_g) 2^((c d) d): 4 FP32 operations and one ex2.
+# the closed-form C(m1)) per second-pass sample with a weight, and per grid term the
+# kernel's value by the product recurrence and its accumulation, T += p_LOS(z_g) e,
+# e *= r, r *= q (3 FP32 operations), plus each block of 4 terms' start, d_0, e_0 =
+# 2^((c d_0) d_0) and r_0 (5 FP32 operations, two ex2): 4.25 FP32 and 0.5 ex2 a term.
 # The first pass's evaluations (which repeat the second's for kept samples) and the
 # bandwidths' order statistics are not charged.
 KDE_WORK_EVAL = (46, {"ex2": 4, "lg2": 2, "rcp": 2, "rsqrt": 1})
-KDE_WORK_TERM = (4, {"ex2": 1})
+KDE_WORK_TERM = (4.25, {"ex2": 0.5})
 
 
 def kde_timing(g, ctx, lam, n_evals, stream, peaks):
@@ -400,7 +422,7 @@ def kde_timing(g, ctx, lam, n_evals, stream, peaks):
            for t in SFU_TYPES}
     roof = alu_roofline({"fp32_method": fp32, "fp32_precision": 0, "sfu": sfu}, kde_ms / 1e3, peaks, None)
     roof["census"] = census
-    roof["work"] = "lower bound: w' once per weighted second-pass sample, 4 FP32 + 1 ex2 per grid term"
+    roof["work"] = "lower bound: w' once per weighted second-pass sample, 4.25 FP32 + 0.5 ex2 per grid term"
     return {"K": k, "bandwidth": "scott", "n_grid": 256, "ms_per_call": ms, "kde_kernel_ms": kde_ms,
             "value": n_evals * k / (ms / 1e3), "unit": "evals/s (value only)", "roofline": roof}
 
@@ -429,7 +451,7 @@ def multipeak_timing(g, synth, cat, K, n_evals, stream, steps=3):
 # The reference arm's sample per step: enough events that every core has several (the
 # oracle runs events in parallel, and injections in chunks of about n_inj / (4 cores)),
 # about 3 s of work per step on 16 cores
-REF_EVENTS, REF_INJECTIONS = 64, 400_000
+REF_EVENTS = 64
 
 
 def run_reference(args):
@@ -444,7 +466,8 @@ def run_reference(args):
     lam = synth.lambda_batch(K_LAMBDA, purpose=4)
     cores = os.cpu_count() or 1
     n_ev = max(REF_EVENTS, 4 * cores)
-    sub, evals = oracle_sample(cat, n_ev, REF_INJECTIONS)
+    sub, evals = oracle_sample(cat, n_ev)
+    n_inj = len(sub["inj_m1"])
     for w in range(args.warmup):
         oracle.loglik(sub, lam[w % K_LAMBDA:w % K_LAMBDA + 1], grad=True, n_threads=cores)
     t0 = time.perf_counter()
@@ -454,7 +477,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = evals * args.steps / dt
     sample = (f"per step 1 Lambda of the bench's batch x ({int(sub['offsets'][-1])} samples of the first "
-              f"{n_ev} events + the first {REF_INJECTIONS} injections), FP64 value+gradient")
+              f"{n_ev} events + the first {n_inj} injections, the workload's mix), FP64 value+gradient")
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

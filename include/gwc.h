@@ -135,8 +135,8 @@ typedef struct {
                             in [16, 4096] (default 512) */
   int32_t max_K;         /* largest Lambda batch a call may pass (default 256) */
   int32_t chunk;         /* samples per work item, 64..4096 (default 2048) */
-  int32_t lambda_tile;   /* Lambda points per CTA tile, 0..256 (0 = default 64); a tile holds
-                            at most 512 / lambda_group points */
+  int32_t lambda_tile;   /* Lambda points per CTA tile, 0..256 (0 = default 256); a tile
+                            holds at most 512 / lambda_group points */
   int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 1) */
   int32_t cap_per_pixel; /* > 0: keep at most this many samples of each (event, pixel), chosen
                             at random as the paper's memory option does (it quotes 2500);
@@ -185,13 +185,15 @@ gwc_status gwc_loglik_grad(gwc_ctx* ctx, int32_t K, const double* d_lambda, doub
  * order statistics), biweight 1.06 s_bi n^-1/5 (s_bi^2 the printed biweight
  * midvariance about the median, u = (z - Q)/(9 MAD)); a pixel with fewer than two
  * samples in [0, z_max] or a zero bandwidth is dropped.  Kernels are summed over the
- * grid points within 6 h of each sample (the kernel's mass beyond is 2e-9).  The
+ * grid points within 6 h of each sample, rounded out to aligned blocks of 4 points (the
+ * kernel's mass beyond 6 h is 2e-9).  The
  * selection term is the Monte-Carlo sum of gwc_loglik.  Outputs as gwc_loglik, except
  * that d_neff_event[K][n_events] receives the effective number of kept pixels,
  * (sum_j L_ij)^2 / sum_j L_ij^2, and flag bit 1 is never set (no per-event cut); an
  * event with no kept pixel makes the total -inf.  kopt may be NULL (defaults).  The
  * first call (and a call with another n_grid) allocates the form's device buffers:
- * about max_K x (groups + work items) x 72 bytes plus n_pix x n_grid floats.  Needs the
+ * about max_K x (groups + work items) x 92 bytes plus n_pix x n_grid floats (rows rounded
+ * up to a multiple of 4).  Needs the
  * LOS table stored as FP32 (GWC_E_UNSUPPORTED otherwise). */
 enum { GWC_BW_SCOTT = 0, GWC_BW_SILVERMAN = 1, GWC_BW_BIWEIGHT = 2 };
 typedef struct {

@@ -152,6 +152,9 @@ constexpr int PROF_SLOTS = 256;
 // one warp per Lambda point: warps then claim points from a shared counter, so uneven
 // per-point work (cuts, early rejections) leaves no warp idle at the unit's barrier
 constexpr int DEFAULT_LAMBDA_GROUP = 1;
+// the whole batch in one tile (up to 256 points): each staged chunk serves every point,
+// and a warp's share of points is large enough that the warps finish a unit together
+constexpr int DEFAULT_LAMBDA_TILE = MAX_SLAB;
 
 // fold the recorded quadruples into the sums (waits for them)
 cudaError_t prof_drain(gwc_ctx* c) {
@@ -251,7 +254,7 @@ bool make_items(const int64_t* offsets, int32_t ne, int64_t ns, int64_t ni, int 
 
 // launch geometry of the fused kernel for a batch of K points
 void fused_geometry(const gwc_ctx* c, int K, int& slab, int& n_slabs) {
-  slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : 64;
+  slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : DEFAULT_LAMBDA_TILE;
   const int group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
   slab = std::max(1, std::min(std::min(slab, K), std::min(MAX_SLAB, MAX_SLAB_GROUP / group)));
   n_slabs = (K + slab - 1) / slab;
@@ -499,7 +502,7 @@ gwc_status kde_prepare(gwc_ctx* c, int G, cudaStream_t s) {
   }
   if (c->kde_G != G) {
     if (c->kde_pgrid) { cudaFree(c->kde_pgrid); c->kde_pgrid = nullptr; c->kde_G = 0; }
-    e = dalloc(c, &c->kde_pgrid, (size_t)c->n_pix * G);
+    e = dalloc(c, &c->kde_pgrid, (size_t)c->n_pix * kde_row(G));
     if (e != cudaSuccess) return oom(e, "KDE grid table");
     e = launch_los_grid(static_cast<const float*>(c->los), c->n_pix, c->n_z, c->z_max, G, c->kde_pgrid, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "KDE grid table");

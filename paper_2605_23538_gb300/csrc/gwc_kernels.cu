@@ -1181,10 +1181,19 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   unsigned n_w = 0, n_terms = 0;   // census counts of this lane (measurement only)
 
   // ---- pass 2: sum_k w'_k sum_g c_g p_LOS(z_g) K_h(z_g - z_k), scaled by 2^-m; each
-  //      kernel over the grid points within 6 h (its mass beyond is 2e-9)
-  const float* pg = A.pgrid + (size_t)grp.pix * A.G;
+  //      kernel over the grid points within 6 h (its mass beyond is 2e-9), taken in
+  //      aligned blocks of 4.  On a uniform grid the Gaussian's values follow a product
+  //      recurrence: with e_j = 2^(c d_j^2), d_j = z_j - z, c = -log2(e) / (2 h^2),
+  //      e_(j+1) = e_j r_j, r_j = 2^(c (2 d_j dz + dz^2)), r_(j+1) = r_j q, q = 2^(2 c dz^2);
+  //      each block starts from its own e_0 and r_0 (two ex2), so the rounding drift stays
+  //      within ~10 ulp.  For h >= dz a block's e_0 >= 2^-72 and r <= 2^14 (no underflow or
+  //      overflow inside a block); narrower kernels take every value from ex2.
+  const int GS = kde_row(A.G);
+  const float* pg = A.pgrid + (size_t)grp.pix * GS;
   const float dzg = A.dzg, inv_dzg = 1.f / dzg, reach = 6.f * h;
   const float cexp = -0.5f * LOG2EF / (h * h);
+  const bool recur = dzg <= h;
+  const float lq = 2.f * cexp * dzg * dzg;        // log2 q
   float acc = 0.f;
   for (int i = lane; i < n; i += 32) {
     float z, lw;
@@ -1192,18 +1201,41 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
     if (!(lw > -INFINITY)) continue;
     const int g0 = max(0, (int)ceilf((z - reach) * inv_dzg));
     const int g1 = min(A.G - 1, (int)floorf((z + reach) * inv_dzg));
+    float T = 0.f;
+    int lo = g0, hi = g1;                         // the grid points summed
+    if (recur && g0 <= g1) {
+      lo = g0 & ~(KDE_BLOCK - 1);
+      hi = min(g1 | (KDE_BLOCK - 1), GS - 1);     // padding beyond the grid holds zeros
+      const float ql = ex2(lq);
+      for (int b = lo; b <= hi; b += KDE_BLOCK) {
+        const float d0 = fmaf((float)b, dzg, -z);
+        float e = ex2((cexp * d0) * d0);
+        float r = ex2(cexp * fmaf(2.f * d0, dzg, dzg * dzg));
+        static_assert(KDE_BLOCK == 4, "one float4 of grid values a block");
+        const float4 pa = __ldg(reinterpret_cast<const float4*>(pg + b));
+        const float pv[KDE_BLOCK] = {pa.x, pa.y, pa.z, pa.w};
+#pragma unroll
+        for (int j = 0; j < KDE_BLOCK; ++j) {
+          T = fmaf(pv[j], e, T);
+          e *= r;
+          r *= ql;
+        }
+      }
+      hi = min(hi, A.G - 1);
+    } else {
+      float gf = (float)g0;
+      for (int gg = g0; gg <= g1; ++gg, gf += 1.f) {
+        const float d = fmaf(gf, dzg, -z);
+        T = fmaf(__ldg(pg + gg), ex2((cexp * d) * d), T);
+      }
+    }
     if (A.census) {
       ++n_w;
-      n_terms += (unsigned)max(g1 - g0 + 1, 0);
+      n_terms += (unsigned)max(hi - lo + 1, 0);
     }
-    float T = 0.f, gf = (float)g0;
-    for (int gg = g0; gg <= g1; ++gg, gf += 1.f) {
-      const float d = fmaf(gf, dzg, -z);
-      T = fmaf(__ldg(pg + gg), ex2((cexp * d) * d), T);
-    }
-    // trapezoid: the two end points of the grid weigh half
-    if (g0 == 0 && g1 >= 0) T = fmaf(-0.5f * __ldg(pg), ex2((cexp * z) * z), T);
-    if (g1 == A.G - 1 && g0 <= g1) {
+    // trapezoid: the two end points of the grid weigh half (when summed)
+    if (lo == 0 && hi >= 0) T = fmaf(-0.5f * __ldg(pg), ex2((cexp * z) * z), T);
+    if (hi == A.G - 1 && lo <= hi) {
       const float d = fmaf((float)(A.G - 1), dzg, -z);
       T = fmaf(-0.5f * __ldg(pg + A.G - 1), ex2((cexp * d) * d), T);
     }
@@ -1231,9 +1263,14 @@ __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
 
 __global__ void k_los_grid(const float* __restrict__ los, int n_pix, int nz, double zmax, int G,
                            float* __restrict__ out) {
+  const int GS = kde_row(G);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)n_pix * G) return;
-  const int p = (int)(t / G), gq = (int)(t - (long long)p * G);
+  if (t >= (long long)n_pix * GS) return;
+  const int p = (int)(t / GS), gq = (int)(t - (long long)p * GS);
+  if (gq >= G) {   // padding of the row to whole blocks
+    out[t] = 0.f;
+    return;
+  }
   const double zg = gq * (zmax / (G - 1));
   const double sc = (double)(nz - 1) / zmax;
   int j = (int)floor(zg * sc);
@@ -1267,7 +1304,7 @@ cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s) {
 
 cudaError_t launch_los_grid(const float* los, int n_pix, int nz, double zmax, int G, float* out,
                             cudaStream_t s) {
-  const long long n = (long long)n_pix * G;
+  const long long n = (long long)n_pix * kde_row(G);
   k_los_grid<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(los, n_pix, nz, zmax, G, out);
   return cudaGetLastError();
 }

@@ -67,7 +67,8 @@ struct KdeArgs {
   const float2* lm;       // log2 m1_det, log2 m2_det of every sample
   const KdeGroup* groups;
   int n_groups;
-  const float* pgrid;     // [n_pix][G]: the LOS prior at the KDE grid points
+  const float* pgrid;     // [n_pix][kde_row(G)]: the LOS prior at the KDE grid points, rows
+                          // padded with zeros to whole blocks of KDE_BLOCK floats
   int G;
   float dzg;              // grid step z_max / (G - 1)
   int rule;               // 0 Scott, 1 Silverman, 2 biweight
@@ -85,6 +86,9 @@ struct KdeArgs {
   unsigned long long* census = nullptr;
 };
 constexpr int KDE_CENSUS_SLOTS = 4;
+// a KDE grid row's stride: the grid points rounded up to whole blocks of 4 (16 bytes)
+constexpr int KDE_BLOCK = 4;
+__host__ __device__ constexpr int kde_row(int G) { return (G + KDE_BLOCK - 1) / KDE_BLOCK * KDE_BLOCK; }
 cudaError_t launch_kde(const KdeArgs& a, cudaStream_t s);
 cudaError_t launch_log2_masses(const float4* smp, long long n, float2* out, cudaStream_t s);
 cudaError_t launch_los_grid(const float* los, int n_pix, int nz, double zmax, int G, float* out,
