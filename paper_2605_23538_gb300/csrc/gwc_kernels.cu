@@ -501,15 +501,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   block_sum<13>(wv, red);
   if (tid < 13) s_wv[tid] = wv[tid];
   pro_sync();
-  if (rank == Sh::WIN0) {
-  // ---- rank WIN0 gathers the shares in rank order (the window sums, and each panel's
-  //      integrals from the CTA that owns it), then an inclusive scan over the panels:
-  //      thread p holds the cumulative integrals at node p + 1
-  for (int i = 0; i < 13; ++i) wv[i] = 0.0;
-  for (int r = 0; r < Sh::NWIN; ++r) {
-    const double* o = peer(s_wv, Sh::WIN0 + r);
-    for (int i = 0; i < 13; ++i) wv[i] += o[i];
-  }
+  // ---- every window rank gathers each panel's integrals from the CTA that owns it (one
+  //      panel a thread) and scans them inclusively: thread p holds the cumulative
+  //      integrals at node p + 1.  The window tables' nodes are then split over the
+  //      window ranks; rank WIN0 also gathers the window sums and writes the constants.
   double cum[4] = {0.0, 0.0, 0.0, 0.0};
   if (tid < NW_WIN) {
     int r = 0;
@@ -519,15 +514,6 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     for (int i = 0; i < 4; ++i) cum[i] = o[i * NW_WIN + loc];
   }
   block_scan<4>(cum, red);
-  const double xmax = *peer(&sD[ZPANELS], 0);   // D(z_max): rank 0's with CL, else this CTA's
-  const double dx = xmax / (nx - 1);
-  const double W = wv[0];
-  const double Zm1 = 1.0 - W;
-  // d ln Z_m1 / d theta = -dW/d theta / Z_m1
-  const double dWa = wv[1], dWl = wv[2], dWmu = wv[3], dWsig = wv[4];
-  const double dWmax = -(1.0 - lam) * dZPmax * wv[5] - lam * dZGmax * wv[6] - lam * dZG2max * wv[12];
-  const double dWmin = wv[7], dWdm = wv[8];
-  const double dWmu2 = wv[9], dWsig2 = wv[10], dWl1 = wv[11];
 
   // window tables at nodes m_k = mmin + k hw: with R_X = X / (m^beta S(m)),
   //   Q_C = R_C dm / m'^2, Q_beta = R_beta / R_C, Q_J = R_J / R_C, Q_K = R_K dm / m'
@@ -542,19 +528,30 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   if (tid == 0)
     for (int i = 0; i < 4; ++i) scum[i][0] = 0.0;
   __syncthreads();
-  double qv[4] = {1.0, log(mmin), 1.0 / mmin, -1.0}, qd[4] = {0.0, 0.0, 0.0, 0.0};
-  if (tid <= NW_WIN && tid > 0 && dm > 0.0) {
-    const double mp = tid * hw, m = mmin + mp, lm = log(m);
+  // this rank's nodes [nd0, nd1) of the NW_WIN + 1.  With several window ranks, rank WIN0
+  // takes none (it writes the constants meanwhile) and the others split them; the rank
+  // with node 0 also evaluates node 1, whose value the secant slope at node 0 needs
+  const int tw = Sh::NWIN > 1 ? Sh::NWIN - 1 : 1, tr = Sh::NWIN > 1 ? wr - 1 : 0;
+  const int nd0 = tr >= 0 ? tr * (NW_WIN + 1) / tw : 0, nd1 = tr >= 0 ? (tr + 1) * (NW_WIN + 1) / tw : 0;
+  const int node = nd0 + tid;
+  const bool mine = node < nd1, eval = mine || (node == 1 && nd0 == 0 && nd1 > 0);
+  double qv[4] = {1.0, 0.0, 0.0, -1.0}, qd[4] = {0.0, 0.0, 0.0, 0.0};
+  if (eval) {   // the m' -> 0 limits (every node's values without a window)
+    qv[1] = log(mmin);
+    qv[2] = 1.0 / mmin;
+  }
+  if (eval && node > 0 && dm > 0.0) {
+    const double mp = node * hw, m = mmin + mp, lm = log(m);
     double S = 1.0, oneS = 0.0, dSddm = 0.0, dlnS = 0.0, dSS = 0.0;
-    if (tid < NW_WIN) {
+    if (node < NW_WIN) {
       smooth_d(mp, dm, S, oneS, dSddm);
       dlnS = oneS * dm * (1.0 / (mp * mp) + 1.0 / ((mp - dm) * (mp - dm)));
       dSS = -oneS * (1.0 / mp + mp / ((mp - dm) * (mp - dm)));   // (dS/d delta_m) / S
     }
     const double gg = exp(beta * lm) * S;
     const double gl = beta / m + dlnS;     // g'/g
-    const double Rc = scum[0][tid] / gg, Rb = scum[1][tid] / gg;
-    const double Rj = scum[2][tid] / gg, Rk = scum[3][tid] / gg;
+    const double Rc = scum[0][node] / gg, Rb = scum[1][node] / gg;
+    const double Rj = scum[2][node] / gg, Rk = scum[3][node] / gg;
     const double dRc = 1.0 - Rc * gl, dRb = lm - Rb * gl, dRj = 1.0 / m - Rj * gl, dRk = dSS - Rk * gl;
     qv[0] = Rc * dm / (mp * mp);
     qv[1] = Rb / Rc;
@@ -565,35 +562,84 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     qd[2] = (dRj - qv[2] * dRc) / Rc;
     qd[3] = dm * (dRk / mp - Rk / (mp * mp));
   }
-  if (tid <= NW_WIN)
-    for (int i = 0; i < 4; ++i) sq[i][tid] = qv[i];
+  if (eval)
+    for (int i = 0; i < 4; ++i) sq[i][node] = qv[i];
   __syncthreads();
-  if (tid == 0 && dm > 0.0)
+  if (mine && node == 0 && dm > 0.0)
     for (int i = 0; i < 4; ++i) qd[i] = (sq[i][1] - sq[i][0]) / hw;
-  if (tid <= NW_WIN) {
-    wval[tid] = make_float4((float)qv[0], (float)qv[1], (float)qv[2], (float)qv[3]);
-    wslp[tid] = make_float4((float)(qd[0] * hw), (float)(qd[1] * hw), (float)(qd[2] * hw), (float)(qd[3] * hw));
+  if (mine) {
+    wval[node] = make_float4((float)qv[0], (float)qv[1], (float)qv[2], (float)qv[3]);
+    wslp[node] = make_float4((float)(qd[0] * hw), (float)(qd[1] * hw), (float)(qd[2] * hw), (float)(qd[3] * hw));
   }
 
-  // ---- (6) constants
+  if (rank == Sh::WIN0) {
+  // ---- rank WIN0: the window sums gathered in rank order, one component a lane
+  __shared__ double s_wsum[13];
+  __shared__ double s_tv[32];
+  if (tid < 13) {
+    double v = 0.0;
+    for (int r = 0; r < Sh::NWIN; ++r) v += peer(s_wv, Sh::WIN0 + r)[tid];
+    s_wsum[tid] = v;
+  }
+  const double xmax = *peer(&sD[ZPANELS], 0);   // D(z_max): rank 0's with CL, else this CTA's
+  const double dx = xmax / (nx - 1);
+  __syncthreads();
+  for (int i = 0; i < 13; ++i) wv[i] = s_wsum[i];
+  // Z_m1 = 1 - W with W = wv[0]; d ln Z_m1 / d theta = -dW/d theta / Z_m1
+  const double dWa = wv[1], dWl = wv[2], dWmu = wv[3], dWsig = wv[4];
+  const double dWmax = -(1.0 - lam) * dZPmax * wv[5] - lam * dZGmax * wv[6] - lam * dZG2max * wv[12];
+  const double dWmin = wv[7], dWdm = wv[8];
+  const double dWmu2 = wv[9], dWsig2 = wv[10], dWl1 = wv[11];
+
+  // ---- (6) constants.  Their logarithms, exponentials and divisions are long FP64
+  //      latency chains; the lanes of warp 0 evaluate them side by side (the same
+  //      expressions, one per lane, all lanes running the same instructions on arguments
+  //      chosen by the lane) before thread 0 assembles the fields into s_tv[]:
+  //        [0..5]   log of lam lam1, lam, mw, lam1, 1 - W, H0/c       [6, 7] log1p(-lam), log1p(-lam1)
+  //        [8]      exp(eps log mw)
+  //        [9..23]  1/sig, 1/sig2, 1/eps, N_w/dm, 1/dm, 1/H0, 1/(1+zp), 1/lam, 1/(1-lam),
+  //                 1/(1-W), 1/lam1, 1/(1-lam1), gpk/(1+zp), (H0/c)/dx, zmax/(nz-1)
+  const double mw = mmin + dm, eps = 1.0 + beta;
+  if (tid < 32) {
+    const int l = tid;
+    const double W0 = wv[0];
+    const double la = l == 0 ? lam * lam1 : l == 1 ? lam : l == 2 ? mw : l == 3 ? lam1 : l == 4 ? 1.0 - W0
+                    : l == 5 ? H0 / C_KMS : 1.0;
+    const double lb = l == 0 ? -lam : l == 1 ? -lam1 : 0.0;
+    const double vlog = log(la), vlog1p = log1p(lb);
+    const double vexp = exp(l == 2 ? eps * vlog : 0.0);
+    // numerators and denominators of the divisions (lane 22's numerator is itself H0/c)
+    const double num0 = l == 22 ? H0 : 1.0, den0 = l == 22 ? C_KMS : 1.0;
+    const double q0 = num0 / den0;
+    const double num = l == 12 ? (double)NW_WIN : l == 21 ? gpk : l == 22 ? q0 : l == 23 ? zmax : 1.0;
+    const double den = l == 9 ? sig : l == 10 ? sig2 : l == 11 ? eps : l == 12 ? dm : l == 13 ? dm
+                     : l == 14 ? H0 : l == 15 ? 1.0 + zp : l == 16 ? lam : l == 17 ? 1.0 - lam
+                     : l == 18 ? 1.0 - W0 : l == 19 ? lam1 : l == 20 ? 1.0 - lam1 : l == 21 ? 1.0 + zp
+                     : l == 22 ? dx : l == 23 ? (double)(nz - 1) : 1.0;
+    const double vdiv = num / den;
+    if (l < 6) s_tv[l] = vlog;
+    if (l < 2) s_tv[6 + l] = vlog1p;
+    if (l == 2) s_tv[8] = vexp;
+    if (l >= 9 && l < 24) s_tv[l] = vdiv;
+  }
+  __syncwarp();
   if (tid == 0) {
     const double Cw = dm > 0.0 ? scum[0][NW_WIN] : 0.0;
     const double Cwb = dm > 0.0 ? scum[1][NW_WIN] : 0.0;
     const double Jw = dm > 0.0 ? scum[2][NW_WIN] : 0.0;
     const double Kw = dm > 0.0 ? scum[3][NW_WIN] : 0.0;
-    const double mw = mmin + dm, eps = 1.0 + beta;
     const double LOG2E = 1.44269504088896340736;
     LamF f;
     memset(&f, 0, sizeof(f));
     f.H0c = (float)(H0 / C_KMS);
     f.H0c_lo = (float)(H0 / C_KMS - (double)f.H0c);
-    const double sxa = H0 / C_KMS / dx;
+    const double sxa = s_tv[22];
     f.sxa = (float)sxa;
     f.sxa_lo = (float)(sxa - (double)f.sxa);
     f.xmax = (float)xmax;
     f.live = 1.f;
-    f.zstep = (float)(zmax / (nz - 1));
-    f.zstep_lo = (float)(zmax / (nz - 1) - (double)f.zstep);
+    f.zstep = (float)s_tv[23];
+    f.zstep_lo = (float)(s_tv[23] - (double)f.zstep);
     f.inv_zstep = (float)pscale;
     f.om = (float)om;
     f.lp2 = (float)(lp * LOG2E);
@@ -613,33 +659,33 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.dm_l2 = (float)(dm * LOG2E);
     f.mw = (float)mw;
     f.mu = (float)mu;
-    f.inv_sig = (float)(1.0 / sig);
+    f.inv_sig = (float)s_tv[9];
     // the two components' log2 normalisations, less an anchor R (log2 units) that c
     // carries in FP64: only their difference is rounded to FP32, so the rounding no
     // longer shifts every sample's weight by the same amount
     // (multi-peak: the low peak carries lam lam1, the high one lam (1 - lam1))
-    const double la2d = lam < 1.0 ? (log1p(-lam) - lnZP) * LOG2E : -INFINITY;
-    const double lb2d = lam > 0.0 && lam1 > 0.0 ? (log(lam * lam1) - lnsig2pi - lnZG) * LOG2E : -INFINITY;
-    const double lc2d = mp && lam > 0.0 && lam1 < 1.0 ? (log(lam) + log1p(-lam1) - lnsig2pi2 - lnZG2) * LOG2E
+    const double la2d = lam < 1.0 ? (s_tv[6] - lnZP) * LOG2E : -INFINITY;
+    const double lb2d = lam > 0.0 && lam1 > 0.0 ? (s_tv[0] - lnsig2pi - lnZG) * LOG2E : -INFINITY;
+    const double lc2d = mp && lam > 0.0 && lam1 < 1.0 ? (s_tv[1] + s_tv[7] - lnsig2pi2 - lnZG2) * LOG2E
                                                      : -INFINITY;
     const double R = lam < 1.0 ? la2d : (lb2d > -INFINITY ? lb2d : lc2d);
     f.la2 = lam < 1.0 ? (float)(la2d - R) : -INFINITY;
     f.lb2 = lb2d > -INFINITY ? (float)(lb2d - R) : -INFINITY;
     f.lc2 = lc2d > -INFINITY ? (float)(lc2d - R) : -INFINITY;
     f.mu2 = (float)mu2;
-    f.inv_sig2 = (float)(1.0 / sig2);
+    f.inv_sig2 = (float)s_tv[10];
     const bool small = fabs(eps) < 1e-3;
-    const double mw1b = exp(eps * log(mw));
+    const double mw1b = s_tv[8];
     f.beta_small = small ? 1.f : 0.f;
-    f.inv_eps_b = small ? 0.f : (float)(1.0 / eps);
+    f.inv_eps_b = small ? 0.f : (float)s_tv[11];
     f.C0 = small ? 0.f : (float)(Cw - mw1b / eps);
     f.Cw = (float)Cw;
     f.mw1b = (float)mw1b;
-    f.lmw = (float)log(mw);
-    f.inv_wh = dm > 0.0 ? (float)(NW_WIN / dm) : 0.f;
-    f.inv_dm = dm > 0.0 ? (float)(1.0 / dm) : 0.f;
-    f.invH0 = (float)(1.0 / H0);
-    f.inv1zp = (float)(1.0 / (1.0 + zp));
+    f.lmw = (float)s_tv[2];
+    f.inv_wh = dm > 0.0 ? (float)s_tv[12] : 0.f;
+    f.inv_dm = dm > 0.0 ? (float)s_tv[13] : 0.f;
+    f.invH0 = (float)s_tv[14];
+    f.inv1zp = (float)s_tv[15];
     f.lam_edge = (lam > 0.0 && lam < 1.0) ? 0.f : 1.f;
     f.lam = (float)lam;
     f.lam_sig = lam >= 1.0 ? 1.f : (lam <= 0.0 ? -1.f : 0.f);
@@ -649,9 +695,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.lam1_edge = e1 ? 1.f : 0.f;
     f.o2_hi = lam1 >= 1.0 ? 1.f : 0.f;
     f.o2_l2 = !e1 ? 0.f
-                  : (float)((log(lam) - (lam1 >= 1.0 ? lnsig2pi2 + lnZG2 : lnsig2pi + lnZG)) * LOG2E - R);
-    f.lb1_2 = mp && lam1 > 0.0 ? (float)((log(lam1) - lnsig2pi - lnZG) * LOG2E - R) : -INFINITY;
-    f.lc1_2 = mp && lam1 < 1.0 ? (float)((log1p(-lam1) - lnsig2pi2 - lnZG2) * LOG2E - R) : -INFINITY;
+                  : (float)((s_tv[1] - (lam1 >= 1.0 ? lnsig2pi2 + lnZG2 : lnsig2pi + lnZG)) * LOG2E - R);
+    f.lb1_2 = mp && lam1 > 0.0 ? (float)((s_tv[3] - lnsig2pi - lnZG) * LOG2E - R) : -INFINITY;
+    f.lc1_2 = mp && lam1 < 1.0 ? (float)((s_tv[7] - lnsig2pi2 - lnZG2) * LOG2E - R) : -INFINITY;
     f.dZPa = (float)dZPa;
     f.dZPmin = (float)dZPmin;
     f.dZPmax = (float)dZPmax;
@@ -664,16 +710,16 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.Kw = (float)Kw;
     f.la0_2 = (float)(-lnZP * LOG2E - R);
     f.lb0_2 = (float)((-lnsig2pi - lnZG) * LOG2E - R);
-    f.inv_lam = lam > 0.0 ? (float)(1.0 / lam) : 0.f;
-    f.inv_1ml = lam < 1.0 ? (float)(1.0 / (1.0 - lam)) : 0.f;
+    f.inv_lam = lam > 0.0 ? (float)s_tv[16] : 0.f;
+    f.inv_1ml = lam < 1.0 ? (float)s_tv[17] : 0.f;
     *lf = f;
     // c = -ln Z_m1 + ln(H0 / c) + R ln 2 (the anchor taken out of la2, lb2); -ln N'_z
     // and its derivatives are in cz, dcz
-    ld->c = -log(Zm1) + log(H0 / C_KMS) + R * 0.69314718055994530942;
+    ld->c = -s_tv[4] + s_tv[5] + R * 0.69314718055994530942;
     double dc[NP_MAX];
     for (int i = 0; i < NP_MAX; ++i) dc[i] = 0.0;
-    const double iZ = 1.0 / Zm1;   // -d ln Z_m1 = dW / Z_m1
-    dc[P_H0] = 1.0 / H0;
+    const double iZ = s_tv[18];   // -d ln Z_m1 = dW / Z_m1
+    dc[P_H0] = s_tv[14];
     dc[P_ALPHA] = dWa * iZ;
     dc[P_MMIN] = dWmin * iZ;
     dc[P_MMAX] = dWmax * iZ;
@@ -695,10 +741,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     ld->dZG2max = dZG2max;
     ld->dZG2mu = dZG2mu;
     ld->dZG2sig = dZG2sig;
-    ld->inv_sig2 = 1.0 / sig2;
-    ld->inv_lam1 = lam1 > 0.0 ? 1.0 / lam1 : 0.0;
-    ld->inv_1ml1 = lam1 < 1.0 ? 1.0 / (1.0 - lam1) : 0.0;
-    ld->invH0 = 1.0 / H0;
+    ld->inv_sig2 = s_tv[10];
+    ld->inv_lam1 = lam1 > 0.0 ? s_tv[19] : 0.0;
+    ld->inv_1ml1 = lam1 < 1.0 ? s_tv[20] : 0.0;
+    ld->invH0 = s_tv[14];
     ld->dZPa = dZPa;
     ld->dZPmin = dZPmin;
     ld->dZPmax = dZPmax;
@@ -706,10 +752,10 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     ld->dZGmax = dZGmax;
     ld->dZGmu = dZGmu;
     ld->dZGsig = dZGsig;
-    ld->inv_sig = 1.0 / sig;
-    ld->inv_lam = lam > 0.0 ? 1.0 / lam : 0.0;
-    ld->inv_1ml = lam < 1.0 ? 1.0 / (1.0 - lam) : 0.0;
-    ld->gpk_inv1zp = gpk / (1.0 + zp);
+    ld->inv_sig = s_tv[9];
+    ld->inv_lam = lam > 0.0 ? s_tv[16] : 0.0;
+    ld->inv_1ml = lam < 1.0 ? s_tv[17] : 0.0;
+    ld->gpk_inv1zp = s_tv[21];
   }
   }   // rank WIN0
   if constexpr (CL) pro_sync();   // the window CTAs' shared memory stays until rank WIN0 has read it
@@ -1427,7 +1473,7 @@ __device__ __forceinline__ double pow2i(double k) {
 }
 constexpr double LN2D = 0.69314718055994530942;
 
-template <bool GRAD>
+template <bool GRAD, bool MP>
 __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   __shared__ double rs[8][2 + NP_MAX];
   __shared__ double rsel[8][3 + NP_MAX];
@@ -1437,7 +1483,8 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   const int nt = blockDim.x, nw = nt >> 5;   // sized to the work by launch_merge
   const LamD D = A.ld[k];
   const int ne = A.n_events;
-  const int NPK = n_params(A.mp != 0);   // gradient width of the mass model
+  constexpr int NPK = n_params(MP);   // gradient width of the mass model (a constant, so the
+                                      // per-component arrays stay in registers)
   if (D.flag & 1) {
     for (int e = tid; e < ne; e += nt) {
       A.lnL_event[(size_t)k * ne + e] = -INFINITY;
@@ -2001,8 +2048,13 @@ cudaError_t launch_plain_reduce(const PlainArgs& a, bool grad, cudaStream_t s) {
 cudaError_t launch_merge(const MergeArgs& a, int K, bool grad, cudaStream_t s) {
   const long long work = std::max<long long>(a.n_events, (long long)(a.n_items - a.inj_item0) * a.P);
   const int threads = (int)std::min<long long>(256, std::max<long long>(32, (work + 31) / 32 * 32));
-  if (grad) k_merge<true><<<K, threads, 0, s>>>(a);
-  else k_merge<false><<<K, threads, 0, s>>>(a);
+  if (a.mp) {
+    if (grad) k_merge<true, true><<<K, threads, 0, s>>>(a);
+    else k_merge<false, true><<<K, threads, 0, s>>>(a);
+  } else {
+    if (grad) k_merge<true, false><<<K, threads, 0, s>>>(a);
+    else k_merge<false, false><<<K, threads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
