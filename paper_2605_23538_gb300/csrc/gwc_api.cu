@@ -808,7 +808,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(cudaMemcpy(c->sched, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(c->ev_item0, ev_item0.data(), sizeof(int32_t) * ev_item0.size(), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(c->ev_n, ev_n.data(), sizeof(double) * ev_n.size(), cudaMemcpyHostToDevice));
-  chk(ensure_gauss_legendre());
+  chk(ensure_prologue_ready());
   if (e != cudaSuccess) {
     std::string msg = std::string("device upload failed: ") + cudaGetErrorString(e);
     free_all(c);

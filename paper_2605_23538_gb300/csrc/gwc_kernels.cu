@@ -54,7 +54,10 @@ static void gauss_legendre(int n, double* x, double* w) {
 
 // One upload per device for the life of the process (the values never change), shared by
 // gwc_create and the context-free entry point.
-cudaError_t ensure_gauss_legendre() {
+struct ProArgs;
+template <bool CL> __global__ void k_prologue(ProArgs A);
+
+cudaError_t ensure_prologue_ready() {
   constexpr int MAX_DEV = 64;
   static std::mutex mu;
   static bool done[MAX_DEV] = {false};
@@ -68,6 +71,8 @@ cudaError_t ensure_gauss_legendre() {
   gauss_legendre(NGL, x, w);
   e = cudaMemcpyToSymbol(c_glx, x, sizeof(double) * NGL);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, w, sizeof(double) * NGL);
+  // the small-batch shape is a cluster of 16 CTAs, beyond the portable size of 8
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prologue<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
@@ -207,23 +212,26 @@ __device__ void z_panels(double om, double zmax, double* sI, double* sJ, double*
 }
 
 // The prologue's CTAs per Lambda point and their roles, in two shapes.  CL (small
-// batches, whose few CTAs would leave most SMs idle): a thread-block cluster of eight
-// CTAs, so that the FP64 work, which this GPU runs at 1/64 of its FP32 rate, is spread
-// over eight SMs -- ranks 0 and 1 build the two halves of the d_L -> z inversion table
-// (each after step (1)), rank 2 the redshift normalisation N'_z, ranks 3..7 each
-// integrate a share of the smoothing window's panels; after a cluster barrier rank 3
-// gathers the window CTAs' sums and panel integrals from their shared memory in rank
-// order, scans them, and writes the window tables and the constants (xmax it reads from
-// rank 0's shared memory), and a second barrier keeps every CTA's shared memory alive
-// until rank 3 is done.  Every CTA passes both barriers, except that all of them return
-// at once for a Lambda outside the domain.  Not CL (large batches, where every SM has
-// work anyway): three CTAs, no redundant work -- rank 0 the whole inversion table, rank 1
-// N'_z, rank 2 step (1), the whole window, the tables and the constants.
+// batches, whose few CTAs would leave most SMs idle): a thread-block cluster of 16 CTAs
+// (the non-portable size), so that the FP64 work, which this GPU runs at 1/75 of its FP32
+// rate, is spread over 16 SMs -- ranks 0..3 build a quarter of the d_L -> z inversion
+// table each (each after step (1)), ranks 4 and 5 half of the redshift normalisation
+// N'_z each (rank 4 adds them after the first barrier and writes it), ranks 6..15 each
+// integrate a share of the smoothing window's panels.  After a cluster barrier every
+// window rank gathers the panel integrals from their owners' shared memory and scans
+// them; ranks 7..15 split the window tables' nodes while rank 6 gathers the window sums
+// and writes the constants (xmax it reads from rank 0's shared memory), and a second
+// barrier keeps every CTA's shared memory alive until all have read it.  Every CTA
+// passes both barriers, except that all of them return at once for a Lambda outside the
+// domain.  Not CL (large batches, where every SM has work anyway): three CTAs, no
+// redundant work -- rank 0 the whole inversion table, rank 1 N'_z, rank 2 step (1), the
+// whole window, the tables and the constants.
 template <bool CL> struct ProShape {
-  static constexpr int CTAS = CL ? 8 : 3;
-  static constexpr int INV = CL ? 2 : 1;   // ranks [0, INV) build the inversion table
-  static constexpr int NZR = INV;          // the N'_z rank
-  static constexpr int WIN0 = NZR + 1;     // ranks [WIN0, CTAS) integrate the window; WIN0 gathers
+  static constexpr int CTAS = CL ? 16 : 3;  // a cluster of 16 (the non-portable size) per point
+  static constexpr int INV = CL ? 4 : 1;    // ranks [0, INV) build the inversion table
+  static constexpr int NZR = INV;           // ranks [NZR, NZR + NNZ) sum N'_z; NZR writes it
+  static constexpr int NNZ = CL ? 2 : 1;
+  static constexpr int WIN0 = NZR + NNZ;    // ranks [WIN0, CTAS) integrate the window; WIN0 gathers
   static constexpr int NWIN = CTAS - WIN0;
 };
 constexpr int PRO_CLUSTER_MAX_K = 32;      // batches up to this size use the cluster shape
@@ -300,12 +308,15 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   // multi-peak: the high peak and the low peak's share (lam1 = 1 leaves one Gaussian)
   const double mu2 = mp ? L[P_MU2] : 0.0, sig2 = mp ? L[P_SIG2] : 1.0, lam1 = mp ? L[P_LAM1] : 1.0;
 
-  if (rank == Sh::NZR) {
+  if (rank >= Sh::NZR && rank < Sh::NZR + Sh::NNZ) {
     // ---- (5) redshift normalisation N'_z = sum_j c_j dz pbar_j psi'(z_j) / (1 + z_j),
-    //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa))
+    //          psi' = (1+z)^gamma / (1 + ((1+z)/(1+zp))^(gamma+kappa)); the N'_z ranks
+    //          split the grid, rank NZR adds their sums in rank order and writes N'_z
     const double dzg = zmax / (nz - 1);
+    const int zr = rank - Sh::NZR;
+    const int j0 = zr * nz / Sh::NNZ, j1 = (zr + 1) * nz / Sh::NNZ;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < nz; j += PRO_THREADS) {
+    for (int j = j0 + tid; j < j1; j += PRO_THREADS) {
       const double zj = j * dzg, l = log1p(zj);
       const double r = gpk * (l - lp);
       const double term = ((j == 0 || j == nz - 1) ? 0.5 : 1.0) * dzg * A.pbar64[j] *
@@ -317,13 +328,25 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       v[3] += term * (s * gpk / (1.0 + zp));
     }
     block_sum<4>(v, red);
-    if (tid == 0) {
-      ld->cz = -log(v[0]);
-      ld->dcz[0] = -v[1] / v[0];
-      ld->dcz[1] = -v[2] / v[0];
-      ld->dcz[2] = -v[3] / v[0];
+    if (tid < 4) s_wv[tid] = v[tid];
+    auto write_nz = [&](const double* t) {
+      ld->cz = -log(t[0]);
+      ld->dcz[0] = -t[1] / t[0];
+      ld->dcz[1] = -t[2] / t[0];
+      ld->dcz[2] = -t[3] / t[0];
+    };
+    if constexpr (CL) {
+      pro_sync();
+      if (rank == Sh::NZR && tid == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int r = 0; r < Sh::NNZ; ++r)
+          for (int i = 0; i < 4; ++i) t[i] += peer(s_wv, Sh::NZR + r)[i];
+        write_nz(t);
+      }
+      pro_sync();
+    } else if (tid == 0) {
+      write_nz(v);
     }
-    if constexpr (CL) { pro_sync(); pro_sync(); }
     return;
   }
   const double pscale = (double)(nz - 1) / zmax;   // LOS grid units per unit z
@@ -416,8 +439,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   if constexpr (!CL) z_panels(om, zmax, sI, sJ, sD, sDp, red);
 
   // ---- (3) mass-model normalisations (Z_P on thread 0, Z_G on thread 32, Z_G2 on
-  //          thread 64, so the serial chains run in different warps), broadcast through
-  //          shared memory
+  //          thread 64, ln(sig sqrt(2 pi)) of the two peaks on threads 96 and 128, so the
+  //          serial chains run in different warps), broadcast through shared memory
   if (tid == 0) {
     // Z_P = int_{mmin}^{mmax} m^-alpha dm = e^{t a} (b - a) phi1(t (b - a)), t = 1 - alpha
     const double t = 1.0 - alpha, a = log(mmin), b = log(mmax), Lr = b - a, y = t * Lr;
@@ -432,14 +455,18 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     gauss_mass(mu, sig, mmin, mmax, sc + 4);         // Z_G = Phi(B) - Phi(A)
   } else if (tid == 64 && mp) {
     gauss_mass(mu2, sig2, mmin, mmax, sc + 9);
+  } else if (tid == 96) {
+    sc[14] = log(sig) + 0.91893853320467274178;
+  } else if (tid == 128) {
+    sc[15] = log(sig2) + 0.91893853320467274178;
   }
   __syncthreads();
   const double lnZP = sc[0], dZPa = sc[1], dZPmin = sc[2], dZPmax = sc[3];
   const double lnZG = sc[4], dZGmu = sc[5], dZGsig = sc[6], dZGmin = sc[7], dZGmax = sc[8];
   const double lnZG2 = mp ? sc[9] : 0.0, dZG2mu = mp ? sc[10] : 0.0, dZG2sig = mp ? sc[11] : 0.0;
   const double dZG2min = mp ? sc[12] : 0.0, dZG2max = mp ? sc[13] : 0.0;
-  const double lnsig2pi = log(sig) + 0.91893853320467274178;
-  const double lnsig2pi2 = log(sig2) + 0.91893853320467274178;
+  const double lnsig2pi = sc[14];
+  const double lnsig2pi2 = sc[15];
 
   // ---- (4) smoothing window [mmin, mmin + dm]: W = int h (1 - S), its derivatives,
   //          and the cumulative C-family integrals at the table nodes

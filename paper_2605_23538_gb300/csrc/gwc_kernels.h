@@ -170,8 +170,9 @@ struct HmcArgs {
 };
 cudaError_t launch_hmc(const HmcArgs& a, cudaStream_t s);
 
-// upload the prologue's Gauss-Legendre constants to the current device (once per device)
-cudaError_t ensure_gauss_legendre();
+// the prologue's per-device setup, once per device and outside any stream capture: its
+// Gauss-Legendre constants, and permission for its 16-CTA cluster shape
+cudaError_t ensure_prologue_ready();
 cudaError_t launch_prologue(const ProArgs& a, int K, cudaStream_t s);
 constexpr int MAX_SLAB = 256;        // Lambda points per CTA tile at most
 constexpr int MAX_SLAB_GROUP = 512;  // tile points x warps per point at most (the combine's

@@ -94,7 +94,7 @@ gwc_status setup(int dev, unsigned char** out) {
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) return err(GWC_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  e = ensure_gauss_legendre();
+  e = ensure_prologue_ready();
   if (e != cudaSuccess) return err(GWC_E_CUDA, std::string("constant upload: ") + cudaGetErrorString(e));
   g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
   *out = g_scratch_ptr[dev];
