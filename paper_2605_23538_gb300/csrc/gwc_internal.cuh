@@ -58,7 +58,7 @@ enum { P_H0, P_OM, P_ALPHA, P_BETA, P_MMIN, P_MMAX, P_DM, P_MU, P_SIG, P_LAM, P_
 enum { S_H0, S_OM, S_A1, S_LX, S_AL, S_BE, S_MMIN, S_DM, S_MU, S_SIG, S_LU, S_SRD, S_SR,
        S_MU2, S_SIG2, S_LX2 };
 
-// FP32 constants of one Lambda point for the sample kernels (60 floats = 15 float4).
+// FP32 constants of one Lambda point for the sample kernels (68 floats = 17 float4).
 // Fields ending in 2 are in log2 units (the value path works in log2 so that the
 // special-function unit's ex2/lg2 apply directly).
 struct __align__(16) LamF {

@@ -103,3 +103,42 @@ def test_noalloc_out_of_range_pixel_gets_zero_weight(torch, synth):
     rest[bad] = False
     np.testing.assert_array_equal(b_lnw[rest], a_lnw[rest])
     np.testing.assert_array_equal(b_d[:, rest], a_d[:, rest])
+
+
+def test_noalloc_replays_inside_a_cuda_graph(torch, synth):
+    # The use case the entry point exists for: one warm-up call (the per-device set-up
+    # runs there), then the call recorded inside the caller's own CUDA graph capture.  A
+    # second Lambda copied into the captured lam tensor and a replay must give what a
+    # context computes at that Lambda.
+    import paper_2605_23538_gb300 as g
+    w = synth.scaled("noalloc_graph", 4, ("uniform", 200, 800), 4, 256, 3000, "found")
+    cat = synth.catalogue(w)
+    dev = "cuda"
+    samples = torch.tensor(np.stack([cat["m1"], cat["m2"], cat["dl"], cat["lnpe"]], axis=1), device=dev)
+    inj = torch.tensor(np.stack([cat["inj_m1"], cat["inj_m2"], cat["inj_dl"], cat["inj_lnpd"]], axis=1),
+                       device=dev)
+    pix = torch.tensor(cat["pix"], dtype=torch.int32, device=dev)
+    los = torch.tensor(cat["los"], device=dev)
+    lam = torch.tensor(synth.FIDUCIAL, dtype=torch.float64, device=dev)
+    g.sample_terms_noalloc(lam, samples, pix, inj, los, cat["z_max"])
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        n_lnw, n_d, n_c = g.sample_terms_noalloc(lam, samples, pix, inj, los, cat["z_max"])
+    lam2 = synth.lambda_batch(1, purpose=22)[0]
+    lam.copy_(torch.tensor(lam2, dtype=torch.float64))
+    graph.replay()
+    torch.cuda.synchronize()
+    n_lnw, n_d, n_c = n_lnw.cpu().numpy(), n_d.cpu().numpy(), n_c.cpu().numpy()
+    with g.Context(cat, max_K=1) as ctx:
+        r_lnw, r_d, r_c = ctx.sample_terms(torch.tensor(lam2, dtype=torch.float64, device=dev))
+        torch.cuda.synchronize()
+        r_lnw, r_d, r_c = r_lnw.cpu().numpy(), r_d.cpu().numpy(), r_c.cpu().numpy()
+    perm = np.concatenate([g.sample_order(cat), len(cat["pix"]) + g.injection_order(cat)])
+    n_lnw, n_d = n_lnw[perm], n_d[:, perm]
+    np.testing.assert_allclose(n_c, r_c, rtol=1e-12, atol=1e-12)
+    fin = np.isfinite(r_lnw)
+    assert np.array_equal(fin, np.isfinite(n_lnw)) and fin.sum() > 500
+    assert np.max(np.abs(n_lnw[fin] - r_lnw[fin])) <= 2e-5
+    scale = np.abs(r_d[:, fin]) + np.abs(r_d[:, fin]).mean(axis=1, keepdims=True)
+    assert np.all(np.abs(n_d[:, fin] - r_d[:, fin]) <= 2e-4 * scale)
