@@ -797,10 +797,12 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
 // its (max, sums) for each of its Lambda points in shared memory; after the tile the
 // G entries of each Lambda are combined in warp order into one partial per
 // (item, Lambda).
-// Occupancy: the value kernel fits three CTAs per SM (<= 80 registers per thread), the
-// gradient kernel two (<= 128): at three it spills ~340 bytes per thread and runs at
-// half the speed.
-constexpr int MINB_VALUE = 3, MINB_GRAD = 2;
+// Occupancy: three CTAs per SM (<= 80 registers per thread) for both kernels.  The
+// gradient kernel fits there because each warp's Lambda index is formed by a warp
+// reduction (a value the compiler knows to be the same in every lane), so the point's
+// constants are loaded once per warp and kept out of the per-thread registers; with the
+// index as a plain per-thread value the same bound spilled ~400 bytes per thread.
+constexpr int MINB_VALUE = 3, MINB_GRAD = 3;
 
 // One (item, Lambda-slab) unit: stage the item's samples, sweep them for the slab's
 // Lambda points, combine the warp groups' sums into the unit's partials.
@@ -850,7 +852,8 @@ __device__ __forceinline__ void fused_unit(const FusedArgs& A, int unit, float* 
     return __shfl_sync(0xffffffffu, v, 0);
   };
   for (int kk = (G == 1) ? next_k(0) : gidx; kk < nk; kk = next_k(kk)) {
-    const int k = A.order ? A.order[k0 + kk] : k0 + kk;
+    // the same k in every lane of the warp, formed so that the compiler can tell
+    const int k = __reduce_max_sync(0xffffffffu, A.order ? A.order[k0 + kk] : k0 + kk);
     const LamF L = A.lf[k];
     Acc<GRAD, KAHAN, NS> acc;
     if (L.live != 0.f) {
