@@ -137,7 +137,9 @@ typedef struct {
   int32_t chunk;         /* samples per work item, 64..4096 (default 2048) */
   int32_t lambda_tile;   /* Lambda points per CTA tile, 0..256 (0 = default 256); a tile
                             holds at most 512 / lambda_group points */
-  int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = default 1) */
+  int32_t lambda_group;  /* warps of a CTA sharing one Lambda point: 1, 2, 4, 8 (0 = automatic:
+                            1 for a batch of 8 or more points, else the largest power of two
+                            <= 8 / K, so that a small batch keeps every warp of a CTA busy) */
   int32_t cap_per_pixel; /* > 0: keep at most this many samples of each (event, pixel), chosen
                             at random as the paper's memory option does (it quotes 2500);
                             0 = keep all (default).  The kept samples of a group are those
@@ -308,7 +310,7 @@ void gwc_hmc_destroy(gwc_hmc* hmc);   /* NULL is a no-op */
 
 /* Launch-shape autotuner.  Times whole calls (gwc_loglik_grad when want_grad != 0,
  * gwc_loglik otherwise) on the caller's K points d_lambda[K][P] (device) at every
- * shape of chunk in {1024, 2048} x Lambda tile in {16, 32, 64, 128, 256} (clamped to K)
+ * shape of chunk in {1024, 1536, 2048} x Lambda tile in {16, 32, 64, 128, 256} (clamped to K)
  * x warp group in {1, 2, 4, 8} with tile x group <= 512: one untimed call, then two
  * timed with CUDA events on the
  * stream.  The fastest shape becomes the context's chunk, lambda_tile and lambda_group

@@ -152,6 +152,16 @@ constexpr int PROF_SLOTS = 256;
 // one warp per Lambda point: warps then claim points from a shared counter, so uneven
 // per-point work (cuts, early rejections) leaves no warp idle at the unit's barrier
 constexpr int DEFAULT_LAMBDA_GROUP = 1;
+// warps sharing one Lambda point for a batch of K: the context's setting, else the
+// default, except that a batch of fewer than 8 points takes the largest power of two
+// <= 8 / K, so that a small batch (K = 1 in an HMC chain) still keeps every warp of a
+// CTA working (with one warp per point, a K = 1 unit would run on one warp of eight)
+int group_for(const gwc_ctx* c, int K) {
+  if (c->opt.lambda_group > 0) return c->opt.lambda_group;
+  int g = DEFAULT_LAMBDA_GROUP;
+  while (g < WARPS && 2 * g * K <= WARPS) g *= 2;
+  return g;
+}
 // the whole batch in one tile (up to 256 points): each staged chunk serves every point,
 // and a warp's share of points is large enough that the warps finish a unit together
 constexpr int DEFAULT_LAMBDA_TILE = MAX_SLAB;
@@ -255,7 +265,7 @@ bool make_items(const int64_t* offsets, int32_t ne, int64_t ns, int64_t ni, int 
 // launch geometry of the fused kernel for a batch of K points
 void fused_geometry(const gwc_ctx* c, int K, int& slab, int& n_slabs) {
   slab = c->opt.lambda_tile > 0 ? c->opt.lambda_tile : DEFAULT_LAMBDA_TILE;
-  const int group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+  const int group = group_for(c, K);
   slab = std::max(1, std::min(std::min(slab, K), std::min(MAX_SLAB, MAX_SLAB_GROUP / group)));
   n_slabs = (K + slab - 1) / slab;
 }
@@ -346,7 +356,7 @@ gwc_status launch_fused_items(gwc_ctx* c, int32_t K, bool grad, const int32_t* s
   fa.n_items = c->n_items;
   fa.n_slabs = n_slabs;
   fa.slab = slab;
-  fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+  fa.group = group_for(c, K);
   fa.K = K;
   fa.chunk = c->opt.chunk;
   fa.lf = c->lf;
@@ -1236,7 +1246,7 @@ gwc_status gwc_graph_create(gwc_ctx* c, int32_t K, const double* d_lambda, int32
     FusedArgs fa{};
     fa.chunk = c->opt.chunk;
     fa.slab = slab;
-    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+    fa.group = group_for(c, K);
     fa.mp = c->mp ? 1 : 0;
     const bool grad = want_grad != 0, kahan = c->opt.accum == 1;
     const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
@@ -1405,7 +1415,7 @@ gwc_status gwc_hmc_create(gwc_ctx* c, int32_t K, int32_t n_leapfrog, const doubl
     FusedArgs fa{};
     fa.chunk = c->opt.chunk;
     fa.slab = slab;
-    fa.group = c->opt.lambda_group > 0 ? c->opt.lambda_group : DEFAULT_LAMBDA_GROUP;
+    fa.group = group_for(c, K);
     fa.mp = c->mp ? 1 : 0;
     const bool kahan = c->opt.accum == 1;
     const uint64_t key = ((uint64_t)fa.chunk << 20) | ((uint64_t)fa.slab << 8) | ((uint64_t)fa.group << 3) |
@@ -1536,7 +1546,7 @@ gwc_status gwc_autotune(gwc_ctx* c, int32_t K, const double* d_lambda, int32_t w
   int n_tried = 0;
   gwc_status st = GWC_OK;
   c->prof_off = true;
-  const int chunks[] = {1024, 2048};
+  const int chunks[] = {1024, 1536, 2048};
   const int tiles[] = {16, 32, 64, 128, 256};
   const int groups[] = {1, 2, 4, 8};
   for (int chunk : chunks) {

@@ -1111,7 +1111,9 @@ __device__ float kde_kth_dev(const KdeCtx& C, const float4* smp, int64_t v0, int
 
 __global__ void __launch_bounds__(THREADS) k_kde(KdeArgs A) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = blockIdx.x, k = blockIdx.y * WARPS + warp;
+  // the Lambda index by a warp reduction: the compiler then knows it is the same in
+  // every lane and keeps the point's constants out of the per-thread registers
+  const int g = blockIdx.x, k = __reduce_max_sync(0xffffffffu, blockIdx.y * WARPS + warp);
   if (k >= A.K) return;
   const KdeGroup grp = A.groups[g];
   float* out = A.partials + ((size_t)k * A.stride + g) * PSTRIDE;

@@ -219,9 +219,9 @@ def test_autotune_picks_a_timed_shape_and_keeps_parity(torch, g, orc, synth, cat
         graph.close()
         ctx.loglik_plain(lt[:2])                       # plain-path scratch exists before the re-split
         r = ctx.autotune(lt)
-        # tiles 16 .. 256 clamp to 16, 24, 24, 24, 24 at K = 24: 2 chunks x 2 tiles x 4 groups
-        assert r["chunk"] in (1024, 2048) and r["lambda_tile"] in (16, K) and r["lambda_group"] in (1, 2, 4, 8)
-        assert r["n_tried"] == 16 and r["ms"] > 0
+        # tiles 16 .. 256 clamp to 16, 24, 24, 24, 24 at K = 24: 3 chunks x 2 tiles x 4 groups
+        assert r["chunk"] in (1024, 1536, 2048) and r["lambda_tile"] in (16, K) and r["lambda_group"] in (1, 2, 4, 8)
+        assert r["n_tried"] == 24 and r["ms"] > 0
         assert ctx.info()["chunk"] == r["chunk"]
         got = ctx.loglik(lt)
         plain = ctx.loglik_plain(lt[:2], grad=False)
