@@ -34,6 +34,7 @@ METRIC = "posterior-sample×Λ log-lik+grad evals/s at O5 scale vs plain GPU pat
 WORKLOAD = "c3"
 K_LAMBDA = 256
 WORKLOAD_NAMES = {
+    "c1": "c1: 10 events x 1000 samples, 1e4 injection draws (the HMC chain's workload)",
     "c2": "c2: 150 events x U{2000..8000} samples, nside-32 (12288 px) x 2048-z LOS, 1e6 injections",
     "c3": "c3: 2000 events x log-uniform 1k-16k samples (O5-like), nside-64 (49152 px) x 2048-z LOS, "
           "1e7 detected injections",
@@ -497,8 +498,8 @@ def main():
     ap.add_argument("--impl", default="gwc", choices=["gwc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-k", type=int, default=32, help="Lambda points timed on the plain path")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["c2", "c3", "c5"],
-                    help="catalogue size (c3 = the O5-scale headline; c2 for small profiling cases)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["c1", "c2", "c3", "c5"],
+                    help="catalogue size (c3 = the O5-scale headline; c1, c2 for small profiling cases)")
     ap.add_argument("--K", type=int, default=K_LAMBDA, help="Lambda points per call")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-extras", action="store_true",
