@@ -62,7 +62,7 @@ struct gwc_ctx {
   Item* items = nullptr;
   int32_t* sched = nullptr;
   int32_t* ev_item0 = nullptr;
-  double* ev_n = nullptr;
+  double* ln_ev_n = nullptr;      // ln N_i per event (the merge's normaliser)
   LamF* lf = nullptr;
   LamD* ld = nullptr;
   float* tables = nullptr;
@@ -138,7 +138,7 @@ void free_all(gwc_ctx* c) {
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   c->prof_ev.clear();
   void* dev[] = {c->smp, c->pix, c->inj, c->los, c->pbar32, c->pbar64, c->items, c->sched,
-                 c->ev_item0, c->ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->order, c->d_lam, c->d_out,
+                 c->ev_item0, c->ln_ev_n, c->lf, c->ld, c->tables, c->partials, c->counter, c->order, c->d_lam, c->d_out,
                  c->kde_groups, c->kde_ev_group0, c->kde_sched_inj, c->kde_pgrid, c->kde_partials, c->kde_lm,
                  c->d_flags, c->sample_item, c->plain_lw, c->plain_tg};
   for (void* p : dev)
@@ -320,8 +320,8 @@ gwc_status run_merge(gwc_ctx* c, int K, int P, bool grad, double* lnL_event, dou
   ma.ev_item0 = c->ev_item0;
   ma.n_events = c->n_events;
   ma.inj_item0 = c->inj_item0;
-  ma.ev_n = c->ev_n;
-  ma.n_draw = c->n_draw;
+  ma.ln_ev_n = c->ln_ev_n;
+  ma.ln_n_draw = std::log(c->n_draw);
   ma.ld = c->ld;
   ma.neff_min_event = c->opt.neff_min_event;
   ma.neff_min_sel = c->opt.neff_min_sel;
@@ -734,8 +734,8 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
       h_inj[(size_t)q] = make_float4(inj->m1_det[k], inj->m2_det[k], inj->dl_mpc[k], inj->ln_p_draw[k]);
     }
   }
-  std::vector<double> ev_n((size_t)std::max(ne, 1));
-  for (int32_t e = 0; e < ne; ++e) ev_n[(size_t)e] = (double)(ev->offsets[e + 1] - ev->offsets[e]);
+  std::vector<double> ln_ev_n((size_t)std::max(ne, 1));
+  for (int32_t e = 0; e < ne; ++e) ln_ev_n[(size_t)e] = std::log((double)(ev->offsets[e + 1] - ev->offsets[e]));
   c->h_offsets.assign(ev->offsets, ev->offsets + (size_t)ne + 1);
   ItemLayout lay;
   if (!make_items(ev->offsets, ne, ns, ni, o.chunk, lay)) {
@@ -780,7 +780,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(dalloc(c, &c->items, items.size()));
   chk(dalloc(c, &c->sched, sched.size()));
   chk(dalloc(c, &c->ev_item0, ev_item0.size()));
-  chk(dalloc(c, &c->ev_n, ev_n.size()));
+  chk(dalloc(c, &c->ln_ev_n, ln_ev_n.size()));
   chk(dalloc(c, &c->lf, (size_t)o.max_K));
   chk(dalloc(c, &c->ld, (size_t)o.max_K));
   chk(dalloc(c, &c->tables, (size_t)o.max_K * c->tstride));
@@ -817,7 +817,7 @@ gwc_status gwc_create(const gwc_events* ev, const gwc_los* los, const gwc_inject
   chk(cudaMemcpy(c->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(c->sched, sched.data(), sizeof(int32_t) * sched.size(), cudaMemcpyHostToDevice));
   chk(cudaMemcpy(c->ev_item0, ev_item0.data(), sizeof(int32_t) * ev_item0.size(), cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(c->ev_n, ev_n.data(), sizeof(double) * ev_n.size(), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(c->ln_ev_n, ln_ev_n.data(), sizeof(double) * ln_ev_n.size(), cudaMemcpyHostToDevice));
   chk(ensure_prologue_ready());
   if (e != cudaSuccess) {
     std::string msg = std::string("device upload failed: ") + cudaGetErrorString(e);
@@ -933,8 +933,8 @@ gwc_status gwc_loglik_kde(gwc_ctx* c, int32_t K, const double* d_lambda, const g
   ma.ev_item0 = c->kde_ev_group0;
   ma.n_events = c->n_events;
   ma.inj_item0 = (int)(ng + c->inj_item0);
-  ma.ev_n = c->ev_n;
-  ma.n_draw = c->n_draw;
+  ma.ln_ev_n = c->ln_ev_n;
+  ma.ln_n_draw = std::log(c->n_draw);
   ma.ld = c->ld;
   ma.neff_min_event = 0.0;   // the per-pixel cut replaces the per-event one
   ma.neff_min_sel = c->opt.neff_min_sel;

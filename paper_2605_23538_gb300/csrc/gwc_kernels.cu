@@ -1576,7 +1576,7 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     }
     double lnL = -INFINITY, neff = 0.0;
     if (S1 > 0.0) {
-      lnL = M * LN2D + log(S1) - log(A.ev_n[e]) + lamd_c(D);
+      lnL = M * LN2D + log(S1) - A.ln_ev_n[e] + lamd_c(D);
       neff = S1 * S1 / S2;
       if (GRAD) {
         const double iS1 = 1.0 / S1;
@@ -1629,9 +1629,11 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       for (int i = 0; i < NPK; ++i) sG[i] += (double)p[3 + i] * r;
   }
 
-  // ---- fixed-order reductions: butterfly within warps, then warps in order
+  // ---- fixed-order reductions: butterfly within warps, then warps in order.  The five
+  // levels run as a loop, not unrolled: at small K the merge is one CTA whose code runs
+  // once, and the unrolled levels' instruction fetches cost more than the loop
   sumL += cmp;
-#pragma unroll
+#pragma unroll 1
   for (int o = 16; o > 0; o >>= 1) {
     if (GRAD)
 #pragma unroll
@@ -1711,12 +1713,13 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     const bool dead = (fl & 2) != 0;
     double lnxi = -INFINITY, neffs = 0.0;
     if (S1 > 0.0) {
-      lnxi = M * LN2D + log(S1) - log(A.n_draw) + lamd_c(D);
+      lnxi = M * LN2D + log(S1) - A.ln_n_draw + lamd_c(D);
       neffs = S1 * S1 / S2;
     } else {
       flag |= 8;
     }
     if (A.neff_min_sel > 0.0 && !(neffs >= A.neff_min_sel)) flag |= 4;
+    const double iS = S1 > 0.0 ? 1.0 / S1 : 0.0;   // one division for all components
     A.ln_xi[k] = lnxi;
     A.neff_sel[k] = neffs;
     A.flags[k] = flag;
@@ -1724,11 +1727,11 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
     if (GRAD && A.grad_total)
       for (int i = 0; i < NPK; ++i)
         A.grad_total[(size_t)k * NPK + i] =
-            (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] / S1 + lamd_dc(D, i));
+            (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] * iS + lamd_dc(D, i));
     if (A.sum_events) A.sum_events[k] = dead ? -INFINITY : tot;
     for (int i = 0; i < NPK; ++i) {
       if (GRAD && A.grad_events) A.grad_events[(size_t)k * NPK + i] = dead ? 0.0 : gt[i];
-      if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NPK + i] = S1 > 0.0 ? G[i] / S1 + lamd_dc(D, i) : 0.0;
+      if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NPK + i] = S1 > 0.0 ? G[i] * iS + lamd_dc(D, i) : 0.0;
     }
   }
 }

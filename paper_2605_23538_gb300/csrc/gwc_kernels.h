@@ -124,8 +124,8 @@ struct MergeArgs {
   const int32_t* ev_item0;  // [n_events + 1]
   int n_events;
   int inj_item0;
-  const double* ev_n;       // [n_events] samples per event
-  double n_draw;
+  const double* ln_ev_n;    // [n_events] ln of the samples per event, N_i
+  double ln_n_draw;         // ln of the injection draws
   const LamD* ld;
   double neff_min_event;
   double neff_min_sel;
