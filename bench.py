@@ -145,8 +145,14 @@ def alu_roofline(work, seconds, peaks, kernel_mhz):
     t_fp32_all = (work["fp32_method"] + work["fp32_precision"]) / fp32_peak
     sfu_ops = sum(work["sfu"].values())
     t_sfu = sum(work["sfu"][t] / (u[t]["ops_per_s"] * scale) for t in SFU_TYPES)
+    # the issue port: an SM issues one warp-instruction per scheduler per clock, and the
+    # FP32 pipe's measured peak is that rate (32 lanes x 4 schedulers, less a few percent),
+    # so the method's FP32 and special-function instructions together need at least
+    # (FP32 + SFU lane operations) / FP32 peak, whatever each pipe's own rate
+    t_issue = (work["fp32_method"] + sfu_ops) / fp32_peak
     common = {"bound": "alu", "peak_source": "measured (gwc_alu_probe on this GPU)",
               "clock_scale": scale, "t_fp32_ms": t_fp32 * 1e3, "t_sfu_ms": t_sfu * 1e3,
+              "t_issue_fp32_plus_sfu_ms": t_issue * 1e3, "frac_issue_fp32_plus_sfu": t_issue / seconds,
               "t_fp32_with_precision_ms": t_fp32_all * 1e3, "kernel_ms": seconds * 1e3,
               "fp32_method_ops": work["fp32_method"], "fp32_precision_ops": work["fp32_precision"],
               "sfu_ops": work["sfu"]}
