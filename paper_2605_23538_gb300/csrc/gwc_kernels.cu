@@ -236,11 +236,8 @@ template <bool CL> struct ProShape {
 };
 constexpr int PRO_CLUSTER_MAX_K = 32;      // batches up to this size use the cluster shape
 
-// The batch shape's CTAs are bound to two per SM (128 registers, a few spilled values):
-// its FP64 chains leave the pipe idle between dependent instructions, which a second CTA
-// fills (0.63 -> 0.59 ms at K = 256); the cluster shape keeps one CTA per SM.
 template <bool CL>
-__global__ void __launch_bounds__(PRO_THREADS, CL ? 1 : 2) k_prologue(ProArgs A) {
+__global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   namespace cg = cooperative_groups;
   using Sh = ProShape<CL>;
   extern __shared__ double sdyn[];               // 4 * nx doubles: P_n, D_n, then J_n, J'_n
