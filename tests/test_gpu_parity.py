@@ -117,6 +117,16 @@ def test_c1_each_lambda_alone(torch, g, orc, cat_c1, lam_c1):
             compare(got, r, grad=True, label=f"c1 K=1 #{k}")
 
 
+@pytest.mark.parametrize("K", [2, 3, 5])
+def test_c1_small_batches(torch, g, orc, cat_c1, lam_c1, K):
+    # batches of fewer than 8 points split each point's samples over 8/K warps (the
+    # largest power of two: 4 at K = 2, 2 at K = 3, 1 at K = 5); each shape against the oracle
+    ref = orc.loglik(cat_c1, lam_c1[:K], grad=True)
+    with g.Context(cat_c1, max_K=8) as ctx:
+        got = ctx.loglik_grad(dev(torch, lam_c1[:K]))
+        compare(got, ref, grad=True, label=f"c1 K={K}")
+
+
 @pytest.fixture(scope="module")
 def cat_ragged(synth):
     # several chunks per event and ragged tails: 24 events of 300..5000 samples
