@@ -1,13 +1,15 @@
 // gwc_kernels.cu -- CUDA kernels of the dark-siren likelihood (sm_103a).
 //
-//   k_prologue   one CTA per Lambda, FP64: domain check, the d_L(z) inversion table
+//   k_prologue   several CTAs per Lambda (a 16-CTA cluster for small batches, three
+//                CTAs otherwise), FP64: domain check, the d_L(z) inversion table
 //                (Eq. 1), mass-model normalisations and smoothing-window tables, the
 //                redshift-prior normalisation, and the constants each sample needs.
-//   k_fused      the hot loop: a CTA stages a chunk of samples (or injections) in
-//                shared memory once and its warps sweep them for a tile of Lambda
-//                points, each warp accumulating the per-(chunk, Lambda) logsumexp
-//                partial (max, sum w, sum w^2 and, with the gradient, 13 weighted
-//                derivatives) of Eqs. 5-7 online in registers.
+//   k_fused      the hot loop, persistent: a CTA stages a chunk of samples (or
+//                injections) in shared memory once and its warps sweep them for a tile
+//                of Lambda points, each warp accumulating the per-(chunk, Lambda)
+//                logsumexp partial (max, sum w, sum w^2 and, with the gradient, 13 or 16
+//                weighted statistics) of Eqs. 5-7 online in registers.
+//   k_kde        the paper's KDE form of the event term (Eqs. 5-7 with a finite kernel).
 //   k_plain_*    the single-Lambda baseline: per-sample weights written to memory and
 //                reduced in separate passes.
 //   k_merge      one CTA per Lambda, FP64: merges the partials of each event in a fixed
