@@ -101,7 +101,7 @@ def work_from_census(census, grad=True):
 # Throughput probes (gwc_alu_probe): CTAs per launch and iterations per chain, sized so
 # that each launch takes ~10-40 ms
 PROBES = {"ffma": 320_000, "ffma2": 160_000, "ex2": 40_000, "lg2": 40_000, "rcp": 40_000,
-          "rsqrt": 40_000, "dfma": 5_000}
+          "rsqrt": 40_000, "dfma": 5_000, "dfma_lane1": 5_000}
 PROBE_BLOCKS = SMS * 8
 
 

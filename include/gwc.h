@@ -464,10 +464,12 @@ gwc_status gwc_kde_census(gwc_ctx* ctx, int32_t K, const double* d_lambda, const
  *   GWC_UNIT_EX2, GWC_UNIT_LG2, GWC_UNIT_RCP, GWC_UNIT_RSQRT   special-function unit
  *                   approximations (each chain also adds a constant in FP32)
  *   GWC_UNIT_DFMA   FP64 fused multiply-add
+ *   GWC_UNIT_DFMA_LANE1  the same with only lane 0 of each warp active
  * *ops (host, may be NULL) receives the operations the launch performs (a packed FMA
- * counts as two); the caller times the launch, e.g. with CUDA events on the stream. */
+ * counts as two; DFMA_LANE1 counts only the active lanes' operations); the caller times
+ * the launch, e.g. with CUDA events on the stream. */
 enum { GWC_UNIT_FFMA = 0, GWC_UNIT_FFMA2 = 1, GWC_UNIT_EX2 = 2, GWC_UNIT_LG2 = 3,
-       GWC_UNIT_RCP = 4, GWC_UNIT_RSQRT = 5, GWC_UNIT_DFMA = 6 };
+       GWC_UNIT_RCP = 4, GWC_UNIT_RSQRT = 5, GWC_UNIT_DFMA = 6, GWC_UNIT_DFMA_LANE1 = 7 };
 gwc_status gwc_alu_probe(int32_t unit, int32_t blocks, int32_t iters, double* ops, void* stream);
 
 #ifdef __cplusplus

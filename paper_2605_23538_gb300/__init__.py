@@ -407,7 +407,7 @@ def sample_terms_noalloc(lam, samples, pix, injections, los, z_max, n_x_table=51
 
 CENSUS_SLOTS = ("live", "in_range", "mass_order", "support", "value", "value_win1", "value_win2",
                 "weight", "weight_win1", "weight_win2")
-UNITS = {"ffma": 0, "ffma2": 1, "ex2": 2, "lg2": 3, "rcp": 4, "rsqrt": 5, "dfma": 6}
+UNITS = {"ffma": 0, "ffma2": 1, "ex2": 2, "lg2": 3, "rcp": 4, "rsqrt": 5, "dfma": 6, "dfma_lane1": 7}
 
 
 def path_census(ctx, lam, stream=None):

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -1507,18 +1508,76 @@ __device__ __forceinline__ double pow2i(double k) {
 }
 constexpr double LN2D = 0.69314718055994530942;
 
+// The CTA-wide sums of the merge.  Every thread holds NV values; the sum of each column
+// over the CTA's threads is formed in shared memory in a fixed order (a transposed
+// reduction): CB columns at a time, each thread first adds MB rows of one column, then
+// the segment sums are added MB at a time until one is left.  GB300's FP64 pipe charges a
+// warp-instruction the same whatever its active lanes, so this costs a few FP64
+// instructions a column where a warp butterfly would spend five levels of every value
+// in every warp and a serial pass over the warps.  nt (the CTA's threads) is a power of
+// two from 32 to 256; the column sums land in res[NV].
+constexpr int MERGE_CB = 8, MERGE_MB = 8;
+template <int NV>
+__device__ void merge_column_sums(const double (&v)[NV], double* buf, double* res) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+  for (int c0 = 0; c0 < NV; c0 += MERGE_CB) {
+#pragma unroll
+    for (int j = 0; j < MERGE_CB; ++j) buf[tid * MERGE_CB + j] = (c0 + j < NV) ? v[c0 + j] : 0.0;
+    __syncthreads();
+    int nseg = nt;   // rows still to be added, per column
+    while (nseg > 1) {
+      const int g = nseg < MERGE_MB ? nseg : MERGE_MB;
+      const int out = nseg / g;
+      double acc = 0.0;
+      const int j = tid % MERGE_CB, s = tid / MERGE_CB;
+      if (s < out) {
+        acc = buf[(s * g) * MERGE_CB + j];
+        for (int q = 1; q < g; ++q) acc += buf[(s * g + q) * MERGE_CB + j];
+      }
+      __syncthreads();
+      if (s < out) buf[s * MERGE_CB + j] = acc;
+      __syncthreads();
+      nseg = out;
+    }
+    if (tid < MERGE_CB && c0 + tid < NV) res[c0 + tid] = buf[tid];
+    __syncthreads();
+  }
+}
+
+// CTA-wide maximum of an integer per thread, the same in every thread
+__device__ int merge_imax(int x, int* s_i) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  x = __reduce_max_sync(0xffffffffu, x);
+  if (lane == 0) s_i[w] = x;
+  __syncthreads();
+  int m = s_i[0];
+  for (int q = 1; q < nw; ++q) m = max(m, s_i[q]);
+  __syncthreads();
+  return m;
+}
+// an integer-valued reference (or -inf) as an int, and back
+__device__ __forceinline__ int ref_to_int(double m) { return m > -INFINITY ? (int)m : INT_MIN; }
+__device__ __forceinline__ double int_to_ref(int m) { return m == INT_MIN ? -INFINITY : (double)m; }
+
 template <bool GRAD, bool MP>
 __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
-  __shared__ double rs[8][2 + NP_MAX];
-  __shared__ double rsel[8][3 + NP_MAX];
-  __shared__ double rO[8][4];
-  __shared__ int rfail[8];
+  constexpr int NPK = n_params(MP);   // gradient width of the mass model (a constant, so the
+                                      // per-component arrays stay in registers)
+  // per-thread columns: the events' sum of ln L_i, and with the gradient the events'
+  // normalised statistics U (13/16), the events' other-component sums (2); the selection
+  // sums S1, S2 (and G, 13/16) and its other-component sums (2), all rescaled to the
+  // CTA's references
+  constexpr int C_U = 1, C_OE = C_U + (GRAD ? NPK : 0), C_S1 = C_OE + (GRAD ? 2 : 0);
+  constexpr int C_S2 = C_S1 + 1, C_G = C_S2 + 1, C_OS = C_G + (GRAD ? NPK : 0);
+  constexpr int NV = C_OS + (GRAD ? 2 : 0);
+  __shared__ double s_buf[256 * MERGE_CB];
+  __shared__ double s_res[NV];
+  __shared__ int s_i[8], s_ok[8], s_fail[8];
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int nt = blockDim.x, nw = nt >> 5;   // sized to the work by launch_merge
   const LamD D = A.ld[k];
   const int ne = A.n_events;
-  constexpr int NPK = n_params(MP);   // gradient width of the mass model (a constant, so the
-                                      // per-component arrays stay in registers)
   if (D.flag & 1) {
     for (int e = tid; e < ne; e += nt) {
       A.lnL_event[(size_t)k * ne + e] = -INFINITY;
@@ -1540,16 +1599,22 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
   }
   const int P = A.P;
   const float* pk = A.partials + (size_t)k * A.n_items * P * PSTRIDE;
+  double v[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) v[c] = 0.0;
 
-  // ---- events: thread-strided, each event merged in item order
-  double sumL = 0.0, cmp = 0.0, sg[NP_MAX];
-  for (int i = 0; i < NPK; ++i) sg[i] = 0.0;
+  // ---- events: thread-strided, each event merged in item order.  Its gradient
+  // d ln L_i = stats_to_grad(st_i, S1_i) / S1_i + dc is linear in the statistics, so the
+  // CTA sums st_i / S1_i (and the other-component sums / S1_i) and the tail applies
+  // stats_to_grad once, with n_ok (the events with a weight) in place of S1
+  double sumL = 0.0, cmp = 0.0;
   int fail = 0;   // bit 0: an event below the N_eff threshold; bit 1: an event with no weight
+  int n_ok = 0;
   for (int e = tid; e < ne; e += nt) {
     const int s0 = A.ev_item0[e] * P, s1 = A.ev_item0[e + 1] * P;
     double M = -INFINITY;
     for (int s = s0; s < s1; ++s) M = fmax(M, (double)pk[(size_t)s * PSTRIDE]);
-    double S1 = 0.0, S2 = 0.0, G[GRAD ? NP_MAX : 1];
+    double S1 = 0.0, S2 = 0.0, G[GRAD ? NP_MAX : 1], O[2] = {0.0, 0.0};
     if (GRAD)
       for (int i = 0; i < NPK; ++i) G[i] = 0.0;
     if (M > -INFINITY) {
@@ -1562,27 +1627,23 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
         if (GRAD)
           for (int i = 0; i < NPK; ++i) G[i] += (double)p[3 + i] * r;
       }
-      if (GRAD) {
-        double st[NP_MAX];
-        for (int i = 0; i < NPK; ++i) st[i] = G[i];
-        stats_to_grad(st, S1, D, G);
-      }
       if (GRAD && (D.lam_sigma != 0 || D.lam1_sigma != 0))   // other-component sums at the bounds
         for (int s = s0; s < s1; ++s) {
           const float* p = pk + (size_t)s * PSTRIDE;
-          if (D.lam_sigma != 0 && p[PART_MO] > -INFINITY)
-            G[P_LAM] -= D.lam_sigma * (double)p[PART_SO] * pow2i((double)p[PART_MO] - M);
-          if (D.lam1_sigma != 0 && p[PART_MO2] > -INFINITY)
-            G[P_LAM1] -= D.lam1_sigma * (double)p[PART_SO2] * pow2i((double)p[PART_MO2] - M);
+          if (D.lam_sigma != 0 && p[PART_MO] > -INFINITY) O[0] += (double)p[PART_SO] * pow2i((double)p[PART_MO] - M);
+          if (D.lam1_sigma != 0 && p[PART_MO2] > -INFINITY) O[1] += (double)p[PART_SO2] * pow2i((double)p[PART_MO2] - M);
         }
     }
     double lnL = -INFINITY, neff = 0.0;
     if (S1 > 0.0) {
       lnL = M * LN2D + log(S1) - A.ln_ev_n[e] + lamd_c(D);
       neff = S1 * S1 / S2;
-      if (GRAD) {
+      if constexpr (GRAD) {
         const double iS1 = 1.0 / S1;
-        for (int i = 0; i < NPK; ++i) sg[i] += G[i] * iS1 + lamd_dc(D, i);
+#pragma unroll
+        for (int i = 0; i < NPK; ++i) v[C_U + i] = fma(G[i], iS1, v[C_U + i]);
+        v[C_OE] = fma(O[0], iS1, v[C_OE]);
+        v[C_OE + 1] = fma(O[1], iS1, v[C_OE + 1]);
       }
     }
     A.lnL_event[(size_t)k * ne + e] = lnL;
@@ -1592,11 +1653,13 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       fail |= 2;   // a zero-weight event makes the product of Eq. 3 vanish
       continue;
     }
+    ++n_ok;
     // Neumaier-compensated sum in this thread's event order
     const double t = sumL + lnL;
     if (fabs(sumL) >= fabs(lnL)) cmp += (sumL - t) + lnL; else cmp += (lnL - t) + sumL;
     sumL = t;
   }
+  v[0] = sumL + cmp;
 
   // ---- injections: online merge of the injection partials
   double sM = -INFINITY, sS1 = 0.0, sS2 = 0.0, sG[GRAD ? NP_MAX : 1];
@@ -1631,110 +1694,92 @@ __global__ void __launch_bounds__(256, 1) k_merge(MergeArgs A) {
       for (int i = 0; i < NPK; ++i) sG[i] += (double)p[3 + i] * r;
   }
 
-  // ---- fixed-order reductions: butterfly within warps, then warps in order.  The five
-  // levels run as a loop, not unrolled: at small K the merge is one CTA whose code runs
-  // once, and the unrolled levels' instruction fetches cost more than the loop
-  sumL += cmp;
-#pragma unroll 1
-  for (int o = 16; o > 0; o >>= 1) {
-    if (GRAD)
+  // ---- the CTA's references: every partial reference is an integer (or -inf), and so
+  // are the threads' maxima, so the CTA-wide maxima are exact integer maxima; each thread
+  // rescales its sums to them by exact powers of two, which leaves plain column sums
+  const double M = int_to_ref(merge_imax(ref_to_int(sM), s_i));
+  {
+    const double r = (M > -INFINITY && sM > -INFINITY) ? pow2i(sM - M) : 0.0;
+    v[C_S1] = sS1 * r;
+    v[C_S2] = sS2 * r * r;
+    if constexpr (GRAD)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const double x_m = __shfl_xor_sync(0xffffffffu, oM[q], o), x_s = __shfl_xor_sync(0xffffffffu, oS[q], o);
-        const double MO = fmax(oM[q], x_m);
-        if (MO > -INFINITY) { oS[q] = oS[q] * pow2i(oM[q] - MO) + x_s * pow2i(x_m - MO); oM[q] = MO; }
-      }
-    sumL += __shfl_xor_sync(0xffffffffu, sumL, o);
-    fail |= __shfl_xor_sync(0xffffffffu, fail, o);
-    if (GRAD)
-      for (int i = 0; i < NPK; ++i) sg[i] += __shfl_xor_sync(0xffffffffu, sg[i], o);
-    const double oM = __shfl_xor_sync(0xffffffffu, sM, o);
-    const double o1 = __shfl_xor_sync(0xffffffffu, sS1, o);
-    const double o2 = __shfl_xor_sync(0xffffffffu, sS2, o);
-    double oG[GRAD ? NP_MAX : 1];
-    if (GRAD)
-      for (int i = 0; i < NPK; ++i) oG[i] = __shfl_xor_sync(0xffffffffu, sG[i], o);
-    const double M = fmax(sM, oM);
-    if (M > -INFINITY) {
-      const double ra = pow2i(sM - M), rb = pow2i(oM - M);
-      sS1 = sS1 * ra + o1 * rb;
-      sS2 = sS2 * ra * ra + o2 * rb * rb;
-      if (GRAD)
-        for (int i = 0; i < NPK; ++i) sG[i] = sG[i] * ra + oG[i] * rb;
-      sM = M;
+      for (int i = 0; i < NPK; ++i) v[C_G + i] = sG[i] * r;
+  }
+  double MO[2] = {-INFINITY, -INFINITY};
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      MO[q] = int_to_ref(merge_imax(ref_to_int(oM[q]), s_i));
+      v[C_OS + q] = (MO[q] > -INFINITY && oM[q] > -INFINITY) ? oS[q] * pow2i(oM[q] - MO[q]) : 0.0;
     }
   }
-  if (lane == 0) {
-    rs[w][0] = sumL;
-    if (GRAD)
-      for (int i = 0; i < NPK; ++i) rs[w][2 + i] = sg[i];
-    rfail[w] = fail;
-    rsel[w][0] = sM;
-    rsel[w][1] = sS1;
-    rsel[w][2] = sS2;
-    rO[w][0] = oM[0];
-    rO[w][1] = oS[0];
-    rO[w][2] = oM[1];
-    rO[w][3] = oS[1];
-    if (GRAD)
-      for (int i = 0; i < NPK; ++i) rsel[w][3 + i] = sG[i];
+  {
+    const int f = __reduce_or_sync(0xffffffffu, fail), c = __reduce_add_sync(0xffffffffu, n_ok);
+    if (lane == 0) { s_fail[w] = f; s_ok[w] = c; }
   }
-  __syncthreads();
+  merge_column_sums<NV>(v, s_buf, s_res);   // (its barriers also publish s_fail, s_ok)
+  int fl = 0, nok = 0;
+  for (int q = 0; q < nw; ++q) { fl |= s_fail[q]; nok += s_ok[q]; }
+
+  // ---- the tail: ln xi, N_eff,sel, flags and the total; the gradient components one
+  // lane each
+  const double S1 = s_res[C_S1], S2 = s_res[C_S2];
+  int flag = (fl & 1) ? 2 : 0;
+  const bool dead = (fl & 2) != 0;
+  double lnxi = -INFINITY, neffs = 0.0;
+  if (S1 > 0.0) {
+    lnxi = M * LN2D + log(S1) - A.ln_n_draw + lamd_c(D);
+    neffs = S1 * S1 / S2;
+  } else {
+    flag |= 8;
+  }
+  if (A.neff_min_sel > 0.0 && !(neffs >= A.neff_min_sel)) flag |= 4;
+  const double tot = s_res[0];
   if (tid == 0) {
-    double tot = 0.0, gt[NP_MAX], M = -INFINITY, S1 = 0.0, S2 = 0.0, G[NP_MAX];
-    int fl = 0;
-    for (int i = 0; i < NPK; ++i) { gt[i] = 0.0; G[i] = 0.0; }
-    for (int q = 0; q < nw; ++q) {
-      tot += rs[q][0];
-      fl |= rfail[q];
-      if (GRAD)
-        for (int i = 0; i < NPK; ++i) gt[i] += rs[q][2 + i];
-      M = fmax(M, rsel[q][0]);
-    }
-    if (M > -INFINITY) {
-      for (int q = 0; q < nw; ++q) {
-        if (!(rsel[q][0] > -INFINITY)) continue;
-        const double r = pow2i(rsel[q][0] - M);
-        S1 += rsel[q][1] * r;
-        S2 += rsel[q][2] * r * r;
-        if (GRAD)
-          for (int i = 0; i < NPK; ++i) G[i] += rsel[q][3 + i] * r;
-      }
-      if (GRAD) {
-        double st[NP_MAX];
-        for (int i = 0; i < NPK; ++i) st[i] = G[i];
-        stats_to_grad(st, S1, D, G);
-      }
-      if (GRAD)
-        for (int q = 0; q < nw; ++q) {
-          if (D.lam_sigma != 0 && rO[q][0] > -INFINITY) G[P_LAM] -= D.lam_sigma * rO[q][1] * pow2i(rO[q][0] - M);
-          if (D.lam1_sigma != 0 && rO[q][2] > -INFINITY) G[P_LAM1] -= D.lam1_sigma * rO[q][3] * pow2i(rO[q][2] - M);
-        }
-    }
-    int flag = (fl & 1) ? 2 : 0;
-    const bool dead = (fl & 2) != 0;
-    double lnxi = -INFINITY, neffs = 0.0;
-    if (S1 > 0.0) {
-      lnxi = M * LN2D + log(S1) - A.ln_n_draw + lamd_c(D);
-      neffs = S1 * S1 / S2;
-    } else {
-      flag |= 8;
-    }
-    if (A.neff_min_sel > 0.0 && !(neffs >= A.neff_min_sel)) flag |= 4;
-    const double iS = S1 > 0.0 ? 1.0 / S1 : 0.0;   // one division for all components
     A.ln_xi[k] = lnxi;
     A.neff_sel[k] = neffs;
     A.flags[k] = flag;
     if (A.lnL_total) A.lnL_total[k] = (flag || dead) ? -INFINITY : tot - (double)ne * lnxi;
-    if (GRAD && A.grad_total)
-      for (int i = 0; i < NPK; ++i)
-        A.grad_total[(size_t)k * NPK + i] =
-            (flag || dead) ? 0.0 : gt[i] - (double)ne * (G[i] * iS + lamd_dc(D, i));
     if (A.sum_events) A.sum_events[k] = dead ? -INFINITY : tot;
-    for (int i = 0; i < NPK; ++i) {
-      if (GRAD && A.grad_events) A.grad_events[(size_t)k * NPK + i] = dead ? 0.0 : gt[i];
-      if (GRAD && A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NPK + i] = S1 > 0.0 ? G[i] * iS + lamd_dc(D, i) : 0.0;
+  }
+  if constexpr (GRAD) {
+   if (w == 0) {
+    // the events' gradient: stats_to_grad of the summed normalised statistics with n_ok
+    // for S1, the other-component sums, and n_ok times the per-Lambda constant's
+    // derivative; the selection's: stats_to_grad(G, S1) less its other-component sums,
+    // over S1.  Every lane forms both (FP64 instructions cost the same for one lane as
+    // for the warp) and lane i writes component i.
+    double st[NP_MAX], ge[NP_MAX], gs[NP_MAX];
+#pragma unroll
+    for (int i = 0; i < NPK; ++i) st[i] = s_res[C_U + i];
+    stats_to_grad(st, (double)nok, D, ge);
+#pragma unroll
+    for (int i = 0; i < NPK; ++i) st[i] = s_res[C_G + i];
+    stats_to_grad(st, S1, D, gs);
+    if (D.lam_sigma != 0) {
+      ge[P_LAM] -= D.lam_sigma * s_res[C_OE];
+      if (MO[0] > -INFINITY && M > -INFINITY) gs[P_LAM] -= D.lam_sigma * s_res[C_OS] * pow2i(MO[0] - M);
     }
+    if (D.lam1_sigma != 0) {
+      ge[P_LAM1] -= D.lam1_sigma * s_res[C_OE + 1];
+      if (MO[1] > -INFINITY && M > -INFINITY) gs[P_LAM1] -= D.lam1_sigma * s_res[C_OS + 1] * pow2i(MO[1] - M);
+    }
+    const double iS = S1 > 0.0 ? 1.0 / S1 : 0.0;   // one division for all components
+    double gev = 0.0, gsel = 0.0;
+#pragma unroll
+    for (int i = 0; i < NPK; ++i)
+      if (lane == i) {
+        gev = ge[i] + (double)nok * lamd_dc(D, i);
+        gsel = gs[i] * iS + lamd_dc(D, i);
+      }
+    if (lane < NPK) {
+      if (A.grad_total)
+        A.grad_total[(size_t)k * NPK + lane] = (flag || dead) ? 0.0 : gev - (double)ne * gsel;
+      if (A.grad_events) A.grad_events[(size_t)k * NPK + lane] = dead ? 0.0 : gev;
+      if (A.grad_ln_xi) A.grad_ln_xi[(size_t)k * NPK + lane] = S1 > 0.0 ? gsel : 0.0;
+    }
+   }
   }
 }
 
@@ -2084,7 +2129,8 @@ cudaError_t launch_plain_reduce(const PlainArgs& a, bool grad, cudaStream_t s) {
 // butterflies (1/64 of the FP32 rate on this GPU) would otherwise run in all eight.
 cudaError_t launch_merge(const MergeArgs& a, int K, bool grad, cudaStream_t s) {
   const long long work = std::max<long long>(a.n_events, (long long)(a.n_items - a.inj_item0) * a.P);
-  const int threads = (int)std::min<long long>(256, std::max<long long>(32, (work + 31) / 32 * 32));
+  int threads = 32;   // a power of two (the column sums' segments halve evenly)
+  while (threads < 256 && threads < work) threads *= 2;
   if (a.mp) {
     if (grad) k_merge<true, true><<<K, threads, 0, s>>>(a);
     else k_merge<false, true><<<K, threads, 0, s>>>(a);

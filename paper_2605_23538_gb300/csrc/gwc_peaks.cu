@@ -58,13 +58,17 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
 template <int UNIT>
 __global__ void __launch_bounds__(PROBE_THREADS) k_probe(int iters) {
   const float seed = 1e-3f * (float)(threadIdx.x & 7);
-  if constexpr (UNIT == GWC_UNIT_DFMA) {
+  if constexpr (UNIT == GWC_UNIT_DFMA || UNIT == GWC_UNIT_DFMA_LANE1) {
     double a[CHAINS];
 #pragma unroll
     for (int c = 0; c < CHAINS; ++c) a[c] = 0.5 + seed + 0.01 * c;
-    for (int it = 0; it < iters; ++it) {
+    // DFMA_LANE1: only lane 0 of each warp runs the chains (does the FP64 pipe charge a
+    // warp-instruction by its active lanes or as a whole?)
+    if (UNIT == GWC_UNIT_DFMA || (threadIdx.x & 31) == 0) {
+      for (int it = 0; it < iters; ++it) {
 #pragma unroll
-      for (int c = 0; c < CHAINS; ++c) a[c] = fma(a[c], 0.999, 1e-3);
+        for (int c = 0; c < CHAINS; ++c) a[c] = fma(a[c], 0.999, 1e-3);
+      }
     }
     double s = 0.0;
 #pragma unroll
@@ -125,6 +129,10 @@ extern "C" gwc_status gwc_alu_probe(int32_t unit, int32_t blocks, int32_t iters,
     case GWC_UNIT_RCP: k_probe<GWC_UNIT_RCP><<<blocks, PROBE_THREADS, 0, s>>>(iters); break;
     case GWC_UNIT_RSQRT: k_probe<GWC_UNIT_RSQRT><<<blocks, PROBE_THREADS, 0, s>>>(iters); break;
     case GWC_UNIT_DFMA: k_probe<GWC_UNIT_DFMA><<<blocks, PROBE_THREADS, 0, s>>>(iters); break;
+    case GWC_UNIT_DFMA_LANE1:
+      k_probe<GWC_UNIT_DFMA_LANE1><<<blocks, PROBE_THREADS, 0, s>>>(iters);
+      per_op = 1.0 / 32.0;   // one lane of 32 works
+      break;
     default: return probe_err(GWC_E_INVALID, "unknown unit");
   }
   const cudaError_t e = cudaGetLastError();

@@ -58,7 +58,7 @@ def test_census_matches_per_sample_terms(torch, g, synth):
     print("census of the batch:", whole)
 
 
-@pytest.mark.parametrize("unit", ["ffma", "ffma2", "ex2", "lg2", "rcp", "rsqrt", "dfma"])
+@pytest.mark.parametrize("unit", ["ffma", "ffma2", "ex2", "lg2", "rcp", "rsqrt", "dfma", "dfma_lane1"])
 def test_alu_probe_runs(torch, g, unit):
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -67,7 +67,7 @@ def test_alu_probe_runs(torch, g, unit):
     e1.record(s)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
-    assert ops == 152 * 256 * 8 * 200 * (2 if unit == "ffma2" else 1)
+    assert ops == 152 * 256 * 8 * 200 * {"ffma2": 2, "dfma_lane1": 1 / 32}.get(unit, 1)
     assert ms > 0.0
     print(f"{unit}: {ops / (ms / 1e3) / 1e12:.2f} Tops/s on a small launch")
     with pytest.raises(g.GwcError):
