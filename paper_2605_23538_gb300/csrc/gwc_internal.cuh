@@ -32,7 +32,10 @@ constexpr int NW_WIN = 128;          // panels of the smoothing-window tables
 constexpr int PSTRIDE = 23;          // floats per partial sum: m, s1, s2, g[16], mO, sO, mO2, sO2
 constexpr int PART_MO = 3 + NP_MAX, PART_SO = 4 + NP_MAX;     // where mO, sO sit
 constexpr int PART_MO2 = 5 + NP_MAX, PART_SO2 = 6 + NP_MAX;   // the second pair (multi-peak)
-constexpr int NGL = 8;               // Gauss-Legendre nodes per panel in the prologue
+constexpr int NGL = 8;               // Gauss-Legendre nodes per panel of the smoothing window (near
+                                     // m_min its integrand m^beta S(m) changes by many e-folds a panel)
+constexpr int NGL_Z = 4;             // and per panel of the z quadrature (1/E is smooth, the panels
+                                     // narrow: 4 nodes are exact there to far below FP64 rounding)
 
 // The multi-peak model appends the higher-mass Gaussian and the lower one's share of
 // the Gaussian fraction; (mu_g, sigma_g, lambda_peak) are then the low peak's

@@ -29,8 +29,10 @@
 
 namespace gwc {
 
-__constant__ double c_glx[NGL];   // Gauss-Legendre nodes on [-1, 1]
+__constant__ double c_glx[NGL];   // Gauss-Legendre nodes on [-1, 1] (the smoothing window)
 __constant__ double c_glw[NGL];   // and weights
+__constant__ double c_gzx[NGL_Z];  // the same for the z quadrature
+__constant__ double c_gzw[NGL_Z];
 
 // n-point Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on the Legendre
 // polynomial from the three-term recurrence, started at the usual cosine estimate.
@@ -70,10 +72,13 @@ cudaError_t ensure_prologue_ready() {
   if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(mu);
   if (done[dev]) return cudaSuccess;
-  double x[NGL], w[NGL];
+  double x[NGL], w[NGL], xz[NGL_Z], wz[NGL_Z];
   gauss_legendre(NGL, x, w);
+  gauss_legendre(NGL_Z, xz, wz);
   e = cudaMemcpyToSymbol(c_glx, x, sizeof(double) * NGL);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, w, sizeof(double) * NGL);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gzx, xz, sizeof(double) * NGL_Z);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gzw, wz, sizeof(double) * NGL_Z);
   // the small-batch shape is a cluster of 16 CTAs, beyond the portable size of 8
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prologue<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) done[dev] = true;
@@ -183,7 +188,7 @@ __device__ void gauss_mass(double mu, double sig, double mmin, double mmax, doub
 constexpr int PRO_THREADS = 256;
 constexpr int ZPANELS = 256;   // panels of the z quadrature (one per thread)
 
-// (1) I(z) and J(z) = dI/dOm on the ZPANELS + 1 panel edges of [0, zmax] (an 8-point
+// (1) I(z) and J(z) = dI/dOm on the ZPANELS + 1 panel edges of [0, zmax] (an NGL_Z-point
 // Gauss-Legendre rule per panel, one panel per thread, then a block scan), and D(z),
 // D'(z) = I + (1+z)/E there.
 __device__ void z_panels(double om, double zmax, double* sI, double* sJ, double* sD, double* sDp,
@@ -192,12 +197,12 @@ __device__ void z_panels(double om, double zmax, double* sI, double* sJ, double*
   const double hz = zmax / ZPANELS;
   double v[2] = {0.0, 0.0};
   const double za = tid * hz;
-  for (int q = 0; q < NGL; ++q) {
-    const double zq = za + 0.5 * hz * (1.0 + c_glx[q]);
+  for (int q = 0; q < NGL_Z; ++q) {
+    const double zq = za + 0.5 * hz * (1.0 + c_gzx[q]);
     const double u3m1 = zq * (3.0 + zq * (3.0 + zq));   // (1+z)^3 - 1
     const double iE = rsqrt(om * u3m1 + 1.0);            // 1/E
-    v[0] += c_glw[q] * iE;
-    v[1] += c_glw[q] * (-0.5 * u3m1 * (iE * iE * iE));
+    v[0] += c_gzw[q] * iE;
+    v[1] += c_gzw[q] * (-0.5 * u3m1 * (iE * iE * iE));
   }
   v[0] *= 0.5 * hz;
   v[1] *= 0.5 * hz;
@@ -393,11 +398,11 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
       // J are kept from that pass (the step moves z by ~1e-11)
       const double h = z - z0;
       double acc = 0.0, accj = 0.0;
-      for (int q = 0; q < NGL; ++q) {
-        const double zq = z0 + 0.5 * h * (1.0 + c_glx[q]);
+      for (int q = 0; q < NGL_Z; ++q) {
+        const double zq = z0 + 0.5 * h * (1.0 + c_gzx[q]);
         const double u3m1 = zq * (3.0 + zq * (3.0 + zq)), iE = rsqrt(om * u3m1 + 1.0);
-        acc += c_glw[q] * iE;
-        accj += c_glw[q] * (-0.5 * u3m1 * iE * iE * iE);
+        acc += c_gzw[q] * iE;
+        accj += c_gzw[q] * (-0.5 * u3m1 * iE * iE * iE);
       }
       const double Iz = sI[p] + 0.5 * h * acc;
       Jz = sJ[p] + 0.5 * h * accj;
