@@ -142,20 +142,17 @@ __device__ __forceinline__ double sigmoid_d(double a) {
   return a >= 0.0 ? 1.0 / (1.0 + exp(-a)) : exp(a) / (1.0 + exp(a));
 }
 
-// S(m), 1 - S(m) and dS/d(delta_m) inside the smoothing window (0 < mp < dm)
-__device__ __forceinline__ void smooth_d(double mp, double dm, double& S, double& oneS, double& dSddm) {
-  const double f = dm / mp + dm / (mp - dm);
-  if (f > 0.0) {
-    const double e = exp(-f);
-    S = e / (1.0 + e);
-    oneS = 1.0 / (1.0 + e);
-  } else {
-    const double e = exp(f);
-    S = 1.0 / (1.0 + e);
-    oneS = e / (1.0 + e);
-  }
-  const double dfddm = 1.0 / mp + mp / ((mp - dm) * (mp - dm));
-  dSddm = -S * oneS * dfddm;
+// S(m), 1 - S(m) and dS/d(delta_m) inside the smoothing window (0 < mp < dm), from
+// r1 = 1/mp and r2 = 1/(mp - dm), which the callers reuse: on this GPU an FP64 division
+// is a long sequence of FP64 instructions, each costing a whole warp-instruction
+__device__ __forceinline__ void smooth_d(double mp, double dm, double r1, double r2, double& S,
+                                         double& oneS, double& dSddm) {
+  const double f = dm * (r1 + r2);
+  const double e = exp(-fabs(f));
+  const double q = 1.0 / (1.0 + e);
+  S = f > 0.0 ? e * q : q;
+  oneS = f > 0.0 ? q : e * q;
+  dSddm = -S * oneS * (r1 + mp * (r2 * r2));
 }
 
 __device__ bool lambda_ok(const double* L, bool mp) {
@@ -169,19 +166,30 @@ __device__ bool lambda_ok(const double* L, bool mp) {
 
 // ln Z_G = ln of the mass of N(mu, sig) inside [mmin, mmax] (erfc forms without
 // cancellation on either side) and d ln Z_G / d(mu, sig, mmin, mmax) into out[0..4]
+// Called by a whole warp: its lanes evaluate the two erfc and the two exp side by side
+// (the same instructions on arguments chosen by the lane), so the warp runs one erfc
+// and one exp where a single thread would run two of each; lane 0 writes out.
 __device__ void gauss_mass(double mu, double sig, double mmin, double mmax, double* out) {
-  const double A_ = (mmin - mu) / sig, B_ = (mmax - mu) / sig, r2 = 0.70710678118654752440;
-  double ZG;
-  if (A_ > 0.0) ZG = 0.5 * (erfc(A_ * r2) - erfc(B_ * r2));
-  else if (B_ < 0.0) ZG = 0.5 * (erfc(-B_ * r2) - erfc(-A_ * r2));
-  else ZG = 1.0 - 0.5 * (erfc(B_ * r2) + erfc(-A_ * r2));
-  const double phA = 0.39894228040143267794 * exp(-0.5 * A_ * A_);
-  const double phB = 0.39894228040143267794 * exp(-0.5 * B_ * B_);
-  out[0] = log(ZG);
-  out[1] = (phA - phB) / (sig * ZG);                // d ln Z_G / d mu
-  out[2] = (A_ * phA - B_ * phB) / (sig * ZG);      // d ln Z_G / d sigma
-  out[3] = -phA / (sig * ZG);                       // d ln Z_G / d m_min
-  out[4] = phB / (sig * ZG);                        // d ln Z_G / d m_max
+  const int l = threadIdx.x & 31;
+  const double is = 1.0 / sig;
+  const double A_ = (mmin - mu) * is, B_ = (mmax - mu) * is, r2 = 0.70710678118654752440;
+  // erfc arguments: A > 0: erfc(A) - erfc(B); B < 0: erfc(-B) - erfc(-A); else both tails
+  const double x0 = A_ > 0.0 ? A_ : (B_ < 0.0 ? -B_ : B_);
+  const double x1 = A_ > 0.0 ? B_ : -A_;
+  const double ef = erfc((l == 1 ? x1 : x0) * r2);
+  const double E0 = __shfl_sync(0xffffffffu, ef, 0), E1 = __shfl_sync(0xffffffffu, ef, 1);
+  const double ZG = (A_ > 0.0 || B_ < 0.0) ? 0.5 * (E0 - E1) : 1.0 - 0.5 * (E0 + E1);
+  const double ph = 0.39894228040143267794 * exp(-0.5 * (l == 1 ? B_ * B_ : A_ * A_));
+  const double phA = __shfl_sync(0xffffffffu, ph, 0), phB = __shfl_sync(0xffffffffu, ph, 1);
+  const double lz = log(ZG);
+  const double iz = 1.0 / (sig * ZG);
+  if (l == 0) {
+    out[0] = lz;
+    out[1] = (phA - phB) * iz;                // d ln Z_G / d mu
+    out[2] = (A_ * phA - B_ * phB) * iz;      // d ln Z_G / d sigma
+    out[3] = -phA * iz;                       // d ln Z_G / d m_min
+    out[4] = phB * iz;                        // d ln Z_G / d m_max
+  }
 }
 
 // ---------------------------------------------------------------------- prologue
@@ -446,23 +454,41 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   // ---- the window ranks; without CL the single window rank also needs step (1) for xmax
   if constexpr (!CL) z_panels(om, zmax, sI, sJ, sD, sDp, red);
 
-  // ---- (3) mass-model normalisations (Z_P on thread 0, Z_G on thread 32, Z_G2 on
-  //          thread 64, ln(sig sqrt(2 pi)) of the two peaks on threads 96 and 128, so the
-  //          serial chains run in different warps), broadcast through shared memory
-  if (tid == 0) {
+  // ---- (3) mass-model normalisations (Z_P by warp 0, Z_G by warp 1, Z_G2 by warp 2,
+  //          ln(sig sqrt(2 pi)) of the two peaks on threads 96 and 128, so the serial
+  //          chains run in different warps), broadcast through shared memory.  Within a
+  //          warp the lanes evaluate a chain's logarithms, expm1s, divisions and
+  //          exponentials of one level side by side (the same instructions on arguments
+  //          chosen by the lane): each level costs the warp one such evaluation
+  if (tid < 32) {
     // Z_P = int_{mmin}^{mmax} m^-alpha dm = e^{t a} (b - a) phi1(t (b - a)), t = 1 - alpha
-    const double t = 1.0 - alpha, a = log(mmin), b = log(mmax), Lr = b - a, y = t * Lr;
-    const double phi1 = fabs(y) < 1e-5 ? 1.0 + y * (0.5 + y / 6.0) : expm1(y) / y;
-    const double gy = fabs(y) < 1e-5 ? 0.5 + y / 12.0 : 1.0 / (-expm1(-y)) - 1.0 / y;
-    const double lnZP = t * a + log(Lr) + log(phi1);
-    sc[0] = lnZP;
-    sc[1] = -(a + Lr * gy);                          // d ln Z_P / d alpha
-    sc[2] = -exp(-alpha * a - lnZP);                 // d ln Z_P / d m_min
-    sc[3] = exp(-alpha * b - lnZP);                  // d ln Z_P / d m_max
-  } else if (tid == 32) {
+    const int l = tid;
+    const unsigned full = 0xffffffffu;
+    const double t = 1.0 - alpha;
+    const double la = log(l == 1 ? mmax : mmin);                       // a (lane 0), b (lane 1)
+    const double a = __shfl_sync(full, la, 0), b = __shfl_sync(full, la, 1);
+    const double Lr = b - a, y = t * Lr;
+    const bool small = fabs(y) < 1e-5;
+    const double em = expm1(l == 1 ? -y : y);                          // expm1(y), expm1(-y)
+    const double emp = __shfl_sync(full, em, 0), emm = __shfl_sync(full, em, 1);
+    const double dv = 1.0 / (l == 1 ? (small ? 1.0 : -emm) : (small ? 1.0 : y));   // 1/y, -1/expm1(-y)
+    const double iy = __shfl_sync(full, dv, 0), iq = __shfl_sync(full, dv, 1);
+    const double phi1 = small ? 1.0 + y * (0.5 + y * (1.0 / 6.0)) : emp * iy;
+    const double gy = small ? 0.5 + y * (1.0 / 12.0) : iq - iy;
+    const double lg = log(l == 1 ? phi1 : Lr);                         // ln Lr, ln phi1
+    const double lnZP = t * a + __shfl_sync(full, lg, 0) + __shfl_sync(full, lg, 1);
+    const double ex = exp(-alpha * (l == 1 ? b : a) - lnZP);
+    if (l == 0) {
+      sc[0] = lnZP;
+      sc[1] = -(a + Lr * gy);                        // d ln Z_P / d alpha
+      sc[2] = -ex;                                   // d ln Z_P / d m_min
+    } else if (l == 1) {
+      sc[3] = ex;                                    // d ln Z_P / d m_max
+    }
+  } else if (tid < 64) {
     gauss_mass(mu, sig, mmin, mmax, sc + 4);         // Z_G = Phi(B) - Phi(A)
-  } else if (tid == 64 && mp) {
-    gauss_mass(mu2, sig2, mmin, mmax, sc + 9);
+  } else if (tid < 96) {
+    if (mp) gauss_mass(mu2, sig2, mmin, mmax, sc + 9);
   } else if (tid == 96) {
     sc[14] = log(sig) + 0.91893853320467274178;
   } else if (tid == 128) {
@@ -486,6 +512,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const int wr = rank - Sh::WIN0;
   const int pa0 = wr * NW_WIN / Sh::NWIN, pa1 = (wr + 1) * NW_WIN / Sh::NWIN;   // this CTA's panels
   double wv[13] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const double isig = 1.0 / sig, isig2 = mp ? 1.0 / sig2 : 0.0;
   for (int base = 0; base < (pa1 - pa0) * NGL; base += PRO_THREADS) {   // uniform trip count
   const int pl = (base + tid) / NGL, q = tid % NGL;                        // panel (local), node
   double cum[4] = {0.0, 0.0, 0.0, 0.0};   // C, C_beta, J, K at this thread's node
@@ -493,35 +520,35 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const double ma = mmin + (pa0 + pl) * hw;
     {
       const double m = ma + 0.5 * hw * (1.0 + c_glx[q]);
-      const double mp = m - mmin, lm = log(m);
+      const double mr = m - mmin, lm = log(m), im = 1.0 / m;
       double S, oneS, dSddm;
-      smooth_d(mp, dm, S, oneS, dSddm);
+      smooth_d(mr, dm, 1.0 / mr, 1.0 / (mr - dm), S, oneS, dSddm);
       const double mb = exp(beta * lm);
       const double w = c_glw[q] * 0.5 * hw;
       cum[0] += w * mb * S;
       cum[1] += w * mb * lm * S;
-      cum[2] += w * mb / m * S;
+      cum[2] += w * mb * im * S;
       cum[3] += w * mb * dSddm;
       const double P = exp(-alpha * lm - lnZP);
-      const double zg = (m - mu) / sig;
+      const double zg = (m - mu) * isig;
       const double G1 = exp(-0.5 * zg * zg - lnsig2pi - lnZG);
-      const double zg2 = (m - mu2) / sig2;
+      const double zg2 = (m - mu2) * isig2;
       const double G2 = mp ? exp(-0.5 * zg2 * zg2 - lnsig2pi2 - lnZG2) : 0.0;
       const double G = lam1 * G1, Gb = (1.0 - lam1) * G2;   // the two peaks' shares
       const double h = (1.0 - lam) * P + lam * (G + Gb);
       wv[0] += w * h * oneS;
       wv[1] += w * (1.0 - lam) * P * (-lm - dZPa) * oneS;
       wv[2] += w * (G + Gb - P) * oneS;
-      wv[3] += w * lam * G * (zg / sig - dZGmu) * oneS;
-      wv[4] += w * lam * G * ((zg * zg - 1.0) / sig - dZGsig) * oneS;
+      wv[3] += w * lam * G * (zg * isig - dZGmu) * oneS;
+      wv[4] += w * lam * G * ((zg * zg - 1.0) * isig - dZGsig) * oneS;
       wv[5] += w * P * oneS;
       wv[6] += w * G * oneS;
-      wv[7] += w * ((1.0 - lam) * P * (-alpha / m - dZPmin) + lam * G * (-zg / sig - dZGmin) +
-                    lam * Gb * (-zg2 / sig2 - dZG2min)) * oneS;
+      wv[7] += w * ((1.0 - lam) * P * (-alpha * im - dZPmin) + lam * G * (-zg * isig - dZGmin) +
+                    lam * Gb * (-zg2 * isig2 - dZG2min)) * oneS;
       wv[8] += w * (-h * dSddm);
       if (mp) {
-        wv[9] += w * lam * Gb * (zg2 / sig2 - dZG2mu) * oneS;
-        wv[10] += w * lam * Gb * ((zg2 * zg2 - 1.0) / sig2 - dZG2sig) * oneS;
+        wv[9] += w * lam * Gb * (zg2 * isig2 - dZG2mu) * oneS;
+        wv[10] += w * lam * Gb * ((zg2 * zg2 - 1.0) * isig2 - dZG2sig) * oneS;
         wv[11] += w * lam * (G1 - G2) * oneS;
         wv[12] += w * Gb * oneS;
       }
@@ -576,26 +603,30 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     qv[2] = 1.0 / mmin;
   }
   if (eval && node > 0 && dm > 0.0) {
-    const double mp = node * hw, m = mmin + mp, lm = log(m);
+    // with r1 = 1/m', r2 = 1/(m' - dm), im = 1/m, 1/g and 1/R_C: five divisions where the
+    // expressions written out would take about twenty (each a long FP64 sequence here)
+    const double mr = node * hw, m = mmin + mr, lm = log(m), im = 1.0 / m, r1 = 1.0 / mr;
     double S = 1.0, oneS = 0.0, dSddm = 0.0, dlnS = 0.0, dSS = 0.0;
     if (node < NW_WIN) {
-      smooth_d(mp, dm, S, oneS, dSddm);
-      dlnS = oneS * dm * (1.0 / (mp * mp) + 1.0 / ((mp - dm) * (mp - dm)));
-      dSS = -oneS * (1.0 / mp + mp / ((mp - dm) * (mp - dm)));   // (dS/d delta_m) / S
+      const double r2 = 1.0 / (mr - dm);
+      smooth_d(mr, dm, r1, r2, S, oneS, dSddm);
+      dlnS = oneS * dm * (r1 * r1 + r2 * r2);
+      dSS = -oneS * (r1 + mr * (r2 * r2));   // (dS/d delta_m) / S
     }
-    const double gg = exp(beta * lm) * S;
-    const double gl = beta / m + dlnS;     // g'/g
-    const double Rc = scum[0][node] / gg, Rb = scum[1][node] / gg;
-    const double Rj = scum[2][node] / gg, Rk = scum[3][node] / gg;
-    const double dRc = 1.0 - Rc * gl, dRb = lm - Rb * gl, dRj = 1.0 / m - Rj * gl, dRk = dSS - Rk * gl;
-    qv[0] = Rc * dm / (mp * mp);
-    qv[1] = Rb / Rc;
-    qv[2] = Rj / Rc;
-    qv[3] = Rk * dm / mp;
-    qd[0] = dm * (dRc / (mp * mp) - 2.0 * Rc / (mp * mp * mp));
-    qd[1] = (dRb - qv[1] * dRc) / Rc;
-    qd[2] = (dRj - qv[2] * dRc) / Rc;
-    qd[3] = dm * (dRk / mp - Rk / (mp * mp));
+    const double ig = 1.0 / (exp(beta * lm) * S);
+    const double gl = beta * im + dlnS;     // g'/g
+    const double Rc = scum[0][node] * ig, Rb = scum[1][node] * ig;
+    const double Rj = scum[2][node] * ig, Rk = scum[3][node] * ig;
+    const double iRc = 1.0 / Rc;
+    const double dRc = 1.0 - Rc * gl, dRb = lm - Rb * gl, dRj = im - Rj * gl, dRk = dSS - Rk * gl;
+    qv[0] = Rc * dm * (r1 * r1);
+    qv[1] = Rb * iRc;
+    qv[2] = Rj * iRc;
+    qv[3] = Rk * dm * r1;
+    qd[0] = dm * (dRc * (r1 * r1) - 2.0 * Rc * (r1 * r1 * r1));
+    qd[1] = (dRb - qv[1] * dRc) * iRc;
+    qd[2] = (dRj - qv[2] * dRc) * iRc;
+    qd[3] = dm * (dRk * r1 - Rk * (r1 * r1));
   }
   if (eval)
     for (int i = 0; i < 4; ++i) sq[i][node] = qv[i];
@@ -632,8 +663,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   //      chosen by the lane) before thread 0 assembles the fields into s_tv[]:
   //        [0..5]   log of lam lam1, lam, mw, lam1, 1 - W, H0/c       [6, 7] log1p(-lam), log1p(-lam1)
   //        [8]      exp(eps log mw)
-  //        [9..23]  1/sig, 1/sig2, 1/eps, N_w/dm, 1/dm, 1/H0, 1/(1+zp), 1/lam, 1/(1-lam),
-  //                 1/(1-W), 1/lam1, 1/(1-lam1), gpk/(1+zp), (H0/c)/dx, zmax/(nz-1)
+  //        [9..24]  1/sig, 1/sig2, 1/eps, N_w/dm, 1/dm, 1/H0, 1/(1+zp), 1/lam, 1/(1-lam),
+  //                 1/(1-W), 1/lam1, 1/(1-lam1), gpk/(1+zp), (H0/c)/dx, zmax/(nz-1), 1/mw
   const double mw = mmin + dm, eps = 1.0 + beta;
   if (tid < 32) {
     const int l = tid;
@@ -650,12 +681,12 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const double den = l == 9 ? sig : l == 10 ? sig2 : l == 11 ? eps : l == 12 ? dm : l == 13 ? dm
                      : l == 14 ? H0 : l == 15 ? 1.0 + zp : l == 16 ? lam : l == 17 ? 1.0 - lam
                      : l == 18 ? 1.0 - W0 : l == 19 ? lam1 : l == 20 ? 1.0 - lam1 : l == 21 ? 1.0 + zp
-                     : l == 22 ? dx : l == 23 ? (double)(nz - 1) : 1.0;
+                     : l == 22 ? dx : l == 23 ? (double)(nz - 1) : l == 24 ? mw : 1.0;
     const double vdiv = num / den;
     if (l < 6) s_tv[l] = vlog;
     if (l < 2) s_tv[6 + l] = vlog1p;
     if (l == 2) s_tv[8] = vexp;
-    if (l >= 9 && l < 24) s_tv[l] = vdiv;
+    if (l >= 9 && l < 25) s_tv[l] = vdiv;
   }
   __syncwarp();
   if (tid == 0) {
@@ -713,7 +744,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const double mw1b = s_tv[8];
     f.beta_small = small ? 1.f : 0.f;
     f.inv_eps_b = small ? 0.f : (float)s_tv[11];
-    f.C0 = small ? 0.f : (float)(Cw - mw1b / eps);
+    f.C0 = small ? 0.f : (float)(Cw - mw1b * s_tv[11]);
     f.Cw = (float)Cw;
     f.mw1b = (float)mw1b;
     f.lmw = (float)s_tv[2];
@@ -741,7 +772,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     f.dZGmin = (float)dZGmin;
     f.dZGmax = (float)dZGmax;
     f.Cwb = (float)Cwb;
-    f.Cmin = (float)(beta * Jw - mw1b / mw);
+    f.Cmin = (float)(beta * Jw - mw1b * s_tv[24]);
     f.Kw = (float)Kw;
     f.la0_2 = (float)(-lnZP * LOG2E - R);
     f.lb0_2 = (float)((-lnsig2pi - lnZG) * LOG2E - R);
