@@ -648,7 +648,6 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     s_wsum[tid] = v;
   }
   const double xmax = *peer(&sD[ZPANELS], 0);   // D(z_max): rank 0's with CL, else this CTA's
-  const double dx = xmax / (nx - 1);
   __syncthreads();
   for (int i = 0; i < 13; ++i) wv[i] = s_wsum[i];
   // Z_m1 = 1 - W with W = wv[0]; d ln Z_m1 / d theta = -dW/d theta / Z_m1
@@ -658,37 +657,44 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
   const double dWmu2 = wv[9], dWsig2 = wv[10], dWl1 = wv[11];
 
   // ---- (6) constants.  Their logarithms, exponentials and divisions are long FP64
-  //      latency chains; the lanes of warp 0 evaluate them side by side (the same
+  //      sequences; the lanes of a warp evaluate one kind of them side by side (the same
   //      expressions, one per lane, all lanes running the same instructions on arguments
-  //      chosen by the lane) before thread 0 assembles the fields into s_tv[]:
+  //      chosen by the lane), the logarithms in warp 0, log1p in warp 1, the divisions in
+  //      warp 2 and mw^(1+beta) in warp 3, so that the four run on the SM's four
+  //      schedulers at once, before thread 0 assembles the fields into s_tv[]:
   //        [0..5]   log of lam lam1, lam, mw, lam1, 1 - W, H0/c       [6, 7] log1p(-lam), log1p(-lam1)
   //        [8]      exp(eps log mw)
   //        [9..24]  1/sig, 1/sig2, 1/eps, N_w/dm, 1/dm, 1/H0, 1/(1+zp), 1/lam, 1/(1-lam),
   //                 1/(1-W), 1/lam1, 1/(1-lam1), gpk/(1+zp), (H0/c)/dx, zmax/(nz-1), 1/mw
   const double mw = mmin + dm, eps = 1.0 + beta;
-  if (tid < 32) {
-    const int l = tid;
+  const double h0c = H0 * (1.0 / C_KMS);   // H0/c (within an ulp of the quotient)
+  if (tid < 128) {
+    const int l = tid & 31, wq = tid >> 5;
     const double W0 = wv[0];
-    const double la = l == 0 ? lam * lam1 : l == 1 ? lam : l == 2 ? mw : l == 3 ? lam1 : l == 4 ? 1.0 - W0
-                    : l == 5 ? H0 / C_KMS : 1.0;
-    const double lb = l == 0 ? -lam : l == 1 ? -lam1 : 0.0;
-    const double vlog = log(la), vlog1p = log1p(lb);
-    const double vexp = exp(l == 2 ? eps * vlog : 0.0);
-    // numerators and denominators of the divisions (lane 22's numerator is itself H0/c)
-    const double num0 = l == 22 ? H0 : 1.0, den0 = l == 22 ? C_KMS : 1.0;
-    const double q0 = num0 / den0;
-    const double num = l == 12 ? (double)NW_WIN : l == 21 ? gpk : l == 22 ? q0 : l == 23 ? zmax : 1.0;
-    const double den = l == 9 ? sig : l == 10 ? sig2 : l == 11 ? eps : l == 12 ? dm : l == 13 ? dm
-                     : l == 14 ? H0 : l == 15 ? 1.0 + zp : l == 16 ? lam : l == 17 ? 1.0 - lam
-                     : l == 18 ? 1.0 - W0 : l == 19 ? lam1 : l == 20 ? 1.0 - lam1 : l == 21 ? 1.0 + zp
-                     : l == 22 ? dx : l == 23 ? (double)(nz - 1) : l == 24 ? mw : 1.0;
-    const double vdiv = num / den;
-    if (l < 6) s_tv[l] = vlog;
-    if (l < 2) s_tv[6 + l] = vlog1p;
-    if (l == 2) s_tv[8] = vexp;
-    if (l >= 9 && l < 25) s_tv[l] = vdiv;
+    if (wq == 0) {
+      const double la = l == 0 ? lam * lam1 : l == 1 ? lam : l == 2 ? mw : l == 3 ? lam1 : l == 4 ? 1.0 - W0
+                      : l == 5 ? h0c : 1.0;
+      const double vlog = log(la);
+      if (l < 6) s_tv[l] = vlog;
+    } else if (wq == 1) {
+      const double vlog1p = log1p(l == 0 ? -lam : l == 1 ? -lam1 : 0.0);
+      if (l < 2) s_tv[6 + l] = vlog1p;
+    } else if (wq == 2) {
+      // lane 22: (H0/c)/dx = (H0/c)(nx - 1)/xmax
+      const double num = l == 12 ? (double)NW_WIN : l == 21 ? gpk : l == 22 ? h0c * (double)(nx - 1)
+                       : l == 23 ? zmax : 1.0;
+      const double den = l == 9 ? sig : l == 10 ? sig2 : l == 11 ? eps : l == 12 ? dm : l == 13 ? dm
+                       : l == 14 ? H0 : l == 15 ? 1.0 + zp : l == 16 ? lam : l == 17 ? 1.0 - lam
+                       : l == 18 ? 1.0 - W0 : l == 19 ? lam1 : l == 20 ? 1.0 - lam1 : l == 21 ? 1.0 + zp
+                       : l == 22 ? xmax : l == 23 ? (double)(nz - 1) : l == 24 ? mw : 1.0;
+      const double vdiv = num / den;
+      if (l >= 9 && l < 25) s_tv[l] = vdiv;
+    } else {
+      const double vexp = exp(eps * log(mw));
+      if (l == 0) s_tv[8] = vexp;
+    }
   }
-  __syncwarp();
+  __syncthreads();
   if (tid == 0) {
     const double Cw = dm > 0.0 ? scum[0][NW_WIN] : 0.0;
     const double Cwb = dm > 0.0 ? scum[1][NW_WIN] : 0.0;
@@ -697,8 +703,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const double LOG2E = 1.44269504088896340736;
     LamF f;
     memset(&f, 0, sizeof(f));
-    f.H0c = (float)(H0 / C_KMS);
-    f.H0c_lo = (float)(H0 / C_KMS - (double)f.H0c);
+    f.H0c = (float)h0c;
+    f.H0c_lo = (float)(h0c - (double)f.H0c);
     const double sxa = s_tv[22];
     f.sxa = (float)sxa;
     f.sxa_lo = (float)(sxa - (double)f.sxa);
