@@ -2,13 +2,16 @@
 //
 // Device layout built by gwc_create:
 //   samples      float4 {m1_det, m2_det, d_L, ln pi_PE} + int32 pixel, sorted by event
-//                and, within an event, by pixel (so a chunk touches few LOS rows)
-//   injections   float4 {m1_det, m2_det, d_L, ln p_draw}
+//                and, within an event, by (pixel, d_L) (a chunk touches few LOS rows, and
+//                a warp's lanes read neighbouring table nodes and LOS cells)
+//   injections   float4 {m1_det, m2_det, d_L, ln p_draw}, sorted by d_L, then each block
+//                of 256 by m1_det (lanes outside the mass support gather into whole warps)
 //   LOS table    [n_pix][n_z] float (or bfloat16); the pixel mean in float and double
 //   work items   runs of <= chunk samples of one event (events split evenly), then runs
 //                of injections; launched largest first
 // Per call (sized for max_K at create, so calls allocate nothing):
-//   per-Lambda constants and tables, and the partial sums [K][items][parts][16].
+//   per-Lambda constants and tables, the batch's order by H0, and the partial sums
+//   [K][items][PSTRIDE floats].
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
