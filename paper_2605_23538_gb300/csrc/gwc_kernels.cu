@@ -575,7 +575,34 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prologue(ProArgs A) {
     const int loc = tid - r * NW_WIN / Sh::NWIN;
     for (int i = 0; i < 4; ++i) cum[i] = o[i * NW_WIN + loc];
   }
-  block_scan<4>(cum, red);
+  // the scan over the NW_WIN panels in the warps that hold them (the others would add
+  // zeros, and an FP64 warp-instruction costs the same with no useful lane); the same
+  // order of additions as block_scan, so the same sums
+  static_assert(NW_WIN % 32 == 0 && NW_WIN <= PRO_THREADS, "panel scan layout");
+  {
+    const int lane = tid & 31, w = tid >> 5;
+    if (tid < NW_WIN) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const double y = __shfl_up_sync(0xffffffffu, cum[i], o);
+          if (lane >= o) cum[i] += y;
+        }
+      }
+      if (lane == 31)
+        for (int i = 0; i < 4; ++i) red[i * 32 + w] = cum[i];
+    }
+    __syncthreads();
+    if (tid < NW_WIN) {
+      for (int i = 0; i < 4; ++i) {
+        double off = 0.0;
+        for (int k = 0; k < w; ++k) off += red[i * 32 + k];
+        cum[i] += off;
+      }
+    }
+    __syncthreads();
+  }
 
   // window tables at nodes m_k = mmin + k hw: with R_X = X / (m^beta S(m)),
   //   Q_C = R_C dm / m'^2, Q_beta = R_beta / R_C, Q_J = R_J / R_C, Q_K = R_K dm / m'
